@@ -1,0 +1,353 @@
+"""ctypes front end of the FP64 CPU oracle (``liboracle.so``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg call this; the library never does.  It imports
+nothing from the CUDA package.  Inputs are the float32 arrays and records of
+``hdof_inputs``, widened exactly to float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hdof_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False, openmp: bool = True) -> str:
+    """Compile liboracle.so with the host C compiler (plain C99, FP64)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "hdof_oracle.h"))):
+        return _LIB_PATH
+    cmd = ["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
+           _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    if openmp:
+        cmd.insert(1, "-fopenmp")
+    subprocess.check_call(cmd)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+class Cam(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("right", C.c_double * 3), ("up", C.c_double * 3),
+                ("fwd", C.c_double * 3), ("tan_half_fovy", C.c_double), ("width", C.c_int32),
+                ("height", C.c_int32), ("jitter", C.c_double * 2)]
+
+
+class Lens(C.Structure):
+    _fields_ = [("focus_dist", C.c_double), ("aperture_radius", C.c_double),
+                ("focal_length", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("gauss_sigma", C.c_double), ("edge_tau", C.c_double), ("tile", C.c_int32),
+                ("dilate", C.c_int32), ("spp_max", C.c_int32), ("variance_on", C.c_int32),
+                ("var_tau", C.c_double), ("var_scale", C.c_double), ("hlen_young", C.c_int32),
+                ("seed", C.c_uint32), ("frame", C.c_int32), ("view", C.c_int32),
+                ("k_ambient", C.c_double), ("n_lights", C.c_int32),
+                ("light_dir", (C.c_double * 3) * 4), ("light_E", C.c_double * 4),
+                ("miss_dist", C.c_double), ("ema_alpha", C.c_double), ("camera_moved", C.c_int32),
+                ("r_s", C.c_double), ("var_ref", C.c_double), ("r_max", C.c_double),
+                ("kz_rel", C.c_double), ("h_tau", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB_PATH)
+        dp, ip, up8, vp = (C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
+                           C.c_void_p)
+        u32p = C.POINTER(C.c_uint32)
+        L.orc_philox.argtypes = [u32p, u32p, u32p]
+        L.orc_philox_limb.argtypes = [u32p, u32p, u32p]
+        L.orc_coc.argtypes = [C.c_double, C.POINTER(Lens), C.c_int32, C.c_double]
+        L.orc_coc.restype = C.c_double
+        L.orc_pinhole_dir.argtypes = [C.POINTER(Cam), C.c_double, C.c_double, dp]
+        L.orc_project.argtypes = [C.POINTER(Cam), dp, dp]
+        L.orc_project.restype = C.c_int
+        L.orc_scene_create.argtypes = [C.c_int32, dp, dp, dp]
+        L.orc_scene_create.restype = vp
+        L.orc_scene_destroy.argtypes = [vp]
+        L.orc_intersect_tri.argtypes = [dp, dp, dp, dp, dp]
+        L.orc_intersect_tri.restype = C.c_int32
+        L.orc_closest_hit.argtypes = [vp, dp, dp, C.c_int32, dp, dp]
+        L.orc_closest_hit.restype = C.c_int32
+        L.orc_closest_hits.argtypes = [vp, C.c_int32, dp, dp, C.c_int32, ip, dp]
+        L.orc_gbuffer.argtypes = [vp, C.POINTER(Cam), C.POINTER(Cam), C.POINTER(Params), dp, dp, dp, ip]
+        L.orc_gaussian_weights.argtypes = [C.c_double, dp]
+        L.orc_mask.argtypes = [C.c_int32, C.c_int32, dp, dp, dp, up8, C.POINTER(Params), up8, up8, dp]
+        L.orc_trace.argtypes = [vp, C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), up8, dp,
+                                C.c_int32, ip]
+        L.orc_temporal.argtypes = [C.POINTER(Cam), C.POINTER(Cam), C.POINTER(Params), dp, up8, dp, dp,
+                                   dp, dp, dp, up8, dp, dp, dp, up8, dp, dp]
+        L.orc_spatial.argtypes = [C.c_int32, C.c_int32, C.POINTER(Params), dp, up8, dp, up8, dp,
+                                  C.c_int32, ip]
+        L.orc_postfilter.argtypes = [C.c_int32, C.c_int32, C.POINTER(Lens), C.c_double,
+                                     C.POINTER(Params), dp, dp, dp, C.c_int32, ip]
+        L.orc_composite.argtypes = [C.c_int32, C.c_int32, C.POINTER(Lens), C.c_double,
+                                    C.POINTER(Params), dp, dp, up8, dp, dp, dp, dp, dp]
+        L.orc_num_threads.restype = C.c_int32
+        L.orc_disk_area.argtypes = [C.c_double]
+        L.orc_disk_area.restype = C.c_double
+        _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------
+# marshalling
+# --------------------------------------------------------------------------
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _u8(a):
+    a = np.ascontiguousarray(a, dtype=np.uint8)
+    return a, a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def cam(c) -> Cam:
+    o = Cam()
+    o.pos[:] = c.pos
+    o.right[:] = c.right
+    o.up[:] = c.up
+    o.fwd[:] = c.fwd
+    o.tan_half_fovy = c.tan_half_fovy
+    o.width, o.height = c.width, c.height
+    o.jitter[:] = c.jitter
+    return o
+
+
+def lens(l) -> Lens:
+    return Lens(l.focus_dist, l.aperture_radius, l.focal_length)
+
+
+def params(p) -> Params:
+    o = Params()
+    for name in ("gauss_sigma", "edge_tau", "tile", "dilate", "spp_max", "variance_on", "var_tau",
+                 "var_scale", "hlen_young", "seed", "frame", "view", "k_ambient", "miss_dist",
+                 "ema_alpha", "camera_moved", "r_s", "var_ref", "r_max", "kz_rel", "h_tau"):
+        setattr(o, name, getattr(p, name))
+    lights = p.unit_lights()
+    o.n_lights = len(lights)
+    for k, (d, e) in enumerate(zip(lights, p.light_E)):
+        o.light_dir[k][:] = d
+        o.light_E[k] = float(np.float32(e))
+    return o
+
+
+class OScene:
+    """Oracle scene: triangle soup + its own object-median BVH."""
+
+    def __init__(self, scene):
+        self.n = scene.n_tris
+        self._v, pv = _d(scene.tri_verts())
+        self._m, pm = _d(scene.mat)
+        self._uv, pu = _d(scene.uv)
+        self.h = lib().orc_scene_create(self.n, pv, pm, pu)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_scene_destroy(self.h)
+            self.h = None
+
+    def closest_hits(self, org, dirs, use_bvh=True):
+        org, po = _d(np.asarray(org).reshape(-1, 3))
+        dirs, pd = _d(np.asarray(dirs).reshape(-1, 3))
+        n = org.shape[0]
+        ids = np.empty(n, np.int32)
+        ts = np.empty(n, np.float64)
+        lib().orc_closest_hits(self.h, n, po, pd, int(use_bvh), ids.ctypes.data_as(C.POINTER(C.c_int32)),
+                               ts.ctypes.data_as(C.POINTER(C.c_double)))
+        return ids, ts
+
+
+def philox(ctr, key, limb=False):
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (C.c_uint32 * 4)()
+    (lib().orc_philox_limb if limb else lib().orc_philox)(c, k, o)
+    return list(o)
+
+
+def coc(z, lens_, height, tan_half_fovy):
+    return lib().orc_coc(float(z), C.byref(lens(lens_)), int(height), float(tan_half_fovy))
+
+
+def pinhole_dir(cam_, sx, sy):
+    d = (C.c_double * 3)()
+    lib().orc_pinhole_dir(C.byref(cam(cam_)), float(sx), float(sy), d)
+    return np.array(list(d))
+
+
+def project(cam_, P):
+    Pv = (C.c_double * 3)(*[float(x) for x in P])
+    u = (C.c_double * 2)()
+    ok = lib().orc_project(C.byref(cam(cam_)), Pv, u)
+    return (np.array(list(u)) if ok else None)
+
+
+def gaussian_weights(sigma):
+    w = (C.c_double * 5)()
+    lib().orc_gaussian_weights(float(sigma), w)
+    return np.array(list(w))
+
+
+def gbuffer(oscene: OScene, cam_, prev_cam, params_):
+    W, H = cam_.width, cam_.height
+    nd = np.empty((H, W, 4))
+    col = np.empty((H, W, 4))
+    mv = np.empty((H, W, 2))
+    tri = np.empty((H, W), np.int32)
+    lib().orc_gbuffer(oscene.h, C.byref(cam(cam_)), C.byref(cam(prev_cam)), C.byref(params(params_)),
+                      _d(nd)[1], _d(col)[1], _d(mv)[1], _i32(tri)[1])
+    return dict(nd=nd, col=col, mv=mv, tri=tri)
+
+
+def mask(nd, mv, params_, hist_mom=None, hist_hlen=None):
+    H, W = nd.shape[:2]
+    nd, pnd = _d(nd)
+    mv, pmv = _d(mv)
+    edge = np.empty((H, W), np.uint8)
+    spp = np.empty((H, W), np.uint8)
+    em = np.empty((H, W))
+    if hist_mom is not None:
+        hm, phm = _d(hist_mom)
+        hh, phh = _u8(hist_hlen)
+    else:
+        phm, phh = None, None
+    lib().orc_mask(W, H, pnd, pmv, phm, phh, C.byref(params(params_)), _u8(edge)[1], _u8(spp)[1],
+                   _d(em)[1])
+    return dict(edge=edge, spp=spp, emetric=em)
+
+
+def trace(oscene: OScene, cam_, lens_, params_, spp, pix=None):
+    """Per-pixel normalised trace output rt [H,W,12] (or [n_pix,12] for a pixel list)."""
+    H, W = cam_.height, cam_.width
+    spp, pspp = _u8(spp)
+    if pix is None:
+        rt = np.empty((H, W, 12))
+        lib().orc_trace(oscene.h, C.byref(cam(cam_)), C.byref(lens(lens_)), C.byref(params(params_)),
+                        pspp, _d(rt)[1], 0, None)
+    else:
+        pix, ppix = _i32(pix)
+        rt = np.empty((pix.shape[0], 12))
+        lib().orc_trace(oscene.h, C.byref(cam(cam_)), C.byref(lens(lens_)), C.byref(params(params_)),
+                        pspp, _d(rt)[1], int(pix.shape[0]), ppix)
+    return rt
+
+
+def empty_history(W, H):
+    return dict(near=np.zeros((H, W, 4)), far=np.zeros((H, W, 4)), mom=np.zeros((H, W, 2)),
+                hlen=np.zeros((H, W), np.uint8))
+
+
+def temporal(cam_, prev_cam, params_, rt, spp, nd, mv, hist):
+    H, W = cam_.height, cam_.width
+    out = empty_history(W, H)
+    crt = np.empty((H, W, 4))
+    hacc = np.empty((H, W))
+    args = [_d(rt)[1], _u8(spp)[1], _d(nd)[1], _d(mv)[1]]
+    hn, hf, hm, hh = (_d(hist["near"]), _d(hist["far"]), _d(hist["mom"]), _u8(hist["hlen"]))
+    lib().orc_temporal(C.byref(cam(cam_)), C.byref(cam(prev_cam)), C.byref(params(params_)), *args,
+                       hn[1], hf[1], hm[1], hh[1], _d(out["near"])[1], _d(out["far"])[1],
+                       _d(out["mom"])[1], _u8(out["hlen"])[1], _d(crt)[1], _d(hacc)[1])
+    return out, crt, hacc
+
+
+def spatial(params_, crt, spp, mom, hlen, pix=None):
+    H, W = spp.shape
+    crt, pc = _d(crt)
+    spp, ps = _u8(spp)
+    mom, pm = _d(mom)
+    hlen, ph = _u8(hlen)
+    if pix is None:
+        crec = np.empty((H, W, 4))
+        lib().orc_spatial(W, H, C.byref(params(params_)), pc, ps, pm, ph, _d(crec)[1], 0, None)
+    else:
+        pix, ppix = _i32(pix)
+        crec = np.empty((pix.shape[0], 4))
+        lib().orc_spatial(W, H, C.byref(params(params_)), pc, ps, pm, ph, _d(crec)[1],
+                          int(pix.shape[0]), ppix)
+    return crec
+
+
+def postfilter(nd, col, lens_, tan_half_fovy, params_, pix=None):
+    H, W = nd.shape[:2]
+    nd, pnd = _d(nd)
+    col, pcol = _d(col)
+    if pix is None:
+        pp = np.empty((H, W, 4))
+        lib().orc_postfilter(W, H, C.byref(lens(lens_)), float(tan_half_fovy), C.byref(params(params_)),
+                             pnd, pcol, _d(pp)[1], 0, None)
+    else:
+        pix, ppix = _i32(pix)
+        pp = np.empty((pix.shape[0], 4))
+        lib().orc_postfilter(W, H, C.byref(lens(lens_)), float(tan_half_fovy), C.byref(params(params_)),
+                             pnd, pcol, _d(pp)[1], int(pix.shape[0]), ppix)
+    return pp
+
+
+def composite(nd, col, spp, pp, crt, crec, hacc, lens_, tan_half_fovy, params_, height):
+    """Per-pixel composite of planes of any leading shape (image or pixel list);
+    ``height`` is the image height the CoC is measured against."""
+    shape = np.asarray(spp).shape
+    n = int(np.prod(shape))
+    out = np.empty(shape + (4,))
+    lib().orc_composite(n, int(height), C.byref(lens(lens_)), float(tan_half_fovy), C.byref(params(params_)),
+                        _d(nd)[1], _d(col)[1], _u8(spp)[1], _d(pp)[1], _d(crt)[1], _d(crec)[1],
+                        _d(hacc)[1], _d(out)[1])
+    return out
+
+
+def frame(oscene, cam_, prev_cam, lens_, params_, hist=None, pp_pix=None):
+    """One full frame in the paper's order.  ``pp_pix`` restricts the
+    post-filter (and therefore the composite) to a pixel list, for frames too
+    large for the full O(R_max^2) gather; the composite is then returned only
+    at those pixels."""
+    W, H = cam_.width, cam_.height
+    g = gbuffer(oscene, cam_, prev_cam, params_)
+    if hist is None:
+        hist = empty_history(W, H)
+    m = mask(g["nd"], g["mv"], params_, hist["mom"], hist["hlen"])
+    rt = trace(oscene, cam_, lens_, params_, m["spp"])
+    newh, crt, hacc = temporal(cam_, prev_cam, params_, rt, m["spp"], g["nd"], g["mv"], hist)
+    crec = spatial(params_, crt, m["spp"], newh["mom"], newh["hlen"])
+    t = cam_.tan_half_fovy
+    if pp_pix is None:
+        pp = postfilter(g["nd"], g["col"], lens_, t, params_)
+        out = composite(g["nd"], g["col"], m["spp"], pp, crt, crec, hacc, lens_, t, params_, H)
+    else:
+        pp = postfilter(g["nd"], g["col"], lens_, t, params_, pix=pp_pix)
+        sel = np.asarray(pp_pix)
+        flat = lambda a: a.reshape(H * W, *a.shape[2:])[sel]  # noqa: E731
+        out = composite(flat(g["nd"]), flat(g["col"]), flat(m["spp"]), pp, flat(crt),
+                        flat(crec), flat(hacc), lens_, t, params_, H)
+    return dict(g=g, mask=m, rt=rt, hist=newh, crt=crt, hacc=hacc, crec=crec, pp=pp, out=out)
+
+
+def disk_area(r: float) -> float:
+    return lib().orc_disk_area(float(r))
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+if __name__ == "__main__":  # pragma: no cover - manual build
+    print(build(force="--force" in sys.argv))
