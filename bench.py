@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark: one hybrid depth-of-field frame per step on the procedural room
+at 1920x1080 (the 1080p room workload: ~164.6k triangles, focus 3.0, f/1.4
+equivalent aperture, 1-8 rays per masked pixel, EMA 0.2, camera +0.01/frame
+with +-0.5 px jitter), through the C ABI on one GB300.
+
+Prints one JSON line.  ``value`` is ms/frame (lower is better) of the whole
+hot path: G-buffer, adaptive mask, compaction + thin-lens trace,
+post-filter, temporal + spatial reconstruction and composite.  The BVH is
+built once (static scene) and reported separately.  Each step renders the
+next consecutive frame with its history; L2 is flushed (256 MiB write)
+between steps, outside the timed events.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead, on
+a bounded sample of the same frame (see ``cpu_sample``).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hdof_inputs as hi  # noqa: E402
+
+METRIC = "Hybrid DoF ms/frame @1080p & masked thin-lens Mrays/s vs plain form, 1 GB300"
+WORKLOAD = "procedural room 1920x1080, 164620 tris, 1-8 spp masked thin-lens, consecutive frames"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+# FP32 lanes x 2 flops per FMA x SMs (GB300: 152 SMs x 128 FP32 lanes)
+FP32_LANES = 152 * 128
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("clocks_under_load", {}).get("sm_mhz_median", 1500.0)), "measured"
+    except Exception:
+        return FALLBACK_HBM, 1500.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(smax)), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ------------------------------------------------------------- distributed --
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------- our kernels ---
+
+def algorithmic_bytes(W, Hh, n_traced, variance_px):
+    """HBM bytes each call must move at minimum (FP32 planes), per frame."""
+    px = W * Hh
+    return {
+        "gbuffer": 44 * px,                                   # write nd, col, mv, tri
+        "mask": (16 + 1 + 1) * px + (8 + 8 + 1) * variance_px,  # nd -> edge, spp; mv + history where needed
+        "trace": 2 * px + (4 + 4 + 1 + 48) * n_traced,          # spp twice; queue w/r; spp; rt
+        "postfilter": (16 + 16 + 16 + 16 + 16) * px,            # nd -> prep; prep + col -> pp
+        "reconstruct": (1 + 1 + 16) * px + (48 + 8 + 16 + 41 + 41 + 16 + 4 + 16 + 9 + 16) * n_traced,
+        "composite": (16 + 16 + 1 + 16 + 16) * px + (16 + 16 + 4) * n_traced,
+    }
+
+
+def contributing_taps(z, lens, Hh, t, r_max):
+    """Number of (pixel, tap) pairs with non-zero post-filter weight:
+    sum over source pixels q of the lattice points within r_q + 1/2
+    (ignoring the image border)."""
+    c = lens.aperture_radius * Hh * (lens.focus_dist - z) / (z * lens.focus_dist * t)
+    r = np.minimum(np.abs(c) * 0.5, r_max)
+    R = int(math.ceil(r_max + 0.5))
+    o = np.arange(-R, R + 1)
+    d = np.sort(np.sqrt(o[:, None] ** 2 + o[None, :] ** 2).ravel())
+    return int(np.searchsorted(d, r.ravel() + 0.5, side="left").sum())
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2210_04981_gb300.hdof as H
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    W, Hh = args.width, args.height
+    scene = hi.room_scene(seed=0, aspect=W / Hh)
+    lens = hi.room_lens()
+    p0 = hi.room_params()
+    cams = [hi.room_camera(k, W, Hh) for k in range(args.warmup + args.steps + 1)]
+    t0 = time.perf_counter()
+    verts, idx = torch.from_numpy(scene.verts).to(dev), torch.from_numpy(scene.idx).to(dev)
+    mat, uv = torch.from_numpy(scene.mat).to(dev), torch.from_numpy(scene.uv).to(dev)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    bvh = H.hdof_build_bvh(verts, idx, mat, uv)
+    torch.cuda.synchronize()
+    bvh_ms = (time.perf_counter() - t1) * 1e3
+    upload_ms = (t1 - t0) * 1e3
+    st = bvh.stats()
+    r = H.Renderer(bvh, W, Hh, p0, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def params_of(k):
+        return p0.replace(frame=k % 65536, camera_moved=int(k > 0))
+
+    stages = ["gbuffer", "mask", "trace", "postfilter", "reconstruct", "composite"]
+
+    def frame(k, ev=None):
+        cam, prev, p = cams[k], cams[max(k - 1, 0)], params_of(k)
+        hin, hout = r.hist[r.cur], r.hist[1 - r.cur]
+        calls = [
+            lambda: H.hdof_gbuffer(bvh, cam, prev, p, r.g),
+            lambda: H.hdof_mask(r.g, hin, p, r.edge, r.spp, r.ws),
+            lambda: H.hdof_trace(bvh, cam, lens, p, r.spp, r.rt, r.stats, r.ws),
+            lambda: H.hdof_postfilter(r.g, cam, lens, p, r.pp, r.ws),
+            lambda: H.hdof_reconstruct(r.rt, r.g, r.spp, cam, prev, lens, p, hin, hout, r.crt, r.hacc, r.crec),
+            lambda: H.hdof_composite(r.g, r.spp, r.pp, r.crt, r.crec, r.hacc, cam, lens, p, r.out),
+        ]
+        for i, c in enumerate(calls):
+            if ev is not None:
+                ev[i].record(stream)
+            c()
+        if ev is not None:
+            ev[len(calls)].record(stream)
+        r.cur = 1 - r.cur
+
+    # warm-up frames 0 .. W-1
+    for k in range(args.warmup):
+        frame(k)
+    H.hdof_sync()
+    # timed frames
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(K)]
+    stats_all = torch.zeros((K, 2), dtype=torch.int32, device=dev)
+    var_px = np.zeros(K, np.int64)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    with sampler:
+        wall0 = time.perf_counter()
+        for s in range(K):
+            flush.zero_()  # evict L2 between steps (outside the step's events)
+            frame(args.warmup + s, evs[s])
+            stats_all[s].copy_(r.stats)  # ray counts of this frame (after its events)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if ws > 1:
+        torch.distributed.barrier()
+    H.hdof_sync()
+    stage_ms = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(len(stages))] for s in range(K)])
+    step_ms = stage_ms.sum(1)
+    total_ms = float(step_ms.sum())
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    clocks = sampler.summary()
+
+    st_all = stats_all.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    traced, rays = st_all[:, 0], st_all[:, 1]
+    spp_h = r.spp.cpu().numpy()
+    var_px[:] = int(((spp_h > 0) & (spp_h < p0.spp_max)).sum())
+
+    mean_stage = stage_ms.mean(0)
+    trace_ms = float(mean_stage[stages.index("trace")])
+    mrays = float(rays.mean()) / (trace_ms * 1e-3) / 1e6
+    hbm, sm_med, peak_src = peaks()
+    ab = algorithmic_bytes(W, Hh, float(traced.mean()), float(var_px.mean()))
+    per_stage = {}
+    for i, n in enumerate(stages):
+        gbs = ab[n] / (mean_stage[i] * 1e-3) / 1e9
+        per_stage[n] = {"ms": round(float(mean_stage[i]), 4), "alg_bytes": int(ab[n]),
+                        "alg_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3)}
+    # post-filter gather as arithmetic: contributing taps x 24 FP32 ops
+    z = r.g.nd[..., 3].float().cpu().numpy().astype(np.float64)
+    taps = contributing_taps(z, lens, Hh, cams[0].tan_half_fovy, p0.r_max)
+    fp32_peak = FP32_LANES * 2 * (clocks["sm_mhz"] or sm_med) * 1e6 / 1e12
+    pf_ms = float(mean_stage[stages.index("postfilter")])
+    per_stage["postfilter"]["contributing_taps"] = taps
+    per_stage["postfilter"]["alg_TFLOPs"] = round(taps * 24 / (pf_ms * 1e-3) / 1e12, 2)
+    dom = stages[int(np.argmax(mean_stage))]
+    if dom == "postfilter":
+        ach = taps * 24 / (pf_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                "frac": round(ach / fp32_peak, 3), "traffic": None, "kernel": "postfilter (k_pf_prep + k_pf_gather)",
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock under load"}
+    elif dom == "trace":
+        roof = {"bound": "alu", "achieved": None, "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": "trace", "mrays_per_s": round(mrays, 1)}
+    else:
+        gbs = ab[dom] / (mean_stage[stages.index(dom)] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 3),
+                "traffic": None, "kernel": dom, "peak_source": peak_src}
+
+    # end-to-end through the C ABI with a host-side result: each step renders
+    # the next frame from host camera records and copies the image to pinned memory
+    e2e = None
+    if not args.no_e2e:
+        host_img = torch.empty((Hh, W, 4), dtype=torch.float32, pin_memory=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        r.reset_history()
+        for k in range(args.warmup):
+            frame(k)
+        torch.cuda.synchronize()
+        e_ms = 0.0
+        ne = K
+        for s in range(ne):
+            flush.zero_()
+            e0.record(stream)
+            frame(args.warmup + s)
+            host_img.copy_(r.out, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e_ms += e0.elapsed_time(e1)
+        import ctypes
+        rec_bytes = ctypes.sizeof(H.hdof_camera) * 2 + ctypes.sizeof(H.hdof_lens) + ctypes.sizeof(H.hdof_params)
+        e2e = {"value": round(e_ms / max(ne, 1), 4), "unit": "ms/frame", "h2d_bytes_per_step": int(rec_bytes),
+               "d2h_bytes_per_step": int(host_img.numel() * 4),
+               "note": "h2d = camera/lens/params records passed by value to the C calls; d2h = RGBA32F image"}
+
+    value = total_ms / (K * ws)
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "ms/frame", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / K, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": W, "height": Hh, "triangles": int(st.n_tris),
+                   "bvh_depth": int(st.depth), "spp_max": p0.spp_max, "r_max": p0.r_max,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single", "l2": "flushed between steps (256 MiB write)"},
+        "mrays_per_s": round(mrays, 1), "rays_per_frame": int(rays.mean()),
+        "traced_px_per_frame": int(traced.mean()), "trace_ms": round(trace_ms, 4),
+        "stages": per_stage, "bvh_build_ms": round(bvh_ms, 3), "scene_upload_ms": round(upload_ms, 3),
+        "wall_s_timed": round(wall, 3),
+        "roofline": roof, "e2e": e2e, "gpu_launches": 12 * K, "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------ the oracle ---
+
+def oracle_frame_sample(O, osc, cams, lens, p0, k, hist, W, Hh, pf_stride):
+    """One oracle frame: every stage at full resolution except the post-filter
+    and composite, evaluated on every pf_stride-th pixel.  Returns the
+    history, the stage times and the extrapolated full-frame time."""
+    cam, prev = cams[k], cams[max(k - 1, 0)]
+    p = p0.replace(frame=k, camera_moved=int(k > 0))
+    t = {}
+    t0 = time.perf_counter()
+    g = O.gbuffer(osc, cam, prev, p)
+    t["gbuffer"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    m = O.mask(g["nd"], g["mv"], p, hist["mom"], hist["hlen"])
+    t["mask"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rt = O.trace(osc, cam, lens, p, m["spp"])
+    t["trace"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    nh, crt, hacc = O.temporal(cam, prev, p, rt, m["spp"], g["nd"], g["mv"], hist)
+    crec = O.spatial(p, crt, m["spp"], nh["mom"], nh["hlen"])
+    t["reconstruct"] = time.perf_counter() - t0
+    pix = np.arange(0, W * Hh, pf_stride, dtype=np.int32)
+    t0 = time.perf_counter()
+    pp = O.postfilter(g["nd"], g["col"], lens, cam.tan_half_fovy, p, pix=pix)
+    sel = pix
+    flat = lambda a: a.reshape(W * Hh, *a.shape[2:])[sel]  # noqa: E731
+    O.composite(flat(g["nd"]), flat(g["col"]), flat(m["spp"]), pp, flat(crt), flat(crec), flat(hacc), lens,
+                cam.tan_half_fovy, p, Hh)
+    t["postfilter_sample"] = time.perf_counter() - t0
+    est = sum(v for n, v in t.items() if n != "postfilter_sample") + t["postfilter_sample"] * pf_stride
+    return nh, t, est
+
+
+def cpu_baseline(args, budget_s=30.0):
+    from oracle import oracle as O
+    O.build()
+    W, Hh = args.width, args.height
+    scene = hi.room_scene(seed=0, aspect=W / Hh)
+    lens = hi.room_lens()
+    p0 = hi.room_params()
+    cams = [hi.room_camera(k, W, Hh) for k in range(2)]
+    osc = O.OScene(scene)
+    hist = O.empty_history(W, Hh)
+    stride = 64
+    _, t, est = oracle_frame_sample(O, osc, cams, lens, p0, 0, hist, W, Hh, stride)
+    return {"value": round(est * 1e3, 1), "unit": "ms/frame", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"frame 0 at {W}x{Hh}: all stages full-frame except post-filter+composite on every "
+                      f"{stride}th pixel, scaled x{stride}; measured {sum(t.values()):.1f} s",
+            "stage_s": {k: round(v, 3) for k, v in t.items()}}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    W, Hh = args.width, args.height
+    scene = hi.room_scene(seed=0, aspect=W / Hh)
+    lens = hi.room_lens()
+    p0 = hi.room_params()
+    n = args.warmup + args.steps
+    cams = [hi.room_camera(k, W, Hh) for k in range(n)]
+    osc = O.OScene(scene)
+    hist = O.empty_history(W, Hh)
+    stride = args.ref_pf_stride
+    ests = []
+    for k in range(n):
+        hist, t, est = oracle_frame_sample(O, osc, cams, lens, p0, k, hist, W, Hh, stride)
+        if k >= args.warmup:
+            ests.append(est)
+    value = float(np.mean(ests)) * 1e3
+    sample = (f"each step: one consecutive {W}x{Hh} frame, every stage full-frame except post-filter+composite on "
+              f"every {stride}th pixel, post-filter time scaled x{stride}")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms/frame", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "width": W, "height": Hh, "triangles": scene.n_tris},
+           "cpu_baseline": {"value": round(value, 1), "unit": "ms/frame", "cores": O.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 1), "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=30.0)
+    ap.add_argument("--ref-pf-stride", type=int, default=256)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,6 +84,7 @@ class Params:
     light_dir: list = field(default_factory=lambda: [[0.3, 0.5, -1.0]])
     light_E: list = field(default_factory=lambda: [1.0])
     miss_dist: float = 1.0e4
+    trav_cap: int = 0
     # temporal reconstruction
     ema_alpha: float = 0.2
     camera_moved: int = 0
@@ -387,7 +388,7 @@ def random_history(width: int, height: int, seed: int = 0, frac_valid: float = 0
     Bf = (1.0 - B).astype(F32)
     far = np.concatenate([rng.uniform(0, 1, (H, W, 3)) * Bf[..., None], Bf[..., None]], -1)
     mu1 = rng.uniform(0.05, 0.9, (H, W))
-    var = rng.uniform(0.0, 0.01, (H, W)) ** 2 * rng.integers(0, 2, (H, W))
+    var = rng.uniform(0.0, 0.12, (H, W)) ** 2 * rng.integers(0, 2, (H, W))
     mom = np.stack([mu1, mu1 * mu1 + var], -1)
     hlen = rng.integers(1, 12, (H, W)) * (rng.uniform(size=(H, W)) < frac_valid)
     return dict(near=near.astype(F32), far=far.astype(F32), mom=mom.astype(F32),

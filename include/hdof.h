@@ -1,0 +1,266 @@
+/* hdof -- hybrid ray-traced / post-processed depth of field on one GPU.
+ *
+ * C ABI of the per-frame hot path of "Hybrid DoF: Ray-Traced and
+ * Post-Processed Hybrid Depth of Field Effect for Real-Time Rendering"
+ * (Tan, Chua, Biette, Bhojan; SIGGRAPH '20 Posters).  The paper's pipeline
+ * (Design section): a G-buffer with a sharp image, a post-process CoC filter
+ * of that image, an adaptive ray mask, thin-lens distributed ray tracing of
+ * the masked pixels, spatio-temporal reconstruction, and a composite.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers to image planes and scene arrays are DEVICE pointers owned by
+ *   the caller.  Planes are row-major [height][width][channels], densely
+ *   packed (pitch = width), pixel (i, j) = column i, row j from the top.
+ * - Opaque handles (hdof_bvh) are owned by the library: create/destroy pairs.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every compute call only enqueues work and returns; results are ready
+ *   when the stream reaches that point.
+ * - Return value: HDOF_OK (0) or a negative HDOF_E* code.  Arguments are
+ *   validated on the host before anything is enqueued (HDOF_EINVAL).  A
+ *   launch failure returns HDOF_ECUDA.  hdof_last_error() gives the
+ *   message of the calling thread's last failure.  Calls never throw.
+ * - Kernel-side watchdogs (a capped traversal loop) never hang: they record
+ *   HDOF_ETIMEOUT in a device status word that hdof_sync() reports.
+ * - Camera space: the camera at `pos` looks along +fwd with +right, +up;
+ *   the screen point of pixel (i, j) this frame is (i + 0.5 + jitter[0],
+ *   j + 0.5 + jitter[1]).  Depth is view-space z (distance along fwd).
+ */
+#ifndef HDOF_H
+#define HDOF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HDOF_OK 0
+#define HDOF_EINVAL (-1)
+#define HDOF_ECUDA (-2)
+#define HDOF_ENOMEM (-3)
+#define HDOF_ETIMEOUT (-4)
+#define HDOF_EUNSUPPORTED (-5)
+
+/* storage types of the G-buffer planes */
+#define HDOF_F32 0
+#define HDOF_F16 1  /* nd: four halves (nx, ny, nz, z) */
+#define HDOF_BF16 2 /* col: four bfloat16 (r, g, b, luminance) */
+
+/* Pinhole camera of the frame (Design: the G-buffer is rendered with it;
+ * Ray Trace: the thin-lens rays share its pose). */
+typedef struct hdof_camera {
+    float pos[3], right[3], up[3], fwd[3];
+    float tan_half_fovy;
+    int32_t width, height;
+    float jitter[2];
+} hdof_camera;
+
+/* Thin lens (Potmesil and Chakravarty, cited in the Design section):
+ * focus distance = view depth of the focus plane; aperture radius in scene
+ * units.  CoC diameter in pixels: c(z) = A H (zf - z) / (z zf tan(fovy/2)),
+ * positive in the near field.  focal_length is recorded, not used (it
+ * cancels at fixed field of view). */
+typedef struct hdof_lens {
+    float focus_dist, aperture_radius, focal_length;
+} hdof_lens;
+
+/* Every constant of the method.  The paper prints none; each field is a
+ * stated reading of its prose (see the per-call comments). */
+typedef struct hdof_params {
+    /* adaptive ray mask (Ray Trace section) */
+    float gauss_sigma;   /* Gaussian 5x5 sigma on (n, z) */
+    float edge_tau;      /* edge threshold on max(|grad n|, |grad z|/z) */
+    int32_t tile;        /* mask tile edge in pixels */
+    int32_t dilate;      /* tile dilation radius (tiles) */
+    int32_t spp_max;     /* rays per edge-tile pixel, 1..255 */
+    int32_t variance_on; /* add the temporal variance term */
+    float var_tau;       /* luminance std-dev that keeps a pixel traced */
+    float var_scale;     /* std-dev that earns spp_max rays */
+    int32_t hlen_young;  /* history length below which a pixel gets spp_max */
+    /* thin-lens ray trace (Ray Trace section) */
+    uint32_t seed;       /* Philox key word 0 */
+    int32_t frame, view; /* Philox key word 1 = view * 65536 + frame */
+    float k_ambient;
+    int32_t n_lights;    /* directional lights, 0..4 */
+    float light_dir[4][3]; /* unit vectors towards the lights */
+    float light_E[4];
+    float miss_dist;     /* far position of a ray that hits nothing */
+    int32_t trav_cap;    /* traversal step watchdog; 0 = default (64 x nodes) */
+    /* temporal reconstruction (Reconstruction section) */
+    float ema_alpha;
+    int32_t camera_moved; /* compose with this frame's hit ratio */
+    /* spatial reconstruction */
+    float r_s;           /* gather radius cap, pixels */
+    float var_ref;       /* std-dev at which the spatial gather is fully used */
+    /* post-filter (Design section) */
+    float r_max;         /* CoC radius cap, pixels, <= 127 */
+    float kz_rel;        /* relative depth band of the far-field depth test */
+    /* composite (Composite section) */
+    float h_tau;         /* hit ratio above which far pixels take the post-process */
+} hdof_params;
+
+/* G-buffer of one frame.  nd: (nx, ny, nz, z) per pixel, n the geometric
+ * normal facing the viewer, z view depth (misses: z = miss_dist, n = -fwd);
+ * col: (r, g, b, luminance) sharp shaded colour; mv: float2 motion (i, j)
+ * minus the previous-frame index-space position of the surface point
+ * (1e6 when the previous camera cannot see it); tri: original id of the hit
+ * triangle, -1 for a miss.  mv and tri may be NULL for calls that do not
+ * read them. */
+typedef struct hdof_gbuf {
+    int32_t width, height;
+    int32_t dtype_nd;  /* HDOF_F32 (float4) or HDOF_F16 (half x4) */
+    int32_t dtype_col; /* HDOF_F32 (float4) or HDOF_BF16 (bfloat16 x4) */
+    void* nd;
+    void* col;
+    float* mv;
+    int32_t* tri;
+} hdof_gbuf;
+
+/* Accumulated temporal history (one buffer per frame parity; a frame reads
+ * the previous buffer and writes the other).  near = (EMA of h*C_near rgb,
+ * EMA of h), far = (EMA of (1-h)*C_far rgb, EMA of 1-h), mom = (EMA of Y,
+ * EMA of Y^2), hlen = frames accumulated (0 = no history).  All float32
+ * except hlen (uint8).  Pixels with hlen = 0 hold don't-care values. */
+typedef struct hdof_history {
+    float* near_acc; /* [H][W][4] */
+    float* far_acc;  /* [H][W][4] */
+    float* mom;      /* [H][W][2] */
+    uint8_t* hlen;   /* [H][W] */
+} hdof_history;
+
+typedef struct hdof_bvh hdof_bvh;
+
+typedef struct hdof_bvh_stats {
+    int32_t n_tris;
+    int32_t n_nodes;  /* internal nodes */
+    int32_t depth;    /* maximum leaf depth */
+    int32_t reserved;
+    int64_t device_bytes;
+} hdof_bvh_stats;
+
+/* ---------------------------------------------------------------- misc -- */
+const char* hdof_version(void);
+/* Copies the calling thread's last error message; returns its length. */
+int hdof_last_error(char* buf, size_t n);
+/* Synchronises `stream`, then reports (and clears) the device status word:
+ * HDOF_ETIMEOUT if a kernel watchdog fired since the last call, HDOF_ECUDA
+ * on a CUDA error, else HDOF_OK. */
+int hdof_sync(void* stream);
+/* Fills *p with the library defaults (the tiny-scene values). */
+void hdof_default_params(hdof_params* p);
+
+/* ------------------------------------------------------------ BVH -- */
+/* Builds a linear BVH (Karras 2012: 30-bit Morton codes of the triangle
+ * centroids, radix sort, split search, bottom-up refit) over a triangle
+ * soup, standing in for the paper's hardware ray-tracing acceleration
+ * structure (Abstract).  verts: float [n_verts][3]; idx: int32 [n_tris][3];
+ * mat: float [n_tris][8] = (albedo_a rgb, checker_n, albedo_b rgb, 0);
+ * uv: float [n_tris][6] (may be NULL when no material uses a checker).
+ * All device pointers; they are read during the call only.  Synchronous
+ * with respect to the host (returns once the structure is built).
+ * Errors: HDOF_EINVAL (n_tris < 1, bad index), HDOF_ENOMEM, HDOF_ECUDA,
+ * HDOF_EUNSUPPORTED (tree deeper than the traversal stack). */
+int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t* idx, int32_t n_tris,
+                   const float* mat, const float* uv, hdof_bvh** out, void* stream);
+int hdof_bvh_destroy(hdof_bvh* bvh);
+int hdof_bvh_info(const hdof_bvh* bvh, hdof_bvh_stats* info);
+
+/* Closest hit of n arbitrary rays (org, dir: float [n][3], dir need not be
+ * normalised).  ids: int32 [n] original triangle id or -1; ts: float [n]
+ * ray parameter of the hit (unspecified on a miss).  Closest = smallest t;
+ * equal t -> lower triangle id (watertight test, edges inclusive, t > 0). */
+int hdof_closest_hits(const hdof_bvh* bvh, int32_t n, const float* org, const float* dir,
+                      int32_t* ids, float* ts, void* stream);
+
+/* ------------------------------------------------------- G-buffer -- */
+/* Deferred-shading G-buffer and sharp image (Design section), rendered as
+ * the closest hit of the pinhole ray through each pixel's screen point.
+ * Lambert shading: L = albedo (k_a + sum_l E_l max(0, n . w_l)).  prev is
+ * the previous frame's camera (pass cam itself for the first frame). */
+int hdof_gbuffer(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_camera* prev,
+                 const hdof_params* p, const hdof_gbuf* out, void* stream);
+
+/* ---------------------------------------------------- scratch memory -- */
+/* Bytes of caller-owned device scratch the calls below need for a
+ * width x height frame (the maximum over calls; one buffer serves them all
+ * when they run in order on one stream). */
+size_t hdof_workspace_bytes(int32_t width, int32_t height, const hdof_params* p);
+
+/* ----------------------------------------------------------- mask -- */
+/* Adaptive ray mask (Ray Trace section): 5x5 Gaussian (sigma) on the
+ * G-buffer normal and depth, 3x3 Sobel scaled by 1/8, edge metric
+ * e = max(|grad n|, |grad z| / z~), edge = e > edge_tau; tiles containing an
+ * edge, dilated by `dilate` tiles, get spp_max rays per pixel; with
+ * variance_on, other pixels whose previous-frame history (nearest pixel at
+ * the motion-reprojected position, prev_hist may be NULL) is young or whose
+ * luminance std-dev exceeds var_tau get clamp(ceil(spp_max sigma /
+ * var_scale), 1, spp_max) rays (spp_max while young).
+ * edge, spp: uint8 [H][W] outputs. */
+int hdof_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p,
+              uint8_t* edge, uint8_t* spp, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------- trace */
+/* Thin-lens distributed ray trace of the masked pixels (Ray Trace section).
+ * Compacts the pixels with spp > 0 into a queue (tile order), then a
+ * persistent kernel traces spp[p] lens rays per queued pixel: Philox4x32-10
+ * (key = (seed, view*65536+frame), counter = (pixel, sample, 0, 0)) gives
+ * u1, u2 -> lens point rho = A sqrt(u1), theta = 2 pi u2; the ray aims at
+ * the pixel's focus-plane point; closest hit; Lambert radiance; split
+ * weight w = clamp((c(z) + sqrt2) / (2 sqrt2), 0, 1) into the near layer.
+ * rt: float [H][W][12] = (C_near rgb, h | C_far rgb, c_near | P_far xyz,
+ * c_far); h = sum w / n is the hit ratio; an empty layer (weight < 1e-6)
+ * has colour 0 and CoC -1.  Untraced pixels are not written.
+ * stats (device, may be NULL): uint32 [2] = (traced pixels, rays). */
+int hdof_trace(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* lens,
+               const hdof_params* p, const uint8_t* spp, float* rt, uint32_t* stats,
+               void* workspace, size_t workspace_bytes, void* stream);
+
+/* ----------------------------------------------------- post-filter -- */
+/* CoC gather post-filter of the sharp image (Design section; the rejection
+ * rule of the Reconstruction section).  Scatter-as-gather over soft disks
+ * s(r_q - d), s(x) = clamp(x + 1/2, 0, 1), r_q = min(|c(z_q)|/2, r_max),
+ * normalised by the disk's lattice area; near layer weighted by w_near(q),
+ * far layer by 1 - w_near(q) and the depth test clamp(1 - (z_q - z_p) /
+ * (kz_rel z_p), 0, 1).  pp: float [H][W][4] = (alpha N + (1-alpha) F, alpha).
+ * Gathers are bounded per 16x16 tile by the largest reaching CoC. */
+int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, const hdof_lens* lens,
+                    const hdof_params* p, float* pp, void* workspace, size_t workspace_bytes,
+                    void* stream);
+
+/* ------------------------------------------------- reconstruct -- */
+/* Spatio-temporal reconstruction (Reconstruction section).  Temporal: near
+ * terms and moments reprojected by mv, far terms by the previous-frame
+ * projection of the far position (own far hits, else the 3x3 neighbours',
+ * else the G-buffer point); bilinear over taps with history, invalid below
+ * weight 1e-3; EMA with ema_alpha; layer colours normalised by their
+ * accumulated hit ratio; composed with this frame's hit ratio when
+ * camera_moved, else the accumulated one; CoC = H_acc c_near + (1-H_acc)
+ * c_far.  Spatial: for traced pixels, gather of traced neighbours with
+ * weight s(r_p - d) s(r_q - d), r = min(c/2, r_s), blended by
+ * beta = clamp(sigma_L / var_ref, 0, 1) (1 while hlen < 2).
+ * hist_in (previous frame) is read, hist_out written; they must differ.
+ * crt: float [H][W][4] (C_rt rgb, c_rt), untraced pixels (0,0,0,-1);
+ * hacc: float [H][W] accumulated hit ratio; crec: float [H][W][4]
+ * (C_rec rgb, 0).  hacc and crec are written for traced pixels only. */
+int hdof_reconstruct(const float* rt, const hdof_gbuf* in, const uint8_t* spp,
+                     const hdof_camera* cam, const hdof_camera* prev, const hdof_lens* lens,
+                     const hdof_params* p, const hdof_history* hist_in,
+                     const hdof_history* hist_out, float* crt, float* hacc, float* crec,
+                     void* stream);
+
+/* ------------------------------------------------------- composite -- */
+/* Composite (Composite section): focus weight f = clamp(sqrt2 + 1/2 - c, 0,
+ * 1) with c the reconstructed CoC where traced, else |c(z)|; near branch
+ * = C_rec where traced, else C_pp; far branch = lerp(C_rec, C_pp,
+ * clamp(H_acc / h_tau, 0, 1)) where traced, else C_pp; blended by
+ * w_near(c(z)); out = lerp(blur, sharp, f).  out: float [H][W][4]. */
+int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt,
+                   const float* crec, const float* hacc, const hdof_camera* cam,
+                   const hdof_lens* lens, const hdof_params* p, float* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDOF_H */

@@ -1,0 +1,386 @@
+// Device-side building blocks shared by the hdof kernels: small vector math,
+// the thin-lens camera, the Philox4x32-10 counter-based generator, G-buffer
+// storage conversions, BVH layout and the watertight ray/triangle test.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hdof.h"
+
+#define HDOF_SQRT2 1.41421356237309505f
+#define HDOF_EMPTY_W 1e-6f      // layer weight below which a layer is empty
+#define HDOF_HIST_MIN_W 1e-3f   // bilinear history weight below which history is invalid
+#define HDOF_PP_MIN_W 1e-8f     // post-filter layer weight below which a layer is empty
+#define HDOF_MV_OFFSCREEN 1e6f  // motion written when the previous camera cannot see a point
+#define HDOF_STACK 64           // traversal stack entries (>= maximum tree depth)
+#define HDOF_TILE_PF 16         // post-filter bounding tile edge
+#define HDOF_STATUS_TIMEOUT 1u
+
+namespace hdof {
+
+
+// ------------------------------------------------------------------ math --
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize(float3 a) { return rsqrtf(dot(a, a)) * a; }
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
+__device__ __forceinline__ float luminance(float3 c) { return 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z; }
+__device__ __forceinline__ float3 ld3(const float* p) { return f3(p[0], p[1], p[2]); }
+
+// soft step of the gather kernels: s(x) = clamp(x + 1/2, 0, 1)
+__device__ __forceinline__ float soft_step(float x) { return clamp01(x + 0.5f); }
+
+// --------------------------------------------------------------- camera --
+struct Cam {
+    float3 pos, right, up, fwd;
+    float t, aspect;
+    int W, H;
+    float jx, jy;
+};
+
+__host__ __device__ inline Cam make_cam(const hdof_camera& c) {
+    Cam o;
+    o.pos = make_float3(c.pos[0], c.pos[1], c.pos[2]);
+    o.right = make_float3(c.right[0], c.right[1], c.right[2]);
+    o.up = make_float3(c.up[0], c.up[1], c.up[2]);
+    o.fwd = make_float3(c.fwd[0], c.fwd[1], c.fwd[2]);
+    o.t = c.tan_half_fovy;
+    o.aspect = (float)c.width / (float)c.height;
+    o.W = c.width;
+    o.H = c.height;
+    o.jx = c.jitter[0];
+    o.jy = c.jitter[1];
+    return o;
+}
+
+// Pinhole direction through screen point (sx, sy); its fwd component is 1,
+// so the point at view depth z along it is pos + z * d.
+__device__ __forceinline__ float3 pinhole_dir(const Cam& c, float sx, float sy) {
+    float X = (2.f * sx / c.W - 1.f) * c.aspect * c.t;
+    float Y = (1.f - 2.f * sy / c.H) * c.t;
+    return X * c.right + Y * c.up + c.fwd;
+}
+
+// Index-space projection (u = (i, j) is exactly pixel (i, j)'s sample point).
+__device__ __forceinline__ bool project(const Cam& c, float3 P, float& ux, float& uy) {
+    float3 v = P - c.pos;
+    float zc = dot(v, c.fwd);
+    if (!(zc > 0.f)) return false;
+    float X = dot(v, c.right) / zc, Y = dot(v, c.up) / zc;
+    float sx = (X / (c.aspect * c.t) + 1.f) * 0.5f * c.W;
+    float sy = (1.f - Y / c.t) * 0.5f * c.H;
+    ux = sx - 0.5f - c.jx;
+    uy = sy - 0.5f - c.jy;
+    return true;
+}
+
+// Signed CoC diameter in pixels (thin lens): c(z) = A H (zf - z) / (z zf t).
+struct Coc {
+    float k;   // A H / t
+    float izf; // 1 / zf
+    __device__ __forceinline__ float operator()(float z) const { return k * (1.f / z - izf); }
+    __device__ __forceinline__ float at_infinity() const { return -k * izf; }
+};
+__host__ __device__ inline Coc make_coc(const hdof_lens& l, int H, float t) {
+    Coc c;
+    c.k = l.aperture_radius * (float)H / t;
+    c.izf = 1.f / l.focus_dist;
+    return c;
+}
+
+// Near-layer split weight, linear across the focus zone |c| < sqrt2.
+__device__ __forceinline__ float w_near(float c) {
+    return clamp01((c + HDOF_SQRT2) * (0.5f / HDOF_SQRT2));
+}
+
+// ---------------------------------------------------------------- Philox --
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products on a four-word counter, Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+// uniform in [0, 1) with 24 bits: exact in float
+__device__ __forceinline__ float u01(unsigned x) { return (float)(x >> 8) * (1.f / 16777216.f); }
+
+// ------------------------------------------------------- G-buffer storage --
+struct alignas(8) half4s { __half2 a, b; };
+struct alignas(8) bf164s { __nv_bfloat162 a, b; };
+
+__device__ __forceinline__ float4 ld4(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ float4 ld4(const half4s* p) {
+    uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    half4s h = *reinterpret_cast<half4s*>(&r);
+    float2 a = __half22float2(h.a), b = __half22float2(h.b);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 ld4(const bf164s* p) {
+    uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    bf164s h = *reinterpret_cast<bf164s*>(&r);
+    float2 a = __bfloat1622float2(h.a), b = __bfloat1622float2(h.b);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st4(float4* p, float4 v) { *p = v; }
+__device__ __forceinline__ void st4(half4s* p, float4 v) {
+    half4s h;
+    h.a = __floats2half2_rn(v.x, v.y);
+    h.b = __floats2half2_rn(v.z, v.w);
+    *p = h;
+}
+__device__ __forceinline__ void st4(bf164s* p, float4 v) {
+    bf164s h;
+    h.a = __floats2bfloat162_rn(v.x, v.y);
+    h.b = __floats2bfloat162_rn(v.z, v.w);
+    *p = h;
+}
+// depth channel only
+__device__ __forceinline__ float ldz(const float4* p) { return __ldg(&p->w); }
+__device__ __forceinline__ float ldz(const half4s* p) { return __high2float(__ldg(&p->b)); }
+
+// ------------------------------------------------------------------- BVH --
+// Binary BVH, child boxes stored in the parent (one 64-byte fetch tests both
+// children).  Child index >= 0: internal node; < 0: leaf holding sorted
+// triangle ~index.
+struct __align__(16) Node {
+    float4 xy0;  // c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y
+    float4 xy1;  // c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y
+    float4 z01;  // c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z
+    int4 child;  // c0, c1, parent, unused
+};
+// triangle in leaf order: (v0, original id), (v1, 0), (v2, 0)
+struct __align__(16) Tri {
+    float4 v0, v1, v2;
+};
+
+struct BvhView {
+    const Node* nodes;
+    const Tri* tris;
+    const float4* mat;  // sorted order: [2] per triangle (albedo_a rgb + checker_n, albedo_b)
+    const float2* uv;   // sorted order: [3] per triangle
+    int n_tris;
+    int root;           // root child-reference (internal 0, or ~0 for a single triangle)
+};
+
+struct Ray {
+    float3 o, d, id;  // id = 1 / d (finite)
+    float3 ood;       // o * id
+};
+
+__device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
+    Ray r;
+    r.o = o;
+    r.d = d;
+    const float eps = 1e-20f;
+    r.id = f3(1.f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
+              1.f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
+              1.f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
+    r.ood = f3(o.x * r.id.x, o.y * r.id.y, o.z * r.id.z);
+    return r;
+}
+
+// Slab test of one box; returns entry distance (or +inf on a miss).  The exit
+// distance is widened by 2 gamma_3 (Ize 2013) so no box the ray touches is culled.
+__device__ __forceinline__ float slab(const Ray& r, float lx, float hx, float ly, float hy, float lz,
+                                      float hz, float tmax) {
+    float tx0 = fmaf(lx, r.id.x, -r.ood.x), tx1 = fmaf(hx, r.id.x, -r.ood.x);
+    float ty0 = fmaf(ly, r.id.y, -r.ood.y), ty1 = fmaf(hy, r.id.y, -r.ood.y);
+    float tz0 = fmaf(lz, r.id.z, -r.ood.z), tz1 = fmaf(hz, r.id.z, -r.ood.z);
+    float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    tf *= 1.0000004f;
+    return tn <= tf ? tn : __int_as_float(0x7f800000);
+}
+
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013).  Edge
+// functions are evaluated without contraction so a shared edge gives exactly
+// negated values in its two triangles; exact zeros are re-evaluated in double.
+// Returns true for a hit with 0 < t; writes t and barycentrics (b0 at v0).
+struct Shear {
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+__device__ __forceinline__ Shear make_shear(float3 d) {
+    Shear s;
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    s.kz = 0;
+    if (ay > ax && ay >= az) s.kz = 1;
+    else if (az > ax && az > ay) s.kz = 2;
+    s.kx = s.kz == 2 ? 0 : s.kz + 1;
+    s.ky = s.kx == 2 ? 0 : s.kx + 1;
+    float dk[3] = {d.x, d.y, d.z};
+    if (dk[s.kz] < 0.f) {
+        int t = s.kx;
+        s.kx = s.ky;
+        s.ky = t;
+    }
+    s.Sx = dk[s.kx] / dk[s.kz];
+    s.Sy = dk[s.ky] / dk[s.kz];
+    s.Sz = 1.f / dk[s.kz];
+    return s;
+}
+__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ bool intersect_tri(float3 o, const Shear& s, float3 v0, float3 v1, float3 v2,
+                                              float& t, float& b0, float& b1, float& b2) {
+    float3 A = v0 - o, B = v1 - o, C = v2 - o;
+    float Akz = comp(A, s.kz), Bkz = comp(B, s.kz), Ckz = comp(C, s.kz);
+    float Ax = __fsub_rn(comp(A, s.kx), __fmul_rn(s.Sx, Akz));
+    float Ay = __fsub_rn(comp(A, s.ky), __fmul_rn(s.Sy, Akz));
+    float Bx = __fsub_rn(comp(B, s.kx), __fmul_rn(s.Sx, Bkz));
+    float By = __fsub_rn(comp(B, s.ky), __fmul_rn(s.Sy, Bkz));
+    float Cx = __fsub_rn(comp(C, s.kx), __fmul_rn(s.Sx, Ckz));
+    float Cy = __fsub_rn(comp(C, s.ky), __fmul_rn(s.Sy, Ckz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.f || V == 0.f || W == 0.f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+    float det = U + V + W;
+    if (det == 0.f) return false;
+    float T = U * (s.Sz * Akz) + V * (s.Sz * Bkz) + W * (s.Sz * Ckz);
+    if (det > 0.f ? !(T > 0.f) : !(T < 0.f)) return false;
+    float inv = 1.f / det;
+    t = T * inv;
+    b0 = U * inv;
+    b1 = V * inv;
+    b2 = W * inv;
+    return true;
+}
+
+struct Hit {
+    float t, b0, b1, b2;
+    int slot;  // sorted triangle slot, -1 = miss
+    int id;    // original triangle id
+};
+
+// Closest hit: smallest t, equal t -> lower original id.  Stack traversal
+// (push far child, descend near child); cap bounds the steps (watchdog).
+__device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 d, int cap, unsigned* status) {
+    Ray r = make_ray(o, d);
+    Shear sh = make_shear(d);
+    Hit h;
+    h.t = __int_as_float(0x7f800000);
+    h.slot = -1;
+    h.id = 0x7fffffff;
+    h.b0 = h.b1 = h.b2 = 0.f;
+    int stack[HDOF_STACK];
+    int sp = 0;
+    int cur = bvh.root;
+    int steps = 0;
+    while (true) {
+        if (cur >= 0) {
+            const Node* n = bvh.nodes + cur;
+            float4 a = __ldg(&n->xy0), b = __ldg(&n->xy1), z = __ldg(&n->z01);
+            int4 ch = __ldg(&n->child);
+            float t0 = slab(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t);
+            float t1 = slab(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t);
+            bool h0 = t0 < __int_as_float(0x7f800000), h1 = t1 < __int_as_float(0x7f800000);
+            if (h0 && h1) {
+                int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
+                if (sp < HDOF_STACK) stack[sp++] = farc;
+                else atomicOr(status, HDOF_STATUS_TIMEOUT);
+                cur = nearc;
+            } else if (h0) {
+                cur = ch.x;
+            } else if (h1) {
+                cur = ch.y;
+            } else {
+                if (sp == 0) break;
+                cur = stack[--sp];
+            }
+        } else {
+            int slot = ~cur;
+            const Tri* tr = bvh.tris + slot;
+            float4 p0 = __ldg(&tr->v0), p1 = __ldg(&tr->v1), p2 = __ldg(&tr->v2);
+            float t, b0, b1, b2;
+            if (intersect_tri(o, sh, f3(p0.x, p0.y, p0.z), f3(p1.x, p1.y, p1.z), f3(p2.x, p2.y, p2.z), t, b0,
+                              b1, b2)) {
+                int id = __float_as_int(p0.w);
+                if (t < h.t || (t == h.t && id < h.id)) {
+                    h.t = t;
+                    h.b0 = b0;
+                    h.b1 = b1;
+                    h.b2 = b2;
+                    h.slot = slot;
+                    h.id = id;
+                }
+            }
+            if (sp == 0) break;
+            cur = stack[--sp];
+        }
+        if (++steps > cap) {
+            atomicOr(status, HDOF_STATUS_TIMEOUT);
+            break;
+        }
+    }
+    if (h.slot < 0) h.id = -1;
+    return h;
+}
+
+// Lambert shading at a hit: face normal turned towards the ray, albedo from
+// the material (checkerboard over the triangle's (u, v) when checker_n > 0).
+struct Lights {
+    int n;
+    float3 dir[4];
+    float E[4];
+    float ka;
+};
+__host__ __device__ inline Lights make_lights(const hdof_params& p) {
+    Lights l;
+    l.n = p.n_lights;
+    for (int k = 0; k < 4; ++k) {
+        l.dir[k] = make_float3(p.light_dir[k][0], p.light_dir[k][1], p.light_dir[k][2]);
+        l.E[k] = p.light_E[k];
+    }
+    l.ka = p.k_ambient;
+    return l;
+}
+
+__device__ __forceinline__ void shade(const BvhView& bvh, const Lights& L, const Hit& h, float3 d, float3& n,
+                                      float3& rad) {
+    const Tri* tr = bvh.tris + h.slot;
+    float4 p0 = __ldg(&tr->v0), p1 = __ldg(&tr->v1), p2 = __ldg(&tr->v2);
+    float3 v0 = f3(p0.x, p0.y, p0.z);
+    n = normalize(cross(f3(p1.x, p1.y, p1.z) - v0, f3(p2.x, p2.y, p2.z) - v0));
+    if (dot(n, d) > 0.f) n = -1.f * n;
+    float4 ma = __ldg(&bvh.mat[2 * h.slot]);
+    float3 alb = f3(ma.x, ma.y, ma.z);
+    if (ma.w > 0.f) {
+        float2 u0 = __ldg(&bvh.uv[3 * h.slot]), u1 = __ldg(&bvh.uv[3 * h.slot + 1]),
+               u2 = __ldg(&bvh.uv[3 * h.slot + 2]);
+        float uu = h.b0 * u0.x + h.b1 * u1.x + h.b2 * u2.x;
+        float vv = h.b0 * u0.y + h.b1 * u1.y + h.b2 * u2.y;
+        int cell = (int)floorf(ma.w * uu) + (int)floorf(ma.w * vv);
+        if (cell & 1) {
+            float4 mb = __ldg(&bvh.mat[2 * h.slot + 1]);
+            alb = f3(mb.x, mb.y, mb.z);
+        }
+    }
+    float irr = L.ka;
+    for (int k = 0; k < L.n; ++k) irr += L.E[k] * fmaxf(0.f, dot(n, L.dir[k]));
+    rad = irr * alb;
+}
+
+}  // namespace hdof

@@ -1,0 +1,79 @@
+// composite (Composite section).  Pixels in the focus zone (CoC below
+// sqrt2) take the sharp rasterised colour; outside it, near geometry takes
+// the ray-traced colour and far geometry blends ray-traced and post-process
+// colour by the hit ratio, only below a threshold hit ratio so the edges of
+// the ray mask do not show.  One thread per pixel, float4 planes.
+#include "internal.h"
+
+namespace hdof {
+namespace {
+
+template <class ND, class COL>
+__global__ void __launch_bounds__(256) k_composite(const ND* __restrict__ nd, const COL* __restrict__ col,
+                                                   const uint8_t* __restrict__ spp, const float4* __restrict__ pp,
+                                                   const float4* __restrict__ crt, const float4* __restrict__ crec,
+                                                   const float* __restrict__ hacc, int W, int H, Coc coc,
+                                                   float h_tau, float4* __restrict__ out) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= W || j >= H) return;
+    size_t q = (size_t)j * W + i;
+    float c = coc(ldz(nd + q));
+    bool traced = __ldg(&spp[q]) > 0;
+    float4 s4 = ld4(col + q);
+    float4 p4 = __ldg(&pp[q]);
+    float3 sharp = f3(s4.x, s4.y, s4.z), cpp = f3(p4.x, p4.y, p4.z);
+    float ce = fabsf(c);
+    float3 nearc = cpp, farc = cpp;
+    if (traced) {
+        ce = __ldg(&crt[q].w);
+        float4 r4 = __ldg(&crec[q]);
+        float3 rec = f3(r4.x, r4.y, r4.z);
+        float b = clamp01(__ldg(&hacc[q]) / h_tau);
+        nearc = rec;  // specular-bokeh preference: zero for Lambert materials
+        farc = rec + b * (cpp - rec);
+    }
+    float f = clamp01(HDOF_SQRT2 + 0.5f - ce);
+    float wn = w_near(c);
+    float3 blur = wn * nearc + (1.f - wn) * farc;
+    float3 o = blur + f * (sharp - blur);
+    out[q] = make_float4(o.x, o.y, o.z, 0.f);
+}
+
+template <class ND, class COL>
+void launch(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
+            const float* hacc, Coc coc, float h_tau, float* out, cudaStream_t s) {
+    dim3 g((in->width + 31) / 32, (in->height + 7) / 8);
+    k_composite<ND, COL><<<g, 256, 0, s>>>(static_cast<const ND*>(in->nd), static_cast<const COL*>(in->col), spp,
+                                            reinterpret_cast<const float4*>(pp), reinterpret_cast<const float4*>(crt),
+                                            reinterpret_cast<const float4*>(crec), hacc, in->width, in->height, coc,
+                                            h_tau, reinterpret_cast<float4*>(out));
+}
+
+}  // namespace
+}  // namespace hdof
+
+using namespace hdof;
+
+extern "C" int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt,
+                              const float* crec, const float* hacc, const hdof_camera* cam, const hdof_lens* lens,
+                              const hdof_params* p, float* out, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_camera(cam, "hdof_composite")) || (rc = check_lens(lens, "hdof_composite")) ||
+        (rc = check_params(p, "hdof_composite")) || (rc = check_gbuf(in, "hdof_composite", false)))
+        return rc;
+    HDOF_CHECK_ARG(spp && pp && crt && crec && hacc && out, "hdof_composite: NULL buffer");
+    HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "hdof_composite: gbuf/camera size mismatch");
+    Coc coc = make_coc(*lens, cam->height, cam->tan_half_fovy);
+    cudaStream_t s = as_stream(stream);
+    if (in->dtype_nd == HDOF_F32 && in->dtype_col == HDOF_F32)
+        launch<float4, float4>(in, spp, pp, crt, crec, hacc, coc, p->h_tau, out, s);
+    else if (in->dtype_nd == HDOF_F16 && in->dtype_col == HDOF_BF16)
+        launch<half4s, bf164s>(in, spp, pp, crt, crec, hacc, coc, p->h_tau, out, s);
+    else if (in->dtype_nd == HDOF_F16)
+        launch<half4s, float4>(in, spp, pp, crt, crec, hacc, coc, p->h_tau, out, s);
+    else
+        launch<float4, bf164s>(in, spp, pp, crt, crec, hacc, coc, p->h_tau, out, s);
+    HDOF_LAUNCHED("hdof_composite");
+    return HDOF_OK;
+}

@@ -1,0 +1,95 @@
+// Host-side helpers shared by the C-ABI entry points: thread-local error
+// message, CUDA error mapping, argument checks and the BVH handle layout.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "../../include/hdof.h"
+#include "common.cuh"
+
+namespace hdof {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// returns HDOF_ECUDA with a message when err != cudaSuccess
+int cuda_fail(cudaError_t err, const char* where);
+
+#define HDOF_CHECK_ARG(cond, ...)        \
+    do {                                 \
+        if (!(cond)) {                   \
+            ::hdof::set_error(__VA_ARGS__); \
+            return HDOF_EINVAL;          \
+        }                                \
+    } while (0)
+
+#define HDOF_CUDA(call, where)                                  \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return ::hdof::cuda_fail(e_, where); \
+    } while (0)
+
+#define HDOF_LAUNCHED(where)                                         \
+    do {                                                             \
+        cudaError_t e_ = cudaGetLastError();                         \
+        if (e_ != cudaSuccess) return ::hdof::cuda_fail(e_, where);  \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check_camera(const hdof_camera* c, const char* who);
+int check_lens(const hdof_lens* l, const char* who);
+int check_params(const hdof_params* p, const char* who);
+int check_gbuf(const hdof_gbuf* g, const char* who, bool need_mv);
+
+// number of SMs of the current device (cached per device)
+int sm_count();
+
+// Device address of the status word (kernels OR in HDOF_STATUS_* bits;
+// hdof_sync reads and clears it), for the current device.  NULL on error.
+unsigned* status_ptr();
+
+// workspace layout (bytes) for a width x height frame
+struct WsLayout {
+    size_t mask_tiles;      // uint8 per mask tile
+    size_t trace_counts;    // uint32 per 16x16 tile: traced pixels, rays; + scan output
+    size_t trace_queue;     // uint32 per pixel
+    size_t pf_prep;         // float4 per pixel
+    size_t pf_tiles;        // float per 16x16 tile
+    size_t total;
+};
+WsLayout ws_layout(int W, int H, const hdof_params* p);
+
+// Lattice-area table of the soft disk (post-filter normalisation), uploaded
+// once per device.  Returns HDOF_OK or an error.
+int ensure_area_table(cudaStream_t s);
+int area_table_size();
+
+}  // namespace hdof
+
+struct hdof_bvh {
+    int device;
+    int n_tris;
+    int n_nodes;
+    int depth;
+    size_t bytes;
+    hdof::Node* nodes;
+    hdof::Tri* tris;
+    float4* mat;
+    float2* uv;
+    void* pool;  // single allocation holding all of the above
+    hdof::BvhView view() const {
+        hdof::BvhView v;
+        v.nodes = nodes;
+        v.tris = tris;
+        v.mat = mat;
+        v.uv = uv;
+        v.n_tris = n_tris;
+        v.root = 0;
+        return v;
+    }
+};

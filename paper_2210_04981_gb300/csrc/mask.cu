@@ -1,0 +1,199 @@
+// adaptive ray mask (Ray Trace section).  "Like Canny edge detection",
+// a Gaussian filter on the G-buffer reduces noise and jaggies, a Sobel kernel
+// on the filtered normal and depth finds geometry edges, and a temporally
+// accumulated luminance variance from previous frames adds rays where the
+// ray-traced output is noisy or new.
+//
+// k_mask_edge: one 16x16 pixel block per CUDA block; the block's (16+6)^2
+//   nd halo is staged in shared memory once, the separable 5-tap Gaussian
+//   runs as a row pass and a column pass in shared memory, then the 1/8
+//   scaled 3x3 Sobel; writes edge bits and marks the mask tiles that hold
+//   an edge.
+// k_mask_spp: per pixel, dilated tile flag and the variance term -> spp.
+#include <cmath>
+
+#include "internal.h"
+
+namespace hdof {
+namespace {
+
+constexpr int B = 16;            // pixel block edge
+constexpr int HALO = 3;          // 2 (Gaussian) + 1 (Sobel)
+constexpr int SRC = B + 2 * HALO;  // 22
+constexpr int FIL = B + 2;         // 18: filtered values needed by the Sobel
+
+struct GaussW {
+    float w[5];
+};
+
+template <class ND>
+__global__ void __launch_bounds__(256) k_mask_edge(const ND* __restrict__ nd, int W, int H, GaussW g, float tau,
+                                                   int tile, int ntx, uint8_t* __restrict__ edge,
+                                                   uint8_t* __restrict__ tiles) {
+    __shared__ float4 src[SRC][SRC];
+    __shared__ float4 row[SRC][FIL];
+    __shared__ float4 fil[FIL][FIL];
+    const int x0 = blockIdx.x * B, y0 = blockIdx.y * B;
+    const int tid = threadIdx.x;
+    // stage nd with clamp-to-edge (the Gaussian's border rule)
+    for (int k = tid; k < SRC * SRC; k += 256) {
+        int r = k / SRC, c = k % SRC;
+        int x = min(max(x0 - HALO + c, 0), W - 1), y = min(max(y0 - HALO + r, 0), H - 1);
+        src[r][c] = ld4(nd + (size_t)y * W + x);
+    }
+    __syncthreads();
+    // row pass: filtered columns x0-1 .. x0+16 for all 22 staged rows
+    for (int k = tid; k < SRC * FIL; k += 256) {
+        int r = k / FIL, c = k % FIL;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            float4 v = src[r][c + t];
+            a.x = fmaf(g.w[t], v.x, a.x);
+            a.y = fmaf(g.w[t], v.y, a.y);
+            a.z = fmaf(g.w[t], v.z, a.z);
+            a.w = fmaf(g.w[t], v.w, a.w);
+        }
+        row[r][c] = a;
+    }
+    __syncthreads();
+    // column pass: filtered rows y0-1 .. y0+16
+    for (int k = tid; k < FIL * FIL; k += 256) {
+        int r = k / FIL, c = k % FIL;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            float4 v = row[r + t][c];
+            a.x = fmaf(g.w[t], v.x, a.x);
+            a.y = fmaf(g.w[t], v.y, a.y);
+            a.z = fmaf(g.w[t], v.z, a.z);
+            a.w = fmaf(g.w[t], v.w, a.w);
+        }
+        fil[r][c] = a;
+    }
+    __syncthreads();
+    const int lx = tid & 15, ly = tid >> 4;
+    const int i = x0 + lx, j = y0 + ly;
+    if (i >= W || j >= H) return;
+    // Sobel on the filtered image with clamp-to-edge (the Sobel's border rule):
+    // an out-of-image neighbour reads the filtered value of the border pixel
+    auto F = [&](int dx, int dy) -> float4 {
+        int x = min(max(i + dx, 0), W - 1), y = min(max(j + dy, 0), H - 1);
+        return fil[y - (y0 - 1)][x - (x0 - 1)];
+    };
+    float gx[4] = {0, 0, 0, 0}, gy[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = -1; k <= 1; ++k) {
+        float wk = k == 0 ? 2.f : 1.f;
+        float4 r = F(1, k), l = F(-1, k), dn = F(k, 1), up = F(k, -1);
+        gx[0] += wk * (r.x - l.x);
+        gx[1] += wk * (r.y - l.y);
+        gx[2] += wk * (r.z - l.z);
+        gx[3] += wk * (r.w - l.w);
+        gy[0] += wk * (dn.x - up.x);
+        gy[1] += wk * (dn.y - up.y);
+        gy[2] += wk * (dn.z - up.z);
+        gy[3] += wk * (dn.w - up.w);
+    }
+    for (int c = 0; c < 4; ++c) {
+        gx[c] *= 0.125f;
+        gy[c] *= 0.125f;
+    }
+    float en = sqrtf(gx[0] * gx[0] + gy[0] * gy[0] + gx[1] * gx[1] + gy[1] * gy[1] + gx[2] * gx[2] + gy[2] * gy[2]);
+    float ez = sqrtf(gx[3] * gx[3] + gy[3] * gy[3]) / fil[ly + 1][lx + 1].w;
+    float e = fmaxf(en, ez);
+    uint8_t bit = e > tau ? 1 : 0;
+    edge[(size_t)j * W + i] = bit;
+    if (bit) tiles[(j / tile) * ntx + i / tile] = 1;
+}
+
+__global__ void __launch_bounds__(256) k_mask_spp(int W, int H, int tile, int ntx, int nty, int dil,
+                                                  const uint8_t* __restrict__ tiles, int variance_on,
+                                                  const float2* __restrict__ mv, const float2* __restrict__ hmom,
+                                                  const uint8_t* __restrict__ hhlen, int spp_max, float var_tau,
+                                                  float var_scale, int hlen_young, uint8_t* __restrict__ spp) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= W || j >= H) return;
+    size_t q = (size_t)j * W + i;
+    int tx = i / tile, ty = j / tile;
+    bool on = false;
+    for (int b = -dil; b <= dil && !on; ++b) {
+        int y = ty + b;
+        if (y < 0 || y >= nty) continue;
+        for (int a = -dil; a <= dil; ++a) {
+            int x = tx + a;
+            if (x >= 0 && x < ntx && __ldg(&tiles[y * ntx + x])) {
+                on = true;
+                break;
+            }
+        }
+    }
+    int s = on ? spp_max : 0;
+    if (!on && variance_on) {
+        float2 m = __ldg(&mv[q]);
+        float fx = floorf((float)i - m.x + 0.5f), fy = floorf((float)j - m.y + 0.5f);
+        int hl = 0;
+        float m1 = 0.f, m2 = 0.f;
+        if (fx >= 0.f && fy >= 0.f && fx < (float)W && fy < (float)H) {
+            size_t t = (size_t)fy * W + (size_t)fx;
+            hl = __ldg(&hhlen[t]);
+            float2 mm = __ldg(&hmom[t]);
+            m1 = mm.x;
+            m2 = mm.y;
+        }
+        float sig = sqrtf(fmaxf(0.f, m2 - m1 * m1));
+        bool young = hl < hlen_young;
+        if (hl >= 1 && (young || sig > var_tau)) {
+            if (young) s = spp_max;
+            else s = (int)fminf(fmaxf(ceilf((float)spp_max * sig / var_scale), 1.f), (float)spp_max);
+        }
+    }
+    spp[q] = (uint8_t)s;
+}
+
+}  // namespace
+}  // namespace hdof
+
+using namespace hdof;
+
+extern "C" int hdof_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p, uint8_t* edge,
+                         uint8_t* spp, void* workspace, size_t workspace_bytes, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_params(p, "hdof_mask")) || (rc = check_gbuf(in, "hdof_mask", false))) return rc;
+    HDOF_CHECK_ARG(edge && spp, "hdof_mask: edge and spp outputs are required");
+    const int W = in->width, H = in->height;
+    bool var = p->variance_on && prev_hist;
+    HDOF_CHECK_ARG(!var || (prev_hist->mom && prev_hist->hlen && in->mv),
+                   "hdof_mask: the variance term needs mv and the history mom/hlen planes");
+    WsLayout L = ws_layout(W, H, p);
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.mask_tiles, "hdof_mask: workspace of %zu bytes < %zu",
+                   workspace_bytes, L.mask_tiles);
+    cudaStream_t s = as_stream(stream);
+    const int T = p->tile, ntx = (W + T - 1) / T, nty = (H + T - 1) / T;
+    uint8_t* tiles = static_cast<uint8_t*>(workspace);
+    HDOF_CUDA(cudaMemsetAsync(tiles, 0, (size_t)ntx * nty, s), "hdof_mask: clear tiles");
+    GaussW g;
+    double w[5], sum = 0.0;
+    for (int k = -2; k <= 2; ++k) {
+        w[k + 2] = std::exp(-(double)(k * k) / (2.0 * (double)p->gauss_sigma * (double)p->gauss_sigma));
+        sum += w[k + 2];
+    }
+    for (int k = 0; k < 5; ++k) g.w[k] = (float)(w[k] / sum);
+    dim3 grid((W + B - 1) / B, (H + B - 1) / B);
+    if (in->dtype_nd == HDOF_F32)
+        k_mask_edge<float4><<<grid, 256, 0, s>>>(static_cast<const float4*>(in->nd), W, H, g, p->edge_tau, T, ntx,
+                                                 edge, tiles);
+    else
+        k_mask_edge<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, g, p->edge_tau, T, ntx,
+                                                 edge, tiles);
+    HDOF_LAUNCHED("hdof_mask: edge");
+    dim3 g2((W + 31) / 32, (H + 7) / 8);
+    k_mask_spp<<<g2, 256, 0, s>>>(W, H, T, ntx, nty, p->dilate, tiles, var ? 1 : 0,
+                                  reinterpret_cast<const float2*>(in->mv),
+                                  var ? reinterpret_cast<const float2*>(prev_hist->mom) : nullptr,
+                                  var ? prev_hist->hlen : nullptr, p->spp_max, p->var_tau, p->var_scale,
+                                  p->hlen_young, spp);
+    HDOF_LAUNCHED("hdof_mask: spp");
+    return HDOF_OK;
+}

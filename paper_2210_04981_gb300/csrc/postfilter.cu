@@ -1,0 +1,246 @@
+// post-process CoC filter of the sharp image (Design section: the sharp
+// rasterised image "undergoes post-process filtering"; the Reconstruction
+// section states its rejection rule: samples whose CoC radius is smaller
+// than their distance to the pixel are rejected).
+//
+// Scatter-as-gather with soft disks.  Pixel q scatters its colour over
+// s(r_q - d), s(x) = clamp(x + 1/2, 0, 1), r_q = min(|c(z_q)|/2, r_max),
+// normalised by the disk's lattice area a(r) = sum_o s(r - |o|) so that each
+// pixel scatters unit weight.  a(r) is piecewise linear in r with breaks at
+// |o| +- 1/2; a table of its breakpoints is built once per device and
+// evaluated by binary search, which is exact up to float rounding.
+//
+// k_pf_prep: per pixel (r, w_near/a, (1-w_near)/a, z) and per 16x16 tile the
+//   largest r.  k_pf_gather: per tile the gather window is bounded by the
+//   largest radius among tiles that can reach it; every tap outside that
+//   window has zero weight, so the bounded gather equals the full one.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace hdof {
+namespace {
+
+constexpr int TP = HDOF_TILE_PF;
+constexpr int AREA_MAX = 16384;  // breakpoints for radii up to 127.5
+
+// (x_m, a(x_m), slope on [x_m, x_{m+1}], 0)
+__device__ float4 g_area[AREA_MAX];
+__device__ int g_area_n;
+
+__device__ __forceinline__ float disk_area(float r) {
+    int lo = 0, hi = g_area_n - 1;  // largest m with x_m <= r
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&g_area[mid].x) <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    float4 e = __ldg(&g_area[lo]);
+    return fmaf(e.z, r - e.x, e.y);
+}
+
+template <class ND>
+__global__ void __launch_bounds__(256) k_pf_prep(const ND* __restrict__ nd, int W, int H, Coc coc, float rmax,
+                                                 int ntx, float4* __restrict__ prep, float* __restrict__ tmax) {
+    int i = blockIdx.x * TP + (threadIdx.x & 15), j = blockIdx.y * TP + (threadIdx.x >> 4);
+    float r = 0.f;
+    if (i < W && j < H) {
+        size_t q = (size_t)j * W + i;
+        float z = ldz(nd + q);
+        float c = coc(z);
+        r = fminf(fabsf(c) * 0.5f, rmax);
+        float ia = 1.f / disk_area(r);
+        float wn = w_near(c);
+        prep[q] = make_float4(r, wn * ia, (1.f - wn) * ia, z);
+    }
+    for (int o = 16; o; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    __shared__ float red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = red[0];
+        for (int k = 1; k < 8; ++k) m = fmaxf(m, red[k]);
+        tmax[blockIdx.y * ntx + blockIdx.x] = m;
+    }
+}
+
+template <class COL>
+__global__ void __launch_bounds__(256) k_pf_gather(const float4* __restrict__ prep, const COL* __restrict__ col,
+                                                   const float* __restrict__ tmax, int W, int H, int ntx, int nty,
+                                                   int kt, float kz_rel, float4* __restrict__ pp) {
+    __shared__ int s_win;
+    if (threadIdx.x == 0) s_win = 0;
+    __syncthreads();
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    // window: largest r + 1/2 over tiles whose pixels can reach this tile
+    for (int k = threadIdx.x; k < (2 * kt + 1) * (2 * kt + 1); k += blockDim.x) {
+        int ox = k % (2 * kt + 1) - kt, oy = k / (2 * kt + 1) - kt;
+        int x = tx + ox, y = ty + oy;
+        if (x < 0 || y < 0 || x >= ntx || y >= nty) continue;
+        float r = __ldg(&tmax[y * ntx + x]);
+        // pixel gap between the two tiles along each axis
+        float gx = (float)max(0, (abs(ox) - 1) * TP + 1), gy = (float)max(0, (abs(oy) - 1) * TP + 1);
+        if (ox == 0) gx = 0.f;
+        if (oy == 0) gy = 0.f;
+        if (gx * gx + gy * gy < (r + 0.5f) * (r + 0.5f)) atomicMax(&s_win, (int)ceilf(r + 0.5f));
+    }
+    __syncthreads();
+    const int G = s_win;
+    // warp w covers the 8x4 sub-block ((w & 1) * 8, (w >> 1) * 4) of the 16x16 tile
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int i = tx * TP + (w & 1) * 8 + (l & 7), j = ty * TP + (w >> 1) * 4 + (l >> 3);
+    if (i >= W || j >= H) return;
+    const size_t pq = (size_t)j * W + i;
+    const float zp = __ldg(&prep[pq].w);
+    const float ka = 1.f + 1.f / kz_rel, kb = 1.f / (kz_rel * zp);  // k_z = clamp(ka - z_q kb)
+    float3 Sn = f3(0, 0, 0), Sf = f3(0, 0, 0);
+    float Wn = 0.f, Wf = 0.f;
+    const int y0 = max(j - G, 0), y1 = min(j + G, H - 1), x0 = max(i - G, 0), x1 = min(i + G, W - 1);
+    for (int y = y0; y <= y1; ++y) {
+        const float dy = (float)(y - j);
+        for (int x = x0; x <= x1; ++x) {
+            const float dx = (float)(x - i);
+            const size_t q = (size_t)y * W + x;
+            float4 e = __ldg(&prep[q]);
+            float s = soft_step(e.x - sqrtf(fmaf(dx, dx, dy * dy)));
+            if (s > 0.f) {
+                float4 c = ld4(col + q);
+                float an = s * e.y;
+                float af = s * e.z * clamp01(fmaf(-e.w, kb, ka));
+                Sn = Sn + an * f3(c.x, c.y, c.z);
+                Sf = Sf + af * f3(c.x, c.y, c.z);
+                Wn += an;
+                Wf += af;
+            }
+        }
+    }
+    float alpha = clamp01(Wn);
+    float3 N = Wn > HDOF_PP_MIN_W ? (1.f / Wn) * Sn : f3(0, 0, 0);
+    float3 F;
+    if (Wf > HDOF_PP_MIN_W) F = (1.f / Wf) * Sf;
+    else {
+        float4 c = ld4(col + pq);
+        F = f3(c.x, c.y, c.z);
+    }
+    float3 o = alpha * N + (1.f - alpha) * F;
+    pp[pq] = make_float4(o.x, o.y, o.z, alpha);
+}
+
+std::mutex g_area_mu;
+bool g_area_ready[64] = {false};
+
+}  // namespace
+
+int area_table_size() { return AREA_MAX; }
+
+int ensure_area_table(cudaStream_t s) {
+    int dev = 0;
+    HDOF_CUDA(cudaGetDevice(&dev), "area table: device");
+    if (dev < 0 || dev >= 64) {
+        set_error("area table: device index %d unsupported", dev);
+        return HDOF_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_area_mu);
+    if (g_area_ready[dev]) return HDOF_OK;
+    // lattice distances sqrt(k) with multiplicity n(k), |o| < 128.5
+    const int R = 129;
+    std::vector<int> mult(R * R + 1, 0);
+    for (int b = -R; b <= R; ++b)
+        for (int a = -R; a <= R; ++a) {
+            int k = a * a + b * b;
+            if (k <= R * R) mult[k]++;
+        }
+    std::vector<double> rad, pre_n, pre_nr;  // sorted sqrt(k), prefix sums of n and n*sqrt(k)
+    double cn = 0, cnr = 0;
+    for (int k = 0; k <= R * R; ++k)
+        if (mult[k]) {
+            double r = std::sqrt((double)k);
+            rad.push_back(r);
+            cn += mult[k];
+            cnr += mult[k] * r;
+            pre_n.push_back(cn);
+            pre_nr.push_back(cnr);
+        }
+    // a(x) = #{|o| <= x - 1/2} + sum_{x-1/2 < |o| < x+1/2} (x + 1/2 - |o|)
+    auto area = [&](double x) {
+        auto cnt_le = [&](double v, bool strict) -> int {  // number of radii (<= v) or (< v)
+            return (int)(strict ? std::lower_bound(rad.begin(), rad.end(), v) - rad.begin()
+                                : std::upper_bound(rad.begin(), rad.end(), v) - rad.begin());
+        };
+        int full = cnt_le(x - 0.5, false);
+        int part_end = cnt_le(x + 0.5, true);
+        double nf = full ? pre_n[full - 1] : 0.0;
+        double np = (part_end ? pre_n[part_end - 1] : 0.0) - nf;
+        double nrp = (part_end ? pre_nr[part_end - 1] : 0.0) - (full ? pre_nr[full - 1] : 0.0);
+        return nf + (x + 0.5) * np - nrp;
+    };
+    std::vector<double> bp;
+    for (double r : rad) {
+        if (r - 0.5 <= 128.0) bp.push_back(r - 0.5);
+        if (r + 0.5 <= 128.0) bp.push_back(r + 0.5);
+    }
+    std::sort(bp.begin(), bp.end());
+    bp.erase(std::unique(bp.begin(), bp.end()), bp.end());
+    if ((int)bp.size() > AREA_MAX) {
+        set_error("area table: %zu breakpoints exceed %d", bp.size(), AREA_MAX);
+        return HDOF_EUNSUPPORTED;
+    }
+    std::vector<float4> tab(bp.size());
+    for (size_t m = 0; m < bp.size(); ++m) {
+        double a0 = area(bp[m]);
+        double slope = 0.0;
+        if (m + 1 < bp.size()) slope = (area(bp[m + 1]) - a0) / (bp[m + 1] - bp[m]);
+        tab[m] = make_float4((float)bp[m], (float)a0, (float)slope, 0.f);
+    }
+    int n = (int)tab.size();
+    HDOF_CUDA(cudaMemcpyToSymbolAsync(g_area, tab.data(), sizeof(float4) * tab.size(), 0, cudaMemcpyHostToDevice, s),
+              "area table: upload");
+    HDOF_CUDA(cudaMemcpyToSymbolAsync(g_area_n, &n, sizeof n, 0, cudaMemcpyHostToDevice, s), "area table: upload");
+    HDOF_CUDA(cudaStreamSynchronize(s), "area table: upload");
+    g_area_ready[dev] = true;
+    return HDOF_OK;
+}
+
+}  // namespace hdof
+
+using namespace hdof;
+
+extern "C" int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, const hdof_lens* lens,
+                               const hdof_params* p, float* pp, void* workspace, size_t workspace_bytes,
+                               void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_camera(cam, "hdof_postfilter")) || (rc = check_lens(lens, "hdof_postfilter")) ||
+        (rc = check_params(p, "hdof_postfilter")) || (rc = check_gbuf(in, "hdof_postfilter", false)))
+        return rc;
+    HDOF_CHECK_ARG(pp, "hdof_postfilter: pp output is required");
+    HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "hdof_postfilter: gbuf/camera size mismatch");
+    const int W = in->width, H = in->height;
+    WsLayout L = ws_layout(W, H, p);
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.pf_prep + L.pf_tiles,
+                   "hdof_postfilter: workspace of %zu bytes < %zu", workspace_bytes, L.pf_prep + L.pf_tiles);
+    cudaStream_t s = as_stream(stream);
+    if ((rc = ensure_area_table(s))) return rc;
+    float4* prep = static_cast<float4*>(workspace);
+    float* tmax = reinterpret_cast<float*>(static_cast<char*>(workspace) + L.pf_prep);
+    const int ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
+    Coc coc = make_coc(*lens, H, cam->tan_half_fovy);
+    dim3 grid(ntx, nty);
+    if (in->dtype_nd == HDOF_F32)
+        k_pf_prep<float4><<<grid, 256, 0, s>>>(static_cast<const float4*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
+    else
+        k_pf_prep<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
+    HDOF_LAUNCHED("hdof_postfilter: prep");
+    int kt = (int)std::ceil((p->r_max + 0.5f) / TP) + 1;
+    if (in->dtype_col == HDOF_F32)
+        k_pf_gather<float4><<<grid, 256, 0, s>>>(prep, static_cast<const float4*>(in->col), tmax, W, H, ntx, nty, kt,
+                                                 p->kz_rel, reinterpret_cast<float4*>(pp));
+    else
+        k_pf_gather<bf164s><<<grid, 256, 0, s>>>(prep, static_cast<const bf164s*>(in->col), tmax, W, H, ntx, nty, kt,
+                                                 p->kz_rel, reinterpret_cast<float4*>(pp));
+    HDOF_LAUNCHED("hdof_postfilter: gather");
+    return HDOF_OK;
+}

@@ -1,0 +1,273 @@
+// spatio-temporal reconstruction of the ray-traced layers
+// (Reconstruction section).
+//
+// Temporal (k_temporal, one thread per pixel): near and far colours are
+// accumulated separately with an exponential moving average, each weighted
+// by its share of the hit ratio.  Near terms are reprojected with the
+// screen-space motion vector; far terms with the previous-frame projection
+// of the average far world position of the pixel's far hits (or of its
+// neighbours' when it has none, or of its G-buffer surface).  The composed
+// colour uses this frame's hit ratio when the camera moved and the
+// accumulated one otherwise; each layer is normalised by its accumulated
+// hit-ratio weight.  The reconstructed CoC blends this frame's near and far
+// CoC by the accumulated hit ratio.
+//
+// Spatial (k_spatial, one thread per traced pixel): a circular gather scaled
+// by the pixel's CoC that rejects samples whose CoC radius is smaller than
+// their distance, blended by the clamped luminance variance so converged
+// regions are not over-blurred.
+#include "internal.h"
+
+namespace hdof {
+namespace {
+
+struct TemporalArgs {
+    Cam cam, prev;
+    int W, H;
+    float alpha;
+    int moved;
+    const float4* rt;  // 3 per pixel
+    const uint8_t* spp;
+    const float2* mv;
+    const float4* hn;  // previous history
+    const float4* hf;
+    const float2* hm;
+    const uint8_t* hl;
+    float4* on;  // new history
+    float4* of;
+    float2* om;
+    uint8_t* ol;
+    float4* crt;
+    float* hacc;
+};
+
+__device__ __forceinline__ void acc(float4& o, float w, float4 v) {
+    o.x = fmaf(w, v.x, o.x);
+    o.y = fmaf(w, v.y, o.y);
+    o.z = fmaf(w, v.z, o.z);
+    o.w = fmaf(w, v.w, o.w);
+}
+__device__ __forceinline__ void acc(float2& o, float w, float2 v) {
+    o.x = fmaf(w, v.x, o.x);
+    o.y = fmaf(w, v.y, o.y);
+}
+__device__ __forceinline__ void scale(float4& o, float s) {
+    o.x *= s;
+    o.y *= s;
+    o.z *= s;
+    o.w *= s;
+}
+__device__ __forceinline__ void scale(float2& o, float s) {
+    o.x *= s;
+    o.y *= s;
+}
+__device__ __forceinline__ void zero(float4& o) { o = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void zero(float2& o) { o = make_float2(0.f, 0.f); }
+
+// bilinear history sample over taps that hold history (hlen > 0), renormalised;
+// invalid below a total tap weight of 1e-3.  hmax: largest hlen among taps
+// with non-zero weight.
+template <class T>
+__device__ __forceinline__ bool hist_sample(const TemporalArgs& a, float ux, float uy, const T* plane, T& out,
+                                            int* hmax) {
+    float x0 = floorf(ux), y0 = floorf(uy), fx = ux - x0, fy = uy - y0;
+    float ws = 0.f;
+    zero(out);
+    if (hmax) *hmax = 0;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float x = x0 + c, y = y0 + b;
+            if (x < 0.f || y < 0.f || x >= (float)a.W || y >= (float)a.H) continue;
+            size_t q = (size_t)y * a.W + (size_t)x;
+            int hl = __ldg(&a.hl[q]);
+            if (hl == 0) continue;
+            float w = (c ? fx : 1.f - fx) * (b ? fy : 1.f - fy);
+            ws += w;
+            acc(out, w, __ldg(&plane[q]));
+            if (hmax && w > 0.f && hl > *hmax) *hmax = hl;
+        }
+    if (!(ws >= HDOF_HIST_MIN_W)) return false;
+    scale(out, 1.f / ws);
+    return true;
+}
+
+template <class ND>
+__global__ void __launch_bounds__(256) k_temporal(TemporalArgs a, const ND* __restrict__ nd) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= a.W || j >= a.H) return;
+    size_t q = (size_t)j * a.W + i;
+    if (a.spp[q] == 0) {
+        a.ol[q] = 0;
+        a.crt[q] = make_float4(0.f, 0.f, 0.f, -1.f);
+        return;
+    }
+    const float4 r0 = __ldg(&a.rt[3 * q]), r1 = __ldg(&a.rt[3 * q + 1]), r2 = __ldg(&a.rt[3 * q + 2]);
+    const float h = r0.w, cn = r1.w, cf = r2.w;
+    const bool nok = cn >= 0.f, fok = cf >= 0.f;
+    float3 Cn = f3(r0.x, r0.y, r0.z), Cf = f3(r1.x, r1.y, r1.z);
+    float3 Ccur = nok ? (fok ? h * Cn + (1.f - h) * Cf : Cn) : Cf;
+    float Y = luminance(Ccur);
+    // near reprojection
+    float2 m = __ldg(&a.mv[q]);
+    float un = (float)i - m.x, vn = (float)j - m.y;
+    float4 hn;
+    float2 hm = make_float2(0.f, 0.f);
+    int hl = 0;
+    bool vn_ok = hist_sample(a, un, vn, a.hn, hn, &hl);
+    if (vn_ok) hist_sample(a, un, vn, a.hm, hm, (int*)nullptr);
+    // far world position
+    float3 P;
+    if (fok) {
+        P = f3(r2.x, r2.y, r2.z);
+    } else {
+        float3 s = f3(0.f, 0.f, 0.f);
+        int cnt = 0;
+        for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+                if (!b && !c) continue;
+                int x = i + c, y = j + b;
+                if (x < 0 || y < 0 || x >= a.W || y >= a.H) continue;
+                size_t qq = (size_t)y * a.W + x;
+                if (a.spp[qq] == 0) continue;
+                float4 p2 = __ldg(&a.rt[3 * qq + 2]);
+                if (p2.w < 0.f) continue;
+                s = s + f3(p2.x, p2.y, p2.z);
+                ++cnt;
+            }
+        if (cnt > 0) {
+            P = (1.f / (float)cnt) * s;
+        } else {
+            float3 d = pinhole_dir(a.cam, i + 0.5f + a.cam.jx, j + 0.5f + a.cam.jy);
+            P = a.cam.pos + ldz(nd + q) * d;
+        }
+    }
+    float uf, vf;
+    float4 hf;
+    bool vf_ok = project(a.prev, P, uf, vf) && hist_sample(a, uf, vf, a.hf, hf, (int*)nullptr);
+    // EMA
+    const float al = a.alpha;
+    float4 cur_n = make_float4(h * Cn.x, h * Cn.y, h * Cn.z, h);
+    float4 cur_f = make_float4((1.f - h) * Cf.x, (1.f - h) * Cf.y, (1.f - h) * Cf.z, 1.f - h);
+    float4 on = vn_ok ? make_float4(fmaf(al, cur_n.x - hn.x, hn.x), fmaf(al, cur_n.y - hn.y, hn.y),
+                                    fmaf(al, cur_n.z - hn.z, hn.z), fmaf(al, cur_n.w - hn.w, hn.w))
+                      : cur_n;
+    float4 of = vf_ok ? make_float4(fmaf(al, cur_f.x - hf.x, hf.x), fmaf(al, cur_f.y - hf.y, hf.y),
+                                    fmaf(al, cur_f.z - hf.z, hf.z), fmaf(al, cur_f.w - hf.w, hf.w))
+                      : cur_f;
+    float2 om = vn_ok ? make_float2(fmaf(al, Y - hm.x, hm.x), fmaf(al, Y * Y - hm.y, hm.y)) : make_float2(Y, Y * Y);
+    int nh = vn_ok ? hl + 1 : 1;
+    a.on[q] = on;
+    a.of[q] = of;
+    a.om[q] = om;
+    a.ol[q] = (uint8_t)(nh > 255 ? 255 : nh);
+    // accumulated hit ratio and composition
+    float Bn = on.w, Bf = of.w;
+    float Hacc = (Bn + Bf >= HDOF_EMPTY_W) ? Bn / (Bn + Bf) : h;
+    bool an = Bn >= HDOF_EMPTY_W, af = Bf >= HDOF_EMPTY_W;
+    float hw = a.moved ? h : Hacc;
+    float3 CnA = an ? (1.f / Bn) * f3(on.x, on.y, on.z) : f3(0, 0, 0);
+    float3 CfA = af ? (1.f / Bf) * f3(of.x, of.y, of.z) : f3(0, 0, 0);
+    float3 C = !an ? CfA : (!af ? CnA : hw * CnA + (1.f - hw) * CfA);
+    float crt_c = !nok ? cf : (!fok ? cn : Hacc * cn + (1.f - Hacc) * cf);
+    a.crt[q] = make_float4(C.x, C.y, C.z, crt_c);
+    a.hacc[q] = Hacc;
+}
+
+__global__ void __launch_bounds__(256) k_spatial(const float4* __restrict__ crt, const float2* __restrict__ mom,
+                                                 const uint8_t* __restrict__ hlen, int W, int H, float r_s,
+                                                 float var_ref, float4* __restrict__ crec) {
+    // warp = 8x4 pixel block, block = 16x16 pixels
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7), j = blockIdx.y * 16 + (w >> 1) * 4 + (l >> 3);
+    if (i >= W || j >= H) return;
+    const size_t q = (size_t)j * W + i;
+    const float4 cp = __ldg(&crt[q]);
+    if (cp.w < 0.f) return;  // untraced
+    const float rp = fminf(cp.w * 0.5f, r_s);
+    const int K = (int)ceilf(rp + 0.5f);
+    float3 S = f3(0, 0, 0);
+    float Ws = 0.f;
+    const int y0 = max(j - K, 0), y1 = min(j + K, H - 1), x0 = max(i - K, 0), x1 = min(i + K, W - 1);
+    for (int y = y0; y <= y1; ++y) {
+        float dy = (float)(y - j);
+        for (int x = x0; x <= x1; ++x) {
+            float dx = (float)(x - i);
+            float4 c = __ldg(&crt[(size_t)y * W + x]);
+            if (c.w < 0.f) continue;
+            float d = sqrtf(fmaf(dx, dx, dy * dy));
+            float wq = soft_step(rp - d) * soft_step(fminf(c.w * 0.5f, r_s) - d);
+            if (wq > 0.f) {
+                S = S + wq * f3(c.x, c.y, c.z);
+                Ws += wq;
+            }
+        }
+    }
+    float2 m = __ldg(&mom[q]);
+    float sig = sqrtf(fmaxf(0.f, m.y - m.x * m.x));
+    float beta = __ldg(&hlen[q]) < 2 ? 1.f : clamp01(sig / var_ref);
+    float3 Csp = (1.f / Ws) * S;
+    crec[q] = make_float4(cp.x + beta * (Csp.x - cp.x), cp.y + beta * (Csp.y - cp.y), cp.z + beta * (Csp.z - cp.z),
+                          0.f);
+}
+
+}  // namespace
+}  // namespace hdof
+
+using namespace hdof;
+
+static bool hist_ok(const hdof_history* h) { return h && h->near_acc && h->far_acc && h->mom && h->hlen; }
+
+extern "C" int hdof_reconstruct(const float* rt, const hdof_gbuf* in, const uint8_t* spp, const hdof_camera* cam,
+                                const hdof_camera* prev, const hdof_lens* lens, const hdof_params* p,
+                                const hdof_history* hist_in, const hdof_history* hist_out, float* crt, float* hacc,
+                                float* crec, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_camera(cam, "hdof_reconstruct")) || (rc = check_camera(prev, "hdof_reconstruct: prev")) ||
+        (rc = check_lens(lens, "hdof_reconstruct")) || (rc = check_params(p, "hdof_reconstruct")) ||
+        (rc = check_gbuf(in, "hdof_reconstruct", true)))
+        return rc;
+    HDOF_CHECK_ARG(rt && spp && crt && hacc && crec, "hdof_reconstruct: NULL buffer");
+    HDOF_CHECK_ARG(hist_ok(hist_in) && hist_ok(hist_out), "hdof_reconstruct: history planes are required");
+    HDOF_CHECK_ARG(hist_in->near_acc != hist_out->near_acc && hist_in->far_acc != hist_out->far_acc &&
+                       hist_in->mom != hist_out->mom && hist_in->hlen != hist_out->hlen,
+                   "hdof_reconstruct: hist_in and hist_out must be distinct buffers");
+    HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height && prev->width == cam->width &&
+                       prev->height == cam->height,
+                   "hdof_reconstruct: size mismatch");
+    cudaStream_t s = as_stream(stream);
+    const int W = cam->width, H = cam->height;
+    TemporalArgs a;
+    a.cam = make_cam(*cam);
+    a.prev = make_cam(*prev);
+    a.W = W;
+    a.H = H;
+    a.alpha = p->ema_alpha;
+    a.moved = p->camera_moved;
+    a.rt = reinterpret_cast<const float4*>(rt);
+    a.spp = spp;
+    a.mv = reinterpret_cast<const float2*>(in->mv);
+    a.hn = reinterpret_cast<const float4*>(hist_in->near_acc);
+    a.hf = reinterpret_cast<const float4*>(hist_in->far_acc);
+    a.hm = reinterpret_cast<const float2*>(hist_in->mom);
+    a.hl = hist_in->hlen;
+    a.on = reinterpret_cast<float4*>(hist_out->near_acc);
+    a.of = reinterpret_cast<float4*>(hist_out->far_acc);
+    a.om = reinterpret_cast<float2*>(hist_out->mom);
+    a.ol = hist_out->hlen;
+    a.crt = reinterpret_cast<float4*>(crt);
+    a.hacc = hacc;
+    dim3 g1((W + 31) / 32, (H + 7) / 8);
+    if (in->dtype_nd == HDOF_F32)
+        k_temporal<float4><<<g1, 256, 0, s>>>(a, static_cast<const float4*>(in->nd));
+    else
+        k_temporal<half4s><<<g1, 256, 0, s>>>(a, static_cast<const half4s*>(in->nd));
+    HDOF_LAUNCHED("hdof_reconstruct: temporal");
+    dim3 g2((W + 15) / 16, (H + 15) / 16);
+    k_spatial<<<g2, 256, 0, s>>>(reinterpret_cast<const float4*>(crt), reinterpret_cast<const float2*>(hist_out->mom),
+                                 hist_out->hlen, W, H, p->r_s, p->var_ref, reinterpret_cast<float4*>(crec));
+    HDOF_LAUNCHED("hdof_reconstruct: spatial");
+    return HDOF_OK;
+}

@@ -1,0 +1,365 @@
+"""Python binding of ``libhdof.so`` (ctypes).
+
+One function per C entry point, with the same name; each marshals torch
+tensors (device memory, current stream) and parameter records into the C
+structs, calls the library and raises :class:`HdofError` on a non-zero
+status.  No step of the frame runs here: every computation is a kernel in
+the library.  The library must be built (``paper_2210_04981_gb300.build``);
+loading fails loudly when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhdof.so")
+
+HDOF_F32, HDOF_F16, HDOF_BF16 = 0, 1, 2
+_ERRNAMES = {-1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ETIMEOUT", -5: "EUNSUPPORTED"}
+
+
+class HdofError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hdof_camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3),
+                ("fwd", C.c_float * 3), ("tan_half_fovy", C.c_float), ("width", C.c_int32),
+                ("height", C.c_int32), ("jitter", C.c_float * 2)]
+
+
+class hdof_lens(C.Structure):
+    _fields_ = [("focus_dist", C.c_float), ("aperture_radius", C.c_float),
+                ("focal_length", C.c_float)]
+
+
+class hdof_params(C.Structure):
+    _fields_ = [("gauss_sigma", C.c_float), ("edge_tau", C.c_float), ("tile", C.c_int32),
+                ("dilate", C.c_int32), ("spp_max", C.c_int32), ("variance_on", C.c_int32),
+                ("var_tau", C.c_float), ("var_scale", C.c_float), ("hlen_young", C.c_int32),
+                ("seed", C.c_uint32), ("frame", C.c_int32), ("view", C.c_int32),
+                ("k_ambient", C.c_float), ("n_lights", C.c_int32),
+                ("light_dir", (C.c_float * 3) * 4), ("light_E", C.c_float * 4),
+                ("miss_dist", C.c_float), ("trav_cap", C.c_int32), ("ema_alpha", C.c_float),
+                ("camera_moved", C.c_int32), ("r_s", C.c_float), ("var_ref", C.c_float),
+                ("r_max", C.c_float), ("kz_rel", C.c_float), ("h_tau", C.c_float)]
+
+
+class hdof_gbuf(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("dtype_nd", C.c_int32),
+                ("dtype_col", C.c_int32), ("nd", C.c_void_p), ("col", C.c_void_p),
+                ("mv", C.c_void_p), ("tri", C.c_void_p)]
+
+
+class hdof_history(C.Structure):
+    _fields_ = [("near_acc", C.c_void_p), ("far_acc", C.c_void_p), ("mom", C.c_void_p),
+                ("hlen", C.c_void_p)]
+
+
+class hdof_bvh_stats(C.Structure):
+    _fields_ = [("n_tris", C.c_int32), ("n_nodes", C.c_int32), ("depth", C.c_int32),
+                ("reserved", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libhdof.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhdof.so not found at {LIB_PATH}: build it with "
+                           "`python -m paper_2210_04981_gb300.build` (nvcc, sm_103a)")
+    L = C.CDLL(LIB_PATH)
+    P, vp, i32, sz = C.POINTER, C.c_void_p, C.c_int32, C.c_size_t
+    sig = {
+        "hdof_version": ([], C.c_char_p),
+        "hdof_last_error": ([C.c_char_p, sz], C.c_int),
+        "hdof_sync": ([vp], C.c_int),
+        "hdof_default_params": ([P(hdof_params)], None),
+        "hdof_build_bvh": ([vp, i32, vp, i32, vp, vp, P(vp), vp], C.c_int),
+        "hdof_bvh_destroy": ([vp], C.c_int),
+        "hdof_bvh_info": ([vp, P(hdof_bvh_stats)], C.c_int),
+        "hdof_closest_hits": ([vp, i32, vp, vp, vp, vp, vp], C.c_int),
+        "hdof_gbuffer": ([vp, P(hdof_camera), P(hdof_camera), P(hdof_params), P(hdof_gbuf), vp], C.c_int),
+        "hdof_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
+        "hdof_mask": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp, sz, vp], C.c_int),
+        "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, sz, vp], C.c_int),
+        "hdof_postfilter": ([P(hdof_gbuf), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, sz, vp],
+                            C.c_int),
+        "hdof_reconstruct": ([vp, P(hdof_gbuf), vp, P(hdof_camera), P(hdof_camera), P(hdof_lens),
+                              P(hdof_params), P(hdof_history), P(hdof_history), vp, vp, vp, vp], C.c_int),
+        "hdof_composite": ([P(hdof_gbuf), vp, vp, vp, vp, vp, P(hdof_camera), P(hdof_lens), P(hdof_params),
+                            vp, vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C entry points this binding declares."""
+    return ["hdof_version", "hdof_last_error", "hdof_sync", "hdof_default_params", "hdof_build_bvh",
+            "hdof_bvh_destroy", "hdof_bvh_info", "hdof_closest_hits", "hdof_gbuffer", "hdof_workspace_bytes",
+            "hdof_mask", "hdof_trace", "hdof_postfilter", "hdof_reconstruct", "hdof_composite"]
+
+
+def _check(rc):
+    if rc != 0:
+        buf = C.create_string_buffer(1024)
+        load().hdof_last_error(buf, 1024)
+        raise HdofError(rc, buf.value.decode(errors="replace"))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("hdof buffers must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("hdof buffers must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------ records ----
+
+def camera(c) -> hdof_camera:
+    o = hdof_camera()
+    o.pos[:] = list(c.pos)
+    o.right[:] = list(c.right)
+    o.up[:] = list(c.up)
+    o.fwd[:] = list(c.fwd)
+    o.tan_half_fovy = c.tan_half_fovy
+    o.width, o.height = int(c.width), int(c.height)
+    o.jitter[:] = list(c.jitter)
+    return o
+
+
+def lens(l) -> hdof_lens:
+    return hdof_lens(l.focus_dist, l.aperture_radius, l.focal_length)
+
+
+_PARAM_NAMES = ("gauss_sigma", "edge_tau", "tile", "dilate", "spp_max", "variance_on", "var_tau", "var_scale",
+                "hlen_young", "seed", "frame", "view", "k_ambient", "miss_dist", "trav_cap", "ema_alpha",
+                "camera_moved", "r_s", "var_ref", "r_max", "kz_rel", "h_tau")
+
+
+def params(p=None) -> hdof_params:
+    """Marshal a parameter record (attributes named as the C fields; light
+    directions are normalised here); None gives the library defaults."""
+    o = hdof_params()
+    load().hdof_default_params(C.byref(o))
+    if p is None:
+        return o
+    for name in _PARAM_NAMES:
+        if hasattr(p, name):
+            setattr(o, name, getattr(p, name))
+    dirs = list(p.light_dir)
+    o.n_lights = len(dirs)
+    for k, (d, e) in enumerate(zip(dirs, p.light_E)):
+        n = math.sqrt(sum(float(x) ** 2 for x in d))
+        o.light_dir[k][:] = [float(x) / n for x in d]
+        o.light_E[k] = float(e)
+    return o
+
+
+# ------------------------------------------------------------- buffers ---
+
+class GBuffer:
+    """Device planes of one frame's G-buffer (torch tensors)."""
+
+    def __init__(self, width, height, device="cuda", nd_dtype=torch.float32, col_dtype=torch.float32):
+        self.width, self.height = int(width), int(height)
+        self.nd = torch.empty((height, width, 4), dtype=nd_dtype, device=device)
+        self.col = torch.empty((height, width, 4), dtype=col_dtype, device=device)
+        self.mv = torch.empty((height, width, 2), dtype=torch.float32, device=device)
+        self.tri = torch.empty((height, width), dtype=torch.int32, device=device)
+
+    @classmethod
+    def from_tensors(cls, nd, col, mv=None, tri=None):
+        g = cls.__new__(cls)
+        g.height, g.width = int(nd.shape[0]), int(nd.shape[1])
+        g.nd, g.col, g.mv, g.tri = nd, col, mv, tri
+        return g
+
+    def struct(self) -> hdof_gbuf:
+        code = {torch.float32: HDOF_F32, torch.float16: HDOF_F16, torch.bfloat16: HDOF_BF16}
+        return hdof_gbuf(self.width, self.height, code[self.nd.dtype], code[self.col.dtype], _ptr(self.nd),
+                         _ptr(self.col), _ptr(self.mv), _ptr(self.tri))
+
+
+class History:
+    """Temporal history planes (near, far, mom, hlen)."""
+
+    def __init__(self, width, height, device="cuda"):
+        self.near = torch.zeros((height, width, 4), dtype=torch.float32, device=device)
+        self.far = torch.zeros((height, width, 4), dtype=torch.float32, device=device)
+        self.mom = torch.zeros((height, width, 2), dtype=torch.float32, device=device)
+        self.hlen = torch.zeros((height, width), dtype=torch.uint8, device=device)
+
+    @classmethod
+    def from_tensors(cls, near, far, mom, hlen):
+        h = cls.__new__(cls)
+        h.near, h.far, h.mom, h.hlen = near, far, mom, hlen
+        return h
+
+    def struct(self) -> hdof_history:
+        return hdof_history(_ptr(self.near), _ptr(self.far), _ptr(self.mom), _ptr(self.hlen))
+
+    def reset(self):
+        self.hlen.zero_()
+
+
+class Bvh:
+    """Owning wrapper of an hdof_bvh handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def stats(self) -> hdof_bvh_stats:
+        s = hdof_bvh_stats()
+        _check(load().hdof_bvh_info(self.handle, C.byref(s)))
+        return s
+
+    def close(self):
+        if self.handle:
+            load().hdof_bvh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------- entry points --
+
+def hdof_version() -> str:
+    return load().hdof_version().decode()
+
+
+def hdof_sync(stream=None):
+    _check(load().hdof_sync(_stream(stream)))
+
+
+def hdof_workspace_bytes(width, height, p=None) -> int:
+    return int(load().hdof_workspace_bytes(int(width), int(height), C.byref(params(p))))
+
+
+def hdof_build_bvh(verts, idx, mat, uv=None, stream=None) -> Bvh:
+    h = C.c_void_p()
+    _check(load().hdof_build_bvh(_ptr(verts), int(verts.shape[0]), _ptr(idx), int(idx.shape[0]), _ptr(mat),
+                                 _ptr(uv), C.byref(h), _stream(stream)))
+    return Bvh(h)
+
+
+def hdof_closest_hits(bvh: Bvh, org, dirs, ids, ts, stream=None):
+    _check(load().hdof_closest_hits(bvh.handle, int(org.shape[0]), _ptr(org), _ptr(dirs), _ptr(ids), _ptr(ts),
+                                    _stream(stream)))
+
+
+def hdof_gbuffer(bvh: Bvh, cam, prev, p, gbuf: GBuffer, stream=None):
+    _check(load().hdof_gbuffer(bvh.handle, C.byref(camera(cam)), C.byref(camera(prev)), C.byref(params(p)),
+                               C.byref(gbuf.struct()), _stream(stream)))
+
+
+def hdof_mask(gbuf: GBuffer, prev_hist, p, edge, spp, workspace, stream=None):
+    hs = C.byref(prev_hist.struct()) if prev_hist is not None else None
+    _check(load().hdof_mask(C.byref(gbuf.struct()), hs, C.byref(params(p)), _ptr(edge), _ptr(spp),
+                            _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None):
+    _check(load().hdof_trace(bvh.handle, C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)),
+                             _ptr(spp), _ptr(rt), _ptr(stats), _ptr(workspace),
+                             workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def hdof_postfilter(gbuf: GBuffer, cam, lns, p, pp, workspace, stream=None):
+    _check(load().hdof_postfilter(C.byref(gbuf.struct()), C.byref(camera(cam)), C.byref(lens(lns)),
+                                  C.byref(params(p)), _ptr(pp), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def hdof_reconstruct(rt, gbuf: GBuffer, spp, cam, prev, lns, p, hist_in: History, hist_out: History, crt, hacc,
+                     crec, stream=None):
+    _check(load().hdof_reconstruct(_ptr(rt), C.byref(gbuf.struct()), _ptr(spp), C.byref(camera(cam)),
+                                   C.byref(camera(prev)), C.byref(lens(lns)), C.byref(params(p)),
+                                   C.byref(hist_in.struct()), C.byref(hist_out.struct()), _ptr(crt), _ptr(hacc),
+                                   _ptr(crec), _stream(stream)))
+
+
+def hdof_composite(gbuf: GBuffer, spp, pp, crt, crec, hacc, cam, lns, p, out, stream=None):
+    _check(load().hdof_composite(C.byref(gbuf.struct()), _ptr(spp), _ptr(pp), _ptr(crt), _ptr(crec), _ptr(hacc),
+                                 C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)), _ptr(out),
+                                 _stream(stream)))
+
+
+# ---------------------------------------------------------- frame driver --
+
+class Renderer:
+    """Owns the device buffers of a width x height frame and enqueues the
+    paper's per-frame sequence (G-buffer, mask, trace, post-filter,
+    reconstruction, composite) on one stream.  History is double-buffered
+    and swapped after each frame."""
+
+    def __init__(self, bvh: Bvh, width, height, p, device="cuda", nd_dtype=torch.float32,
+                 col_dtype=torch.float32):
+        self.bvh, self.W, self.H = bvh, int(width), int(height)
+        dev = torch.device(device)
+        self.g = GBuffer(width, height, dev, nd_dtype, col_dtype)
+        self.edge = torch.empty((height, width), dtype=torch.uint8, device=dev)
+        self.spp = torch.empty((height, width), dtype=torch.uint8, device=dev)
+        self.rt = torch.empty((height, width, 12), dtype=torch.float32, device=dev)
+        self.pp = torch.empty((height, width, 4), dtype=torch.float32, device=dev)
+        self.crt = torch.empty((height, width, 4), dtype=torch.float32, device=dev)
+        self.hacc = torch.empty((height, width), dtype=torch.float32, device=dev)
+        self.crec = torch.empty((height, width, 4), dtype=torch.float32, device=dev)
+        self.out = torch.empty((height, width, 4), dtype=torch.float32, device=dev)
+        self.stats = torch.zeros(2, dtype=torch.int32, device=dev)
+        self.hist = [History(width, height, dev), History(width, height, dev)]
+        self.cur = 0
+        nbytes = hdof_workspace_bytes(width, height, p)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+    @property
+    def history(self) -> History:
+        """History written by the last frame."""
+        return self.hist[self.cur]
+
+    def reset_history(self):
+        for h in self.hist:
+            h.reset()
+
+    def frame(self, cam, prev, lns, p, stream=None, with_history=True):
+        hin = self.hist[self.cur]
+        hout = self.hist[1 - self.cur]
+        hdof_gbuffer(self.bvh, cam, prev, p, self.g, stream)
+        hdof_mask(self.g, hin if with_history else None, p, self.edge, self.spp, self.ws, stream)
+        hdof_trace(self.bvh, cam, lns, p, self.spp, self.rt, self.stats, self.ws, stream)
+        hdof_postfilter(self.g, cam, lns, p, self.pp, self.ws, stream)
+        hdof_reconstruct(self.rt, self.g, self.spp, cam, prev, lns, p, hin, hout, self.crt, self.hacc,
+                         self.crec, stream)
+        hdof_composite(self.g, self.spp, self.pp, self.crt, self.crec, self.hacc, cam, lns, p, self.out, stream)
+        self.cur = 1 - self.cur
+        return self.out

@@ -1,0 +1,404 @@
+"""GPU parity: every C-ABI call against the FP64 oracle on the same seeded
+inputs, element by element.
+
+Tolerances: radiance |d| <= 1e-3 on >= 99.9% of pixels (the stated target);
+integer outputs (mask bits, spp, hit ids, history length) identical except at
+documented ties, where float32 and float64 may legitimately decide
+differently: a mask metric within 1e-4 (relative) of its threshold, a ray
+within 1e-5 (barycentric) of a triangle edge or two hits at equal t.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import hdof_inputs as hi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2210_04981_gb300.hdof as H  # noqa: E402
+from gpu_util import bvh_of, dev, frac_close, gbuf_from, history_from, host, report, workspace  # noqa: E402
+
+T30 = math.tan(math.radians(30.0))
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+# ------------------------------------------------------------------ BVH ----
+
+def _soup(rng, n):
+    c = rng.uniform(-1, 1, (n, 1, 3)) + np.array([0, 0, 4.0])
+    v = (c + rng.normal(scale=0.4, size=(n, 3, 3))).astype(np.float32)
+    return hi.Scene(v.reshape(-1, 3), np.arange(3 * n).reshape(n, 3).astype(np.int32),
+                    np.tile(np.array(hi.grey(0.5), np.float32), (n, 1)), np.zeros((n, 6), np.float32))
+
+
+def _bary_margin(tv, o, d):
+    """Smallest barycentric coordinate of the ray/plane intersection (float64)."""
+    v0, v1, v2 = tv[0:3], tv[3:6], tv[6:9]
+    e1, e2 = v1 - v0, v2 - v0
+    p = np.cross(d, e2)
+    det = e1 @ p
+    if abs(det) < 1e-300:
+        return 0.0
+    s = o - v0
+    u = (s @ p) / det
+    q = np.cross(s, e1)
+    v = (d @ q) / det
+    return min(1 - u - v, u, v)
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 17, 64, 3000])
+def test_closest_hits_match_brute_force(orc, n):
+    rng = np.random.default_rng(100 + n)
+    sc = _soup(rng, n)
+    bvh = bvh_of(sc)
+    st = bvh.stats()
+    assert st.n_tris == n and st.depth < 64
+    org = rng.uniform(-0.5, 0.5, (20000, 3)).astype(np.float32)
+    d = (rng.uniform(-1.2, 1.2, (20000, 3)) + np.array([0, 0, 4.0]) - org).astype(np.float32)
+    ids = torch.empty(20000, dtype=torch.int32, device="cuda")
+    ts = torch.empty(20000, dtype=torch.float32, device="cuda")
+    H.hdof_closest_hits(bvh, dev(org), dev(d), ids, ts)
+    H.hdof_sync()
+    g_id, g_t = host(ids), host(ts)
+    osc = orc.OScene(sc)
+    o_id, o_t = osc.closest_hits(org.astype(np.float64), d.astype(np.float64), use_bvh=(n > 64))
+    tv = sc.tri_verts().astype(np.float64)
+    bad = []
+    for k in np.nonzero(g_id != o_id)[0]:
+        o, dd = org[k].astype(np.float64), d[k].astype(np.float64)
+        margins = [abs(_bary_margin(tv[t], o, dd)) for t in (g_id[k], o_id[k]) if t >= 0]
+        tie_t = g_id[k] >= 0 and o_id[k] >= 0 and abs(g_t[k] - o_t[k]) <= 1e-5 * o_t[k]
+        if not (tie_t or (margins and min(margins) < 1e-5)):
+            bad.append(k)
+    assert not bad, f"{len(bad)} non-tie hit mismatches, e.g. ray {bad[0]}"
+    hit = (g_id >= 0) & (g_id == o_id)
+    assert np.allclose(g_t[hit], o_t[hit], rtol=1e-5)
+    assert (g_id != o_id).mean() < 1e-3
+
+
+def test_watertight_fan_gpu():
+    n = 12
+    cen = np.array([0.1, -0.05, 3.0])
+    ring = [cen + np.array([math.cos(2 * math.pi * k / n), math.sin(2 * math.pi * k / n), 0.3 * (k % 2)])
+            for k in range(n)]
+    v = []
+    for k in range(n):
+        v += [cen, ring[k], ring[(k + 1) % n]]
+    v = np.array(v, np.float32)
+    sc = hi.Scene(v, np.arange(3 * n).reshape(n, 3).astype(np.int32),
+                  np.tile(np.array(hi.grey(0.5), np.float32), (n, 1)), np.zeros((n, 6), np.float32))
+    bvh = bvh_of(sc)
+    vv = v.astype(np.float64)
+    tgt = [vv[0]] + [vv[0] + s * (vv[3 * k + 1] - vv[0]) for k in range(n) for s in np.linspace(0.05, 0.95, 19)]
+    tgt = np.array(tgt)
+    for o in (np.zeros(3), np.array([0.3, 0.2, -0.1])):
+        d = (tgt - o).astype(np.float32)
+        ids = torch.empty(len(d), dtype=torch.int32, device="cuda")
+        ts = torch.empty(len(d), dtype=torch.float32, device="cuda")
+        H.hdof_closest_hits(bvh, dev(np.tile(o, (len(d), 1)).astype(np.float32)), dev(d), ids, ts)
+        H.hdof_sync()
+        assert np.all(host(ids) >= 0)
+
+
+# -------------------------------------------------------------- G-buffer ----
+
+def _gbuffer(scene, cam, prev, p, nd_dtype=torch.float32, col_dtype=torch.float32):
+    bvh = bvh_of(scene)
+    g = H.GBuffer(cam.width, cam.height, nd_dtype=nd_dtype, col_dtype=col_dtype)
+    H.hdof_gbuffer(bvh, cam, prev, p, g)
+    H.hdof_sync()
+    return bvh, g
+
+
+def test_gbuffer_tiny(orc):
+    scene, cam, lens, p = hi.tiny_config()
+    _, g = _gbuffer(scene, cam, cam, p)
+    ref = orc.gbuffer(orc.OScene(scene), cam, cam, p)
+    tri, rtri = host(g.tri), ref["tri"]
+    # the background quad's diagonal (i + j = 127) is a shared edge: either triangle is correct
+    jj, ii = np.mgrid[0:128, 0:128]
+    diag = (ii + jj == 127)
+    assert np.array_equal(tri[~diag], rtri[~diag])
+    assert set(np.unique(tri[diag])) <= {0, 1}
+    assert np.allclose(host(g.nd), ref["nd"], atol=1e-5)
+    assert frac_close(host(g.col), ref["col"], 1e-5) == 1.0
+    assert np.abs(host(g.mv)).max() < 1e-3
+
+
+def test_gbuffer_room_moving_camera(orc):
+    scene = hi.room_scene(seed=0, aspect=16 / 9)
+    cam0 = hi.room_camera(0, 320, 180)
+    cam1 = hi.room_camera(1, 320, 180)
+    p = hi.room_params()
+    _, g = _gbuffer(scene, cam1, cam0, p)
+    ref = orc.gbuffer(orc.OScene(scene), cam1, cam0, p)
+    tri, rtri = host(g.tri), ref["tri"]
+    mism = tri != rtri
+    assert mism.mean() < 2e-3, f"{mism.sum()} hit-id mismatches"
+    # mismatched pixels must be ties: same depth (shared edge of one surface) or a silhouette graze
+    z, rz = host(g.nd)[..., 3], ref["nd"][..., 3]
+    same = ~mism
+    assert np.allclose(z[same], rz[same], rtol=1e-5)
+    assert frac_close(host(g.col)[same], ref["col"][same], 1e-4, axis=-1) >= 0.999
+    assert frac_close(host(g.mv)[same], ref["mv"][same], 1e-3, axis=-1) >= 0.999
+
+
+# ------------------------------------------------------------------ mask ----
+
+def _mask(g, hist, p):
+    W, Hh = g.width, g.height
+    edge = torch.empty((Hh, W), dtype=torch.uint8, device="cuda")
+    spp = torch.empty((Hh, W), dtype=torch.uint8, device="cuda")
+    H.hdof_mask(g, hist, p, edge, spp, workspace(W, Hh, p))
+    H.hdof_sync()
+    return host(edge), host(spp)
+
+
+def _tie_tiles(emetric, tau, tile, dilate, tol=1e-4):
+    """Pixels whose spp may legitimately differ: inside (dilated) tiles whose
+    edge OR involves a pixel at the threshold."""
+    Hh, W = emetric.shape
+    tie = np.abs(emetric - tau) < tol * max(1.0, tau)
+    nty, ntx = (Hh + tile - 1) // tile, (W + tile - 1) // tile
+    tt = np.zeros((nty, ntx), bool)
+    ys, xs = np.nonzero(tie)
+    tt[ys // tile, xs // tile] = True
+    dil = np.zeros_like(tt)
+    for dy in range(-dilate, dilate + 1):
+        for dx in range(-dilate, dilate + 1):
+            sh = np.zeros_like(tt)
+            sy = slice(max(0, dy), nty + min(0, dy))
+            sx = slice(max(0, dx), ntx + min(0, dx))
+            ty = slice(max(0, -dy), nty + min(0, -dy))
+            tx = slice(max(0, -dx), ntx + min(0, -dx))
+            sh[ty, tx] = tt[sy, sx]
+            dil |= sh
+    return tie, np.kron(dil, np.ones((tile, tile), bool))[:Hh, :W]
+
+
+@pytest.mark.parametrize("seed,W,Hh", [(0, 128, 128), (1, 257, 131), (2, 64, 40)])
+def test_mask_random_gbuffer(orc, seed, W, Hh):
+    gb = hi.random_gbuffer(W, Hh, seed=seed)
+    p = hi.Params(spp_max=8)
+    edge, spp = _mask(gbuf_from(gb["nd"], gb["col"], gb["mv"]), None, p)
+    ref = orc.mask(gb["nd"].astype(np.float64), gb["mv"].astype(np.float64), p)
+    tie, tie_px = _tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
+    assert np.array_equal(edge[~tie], ref["edge"][~tie])
+    assert np.array_equal(spp[~tie_px], ref["spp"][~tie_px])
+    assert edge.sum() > 0
+    if W * Hh > 64 * 64:
+        assert (spp == 0).sum() > 0
+
+
+def test_mask_variance_term(orc):
+    W, Hh = 200, 120
+    gb = hi.random_gbuffer(W, Hh, seed=5, n_regions=2)
+    hist = hi.random_history(W, Hh, seed=6)
+    p = hi.room_params(spp_max=8)
+    edge, spp = _mask(gbuf_from(gb["nd"], gb["col"], gb["mv"]), history_from(hist), p)
+    ref = orc.mask(gb["nd"].astype(np.float64), gb["mv"].astype(np.float64), p, hist["mom"].astype(np.float64),
+                   hist["hlen"])
+    tie, tie_px = _tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
+    # nearest-pixel reprojection ties: u within 1e-4 of a half-integer
+    jj, ii = np.mgrid[0:Hh, 0:W]
+    ux, uy = ii - gb["mv"][..., 0].astype(np.float64), jj - gb["mv"][..., 1].astype(np.float64)
+    near_half = (np.abs((ux + 0.5) - np.round(ux + 0.5)) < 1e-4) | (np.abs((uy + 0.5) - np.round(uy + 0.5)) < 1e-4)
+    ok = ~(tie_px | near_half)
+    assert np.array_equal(spp[ok], ref["spp"][ok])
+    assert len(np.unique(spp)) > 3  # variance term produced intermediate ray counts
+
+
+# ----------------------------------------------------------------- trace ----
+
+def _trace(bvh, cam, lens, p, spp_np):
+    W, Hh = cam.width, cam.height
+    spp = dev(spp_np.astype(np.uint8))
+    rt = torch.full((Hh, W, 12), float("nan"), dtype=torch.float32, device="cuda")
+    stats = torch.zeros(2, dtype=torch.int32, device="cuda")
+    H.hdof_trace(bvh, cam, lens, p, spp, rt, stats, workspace(W, Hh, p))
+    H.hdof_sync()
+    return host(rt), host(stats)
+
+
+def _rt_close(rt, ref, traced):
+    """Per traced pixel: colours 1e-3, hit ratio 1e-4, CoC 1e-3 rel, position 1e-4 rel."""
+    a, b = rt[traced], ref[traced]
+    col = np.r_[0:3, 4:7]
+    ok = np.all(np.abs(a[:, col] - b[:, col]) <= 1e-3, axis=1)
+    ok &= np.abs(a[:, 3] - b[:, 3]) <= 1e-4
+    ok &= np.all(np.abs(a[:, [7, 11]] - b[:, [7, 11]]) <= 1e-3 * np.maximum(1, np.abs(b[:, [7, 11]])), axis=1)
+    ok &= np.all(np.abs(a[:, 8:11] - b[:, 8:11]) <= 1e-4 * np.maximum(1, np.abs(b[:, 8:11])), axis=1)
+    return ok
+
+
+def test_trace_tiny(orc):
+    scene, cam, lens, p = hi.tiny_config()
+    osc = orc.OScene(scene)
+    g = orc.gbuffer(osc, cam, cam, p)
+    spp = orc.mask(g["nd"], g["mv"], p)["spp"]
+    bvh = bvh_of(scene)
+    rt, stats = _trace(bvh, cam, lens, p, spp)
+    ref = orc.trace(osc, cam, lens, p, spp)
+    traced = spp > 0
+    assert stats[0] == traced.sum() and stats[1] == spp.astype(np.int64).sum()
+    assert np.all(np.isnan(rt[~traced]))  # untraced pixels untouched
+    ok = _rt_close(rt, ref, traced)
+    assert ok.mean() >= 0.999, f"{(~ok).sum()} of {ok.size} traced pixels differ; " + report("rt", rt[traced], ref[traced])
+
+
+def test_trace_room(orc):
+    W, Hh = 320, 180
+    scene = hi.room_scene(seed=0, aspect=W / Hh)
+    cam = hi.room_camera(2, W, Hh)
+    lens = hi.room_lens()
+    p = hi.room_params(frame=2)
+    rng = np.random.default_rng(3)
+    spp = (rng.integers(0, 9, (Hh, W)) * (rng.uniform(size=(Hh, W)) < 0.6)).astype(np.uint8)
+    bvh = bvh_of(scene)
+    rt, stats = _trace(bvh, cam, lens, p, spp)
+    ref = orc.trace(orc.OScene(scene), cam, lens, p, spp)
+    traced = spp > 0
+    ok = _rt_close(rt, ref, traced)
+    assert ok.mean() >= 0.999, f"{(~ok).sum()} of {ok.size}; " + report("rt", rt[traced], ref[traced])
+
+
+def test_trace_empty_mask():
+    scene, cam, lens, p = hi.tiny_config()
+    bvh = bvh_of(scene)
+    rt, stats = _trace(bvh, cam, lens, p, np.zeros((128, 128), np.uint8))
+    assert stats[0] == 0 and stats[1] == 0 and np.all(np.isnan(rt))
+
+
+# ----------------------------------------------------------- post-filter ----
+
+@pytest.mark.parametrize("seed,W,Hh,rmax,A", [(0, 96, 80, 16.0, 0.05), (1, 203, 97, 32.0, 0.02),
+                                              (2, 64, 64, 0.0, 0.05), (3, 150, 70, 8.0, 0.0)])
+def test_postfilter(orc, seed, W, Hh, rmax, A):
+    gb = hi.random_gbuffer(W, Hh, seed=seed)
+    cam = hi.Camera(width=W, height=Hh).f32()
+    lens = hi.Lens(3.0, A, 0.05).f32()
+    p = hi.Params(r_max=rmax)
+    pp = torch.empty((Hh, W, 4), dtype=torch.float32, device="cuda")
+    H.hdof_postfilter(gbuf_from(gb["nd"], gb["col"]), cam, lens, p, pp, workspace(W, Hh, p))
+    H.hdof_sync()
+    ref = orc.postfilter(gb["nd"].astype(np.float64), gb["col"].astype(np.float64), lens, cam.tan_half_fovy, p)
+    got = host(pp)
+    assert frac_close(got, ref, 1e-4) == 1.0, report("pp", got, ref)
+
+
+# -------------------------------------------------------- reconstruction ----
+
+def _reconstruct_inputs(W, Hh, seed):
+    rng = np.random.default_rng(seed)
+    spp = (rng.integers(1, 9, (Hh, W)) * (rng.uniform(size=(Hh, W)) < 0.7)).astype(np.uint8)
+    cam0 = hi.Camera(pos=(0.0, 0.0, 0.0), width=W, height=Hh, jitter=hi.dyadic_jitter(seed, 0)).f32()
+    cam1 = hi.Camera(pos=(0.03, -0.01, 0.02), width=W, height=Hh, jitter=hi.dyadic_jitter(seed, 1)).f32()
+    rt = hi.random_rt(W, Hh, spp, seed=seed)
+    gb = hi.random_gbuffer(W, Hh, seed=seed)
+    hist = hi.random_history(W, Hh, seed=seed)
+    return spp, cam0, cam1, rt, gb, hist
+
+
+@pytest.mark.parametrize("seed,W,Hh,moved", [(0, 96, 64, 1), (1, 131, 77, 0)])
+def test_reconstruct(orc, seed, W, Hh, moved):
+    spp, cam0, cam1, rt, gb, hist = _reconstruct_inputs(W, Hh, seed)
+    lens = hi.Lens(3.0, 0.02, 0.05).f32()
+    p = hi.room_params(camera_moved=moved, r_s=8.0)
+    hin = history_from(hist)
+    hout = H.History(W, Hh)
+    crt = torch.empty((Hh, W, 4), dtype=torch.float32, device="cuda")
+    hacc = torch.empty((Hh, W), dtype=torch.float32, device="cuda")
+    crec = torch.empty((Hh, W, 4), dtype=torch.float32, device="cuda")
+    g = gbuf_from(gb["nd"], gb["col"], gb["mv"])
+    H.hdof_reconstruct(dev(rt), g, dev(spp), cam1, cam0, lens, p, hin, hout, crt, hacc, crec)
+    H.hdof_sync()
+    f64 = {k: (v.astype(np.float64) if v.dtype != np.uint8 else v) for k, v in hist.items()}
+    oh, ocrt, ohacc = orc.temporal(cam1, cam0, p, rt.astype(np.float64), spp, gb["nd"].astype(np.float64),
+                                   gb["mv"].astype(np.float64), f64)
+    ocrec = orc.spatial(p, ocrt, spp, oh["mom"], oh["hlen"])
+    tr = spp > 0
+    hl = host(hout.hlen)
+    assert np.array_equal(hl[~tr], np.zeros((~tr).sum(), np.uint8))
+    hl_ok = hl[tr] == oh["hlen"][tr]
+    assert hl_ok.mean() >= 0.999
+    sel = tr.copy()
+    sel[tr] = hl_ok
+    for name, a, b, tol in (("near", host(hout.near), oh["near"], 1e-4), ("far", host(hout.far), oh["far"], 1e-4),
+                            ("mom", host(hout.mom), oh["mom"], 1e-4), ("crt", host(crt), ocrt, 1e-4),
+                            ("crec", host(crec)[..., :3], ocrec[..., :3], 1e-4)):
+        assert frac_close(a[sel], b[sel], tol, 1e-4) >= 0.999, report(name, a[sel], b[sel])
+    assert frac_close(host(hacc)[sel], ohacc[sel], 1e-4, axis=None) >= 0.999
+    assert np.all(host(crt)[~tr][:, 3] == -1.0)
+
+
+# --------------------------------------------------------------- composite --
+
+def test_composite(orc):
+    W, Hh = 77, 53
+    rng = np.random.default_rng(4)
+    gb = hi.random_gbuffer(W, Hh, seed=4)
+    spp = (rng.integers(1, 9, (Hh, W)) * (rng.uniform(size=(Hh, W)) < 0.5)).astype(np.uint8)
+    pp = rng.uniform(0, 1, (Hh, W, 4)).astype(np.float32)
+    crt = rng.uniform(0, 1, (Hh, W, 4)).astype(np.float32)
+    crt[..., 3] = rng.uniform(0, 4, (Hh, W))
+    crec = rng.uniform(0, 1, (Hh, W, 4)).astype(np.float32)
+    hacc = rng.uniform(0, 1, (Hh, W)).astype(np.float32)
+    cam = hi.Camera(width=W, height=Hh).f32()
+    lens = hi.Lens(3.0, 0.03, 0.05).f32()
+    p = hi.Params()
+    out = torch.empty((Hh, W, 4), dtype=torch.float32, device="cuda")
+    H.hdof_composite(gbuf_from(gb["nd"], gb["col"]), dev(spp), dev(pp), dev(crt), dev(crec), dev(hacc), cam, lens, p,
+                     out)
+    H.hdof_sync()
+    ref = orc.composite(gb["nd"], gb["col"], spp, pp, crt, crec, hacc, lens, cam.tan_half_fovy, p, Hh)
+    assert frac_close(host(out)[..., :3], ref[..., :3], 1e-5) == 1.0, report("out", host(out), ref)
+
+
+# ------------------------------------------------------------ full frames --
+
+def _frame_check(r, ref, name):
+    out = host(r.out)[..., :3]
+    ok = frac_close(out, ref["out"][..., :3], 1e-3)
+    spp_eq = float((host(r.spp) == ref["mask"]["spp"]).mean())
+    assert spp_eq >= 0.999, f"{name}: spp agrees on {spp_eq:.5f}"
+    assert ok >= 0.999, f"{name}: {ok:.5f} within 1e-3; " + report("out", out, ref["out"][..., :3])
+
+
+def test_frame_tiny(orc):
+    scene, cam, lens, p = hi.tiny_config()
+    r = H.Renderer(bvh_of(scene), cam.width, cam.height, p)
+    r.frame(cam, cam, lens, p)
+    H.hdof_sync()
+    ref = orc.frame(orc.OScene(scene), cam, cam, lens, p)
+    assert np.array_equal(host(r.spp), ref["mask"]["spp"])
+    assert np.array_equal(host(r.edge), ref["mask"]["edge"])
+    _frame_check(r, ref, "tiny")
+
+
+def test_room_sequence_8_frames(orc):
+    """Procedural room at 480x270, 8 consecutive frames with camera motion,
+    jitter and temporal accumulation, against the oracle's own sequence."""
+    W, Hh = 480, 270
+    scene, cams, lens, p0 = hi.room_config(W, Hh, frames=8)
+    osc = orc.OScene(scene)
+    r = H.Renderer(bvh_of(scene), W, Hh, p0)
+    hist = None
+    for k in range(8):
+        p = p0.replace(frame=k, camera_moved=int(k > 0))
+        prev = cams[k - 1] if k else cams[0]
+        r.frame(cams[k], prev, lens, p)
+        H.hdof_sync()
+        ref = orc.frame(osc, cams[k], prev, lens, p, hist=hist)
+        hist = ref["hist"]
+        _frame_check(r, ref, f"frame {k}")
