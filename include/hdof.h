@@ -201,6 +201,26 @@ size_t hdof_workspace_bytes(int32_t width, int32_t height, const hdof_params* p)
 int hdof_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p,
               uint8_t* edge, uint8_t* spp, void* workspace, size_t workspace_bytes, void* stream);
 
+/* hdof_mask without caller scratch memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * for the library -- for instance a real-time render thread that must not
+ * call cudaMalloc/cudaFree (they can synchronise the device and stall the
+ * frame), or a host application that owns all device memory in its own
+ * arena and offers plug-ins no allocator.  It computes exactly what
+ * hdof_mask computes and allocates nothing: the per-tile flags live in a
+ * fixed device array of HDOF_MASK_NOALLOC_MAX_TILES bytes inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  Frames needing more tiles than that ((W/tile) x (H/tile) rounded
+ * up, e.g. 4096x4096 at tile 16) are rejected with HDOF_EINVAL.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing the stream into a graph.  All calls share the array:
+ * calls that overlap on the GPU (different streams without ordering) race
+ * and give wrong masks.  Each call clears the tiles it uses first. */
+#define HDOF_MASK_NOALLOC_MAX_TILES 65536
+int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p,
+                      uint8_t* edge, uint8_t* spp, void* stream);
+
 /* ---------------------------------------------------------- trace */
 /* Thin-lens distributed ray trace of the masked pixels (Ray Trace section).
  * Compacts the pixels with spp > 0 into a queue (tile order), then a

@@ -11,6 +11,7 @@
 //   an edge.
 // k_mask_spp: per pixel, dilated tile flag and the variance term -> spp.
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -195,5 +196,91 @@ extern "C" int hdof_mask(const hdof_gbuf* in, const hdof_history* prev_hist, con
                                   var ? prev_hist->hlen : nullptr, p->spp_max, p->var_tau, p->var_scale,
                                   p->hlen_young, spp);
     HDOF_LAUNCHED("hdof_mask: spp");
+    return HDOF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of hdof_mask.
+//
+// Some callers cannot hand this library any scratch memory: a real-time
+// render thread that must never call cudaMalloc/cudaFree (they can
+// synchronise the whole device and stall the frame), or a host application
+// that owns all device memory through its own arena and gives plug-ins no
+// allocator.  For them the mask's only scratch -- one flag byte per mask
+// tile -- lives in a fixed file-scope device array instead of the caller's
+// workspace.  The array is sized for HDOF_MASK_NOALLOC_MAX_TILES tiles and
+// stays resident on every device that loads the library until the process
+// exits.  Host code cannot use the array's name as a device address, so its
+// address is looked up once per device with cudaGetSymbolAddress.
+namespace hdof {
+namespace {
+
+static __device__ __align__(256) uint8_t g_mask_tiles_noalloc[HDOF_MASK_NOALLOC_MAX_TILES];
+
+std::mutex g_noalloc_mu;
+uint8_t* g_noalloc_ptr[64] = {nullptr};
+
+// device address of g_mask_tiles_noalloc on the current device (looked up once)
+int noalloc_tiles(uint8_t** out) {
+    int dev = 0;
+    HDOF_CUDA(cudaGetDevice(&dev), "hdof_mask_noalloc: device");
+    if (dev < 0 || dev >= 64) {
+        set_error("hdof_mask_noalloc: device index %d unsupported", dev);
+        return HDOF_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        HDOF_CUDA(cudaGetSymbolAddress(&p, g_mask_tiles_noalloc), "hdof_mask_noalloc: symbol address");
+        g_noalloc_ptr[dev] = static_cast<uint8_t*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return HDOF_OK;
+}
+
+}  // namespace
+}  // namespace hdof
+
+extern "C" int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p,
+                                 uint8_t* edge, uint8_t* spp, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_params(p, "hdof_mask_noalloc")) || (rc = check_gbuf(in, "hdof_mask_noalloc", false))) return rc;
+    HDOF_CHECK_ARG(edge && spp, "hdof_mask_noalloc: edge and spp outputs are required");
+    const int W = in->width, H = in->height;
+    bool var = p->variance_on && prev_hist;
+    HDOF_CHECK_ARG(!var || (prev_hist->mom && prev_hist->hlen && in->mv),
+                   "hdof_mask_noalloc: the variance term needs mv and the history mom/hlen planes");
+    const int T = p->tile, ntx = (W + T - 1) / T, nty = (H + T - 1) / T;
+    HDOF_CHECK_ARG((long long)ntx * nty <= HDOF_MASK_NOALLOC_MAX_TILES,
+                   "hdof_mask_noalloc: %d x %d mask tiles exceed the fixed capacity of %d tiles", ntx, nty,
+                   HDOF_MASK_NOALLOC_MAX_TILES);
+    uint8_t* tiles = nullptr;
+    if ((rc = noalloc_tiles(&tiles))) return rc;
+    cudaStream_t s = as_stream(stream);
+    // the array keeps the previous call's flags: clear the tiles this call uses
+    HDOF_CUDA(cudaMemsetAsync(tiles, 0, (size_t)ntx * nty, s), "hdof_mask_noalloc: clear tiles");
+    GaussW g;
+    double w[5], sum = 0.0;
+    for (int k = -2; k <= 2; ++k) {
+        w[k + 2] = std::exp(-(double)(k * k) / (2.0 * (double)p->gauss_sigma * (double)p->gauss_sigma));
+        sum += w[k + 2];
+    }
+    for (int k = 0; k < 5; ++k) g.w[k] = (float)(w[k] / sum);
+    dim3 grid((W + B - 1) / B, (H + B - 1) / B);
+    if (in->dtype_nd == HDOF_F32)
+        k_mask_edge<float4><<<grid, 256, 0, s>>>(static_cast<const float4*>(in->nd), W, H, g, p->edge_tau, T, ntx,
+                                                 edge, tiles);
+    else
+        k_mask_edge<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, g, p->edge_tau, T, ntx,
+                                                 edge, tiles);
+    HDOF_LAUNCHED("hdof_mask_noalloc: edge");
+    dim3 g2((W + 31) / 32, (H + 7) / 8);
+    k_mask_spp<<<g2, 256, 0, s>>>(W, H, T, ntx, nty, p->dilate, tiles, var ? 1 : 0,
+                                  reinterpret_cast<const float2*>(in->mv),
+                                  var ? reinterpret_cast<const float2*>(prev_hist->mom) : nullptr,
+                                  var ? prev_hist->hlen : nullptr, p->spp_max, p->var_tau, p->var_scale,
+                                  p->hlen_young, spp);
+    HDOF_LAUNCHED("hdof_mask_noalloc: spp");
     return HDOF_OK;
 }

@@ -92,6 +92,7 @@ def load():
         "hdof_gbuffer": ([vp, P(hdof_camera), P(hdof_camera), P(hdof_params), P(hdof_gbuf), vp], C.c_int),
         "hdof_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
         "hdof_mask": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp, sz, vp], C.c_int),
+        "hdof_mask_noalloc": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp], C.c_int),
         "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, sz, vp], C.c_int),
         "hdof_postfilter": ([P(hdof_gbuf), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, sz, vp],
                             C.c_int),
@@ -112,7 +113,7 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["hdof_version", "hdof_last_error", "hdof_sync", "hdof_default_params", "hdof_build_bvh",
             "hdof_bvh_destroy", "hdof_bvh_info", "hdof_closest_hits", "hdof_gbuffer", "hdof_workspace_bytes",
-            "hdof_mask", "hdof_trace", "hdof_postfilter", "hdof_reconstruct", "hdof_composite"]
+            "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_postfilter", "hdof_reconstruct", "hdof_composite"]
 
 
 def _check(rc):
@@ -287,6 +288,14 @@ def hdof_mask(gbuf: GBuffer, prev_hist, p, edge, spp, workspace, stream=None):
     hs = C.byref(prev_hist.struct()) if prev_hist is not None else None
     _check(load().hdof_mask(C.byref(gbuf.struct()), hs, C.byref(params(p)), _ptr(edge), _ptr(spp),
                             _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def hdof_mask_noalloc(gbuf: GBuffer, prev_hist, p, edge, spp, stream=None):
+    """hdof_mask for callers that cannot give the library device memory: the
+    tile flags live in a fixed array inside the library (see include/hdof.h)."""
+    hs = C.byref(prev_hist.struct()) if prev_hist is not None else None
+    _check(load().hdof_mask_noalloc(C.byref(gbuf.struct()), hs, C.byref(params(p)), _ptr(edge), _ptr(spp),
+                                    _stream(stream)))
 
 
 def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None):
