@@ -402,3 +402,34 @@ def test_room_sequence_8_frames(orc):
         ref = orc.frame(osc, cams[k], prev, lens, p, hist=hist)
         hist = ref["hist"]
         _frame_check(r, ref, f"frame {k}")
+
+
+def test_room_1080p_bench_config_sampled(orc):
+    """The benchmark's workload and launch configuration (1920x1080 room,
+    frames 0 and 1 with history and motion): mask, trace, reconstruction
+    and output against the oracle's own frames; the post-filter and the
+    composite on 20000 sampled pixels (the oracle's full-window gather)."""
+    W, Hh = 1920, 1080
+    scene, cams, lens, p0 = hi.room_config(W, Hh, frames=2)
+    osc = orc.OScene(scene)
+    r = H.Renderer(bvh_of(scene), W, Hh, p0)
+    hist = orc.empty_history(W, Hh)
+    pix = np.random.default_rng(11).choice(W * Hh, 20000, replace=False).astype(np.int32)
+    for k in range(2):
+        p = p0.replace(frame=k, camera_moved=int(k > 0))
+        prev = cams[k - 1] if k else cams[0]
+        r.frame(cams[k], prev, lens, p)
+        H.hdof_sync()
+        ref = orc.frame(osc, cams[k], prev, lens, p, hist=hist, pp_pix=pix)
+        hist = ref["hist"]
+        spp = host(r.spp)
+        assert (spp == ref["mask"]["spp"]).mean() >= 0.999
+        same = spp == ref["mask"]["spp"]
+        tr = (spp > 0) & same
+        ok = _rt_close(host(r.rt), ref["rt"], tr)
+        assert ok.mean() >= 0.999, f"frame {k}: rt {ok.mean():.5f}"
+        assert frac_close(host(r.crt)[tr], ref["crt"][tr], 1e-3, 1e-3) >= 0.999
+        pp = host(r.pp).reshape(-1, 4)[pix]
+        assert frac_close(pp, ref["pp"], 1e-4) >= 0.999, report("pp", pp, ref["pp"])
+        out = host(r.out).reshape(-1, 4)[pix][:, :3]
+        assert frac_close(out, ref["out"][:, :3], 1e-3) >= 0.999, report("out", out, ref["out"][:, :3])
