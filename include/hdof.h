@@ -95,7 +95,7 @@ typedef struct hdof_params {
     float r_s;           /* gather radius cap, pixels */
     float var_ref;       /* std-dev at which the spatial gather is fully used */
     /* post-filter (Design section) */
-    float r_max;         /* CoC radius cap, pixels, <= 127 */
+    float r_max;         /* CoC radius cap, pixels, <= 100 */
     float kz_rel;        /* relative depth band of the far-field depth test */
     /* composite (Composite section) */
     float h_tau;         /* hit ratio above which far pixels take the post-process */
@@ -134,9 +134,9 @@ typedef struct hdof_bvh hdof_bvh;
 
 typedef struct hdof_bvh_stats {
     int32_t n_tris;
-    int32_t n_nodes;  /* internal nodes */
-    int32_t depth;    /* maximum leaf depth */
-    int32_t reserved;
+    int32_t n_nodes;  /* 4-wide internal nodes */
+    int32_t depth;    /* levels of 4-wide nodes */
+    int32_t n_big;    /* scene-sized triangles tested outside the tree */
     int64_t device_bytes;
 } hdof_bvh_stats;
 
@@ -152,10 +152,12 @@ int hdof_sync(void* stream);
 void hdof_default_params(hdof_params* p);
 
 /* ------------------------------------------------------------ BVH -- */
-/* Builds a linear BVH (Karras 2012: 30-bit Morton codes of the triangle
- * centroids, radix sort, split search, bottom-up refit) over a triangle
- * soup, standing in for the paper's hardware ray-tracing acceleration
- * structure (Abstract).  verts: float [n_verts][3]; idx: int32 [n_tris][3];
+/* Builds the ray-tracing acceleration structure that stands in for the
+ * paper's hardware ray-tracing acceleration (Abstract): a binary BVH built on
+ * the GPU by parallel locally-ordered clustering (Meister and Bittner 2018):
+ * 63-bit Morton codes of the triangle centroids, radix sort, then rounds
+ * that merge mutual nearest neighbours (smallest union-box surface area
+ * within 16 positions) until one cluster remains.  One triangle per leaf.  verts: float [n_verts][3]; idx: int32 [n_tris][3];
  * mat: float [n_tris][8] = (albedo_a rgb, checker_n, albedo_b rgb, 0);
  * uv: float [n_tris][6] (may be NULL when no material uses a checker).
  * All device pointers; they are read during the call only.  Synchronous

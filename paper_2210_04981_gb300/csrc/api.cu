@@ -70,7 +70,7 @@ int check_params(const hdof_params* p, const char* who) {
     HDOF_CHECK_ARG(p->spp_max >= 1 && p->spp_max <= 255, "%s: spp_max must be 1..255", who);
     HDOF_CHECK_ARG(p->n_lights >= 0 && p->n_lights <= 4, "%s: n_lights must be 0..4", who);
     HDOF_CHECK_ARG(p->gauss_sigma > 0.f && std::isfinite(p->gauss_sigma), "%s: gauss_sigma must be > 0", who);
-    HDOF_CHECK_ARG(p->r_max >= 0.f && p->r_max <= 127.f, "%s: r_max must be 0..127", who);
+    HDOF_CHECK_ARG(p->r_max >= 0.f && p->r_max <= 100.f, "%s: r_max must be 0..100", who);
     HDOF_CHECK_ARG(p->r_s >= 0.f && p->r_s <= 64.f, "%s: r_s must be 0..64", who);
     HDOF_CHECK_ARG(p->ema_alpha > 0.f && p->ema_alpha <= 1.f, "%s: ema_alpha must be in (0, 1]", who);
     HDOF_CHECK_ARG(p->kz_rel > 0.f && p->h_tau > 0.f && p->var_ref > 0.f && p->var_scale > 0.f,
@@ -127,9 +127,24 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     return l;
 }
 
+#if HDOF_TRAV_STATS
+__device__ unsigned long long g_trav_stats[4];
+#endif
+
 }  // namespace hdof
 
 using namespace hdof;
+
+#if HDOF_TRAV_STATS
+// analysis builds only: read and clear (rays, node visits, triangle tests)
+extern "C" int hdof_debug_trav_stats(unsigned long long* out) {
+    unsigned long long z[4] = {0, 0, 0, 0};
+    cudaDeviceSynchronize();
+    cudaMemcpyFromSymbol(out, g_trav_stats, sizeof z);
+    cudaMemcpyToSymbol(g_trav_stats, z, sizeof z);
+    return 0;
+}
+#endif
 
 extern "C" {
 

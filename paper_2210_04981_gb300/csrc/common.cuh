@@ -15,7 +15,13 @@
 #define HDOF_HIST_MIN_W 1e-3f   // bilinear history weight below which history is invalid
 #define HDOF_PP_MIN_W 1e-8f     // post-filter layer weight below which a layer is empty
 #define HDOF_MV_OFFSCREEN 1e6f  // motion written when the previous camera cannot see a point
-#define HDOF_STACK 64           // traversal stack entries (>= maximum tree depth)
+#define HDOF_STACK 64           // traversal stack entries (> tree depth)
+#ifndef HDOF_LEAF_MAX
+#define HDOF_LEAF_MAX 1         // triangles per leaf (<= 8); single-triangle leaves measured fastest
+#endif
+#ifndef HDOF_BIG_MAX
+#define HDOF_BIG_MAX 0          // scene-sized triangles kept out of the tree (0: all in the tree)
+#endif
 #define HDOF_TILE_PF 16         // post-filter bounding tile edge
 #define HDOF_STATUS_TIMEOUT 1u
 
@@ -156,15 +162,17 @@ __device__ __forceinline__ float ldz(const float4* p) { return __ldg(&p->w); }
 __device__ __forceinline__ float ldz(const half4s* p) { return __high2float(__ldg(&p->b)); }
 
 // ------------------------------------------------------------------- BVH --
-// Binary BVH, child boxes stored in the parent (one 64-byte fetch tests both
-// children).  Child index >= 0: internal node; < 0: leaf holding sorted
-// triangle ~index.
+// Binary BVH node: the boxes of both children in one 64-byte record, so one
+// fetch tests both.  Child reference >= 0: internal node; < 0: a leaf of
+// 1..8 consecutive sorted triangles, ~(first << 3 | (count - 1)).
 struct __align__(16) Node {
     float4 xy0;  // c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y
     float4 xy1;  // c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y
     float4 z01;  // c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z
     int4 child;  // c0, c1, parent, unused
 };
+__host__ __device__ inline int leaf_ref(int first, int count) { return ~((first << 3) | (count - 1)); }
+
 // triangle in leaf order: (v0, original id), (v1, 0), (v2, 0)
 struct __align__(16) Tri {
     float4 v0, v1, v2;
@@ -176,7 +184,10 @@ struct BvhView {
     const float4* mat;  // sorted order: [2] per triangle (albedo_a rgb + checker_n, albedo_b)
     const float2* uv;   // sorted order: [3] per triangle
     int n_tris;
-    int root;           // root child-reference (internal 0, or ~0 for a single triangle)
+    int root;           // root reference (node 0, or a leaf)
+    int big_first;      // sorted slots [big_first, big_first + big_count) hold scene-sized
+    int big_count;      //   triangles tested by every ray after the traversal
+    const float4* big_box;  // [2] per scene-sized triangle: (lo xyz, 0), (hi xyz, 0)
 };
 
 struct Ray {
@@ -275,13 +286,40 @@ struct Hit {
     int id;    // original triangle id
 };
 
+__device__ __forceinline__ void hit_tri(const BvhView& bvh, int slot, float3 o, const Shear& sh, Hit& h) {
+    const Tri* tr = bvh.tris + slot;
+    float4 p0 = __ldg(&tr->v0), p1 = __ldg(&tr->v1), p2 = __ldg(&tr->v2);
+    float t, b0, b1, b2;
+    if (intersect_tri(o, sh, f3(p0.x, p0.y, p0.z), f3(p1.x, p1.y, p1.z), f3(p2.x, p2.y, p2.z), t, b0, b1, b2)) {
+        int id = __float_as_int(p0.w);
+        if (t < h.t || (t == h.t && id < h.id)) {
+            h.t = t;
+            h.b0 = b0;
+            h.b1 = b1;
+            h.b2 = b2;
+            h.slot = slot;
+            h.id = id;
+        }
+    }
+}
+
+#ifndef HDOF_TRAV_STATS
+#define HDOF_TRAV_STATS 0  // count node visits and triangle tests (analysis builds only)
+#endif
+#if HDOF_TRAV_STATS
+extern __device__ unsigned long long g_trav_stats[4];
+#endif
+
 // Closest hit: smallest t, equal t -> lower original id.  Stack traversal
-// (push far child, descend near child); cap bounds the steps (watchdog).
+// (descend the nearer hit child, push the farther); scene-sized triangles
+// (when kept out of the tree) are tested last behind a slab test of their
+// box.  cap bounds the node and leaf steps (watchdog).
 __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 d, int cap, unsigned* status) {
+    const float INF = __int_as_float(0x7f800000);
     Ray r = make_ray(o, d);
     Shear sh = make_shear(d);
     Hit h;
-    h.t = __int_as_float(0x7f800000);
+    h.t = INF;
     h.slot = -1;
     h.id = 0x7fffffff;
     h.b0 = h.b1 = h.b2 = 0.f;
@@ -289,14 +327,20 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
     int sp = 0;
     int cur = bvh.root;
     int steps = 0;
+#if HDOF_TRAV_STATS
+    unsigned nv = 0, nt = 0;
+#endif
     while (true) {
         if (cur >= 0) {
+#if HDOF_TRAV_STATS
+            ++nv;
+#endif
             const Node* n = bvh.nodes + cur;
             float4 a = __ldg(&n->xy0), b = __ldg(&n->xy1), z = __ldg(&n->z01);
             int4 ch = __ldg(&n->child);
             float t0 = slab(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t);
             float t1 = slab(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t);
-            bool h0 = t0 < __int_as_float(0x7f800000), h1 = t1 < __int_as_float(0x7f800000);
+            bool h0 = t0 < INF, h1 = t1 < INF;
             if (h0 && h1) {
                 int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
                 if (sp < HDOF_STACK) stack[sp++] = farc;
@@ -311,22 +355,11 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
                 cur = stack[--sp];
             }
         } else {
-            int slot = ~cur;
-            const Tri* tr = bvh.tris + slot;
-            float4 p0 = __ldg(&tr->v0), p1 = __ldg(&tr->v1), p2 = __ldg(&tr->v2);
-            float t, b0, b1, b2;
-            if (intersect_tri(o, sh, f3(p0.x, p0.y, p0.z), f3(p1.x, p1.y, p1.z), f3(p2.x, p2.y, p2.z), t, b0,
-                              b1, b2)) {
-                int id = __float_as_int(p0.w);
-                if (t < h.t || (t == h.t && id < h.id)) {
-                    h.t = t;
-                    h.b0 = b0;
-                    h.b1 = b1;
-                    h.b2 = b2;
-                    h.slot = slot;
-                    h.id = id;
-                }
-            }
+            int e = ~cur, first = e >> 3, count = (e & 7) + 1;
+            for (int k = 0; k < count; ++k) hit_tri(bvh, first + k, o, sh, h);
+#if HDOF_TRAV_STATS
+            nt += count;
+#endif
             if (sp == 0) break;
             cur = stack[--sp];
         }
@@ -335,6 +368,15 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
             break;
         }
     }
+    for (int k = 0; k < bvh.big_count; ++k) {
+        float4 lo = __ldg(&bvh.big_box[2 * k]), hi = __ldg(&bvh.big_box[2 * k + 1]);
+        if (slab(r, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, h.t) < INF) hit_tri(bvh, bvh.big_first + k, o, sh, h);
+    }
+#if HDOF_TRAV_STATS
+    atomicAdd(&g_trav_stats[0], 1ull);
+    atomicAdd(&g_trav_stats[1], (unsigned long long)nv);
+    atomicAdd(&g_trav_stats[2], (unsigned long long)nt);
+#endif
     if (h.slot < 0) h.id = -1;
     return h;
 }

@@ -74,13 +74,16 @@ int area_table_size();
 struct hdof_bvh {
     int device;
     int n_tris;
-    int n_nodes;
-    int depth;
+    int n_nodes;  // binary internal nodes
+    int n_big;    // scene-sized triangles kept out of the tree (sorted slots at the end)
+    int depth;    // deepest leaf of the binary tree
+    int root;
     size_t bytes;
     hdof::Node* nodes;
     hdof::Tri* tris;
     float4* mat;
     float2* uv;
+    float4* big_box;  // [2 * n_big]
     void* pool;  // single allocation holding all of the above
     hdof::BvhView view() const {
         hdof::BvhView v;
@@ -89,7 +92,10 @@ struct hdof_bvh {
         v.mat = mat;
         v.uv = uv;
         v.n_tris = n_tris;
-        v.root = 0;
+        v.root = root;
+        v.big_first = n_tris - n_big;
+        v.big_count = n_big;
+        v.big_box = big_box;
         return v;
     }
 };

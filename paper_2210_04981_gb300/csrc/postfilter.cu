@@ -10,10 +10,12 @@
 // |o| +- 1/2; a table of its breakpoints is built once per device and
 // evaluated by binary search, which is exact up to float rounding.
 //
-// k_pf_prep: per pixel (r, w_near/a, (1-w_near)/a, z) and per 16x16 tile the
-//   largest r.  k_pf_gather: per tile the gather window is bounded by the
-//   largest radius among tiles that can reach it; every tap outside that
-//   window has zero weight, so the bounded gather equals the full one.
+// k_pf_prep: per pixel (r + 1/2, w_near/a, (1-w_near)/a, z) and per 16x16
+//   tile the largest r.  k_pf_gather: per tile the gather window is bounded
+//   by the largest radius among tiles that can reach it; every tap outside
+//   that window has zero weight, so the bounded gather equals the full one.
+//   Each thread gathers two horizontally adjacent pixels so every tap it
+//   loads serves both.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(256) k_pf_prep(const ND* __restrict__ nd, int 
         r = fminf(fabsf(c) * 0.5f, rmax);
         float ia = 1.f / disk_area(r);
         float wn = w_near(c);
-        prep[q] = make_float4(r, wn * ia, (1.f - wn) * ia, z);
+        prep[q] = make_float4(r + 0.5f, wn * ia, (1.f - wn) * ia, z);
     }
     for (int o = 16; o; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
     __shared__ float red[8];
@@ -67,8 +69,55 @@ __global__ void __launch_bounds__(256) k_pf_prep(const ND* __restrict__ nd, int 
     }
 }
 
+// hardware approximate square root (MUFU, relative error ~2^-22): the tap
+// distance only enters the soft weight clamp(r + 1/2 - d, 0, 1)
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct PfAcc {
+    float3 Sn, Sf;
+    float Wn, Wf;
+    float ka, kb;
+};
+
+__device__ __forceinline__ void pf_tap(PfAcc& a, float d, const float4& e, const float4& c) {
+    float s = e.x - d;  // (r_q + 1/2) - d
+    if (s > 0.f) {
+        s = fminf(s, 1.f);
+        float an = s * e.y;
+        float af = s * e.z * clamp01(fmaf(-e.w, a.kb, a.ka));
+        a.Sn.x = fmaf(an, c.x, a.Sn.x);
+        a.Sn.y = fmaf(an, c.y, a.Sn.y);
+        a.Sn.z = fmaf(an, c.z, a.Sn.z);
+        a.Sf.x = fmaf(af, c.x, a.Sf.x);
+        a.Sf.y = fmaf(af, c.y, a.Sf.y);
+        a.Sf.z = fmaf(af, c.z, a.Sf.z);
+        a.Wn += an;
+        a.Wf += af;
+    }
+}
+
 template <class COL>
-__global__ void __launch_bounds__(256) k_pf_gather(const float4* __restrict__ prep, const COL* __restrict__ col,
+__device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size_t pq) {
+    float alpha = clamp01(a.Wn);
+    float3 N = a.Wn > HDOF_PP_MIN_W ? (1.f / a.Wn) * a.Sn : f3(0, 0, 0);
+    float3 F;
+    if (a.Wf > HDOF_PP_MIN_W) F = (1.f / a.Wf) * a.Sf;
+    else {
+        float4 c = ld4(col + pq);
+        F = f3(c.x, c.y, c.z);
+    }
+    float3 o = alpha * N + (1.f - alpha) * F;
+    return make_float4(o.x, o.y, o.z, alpha);
+}
+
+// 128 threads per 16x16 tile; thread t gathers pixels (2 (t & 7), t >> 3) and
+// its right neighbour, so a warp covers a 16x4 pixel block.
+template <class COL>
+__global__ void __launch_bounds__(128, 6) k_pf_gather(const float4* __restrict__ prep, const COL* __restrict__ col,
                                                    const float* __restrict__ tmax, int W, int H, int ntx, int nty,
                                                    int kt, float kz_rel, float4* __restrict__ pp) {
     __shared__ int s_win;
@@ -82,51 +131,42 @@ __global__ void __launch_bounds__(256) k_pf_gather(const float4* __restrict__ pr
         if (x < 0 || y < 0 || x >= ntx || y >= nty) continue;
         float r = __ldg(&tmax[y * ntx + x]);
         // pixel gap between the two tiles along each axis
-        float gx = (float)max(0, (abs(ox) - 1) * TP + 1), gy = (float)max(0, (abs(oy) - 1) * TP + 1);
-        if (ox == 0) gx = 0.f;
-        if (oy == 0) gy = 0.f;
+        float gx = ox == 0 ? 0.f : (float)((abs(ox) - 1) * TP + 1);
+        float gy = oy == 0 ? 0.f : (float)((abs(oy) - 1) * TP + 1);
         if (gx * gx + gy * gy < (r + 0.5f) * (r + 0.5f)) atomicMax(&s_win, (int)ceilf(r + 0.5f));
     }
     __syncthreads();
     const int G = s_win;
-    // warp w covers the 8x4 sub-block ((w & 1) * 8, (w >> 1) * 4) of the 16x16 tile
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int i = tx * TP + (w & 1) * 8 + (l & 7), j = ty * TP + (w >> 1) * 4 + (l >> 3);
+    const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + (threadIdx.x >> 3);
     if (i >= W || j >= H) return;
+    const bool two = i + 1 < W;
     const size_t pq = (size_t)j * W + i;
-    const float zp = __ldg(&prep[pq].w);
-    const float ka = 1.f + 1.f / kz_rel, kb = 1.f / (kz_rel * zp);  // k_z = clamp(ka - z_q kb)
-    float3 Sn = f3(0, 0, 0), Sf = f3(0, 0, 0);
-    float Wn = 0.f, Wf = 0.f;
-    const int y0 = max(j - G, 0), y1 = min(j + G, H - 1), x0 = max(i - G, 0), x1 = min(i + G, W - 1);
+    PfAcc a0, a1;
+    {
+        const float zp0 = __ldg(&prep[pq].w), zp1 = two ? __ldg(&prep[pq + 1].w) : zp0;
+        a0.ka = a1.ka = 1.f + 1.f / kz_rel;  // k_z = clamp(ka - z_q kb), kb = 1 / (kz_rel z_p)
+        a0.kb = 1.f / (kz_rel * zp0);
+        a1.kb = 1.f / (kz_rel * zp1);
+        a0.Sn = a0.Sf = a1.Sn = a1.Sf = f3(0, 0, 0);
+        a0.Wn = a0.Wf = a1.Wn = a1.Wf = 0.f;
+    }
+    const int y0 = max(j - G, 0), y1 = min(j + G, H - 1), x0 = max(i - G, 0), x1 = min(i + 1 + G, W - 1);
     for (int y = y0; y <= y1; ++y) {
-        const float dy = (float)(y - j);
+        const float dy2 = (float)((y - j) * (y - j));
+        const size_t qrow = (size_t)y * W;
         for (int x = x0; x <= x1; ++x) {
+            float4 e = __ldg(&prep[qrow + x]);
             const float dx = (float)(x - i);
-            const size_t q = (size_t)y * W + x;
-            float4 e = __ldg(&prep[q]);
-            float s = soft_step(e.x - sqrtf(fmaf(dx, dx, dy * dy)));
-            if (s > 0.f) {
-                float4 c = ld4(col + q);
-                float an = s * e.y;
-                float af = s * e.z * clamp01(fmaf(-e.w, kb, ka));
-                Sn = Sn + an * f3(c.x, c.y, c.z);
-                Sf = Sf + af * f3(c.x, c.y, c.z);
-                Wn += an;
-                Wf += af;
+            float d0 = sqrt_approx(fmaf(dx, dx, dy2)), d1 = sqrt_approx(fmaf(dx - 1.f, dx - 1.f, dy2));
+            if (e.x > fminf(d0, d1)) {
+                float4 c = ld4(col + qrow + x);
+                pf_tap(a0, d0, e, c);
+                pf_tap(a1, d1, e, c);
             }
         }
     }
-    float alpha = clamp01(Wn);
-    float3 N = Wn > HDOF_PP_MIN_W ? (1.f / Wn) * Sn : f3(0, 0, 0);
-    float3 F;
-    if (Wf > HDOF_PP_MIN_W) F = (1.f / Wf) * Sf;
-    else {
-        float4 c = ld4(col + pq);
-        F = f3(c.x, c.y, c.z);
-    }
-    float3 o = alpha * N + (1.f - alpha) * F;
-    pp[pq] = make_float4(o.x, o.y, o.z, alpha);
+    pp[pq] = pf_finish(a0, col, pq);
+    if (two) pp[pq + 1] = pf_finish(a1, col, pq + 1);
 }
 
 std::mutex g_area_mu;
@@ -235,12 +275,16 @@ extern "C" int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, cons
         k_pf_prep<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
     HDOF_LAUNCHED("hdof_postfilter: prep");
     int kt = (int)std::ceil((p->r_max + 0.5f) / TP) + 1;
-    if (in->dtype_col == HDOF_F32)
-        k_pf_gather<float4><<<grid, 256, 0, s>>>(prep, static_cast<const float4*>(in->col), tmax, W, H, ntx, nty, kt,
+    // the taps are served from L1: prefer the largest L1 carve-out
+    if (in->dtype_col == HDOF_F32) {
+        cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        k_pf_gather<float4><<<grid, 128, 0, s>>>(prep, static_cast<const float4*>(in->col), tmax, W, H, ntx, nty, kt,
                                                  p->kz_rel, reinterpret_cast<float4*>(pp));
-    else
-        k_pf_gather<bf164s><<<grid, 256, 0, s>>>(prep, static_cast<const bf164s*>(in->col), tmax, W, H, ntx, nty, kt,
+    } else {
+        cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        k_pf_gather<bf164s><<<grid, 128, 0, s>>>(prep, static_cast<const bf164s*>(in->col), tmax, W, H, ntx, nty, kt,
                                                  p->kz_rel, reinterpret_cast<float4*>(pp));
+    }
     HDOF_LAUNCHED("hdof_postfilter: gather");
     return HDOF_OK;
 }

@@ -163,7 +163,10 @@ __device__ __forceinline__ void trace_pixel(const TraceArgs& a, unsigned q) {
     o[2] = make_float4(SfP.x * inf_, SfP.y * inf_, SfP.z * inf_, fok ? Sfc * inf_ : -1.f);
 }
 
-__global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
+#ifndef HDOF_TRACE_MINB
+#define HDOF_TRACE_MINB 1
+#endif
+__global__ void __launch_bounds__(128, HDOF_TRACE_MINB) k_trace(TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const unsigned n = __ldcg(&a.totals[0]);
     while (true) {

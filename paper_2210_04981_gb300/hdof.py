@@ -64,7 +64,7 @@ class hdof_history(C.Structure):
 
 class hdof_bvh_stats(C.Structure):
     _fields_ = [("n_tris", C.c_int32), ("n_nodes", C.c_int32), ("depth", C.c_int32),
-                ("reserved", C.c_int32), ("device_bytes", C.c_int64)]
+                ("n_big", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 _lib = None
