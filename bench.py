@@ -34,7 +34,6 @@ import numpy as np  # noqa: E402
 import hdof_inputs as hi  # noqa: E402
 
 METRIC = "Hybrid DoF ms/frame @1080p & masked thin-lens Mrays/s vs plain form, 1 GB300"
-WORKLOAD = "procedural room 1920x1080, 164620 tris, 1-8 spp masked thin-lens, consecutive frames"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 # FP32 lanes x 2 flops per FMA x SMs (GB300: 152 SMs x 128 FP32 lanes)
@@ -119,17 +118,27 @@ def dist_env():
 
 # ----------------------------------------------------------- our kernels ---
 
-def algorithmic_bytes(W, Hh, n_traced, variance_px):
-    """HBM bytes each call must move at minimum (FP32 planes), per frame."""
+def algorithmic_bytes(W, Hh, n_traced, variance_px, nd_b=16, col_b=16):
+    """HBM bytes each call must move at minimum, per frame (nd_b, col_b: bytes
+    per pixel of the normal/depth and colour planes: 16 in FP32, 8 in FP16/BF16)."""
     px = W * Hh
     return {
-        "gbuffer": 44 * px,                                   # write nd, col, mv, tri
-        "mask": (16 + 1 + 1) * px + (8 + 8 + 1) * variance_px,  # nd -> edge, spp; mv + history where needed
-        "trace": 2 * px + (4 + 4 + 1 + 48) * n_traced,          # spp twice; queue w/r; spp; rt
-        "postfilter": (16 + 16 + 16 + 16 + 16) * px,            # nd -> prep; prep + col -> pp
-        "reconstruct": (1 + 1 + 16) * px + (48 + 8 + 16 + 41 + 41 + 16 + 4 + 16 + 9 + 16) * n_traced,
-        "composite": (16 + 16 + 1 + 16 + 16) * px + (16 + 16 + 4) * n_traced,
+        "gbuffer": (nd_b + col_b + 12) * px,                        # write nd, col, mv, tri
+        "mask": (nd_b + 1 + 1) * px + (8 + 8 + 1) * variance_px,     # nd -> edge, spp; mv + history where needed
+        "trace": 2 * px + (4 + 4 + 1 + 48) * n_traced,               # spp twice; queue w/r; spp; rt
+        "postfilter": (nd_b + 16 + 16 + col_b + 16) * px,            # nd -> prep; prep + col -> pp
+        "reconstruct": (1 + 1 + 16) * px + (48 + 8 + nd_b + 41 + 41 + 16 + 4 + 16 + 9 + 16) * n_traced,
+        "composite": (nd_b + col_b + 1 + 16 + 16) * px + (16 + 16 + 4) * n_traced,
     }
+
+
+SCENES = {
+    # name: (width, height, scene builder, params overrides, workload text)
+    "room": (1920, 1080, lambda a: hi.room_scene(seed=0, aspect=a), {},
+             "procedural room 1920x1080, 164620 tris, 1-8 spp masked thin-lens, consecutive frames"),
+    "room4k": (3840, 2160, lambda a: hi.room4k_scene(seed=0, aspect=a), {"r_max": 64.0},
+               "procedural room 3840x2160, 5249036 tris, 1-8 spp masked thin-lens, consecutive frames"),
+}
 
 
 def contributing_taps(z, lens, Hh, t, r_max):
@@ -155,11 +164,15 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    W, Hh = args.width, args.height
-    scene = hi.room_scene(seed=0, aspect=W / Hh)
+    W, Hh, make_scene, over, workload = SCENES[args.scene]
+    if args.width:
+        W, Hh = args.width, args.height
+    scene = make_scene(W / Hh)
     lens = hi.room_lens()
-    p0 = hi.room_params()
+    p0 = hi.room_params(**over)
     cams = [hi.room_camera(k, W, Hh) for k in range(args.warmup + args.steps + 1)]
+    mixed = args.precision == "mixed"
+    nd_dt, col_dt = (torch.float16, torch.bfloat16) if mixed else (torch.float32, torch.float32)
     t0 = time.perf_counter()
     verts, idx = torch.from_numpy(scene.verts).to(dev), torch.from_numpy(scene.idx).to(dev)
     mat, uv = torch.from_numpy(scene.mat).to(dev), torch.from_numpy(scene.uv).to(dev)
@@ -170,7 +183,7 @@ def run_ours(args):
     bvh_ms = (time.perf_counter() - t1) * 1e3
     upload_ms = (t1 - t0) * 1e3
     st = bvh.stats()
-    r = H.Renderer(bvh, W, Hh, p0, device=dev)
+    r = H.Renderer(bvh, W, Hh, p0, device=dev, nd_dtype=nd_dt, col_dtype=col_dt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -240,7 +253,8 @@ def run_ours(args):
     trace_ms = float(mean_stage[stages.index("trace")])
     mrays = float(rays.mean()) / (trace_ms * 1e-3) / 1e6
     hbm, sm_med, peak_src = peaks()
-    ab = algorithmic_bytes(W, Hh, float(traced.mean()), float(var_px.mean()))
+    ab = algorithmic_bytes(W, Hh, float(traced.mean()), float(var_px.mean()), 8 if mixed else 16,
+                           8 if mixed else 16)
     per_stage = {}
     for i, n in enumerate(stages):
         gbs = ab[n] / (mean_stage[i] * 1e-3) / 1e9
@@ -299,7 +313,8 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 4), "unit": "ms/frame", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(total_ms / K, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "width": W, "height": Hh, "triangles": int(st.n_tris),
+        "config": {"workload": workload, "width": W, "height": Hh, "triangles": int(st.n_tris),
+                   "storage": "f16 normal/depth, bf16 colour, f32 elsewhere" if mixed else "f32",
                    "bvh_depth": int(st.depth), "spp_max": p0.spp_max, "r_max": p0.r_max,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single", "l2": "flushed between steps (256 MiB write)"},
         "mrays_per_s": round(mrays, 1), "rays_per_frame": int(rays.mean()),
@@ -353,8 +368,10 @@ def oracle_frame_sample(O, osc, cams, lens, p0, k, hist, W, Hh, pf_stride):
 def cpu_baseline(args, budget_s=30.0):
     from oracle import oracle as O
     O.build()
-    W, Hh = args.width, args.height
-    scene = hi.room_scene(seed=0, aspect=W / Hh)
+    W, Hh, make_scene, over, _ = SCENES["room"]
+    if args.width:
+        W, Hh = args.width, args.height
+    scene = make_scene(W / Hh)
     lens = hi.room_lens()
     p0 = hi.room_params()
     cams = [hi.room_camera(k, W, Hh) for k in range(2)]
@@ -374,8 +391,10 @@ def run_reference(args):
         return
     from oracle import oracle as O
     O.build()
-    W, Hh = args.width, args.height
-    scene = hi.room_scene(seed=0, aspect=W / Hh)
+    W, Hh, make_scene, over, workload = SCENES["room"]
+    if args.width:
+        W, Hh = args.width, args.height
+    scene = make_scene(W / Hh)
     lens = hi.room_lens()
     p0 = hi.room_params()
     n = args.warmup + args.steps
@@ -394,7 +413,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms/frame", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "width": W, "height": Hh, "triangles": scene.n_tris},
+           "config": {"workload": workload, "width": W, "height": Hh, "triangles": scene.n_tris},
            "cpu_baseline": {"value": round(value, 1), "unit": "ms/frame", "cores": O.num_threads(),
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": round(value, 1), "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -407,8 +426,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--width", type=int, default=1920)
-    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--scene", choices=sorted(SCENES), default="room")
+    ap.add_argument("--precision", choices=["f32", "mixed"], default="f32")
+    ap.add_argument("--width", type=int, default=0, help="override the scene's resolution")
+    ap.add_argument("--height", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)

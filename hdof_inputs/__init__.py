@@ -137,26 +137,28 @@ class Scene:
 
 
 class _Builder:
+    """Accumulates triangle-soup chunks as numpy arrays."""
+
     def __init__(self):
         self.v, self.i, self.m, self.uv = [], [], [], []
         self.nv = 0
 
+    def _add(self, verts, tris, mats, uvs):
+        verts = np.asarray(verts, np.float64).reshape(-1, 3)
+        tris = np.asarray(tris, np.int64).reshape(-1, 3) + self.nv
+        self.v.append(verts)
+        self.i.append(tris)
+        self.m.append(np.broadcast_to(np.asarray(mats, np.float64), (len(tris), 8)))
+        self.uv.append(np.broadcast_to(np.asarray(uvs, np.float64).reshape(-1, 6), (len(tris), 6)))
+        self.nv += len(verts)
+
     def quad(self, p0, p1, p2, p3, mat, uvs=((0, 0), (1, 0), (1, 1), (0, 1))):
         """Two triangles (p0,p1,p2), (p0,p2,p3)."""
-        base = self.nv
-        self.v += [p0, p1, p2, p3]
-        self.nv += 4
-        self.i += [(base, base + 1, base + 2), (base, base + 2, base + 3)]
-        self.m += [mat, mat]
-        self.uv += [(*uvs[0], *uvs[1], *uvs[2]), (*uvs[0], *uvs[2], *uvs[3])]
+        self._add([p0, p1, p2, p3], [(0, 1, 2), (0, 2, 3)], mat,
+                  [(*uvs[0], *uvs[1], *uvs[2]), (*uvs[0], *uvs[2], *uvs[3])])
 
     def mesh(self, verts, tris, mat):
-        base = self.nv
-        self.v += [tuple(p) for p in verts]
-        self.nv += len(verts)
-        self.i += [tuple(int(x) + base for x in t) for t in tris]
-        self.m += [mat] * len(tris)
-        self.uv += [(0, 0, 1, 0, 0, 1)] * len(tris)
+        self._add(verts, tris, mat, (0, 0, 1, 0, 0, 1))
 
     def box(self, lo, hi, mat):
         x0, y0, z0 = lo
@@ -168,10 +170,8 @@ class _Builder:
             self.quad(c[a], c[b], c[cc], c[d], mat)
 
     def scene(self) -> Scene:
-        return Scene(np.asarray(self.v, F32).reshape(-1, 3),
-                     np.asarray(self.i, np.int32).reshape(-1, 3),
-                     np.asarray(self.m, F32).reshape(-1, 8),
-                     np.asarray(self.uv, F32).reshape(-1, 6))
+        c = lambda parts, dt: np.ascontiguousarray(np.concatenate(parts), dtype=dt)  # noqa: E731
+        return Scene(c(self.v, F32), c(self.i, np.int32), c(self.m, F32), c(self.uv, F32))
 
 
 def grey(a: float):
@@ -268,6 +268,12 @@ def room_scene(seed: int = 0, n_boxes: int = 64, n_spheres: int = 32, subdiv: in
             tris = np.arange(verts.shape[0]).reshape(-1, 3)
             b.mesh(verts, tris, alb)
     return b.scene()
+
+
+def room4k_scene(seed: int = 0, aspect: float = 16.0 / 9.0) -> Scene:
+    """Mixed-precision 4K workload: 512 boxes and 256 subdivision-5 icospheres
+    (5,249,036 triangles)."""
+    return room_scene(seed=seed, n_boxes=512, n_spheres=256, subdiv=5, aspect=aspect)
 
 
 def room_scene_target(seed: int, target_tris: int, **kw) -> Scene:
@@ -420,3 +426,61 @@ def random_rt(width: int, height: int, spp, seed: int = 0, zf: float = 3.0):
     rt = np.concatenate([Cn, h[..., None], Cf, cn[..., None], P, cf[..., None]], -1)
     rt[np.asarray(spp) == 0] = 0.0
     return rt.astype(F32)
+
+
+# --------------------------------------------------------------------------
+# differentiable post-path workload
+# --------------------------------------------------------------------------
+
+
+def random_hist_samples(width: int, height: int, seed: int = 0, frac_valid: float = 0.7):
+    """History already sampled at reprojected positions, per pixel
+    [H,W,12] = (near rgb*B, B_near, far rgb*B, B_far, mu1, mu2, flags, hlen)
+    with flags = valid_near + 2 valid_far."""
+    rng = np.random.default_rng(seed + 31337)
+    H, W = height, width
+    Bn = rng.uniform(0.0, 1.0, (H, W))
+    hs = np.zeros((H, W, 12))
+    hs[..., 0:3] = rng.uniform(0, 1, (H, W, 3)) * Bn[..., None]
+    hs[..., 3] = Bn
+    hs[..., 4:7] = rng.uniform(0, 1, (H, W, 3)) * (1 - Bn)[..., None]
+    hs[..., 7] = 1 - Bn
+    mu1 = rng.uniform(0.05, 0.9, (H, W))
+    hs[..., 8] = mu1
+    hs[..., 9] = mu1 * mu1 + rng.uniform(0.0, 0.1, (H, W)) ** 2
+    vn = rng.uniform(size=(H, W)) < frac_valid
+    vf = rng.uniform(size=(H, W)) < frac_valid
+    hs[..., 10] = vn + 2 * vf
+    hs[..., 11] = rng.integers(1, 12, (H, W))
+    return hs.astype(F32)
+
+
+def box_filter(a: np.ndarray, k: int) -> np.ndarray:
+    """k x k mean filter with edge replication (input smoothing only)."""
+    r = k // 2
+    p = np.pad(a, r, mode="edge")
+    c = np.cumsum(np.cumsum(p, 0), 1)
+    c = np.pad(c, ((1, 0), (1, 0)))
+    H, W = a.shape
+    return (c[k:k + H, k:k + W] - c[0:H, k:k + W] - c[k:k + H, 0:W] + c[0:H, 0:W]) / (k * k)
+
+
+def diff_inputs(width: int = 1024, height: int = 1024, seed: int = 0):
+    """Colour U[0,1]^3 and depth U[0.3,8] smoothed by a 9x9 box (seeded)."""
+    rng = np.random.default_rng(seed)
+    col = rng.uniform(0.0, 1.0, (height, width, 3)).astype(F32)
+    z = box_filter(rng.uniform(0.3, 8.0, (height, width)), 9).astype(F32)
+    return col, z
+
+
+def diff_config(width: int = 1024, height: int = 1024, seed: int = 0):
+    """Differentiable post-path workload: colour/depth of diff_inputs, and a
+    100k-triangle room (seed 0) whose trace at the target lens (focus 2.5,
+    aperture 0.04) provides the frozen visibility."""
+    col, z = diff_inputs(width, height, seed)
+    scene = room_scene_target(seed, 100_000, aspect=width / height)
+    cam = Camera(width=width, height=height).f32()
+    target = Lens(2.5, 0.04, 0.05).f32()
+    start = Lens(1.0, 0.02, 0.05).f32()
+    params = room_params(r_max=32.0, variance_on=1)
+    return col, z, scene, cam, target, start, params

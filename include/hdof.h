@@ -134,8 +134,8 @@ typedef struct hdof_bvh hdof_bvh;
 
 typedef struct hdof_bvh_stats {
     int32_t n_tris;
-    int32_t n_nodes;  /* 4-wide internal nodes */
-    int32_t depth;    /* levels of 4-wide nodes */
+    int32_t n_nodes;  /* internal nodes */
+    int32_t depth;    /* deepest leaf (bounds the traversal stack) */
     int32_t n_big;    /* scene-sized triangles tested outside the tree */
     int64_t device_bytes;
 } hdof_bvh_stats;
@@ -157,7 +157,8 @@ void hdof_default_params(hdof_params* p);
  * the GPU by parallel locally-ordered clustering (Meister and Bittner 2018):
  * 63-bit Morton codes of the triangle centroids, radix sort, then rounds
  * that merge mutual nearest neighbours (smallest union-box surface area
- * within 16 positions) until one cluster remains.  One triangle per leaf.  verts: float [n_verts][3]; idx: int32 [n_tris][3];
+ * within 16 positions) until one cluster remains.  One triangle per leaf.
+ * verts: float [n_verts][3]; idx: int32 [n_tris][3];
  * mat: float [n_tris][8] = (albedo_a rgb, checker_n, albedo_b rgb, 0);
  * uv: float [n_tris][6] (may be NULL when no material uses a checker).
  * All device pointers; they are read during the call only.  Synchronous
@@ -234,10 +235,15 @@ int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const 
  * rt: float [H][W][12] = (C_near rgb, h | C_far rgb, c_near | P_far xyz,
  * c_far); h = sum w / n is the hit ratio; an empty layer (weight < 1e-6)
  * has colour 0 and CoC -1.  Untraced pixels are not written.
- * stats (device, may be NULL): uint32 [2] = (traced pixels, rays). */
+ * stats (device, may be NULL): uint32 [2] = (traced pixels, rays).
+ * rec, ray_off (device, both NULL or both set): per-ray hit records
+ * rec[ray_off[p] + s] = (L rgb, view depth of the hit, +inf for a miss) of
+ * sample s of traced pixel p -- the frozen visibility that
+ * hdof_post_forward/backward re-evaluate at another focus and aperture;
+ * rec holds stats[1] float4 entries (at most spp_max x W x H). */
 int hdof_trace(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* lens,
                const hdof_params* p, const uint8_t* spp, float* rt, uint32_t* stats,
-               void* workspace, size_t workspace_bytes, void* stream);
+               float* rec, uint32_t* ray_off, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ----------------------------------------------------- post-filter -- */
 /* CoC gather post-filter of the sharp image (Design section; the rejection
@@ -281,6 +287,58 @@ int hdof_reconstruct(const float* rt, const hdof_gbuf* in, const uint8_t* spp,
 int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt,
                    const float* crec, const float* hacc, const hdof_camera* cam,
                    const hdof_lens* lens, const hdof_params* p, float* out, void* stream);
+
+/* ------------------------------------------- differentiable post-path -- */
+/* Buffers the forward writes and the backward reads (device, FP32 unless
+ * noted; [H][W] planes): rt [12] trace output replayed at this lens; crt [4],
+ * hacc, mom [2], hlen (uint8) of the temporal step; crec [4] and sp_aux [4]
+ * (gathered colour, weight sum) of the spatial gather; pp [4] and pp_aux
+ * [8] (near colour, near weight, far colour, far weight) of the post-filter;
+ * out [4] the composite. */
+typedef struct hdof_post_state {
+    float* rt;
+    float* crt;
+    float* hacc;
+    float* mom;
+    uint8_t* hlen;
+    float* crec;
+    float* sp_aux;
+    float* pp;
+    float* pp_aux;
+    float* out;
+} hdof_post_state;
+
+/* Scratch bytes of hdof_post_forward / hdof_post_backward. */
+size_t hdof_post_workspace_bytes(int32_t width, int32_t height, const hdof_params* p);
+
+/* The frame's reconstruction, post-filter and composite as a function of the
+ * sharp colour image (in->col, FP32) and of the lens, with the ray-traced
+ * visibility held fixed (the paper has no gradient; this exposes one).
+ * Frozen inputs: in->nd (view depth in .w), spp, the hit records rec /
+ * ray_off of an hdof_trace call with the same spp, and hist_samples
+ * ([H][W][12]: near (rgb x B, B), far (rgb x B, B), mu1, mu2,
+ * valid_near + 2 valid_far, hlen -- the history already sampled at its
+ * reprojected positions; NULL = no history).  The trace accumulation is
+ * re-evaluated from the records at `lens` (each hit's CoC and split weight
+ * change, not the hits), then the temporal step over the frozen samples, the
+ * spatial gather, the post-filter and the composite run with the frame's
+ * definitions.  Writes every buffer of *st. */
+int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                      const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
+                      const hdof_params* p, const hdof_post_state* st, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Adjoint of hdof_post_forward (same inputs, its state): from grad_out
+ * ([H][W][4], rgb used) writes grad_col ([H][W][4], d/d colour) and
+ * grad_lens (device float [2] = d/d focus_dist, d/d aperture_radius).  Gather
+ * weights are recomputed, not stored; the lens gradient is reduced per block
+ * in double precision and summed in a fixed order (deterministic).  Needs
+ * aperture_radius > 0. */
+int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                       const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
+                       const hdof_params* p, const hdof_post_state* st, const float* grad_out,
+                       float* grad_col, float* grad_lens, void* workspace, size_t workspace_bytes,
+                       void* stream);
 
 #ifdef __cplusplus
 }

@@ -196,15 +196,31 @@ static double g_sort_axis_key(const oscene* s, int32_t tri, int axis) {
     const double* v = s->v + 9 * (size_t)tri;
     return v[axis] + v[3 + axis] + v[6 + axis];
 }
-static const oscene* g_sort_scene;
-static int g_sort_axis;
-static int cmp_tri(const void* a, const void* b) {
-    int32_t ia = *(const int32_t*)a, ib = *(const int32_t*)b;
-    double ka = g_sort_axis_key(g_sort_scene, ia, g_sort_axis);
-    double kb = g_sort_axis_key(g_sort_scene, ib, g_sort_axis);
-    if (ka < kb) return -1;
-    if (ka > kb) return 1;
-    return (ia > ib) - (ia < ib);
+
+/* Reorder ord[0..n) so that ord[k] holds the element of rank k by centroid
+ * (ties by triangle id) with smaller ranks before it and larger after it
+ * (quickselect).  Any split serves the oracle's BVH, which only prunes. */
+static int key_less(const oscene* s, int axis, int32_t a, int32_t b) {
+    double ka = g_sort_axis_key(s, a, axis), kb = g_sort_axis_key(s, b, axis);
+    return ka < kb || (ka == kb && a < b);
+}
+static void select_kth(const oscene* s, int axis, int32_t* ord, int32_t n, int32_t k) {
+    int32_t lo = 0, hi = n - 1;
+    while (hi > lo) {
+        int32_t piv = ord[lo + (hi - lo) / 2];
+        int32_t i = lo, j = hi;
+        while (i <= j) {
+            while (key_less(s, axis, ord[i], piv)) ++i;
+            while (key_less(s, axis, piv, ord[j])) --j;
+            if (i <= j) {
+                int32_t t = ord[i]; ord[i] = ord[j]; ord[j] = t;
+                ++i; --j;
+            }
+        }
+        if (k <= j) hi = j;
+        else if (k >= i) lo = i;
+        else return;
+    }
 }
 
 static int32_t build_node(oscene* s, int32_t first, int32_t count) {
@@ -240,10 +256,8 @@ static int32_t build_node(oscene* s, int32_t first, int32_t count) {
     double ext = chi[0] - clo[0];
     for (int k = 1; k < 3; ++k)
         if (chi[k] - clo[k] > ext) { ext = chi[k] - clo[k]; axis = k; }
-    g_sort_scene = s;
-    g_sort_axis = axis;
-    qsort(s->order + first, (size_t)count, sizeof(int32_t), cmp_tri);
     int32_t half = count / 2;
+    select_kth(s, axis, s->order + first, count, half);
     int32_t l = build_node(s, first, half);
     int32_t r = build_node(s, first + half, count - half);
     s->nodes[id].left = l;
@@ -900,5 +914,139 @@ void orc_composite(int32_t n, int32_t H, const orc_lens* lens, double t, const o
                 out[4 * q + k] = blur + f * (col[4 * q + k] - blur);
             }
             out[4 * q + 3] = 0.0;
+        }
+}
+
+/* ------------------------------------------------------------------------
+ * Differentiable post-path with frozen visibility.  The thin-lens samples of
+ * a forward trace are recorded per ray as (L rgb, z) -- radiance and view
+ * depth of the hit, z = +inf for a miss -- so the trace accumulation can be
+ * re-evaluated at another focus distance and aperture with the same hits
+ * (the visibility is held fixed; only each hit's CoC, split weight and CoC
+ * magnitude change).  rec: [n_rays][4]; off[p]: first ray of pixel p
+ * (row-major prefix of spp).
+ * ---------------------------------------------------------------------- */
+void orc_trace_records(const void* sp, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
+                       const uint8_t* spp, const int64_t* off, double* rec) {
+    const oscene* s = (const oscene*)sp;
+    int32_t W = cam->width, H = cam->height;
+    double A = lens->aperture_radius, zf = lens->focus_dist;
+    uint32_t key[2] = {p->seed, (uint32_t)p->view * 65536u + (uint32_t)p->frame};
+    (void)H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t j = 0; j < cam->height; ++j)
+        for (int32_t i = 0; i < W; ++i) {
+            size_t q = (size_t)j * W + i;
+            int n = spp[q];
+            if (!n) continue;
+            double d[3], Pf[3];
+            orc_pinhole_dir(cam, i + 0.5 + cam->jitter[0], j + 0.5 + cam->jitter[1], d);
+            for (int k = 0; k < 3; ++k) Pf[k] = cam->pos[k] + zf * d[k];
+            for (int smp = 0; smp < n; ++smp) {
+                uint32_t ctr[4] = {(uint32_t)q, (uint32_t)smp, 0u, 0u}, x[4];
+                orc_philox(ctr, key, x);
+                double rho = A * sqrt(u01(x[0])), th = 2.0 * PI_D * u01(x[1]);
+                double O[3], dir[3];
+                for (int k = 0; k < 3; ++k)
+                    O[k] = cam->pos[k] + rho * cos(th) * cam->right[k] + rho * sin(th) * cam->up[k];
+                sub3(Pf, O, dir);
+                normalize3(dir);
+                double th_, bary[3], n_[3], L[3], P[3], z;
+                int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
+                if (id >= 0) {
+                    for (int k = 0; k < 3; ++k) P[k] = O[k] + th_ * dir[k];
+                    double v[3];
+                    sub3(P, cam->pos, v);
+                    z = dot3(v, cam->fwd);
+                    shade_hit(s, id, bary, dir, p, n_, L);
+                } else {
+                    z = INFINITY;
+                    L[0] = L[1] = L[2] = 0.0;
+                }
+                double* r = rec + 4 * (size_t)(off[q] + smp);
+                r[0] = L[0]; r[1] = L[1]; r[2] = L[2]; r[3] = z;
+            }
+        }
+}
+
+/* The trace accumulation (same definitions as orc_trace) from recorded hits;
+ * P_far is not recorded and is left 0. */
+void orc_replay(int32_t W, int32_t H, const orc_lens* lens, double t, const uint8_t* spp, const int64_t* off,
+                const double* rec, double* rt) {
+#pragma omp parallel for
+    for (int32_t j = 0; j < H; ++j)
+        for (int32_t i = 0; i < W; ++i) {
+            size_t q = (size_t)j * W + i;
+            double* o = rt + 12 * q;
+            int n = spp[q];
+            memset(o, 0, 12 * sizeof(double));
+            if (!n) continue;
+            double SwL[3] = {0, 0, 0}, SfL[3] = {0, 0, 0}, Sw = 0, Sf = 0, Swc = 0, Sfc = 0;
+            for (int smp = 0; smp < n; ++smp) {
+                const double* r = rec + 4 * (size_t)(off[q] + smp);
+                double c = orc_coc(r[3], lens, H, t);
+                double w = clampd((c + SQRT2) / (2.0 * SQRT2), 0.0, 1.0), ac = fabs(c);
+                for (int k = 0; k < 3; ++k) { SwL[k] += w * r[k]; SfL[k] += (1.0 - w) * r[k]; }
+                Sw += w; Sf += 1.0 - w; Swc += w * ac; Sfc += (1.0 - w) * ac;
+            }
+            int nok = Sw >= EMPTY_W, fok = Sf >= EMPTY_W;
+            for (int k = 0; k < 3; ++k) {
+                o[k] = nok ? SwL[k] / Sw : 0.0;
+                o[4 + k] = fok ? SfL[k] / Sf : 0.0;
+            }
+            o[3] = Sw / n;
+            o[7] = nok ? Swc / Sw : -1.0;
+            o[11] = fok ? Sfc / Sf : -1.0;
+        }
+}
+
+/* Temporal reconstruction of orc_temporal with the history already sampled
+ * at the reprojected positions and held fixed: hs[p][12] = (near rgb, B_near,
+ * far rgb, B_far, mu1, mu2, flags = valid_near + 2 valid_far, hlen). */
+void orc_temporal_frozen(int32_t W, int32_t H, const orc_params* p, const double* rt, const uint8_t* spp,
+                         const double* hs, double* crt, double* hacc, double* mom, uint8_t* hlen) {
+    double al = p->ema_alpha;
+#pragma omp parallel for
+    for (int32_t j = 0; j < H; ++j)
+        for (int32_t i = 0; i < W; ++i) {
+            size_t q = (size_t)j * W + i;
+            if (spp[q] == 0) {
+                crt[4 * q] = crt[4 * q + 1] = crt[4 * q + 2] = 0.0;
+                crt[4 * q + 3] = -1.0;
+                hacc[q] = 0.0;
+                mom[2 * q] = mom[2 * q + 1] = 0.0;
+                hlen[q] = 0;
+                continue;
+            }
+            const double* r = rt + 12 * q;
+            const double* s = hs + 12 * q;
+            double h = r[3], cn = r[7], cf = r[11];
+            int nok = cn >= 0.0, fok = cf >= 0.0;
+            int flags = (int)s[10], vn = flags & 1, vf = (flags >> 1) & 1;
+            double Ccur[3];
+            for (int k = 0; k < 3; ++k)
+                Ccur[k] = nok ? (fok ? h * r[k] + (1.0 - h) * r[4 + k] : r[k]) : r[4 + k];
+            double Y = luminance(Ccur);
+            double cur_n[4] = {h * r[0], h * r[1], h * r[2], h};
+            double cur_f[4] = {(1 - h) * r[4], (1 - h) * r[5], (1 - h) * r[6], 1 - h};
+            double on[4], of[4];
+            for (int k = 0; k < 4; ++k) {
+                on[k] = vn ? s[k] + al * (cur_n[k] - s[k]) : cur_n[k];
+                of[k] = vf ? s[4 + k] + al * (cur_f[k] - s[4 + k]) : cur_f[k];
+            }
+            mom[2 * q] = vn ? s[8] + al * (Y - s[8]) : Y;
+            mom[2 * q + 1] = vn ? s[9] + al * (Y * Y - s[9]) : Y * Y;
+            int nh = vn ? (int)s[11] + 1 : 1;
+            hlen[q] = (uint8_t)(nh > 255 ? 255 : nh);
+            double Bn = on[3], Bf = of[3];
+            double Hacc = (Bn + Bf >= EMPTY_W) ? Bn / (Bn + Bf) : h;
+            int an = Bn >= EMPTY_W, af = Bf >= EMPTY_W;
+            double hw = p->camera_moved ? h : Hacc;
+            for (int k = 0; k < 3; ++k) {
+                double Cn = an ? on[k] / Bn : 0.0, Cf = af ? of[k] / Bf : 0.0;
+                crt[4 * q + k] = !an ? Cf : (!af ? Cn : hw * Cn + (1.0 - hw) * Cf);
+            }
+            crt[4 * q + 3] = !nok ? cf : (!fok ? cn : Hacc * cn + (1.0 - Hacc) * cf);
+            hacc[q] = Hacc;
         }
 }

@@ -92,5 +92,12 @@ void orc_composite(int32_t n, int32_t H, const orc_lens* lens, double tan_half_f
                    const double* pp, const double* crt, const double* crec, const double* hacc,
                    double* out);
 double orc_disk_area(double r);
+/* ---- differentiable post-path with frozen visibility ---- */
+void orc_trace_records(const void* s, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
+                       const uint8_t* spp, const int64_t* off, double* rec);
+void orc_replay(int32_t W, int32_t H, const orc_lens* lens, double tan_half_fovy, const uint8_t* spp,
+                const int64_t* off, const double* rec, double* rt);
+void orc_temporal_frozen(int32_t W, int32_t H, const orc_params* p, const double* rt, const uint8_t* spp,
+                         const double* hs, double* crt, double* hacc, double* mom, uint8_t* hlen);
 int32_t orc_num_threads(void);
 #endif

@@ -97,6 +97,10 @@ def lib():
                                     C.POINTER(Params), dp, dp, up8, dp, dp, dp, dp, dp]
         L.orc_num_threads.restype = C.c_int32
         L.orc_disk_area.argtypes = [C.c_double]
+        i64p = C.POINTER(C.c_int64)
+        L.orc_trace_records.argtypes = [vp, C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), up8, i64p, dp]
+        L.orc_replay.argtypes = [C.c_int32, C.c_int32, C.POINTER(Lens), C.c_double, up8, i64p, dp, dp]
+        L.orc_temporal_frozen.argtypes = [C.c_int32, C.c_int32, C.POINTER(Params), dp, up8, dp, dp, dp, dp, up8]
         L.orc_disk_area.restype = C.c_double
         _lib = L
     return _lib
@@ -339,6 +343,68 @@ def frame(oscene, cam_, prev_cam, lens_, params_, hist=None, pp_pix=None):
         out = composite(flat(g["nd"]), flat(g["col"]), flat(m["spp"]), pp, flat(crt),
                         flat(crec), flat(hacc), lens_, t, params_, H)
     return dict(g=g, mask=m, rt=rt, hist=newh, crt=crt, hacc=hacc, crec=crec, pp=pp, out=out)
+
+
+def ray_offsets(spp):
+    """Row-major prefix of spp: first ray of each pixel, and the ray count."""
+    s = np.asarray(spp, np.int64).ravel()
+    off = np.zeros(s.size, np.int64)
+    np.cumsum(s[:-1], out=off[1:])
+    return off, int(s.sum())
+
+
+def trace_records(oscene: OScene, cam_, lens_, params_, spp):
+    """Per-ray (L rgb, z) of the thin-lens samples (z = inf for a miss)."""
+    spp = np.ascontiguousarray(spp, np.uint8)
+    off, n = ray_offsets(spp)
+    rec = np.zeros((max(n, 1), 4))
+    lib().orc_trace_records(oscene.h, C.byref(cam(cam_)), C.byref(lens(lens_)), C.byref(params(params_)),
+                            spp.ctypes.data_as(C.POINTER(C.c_uint8)), off.ctypes.data_as(C.POINTER(C.c_int64)),
+                            _d(rec)[1])
+    return rec, off
+
+
+def replay(lens_, tan_half_fovy, spp, rec, off):
+    H, W = np.asarray(spp).shape
+    rt = np.empty((H, W, 12))
+    off = np.ascontiguousarray(off, np.int64)
+    lib().orc_replay(W, H, C.byref(lens(lens_)), float(tan_half_fovy), _u8(spp)[1],
+                     off.ctypes.data_as(C.POINTER(C.c_int64)), _d(rec)[1], _d(rt)[1])
+    return rt
+
+
+def temporal_frozen(params_, rt, spp, hs):
+    H, W = np.asarray(spp).shape
+    crt = np.empty((H, W, 4))
+    hacc = np.empty((H, W))
+    mom = np.empty((H, W, 2))
+    hlen = np.empty((H, W), np.uint8)
+    lib().orc_temporal_frozen(W, H, C.byref(params(params_)), _d(rt)[1], _u8(spp)[1], _d(hs)[1], _d(crt)[1],
+                              _d(hacc)[1], _d(mom)[1], _u8(hlen)[1])
+    return crt, hacc, mom, hlen
+
+
+def post_forward(col, z, spp, rec, off, hs, cam_, lens_, params_, pp_pix=None):
+    """Differentiable post-path with frozen visibility: replay -> temporal
+    (frozen history samples) -> spatial -> post-filter -> composite."""
+    H, W = np.asarray(spp).shape
+    t = cam_.tan_half_fovy
+    nd = np.zeros((H, W, 4))
+    nd[..., 2] = -1.0
+    nd[..., 3] = z
+    col4 = np.zeros((H, W, 4))
+    col4[..., :3] = col
+    rt = replay(lens_, t, spp, rec, off)
+    crt, hacc, mom, hlen = temporal_frozen(params_, rt, spp, hs)
+    crec = spatial(params_, crt, spp, mom, hlen)
+    pp = postfilter(nd, col4, lens_, t, params_, pix=pp_pix)
+    if pp_pix is None:
+        out = composite(nd, col4, spp, pp, crt, crec, hacc, lens_, t, params_, H)
+    else:
+        sel = np.asarray(pp_pix)
+        flat = lambda a: a.reshape(H * W, *a.shape[2:])[sel]  # noqa: E731
+        out = composite(flat(nd), flat(col4), flat(spp), pp, flat(crt), flat(crec), flat(hacc), lens_, t, params_, H)
+    return dict(rt=rt, crt=crt, hacc=hacc, mom=mom, hlen=hlen, crec=crec, pp=pp, out=out)
 
 
 def disk_area(r: float) -> float:

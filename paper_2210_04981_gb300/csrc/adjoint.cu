@@ -1,0 +1,715 @@
+// Differentiable post-path: the frame's reconstruction, post-filter and
+// composite as a function of the sharp colour image and of the lens (focus
+// distance, aperture), with the ray-traced visibility held fixed, and its
+// hand-written adjoint.  The paper has no gradient; this makes the method's
+// post-path usable inside an optimisation loop (e.g. fitting the lens to a
+// reference image).
+//
+// Frozen inputs: per-ray hit records (radiance, view depth) from hdof_trace,
+// the mask (spp), the depth plane, and the history already sampled at its
+// reprojected positions.  Forward: replay of the trace accumulation at the
+// new lens (each hit's CoC, split weight and CoC magnitude change, the hits
+// do not) -> temporal EMA over the frozen history samples -> spatial gather
+// -> post-filter -> composite; the same kernels as the frame path where the
+// definitions coincide.  Backward: composite -> spatial (transposed gather)
+// -> temporal and replay (per pixel, recomputed) -> post-filter (transposed
+// gather over each source pixel's own disk, gather weights recomputed, not
+// stored).  The lens gradient is reduced per block in double precision and
+// summed in a fixed order: the result is deterministic.
+#include <cmath>
+
+#include "internal.h"
+
+namespace hdof {
+namespace {
+
+constexpr float RS2 = 0.35355339059327373f;  // 1 / (2 sqrt2): slope of w_near inside the focus zone
+
+struct LensD {
+    float K;    // A H / t
+    float izf;  // 1 / zf
+    float Ht;   // H / t
+};
+
+__device__ __forceinline__ float coc_z(float z, const LensD& L) {
+    return isinf(z) ? -L.K * L.izf : L.K * (1.f / z - L.izf);
+}
+// (dc/dzf, dc/dA) of the CoC of a point at depth z (z = inf: the miss CoC)
+__device__ __forceinline__ float2 dcoc(float z, const LensD& L) {
+    float u = isinf(z) ? -L.izf : 1.f / z - L.izf;
+    return make_float2(L.K * L.izf * L.izf, L.Ht * u);
+}
+__device__ __forceinline__ float wn_slope(float c) { return (c > -HDOF_SQRT2 && c < HDOF_SQRT2) ? RS2 : 0.f; }
+__device__ __forceinline__ float dot3f(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 ldf3(const float4& v) { return f3(v.x, v.y, v.z); }
+
+// block sum of a per-thread (float, float) in double, fixed order; lane 0 of
+// warp 0 writes the block's partial
+__device__ __forceinline__ void block_partial(float2 v, double2* partial) {
+    __shared__ double red[2][32];
+    double a = v.x, b = v.y;
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    if (l == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int k = 0; k < nw; ++k) {
+            sa += red[0][k];
+            sb += red[1][k];
+        }
+        partial[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(sa, sb);
+    }
+}
+
+// ------------------------------------------------------------ forward ----
+
+struct ReplaySums {
+    float3 SwL, SfL;
+    float Sw, Sf, Swc, Sfc;
+};
+
+__device__ __forceinline__ ReplaySums replay_sums(const float4* rec, unsigned first, int n, const LensD& L) {
+    ReplaySums s;
+    s.SwL = s.SfL = f3(0.f, 0.f, 0.f);
+    s.Sw = s.Sf = s.Swc = s.Sfc = 0.f;
+    for (int k = 0; k < n; ++k) {
+        float4 r = __ldg(&rec[first + k]);
+        float c = coc_z(r.w, L);
+        float w = w_near(c), wf = 1.f - w, ac = fabsf(c);
+        s.SwL = s.SwL + w * ldf3(r);
+        s.SfL = s.SfL + wf * ldf3(r);
+        s.Sw += w;
+        s.Sf += wf;
+        s.Swc += w * ac;
+        s.Sfc += wf * ac;
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(256) k_replay(const float4* __restrict__ rec, const unsigned* __restrict__ ray_off,
+                                                const uint8_t* __restrict__ spp, int W, int H, LensD L,
+                                                float4* __restrict__ rt) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= W || j >= H) return;
+    size_t q = (size_t)j * W + i;
+    int n = spp[q];
+    if (!n) return;
+    ReplaySums s = replay_sums(rec, ray_off[q], n, L);
+    bool nok = s.Sw >= HDOF_EMPTY_W, fok = s.Sf >= HDOF_EMPTY_W;
+    float in = nok ? 1.f / s.Sw : 0.f, inf_ = fok ? 1.f / s.Sf : 0.f;
+    rt[3 * q] = make_float4(s.SwL.x * in, s.SwL.y * in, s.SwL.z * in, s.Sw / (float)n);
+    rt[3 * q + 1] = make_float4(s.SfL.x * inf_, s.SfL.y * inf_, s.SfL.z * inf_, nok ? s.Swc * in : -1.f);
+    rt[3 * q + 2] = make_float4(0.f, 0.f, 0.f, fok ? s.Sfc * inf_ : -1.f);
+}
+
+// history sampled at the reprojected positions: (near rgb, B) (far rgb, B) (mu1, mu2, flags, hlen)
+struct HistS {
+    float4 hn, hf;
+    float m1, m2;
+    bool vn, vf;
+    int hl;
+};
+__device__ __forceinline__ HistS load_hs(const float4* hs, size_t q) {
+    HistS h;
+    if (!hs) {
+        h.hn = h.hf = make_float4(0.f, 0.f, 0.f, 0.f);
+        h.m1 = h.m2 = 0.f;
+        h.vn = h.vf = false;
+        h.hl = 0;
+        return h;
+    }
+    h.hn = __ldg(&hs[3 * q]);
+    h.hf = __ldg(&hs[3 * q + 1]);
+    float4 t = __ldg(&hs[3 * q + 2]);
+    h.m1 = t.x;
+    h.m2 = t.y;
+    int fl = (int)t.z;
+    h.vn = fl & 1;
+    h.vf = (fl >> 1) & 1;
+    h.hl = (int)t.w;
+    return h;
+}
+
+// the temporal step with frozen history samples (forward values used by the adjoint)
+struct TempF {
+    float h, cn, cf;
+    bool nok, fok;
+    float3 Cn, Cf, Ccur;
+    float Y;
+    float4 on, of;
+    float2 om;
+    float Bn, Bf, Hacc, hw;
+    bool an, af, hsum;
+    float3 CnA, CfA, C;
+    float crt_c;
+};
+
+__device__ __forceinline__ TempF temporal_fwd(float4 r0, float4 r1, float4 r2, const HistS& hs, float al, int moved) {
+    TempF t;
+    t.h = r0.w;
+    t.cn = r1.w;
+    t.cf = r2.w;
+    t.nok = t.cn >= 0.f;
+    t.fok = t.cf >= 0.f;
+    t.Cn = ldf3(r0);
+    t.Cf = ldf3(r1);
+    t.Ccur = t.nok ? (t.fok ? t.h * t.Cn + (1.f - t.h) * t.Cf : t.Cn) : t.Cf;
+    t.Y = luminance(t.Ccur);
+    float4 cur_n = make_float4(t.h * t.Cn.x, t.h * t.Cn.y, t.h * t.Cn.z, t.h);
+    float4 cur_f = make_float4((1.f - t.h) * t.Cf.x, (1.f - t.h) * t.Cf.y, (1.f - t.h) * t.Cf.z, 1.f - t.h);
+    const float4 hn = hs.hn, hf = hs.hf;
+    t.on = hs.vn ? make_float4(fmaf(al, cur_n.x - hn.x, hn.x), fmaf(al, cur_n.y - hn.y, hn.y),
+                               fmaf(al, cur_n.z - hn.z, hn.z), fmaf(al, cur_n.w - hn.w, hn.w))
+                 : cur_n;
+    t.of = hs.vf ? make_float4(fmaf(al, cur_f.x - hf.x, hf.x), fmaf(al, cur_f.y - hf.y, hf.y),
+                               fmaf(al, cur_f.z - hf.z, hf.z), fmaf(al, cur_f.w - hf.w, hf.w))
+                 : cur_f;
+    t.om = hs.vn ? make_float2(fmaf(al, t.Y - hs.m1, hs.m1), fmaf(al, t.Y * t.Y - hs.m2, hs.m2))
+                 : make_float2(t.Y, t.Y * t.Y);
+    t.Bn = t.on.w;
+    t.Bf = t.of.w;
+    t.hsum = t.Bn + t.Bf >= HDOF_EMPTY_W;
+    t.Hacc = t.hsum ? t.Bn / (t.Bn + t.Bf) : t.h;
+    t.an = t.Bn >= HDOF_EMPTY_W;
+    t.af = t.Bf >= HDOF_EMPTY_W;
+    t.hw = moved ? t.h : t.Hacc;
+    t.CnA = t.an ? (1.f / t.Bn) * ldf3(t.on) : f3(0, 0, 0);
+    t.CfA = t.af ? (1.f / t.Bf) * ldf3(t.of) : f3(0, 0, 0);
+    t.C = !t.an ? t.CfA : (!t.af ? t.CnA : t.hw * t.CnA + (1.f - t.hw) * t.CfA);
+    t.crt_c = !t.nok ? t.cf : (!t.fok ? t.cn : t.Hacc * t.cn + (1.f - t.Hacc) * t.cf);
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_temporal_frozen(const float4* __restrict__ rt, const uint8_t* __restrict__ spp,
+                                                         const float4* __restrict__ hs, int W, int H, float al,
+                                                         int moved, float4* __restrict__ crt, float* __restrict__ hacc,
+                                                         float2* __restrict__ mom, uint8_t* __restrict__ hlen) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= W || j >= H) return;
+    size_t q = (size_t)j * W + i;
+    if (!spp[q]) {
+        crt[q] = make_float4(0.f, 0.f, 0.f, -1.f);
+        hlen[q] = 0;
+        return;
+    }
+    HistS h = load_hs(hs, q);
+    TempF t = temporal_fwd(rt[3 * q], rt[3 * q + 1], rt[3 * q + 2], h, al, moved);
+    crt[q] = make_float4(t.C.x, t.C.y, t.C.z, t.crt_c);
+    hacc[q] = t.Hacc;
+    mom[q] = t.om;
+    int nh = h.vn ? h.hl + 1 : 1;
+    hlen[q] = (uint8_t)(nh > 255 ? 255 : nh);
+}
+
+// ----------------------------------------------------------- backward ----
+
+// composite adjoint: per pixel; grad_col <- f g (the sharp term), gradients of
+// pp, crec, crt.w, hacc, and this pixel's share of the lens gradient
+__global__ void __launch_bounds__(256) k_composite_bwd(const float4* __restrict__ nd, const float4* __restrict__ col,
+                                                       const uint8_t* __restrict__ spp, const float4* __restrict__ pp,
+                                                       const float4* __restrict__ crt, const float4* __restrict__ crec,
+                                                       const float* __restrict__ hacc, const float4* __restrict__ gout,
+                                                       int W, int H, LensD L, float h_tau, float4* __restrict__ gcol,
+                                                       float4* __restrict__ gpp, float4* __restrict__ gcrec,
+                                                       float4* __restrict__ gcrt, float* __restrict__ ghacc,
+                                                       double2* partial) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    float2 dth = make_float2(0.f, 0.f);
+    if (i < W && j < H) {
+        size_t q = (size_t)j * W + i;
+        float z = __ldg(&nd[q].w);
+        float c = coc_z(z, L);
+        bool traced = spp[q] > 0;
+        float3 C = ldf3(__ldg(&col[q])), P = ldf3(__ldg(&pp[q])), g = ldf3(__ldg(&gout[q]));
+        float ce = traced ? __ldg(&crt[q].w) : fabsf(c);
+        float fu = HDOF_SQRT2 + 0.5f - ce, f = clamp01(fu);
+        float wn = w_near(c);
+        float3 nearc = P, farc = P, R = f3(0, 0, 0);
+        float b = 0.f, bu = 0.f;
+        if (traced) {
+            R = ldf3(__ldg(&crec[q]));
+            bu = __ldg(&hacc[q]) / h_tau;
+            b = clamp01(bu);
+            nearc = R;
+            farc = R + b * (P - R);
+        }
+        float3 blur = wn * nearc + (1.f - wn) * farc;
+        float3 gb = (1.f - f) * g;
+        float gf = dot3f(g, C - blur);
+        float gwn = dot3f(gb, nearc - farc);
+        float3 gnear = wn * gb, gfar = (1.f - wn) * gb;
+        float gc = wn_slope(c) * gwn;
+        float gfu = (fu > 0.f && fu < 1.f) ? gf : 0.f;
+        gcol[q] = make_float4(f * g.x, f * g.y, f * g.z, 0.f);
+        if (traced) {
+            float3 gr = gnear + (1.f - b) * gfar;
+            float3 gp = b * gfar;
+            float gbb = dot3f(gfar, P - R);
+            gpp[q] = make_float4(gp.x, gp.y, gp.z, 0.f);
+            gcrec[q] = make_float4(gr.x, gr.y, gr.z, 0.f);
+            gcrt[q] = make_float4(0.f, 0.f, 0.f, -gfu);
+            ghacc[q] = (bu > 0.f && bu < 1.f) ? gbb / h_tau : 0.f;
+        } else {
+            float3 gp = gnear + gfar;
+            gpp[q] = make_float4(gp.x, gp.y, gp.z, 0.f);
+            gc += -gfu * (c > 0.f ? 1.f : (c < 0.f ? -1.f : 0.f));
+        }
+        float2 dc = dcoc(z, L);
+        dth = make_float2(gc * dc.x, gc * dc.y);
+    }
+    block_partial(dth, partial);
+}
+
+// spatial adjoint, part 1 (per traced pixel): direct term, the variance blend,
+// and the per-gatherer factors a = beta g / W, b = a . C_sp of the gather
+__global__ void __launch_bounds__(256) k_spatial_bwd_prep(const float4* __restrict__ crt, const float2* __restrict__ mom,
+                                                          const uint8_t* __restrict__ hlen, const float4* __restrict__ aux,
+                                                          const float4* __restrict__ gcrec, int W, int H, float var_ref,
+                                                          float4* __restrict__ spb, float4* __restrict__ gcrt,
+                                                          float2* __restrict__ gmom) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= W || j >= H) return;
+    size_t q = (size_t)j * W + i;
+    float4 cp = crt[q];
+    if (cp.w < 0.f) return;
+    float2 m = mom[q];
+    float v = m.y - m.x * m.x;
+    float sig = sqrtf(fmaxf(0.f, v));
+    bool young = hlen[q] < 2;
+    float bu = sig / var_ref;
+    float beta = young ? 1.f : clamp01(bu);
+    float4 ax = aux[q];
+    float3 Csp = ldf3(ax), Crt = ldf3(cp), g = ldf3(gcrec[q]);
+    float gbeta = dot3f(g, Csp - Crt);
+    float2 gm = make_float2(0.f, 0.f);
+    if (!young && bu > 0.f && bu < 1.f && v > 0.f) {
+        float gs = gbeta / var_ref;
+        gm = make_float2(gs * (-m.x / sig), gs * (0.5f / sig));
+    }
+    gmom[q] = gm;
+    float3 a = (beta / ax.w) * g;
+    spb[q] = make_float4(a.x, a.y, a.z, dot3f(a, Csp));
+    float4 gc = gcrt[q];
+    float3 gd = (1.f - beta) * g;
+    gcrt[q] = make_float4(gc.x + gd.x, gc.y + gd.y, gc.z + gd.z, gc.w);
+}
+
+// spatial adjoint, part 2 (per traced pixel x over its own window): x as a
+// gathered sample of its neighbours and x as a gatherer
+__global__ void __launch_bounds__(256) k_spatial_bwd(const float4* __restrict__ crt, const float4* __restrict__ spb,
+                                                     int W, int H, float r_s, float4* __restrict__ gcrt) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7), j = blockIdx.y * 16 + (w >> 1) * 4 + (l >> 3);
+    if (i >= W || j >= H) return;
+    const size_t q = (size_t)j * W + i;
+    const float4 cx = crt[q];
+    if (cx.w < 0.f) return;
+    const float rx = fminf(cx.w * 0.5f, r_s);
+    const float rpx = cx.w * 0.5f < r_s ? 0.5f : 0.f;
+    const float4 bx = spb[q];
+    const float3 Cx = ldf3(cx), ax = ldf3(bx);
+    const int K = (int)ceilf(rx + 0.5f);
+    float3 gC = f3(0, 0, 0);
+    float gcx = 0.f;
+    const int y0 = max(j - K, 0), y1 = min(j + K, H - 1), x0 = max(i - K, 0), x1 = min(i + K, W - 1);
+    for (int y = y0; y <= y1; ++y) {
+        float dy = (float)(y - j);
+        for (int x = x0; x <= x1; ++x) {
+            float dx = (float)(x - i);
+            size_t qq = (size_t)y * W + x;
+            float4 cy = __ldg(&crt[qq]);
+            if (cy.w < 0.f) continue;
+            float d = sqrtf(fmaf(dx, dx, dy * dy));
+            float ux = rx - d + 0.5f, uy = fminf(cy.w * 0.5f, r_s) - d + 0.5f;
+            float sx = clamp01(ux), sy = clamp01(uy);
+            float spx = (ux > 0.f && ux < 1.f) ? 1.f : 0.f;
+            if (sx <= 0.f && spx == 0.f) continue;
+            float4 by = __ldg(&spb[qq]);
+            float3 ay = ldf3(by);
+            gC = gC + (sy * sx) * ay;
+            gcx += sy * spx * (dot3f(ay, Cx) - by.w);              // x gathered by y
+            gcx += spx * sy * (dot3f(ax, ldf3(cy)) - bx.w);        // x gathering y
+        }
+    }
+    float4 g = gcrt[q];
+    gcrt[q] = make_float4(g.x + gC.x, g.y + gC.y, g.z + gC.z, g.w + gcx * rpx);
+}
+
+// temporal + replay adjoint (per traced pixel, forward recomputed): the
+// gradient of crt, hacc and the moments back to each hit's CoC
+__global__ void __launch_bounds__(256) k_temporal_replay_bwd(const float4* __restrict__ rec,
+                                                             const unsigned* __restrict__ ray_off,
+                                                             const uint8_t* __restrict__ spp,
+                                                             const float4* __restrict__ hs, const float4* __restrict__ gcrt,
+                                                             const float* __restrict__ ghacc,
+                                                             const float2* __restrict__ gmom, int W, int H, LensD L,
+                                                             float al, int moved, double2* partial) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    float2 dth = make_float2(0.f, 0.f);
+    size_t q = (size_t)j * W + i;
+    int n = (i < W && j < H) ? spp[q] : 0;
+    if (n) {
+        const unsigned first = ray_off[q];
+        ReplaySums s = replay_sums(rec, first, n, L);
+        bool nok = s.Sw >= HDOF_EMPTY_W, fok = s.Sf >= HDOF_EMPTY_W;
+        float in = nok ? 1.f / s.Sw : 0.f, inf_ = fok ? 1.f / s.Sf : 0.f;
+        float4 r0 = make_float4(s.SwL.x * in, s.SwL.y * in, s.SwL.z * in, s.Sw / (float)n);
+        float4 r1 = make_float4(s.SfL.x * inf_, s.SfL.y * inf_, s.SfL.z * inf_, nok ? s.Swc * in : -1.f);
+        float4 r2 = make_float4(0.f, 0.f, 0.f, fok ? s.Sfc * inf_ : -1.f);
+        HistS hsv = load_hs(hs, q);
+        TempF t = temporal_fwd(r0, r1, r2, hsv, al, moved);
+        // ---- temporal adjoint ----
+        float4 g4 = gcrt[q];
+        float3 gC = ldf3(g4);
+        float gcc = g4.w, gH = ghacc[q];
+        float2 gom = gmom[q];
+        float3 gCnA = f3(0, 0, 0), gCfA = f3(0, 0, 0);
+        float gh = 0.f, ghw = 0.f, gcn = 0.f, gcf = 0.f;
+        if (!t.an) gCfA = gC;
+        else if (!t.af) gCnA = gC;
+        else {
+            gCnA = t.hw * gC;
+            gCfA = (1.f - t.hw) * gC;
+            ghw = dot3f(gC, t.CnA - t.CfA);
+        }
+        if (moved) gh += ghw;
+        else gH += ghw;
+        if (!t.nok) gcf += gcc;
+        else if (!t.fok) gcn += gcc;
+        else {
+            gH += gcc * (t.cn - t.cf);
+            gcn += t.Hacc * gcc;
+            gcf += (1.f - t.Hacc) * gcc;
+        }
+        float gBn = 0.f, gBf = 0.f;
+        if (t.hsum) {
+            float S = t.Bn + t.Bf, iS2 = 1.f / (S * S);
+            gBn += gH * t.Bf * iS2;
+            gBf -= gH * t.Bn * iS2;
+        } else {
+            gh += gH;
+        }
+        float3 gon = f3(0, 0, 0), gof = f3(0, 0, 0);
+        if (t.an) {
+            gon = (1.f / t.Bn) * gCnA;
+            gBn -= dot3f(gCnA, ldf3(t.on)) / (t.Bn * t.Bn);
+        }
+        if (t.af) {
+            gof = (1.f / t.Bf) * gCfA;
+            gBf -= dot3f(gCfA, ldf3(t.of)) / (t.Bf * t.Bf);
+        }
+        const float kn = hsv.vn ? al : 1.f, kf = hsv.vf ? al : 1.f;
+        float3 gcurn = kn * gon, gcurf = kf * gof;
+        float gcurnw = kn * gBn, gcurfw = kf * gBf;
+        float gY = kn * (gom.x + 2.f * t.Y * gom.y);
+        float3 gCn = t.h * gcurn, gCf = (1.f - t.h) * gcurf;
+        gh += dot3f(gcurn, t.Cn) + gcurnw - dot3f(gcurf, t.Cf) - gcurfw;
+        float3 gCcur = gY * f3(0.2126f, 0.7152f, 0.0722f);
+        if (t.nok && t.fok) {
+            gh += dot3f(gCcur, t.Cn - t.Cf);
+            gCn = gCn + t.h * gCcur;
+            gCf = gCf + (1.f - t.h) * gCcur;
+        } else if (t.nok) {
+            gCn = gCn + gCcur;
+        } else {
+            gCf = gCf + gCcur;
+        }
+        // ---- replay adjoint ----
+        float gSw = gh / (float)n, gSf = 0.f, gSwc = 0.f, gSfc = 0.f;
+        float3 gSwL = f3(0, 0, 0), gSfL = f3(0, 0, 0);
+        if (nok) {
+            gSwL = in * gCn;
+            gSw -= dot3f(gCn, s.SwL) * in * in;
+            gSwc = gcn * in;
+            gSw -= gcn * s.Swc * in * in;
+        }
+        if (fok) {
+            gSfL = inf_ * gCf;
+            gSf -= dot3f(gCf, s.SfL) * inf_ * inf_;
+            gSfc = gcf * inf_;
+            gSf -= gcf * s.Sfc * inf_ * inf_;
+        }
+        for (int k = 0; k < n; ++k) {
+            float4 r = __ldg(&rec[first + k]);
+            float c = coc_z(r.w, L);
+            float w = w_near(c), ac = fabsf(c);
+            float gw = gSw - gSf + dot3f(gSwL - gSfL, ldf3(r)) + (gSwc - gSfc) * ac;
+            float gac = gSwc * w + gSfc * (1.f - w);
+            float gc = gw * wn_slope(c) + gac * (c > 0.f ? 1.f : (c < 0.f ? -1.f : 0.f));
+            float2 dc = dcoc(r.w, L);
+            dth.x += gc * dc.x;
+            dth.y += gc * dc.y;
+        }
+    }
+    block_partial(dth, partial);
+}
+
+__device__ __forceinline__ float2 area_and_slope(const float4* tab, int n, float r) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&tab[mid].x) <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    float4 e = __ldg(&tab[lo]);
+    return make_float2(fmaf(e.z, r - e.x, e.y), e.z);
+}
+
+// post-filter adjoint, part 1 (per pixel p): factors of dL/d(near weight) =
+// A . C_q - E and dL/d(far weight) = Af . C_q - Ef, and the sharp-colour
+// fallback of an empty far layer
+__global__ void __launch_bounds__(256) k_pf_bwd_prep(const float4* __restrict__ aux, const float4* __restrict__ gpp,
+                                                     int W, int H, float4* __restrict__ pfb, float4* __restrict__ gcol) {
+    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= W || j >= H) return;
+    size_t q = (size_t)j * W + i;
+    float4 an = aux[2 * q], af = aux[2 * q + 1];
+    float3 g = ldf3(gpp[q]), N = ldf3(an), F = ldf3(af);
+    float Wn = an.w, Wf = af.w;
+    float alpha = clamp01(Wn);
+    float adash = (Wn > 0.f && Wn < 1.f) ? 1.f : 0.f;
+    float3 A = Wn > HDOF_PP_MIN_W ? (alpha / Wn) * g : f3(0, 0, 0);
+    float E = dot3f(A, N) - adash * dot3f(g, N - F);
+    float3 Af = f3(0, 0, 0);
+    float Ef = 0.f;
+    if (Wf > HDOF_PP_MIN_W) {
+        Af = ((1.f - alpha) / Wf) * g;
+        Ef = dot3f(Af, F);
+    } else {
+        float4 gc = gcol[q];  // F is this pixel's sharp colour
+        gcol[q] = make_float4(gc.x + (1.f - alpha) * g.x, gc.y + (1.f - alpha) * g.y, gc.z + (1.f - alpha) * g.z, 0.f);
+    }
+    pfb[2 * q] = make_float4(A.x, A.y, A.z, E);
+    pfb[2 * q + 1] = make_float4(Af.x, Af.y, Af.z, Ef);
+}
+
+// post-filter adjoint, part 2 (per source pixel q over the pixels its soft
+// disk reaches): colour gradient and the gradient of q's CoC
+__global__ void __launch_bounds__(256) k_pf_bwd(const float4* __restrict__ nd, const float4* __restrict__ col,
+                                                const float4* __restrict__ pfb, const float4* __restrict__ tab, int ntab,
+                                                int W, int H, LensD L, float rmax, float kz_rel,
+                                                float4* __restrict__ gcol, double2* partial) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7), j = blockIdx.y * 16 + (w >> 1) * 4 + (l >> 3);
+    float2 dth = make_float2(0.f, 0.f);
+    if (i < W && j < H) {
+        const size_t q = (size_t)j * W + i;
+        const float zq = __ldg(&nd[q].w);
+        const float c = coc_z(zq, L);
+        const bool clip = fabsf(c) * 0.5f >= rmax;
+        const float r = clip ? rmax : fabsf(c) * 0.5f, R = r + 0.5f;
+        const float rp = clip ? 0.f : (c > 0.f ? 0.5f : (c < 0.f ? -0.5f : 0.f));
+        const float2 as = area_and_slope(tab, ntab, r);
+        const float ia = 1.f / as.x, iap = -as.y * ia * ia * rp;
+        const float wn = w_near(c), wnp = wn_slope(c);
+        const float wnia = wn * ia, fia = (1.f - wn) * ia;
+        const float dwnia = wnp * ia + wn * iap, dfia = -wnp * ia + (1.f - wn) * iap;
+        const float3 Cq = ldf3(__ldg(&col[q]));
+        const float ka = 1.f + 1.f / kz_rel;
+        float3 gC = f3(0, 0, 0);
+        float S1 = 0.f, S2 = 0.f, S3 = 0.f, S4 = 0.f;
+        const int K = (int)ceilf(R);
+        const int y0 = max(j - K, 0), y1 = min(j + K, H - 1), x0 = max(i - K, 0), x1 = min(i + K, W - 1);
+        for (int y = y0; y <= y1; ++y) {
+            float dy = (float)(y - j);
+            for (int x = x0; x <= x1; ++x) {
+                float dx = (float)(x - i);
+                float u = R - sqrtf(fmaf(dx, dx, dy * dy));
+                if (u <= 0.f) continue;
+                size_t p = (size_t)y * W + x;
+                float s = fminf(u, 1.f), sp = u < 1.f ? 1.f : 0.f;
+                float kz = clamp01(ka - zq / (kz_rel * __ldg(&nd[p].w)));
+                float4 bn = __ldg(&pfb[2 * p]), bf = __ldg(&pfb[2 * p + 1]);
+                float3 An = ldf3(bn), Af = ldf3(bf);
+                gC = gC + (s * wnia) * An + (s * fia * kz) * Af;
+                float tn = dot3f(An, Cq) - bn.w, tf = (dot3f(Af, Cq) - bf.w) * kz;
+                S1 += tn * s;
+                S2 += tn * sp;
+                S3 += tf * s;
+                S4 += tf * sp;
+            }
+        }
+        float4 g0 = gcol[q];
+        gcol[q] = make_float4(g0.x + gC.x, g0.y + gC.y, g0.z + gC.z, 0.f);
+        float gc = S1 * dwnia + S2 * wnia * rp + S3 * dfia + S4 * fia * rp;
+        float2 dc = dcoc(zq, L);
+        dth = make_float2(gc * dc.x, gc * dc.y);
+    }
+    block_partial(dth, partial);
+}
+
+__global__ void k_reduce(const double2* __restrict__ partial, int n, float* out) {
+    __shared__ double red[2][256];
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        a += partial[k].x;
+        b += partial[k].y;
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = (float)red[0][0];
+        out[1] = (float)red[1][0];
+    }
+}
+
+LensD make_lensd(const hdof_lens& l, int H, float t) {
+    LensD L;
+    L.K = l.aperture_radius * (float)H / t;
+    L.izf = 1.f / l.focus_dist;
+    L.Ht = (float)H / t;
+    return L;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct BwdWs {
+    float4 *gpp, *gcrec, *gcrt, *spb, *pfb;
+    float* ghacc;
+    float2* gmom;
+    double2* partial;
+    int n_partial;
+    size_t bytes;
+};
+
+BwdWs bwd_layout(int W, int H, char* base) {
+    BwdWs b{};
+    size_t px = (size_t)W * H, o = 0;
+    auto take = [&](size_t n) {
+        size_t at = o;
+        o += up256(n);
+        return base ? base + at : nullptr;
+    };
+    b.gpp = reinterpret_cast<float4*>(take(16 * px));
+    b.gcrec = reinterpret_cast<float4*>(take(16 * px));
+    b.gcrt = reinterpret_cast<float4*>(take(16 * px));
+    b.spb = reinterpret_cast<float4*>(take(16 * px));
+    b.pfb = reinterpret_cast<float4*>(take(32 * px));
+    b.ghacc = reinterpret_cast<float*>(take(4 * px));
+    b.gmom = reinterpret_cast<float2*>(take(8 * px));
+    int n1 = ((W + 31) / 32) * ((H + 7) / 8), n2 = ((W + 15) / 16) * ((H + 15) / 16);
+    b.n_partial = 2 * n1 + n2;
+    b.partial = reinterpret_cast<double2*>(take(16 * (size_t)b.n_partial));
+    b.bytes = o;
+    return b;
+}
+
+int check_post(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+               const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p, const hdof_post_state* st,
+               const char* who) {
+    int rc;
+    if ((rc = check_camera(cam, who)) || (rc = check_lens(lens, who)) || (rc = check_params(p, who)) ||
+        (rc = check_gbuf(in, who, false)))
+        return rc;
+    HDOF_CHECK_ARG(in->dtype_nd == HDOF_F32 && in->dtype_col == HDOF_F32, "%s: the differentiable path is FP32", who);
+    HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "%s: gbuf/camera size mismatch", who);
+    HDOF_CHECK_ARG(spp && rec && ray_off && st, "%s: spp, rec, ray_off and state are required", who);
+    HDOF_CHECK_ARG(st->rt && st->crt && st->hacc && st->mom && st->hlen && st->crec && st->sp_aux && st->pp &&
+                       st->pp_aux && st->out,
+                   "%s: every state buffer is required", who);
+    HDOF_CHECK_ARG(lens->aperture_radius > 0.f, "%s: the lens gradient needs an aperture > 0", who);
+    return HDOF_OK;
+}
+
+}  // namespace
+}  // namespace hdof
+
+using namespace hdof;
+
+extern "C" size_t hdof_post_workspace_bytes(int32_t width, int32_t height, const hdof_params* p) {
+    if (width <= 0 || height <= 0) return 0;
+    size_t pf = ws_layout(width, height, p).pf_prep + ws_layout(width, height, p).pf_tiles;
+    size_t bw = bwd_layout(width, height, nullptr).bytes;
+    return pf > bw ? pf : bw;
+}
+
+extern "C" int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                                 const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
+                                 const hdof_params* p, const hdof_post_state* st, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_post(in, spp, rec, ray_off, cam, lens, p, st, "hdof_post_forward"))) return rc;
+    const int W = in->width, H = in->height;
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= hdof_post_workspace_bytes(W, H, p),
+                   "hdof_post_forward: workspace of %zu bytes < %zu", workspace_bytes,
+                   hdof_post_workspace_bytes(W, H, p));
+    cudaStream_t s = as_stream(stream);
+    LensD L = make_lensd(*lens, H, cam->tan_half_fovy);
+    dim3 g1((W + 31) / 32, (H + 7) / 8);
+    k_replay<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(rec), ray_off, spp, W, H, L,
+                                reinterpret_cast<float4*>(st->rt));
+    k_temporal_frozen<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(st->rt), spp,
+                                         reinterpret_cast<const float4*>(hist_samples), W, H, p->ema_alpha,
+                                         p->camera_moved, reinterpret_cast<float4*>(st->crt), st->hacc,
+                                         reinterpret_cast<float2*>(st->mom), st->hlen);
+    HDOF_LAUNCHED("hdof_post_forward: replay/temporal");
+    if ((rc = launch_spatial(reinterpret_cast<const float4*>(st->crt), reinterpret_cast<const float2*>(st->mom),
+                             st->hlen, W, H, p->r_s, p->var_ref, reinterpret_cast<float4*>(st->crec),
+                             reinterpret_cast<float4*>(st->sp_aux), s)))
+        return rc;
+    Coc coc = make_coc(*lens, H, cam->tan_half_fovy);
+    if ((rc = launch_postfilter(in, coc, p, st->pp, reinterpret_cast<float4*>(st->pp_aux), workspace, s))) return rc;
+    return launch_composite(in, spp, st->pp, st->crt, st->crec, st->hacc, coc, p->h_tau, st->out, s);
+}
+
+extern "C" int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                                  const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
+                                  const hdof_params* p, const hdof_post_state* st, const float* grad_out,
+                                  float* grad_col, float* grad_lens, void* workspace, size_t workspace_bytes,
+                                  void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_post(in, spp, rec, ray_off, cam, lens, p, st, "hdof_post_backward"))) return rc;
+    HDOF_CHECK_ARG(grad_out && grad_col && grad_lens, "hdof_post_backward: grad_out, grad_col, grad_lens required");
+    const int W = in->width, H = in->height;
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= hdof_post_workspace_bytes(W, H, p),
+                   "hdof_post_backward: workspace of %zu bytes < %zu", workspace_bytes,
+                   hdof_post_workspace_bytes(W, H, p));
+    cudaStream_t s = as_stream(stream);
+    if ((rc = ensure_area_table(s))) return rc;
+    const float4* tab = nullptr;
+    int ntab = 0;
+    if ((rc = area_table(&tab, &ntab))) return rc;
+    BwdWs b = bwd_layout(W, H, static_cast<char*>(workspace));
+    LensD L = make_lensd(*lens, H, cam->tan_half_fovy);
+    const float4* nd = static_cast<const float4*>(in->nd);
+    const float4* col = static_cast<const float4*>(in->col);
+    float4* gcol = reinterpret_cast<float4*>(grad_col);
+    dim3 g1((W + 31) / 32, (H + 7) / 8), g2((W + 15) / 16, (H + 15) / 16);
+    const int n1 = g1.x * g1.y;
+    HDOF_CUDA(cudaMemsetAsync(b.gcrt, 0, 16 * (size_t)W * H, s), "hdof_post_backward: clear");
+    HDOF_CUDA(cudaMemsetAsync(b.gmom, 0, 8 * (size_t)W * H, s), "hdof_post_backward: clear");
+    k_composite_bwd<<<g1, 256, 0, s>>>(nd, col, spp, reinterpret_cast<const float4*>(st->pp),
+                                       reinterpret_cast<const float4*>(st->crt), reinterpret_cast<const float4*>(st->crec),
+                                       st->hacc, reinterpret_cast<const float4*>(grad_out), W, H, L, p->h_tau, gcol, b.gpp,
+                                       b.gcrec, b.gcrt, b.ghacc, b.partial);
+    k_spatial_bwd_prep<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(st->crt),
+                                          reinterpret_cast<const float2*>(st->mom), st->hlen,
+                                          reinterpret_cast<const float4*>(st->sp_aux), b.gcrec, W, H, p->var_ref, b.spb,
+                                          b.gcrt, b.gmom);
+    k_spatial_bwd<<<g2, 256, 0, s>>>(reinterpret_cast<const float4*>(st->crt), b.spb, W, H, p->r_s, b.gcrt);
+    k_temporal_replay_bwd<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(rec), ray_off, spp,
+                                             reinterpret_cast<const float4*>(hist_samples), b.gcrt, b.ghacc, b.gmom, W,
+                                             H, L, p->ema_alpha, p->camera_moved, b.partial + n1);
+    k_pf_bwd_prep<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(st->pp_aux), b.gpp, W, H, b.pfb, gcol);
+    k_pf_bwd<<<g2, 256, 0, s>>>(nd, col, b.pfb, tab, ntab, W, H, L, p->r_max, p->kz_rel, gcol, b.partial + 2 * n1);
+    k_reduce<<<1, 256, 0, s>>>(b.partial, b.n_partial, grad_lens);
+    HDOF_LAUNCHED("hdof_post_backward");
+    return HDOF_OK;
+}

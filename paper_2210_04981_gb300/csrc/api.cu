@@ -115,7 +115,7 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     size_t mtiles = (size_t)((W + T - 1) / T) * ((H + T - 1) / T);
     size_t ptiles = (size_t)((W + HDOF_TILE_PF - 1) / HDOF_TILE_PF) * ((H + HDOF_TILE_PF - 1) / HDOF_TILE_PF);
     l.mask_tiles = align256(mtiles);
-    l.trace_counts = align256(ptiles * 3 * sizeof(unsigned) + 4 * sizeof(unsigned));
+    l.trace_counts = align256(ptiles * 4 * sizeof(unsigned) + 4 * sizeof(unsigned));
     l.trace_queue = align256(npx * sizeof(unsigned));
     l.pf_prep = align256(npx * sizeof(float4));
     l.pf_tiles = align256(ptiles * sizeof(float));

@@ -50,6 +50,21 @@ void launch(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const floa
 }
 
 }  // namespace
+
+int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
+                     const float* hacc, const Coc& coc, float h_tau, float* out, cudaStream_t s) {
+    if (in->dtype_nd == HDOF_F32 && in->dtype_col == HDOF_F32)
+        launch<float4, float4>(in, spp, pp, crt, crec, hacc, coc, h_tau, out, s);
+    else if (in->dtype_nd == HDOF_F16 && in->dtype_col == HDOF_BF16)
+        launch<half4s, bf164s>(in, spp, pp, crt, crec, hacc, coc, h_tau, out, s);
+    else if (in->dtype_nd == HDOF_F16)
+        launch<half4s, float4>(in, spp, pp, crt, crec, hacc, coc, h_tau, out, s);
+    else
+        launch<float4, bf164s>(in, spp, pp, crt, crec, hacc, coc, h_tau, out, s);
+    HDOF_LAUNCHED("composite");
+    return HDOF_OK;
+}
+
 }  // namespace hdof
 
 using namespace hdof;
@@ -64,16 +79,6 @@ extern "C" int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const flo
         return rc;
     HDOF_CHECK_ARG(spp && pp && crt && crec && hacc && out, "hdof_composite: NULL buffer");
     HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "hdof_composite: gbuf/camera size mismatch");
-    Coc coc = make_coc(*lens, cam->height, cam->tan_half_fovy);
-    cudaStream_t s = as_stream(stream);
-    if (in->dtype_nd == HDOF_F32 && in->dtype_col == HDOF_F32)
-        launch<float4, float4>(in, spp, pp, crt, crec, hacc, coc, p->h_tau, out, s);
-    else if (in->dtype_nd == HDOF_F16 && in->dtype_col == HDOF_BF16)
-        launch<half4s, bf164s>(in, spp, pp, crt, crec, hacc, coc, p->h_tau, out, s);
-    else if (in->dtype_nd == HDOF_F16)
-        launch<half4s, float4>(in, spp, pp, crt, crec, hacc, coc, p->h_tau, out, s);
-    else
-        launch<float4, bf164s>(in, spp, pp, crt, crec, hacc, coc, p->h_tau, out, s);
-    HDOF_LAUNCHED("hdof_composite");
-    return HDOF_OK;
+    return launch_composite(in, spp, pp, crt, crec, hacc, make_coc(*lens, cam->height, cam->tan_half_fovy), p->h_tau,
+                            out, as_stream(stream));
 }

@@ -68,6 +68,16 @@ WsLayout ws_layout(int W, int H, const hdof_params* p);
 // once per device.  Returns HDOF_OK or an error.
 int ensure_area_table(cudaStream_t s);
 int area_table_size();
+// device address of the table ((x, a(x), slope, 0) per breakpoint) and its length
+int area_table(const float4** tab, int* n);
+
+// launches shared by the frame calls and the differentiable post-path (arguments already checked)
+int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, int W, int H, float r_s, float var_ref,
+                   float4* crec, float4* aux, cudaStream_t s);
+int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, float4* aux,
+                      void* workspace, cudaStream_t s);
+int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
+                     const float* hacc, const Coc& coc, float h_tau, float* out, cudaStream_t s);
 
 }  // namespace hdof
 

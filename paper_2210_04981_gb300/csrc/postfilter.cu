@@ -101,7 +101,7 @@ __device__ __forceinline__ void pf_tap(PfAcc& a, float d, const float4& e, const
 }
 
 template <class COL>
-__device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size_t pq) {
+__device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size_t pq, float4* aux) {
     float alpha = clamp01(a.Wn);
     float3 N = a.Wn > HDOF_PP_MIN_W ? (1.f / a.Wn) * a.Sn : f3(0, 0, 0);
     float3 F;
@@ -109,6 +109,10 @@ __device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size
     else {
         float4 c = ld4(col + pq);
         F = f3(c.x, c.y, c.z);
+    }
+    if (aux) {  // layer colours and weights, kept for the adjoint
+        aux[2 * pq] = make_float4(N.x, N.y, N.z, a.Wn);
+        aux[2 * pq + 1] = make_float4(F.x, F.y, F.z, a.Wf);
     }
     float3 o = alpha * N + (1.f - alpha) * F;
     return make_float4(o.x, o.y, o.z, alpha);
@@ -119,7 +123,8 @@ __device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size
 template <class COL>
 __global__ void __launch_bounds__(128, 6) k_pf_gather(const float4* __restrict__ prep, const COL* __restrict__ col,
                                                    const float* __restrict__ tmax, int W, int H, int ntx, int nty,
-                                                   int kt, float kz_rel, float4* __restrict__ pp) {
+                                                   int kt, float kz_rel, float4* __restrict__ pp,
+                                                   float4* __restrict__ aux) {
     __shared__ int s_win;
     if (threadIdx.x == 0) s_win = 0;
     __syncthreads();
@@ -165,12 +170,13 @@ __global__ void __launch_bounds__(128, 6) k_pf_gather(const float4* __restrict__
             }
         }
     }
-    pp[pq] = pf_finish(a0, col, pq);
-    if (two) pp[pq + 1] = pf_finish(a1, col, pq + 1);
+    pp[pq] = pf_finish(a0, col, pq, aux);
+    if (two) pp[pq + 1] = pf_finish(a1, col, pq + 1, aux);
 }
 
 std::mutex g_area_mu;
 bool g_area_ready[64] = {false};
+int g_area_count[64] = {0};
 
 }  // namespace
 
@@ -241,12 +247,57 @@ int ensure_area_table(cudaStream_t s) {
     HDOF_CUDA(cudaMemcpyToSymbolAsync(g_area_n, &n, sizeof n, 0, cudaMemcpyHostToDevice, s), "area table: upload");
     HDOF_CUDA(cudaStreamSynchronize(s), "area table: upload");
     g_area_ready[dev] = true;
+    g_area_count[dev] = n;
+    return HDOF_OK;
+}
+
+int area_table(const float4** tab, int* n) {
+    int dev = 0;
+    HDOF_CUDA(cudaGetDevice(&dev), "area table: device");
+    void* p = nullptr;
+    HDOF_CUDA(cudaGetSymbolAddress(&p, g_area), "area table: symbol");
+    *tab = static_cast<const float4*>(p);
+    *n = (dev >= 0 && dev < 64) ? g_area_count[dev] : 0;
     return HDOF_OK;
 }
 
 }  // namespace hdof
 
 using namespace hdof;
+
+namespace hdof {
+
+int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, float4* aux,
+                      void* workspace, cudaStream_t s) {
+    int rc;
+    if ((rc = ensure_area_table(s))) return rc;
+    const int W = in->width, H = in->height;
+    WsLayout L = ws_layout(W, H, p);
+    float4* prep = static_cast<float4*>(workspace);
+    float* tmax = reinterpret_cast<float*>(static_cast<char*>(workspace) + L.pf_prep);
+    const int ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
+    dim3 grid(ntx, nty);
+    if (in->dtype_nd == HDOF_F32)
+        k_pf_prep<float4><<<grid, 256, 0, s>>>(static_cast<const float4*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
+    else
+        k_pf_prep<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
+    HDOF_LAUNCHED("post-filter prep");
+    int kt = (int)std::ceil((p->r_max + 0.5f) / TP) + 1;
+    // the taps are served from L1: prefer the largest L1 carve-out
+    if (in->dtype_col == HDOF_F32) {
+        cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        k_pf_gather<float4><<<grid, 128, 0, s>>>(prep, static_cast<const float4*>(in->col), tmax, W, H, ntx, nty, kt,
+                                                 p->kz_rel, reinterpret_cast<float4*>(pp), aux);
+    } else {
+        cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        k_pf_gather<bf164s><<<grid, 128, 0, s>>>(prep, static_cast<const bf164s*>(in->col), tmax, W, H, ntx, nty, kt,
+                                                 p->kz_rel, reinterpret_cast<float4*>(pp), aux);
+    }
+    HDOF_LAUNCHED("post-filter gather");
+    return HDOF_OK;
+}
+
+}  // namespace hdof
 
 extern "C" int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, const hdof_lens* lens,
                                const hdof_params* p, float* pp, void* workspace, size_t workspace_bytes,
@@ -258,33 +309,9 @@ extern "C" int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, cons
         return rc;
     HDOF_CHECK_ARG(pp, "hdof_postfilter: pp output is required");
     HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "hdof_postfilter: gbuf/camera size mismatch");
-    const int W = in->width, H = in->height;
-    WsLayout L = ws_layout(W, H, p);
+    WsLayout L = ws_layout(in->width, in->height, p);
     HDOF_CHECK_ARG(workspace && workspace_bytes >= L.pf_prep + L.pf_tiles,
                    "hdof_postfilter: workspace of %zu bytes < %zu", workspace_bytes, L.pf_prep + L.pf_tiles);
-    cudaStream_t s = as_stream(stream);
-    if ((rc = ensure_area_table(s))) return rc;
-    float4* prep = static_cast<float4*>(workspace);
-    float* tmax = reinterpret_cast<float*>(static_cast<char*>(workspace) + L.pf_prep);
-    const int ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
-    Coc coc = make_coc(*lens, H, cam->tan_half_fovy);
-    dim3 grid(ntx, nty);
-    if (in->dtype_nd == HDOF_F32)
-        k_pf_prep<float4><<<grid, 256, 0, s>>>(static_cast<const float4*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
-    else
-        k_pf_prep<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
-    HDOF_LAUNCHED("hdof_postfilter: prep");
-    int kt = (int)std::ceil((p->r_max + 0.5f) / TP) + 1;
-    // the taps are served from L1: prefer the largest L1 carve-out
-    if (in->dtype_col == HDOF_F32) {
-        cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        k_pf_gather<float4><<<grid, 128, 0, s>>>(prep, static_cast<const float4*>(in->col), tmax, W, H, ntx, nty, kt,
-                                                 p->kz_rel, reinterpret_cast<float4*>(pp));
-    } else {
-        cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        k_pf_gather<bf164s><<<grid, 128, 0, s>>>(prep, static_cast<const bf164s*>(in->col), tmax, W, H, ntx, nty, kt,
-                                                 p->kz_rel, reinterpret_cast<float4*>(pp));
-    }
-    HDOF_LAUNCHED("hdof_postfilter: gather");
-    return HDOF_OK;
+    return launch_postfilter(in, make_coc(*lens, in->height, cam->tan_half_fovy), p, pp, nullptr, workspace,
+                             as_stream(stream));
 }

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_temporal(TemporalArgs a, const ND* __re
 
 __global__ void __launch_bounds__(256) k_spatial(const float4* __restrict__ crt, const float2* __restrict__ mom,
                                                  const uint8_t* __restrict__ hlen, int W, int H, float r_s,
-                                                 float var_ref, float4* __restrict__ crec) {
+                                                 float var_ref, float4* __restrict__ crec, float4* __restrict__ aux) {
     // warp = 8x4 pixel block, block = 16x16 pixels
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7), j = blockIdx.y * 16 + (w >> 1) * 4 + (l >> 3);
@@ -208,11 +208,21 @@ __global__ void __launch_bounds__(256) k_spatial(const float4* __restrict__ crt,
     float sig = sqrtf(fmaxf(0.f, m.y - m.x * m.x));
     float beta = __ldg(&hlen[q]) < 2 ? 1.f : clamp01(sig / var_ref);
     float3 Csp = (1.f / Ws) * S;
+    if (aux) aux[q] = make_float4(Csp.x, Csp.y, Csp.z, Ws);  // kept for the adjoint
     crec[q] = make_float4(cp.x + beta * (Csp.x - cp.x), cp.y + beta * (Csp.y - cp.y), cp.z + beta * (Csp.z - cp.z),
                           0.f);
 }
 
 }  // namespace
+
+int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, int W, int H, float r_s, float var_ref,
+                   float4* crec, float4* aux, cudaStream_t s) {
+    dim3 g2((W + 15) / 16, (H + 15) / 16);
+    k_spatial<<<g2, 256, 0, s>>>(crt, mom, hlen, W, H, r_s, var_ref, crec, aux);
+    HDOF_LAUNCHED("spatial reconstruction");
+    return HDOF_OK;
+}
+
 }  // namespace hdof
 
 using namespace hdof;
@@ -265,9 +275,6 @@ extern "C" int hdof_reconstruct(const float* rt, const hdof_gbuf* in, const uint
     else
         k_temporal<half4s><<<g1, 256, 0, s>>>(a, static_cast<const half4s*>(in->nd));
     HDOF_LAUNCHED("hdof_reconstruct: temporal");
-    dim3 g2((W + 15) / 16, (H + 15) / 16);
-    k_spatial<<<g2, 256, 0, s>>>(reinterpret_cast<const float4*>(crt), reinterpret_cast<const float2*>(hist_out->mom),
-                                 hist_out->hlen, W, H, p->r_s, p->var_ref, reinterpret_cast<float4*>(crec));
-    HDOF_LAUNCHED("hdof_reconstruct: spatial");
-    return HDOF_OK;
+    return launch_spatial(reinterpret_cast<const float4*>(crt), reinterpret_cast<const float2*>(hist_out->mom),
+                          hist_out->hlen, W, H, p->r_s, p->var_ref, reinterpret_cast<float4*>(crec), nullptr, s);
 }

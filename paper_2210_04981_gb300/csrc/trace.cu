@@ -37,71 +37,92 @@ __global__ void __launch_bounds__(256) k_count(const uint8_t* __restrict__ spp, 
     }
 }
 
-// one block: exclusive scan of per-tile pixel counts -> offsets; totals -> stats
+// one block: exclusive scans of the per-tile pixel and ray counts -> queue
+// and ray offsets; totals -> stats
 __global__ void __launch_bounds__(1024) k_scan(const unsigned* __restrict__ counts, int ntiles,
-                                               unsigned* __restrict__ offsets, unsigned* __restrict__ totals,
-                                               unsigned* __restrict__ stats) {
-    __shared__ unsigned wsum[32];
-    __shared__ unsigned carry;
-    __shared__ unsigned long long rays;
-    if (threadIdx.x == 0) {
-        carry = 0;
-        rays = 0;
-    }
+                                               unsigned* __restrict__ offsets, unsigned* __restrict__ roffsets,
+                                               unsigned* __restrict__ totals, unsigned* __restrict__ stats) {
+    __shared__ unsigned wsum[2][32];
+    __shared__ unsigned carry[2];
+    if (threadIdx.x == 0) carry[0] = carry[1] = 0;
     __syncthreads();
-    unsigned long long myrays = 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < ntiles; base += 1024) {
         int t = base + threadIdx.x;
-        unsigned v = t < ntiles ? counts[2 * t] : 0u;
-        if (t < ntiles) myrays += counts[2 * t + 1];
-        unsigned x = v;
-        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            unsigned s = wsum[lane];
+        unsigned v[2] = {t < ntiles ? counts[2 * t] : 0u, t < ntiles ? counts[2 * t + 1] : 0u};
+        unsigned x[2] = {v[0], v[1]};
+        for (int c = 0; c < 2; ++c)
             for (int o = 1; o < 32; o <<= 1) {
-                unsigned y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
+                unsigned y = __shfl_up_sync(0xffffffffu, x[c], o);
+                if (lane >= o) x[c] += y;
             }
-            wsum[lane] = s;
+        if (lane == 31) {
+            wsum[0][w] = x[0];
+            wsum[1][w] = x[1];
         }
         __syncthreads();
-        unsigned excl = carry + (w ? wsum[w - 1] : 0u) + x - v;
-        if (t < ntiles) offsets[t] = excl;
+        if (w < 2) {
+            unsigned sv = wsum[w][lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(0xffffffffu, sv, o);
+                if (lane >= o) sv += y;
+            }
+            wsum[w][lane] = sv;
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
+        unsigned e0 = carry[0] + (w ? wsum[0][w - 1] : 0u) + x[0] - v[0];
+        unsigned e1 = carry[1] + (w ? wsum[1][w - 1] : 0u) + x[1] - v[1];
+        if (t < ntiles) {
+            offsets[t] = e0;
+            roffsets[t] = e1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) {
+            carry[0] = e0 + v[0];
+            carry[1] = e1 + v[1];
+        }
         __syncthreads();
     }
-    for (int o = 16; o; o >>= 1) myrays += __shfl_xor_sync(0xffffffffu, myrays, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&rays, myrays);
-    __syncthreads();
     if (threadIdx.x == 0) {
-        totals[0] = carry;  // queue length
-        totals[1] = 0;      // queue head
+        totals[0] = carry[0];  // queue length
+        totals[1] = 0;         // queue head
         if (stats) {
-            stats[0] = carry;
-            stats[1] = (unsigned)rays;
+            stats[0] = carry[0];
+            stats[1] = carry[1];
         }
     }
 }
 
+// queue entries in row-major order within each tile; optionally the first
+// ray of every traced pixel (tile ray offset + prefix of spp in queue order)
 __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ spp, int W, int H, int ntx,
-                                                 const unsigned* __restrict__ offsets, unsigned* __restrict__ queue) {
+                                                 const unsigned* __restrict__ offsets,
+                                                 const unsigned* __restrict__ roffsets, unsigned* __restrict__ queue,
+                                                 unsigned* __restrict__ ray_off) {
     int i = blockIdx.x * TB + (threadIdx.x & 15), j = blockIdx.y * TB + (threadIdx.x >> 4);
-    bool on = (i < W && j < H) && spp[(size_t)j * W + i] > 0;
+    unsigned n = (i < W && j < H) ? spp[(size_t)j * W + i] : 0u;
+    bool on = n > 0;
     unsigned m = __ballot_sync(0xffffffffu, on);
-    __shared__ unsigned wcnt[8];
+    __shared__ unsigned wcnt[8], wray[8];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned r = n;  // inclusive warp prefix of spp
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, r, o);
+        if (lane >= o) r += y;
+    }
     if (lane == 0) wcnt[w] = __popc(m);
+    if (lane == 31) wray[w] = r;
     __syncthreads();
-    unsigned base = offsets[blockIdx.y * ntx + blockIdx.x];
-    for (int k = 0; k < w; ++k) base += wcnt[k];
-    if (on) queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)(j * W + i);
+    const int tile = blockIdx.y * ntx + blockIdx.x;
+    unsigned base = offsets[tile], rbase = roffsets[tile];
+    for (int k = 0; k < w; ++k) {
+        base += wcnt[k];
+        rbase += wray[k];
+    }
+    if (on) {
+        queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)(j * W + i);
+        if (ray_off) ray_off[(size_t)j * W + i] = rbase + r - n;
+    }
 }
 
 struct TraceArgs {
@@ -117,6 +138,8 @@ struct TraceArgs {
     const unsigned* queue;
     unsigned* totals;  // [0] queue length, [1] head
     float4* rt;        // 3 float4 per pixel
+    float4* rec;       // optional per-ray (L rgb, z) records, z = +inf for a miss
+    const unsigned* ray_off;
 };
 
 __device__ __forceinline__ void trace_pixel(const TraceArgs& a, unsigned q) {
@@ -146,6 +169,8 @@ __device__ __forceinline__ void trace_pixel(const TraceArgs& a, unsigned q) {
             c = a.coc.at_infinity();
             L = f3(0.f, 0.f, 0.f);
         }
+        if (a.rec) a.rec[a.ray_off[q] + smp] = make_float4(L.x, L.y, L.z, h.slot >= 0 ? dot(P - a.cam.pos, a.cam.fwd)
+                                                                                   : __int_as_float(0x7f800000));
         float w = w_near(c), wf = 1.f - w, ac = fabsf(c);
         SwL = SwL + w * L;
         SfL = SfL + wf * L;
@@ -185,8 +210,8 @@ __global__ void __launch_bounds__(128, HDOF_TRACE_MINB) k_trace(TraceArgs a) {
 using namespace hdof;
 
 extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
-                          const uint8_t* spp, float* rt, uint32_t* stats, void* workspace, size_t workspace_bytes,
-                          void* stream) {
+                          const uint8_t* spp, float* rt, uint32_t* stats, float* rec, uint32_t* ray_off,
+                          void* workspace, size_t workspace_bytes, void* stream) {
     clear_error();
     HDOF_CHECK_ARG(b, "hdof_trace: bvh is NULL");
     int rc;
@@ -194,6 +219,7 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
         (rc = check_params(p, "hdof_trace")))
         return rc;
     HDOF_CHECK_ARG(spp && rt, "hdof_trace: spp and rt are required");
+    HDOF_CHECK_ARG(!rec == !ray_off, "hdof_trace: rec and ray_off go together");
     const int W = cam->width, H = cam->height;
     WsLayout L = ws_layout(W, H, p);
     HDOF_CHECK_ARG(workspace && workspace_bytes >= L.trace_counts + L.trace_queue,
@@ -204,12 +230,13 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
     const int ntx = (W + TB - 1) / TB, nty = (H + TB - 1) / TB, ntiles = ntx * nty;
     unsigned* counts = static_cast<unsigned*>(workspace);            // [2 * ntiles]
     unsigned* offsets = counts + 2 * ntiles;                        // [ntiles]
-    unsigned* totals = offsets + ntiles;                            // [4]
+    unsigned* roffsets = offsets + ntiles;                          // [ntiles]
+    unsigned* totals = roffsets + ntiles;                           // [4]
     unsigned* queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) + L.trace_counts);
     dim3 tg(ntx, nty);
     k_count<<<tg, 256, 0, s>>>(spp, W, H, ntx, counts);
-    k_scan<<<1, 1024, 0, s>>>(counts, ntiles, offsets, totals, stats);
-    k_scatter<<<tg, 256, 0, s>>>(spp, W, H, ntx, offsets, queue);
+    k_scan<<<1, 1024, 0, s>>>(counts, ntiles, offsets, roffsets, totals, stats);
+    k_scatter<<<tg, 256, 0, s>>>(spp, W, H, ntx, offsets, roffsets, queue, ray_off);
     HDOF_LAUNCHED("hdof_trace: compaction");
 
     TraceArgs a;
@@ -227,6 +254,8 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
     a.queue = queue;
     a.totals = totals;
     a.rt = reinterpret_cast<float4*>(rt);
+    a.rec = reinterpret_cast<float4*>(rec);
+    a.ray_off = ray_off;
     static int occ[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);

@@ -62,6 +62,11 @@ class hdof_history(C.Structure):
                 ("hlen", C.c_void_p)]
 
 
+class hdof_post_state(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("rt", "crt", "hacc", "mom", "hlen", "crec", "sp_aux", "pp", "pp_aux",
+                                          "out")]
+
+
 class hdof_bvh_stats(C.Structure):
     _fields_ = [("n_tris", C.c_int32), ("n_nodes", C.c_int32), ("depth", C.c_int32),
                 ("n_big", C.c_int32), ("device_bytes", C.c_int64)]
@@ -93,13 +98,18 @@ def load():
         "hdof_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
         "hdof_mask": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp, sz, vp], C.c_int),
         "hdof_mask_noalloc": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp], C.c_int),
-        "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, sz, vp], C.c_int),
+        "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
         "hdof_postfilter": ([P(hdof_gbuf), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, sz, vp],
                             C.c_int),
         "hdof_reconstruct": ([vp, P(hdof_gbuf), vp, P(hdof_camera), P(hdof_camera), P(hdof_lens),
                               P(hdof_params), P(hdof_history), P(hdof_history), vp, vp, vp, vp], C.c_int),
         "hdof_composite": ([P(hdof_gbuf), vp, vp, vp, vp, vp, P(hdof_camera), P(hdof_lens), P(hdof_params),
                             vp, vp], C.c_int),
+        "hdof_post_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
+        "hdof_post_forward": ([P(hdof_gbuf), vp, vp, vp, vp, P(hdof_camera), P(hdof_lens), P(hdof_params),
+                               P(hdof_post_state), vp, sz, vp], C.c_int),
+        "hdof_post_backward": ([P(hdof_gbuf), vp, vp, vp, vp, P(hdof_camera), P(hdof_lens), P(hdof_params),
+                                P(hdof_post_state), vp, vp, vp, vp, sz, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -113,7 +123,8 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["hdof_version", "hdof_last_error", "hdof_sync", "hdof_default_params", "hdof_build_bvh",
             "hdof_bvh_destroy", "hdof_bvh_info", "hdof_closest_hits", "hdof_gbuffer", "hdof_workspace_bytes",
-            "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_postfilter", "hdof_reconstruct", "hdof_composite"]
+            "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_postfilter", "hdof_reconstruct", "hdof_composite",
+            "hdof_post_workspace_bytes", "hdof_post_forward", "hdof_post_backward"]
 
 
 def _check(rc):
@@ -298,9 +309,11 @@ def hdof_mask_noalloc(gbuf: GBuffer, prev_hist, p, edge, spp, stream=None):
                                     _stream(stream)))
 
 
-def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None):
+def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None, rec=None, ray_off=None):
+    """rec (float [n_rays][4]) and ray_off (int32 [H][W]) optionally receive
+    the per-ray hit records (L rgb, z) and each traced pixel's first ray."""
     _check(load().hdof_trace(bvh.handle, C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)),
-                             _ptr(spp), _ptr(rt), _ptr(stats), _ptr(workspace),
+                             _ptr(spp), _ptr(rt), _ptr(stats), _ptr(rec), _ptr(ray_off), _ptr(workspace),
                              workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
@@ -372,3 +385,98 @@ class Renderer:
         hdof_composite(self.g, self.spp, self.pp, self.crt, self.crec, self.hacc, cam, lns, p, self.out, stream)
         self.cur = 1 - self.cur
         return self.out
+
+
+# ------------------------------------------------ differentiable post-path --
+
+class PostState:
+    """Buffers written by hdof_post_forward and read by hdof_post_backward."""
+
+    def __init__(self, width, height, device="cuda"):
+        f = lambda *sh: torch.empty((height, width) + sh, dtype=torch.float32, device=device)  # noqa: E731
+        self.rt, self.crt, self.hacc, self.mom = f(12), f(4), f(), f(2)
+        self.hlen = torch.empty((height, width), dtype=torch.uint8, device=device)
+        self.crec, self.sp_aux, self.pp, self.pp_aux, self.out = f(4), f(4), f(4), f(8), f(4)
+
+    def struct(self) -> hdof_post_state:
+        return hdof_post_state(*(_ptr(getattr(self, n)) for n, _ in hdof_post_state._fields_))
+
+
+def hdof_post_workspace_bytes(width, height, p=None) -> int:
+    return int(load().hdof_post_workspace_bytes(int(width), int(height), C.byref(params(p))))
+
+
+def hdof_post_forward(gbuf: GBuffer, spp, rec, ray_off, hist_samples, cam, lns, p, st: PostState, workspace,
+                      stream=None):
+    _check(load().hdof_post_forward(C.byref(gbuf.struct()), _ptr(spp), _ptr(rec), _ptr(ray_off), _ptr(hist_samples),
+                                    C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)),
+                                    C.byref(st.struct()), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                    _stream(stream)))
+
+
+def hdof_post_backward(gbuf: GBuffer, spp, rec, ray_off, hist_samples, cam, lns, p, st: PostState, grad_out,
+                       grad_col, grad_lens, workspace, stream=None):
+    _check(load().hdof_post_backward(C.byref(gbuf.struct()), _ptr(spp), _ptr(rec), _ptr(ray_off),
+                                     _ptr(hist_samples), C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)),
+                                     C.byref(st.struct()), _ptr(grad_out), _ptr(grad_col), _ptr(grad_lens),
+                                     _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+class _Lens:
+    def __init__(self, zf, A, f):
+        self.focus_dist, self.aperture_radius, self.focal_length = zf, A, f
+
+
+class PostPath:
+    """Frozen inputs of the differentiable post-path (depth, mask, hit records,
+    history samples) and its buffers; ``HdofPost.apply(col, lens_params, path)``
+    is the differentiable call."""
+
+    def __init__(self, z, spp, rec, ray_off, hist_samples, cam, p, focal_length=0.05):
+        self.cam, self.p, self.focal = cam, p, focal_length
+        H, W = z.shape
+        self.nd = torch.zeros((H, W, 4), dtype=torch.float32, device=z.device)
+        self.nd[..., 2] = -1.0
+        self.nd[..., 3] = z
+        self.spp, self.rec, self.ray_off, self.hs = spp, rec, ray_off, hist_samples
+        self.st = PostState(W, H, z.device)
+        self.ws = torch.empty(hdof_post_workspace_bytes(W, H, p), dtype=torch.uint8, device=z.device)
+        self.col4 = torch.zeros((H, W, 4), dtype=torch.float32, device=z.device)
+
+    def forward(self, col, zf, A):
+        self.col4[..., :3] = col
+        g = GBuffer.from_tensors(self.nd, self.col4)
+        hdof_post_forward(g, self.spp, self.rec, self.ray_off, self.hs, self.cam, _Lens(zf, A, self.focal), self.p,
+                          self.st, self.ws)
+        return self.st.out[..., :3]
+
+    def backward(self, grad_out, zf, A):
+        H, W = self.spp.shape
+        g4 = torch.zeros((H, W, 4), dtype=torch.float32, device=grad_out.device)
+        g4[..., :3] = grad_out
+        gcol = torch.empty_like(g4)
+        glens = torch.empty(2, dtype=torch.float32, device=grad_out.device)
+        g = GBuffer.from_tensors(self.nd, self.col4)
+        hdof_post_backward(g, self.spp, self.rec, self.ray_off, self.hs, self.cam, _Lens(zf, A, self.focal), self.p,
+                           self.st, g4, gcol, glens, self.ws)
+        return gcol[..., :3], glens
+
+
+class HdofPost(torch.autograd.Function):
+    """out = post-path(col [H,W,3], lens_params [2] = (focus, aperture)) with
+    the hand-written adjoint of hdof_post_backward."""
+
+    @staticmethod
+    def forward(ctx, col, lens_params, path: PostPath):
+        zf, A = (float(x) for x in lens_params.detach().cpu().tolist())
+        out = path.forward(col.detach().contiguous(), zf, A).clone()
+        ctx.path, ctx.zf, ctx.A = path, zf, A
+        ctx.col = col.detach().contiguous()
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        path = ctx.path
+        path.forward(ctx.col, ctx.zf, ctx.A)  # the state buffers are shared: restore this call's
+        gcol, glens = path.backward(grad_out.contiguous().float(), ctx.zf, ctx.A)
+        return gcol, glens.to(grad_out.device), None

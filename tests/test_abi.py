@@ -52,7 +52,8 @@ def test_struct_layout_matches_header(H, tmp_path):
     gives the header's structs."""
     import subprocess
     recs = {"hdof_camera": H.hdof_camera, "hdof_lens": H.hdof_lens, "hdof_params": H.hdof_params,
-            "hdof_gbuf": H.hdof_gbuf, "hdof_history": H.hdof_history, "hdof_bvh_stats": H.hdof_bvh_stats}
+            "hdof_gbuf": H.hdof_gbuf, "hdof_history": H.hdof_history, "hdof_bvh_stats": H.hdof_bvh_stats,
+            "hdof_post_state": H.hdof_post_state}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hdof.h"', "int main(void) {"]
     for name, rec in recs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
@@ -90,7 +91,7 @@ def test_invalid_arguments_rejected_before_launch(H):
     assert b"image size" in buf.value
     p_bad = H.params(hi.Params(spp_max=300))
     assert lib.hdof_trace(C.c_void_p(1), C.byref(cam), C.byref(H.lens(hi.Lens())), C.byref(p_bad), None, None, None,
-                          None, 0, None) == -1
+                          None, None, None, 0, None) == -1
     lib.hdof_last_error(buf, 256)
     assert b"spp_max" in buf.value
 

@@ -92,3 +92,39 @@ def test_mixed_room_sequence_error_report(orc):
         assert report[k]["out_mixed"][1] <= 4 * BF16_REL, report[k]
         assert report[k]["out_f32"][1] <= 1e-3, report[k]
     print("mixed-precision error report:", report)
+
+
+def test_mixed_4k_crop_error_report(orc):
+    """The 4K mixed-precision workload (5.25M triangles, 3840x2160): frame 0
+    in FP32 and in FP16/BF16 storage against the FP64 oracle on the central
+    512x512 crop (post-filter and composite on 8192 sampled crop pixels)."""
+    W, Hh = 3840, 2160
+    scene = hi.room4k_scene(seed=0, aspect=W / Hh)
+    cam = hi.room_camera(0, W, Hh)
+    lens = hi.room_lens()
+    p = hi.room_params(r_max=64.0)
+    bvh = bvh_of(scene)
+    r32 = H.Renderer(bvh, W, Hh, p)
+    rmx = H.Renderer(bvh, W, Hh, p, nd_dtype=torch.float16, col_dtype=torch.bfloat16)
+    r32.frame(cam, cam, lens, p)
+    rmx.frame(cam, cam, lens, p)
+    H.hdof_sync()
+    y0, x0 = (Hh - 512) // 2, (W - 512) // 2
+    crop = (slice(y0, y0 + 512), slice(x0, x0 + 512))
+    rng = np.random.default_rng(5)
+    cy, cx = rng.integers(0, 512, 8192) + y0, rng.integers(0, 512, 8192) + x0
+    pix = (cy * W + cx).astype(np.int32)
+    ref = orc.frame(orc.OScene(scene), cam, cam, lens, p, pp_pix=pix)
+    rep = {}
+    for name, r in (("f32", r32), ("mixed", rmx)):
+        spp = host(r.spp)
+        out = host(r.out).reshape(-1, 4)[pix][:, :3]
+        pp = host(r.pp).reshape(-1, 4)[pix]
+        rep[name] = {"spp_agree": float((spp[crop] == ref["mask"]["spp"][crop]).mean()),
+                     "z_rel": float(np.percentile(np.abs(host(r.g.nd)[crop][..., 3] - ref["g"]["nd"][crop][..., 3]) /
+                                                  ref["g"]["nd"][crop][..., 3], 99.9)),
+                     "pp": _err(pp, ref["pp"]), "out": _err(out, ref["out"][:, :3])}
+    print("4K crop error report:", rep)
+    assert rep["f32"]["spp_agree"] >= 0.999 and rep["f32"]["out"][1] <= 1e-3
+    assert rep["mixed"]["spp_agree"] >= 0.99 and rep["mixed"]["out"][1] <= 4 * BF16_REL
+    assert rep["mixed"]["z_rel"] <= F16_REL * 1.01
