@@ -484,3 +484,53 @@ def diff_config(width: int = 1024, height: int = 1024, seed: int = 0):
     start = Lens(1.0, 0.02, 0.05).f32()
     params = room_params(r_max=32.0, variance_on=1)
     return col, z, scene, cam, target, start, params
+
+
+# --------------------------------------------------------------------------
+# batched multi-view workload
+# --------------------------------------------------------------------------
+
+BATCH_RESOLUTIONS = ((256, 256), (640, 480), (1280, 720), (1920, 1080))
+BATCH_TRIS = (50_000, 150_000, 300_000, 500_000)
+
+
+@dataclass
+class BatchView:
+    """One view of the batched workload: which room, its size, pose and lens."""
+    room: int
+    width: int
+    height: int
+    pos: tuple
+    target: tuple
+    lens: Lens
+    params: Params
+
+    def camera(self, frame: int = 0, step: float = 0.01, seed: int = 10) -> Camera:
+        """Pose translated by frame*step along its right axis, jittered per frame."""
+        r, u, f = look_at(self.pos, self.target)
+        p = tuple(float(a) + frame * step * float(b) for a, b in zip(self.pos, r))
+        return Camera(pos=p, right=r, up=u, fwd=f, width=self.width, height=self.height,
+                      jitter=dyadic_jitter(seed + 1000 * (self.params.view + 1), frame)).f32()
+
+
+def batch_scenes(seeds=(10, 11, 12, 13), tris=BATCH_TRIS):
+    """Four rooms of 50k-500k triangles (room generator, seeds 10-13)."""
+    return [room_scene_target(s, t) for s, t in zip(seeds, tris)]
+
+
+def batch_views(n_views: int = 64, seed: int = 10, resolutions=BATCH_RESOLUTIONS, n_rooms: int = 4):
+    """Views drawn with one generator (seed 10): room uniform over the four,
+    resolution uniform over {256^2, 640x480, 1280x720, 1920x1080}, focus
+    U[0.5, 6], aperture radius U[0.01, 0.1], 1-16 spp by mask, camera at a
+    random point near the room's front looking at a random point 3-6 units in."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for v in range(n_views):
+        room = int(rng.integers(n_rooms))
+        w, h = resolutions[int(rng.integers(len(resolutions)))]
+        pos = (float(rng.uniform(-1.5, 1.5)), float(rng.uniform(-1.0, 1.0)), float(rng.uniform(-0.4, 0.0)))
+        target = (float(rng.uniform(-2.0, 2.0)), float(rng.uniform(-1.0, 1.0)), float(rng.uniform(3.0, 6.0)))
+        lens = Lens(float(rng.uniform(0.5, 6.0)), float(rng.uniform(0.01, 0.1)), ROOM_FOCAL).f32()
+        params = room_params(spp_max=16, view=v, seed=seed)
+        out.append(BatchView(room, w, h, pos, target, lens, params))
+    return out

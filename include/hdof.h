@@ -288,6 +288,84 @@ int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, con
                    const float* crec, const float* hacc, const hdof_camera* cam,
                    const hdof_lens* lens, const hdof_params* p, float* out, void* stream);
 
+/* ------------------------------------------------- batched multi-view -- */
+/* One view of a batch: its scene, cameras, lens, constants and buffers
+ * (every pointer as for the single-view calls; FP32 G-buffer planes, mv
+ * required).  hist_in is the previous frame's history (hlen = 0 everywhere
+ * for none), hist_out the one this frame writes.  workspace: at least
+ * hdof_workspace_bytes(width, height, &params) bytes, one per view.
+ * stats may be NULL. */
+typedef struct hdof_view {
+    const hdof_bvh* bvh;
+    hdof_camera cam, prev;
+    hdof_lens lens;
+    hdof_params params;
+    hdof_gbuf g;
+    uint8_t* edge;
+    uint8_t* spp;
+    float* rt;
+    uint32_t* stats;
+    float* pp;
+    float* crt;
+    float* hacc;
+    float* crec;
+    float* out;
+    hdof_history hist_in, hist_out;
+    void* workspace;
+    size_t workspace_bytes;
+} hdof_view;
+
+/* Launch shapes of the batched frame (chosen by an autotuner).
+ * trace_block: threads per block of the persistent trace (64, 128 or 256);
+ * trace_chunk: pixels each lane takes per queue fetch (1, 2 or 4). */
+typedef struct hdof_tuning {
+    int32_t trace_block;
+    int32_t trace_chunk;
+    int32_t reserved[2];
+} hdof_tuning;
+
+typedef struct hdof_batch hdof_batch;
+
+/* Prepares a batch: validates every view, builds each stage's per-view
+ * launch records and block tables and copies them to device memory the
+ * handle owns (synchronous).  The views' buffers must stay valid while the
+ * handle is used.  tuning may be NULL (defaults 128 / 1). */
+int hdof_batch_create(const hdof_view* views, int32_t n_views, const hdof_tuning* tuning, hdof_batch** out,
+                      void* stream);
+int hdof_batch_destroy(hdof_batch* batch);
+/* Rewrites the launch records for the next frame (cameras, lens, params,
+ * history ping-pong, even the BVH) from views[0..n_views), which must keep
+ * the count, sizes and mask tile the batch was created with.  The records
+ * are uploaded from a pinned host image with one asynchronous copy on
+ * stream, so a CUDA graph captured from hdof_batch_render stays valid and
+ * replays the new frame when launched after this call on the same stream.
+ * Renders enqueued on another stream must be ordered by the caller. */
+int hdof_batch_update(hdof_batch* batch, const hdof_view* views, int32_t n_views, void* stream);
+/* Bytes of the launch records each hdof_batch_update uploads (0 for NULL). */
+size_t hdof_batch_bytes(const hdof_batch* batch);
+/* Enqueues the frame of every view of the batch: one launch per stage over
+ * all views' blocks (G-buffer, mask, compaction, one persistent trace over
+ * the concatenated ray queues, post-filter, reconstruction, composite).
+ * Only kernel launches and device memsets: capturable into a CUDA graph.
+ * Each view's results equal those of the single-view calls bit for bit. */
+int hdof_batch_render(const hdof_batch* batch, void* stream);
+
+/* The batched frame's stages, in order; hdof_batch_render runs all of them. */
+enum {
+    HDOF_STAGE_GBUFFER = 0,     /* 1 launch */
+    HDOF_STAGE_MASK = 1,        /* tile clear, edge, spp: 3 launches */
+    HDOF_STAGE_COMPACT = 2,     /* count, scan, scatter: 3 launches */
+    HDOF_STAGE_TRACE = 3,       /* queue prefix, persistent trace: 2 launches */
+    HDOF_STAGE_POSTFILTER = 4,  /* prep, gather: 2 launches */
+    HDOF_STAGE_RECONSTRUCT = 5, /* temporal, spatial: 2 launches */
+    HDOF_STAGE_COMPOSITE = 6,   /* 1 launch */
+    HDOF_BATCH_STAGES = 7
+};
+/* Enqueues stages first..last (inclusive) of the batched frame, e.g. to time
+ * them one by one or to interleave the caller's own work; running 0..6 in
+ * order, in one call or several, is hdof_batch_render. */
+int hdof_batch_render_range(const hdof_batch* batch, int32_t first, int32_t last, void* stream);
+
 /* ------------------------------------------- differentiable post-path -- */
 /* Buffers the forward writes and the backward reads (device, FP32 unless
  * noted; [H][W] planes): rt [12] trace output replayed at this lens; crt [4],

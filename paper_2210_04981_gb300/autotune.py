@@ -1,0 +1,94 @@
+"""Launch-shape autotuner of the batched multi-view frame.
+
+The batched frame has one free launch shape that changes its speed but not
+its results: the persistent trace's block size (64, 128 or 256 threads) and
+how many queue entries each lane takes per atomic fetch (1, 2 or 4).  Every
+candidate renders bit-identical images, so the tuner only times them: it
+builds one batch handle per candidate over the caller's own buffers, times
+whole batched frames with CUDA events on the current stream (warm-up first,
+median of ``reps``), and keeps the fastest.  Results are cached in a JSON file
+keyed by the GPU and the workload's shape (view sizes, scene sizes, sample
+budgets), so a workload is timed once per machine.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import torch
+
+from . import hdof as H
+
+CANDIDATES = tuple((b, c) for b in (64, 128, 256) for c in (1, 2, 4))
+
+
+def cache_path() -> str:
+    return os.environ.get("HDOF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "hdof_tuning.json"))
+
+
+def signature(batch: "H.Batch") -> str:
+    """GPU name + every view's (width, height, triangles, spp_max, r_max)."""
+    shape = [torch.cuda.get_device_name()]
+    for r, p in zip(batch.views, batch.params):
+        shape.append((r.W, r.H, int(r.bvh.stats().n_tris), int(p.spp_max), float(p.r_max)))
+    return hashlib.sha1(json.dumps(shape).encode()).hexdigest()[:16]
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: dict):
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def time_shape(batch: "H.Batch", frame_args, block: int, chunk: int, reps: int = 5, warmup: int = 2) -> float:
+    """Median milliseconds of one batched frame with the given trace shape."""
+    recs = batch.records(*frame_args)
+    h = H.hdof_batch_create(recs, H.tuning(block, chunk))
+    try:
+        for _ in range(warmup):
+            H.hdof_batch_render(h)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record()
+            H.hdof_batch_render(h)
+            b.record()
+        H.hdof_sync()
+        ts = sorted(a.elapsed_time(b) for a, b in ev)
+        return ts[len(ts) // 2]
+    finally:
+        H.hdof_batch_destroy(h)
+
+
+def tune(batch: "H.Batch", frame_args, candidates=CANDIDATES, reps: int = 5, use_cache: bool = True):
+    """Pick the fastest (trace_block, trace_chunk) for the batch's workload.
+
+    ``frame_args`` = (cams, prevs, lenses, params) of a representative frame.
+    Returns (hdof_tuning, {shape: ms}); the timings are empty on a cache hit.
+    """
+    key = signature(batch)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        b, c = cache[key]["best"]
+        return H.tuning(b, c), {}
+    times = {}
+    for b, c in candidates:
+        times[(b, c)] = time_shape(batch, frame_args, b, c, reps)
+    best = min(times, key=times.get)
+    if use_cache:
+        cache = _load()
+        cache[key] = {"best": list(best), "ms": {f"{b}x{c}": t for (b, c), t in times.items()}}
+        _store(cache)
+    return H.tuning(*best), times

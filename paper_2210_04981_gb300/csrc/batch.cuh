@@ -1,0 +1,97 @@
+// Multi-view launches: one grid over the blocks of every view of a batch.
+// prefix[v] is the first block of view v (prefix[n] = total); gx[v] is the
+// view's grid width in blocks.  A block finds its view by binary search and
+// runs the same per-block body as a single-view launch, so every pixel is
+// computed by the same code either way.
+//
+// Each stage file exports three host hooks for the batched frame:
+//   <stage>_args_size()              bytes of one view's launch record
+//   <stage>_fill(view, ws, st, dst, &gx, &gy)
+//                                    writes the view's record at dst and
+//                                    its grid (gx x gy blocks)
+//   <stage>_launch_batch(args, grid, blocks, stream)
+//                                    one launch over all views' blocks
+#pragma once
+
+#include "internal.h"
+
+namespace hdof {
+
+struct BatchGrid {
+    const int* prefix;
+    const int* gx;
+    int n;
+    __device__ __forceinline__ void locate(int b, int& v, int& bx, int& by) const {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&prefix[mid]) <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        v = lo;
+        int local = b - __ldg(&prefix[lo]), w = __ldg(&gx[lo]);
+        bx = local % w;
+        by = local / w;
+    }
+};
+
+// one view's workspace carved as the single-view calls carve it (the stages
+// run one after another, so their regions overlap as they do there)
+struct ViewWs {
+    uint8_t* tiles;      // mask tile flags
+    unsigned* counts;    // [2 * ntiles] traced pixels, rays per 16x16 tile
+    unsigned* offsets;   // [ntiles]
+    unsigned* roffsets;  // [ntiles]
+    unsigned* totals;    // [4] queue length, head
+    unsigned* queue;     // [W * H]
+    float4* prep;        // post-filter per-pixel record
+    float* tmax;         // post-filter per-tile radius
+};
+
+inline ViewWs view_ws(const hdof_view& v) {
+    WsLayout L = ws_layout(v.cam.width, v.cam.height, &v.params);
+    const int ntx = (v.cam.width + 15) / 16, nty = (v.cam.height + 15) / 16, ntiles = ntx * nty;
+    char* base = static_cast<char*>(v.workspace);
+    ViewWs w;
+    w.tiles = reinterpret_cast<uint8_t*>(base);
+    w.counts = reinterpret_cast<unsigned*>(base);
+    w.offsets = w.counts + 2 * ntiles;
+    w.roffsets = w.offsets + ntiles;
+    w.totals = w.roffsets + ntiles;
+    w.queue = reinterpret_cast<unsigned*>(base + L.trace_counts);
+    w.prep = reinterpret_cast<float4*>(base);
+    w.tmax = reinterpret_cast<float*>(base + L.pf_prep);
+    return w;
+}
+
+#define HDOF_BATCH_STAGE(name)                                                                             \
+    size_t name##_args_size();                                                                             \
+    void name##_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst, int* gx, int* gy);      \
+    void name##_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s);
+
+HDOF_BATCH_STAGE(gbuffer)
+HDOF_BATCH_STAGE(mask_edge)
+HDOF_BATCH_STAGE(mask_spp)
+HDOF_BATCH_STAGE(count)
+HDOF_BATCH_STAGE(scatter)
+HDOF_BATCH_STAGE(pf_prep)
+HDOF_BATCH_STAGE(pf_gather)
+HDOF_BATCH_STAGE(temporal)
+HDOF_BATCH_STAGE(spatial)
+HDOF_BATCH_STAGE(composite)
+#undef HDOF_BATCH_STAGE
+
+// stages that are not one block grid per view
+size_t scan_args_size();
+void scan_fill(const hdof_view& v, const ViewWs& w, void* dst);
+void scan_launch_batch(const void* args, int n, cudaStream_t s);  // one block per view
+size_t trace_args_size();
+void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst);
+// resident grid of the persistent batched trace for a block size
+int trace_batch_grid(int block, int* blocks);
+// queue prefix over the views (gq[0..n], gq[n + 1] = head) then the
+// persistent trace over the concatenated queues
+int trace_launch_batch(const void* scan_args, const void* trace_args, int n, unsigned* gq, int block, int chunk,
+                       int blocks, cudaStream_t s);
+
+}  // namespace hdof

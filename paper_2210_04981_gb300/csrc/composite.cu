@@ -3,18 +3,41 @@
 // the ray-traced colour and far geometry blends ray-traced and post-process
 // colour by the hit ratio, only below a threshold hit ratio so the edges of
 // the ray mask do not show.  One thread per pixel, float4 planes.
+#include "batch.cuh"
 #include "internal.h"
 
 namespace hdof {
 namespace {
 
 template <class ND, class COL>
-__global__ void __launch_bounds__(256) k_composite(const ND* __restrict__ nd, const COL* __restrict__ col,
-                                                   const uint8_t* __restrict__ spp, const float4* __restrict__ pp,
-                                                   const float4* __restrict__ crt, const float4* __restrict__ crec,
-                                                   const float* __restrict__ hacc, int W, int H, Coc coc,
-                                                   float h_tau, float4* __restrict__ out) {
-    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+struct CompositeArgs {
+    const ND* nd;
+    const COL* col;
+    const uint8_t* spp;
+    const float4* pp;
+    const float4* crt;
+    const float4* crec;
+    const float* hacc;
+    int W, H;
+    Coc coc;
+    float h_tau;
+    float4* out;
+};
+
+template <class ND, class COL>
+__device__ __forceinline__ void composite_body(const CompositeArgs<ND, COL>& a, int bx, int by) {
+    const ND* __restrict__ nd = a.nd;
+    const COL* __restrict__ col = a.col;
+    const uint8_t* __restrict__ spp = a.spp;
+    const float4* __restrict__ pp = a.pp;
+    const float4* __restrict__ crt = a.crt;
+    const float4* __restrict__ crec = a.crec;
+    const float* __restrict__ hacc = a.hacc;
+    const int W = a.W, H = a.H;
+    const Coc coc = a.coc;
+    const float h_tau = a.h_tau;
+    float4* __restrict__ out = a.out;
+    int i = bx * 32 + (threadIdx.x & 31), j = by * 8 + (threadIdx.x >> 5);
     if (i >= W || j >= H) return;
     size_t q = (size_t)j * W + i;
     float c = coc(ldz(nd + q));
@@ -40,13 +63,25 @@ __global__ void __launch_bounds__(256) k_composite(const ND* __restrict__ nd, co
 }
 
 template <class ND, class COL>
+__global__ void __launch_bounds__(256) k_composite(CompositeArgs<ND, COL> a) {
+    composite_body(a, blockIdx.x, blockIdx.y);
+}
+
+using CompositeF32 = CompositeArgs<float4, float4>;
+__global__ void __launch_bounds__(256) k_composite_batch(const CompositeF32* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    composite_body(a[v], bx, by);
+}
+
+template <class ND, class COL>
 void launch(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
             const float* hacc, Coc coc, float h_tau, float* out, cudaStream_t s) {
     dim3 g((in->width + 31) / 32, (in->height + 7) / 8);
-    k_composite<ND, COL><<<g, 256, 0, s>>>(static_cast<const ND*>(in->nd), static_cast<const COL*>(in->col), spp,
-                                            reinterpret_cast<const float4*>(pp), reinterpret_cast<const float4*>(crt),
-                                            reinterpret_cast<const float4*>(crec), hacc, in->width, in->height, coc,
-                                            h_tau, reinterpret_cast<float4*>(out));
+    k_composite<ND, COL><<<g, 256, 0, s>>>(CompositeArgs<ND, COL>{
+        static_cast<const ND*>(in->nd), static_cast<const COL*>(in->col), spp, reinterpret_cast<const float4*>(pp),
+        reinterpret_cast<const float4*>(crt), reinterpret_cast<const float4*>(crec), hacc, in->width, in->height, coc,
+        h_tau, reinterpret_cast<float4*>(out)});
 }
 
 }  // namespace
@@ -82,3 +117,28 @@ extern "C" int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const flo
     return launch_composite(in, spp, pp, crt, crec, hacc, make_coc(*lens, cam->height, cam->tan_half_fovy), p->h_tau,
                             out, as_stream(stream));
 }
+
+namespace hdof {
+
+size_t composite_args_size() { return sizeof(CompositeF32); }
+void composite_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int* gx, int* gy) {
+    *reinterpret_cast<CompositeF32*>(dst) = CompositeF32{static_cast<const float4*>(v.g.nd),
+                                                         static_cast<const float4*>(v.g.col),
+                                                         v.spp,
+                                                         reinterpret_cast<const float4*>(v.pp),
+                                                         reinterpret_cast<const float4*>(v.crt),
+                                                         reinterpret_cast<const float4*>(v.crec),
+                                                         v.hacc,
+                                                         v.cam.width,
+                                                         v.cam.height,
+                                                         make_coc(v.lens, v.cam.height, v.cam.tan_half_fovy),
+                                                         v.params.h_tau,
+                                                         reinterpret_cast<float4*>(v.out)};
+    *gx = (v.cam.width + 31) / 32;
+    *gy = (v.cam.height + 7) / 8;
+}
+void composite_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_composite_batch<<<blocks, 256, 0, s>>>(static_cast<const CompositeF32*>(args), g);
+}
+
+}  // namespace hdof

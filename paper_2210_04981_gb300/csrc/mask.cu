@@ -13,6 +13,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "batch.cuh"
 #include "internal.h"
 
 namespace hdof {
@@ -28,13 +29,28 @@ struct GaussW {
 };
 
 template <class ND>
-__global__ void __launch_bounds__(256) k_mask_edge(const ND* __restrict__ nd, int W, int H, GaussW g, float tau,
-                                                   int tile, int ntx, uint8_t* __restrict__ edge,
-                                                   uint8_t* __restrict__ tiles) {
+struct EdgeArgs {
+    const ND* nd;
+    int W, H;
+    GaussW g;
+    float tau;
+    int tile, ntx;
+    uint8_t* edge;
+    uint8_t* tiles;
+};
+
+template <class ND>
+__device__ __forceinline__ void mask_edge_body(const EdgeArgs<ND>& ar, int bx, int by) {
     __shared__ float4 src[SRC][SRC];
     __shared__ float4 row[SRC][FIL];
     __shared__ float4 fil[FIL][FIL];
-    const int x0 = blockIdx.x * B, y0 = blockIdx.y * B;
+    const ND* __restrict__ nd = ar.nd;
+    const int W = ar.W, H = ar.H, tile = ar.tile, ntx = ar.ntx;
+    const GaussW g = ar.g;
+    const float tau = ar.tau;
+    uint8_t* __restrict__ edge = ar.edge;
+    uint8_t* __restrict__ tiles = ar.tiles;
+    const int x0 = bx * B, y0 = by * B;
     const int tid = threadIdx.x;
     // stage nd with clamp-to-edge (the Gaussian's border rule)
     for (int k = tid; k < SRC * SRC; k += 256) {
@@ -108,12 +124,34 @@ __global__ void __launch_bounds__(256) k_mask_edge(const ND* __restrict__ nd, in
     if (bit) tiles[(j / tile) * ntx + i / tile] = 1;
 }
 
-__global__ void __launch_bounds__(256) k_mask_spp(int W, int H, int tile, int ntx, int nty, int dil,
-                                                  const uint8_t* __restrict__ tiles, int variance_on,
-                                                  const float2* __restrict__ mv, const float2* __restrict__ hmom,
-                                                  const uint8_t* __restrict__ hhlen, int spp_max, float var_tau,
-                                                  float var_scale, int hlen_young, uint8_t* __restrict__ spp) {
-    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+template <class ND>
+__global__ void __launch_bounds__(256) k_mask_edge(EdgeArgs<ND> a) {
+    mask_edge_body(a, blockIdx.x, blockIdx.y);
+}
+
+struct SppArgs {
+    int W, H, tile, ntx, nty, dil;
+    const uint8_t* tiles;
+    int variance_on;
+    const float2* mv;
+    const float2* hmom;
+    const uint8_t* hhlen;
+    int spp_max;
+    float var_tau, var_scale;
+    int hlen_young;
+    uint8_t* spp;
+};
+
+__device__ __forceinline__ void mask_spp_body(const SppArgs& ar, int bx, int by) {
+    const int W = ar.W, H = ar.H, tile = ar.tile, ntx = ar.ntx, nty = ar.nty, dil = ar.dil;
+    const uint8_t* __restrict__ tiles = ar.tiles;
+    const int variance_on = ar.variance_on, spp_max = ar.spp_max, hlen_young = ar.hlen_young;
+    const float2* __restrict__ mv = ar.mv;
+    const float2* __restrict__ hmom = ar.hmom;
+    const uint8_t* __restrict__ hhlen = ar.hhlen;
+    const float var_tau = ar.var_tau, var_scale = ar.var_scale;
+    uint8_t* __restrict__ spp = ar.spp;
+    int i = bx * 32 + (threadIdx.x & 31), j = by * 8 + (threadIdx.x >> 5);
     if (i >= W || j >= H) return;
     size_t q = (size_t)j * W + i;
     int tx = i / tile, ty = j / tile;
@@ -152,6 +190,84 @@ __global__ void __launch_bounds__(256) k_mask_spp(int W, int H, int tile, int nt
     spp[q] = (uint8_t)s;
 }
 
+__global__ void __launch_bounds__(256) k_mask_spp(SppArgs a) { mask_spp_body(a, blockIdx.x, blockIdx.y); }
+
+GaussW gauss_weights(float sigma) {
+    GaussW g;
+    double w[5], sum = 0.0;
+    for (int k = -2; k <= 2; ++k) {
+        w[k + 2] = std::exp(-(double)(k * k) / (2.0 * (double)sigma * (double)sigma));
+        sum += w[k + 2];
+    }
+    for (int k = 0; k < 5; ++k) g.w[k] = (float)(w[k] / sum);
+    return g;
+}
+
+template <class ND>
+EdgeArgs<ND> edge_args(const hdof_gbuf* in, const hdof_params* p, uint8_t* edge, uint8_t* tiles) {
+    EdgeArgs<ND> a;
+    a.nd = static_cast<const ND*>(in->nd);
+    a.W = in->width;
+    a.H = in->height;
+    a.g = gauss_weights(p->gauss_sigma);
+    a.tau = p->edge_tau;
+    a.tile = p->tile;
+    a.ntx = (in->width + p->tile - 1) / p->tile;
+    a.edge = edge;
+    a.tiles = tiles;
+    return a;
+}
+
+SppArgs spp_args(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p, const uint8_t* tiles,
+                 uint8_t* spp) {
+    bool var = p->variance_on && prev_hist;
+    SppArgs a;
+    a.W = in->width;
+    a.H = in->height;
+    a.tile = p->tile;
+    a.ntx = (in->width + p->tile - 1) / p->tile;
+    a.nty = (in->height + p->tile - 1) / p->tile;
+    a.dil = p->dilate;
+    a.tiles = tiles;
+    a.variance_on = var ? 1 : 0;
+    a.mv = reinterpret_cast<const float2*>(in->mv);
+    a.hmom = var ? reinterpret_cast<const float2*>(prev_hist->mom) : nullptr;
+    a.hhlen = var ? prev_hist->hlen : nullptr;
+    a.spp_max = p->spp_max;
+    a.var_tau = p->var_tau;
+    a.var_scale = p->var_scale;
+    a.hlen_young = p->hlen_young;
+    a.spp = spp;
+    return a;
+}
+
+// launches of both kernels for one view (tiles already cleared)
+int launch_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p, uint8_t* edge, uint8_t* spp,
+                uint8_t* tiles, cudaStream_t s) {
+    const int W = in->width, H = in->height;
+    dim3 grid((W + B - 1) / B, (H + B - 1) / B);
+    if (in->dtype_nd == HDOF_F32)
+        k_mask_edge<float4><<<grid, 256, 0, s>>>(edge_args<float4>(in, p, edge, tiles));
+    else
+        k_mask_edge<half4s><<<grid, 256, 0, s>>>(edge_args<half4s>(in, p, edge, tiles));
+    HDOF_LAUNCHED("mask: edge");
+    dim3 g2((W + 31) / 32, (H + 7) / 8);
+    k_mask_spp<<<g2, 256, 0, s>>>(spp_args(in, prev_hist, p, tiles, spp));
+    HDOF_LAUNCHED("mask: spp");
+    return HDOF_OK;
+}
+
+__global__ void __launch_bounds__(256) k_mask_edge_batch(const EdgeArgs<float4>* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    mask_edge_body(a[v], bx, by);
+}
+__global__ void __launch_bounds__(256) k_mask_spp_batch(const SppArgs* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    mask_spp_body(a[v], bx, by);
+}
+
 }  // namespace
 }  // namespace hdof
 
@@ -174,29 +290,7 @@ extern "C" int hdof_mask(const hdof_gbuf* in, const hdof_history* prev_hist, con
     const int T = p->tile, ntx = (W + T - 1) / T, nty = (H + T - 1) / T;
     uint8_t* tiles = static_cast<uint8_t*>(workspace);
     HDOF_CUDA(cudaMemsetAsync(tiles, 0, (size_t)ntx * nty, s), "hdof_mask: clear tiles");
-    GaussW g;
-    double w[5], sum = 0.0;
-    for (int k = -2; k <= 2; ++k) {
-        w[k + 2] = std::exp(-(double)(k * k) / (2.0 * (double)p->gauss_sigma * (double)p->gauss_sigma));
-        sum += w[k + 2];
-    }
-    for (int k = 0; k < 5; ++k) g.w[k] = (float)(w[k] / sum);
-    dim3 grid((W + B - 1) / B, (H + B - 1) / B);
-    if (in->dtype_nd == HDOF_F32)
-        k_mask_edge<float4><<<grid, 256, 0, s>>>(static_cast<const float4*>(in->nd), W, H, g, p->edge_tau, T, ntx,
-                                                 edge, tiles);
-    else
-        k_mask_edge<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, g, p->edge_tau, T, ntx,
-                                                 edge, tiles);
-    HDOF_LAUNCHED("hdof_mask: edge");
-    dim3 g2((W + 31) / 32, (H + 7) / 8);
-    k_mask_spp<<<g2, 256, 0, s>>>(W, H, T, ntx, nty, p->dilate, tiles, var ? 1 : 0,
-                                  reinterpret_cast<const float2*>(in->mv),
-                                  var ? reinterpret_cast<const float2*>(prev_hist->mom) : nullptr,
-                                  var ? prev_hist->hlen : nullptr, p->spp_max, p->var_tau, p->var_scale,
-                                  p->hlen_young, spp);
-    HDOF_LAUNCHED("hdof_mask: spp");
-    return HDOF_OK;
+    return launch_mask(in, prev_hist, p, edge, spp, tiles, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -260,27 +354,29 @@ extern "C" int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_h
     cudaStream_t s = as_stream(stream);
     // the array keeps the previous call's flags: clear the tiles this call uses
     HDOF_CUDA(cudaMemsetAsync(tiles, 0, (size_t)ntx * nty, s), "hdof_mask_noalloc: clear tiles");
-    GaussW g;
-    double w[5], sum = 0.0;
-    for (int k = -2; k <= 2; ++k) {
-        w[k + 2] = std::exp(-(double)(k * k) / (2.0 * (double)p->gauss_sigma * (double)p->gauss_sigma));
-        sum += w[k + 2];
-    }
-    for (int k = 0; k < 5; ++k) g.w[k] = (float)(w[k] / sum);
-    dim3 grid((W + B - 1) / B, (H + B - 1) / B);
-    if (in->dtype_nd == HDOF_F32)
-        k_mask_edge<float4><<<grid, 256, 0, s>>>(static_cast<const float4*>(in->nd), W, H, g, p->edge_tau, T, ntx,
-                                                 edge, tiles);
-    else
-        k_mask_edge<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, g, p->edge_tau, T, ntx,
-                                                 edge, tiles);
-    HDOF_LAUNCHED("hdof_mask_noalloc: edge");
-    dim3 g2((W + 31) / 32, (H + 7) / 8);
-    k_mask_spp<<<g2, 256, 0, s>>>(W, H, T, ntx, nty, p->dilate, tiles, var ? 1 : 0,
-                                  reinterpret_cast<const float2*>(in->mv),
-                                  var ? reinterpret_cast<const float2*>(prev_hist->mom) : nullptr,
-                                  var ? prev_hist->hlen : nullptr, p->spp_max, p->var_tau, p->var_scale,
-                                  p->hlen_young, spp);
-    HDOF_LAUNCHED("hdof_mask_noalloc: spp");
-    return HDOF_OK;
+    return launch_mask(in, prev_hist, p, edge, spp, tiles, s);
 }
+
+namespace hdof {
+
+size_t mask_edge_args_size() { return sizeof(EdgeArgs<float4>); }
+void mask_edge_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
+    *reinterpret_cast<EdgeArgs<float4>*>(dst) = edge_args<float4>(&v.g, &v.params, v.edge, w.tiles);
+    *gx = (v.g.width + B - 1) / B;
+    *gy = (v.g.height + B - 1) / B;
+}
+void mask_edge_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_mask_edge_batch<<<blocks, 256, 0, s>>>(static_cast<const EdgeArgs<float4>*>(args), g);
+}
+
+size_t mask_spp_args_size() { return sizeof(SppArgs); }
+void mask_spp_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
+    *reinterpret_cast<SppArgs*>(dst) = spp_args(&v.g, &v.hist_in, &v.params, w.tiles, v.spp);
+    *gx = (v.g.width + 31) / 32;
+    *gy = (v.g.height + 7) / 8;
+}
+void mask_spp_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_mask_spp_batch<<<blocks, 256, 0, s>>>(static_cast<const SppArgs*>(args), g);
+}
+
+}  // namespace hdof

@@ -21,6 +21,7 @@
 #include <mutex>
 #include <vector>
 
+#include "batch.cuh"
 #include "internal.h"
 
 namespace hdof {
@@ -45,9 +46,25 @@ __device__ __forceinline__ float disk_area(float r) {
 }
 
 template <class ND>
-__global__ void __launch_bounds__(256) k_pf_prep(const ND* __restrict__ nd, int W, int H, Coc coc, float rmax,
-                                                 int ntx, float4* __restrict__ prep, float* __restrict__ tmax) {
-    int i = blockIdx.x * TP + (threadIdx.x & 15), j = blockIdx.y * TP + (threadIdx.x >> 4);
+struct PrepArgs {
+    const ND* nd;
+    int W, H;
+    Coc coc;
+    float rmax;
+    int ntx;
+    float4* prep;
+    float* tmax;
+};
+
+template <class ND>
+__device__ __forceinline__ void pf_prep_body(const PrepArgs<ND>& a, int bx, int by) {
+    const ND* __restrict__ nd = a.nd;
+    const int W = a.W, H = a.H, ntx = a.ntx;
+    const Coc coc = a.coc;
+    const float rmax = a.rmax;
+    float4* __restrict__ prep = a.prep;
+    float* __restrict__ tmax = a.tmax;
+    int i = bx * TP + (threadIdx.x & 15), j = by * TP + (threadIdx.x >> 4);
     float r = 0.f;
     if (i < W && j < H) {
         size_t q = (size_t)j * W + i;
@@ -65,9 +82,12 @@ __global__ void __launch_bounds__(256) k_pf_prep(const ND* __restrict__ nd, int 
     if (threadIdx.x == 0) {
         float m = red[0];
         for (int k = 1; k < 8; ++k) m = fmaxf(m, red[k]);
-        tmax[blockIdx.y * ntx + blockIdx.x] = m;
+        tmax[by * ntx + bx] = m;
     }
 }
+
+template <class ND>
+__global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND> a) { pf_prep_body(a, blockIdx.x, blockIdx.y); }
 
 // hardware approximate square root (MUFU, relative error ~2^-22): the tap
 // distance only enters the soft weight clamp(r + 1/2 - d, 0, 1)
@@ -121,14 +141,28 @@ __device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size
 // 128 threads per 16x16 tile; thread t gathers pixels (2 (t & 7), t >> 3) and
 // its right neighbour, so a warp covers a 16x4 pixel block.
 template <class COL>
-__global__ void __launch_bounds__(128, 6) k_pf_gather(const float4* __restrict__ prep, const COL* __restrict__ col,
-                                                   const float* __restrict__ tmax, int W, int H, int ntx, int nty,
-                                                   int kt, float kz_rel, float4* __restrict__ pp,
-                                                   float4* __restrict__ aux) {
+struct GatherArgs {
+    const float4* prep;
+    const COL* col;
+    const float* tmax;
+    int W, H, ntx, nty, kt;
+    float kz_rel;
+    float4* pp;
+    float4* aux;
+};
+
+template <class COL>
+__device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx, int ty) {
+    const float4* __restrict__ prep = ar.prep;
+    const COL* __restrict__ col = ar.col;
+    const float* __restrict__ tmax = ar.tmax;
+    const int W = ar.W, H = ar.H, ntx = ar.ntx, nty = ar.nty, kt = ar.kt;
+    const float kz_rel = ar.kz_rel;
+    float4* __restrict__ pp = ar.pp;
+    float4* __restrict__ aux = ar.aux;
     __shared__ int s_win;
     if (threadIdx.x == 0) s_win = 0;
     __syncthreads();
-    const int tx = blockIdx.x, ty = blockIdx.y;
     // window: largest r + 1/2 over tiles whose pixels can reach this tile
     for (int k = threadIdx.x; k < (2 * kt + 1) * (2 * kt + 1); k += blockDim.x) {
         int ox = k % (2 * kt + 1) - kt, oy = k / (2 * kt + 1) - kt;
@@ -173,6 +207,23 @@ __global__ void __launch_bounds__(128, 6) k_pf_gather(const float4* __restrict__
     pp[pq] = pf_finish(a0, col, pq, aux);
     if (two) pp[pq + 1] = pf_finish(a1, col, pq + 1, aux);
 }
+
+template <class COL>
+__global__ void __launch_bounds__(128, 6) k_pf_gather(GatherArgs<COL> a) { pf_gather_body(a, blockIdx.x, blockIdx.y); }
+
+__global__ void __launch_bounds__(256) k_pf_prep_batch(const PrepArgs<float4>* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    pf_prep_body(a[v], bx, by);
+}
+__global__ void __launch_bounds__(128, 6) k_pf_gather_batch(const GatherArgs<float4>* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    pf_gather_body(a[v], bx, by);
+}
+
+// tiles of reach around a tile: radii up to r_max (+1/2 soft edge) span this many
+int gather_tiles(float r_max) { return (int)std::ceil((r_max + 0.5f) / TP) + 1; }
 
 std::mutex g_area_mu;
 bool g_area_ready[64] = {false};
@@ -278,20 +329,24 @@ int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p,
     const int ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
     dim3 grid(ntx, nty);
     if (in->dtype_nd == HDOF_F32)
-        k_pf_prep<float4><<<grid, 256, 0, s>>>(static_cast<const float4*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
+        k_pf_prep<float4><<<grid, 256, 0, s>>>(
+            PrepArgs<float4>{static_cast<const float4*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax});
     else
-        k_pf_prep<half4s><<<grid, 256, 0, s>>>(static_cast<const half4s*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax);
+        k_pf_prep<half4s><<<grid, 256, 0, s>>>(
+            PrepArgs<half4s>{static_cast<const half4s*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax});
     HDOF_LAUNCHED("post-filter prep");
-    int kt = (int)std::ceil((p->r_max + 0.5f) / TP) + 1;
+    int kt = gather_tiles(p->r_max);
     // the taps are served from L1: prefer the largest L1 carve-out
     if (in->dtype_col == HDOF_F32) {
         cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        k_pf_gather<float4><<<grid, 128, 0, s>>>(prep, static_cast<const float4*>(in->col), tmax, W, H, ntx, nty, kt,
-                                                 p->kz_rel, reinterpret_cast<float4*>(pp), aux);
+        k_pf_gather<float4><<<grid, 128, 0, s>>>(GatherArgs<float4>{prep, static_cast<const float4*>(in->col), tmax,
+                                                                    W, H, ntx, nty, kt, p->kz_rel,
+                                                                    reinterpret_cast<float4*>(pp), aux});
     } else {
         cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        k_pf_gather<bf164s><<<grid, 128, 0, s>>>(prep, static_cast<const bf164s*>(in->col), tmax, W, H, ntx, nty, kt,
-                                                 p->kz_rel, reinterpret_cast<float4*>(pp), aux);
+        k_pf_gather<bf164s><<<grid, 128, 0, s>>>(GatherArgs<bf164s>{prep, static_cast<const bf164s*>(in->col), tmax,
+                                                                    W, H, ntx, nty, kt, p->kz_rel,
+                                                                    reinterpret_cast<float4*>(pp), aux});
     }
     HDOF_LAUNCHED("post-filter gather");
     return HDOF_OK;
@@ -315,3 +370,34 @@ extern "C" int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, cons
     return launch_postfilter(in, make_coc(*lens, in->height, cam->tan_half_fovy), p, pp, nullptr, workspace,
                              as_stream(stream));
 }
+
+namespace hdof {
+
+size_t pf_prep_args_size() { return sizeof(PrepArgs<float4>); }
+void pf_prep_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
+    const int W = v.cam.width, H = v.cam.height, ntx = (W + TP - 1) / TP;
+    *reinterpret_cast<PrepArgs<float4>*>(dst) =
+        PrepArgs<float4>{static_cast<const float4*>(v.g.nd), W, H, make_coc(v.lens, H, v.cam.tan_half_fovy),
+                         v.params.r_max, ntx, w.prep, w.tmax};
+    *gx = ntx;
+    *gy = (H + TP - 1) / TP;
+}
+void pf_prep_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_pf_prep_batch<<<blocks, 256, 0, s>>>(static_cast<const PrepArgs<float4>*>(args), g);
+}
+
+size_t pf_gather_args_size() { return sizeof(GatherArgs<float4>); }
+void pf_gather_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
+    const int W = v.cam.width, H = v.cam.height, ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
+    *reinterpret_cast<GatherArgs<float4>*>(dst) =
+        GatherArgs<float4>{w.prep, static_cast<const float4*>(v.g.col), w.tmax, W, H, ntx, nty,
+                           gather_tiles(v.params.r_max), v.params.kz_rel, reinterpret_cast<float4*>(v.pp), nullptr};
+    *gx = ntx;
+    *gy = nty;
+    cudaFuncSetAttribute(k_pf_gather_batch, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+}
+void pf_gather_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_pf_gather_batch<<<blocks, 128, 0, s>>>(static_cast<const GatherArgs<float4>*>(args), g);
+}
+
+}  // namespace hdof

@@ -16,6 +16,7 @@
 // by the pixel's CoC that rejects samples whose CoC radius is smaller than
 // their distance, blended by the clamped luminance variance so converged
 // regions are not over-blurred.
+#include "batch.cuh"
 #include "internal.h"
 
 namespace hdof {
@@ -94,8 +95,8 @@ __device__ __forceinline__ bool hist_sample(const TemporalArgs& a, float ux, flo
 }
 
 template <class ND>
-__global__ void __launch_bounds__(256) k_temporal(TemporalArgs a, const ND* __restrict__ nd) {
-    int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
+__device__ __forceinline__ void temporal_body(const TemporalArgs& a, const ND* __restrict__ nd, int bx, int by) {
+    int i = bx * 32 + (threadIdx.x & 31), j = by * 8 + (threadIdx.x >> 5);
     if (i >= a.W || j >= a.H) return;
     size_t q = (size_t)j * a.W + i;
     if (a.spp[q] == 0) {
@@ -175,12 +176,42 @@ __global__ void __launch_bounds__(256) k_temporal(TemporalArgs a, const ND* __re
     a.hacc[q] = Hacc;
 }
 
-__global__ void __launch_bounds__(256) k_spatial(const float4* __restrict__ crt, const float2* __restrict__ mom,
-                                                 const uint8_t* __restrict__ hlen, int W, int H, float r_s,
-                                                 float var_ref, float4* __restrict__ crec, float4* __restrict__ aux) {
+template <class ND>
+__global__ void __launch_bounds__(256) k_temporal(TemporalArgs a, const ND* __restrict__ nd) {
+    temporal_body(a, nd, blockIdx.x, blockIdx.y);
+}
+
+struct TemporalBatch {
+    TemporalArgs t;
+    const float4* nd;
+};
+__global__ void __launch_bounds__(256) k_temporal_batch(const TemporalBatch* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    temporal_body(a[v].t, a[v].nd, bx, by);
+}
+
+struct SpatialArgs {
+    const float4* crt;
+    const float2* mom;
+    const uint8_t* hlen;
+    int W, H;
+    float r_s, var_ref;
+    float4* crec;
+    float4* aux;
+};
+
+__device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int by) {
+    const float4* __restrict__ crt = a.crt;
+    const float2* __restrict__ mom = a.mom;
+    const uint8_t* __restrict__ hlen = a.hlen;
+    const int W = a.W, H = a.H;
+    const float r_s = a.r_s, var_ref = a.var_ref;
+    float4* __restrict__ crec = a.crec;
+    float4* __restrict__ aux = a.aux;
     // warp = 8x4 pixel block, block = 16x16 pixels
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7), j = blockIdx.y * 16 + (w >> 1) * 4 + (l >> 3);
+    const int i = bx * 16 + (w & 1) * 8 + (l & 7), j = by * 16 + (w >> 1) * 4 + (l >> 3);
     if (i >= W || j >= H) return;
     const size_t q = (size_t)j * W + i;
     const float4 cp = __ldg(&crt[q]);
@@ -213,12 +244,45 @@ __global__ void __launch_bounds__(256) k_spatial(const float4* __restrict__ crt,
                           0.f);
 }
 
+__global__ void __launch_bounds__(256) k_spatial(SpatialArgs a) { spatial_body(a, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(256) k_spatial_batch(const SpatialArgs* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    spatial_body(a[v], bx, by);
+}
+
+TemporalArgs temporal_args(const float* rt, const hdof_gbuf* in, const uint8_t* spp, const hdof_camera* cam,
+                           const hdof_camera* prev, const hdof_params* p, const hdof_history* hist_in,
+                           const hdof_history* hist_out, float* crt, float* hacc) {
+    TemporalArgs a;
+    a.cam = make_cam(*cam);
+    a.prev = make_cam(*prev);
+    a.W = cam->width;
+    a.H = cam->height;
+    a.alpha = p->ema_alpha;
+    a.moved = p->camera_moved;
+    a.rt = reinterpret_cast<const float4*>(rt);
+    a.spp = spp;
+    a.mv = reinterpret_cast<const float2*>(in->mv);
+    a.hn = reinterpret_cast<const float4*>(hist_in->near_acc);
+    a.hf = reinterpret_cast<const float4*>(hist_in->far_acc);
+    a.hm = reinterpret_cast<const float2*>(hist_in->mom);
+    a.hl = hist_in->hlen;
+    a.on = reinterpret_cast<float4*>(hist_out->near_acc);
+    a.of = reinterpret_cast<float4*>(hist_out->far_acc);
+    a.om = reinterpret_cast<float2*>(hist_out->mom);
+    a.ol = hist_out->hlen;
+    a.crt = reinterpret_cast<float4*>(crt);
+    a.hacc = hacc;
+    return a;
+}
+
 }  // namespace
 
 int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, int W, int H, float r_s, float var_ref,
                    float4* crec, float4* aux, cudaStream_t s) {
     dim3 g2((W + 15) / 16, (H + 15) / 16);
-    k_spatial<<<g2, 256, 0, s>>>(crt, mom, hlen, W, H, r_s, var_ref, crec, aux);
+    k_spatial<<<g2, 256, 0, s>>>(SpatialArgs{crt, mom, hlen, W, H, r_s, var_ref, crec, aux});
     HDOF_LAUNCHED("spatial reconstruction");
     return HDOF_OK;
 }
@@ -249,26 +313,7 @@ extern "C" int hdof_reconstruct(const float* rt, const hdof_gbuf* in, const uint
                    "hdof_reconstruct: size mismatch");
     cudaStream_t s = as_stream(stream);
     const int W = cam->width, H = cam->height;
-    TemporalArgs a;
-    a.cam = make_cam(*cam);
-    a.prev = make_cam(*prev);
-    a.W = W;
-    a.H = H;
-    a.alpha = p->ema_alpha;
-    a.moved = p->camera_moved;
-    a.rt = reinterpret_cast<const float4*>(rt);
-    a.spp = spp;
-    a.mv = reinterpret_cast<const float2*>(in->mv);
-    a.hn = reinterpret_cast<const float4*>(hist_in->near_acc);
-    a.hf = reinterpret_cast<const float4*>(hist_in->far_acc);
-    a.hm = reinterpret_cast<const float2*>(hist_in->mom);
-    a.hl = hist_in->hlen;
-    a.on = reinterpret_cast<float4*>(hist_out->near_acc);
-    a.of = reinterpret_cast<float4*>(hist_out->far_acc);
-    a.om = reinterpret_cast<float2*>(hist_out->mom);
-    a.ol = hist_out->hlen;
-    a.crt = reinterpret_cast<float4*>(crt);
-    a.hacc = hacc;
+    TemporalArgs a = temporal_args(rt, in, spp, cam, prev, p, hist_in, hist_out, crt, hacc);
     dim3 g1((W + 31) / 32, (H + 7) / 8);
     if (in->dtype_nd == HDOF_F32)
         k_temporal<float4><<<g1, 256, 0, s>>>(a, static_cast<const float4*>(in->nd));
@@ -278,3 +323,32 @@ extern "C" int hdof_reconstruct(const float* rt, const hdof_gbuf* in, const uint
     return launch_spatial(reinterpret_cast<const float4*>(crt), reinterpret_cast<const float2*>(hist_out->mom),
                           hist_out->hlen, W, H, p->r_s, p->var_ref, reinterpret_cast<float4*>(crec), nullptr, s);
 }
+
+namespace hdof {
+
+size_t temporal_args_size() { return sizeof(TemporalBatch); }
+void temporal_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int* gx, int* gy) {
+    TemporalBatch* b = reinterpret_cast<TemporalBatch*>(dst);
+    b->t = temporal_args(v.rt, &v.g, v.spp, &v.cam, &v.prev, &v.params, &v.hist_in, &v.hist_out, v.crt, v.hacc);
+    b->nd = static_cast<const float4*>(v.g.nd);
+    *gx = (v.cam.width + 31) / 32;
+    *gy = (v.cam.height + 7) / 8;
+}
+void temporal_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_temporal_batch<<<blocks, 256, 0, s>>>(static_cast<const TemporalBatch*>(args), g);
+}
+
+size_t spatial_args_size() { return sizeof(SpatialArgs); }
+void spatial_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int* gx, int* gy) {
+    *reinterpret_cast<SpatialArgs*>(dst) =
+        SpatialArgs{reinterpret_cast<const float4*>(v.crt), reinterpret_cast<const float2*>(v.hist_out.mom),
+                    v.hist_out.hlen, v.cam.width, v.cam.height, v.params.r_s, v.params.var_ref,
+                    reinterpret_cast<float4*>(v.crec), nullptr};
+    *gx = (v.cam.width + 15) / 16;
+    *gy = (v.cam.height + 15) / 16;
+}
+void spatial_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_spatial_batch<<<blocks, 256, 0, s>>>(static_cast<const SpatialArgs*>(args), g);
+}
+
+}  // namespace hdof

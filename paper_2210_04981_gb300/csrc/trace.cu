@@ -11,6 +11,7 @@
 // per warp; each thread traces all samples of its pixel in sample order and
 // writes the normalised per-pixel result once, so the output does not depend
 // on scheduling.
+#include "batch.cuh"
 #include "internal.h"
 
 namespace hdof {
@@ -18,9 +19,17 @@ namespace {
 
 constexpr int TB = 16;  // compaction tile edge
 
-__global__ void __launch_bounds__(256) k_count(const uint8_t* __restrict__ spp, int W, int H, int ntx,
-                                               unsigned* __restrict__ counts) {
-    int i = blockIdx.x * TB + (threadIdx.x & 15), j = blockIdx.y * TB + (threadIdx.x >> 4);
+struct CountArgs {
+    const uint8_t* spp;
+    int W, H, ntx;
+    unsigned* counts;
+};
+
+__device__ __forceinline__ void count_body(const CountArgs& a, int bx, int by) {
+    const uint8_t* __restrict__ spp = a.spp;
+    const int W = a.W, H = a.H, ntx = a.ntx;
+    unsigned* __restrict__ counts = a.counts;
+    int i = bx * TB + (threadIdx.x & 15), j = by * TB + (threadIdx.x >> 4);
     unsigned s = (i < W && j < H) ? spp[(size_t)j * W + i] : 0u;
     unsigned px = __syncthreads_count(s > 0);
     __shared__ unsigned red[8];
@@ -31,17 +40,32 @@ __global__ void __launch_bounds__(256) k_count(const uint8_t* __restrict__ spp, 
     if (threadIdx.x == 0) {
         unsigned t = 0;
         for (int k = 0; k < 8; ++k) t += red[k];
-        int tile = blockIdx.y * ntx + blockIdx.x;
+        int tile = by * ntx + bx;
         counts[2 * tile] = px;
         counts[2 * tile + 1] = t;
     }
 }
 
+__global__ void __launch_bounds__(256) k_count(CountArgs a) { count_body(a, blockIdx.x, blockIdx.y); }
+
 // one block: exclusive scans of the per-tile pixel and ray counts -> queue
 // and ray offsets; totals -> stats
-__global__ void __launch_bounds__(1024) k_scan(const unsigned* __restrict__ counts, int ntiles,
-                                               unsigned* __restrict__ offsets, unsigned* __restrict__ roffsets,
-                                               unsigned* __restrict__ totals, unsigned* __restrict__ stats) {
+struct ScanArgs {
+    const unsigned* counts;
+    int ntiles;
+    unsigned* offsets;
+    unsigned* roffsets;
+    unsigned* totals;
+    unsigned* stats;
+};
+
+__device__ __forceinline__ void scan_body(const ScanArgs& a) {
+    const unsigned* __restrict__ counts = a.counts;
+    const int ntiles = a.ntiles;
+    unsigned* __restrict__ offsets = a.offsets;
+    unsigned* __restrict__ roffsets = a.roffsets;
+    unsigned* __restrict__ totals = a.totals;
+    unsigned* __restrict__ stats = a.stats;
     __shared__ unsigned wsum[2][32];
     __shared__ unsigned carry[2];
     if (threadIdx.x == 0) carry[0] = carry[1] = 0;
@@ -93,13 +117,27 @@ __global__ void __launch_bounds__(1024) k_scan(const unsigned* __restrict__ coun
     }
 }
 
+__global__ void __launch_bounds__(1024) k_scan(ScanArgs a) { scan_body(a); }
+
 // queue entries in row-major order within each tile; optionally the first
 // ray of every traced pixel (tile ray offset + prefix of spp in queue order)
-__global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ spp, int W, int H, int ntx,
-                                                 const unsigned* __restrict__ offsets,
-                                                 const unsigned* __restrict__ roffsets, unsigned* __restrict__ queue,
-                                                 unsigned* __restrict__ ray_off) {
-    int i = blockIdx.x * TB + (threadIdx.x & 15), j = blockIdx.y * TB + (threadIdx.x >> 4);
+struct ScatterArgs {
+    const uint8_t* spp;
+    int W, H, ntx;
+    const unsigned* offsets;
+    const unsigned* roffsets;
+    unsigned* queue;
+    unsigned* ray_off;
+};
+
+__device__ __forceinline__ void scatter_body(const ScatterArgs& a, int bx, int by) {
+    const uint8_t* __restrict__ spp = a.spp;
+    const int W = a.W, H = a.H, ntx = a.ntx;
+    const unsigned* __restrict__ offsets = a.offsets;
+    const unsigned* __restrict__ roffsets = a.roffsets;
+    unsigned* __restrict__ queue = a.queue;
+    unsigned* __restrict__ ray_off = a.ray_off;
+    int i = bx * TB + (threadIdx.x & 15), j = by * TB + (threadIdx.x >> 4);
     unsigned n = (i < W && j < H) ? spp[(size_t)j * W + i] : 0u;
     bool on = n > 0;
     unsigned m = __ballot_sync(0xffffffffu, on);
@@ -113,7 +151,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ spp
     if (lane == 0) wcnt[w] = __popc(m);
     if (lane == 31) wray[w] = r;
     __syncthreads();
-    const int tile = blockIdx.y * ntx + blockIdx.x;
+    const int tile = by * ntx + bx;
     unsigned base = offsets[tile], rbase = roffsets[tile];
     for (int k = 0; k < w; ++k) {
         base += wcnt[k];
@@ -124,6 +162,8 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ spp
         if (ray_off) ray_off[(size_t)j * W + i] = rbase + r - n;
     }
 }
+
+__global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) { scatter_body(a, blockIdx.x, blockIdx.y); }
 
 struct TraceArgs {
     BvhView bvh;
@@ -204,7 +244,179 @@ __global__ void __launch_bounds__(128, HDOF_TRACE_MINB) k_trace(TraceArgs a) {
     }
 }
 
+TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
+                     unsigned* st, const uint8_t* spp, const unsigned* queue, unsigned* totals, float* rt, float* rec,
+                     const unsigned* ray_off) {
+    TraceArgs a;
+    a.bvh = b->view();
+    a.cam = make_cam(*cam);
+    a.coc = make_coc(*lens, cam->height, cam->tan_half_fovy);
+    a.L = make_lights(*p);
+    a.A = lens->aperture_radius;
+    a.zf = lens->focus_dist;
+    a.miss_dist = p->miss_dist;
+    a.key = make_uint2(p->seed, (unsigned)p->view * 65536u + (unsigned)p->frame);
+    a.cap = p->trav_cap > 0 ? p->trav_cap : 64 * (b->n_nodes + b->n_tris) + 64;
+    a.status = st;
+    a.spp = spp;
+    a.queue = queue;
+    a.totals = totals;
+    a.rt = reinterpret_cast<float4*>(rt);
+    a.rec = reinterpret_cast<float4*>(rec);
+    a.ray_off = ray_off;
+    return a;
+}
+
+// ---- multi-view forms -------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_count_batch(const CountArgs* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    count_body(a[v], bx, by);
+}
+__global__ void __launch_bounds__(1024) k_scan_batch(const ScanArgs* __restrict__ a) { scan_body(a[blockIdx.x]); }
+__global__ void __launch_bounds__(256) k_scatter_batch(const ScatterArgs* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    scatter_body(a[v], bx, by);
+}
+
+// exclusive prefix of the views' queue lengths: gq[v] is the first entry of
+// view v in the concatenated queue, gq[n] the total; gq[n + 1] (the shared
+// queue head) is reset.  One block.
+__global__ void __launch_bounds__(1024) k_queue_prefix(const ScanArgs* __restrict__ a, int n,
+                                                       unsigned* __restrict__ gq) {
+    __shared__ unsigned wsum[32];
+    __shared__ unsigned carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += 1024) {
+        int v = base + threadIdx.x;
+        unsigned c = v < n ? __ldcg(&a[v].totals[0]) : 0u, x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            unsigned sv = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(0xffffffffu, sv, o);
+                if (lane >= o) sv += y;
+            }
+            wsum[lane] = sv;
+        }
+        __syncthreads();
+        unsigned e = carry + (w ? wsum[w - 1] : 0u) + x - c;
+        if (v < n) gq[v] = e;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = e + c;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        gq[n] = carry;
+        gq[n + 1] = 0;
+    }
+}
+
+// persistent trace over the concatenated queues of all views: a warp takes
+// 32 * chunk entries per atomic; each entry finds its view by binary search
+// of gq and is traced exactly as the single-view kernel traces it
+template <int BS>
+__global__ void __launch_bounds__(BS) k_trace_batch(const TraceArgs* __restrict__ a, const unsigned* __restrict__ gq,
+                                                    int n, unsigned* head, int chunk) {
+    const int lane = threadIdx.x & 31;
+    const unsigned total = __ldcg(&gq[n]);
+    const unsigned step = 32u * (unsigned)chunk;
+    while (true) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(head, step);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= total) break;
+        for (int c = 0; c < chunk; ++c) {
+            unsigned k = base + 32u * (unsigned)c + (unsigned)lane;
+            if (k >= total) break;
+            int lo = 0, hi = n - 1;  // last view with gq[v] <= k
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&gq[mid]) <= k) lo = mid;
+                else hi = mid - 1;
+            }
+            const TraceArgs& av = a[lo];
+            trace_pixel(av, __ldg(&av.queue[k - __ldg(&gq[lo])]));
+        }
+    }
+}
+
+template <int BS>
+int trace_batch_occupancy(int* nb) {
+    HDOF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_batch<BS>, BS, 0), "batched trace: occupancy");
+    if (*nb < 1) *nb = 1;
+    return HDOF_OK;
+}
+
 }  // namespace
+
+size_t count_args_size() { return sizeof(CountArgs); }
+void count_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
+    const int W = v.cam.width, H = v.cam.height, ntx = (W + TB - 1) / TB;
+    *reinterpret_cast<CountArgs*>(dst) = CountArgs{v.spp, W, H, ntx, w.counts};
+    *gx = ntx;
+    *gy = (H + TB - 1) / TB;
+}
+void count_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_count_batch<<<blocks, 256, 0, s>>>(static_cast<const CountArgs*>(args), g);
+}
+
+size_t scan_args_size() { return sizeof(ScanArgs); }
+void scan_fill(const hdof_view& v, const ViewWs& w, void* dst) {
+    const int ntiles = ((v.cam.width + TB - 1) / TB) * ((v.cam.height + TB - 1) / TB);
+    *reinterpret_cast<ScanArgs*>(dst) = ScanArgs{w.counts, ntiles, w.offsets, w.roffsets, w.totals, v.stats};
+}
+void scan_launch_batch(const void* args, int n, cudaStream_t s) {
+    k_scan_batch<<<n, 1024, 0, s>>>(static_cast<const ScanArgs*>(args));
+}
+
+size_t scatter_args_size() { return sizeof(ScatterArgs); }
+void scatter_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
+    const int W = v.cam.width, H = v.cam.height, ntx = (W + TB - 1) / TB;
+    *reinterpret_cast<ScatterArgs*>(dst) = ScatterArgs{v.spp, W, H, ntx, w.offsets, w.roffsets, w.queue, nullptr};
+    *gx = ntx;
+    *gy = (H + TB - 1) / TB;
+}
+void scatter_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_scatter_batch<<<blocks, 256, 0, s>>>(static_cast<const ScatterArgs*>(args), g);
+}
+
+size_t trace_args_size() { return sizeof(TraceArgs); }
+void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst) {
+    *reinterpret_cast<TraceArgs*>(dst) =
+        trace_args(v.bvh, &v.cam, &v.lens, &v.params, st, v.spp, w.queue, w.totals, v.rt, nullptr, nullptr);
+}
+int trace_batch_grid(int block, int* blocks) {
+    int nb = 1, rc;
+    if (block == 64) rc = trace_batch_occupancy<64>(&nb);
+    else if (block == 256) rc = trace_batch_occupancy<256>(&nb);
+    else rc = trace_batch_occupancy<128>(&nb);
+    if (rc) return rc;
+    *blocks = sm_count() * nb;
+    return HDOF_OK;
+}
+
+int trace_launch_batch(const void* scan_args, const void* trace_args, int n, unsigned* gq, int block, int chunk,
+                       int blocks, cudaStream_t s) {
+    k_queue_prefix<<<1, 1024, 0, s>>>(static_cast<const ScanArgs*>(scan_args), n, gq);
+    HDOF_LAUNCHED("batched trace: queue prefix");
+    const TraceArgs* a = static_cast<const TraceArgs*>(trace_args);
+    if (block == 64) k_trace_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+    else if (block == 256) k_trace_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+    else k_trace_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+    HDOF_LAUNCHED("batched trace");
+    return HDOF_OK;
+}
+
 }  // namespace hdof
 
 using namespace hdof;
@@ -234,28 +446,12 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
     unsigned* totals = roffsets + ntiles;                           // [4]
     unsigned* queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) + L.trace_counts);
     dim3 tg(ntx, nty);
-    k_count<<<tg, 256, 0, s>>>(spp, W, H, ntx, counts);
-    k_scan<<<1, 1024, 0, s>>>(counts, ntiles, offsets, roffsets, totals, stats);
-    k_scatter<<<tg, 256, 0, s>>>(spp, W, H, ntx, offsets, roffsets, queue, ray_off);
+    k_count<<<tg, 256, 0, s>>>(CountArgs{spp, W, H, ntx, counts});
+    k_scan<<<1, 1024, 0, s>>>(ScanArgs{counts, ntiles, offsets, roffsets, totals, stats});
+    k_scatter<<<tg, 256, 0, s>>>(ScatterArgs{spp, W, H, ntx, offsets, roffsets, queue, ray_off});
     HDOF_LAUNCHED("hdof_trace: compaction");
 
-    TraceArgs a;
-    a.bvh = b->view();
-    a.cam = make_cam(*cam);
-    a.coc = make_coc(*lens, H, cam->tan_half_fovy);
-    a.L = make_lights(*p);
-    a.A = lens->aperture_radius;
-    a.zf = lens->focus_dist;
-    a.miss_dist = p->miss_dist;
-    a.key = make_uint2(p->seed, (unsigned)p->view * 65536u + (unsigned)p->frame);
-    a.cap = p->trav_cap > 0 ? p->trav_cap : 64 * (b->n_nodes + b->n_tris) + 64;
-    a.status = st;
-    a.spp = spp;
-    a.queue = queue;
-    a.totals = totals;
-    a.rt = reinterpret_cast<float4*>(rt);
-    a.rec = reinterpret_cast<float4*>(rec);
-    a.ray_off = ray_off;
+    TraceArgs a = trace_args(b, cam, lens, p, st, spp, queue, totals, rt, rec, ray_off);
     static int occ[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);

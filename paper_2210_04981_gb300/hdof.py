@@ -62,6 +62,18 @@ class hdof_history(C.Structure):
                 ("hlen", C.c_void_p)]
 
 
+class hdof_view(C.Structure):
+    _fields_ = [("bvh", C.c_void_p), ("cam", hdof_camera), ("prev", hdof_camera), ("lens", hdof_lens),
+                ("params", hdof_params), ("g", hdof_gbuf)] + \
+               [(n, C.c_void_p) for n in ("edge", "spp", "rt", "stats", "pp", "crt", "hacc", "crec", "out")] + \
+               [("hist_in", hdof_history), ("hist_out", hdof_history), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
+
+
+class hdof_tuning(C.Structure):
+    _fields_ = [("trace_block", C.c_int32), ("trace_chunk", C.c_int32), ("reserved", C.c_int32 * 2)]
+
+
 class hdof_post_state(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("rt", "crt", "hacc", "mom", "hlen", "crec", "sp_aux", "pp", "pp_aux",
                                           "out")]
@@ -105,6 +117,12 @@ def load():
                               P(hdof_params), P(hdof_history), P(hdof_history), vp, vp, vp, vp], C.c_int),
         "hdof_composite": ([P(hdof_gbuf), vp, vp, vp, vp, vp, P(hdof_camera), P(hdof_lens), P(hdof_params),
                             vp, vp], C.c_int),
+        "hdof_batch_create": ([P(hdof_view), i32, P(hdof_tuning), P(vp), vp], C.c_int),
+        "hdof_batch_update": ([vp, P(hdof_view), i32, vp], C.c_int),
+        "hdof_batch_render": ([vp, vp], C.c_int),
+        "hdof_batch_render_range": ([vp, i32, i32, vp], C.c_int),
+        "hdof_batch_bytes": ([vp], sz),
+        "hdof_batch_destroy": ([vp], C.c_int),
         "hdof_post_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
         "hdof_post_forward": ([P(hdof_gbuf), vp, vp, vp, vp, P(hdof_camera), P(hdof_lens), P(hdof_params),
                                P(hdof_post_state), vp, sz, vp], C.c_int),
@@ -124,6 +142,8 @@ def exported_symbols():
     return ["hdof_version", "hdof_last_error", "hdof_sync", "hdof_default_params", "hdof_build_bvh",
             "hdof_bvh_destroy", "hdof_bvh_info", "hdof_closest_hits", "hdof_gbuffer", "hdof_workspace_bytes",
             "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_postfilter", "hdof_reconstruct", "hdof_composite",
+            "hdof_batch_create", "hdof_batch_update", "hdof_batch_render", "hdof_batch_render_range",
+            "hdof_batch_destroy", "hdof_batch_bytes",
             "hdof_post_workspace_bytes", "hdof_post_forward", "hdof_post_backward"]
 
 
@@ -385,6 +405,117 @@ class Renderer:
         hdof_composite(self.g, self.spp, self.pp, self.crt, self.crec, self.hacc, cam, lns, p, self.out, stream)
         self.cur = 1 - self.cur
         return self.out
+
+
+# ------------------------------------------------------ batched multi-view --
+
+def tuning(trace_block=128, trace_chunk=1) -> hdof_tuning:
+    t = hdof_tuning()
+    t.trace_block, t.trace_chunk = int(trace_block), int(trace_chunk)
+    return t
+
+
+def hdof_batch_create(views, tune=None, stream=None) -> C.c_void_p:
+    arr = (hdof_view * len(views))(*views)
+    h = C.c_void_p()
+    _check(load().hdof_batch_create(arr, len(views), C.byref(tune) if tune is not None else None, C.byref(h),
+                                    _stream(stream)))
+    return h
+
+
+def hdof_batch_update(handle, views, stream=None):
+    arr = (hdof_view * len(views))(*views)
+    _check(load().hdof_batch_update(handle, arr, len(views), _stream(stream)))
+
+
+def hdof_batch_render(handle, stream=None):
+    _check(load().hdof_batch_render(handle, _stream(stream)))
+
+
+BATCH_STAGES = ("gbuffer", "mask", "compaction", "trace", "postfilter", "reconstruct", "composite")
+
+
+def hdof_batch_render_range(handle, first, last, stream=None):
+    _check(load().hdof_batch_render_range(handle, int(first), int(last), _stream(stream)))
+
+
+def hdof_batch_destroy(handle):
+    _check(load().hdof_batch_destroy(handle))
+
+
+class Batch:
+    """Many views (each its own scene, size, camera, lens and constants)
+    rendered by one launch per stage.  Each view owns the buffers of a
+    :class:`Renderer` (FP32 planes).  ``frame`` rewrites the device launch
+    records for the given cameras/lenses/params (history ping-pong
+    included) and enqueues the batched frame; ``render`` only enqueues the
+    launches, so it can be captured in a CUDA graph and replayed after each
+    ``update``."""
+
+    def __init__(self, bvhs, sizes, ps, tune=None, device="cuda"):
+        assert len(bvhs) == len(sizes) == len(ps) and len(bvhs) > 0
+        self.bvhs = list(bvhs)
+        self.params = list(ps)
+        self.views = [Renderer(b, w, h, p, device) for b, (w, h), p in zip(self.bvhs, sizes, ps)]
+        self.tune = tune if tune is not None else tuning()
+        self.handle = None
+
+    def __len__(self):
+        return len(self.views)
+
+    def records(self, cams, prevs, lenses, ps):
+        out = []
+        for r, cam, prev, ln, p in zip(self.views, cams, prevs, lenses, ps):
+            hin, hout = r.hist[r.cur], r.hist[1 - r.cur]
+            v = hdof_view()
+            h = r.bvh.handle
+            v.bvh = h.value if isinstance(h, C.c_void_p) else h
+            v.cam, v.prev, v.lens, v.params = camera(cam), camera(prev), lens(ln), params(p)
+            v.g = r.g.struct()
+            for n in ("edge", "spp", "rt", "stats", "pp", "crt", "hacc", "crec", "out"):
+                setattr(v, n, _ptr(getattr(r, n)))
+            v.hist_in, v.hist_out = hin.struct(), hout.struct()
+            v.workspace, v.workspace_bytes = _ptr(r.ws), r.ws.numel()
+            out.append(v)
+        return out
+
+    def update(self, cams, prevs, lenses, ps, stream=None):
+        """Rewrite the launch records for the next frame (creates the handle
+        on first use)."""
+        recs = self.records(cams, prevs, lenses, ps)
+        if self.handle is None:
+            self.handle = hdof_batch_create(recs, self.tune, stream)
+        else:
+            hdof_batch_update(self.handle, recs, stream)
+
+    def render(self, stream=None):
+        hdof_batch_render(self.handle, stream)
+
+    def handle_bytes(self) -> int:
+        """Bytes of launch records one update uploads."""
+        return int(load().hdof_batch_bytes(self.handle))
+
+    def advance(self):
+        """Swap every view's history ping-pong after a rendered frame."""
+        for r in self.views:
+            r.cur = 1 - r.cur
+
+    def frame(self, cams, prevs, lenses, ps, stream=None):
+        self.update(cams, prevs, lenses, ps, stream)
+        self.render(stream)
+        self.advance()
+        return [r.out for r in self.views]
+
+    def close(self):
+        if self.handle is not None:
+            hdof_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
 
 
 # ------------------------------------------------ differentiable post-path --

@@ -49,3 +49,14 @@ def frac_close(a, b, atol, rtol=0.0, axis=-1):
 def report(name, a, b):
     d = np.abs(a - b)
     return f"{name}: max |d| = {d.max():.3e}, 99.9th pct = {np.percentile(d, 99.9):.3e}"
+
+
+def rt_close(rt, ref, traced):
+    """Per traced pixel: colours 1e-3, hit ratio 1e-4, CoC 1e-3 rel, position 1e-4 rel."""
+    a, b = rt[traced], ref[traced]
+    col = np.r_[0:3, 4:7]
+    ok = np.all(np.abs(a[:, col] - b[:, col]) <= 1e-3, axis=1)
+    ok &= np.abs(a[:, 3] - b[:, 3]) <= 1e-4
+    ok &= np.all(np.abs(a[:, [7, 11]] - b[:, [7, 11]]) <= 1e-3 * np.maximum(1, np.abs(b[:, [7, 11]])), axis=1)
+    ok &= np.all(np.abs(a[:, 8:11] - b[:, 8:11]) <= 1e-4 * np.maximum(1, np.abs(b[:, 8:11])), axis=1)
+    return ok

@@ -53,7 +53,7 @@ def test_struct_layout_matches_header(H, tmp_path):
     import subprocess
     recs = {"hdof_camera": H.hdof_camera, "hdof_lens": H.hdof_lens, "hdof_params": H.hdof_params,
             "hdof_gbuf": H.hdof_gbuf, "hdof_history": H.hdof_history, "hdof_bvh_stats": H.hdof_bvh_stats,
-            "hdof_post_state": H.hdof_post_state}
+            "hdof_post_state": H.hdof_post_state, "hdof_view": H.hdof_view, "hdof_tuning": H.hdof_tuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hdof.h"', "int main(void) {"]
     for name, rec in recs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
@@ -94,6 +94,17 @@ def test_invalid_arguments_rejected_before_launch(H):
                           None, None, None, 0, None) == -1
     lib.hdof_last_error(buf, 256)
     assert b"spp_max" in buf.value
+    # batched calls: empty batch, unsupported launch shape, NULL handle
+    views = (H.hdof_view * 1)()
+    h = C.c_void_p()
+    assert lib.hdof_batch_create(views, 0, None, C.byref(h), None) == -1
+    assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(96, 1)), C.byref(h), None) == -1
+    lib.hdof_last_error(buf, 256)
+    assert b"trace_block" in buf.value
+    assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(128, 0)), C.byref(h), None) == -1
+    assert lib.hdof_batch_render(None, None) == -1
+    assert lib.hdof_batch_update(None, views, 1, None) == -1
+    assert lib.hdof_batch_destroy(None) == 0
 
 
 def test_python_binding_requires_cuda_tensors(H):

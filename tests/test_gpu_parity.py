@@ -21,7 +21,7 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_2210_04981_gb300.hdof as H  # noqa: E402
-from gpu_util import bvh_of, dev, frac_close, gbuf_from, history_from, host, report, workspace  # noqa: E402
+from gpu_util import bvh_of, dev, frac_close, gbuf_from, history_from, host, report, rt_close, workspace  # noqa: E402,E501
 
 T30 = math.tan(math.radians(30.0))
 
@@ -231,17 +231,6 @@ def _trace(bvh, cam, lens, p, spp_np):
     return host(rt), host(stats)
 
 
-def _rt_close(rt, ref, traced):
-    """Per traced pixel: colours 1e-3, hit ratio 1e-4, CoC 1e-3 rel, position 1e-4 rel."""
-    a, b = rt[traced], ref[traced]
-    col = np.r_[0:3, 4:7]
-    ok = np.all(np.abs(a[:, col] - b[:, col]) <= 1e-3, axis=1)
-    ok &= np.abs(a[:, 3] - b[:, 3]) <= 1e-4
-    ok &= np.all(np.abs(a[:, [7, 11]] - b[:, [7, 11]]) <= 1e-3 * np.maximum(1, np.abs(b[:, [7, 11]])), axis=1)
-    ok &= np.all(np.abs(a[:, 8:11] - b[:, 8:11]) <= 1e-4 * np.maximum(1, np.abs(b[:, 8:11])), axis=1)
-    return ok
-
-
 def test_trace_tiny(orc):
     scene, cam, lens, p = hi.tiny_config()
     osc = orc.OScene(scene)
@@ -253,7 +242,7 @@ def test_trace_tiny(orc):
     traced = spp > 0
     assert stats[0] == traced.sum() and stats[1] == spp.astype(np.int64).sum()
     assert np.all(np.isnan(rt[~traced]))  # untraced pixels untouched
-    ok = _rt_close(rt, ref, traced)
+    ok = rt_close(rt, ref, traced)
     assert ok.mean() >= 0.999, f"{(~ok).sum()} of {ok.size} traced pixels differ; " + report("rt", rt[traced], ref[traced])
 
 
@@ -269,7 +258,7 @@ def test_trace_room(orc):
     rt, stats = _trace(bvh, cam, lens, p, spp)
     ref = orc.trace(orc.OScene(scene), cam, lens, p, spp)
     traced = spp > 0
-    ok = _rt_close(rt, ref, traced)
+    ok = rt_close(rt, ref, traced)
     assert ok.mean() >= 0.999, f"{(~ok).sum()} of {ok.size}; " + report("rt", rt[traced], ref[traced])
 
 
@@ -426,7 +415,7 @@ def test_room_1080p_bench_config_sampled(orc):
         assert (spp == ref["mask"]["spp"]).mean() >= 0.999
         same = spp == ref["mask"]["spp"]
         tr = (spp > 0) & same
-        ok = _rt_close(host(r.rt), ref["rt"], tr)
+        ok = rt_close(host(r.rt), ref["rt"], tr)
         assert ok.mean() >= 0.999, f"frame {k}: rt {ok.mean():.5f}"
         assert frac_close(host(r.crt)[tr], ref["crt"][tr], 1e-3, 1e-3) >= 0.999
         pp = host(r.pp).reshape(-1, 4)[pix]
