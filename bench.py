@@ -330,7 +330,7 @@ def run_ours(args):
         "traced_px_per_frame": int(traced.mean()), "trace_ms": round(trace_ms, 4),
         "stages": per_stage, "bvh_build_ms": round(bvh_ms, 3), "scene_upload_ms": round(upload_ms, 3),
         "wall_s_timed": round(wall, 3),
-        "roofline": roof, "e2e": e2e, "gpu_launches": 12 * K, "clocks": clocks,
+        "roofline": roof, "e2e": e2e, "gpu_launches": 13 * K, "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
@@ -352,7 +352,7 @@ def _batch_frame_args(views, k):
 def run_batch(args):
     """64 views over 4 rooms (50k-500k triangles, 256^2 to 1920x1080): each
     step is one batched frame of all views (records update + graph replay of
-    the 14 batched launches), against the plain form (the single-view calls,
+    the 15 batched launches), against the plain form (the single-view calls,
     view after view) on the same buffers' contents."""
     import torch
 
@@ -366,7 +366,7 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     scenes = hi.batch_scenes()
-    views = hi.batch_views(64)
+    views = hi.batch_views(args.views)
     t1 = time.perf_counter()
     bvhs = [H.hdof_build_bvh(*(torch.from_numpy(a).to(dev) for a in (sc.verts, sc.idx, sc.mat, sc.uv)))
             for sc in scenes]
@@ -484,7 +484,7 @@ def run_batch(args):
             e_ms += e0.elapsed_time(e1)
         e2e = {"value": round(e_ms / K, 4), "unit": "ms/frame", "h2d_bytes_per_step": int(b.handle_bytes()),
                "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in outs)),
-               "note": "h2d = the batch's launch records (one pinned upload); d2h = 64 RGBA32F images"}
+               "note": f"h2d = the batch launch records (one pinned upload); d2h = {len(views)} RGBA32F images"}
 
     dom = int(np.argmax(stage_ms))
     hbm, sm_med, peak_src = peaks()
@@ -501,10 +501,10 @@ def run_batch(args):
         "metric": METRIC, "value": round(batch_ms, 4), "unit": "ms/frame", "n_gpus": ws, "steps": K,
         "warmup": Wm, "ms_per_step": round(batch_ms, 4), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "64 views over 4 procedural rooms (50k-500k tris, seeds 10-13), 256^2..1920x1080, "
+        "config": {"workload": f"{len(views)} views over 4 procedural rooms (50k-500k tris, seeds 10-13), 256^2..1920x1080, "
                                "focus U[0.5,6], aperture U[0.01,0.1], 1-16 spp; one batched frame per step",
                    "views": len(views), "pixels": px, "triangles": [int(x.stats().n_tris) for x in bvhs],
-                   "tuning": {"trace_block": tune.trace_block, "trace_chunk": tune.trace_chunk},
+                   "tuning": {"trace_block": tune.trace_block, "trace_refill": tune.trace_refill},
                    "tuning_ms": {f"{k[0]}x{k[1]}": round(v, 3) for k, v in tune_ms.items()},
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single",
                    "l2": "flushed between steps (256 MiB write)"},
@@ -513,7 +513,7 @@ def run_batch(args):
         "mrays_per_s_trace": round(rays / (stage_ms[3] * 1e-3) / 1e6, 1),
         "rays_per_frame": int(rays), "traced_px_per_frame": int(traced),
         "stages": {n: round(float(t), 4) for n, t in zip(H.BATCH_STAGES, stage_ms)},
-        "bvh_build_ms": round(bvh_ms, 3), "roofline": roof, "e2e": e2e, "gpu_launches": 14 * K, "clocks": clocks,
+        "bvh_build_ms": round(bvh_ms, 3), "roofline": roof, "e2e": e2e, "gpu_launches": 15 * K, "clocks": clocks,
     }
     b.close()
     if rank == 0:
@@ -625,6 +625,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--ref-pf-stride", type=int, default=256)
+    ap.add_argument("--views", type=int, default=64, help="views of the batched workload (--scene batch)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -188,7 +188,8 @@ int hdof_gbuffer(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_camera*
 /* ---------------------------------------------------- scratch memory -- */
 /* Bytes of caller-owned device scratch the calls below need for a
  * width x height frame (the maximum over calls; one buffer serves them all
- * when they run in order on one stream). */
+ * when they run in order on one stream).  The trace's share grows with
+ * p->spp_max: 21 bytes per possible ray (pixel, sample index, record). */
 size_t hdof_workspace_bytes(int32_t width, int32_t height, const hdof_params* p);
 
 /* ----------------------------------------------------------- mask -- */
@@ -226,8 +227,11 @@ int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const 
 
 /* ---------------------------------------------------------- trace */
 /* Thin-lens distributed ray trace of the masked pixels (Ray Trace section).
- * Compacts the pixels with spp > 0 into a queue (tile order), then a
- * persistent kernel traces spp[p] lens rays per queued pixel: Philox4x32-10
+ * Compacts the pixels with spp > 0 into a queue (tile order) and lists
+ * their rays; a persistent kernel traces the ray list (idle lanes of a warp
+ * fetch new rays as others finish), then each queued pixel sums its
+ * samples' records in sample order.  min(spp[p], p->spp_max) lens rays
+ * per pixel (the ray lists are sized for spp_max): Philox4x32-10
  * (key = (seed, view*65536+frame), counter = (pixel, sample, 0, 0)) gives
  * u1, u2 -> lens point rho = A sqrt(u1), theta = 2 pi u2; the ray aims at
  * the pixel's focus-plane point; closest hit; Lambert radiance; split
@@ -315,12 +319,14 @@ typedef struct hdof_view {
     size_t workspace_bytes;
 } hdof_view;
 
-/* Launch shapes of the batched frame (chosen by an autotuner).
- * trace_block: threads per block of the persistent trace (64, 128 or 256);
- * trace_chunk: pixels each lane takes per queue fetch (1, 2 or 4). */
+/* Launch shape of the batched frame's persistent trace (chosen by an
+ * autotuner; results do not depend on it).
+ * trace_block: threads per block (64, 128 or 256);
+ * trace_refill: a warp fetches new rays for its idle lanes once fewer than
+ *   this many of its 32 lanes still trace (1..32). */
 typedef struct hdof_tuning {
     int32_t trace_block;
-    int32_t trace_chunk;
+    int32_t trace_refill;
     int32_t reserved[2];
 } hdof_tuning;
 
@@ -329,7 +335,7 @@ typedef struct hdof_batch hdof_batch;
 /* Prepares a batch: validates every view, builds each stage's per-view
  * launch records and block tables and copies them to device memory the
  * handle owns (synchronous).  The views' buffers must stay valid while the
- * handle is used.  tuning may be NULL (defaults 128 / 1). */
+ * handle is used.  tuning may be NULL (defaults 128 / 8). */
 int hdof_batch_create(const hdof_view* views, int32_t n_views, const hdof_tuning* tuning, hdof_batch** out,
                       void* stream);
 int hdof_batch_destroy(hdof_batch* batch);
@@ -355,7 +361,7 @@ enum {
     HDOF_STAGE_GBUFFER = 0,     /* 1 launch */
     HDOF_STAGE_MASK = 1,        /* tile clear, edge, spp: 3 launches */
     HDOF_STAGE_COMPACT = 2,     /* count, scan, scatter: 3 launches */
-    HDOF_STAGE_TRACE = 3,       /* queue prefix, persistent trace: 2 launches */
+    HDOF_STAGE_TRACE = 3,       /* ray prefix, persistent trace, resolve: 3 launches */
     HDOF_STAGE_POSTFILTER = 4,  /* prep, gather: 2 launches */
     HDOF_STAGE_RECONSTRUCT = 5, /* temporal, spatial: 2 launches */
     HDOF_STAGE_COMPOSITE = 6,   /* 1 launch */

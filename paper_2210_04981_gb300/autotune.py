@@ -2,7 +2,8 @@
 
 The batched frame has one free launch shape that changes its speed but not
 its results: the persistent trace's block size (64, 128 or 256 threads) and
-how many queue entries each lane takes per atomic fetch (1, 2 or 4).  Every
+its refill threshold (a warp fetches new rays for its idle lanes once fewer
+than that many lanes still trace: 2, 4, 8 or 16).  Every
 candidate renders bit-identical images, so the tuner only times them: it
 builds one batch handle per candidate over the caller's own buffers, times
 whole batched frames with CUDA events on the current stream (warm-up first,
@@ -20,7 +21,7 @@ import torch
 
 from . import hdof as H
 
-CANDIDATES = tuple((b, c) for b in (64, 128, 256) for c in (1, 2, 4))
+CANDIDATES = tuple((b, c) for b in (64, 128, 256) for c in (2, 4, 8, 16))
 
 
 def cache_path() -> str:
@@ -52,10 +53,10 @@ def _store(d: dict):
     os.replace(tmp, path)
 
 
-def time_shape(batch: "H.Batch", frame_args, block: int, chunk: int, reps: int = 5, warmup: int = 2) -> float:
+def time_shape(batch: "H.Batch", frame_args, block: int, refill: int, reps: int = 5, warmup: int = 2) -> float:
     """Median milliseconds of one batched frame with the given trace shape."""
     recs = batch.records(*frame_args)
-    h = H.hdof_batch_create(recs, H.tuning(block, chunk))
+    h = H.hdof_batch_create(recs, H.tuning(block, refill))
     try:
         for _ in range(warmup):
             H.hdof_batch_render(h)
@@ -73,7 +74,7 @@ def time_shape(batch: "H.Batch", frame_args, block: int, chunk: int, reps: int =
 
 
 def tune(batch: "H.Batch", frame_args, candidates=CANDIDATES, reps: int = 5, use_cache: bool = True):
-    """Pick the fastest (trace_block, trace_chunk) for the batch's workload.
+    """Pick the fastest (trace_block, trace_refill) for the batch's workload.
 
     ``frame_args`` = (cams, prevs, lenses, params) of a representative frame.
     Returns (hdof_tuning, {shape: ms}); the timings are empty on a cache hit.

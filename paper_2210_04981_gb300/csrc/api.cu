@@ -115,12 +115,18 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     size_t mtiles = (size_t)((W + T - 1) / T) * ((H + T - 1) / T);
     size_t ptiles = (size_t)((W + HDOF_TILE_PF - 1) / HDOF_TILE_PF) * ((H + HDOF_TILE_PF - 1) / HDOF_TILE_PF);
     l.mask_tiles = align256(mtiles);
+    size_t nray = npx * (size_t)(p ? p->spp_max : 16);
     l.trace_counts = align256(ptiles * 4 * sizeof(unsigned) + 4 * sizeof(unsigned));
     l.trace_queue = align256(npx * sizeof(unsigned));
+    l.trace_qoff = align256(npx * sizeof(unsigned));
+    l.trace_ray_pix = align256(nray * sizeof(unsigned));
+    l.trace_ray_s = align256(nray);
+    l.trace_rec = align256(nray * sizeof(float4));
+    l.trace = l.trace_counts + l.trace_queue + l.trace_qoff + l.trace_ray_pix + l.trace_ray_s + l.trace_rec;
     l.pf_prep = align256(npx * sizeof(float4));
     l.pf_tiles = align256(ptiles * sizeof(float));
     size_t mask = l.mask_tiles;
-    size_t trace = l.trace_counts + l.trace_queue;
+    size_t trace = l.trace;
     size_t pf = l.pf_prep + l.pf_tiles;
     l.total = mask > trace ? mask : trace;
     if (pf > l.total) l.total = pf;

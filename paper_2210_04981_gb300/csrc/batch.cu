@@ -1,7 +1,7 @@
 // Batched multi-view frame: every stage of the per-frame path runs as one
 // launch over the blocks of all views, so a batch of small views fills the
 // GPU the way one large view does and the whole frame is a fixed sequence
-// of 14 launches that a CUDA graph can capture.
+// of 15 launches that a CUDA graph can capture.
 //
 // hdof_batch_create writes each stage's per-view launch records (the same
 // records the single-view calls pass by value), the per-view block prefix
@@ -39,10 +39,10 @@ struct StageDef {
     LaunchFn launch;
 };
 
-// grid stages in launch order (the scan, the trace and the tile clear are
-// launched between them by hand)
-enum { S_GBUF, S_MASK_EDGE, S_MASK_SPP, S_COUNT, S_SCATTER, S_PF_PREP, S_PF_GATHER, S_TEMPORAL, S_SPATIAL,
-       S_COMPOSITE, N_STAGES };
+// per-view records in launch order (the tile clear, the scan and the
+// persistent trace are launched between the grid stages by hand)
+enum { S_GBUF, S_MASK_EDGE, S_MASK_SPP, S_COUNT, S_SCATTER, S_TRACE, S_PF_PREP, S_PF_GATHER, S_TEMPORAL,
+       S_SPATIAL, S_COMPOSITE, N_STAGES };
 
 const StageDef kStages[N_STAGES] = {
     {"gbuffer", gbuffer_args_size, gbuffer_fill, gbuffer_launch_batch},
@@ -50,6 +50,7 @@ const StageDef kStages[N_STAGES] = {
     {"mask spp", mask_spp_args_size, mask_spp_fill, mask_spp_launch_batch},
     {"count", count_args_size, count_fill, count_launch_batch},
     {"scatter", scatter_args_size, scatter_fill, scatter_launch_batch},
+    {"trace", trace_args_size, trace_fill, nullptr},  // its grid is the per-pixel resolve
     {"post-filter prep", pf_prep_args_size, pf_prep_fill, pf_prep_launch_batch},
     {"post-filter gather", pf_gather_args_size, pf_gather_fill, pf_gather_launch_batch},
     {"temporal", temporal_args_size, temporal_fill, temporal_launch_batch},
@@ -88,10 +89,10 @@ int check_view(const hdof_view& v, int k, int dev) {
 }
 
 // offsets of the handle's device block: per stage [records][prefix][gx],
-// then scan records, trace records, tile-clear records, queue prefix
+// then scan records, tile-clear records, ray prefix
 struct Layout {
     size_t args[N_STAGES], prefix[N_STAGES], gx[N_STAGES];
-    size_t scan, trace, zero, gq, bytes;
+    size_t scan, zero, gq, bytes;
 };
 
 Layout layout(int n) {
@@ -107,8 +108,6 @@ Layout layout(int n) {
     }
     L.scan = b;
     b = align256(b + (size_t)n * scan_args_size());
-    L.trace = b;
-    b = align256(b + (size_t)n * trace_args_size());
     L.zero = b;
     b = align256(b + (size_t)n * sizeof(ZeroRec));
     L.gq = b;
@@ -138,7 +137,6 @@ int fill_image(const hdof_view* views, int n, unsigned* st, const Layout& L, cha
     for (int v = 0; v < n; ++v) {
         ViewWs w = view_ws(views[v]);
         scan_fill(views[v], w, img + L.scan + (size_t)v * scan_args_size());
-        trace_fill(views[v], w, st, img + L.trace + (size_t)v * trace_args_size());
         const hdof_params& p = views[v].params;
         ZeroRec z;
         z.ptr = w.tiles;
@@ -164,7 +162,6 @@ struct hdof_batch {
         int blocks;
     } stage[hdof::N_STAGES];
     const void* scan_args;
-    const void* trace_args;
     const hdof::ZeroRec* zero;
     unsigned* gq;  // [n + 2] queue prefix, total, head
     hdof::Layout L;
@@ -182,12 +179,12 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     *out = nullptr;
     HDOF_CHECK_ARG(views && n_views >= 1 && n_views <= 65536, "hdof_batch_create: need 1..65536 views, got %d",
                    (int)n_views);
-    hdof_tuning t = {128, 1, {0, 0}};
+    hdof_tuning t = {128, 8, {0, 0}};
     if (tuning) t = *tuning;
     HDOF_CHECK_ARG(t.trace_block == 64 || t.trace_block == 128 || t.trace_block == 256,
                    "hdof_batch_create: trace_block %d not in {64, 128, 256}", (int)t.trace_block);
-    HDOF_CHECK_ARG(t.trace_chunk >= 1 && t.trace_chunk <= 8, "hdof_batch_create: trace_chunk %d not in 1..8",
-                   (int)t.trace_chunk);
+    HDOF_CHECK_ARG(t.trace_refill >= 1 && t.trace_refill <= 32, "hdof_batch_create: trace_refill %d not in 1..32",
+                   (int)t.trace_refill);
     int dev = 0;
     HDOF_CUDA(cudaGetDevice(&dev), "hdof_batch_create: device");
     const int n = n_views;
@@ -239,7 +236,6 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
         b->stage[k].blocks = blocks[k];
     }
     b->scan_args = base + L.scan;
-    b->trace_args = base + L.trace;
     b->zero = reinterpret_cast<const ZeroRec*>(base + L.zero);
     b->gq = reinterpret_cast<unsigned*>(base + L.gq);
     b->L = L;
@@ -326,8 +322,9 @@ extern "C" int hdof_batch_render_range(const hdof_batch* b, int32_t first, int32
                 run(S_SCATTER);
                 break;
             case HDOF_STAGE_TRACE: {
-                int rc = trace_launch_batch(b->scan_args, b->trace_args, b->n, b->gq, b->tuning.trace_block,
-                                            b->tuning.trace_chunk, b->trace_blocks, s);
+                const hdof_batch::Stage& t = b->stage[S_TRACE];
+                int rc = trace_launch_batch(b->scan_args, t.args, t.grid, t.blocks, b->n, b->gq,
+                                            b->tuning.trace_block, b->tuning.trace_refill, b->trace_blocks, s);
                 if (rc) return rc;
                 break;
             }

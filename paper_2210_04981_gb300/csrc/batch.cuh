@@ -42,8 +42,12 @@ struct ViewWs {
     unsigned* counts;    // [2 * ntiles] traced pixels, rays per 16x16 tile
     unsigned* offsets;   // [ntiles]
     unsigned* roffsets;  // [ntiles]
-    unsigned* totals;    // [4] queue length, head
-    unsigned* queue;     // [W * H]
+    unsigned* totals;    // [4] queue length, -, ray count, ray head
+    unsigned* queue;     // [W * H] traced pixels
+    unsigned* qoff;      // [W * H] first ray of each queue entry
+    unsigned* ray_pix;   // [W * H * spp_max] pixel of each ray
+    uint8_t* ray_s;      // [W * H * spp_max] sample index of each ray
+    float4* rec;         // [W * H * spp_max] (radiance, hit distance) of each ray
     float4* prep;        // post-filter per-pixel record
     float* tmax;         // post-filter per-tile radius
 };
@@ -58,7 +62,12 @@ inline ViewWs view_ws(const hdof_view& v) {
     w.offsets = w.counts + 2 * ntiles;
     w.roffsets = w.offsets + ntiles;
     w.totals = w.roffsets + ntiles;
-    w.queue = reinterpret_cast<unsigned*>(base + L.trace_counts);
+    size_t o = L.trace_counts;
+    w.queue = reinterpret_cast<unsigned*>(base + o);
+    w.qoff = reinterpret_cast<unsigned*>(base + (o += L.trace_queue));
+    w.ray_pix = reinterpret_cast<unsigned*>(base + (o += L.trace_qoff));
+    w.ray_s = reinterpret_cast<uint8_t*>(base + (o += L.trace_ray_pix));
+    w.rec = reinterpret_cast<float4*>(base + (o += L.trace_ray_s));
     w.prep = reinterpret_cast<float4*>(base);
     w.tmax = reinterpret_cast<float*>(base + L.pf_prep);
     return w;
@@ -86,12 +95,13 @@ size_t scan_args_size();
 void scan_fill(const hdof_view& v, const ViewWs& w, void* dst);
 void scan_launch_batch(const void* args, int n, cudaStream_t s);  // one block per view
 size_t trace_args_size();
-void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst);
+void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst, int* gx, int* gy);
 // resident grid of the persistent batched trace for a block size
 int trace_batch_grid(int block, int* blocks);
-// queue prefix over the views (gq[0..n], gq[n + 1] = head) then the
-// persistent trace over the concatenated queues
-int trace_launch_batch(const void* scan_args, const void* trace_args, int n, unsigned* gq, int block, int chunk,
-                       int blocks, cudaStream_t s);
+// ray-count prefix over the views (gq[0..n], gq[n + 1] = head), the
+// persistent trace over the concatenated ray lists, and the per-pixel
+// resolve (grid of the trace records' gx x gy blocks per view)
+int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid resolve, int resolve_blocks, int n,
+                       unsigned* gq, int block, int refill, int blocks, cudaStream_t s);
 
 }  // namespace hdof

@@ -57,7 +57,12 @@ unsigned* status_ptr();
 struct WsLayout {
     size_t mask_tiles;      // uint8 per mask tile
     size_t trace_counts;    // uint32 per 16x16 tile: traced pixels, rays; + scan output
-    size_t trace_queue;     // uint32 per pixel
+    size_t trace_queue;     // uint32 per pixel: traced pixels in queue order
+    size_t trace_qoff;      // uint32 per pixel: first ray of each queue entry
+    size_t trace_ray_pix;   // uint32 per possible ray (pixels x spp_max): its pixel
+    size_t trace_ray_s;     // uint8 per possible ray: its sample index
+    size_t trace_rec;       // float4 per possible ray: radiance, hit distance
+    size_t trace;           // sum of the trace regions (laid out in this order)
     size_t pf_prep;         // float4 per pixel
     size_t pf_tiles;        // float per 16x16 tile
     size_t total;

@@ -5,12 +5,17 @@
 // and a hit ratio is kept.
 //
 // Compaction (deterministic, tile order): k_count counts traced pixels and
-// rays per 16x16 tile, k_scan turns the counts into queue offsets, k_scatter
-// writes pixel indices in row-major order within each tile.  The persistent
-// kernel k_trace then pulls 32-pixel chunks from the queue with one atomic
-// per warp; each thread traces all samples of its pixel in sample order and
-// writes the normalised per-pixel result once, so the output does not depend
-// on scheduling.
+// rays per 16x16 tile, k_scan turns the counts into queue and ray offsets,
+// k_scatter writes the traced pixels in row-major order within each tile
+// and lists every ray as (pixel, sample).
+//
+// Trace: k_trace_rays is persistent over the ray list.  Each lane holds one
+// ray; when it finishes, its (radiance, hit distance) record is written and,
+// once fewer than `refill` lanes of the warp are still busy, the idle lanes
+// take the next rays with one atomic per warp (dynamic fetch), so warps stay
+// full whatever the per-pixel ray counts and traversal lengths.  k_resolve
+// then sums each pixel's records in sample order, so the output does not
+// depend on scheduling.
 #include "batch.cuh"
 #include "internal.h"
 
@@ -19,9 +24,10 @@ namespace {
 
 constexpr int TB = 16;  // compaction tile edge
 
+// a pixel traces min(spp, spp_max) rays (the ray lists are sized for spp_max)
 struct CountArgs {
     const uint8_t* spp;
-    int W, H, ntx;
+    int W, H, ntx, smax;
     unsigned* counts;
 };
 
@@ -30,7 +36,7 @@ __device__ __forceinline__ void count_body(const CountArgs& a, int bx, int by) {
     const int W = a.W, H = a.H, ntx = a.ntx;
     unsigned* __restrict__ counts = a.counts;
     int i = bx * TB + (threadIdx.x & 15), j = by * TB + (threadIdx.x >> 4);
-    unsigned s = (i < W && j < H) ? spp[(size_t)j * W + i] : 0u;
+    unsigned s = (i < W && j < H) ? min((unsigned)spp[(size_t)j * W + i], (unsigned)a.smax) : 0u;
     unsigned px = __syncthreads_count(s > 0);
     __shared__ unsigned red[8];
     unsigned r = s;
@@ -109,7 +115,9 @@ __device__ __forceinline__ void scan_body(const ScanArgs& a) {
     }
     if (threadIdx.x == 0) {
         totals[0] = carry[0];  // queue length
-        totals[1] = 0;         // queue head
+        totals[1] = 0;
+        totals[2] = carry[1];  // ray count
+        totals[3] = 0;         // ray head
         if (stats) {
             stats[0] = carry[0];
             stats[1] = carry[1];
@@ -123,10 +131,13 @@ __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) { scan_body(a); }
 // ray of every traced pixel (tile ray offset + prefix of spp in queue order)
 struct ScatterArgs {
     const uint8_t* spp;
-    int W, H, ntx;
+    int W, H, ntx, smax;
     const unsigned* offsets;
     const unsigned* roffsets;
     unsigned* queue;
+    unsigned* qoff;
+    unsigned* ray_pix;
+    uint8_t* ray_s;
     unsigned* ray_off;
 };
 
@@ -136,9 +147,12 @@ __device__ __forceinline__ void scatter_body(const ScatterArgs& a, int bx, int b
     const unsigned* __restrict__ offsets = a.offsets;
     const unsigned* __restrict__ roffsets = a.roffsets;
     unsigned* __restrict__ queue = a.queue;
+    unsigned* __restrict__ qoff = a.qoff;
+    unsigned* __restrict__ ray_pix = a.ray_pix;
+    uint8_t* __restrict__ ray_s = a.ray_s;
     unsigned* __restrict__ ray_off = a.ray_off;
     int i = bx * TB + (threadIdx.x & 15), j = by * TB + (threadIdx.x >> 4);
-    unsigned n = (i < W && j < H) ? spp[(size_t)j * W + i] : 0u;
+    unsigned n = (i < W && j < H) ? min((unsigned)spp[(size_t)j * W + i], (unsigned)a.smax) : 0u;
     bool on = n > 0;
     unsigned m = __ballot_sync(0xffffffffu, on);
     __shared__ unsigned wcnt[8], wray[8];
@@ -158,8 +172,14 @@ __device__ __forceinline__ void scatter_body(const ScatterArgs& a, int bx, int b
         rbase += wray[k];
     }
     if (on) {
-        queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)(j * W + i);
-        if (ray_off) ray_off[(size_t)j * W + i] = rbase + r - n;
+        const unsigned k = base + __popc(m & ((1u << lane) - 1u)), q = (unsigned)(j * W + i), ro = rbase + r - n;
+        queue[k] = q;
+        qoff[k] = ro;
+        for (unsigned smp = 0; smp < n; ++smp) {
+            ray_pix[ro + smp] = q;
+            ray_s[ro + smp] = (uint8_t)smp;
+        }
+        if (ray_off) ray_off[q] = ro;
     }
 }
 
@@ -172,45 +192,206 @@ struct TraceArgs {
     Lights L;
     float A, zf, miss_dist;
     uint2 key;
-    int cap;
+    int cap, smax;
     unsigned* status;
     const uint8_t* spp;
     const unsigned* queue;
-    unsigned* totals;  // [0] queue length, [1] head
+    const unsigned* qoff;
+    const unsigned* ray_pix;
+    const uint8_t* ray_s;
+    unsigned* totals;  // [0] queue length, [2] ray count, [3] ray head
+    float4* recs;      // per ray (radiance rgb, hit distance t; +inf for a miss)
     float4* rt;        // 3 float4 per pixel
-    float4* rec;       // optional per-ray (L rgb, z) records, z = +inf for a miss
+    float4* rec;       // optional per-ray (L rgb, view depth z) records, z = +inf for a miss
     const unsigned* ray_off;
 };
 
-__device__ __forceinline__ void trace_pixel(const TraceArgs& a, unsigned q) {
+// lens sample `smp` of pixel q: origin on the lens disk, unit direction to
+// the pixel's focus-plane point
+__device__ __forceinline__ void lens_ray(const TraceArgs& a, unsigned q, unsigned smp, float3& O, float3& dir) {
     const int W = a.cam.W;
     const int i = (int)(q % (unsigned)W), j = (int)(q / (unsigned)W);
-    const int n = a.spp[q];
     const float3 d = pinhole_dir(a.cam, i + 0.5f + a.cam.jx, j + 0.5f + a.cam.jy);
     const float3 Pf = a.cam.pos + a.zf * d;
+    uint4 x = philox4x32_10(make_uint4(q, smp, 0u, 0u), a.key);
+    float rho = a.A * sqrtf(u01(x.x));
+    float sn, cs;
+    sincospif(2.f * u01(x.y), &sn, &cs);
+    O = a.cam.pos + (rho * cs) * a.cam.right + (rho * sn) * a.cam.up;
+    dir = normalize(Pf - O);
+}
+
+// where the rays of the trace come from: one view (the record is the kernel
+// parameter) or many (a record table and the views' ray-count prefix)
+struct OneView {
+    const TraceArgs& a;
+    __device__ __forceinline__ const TraceArgs& at(int) const { return a; }
+    __device__ __forceinline__ int locate(unsigned g, unsigned& r) const {
+        r = g;
+        return 0;
+    }
+};
+struct ManyViews {
+    const TraceArgs* __restrict__ tab;
+    const unsigned* __restrict__ gq;
+    int n;
+    __device__ __forceinline__ const TraceArgs& at(int v) const { return tab[v]; }
+    __device__ __forceinline__ int locate(unsigned g, unsigned& r) const {
+        int lo = 0, hi = n - 1;  // last view with gq[v] <= g
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&gq[mid]) <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        r = g - __ldg(&gq[lo]);
+        return lo;
+    }
+};
+
+// Persistent ray-level trace with dynamic fetch.  Per lane: one ray's
+// traversal state (same node/leaf steps, stack discipline and tie rule as
+// closest_hit).  The fetch is warp-uniform: every lane takes part in the
+// ballots; idle lanes are predicated off during the steps.
+template <class Src>
+__device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, unsigned* head, int refill) {
+    const unsigned FULL = 0xffffffffu;
+    const float INF = __int_as_float(0x7f800000);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    bool live = false, done = false;
+    int v = 0, cur = 0, sp = 0, steps = 0;
+    unsigned r = 0;
+    Ray ray;
+    Shear sh;
+    Hit h;
+    int stack[HDOF_STACK];
+    while (true) {
+        const unsigned need = __ballot_sync(FULL, !live && !done);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(head, (unsigned)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (!live && !done) {
+                const unsigned g = base + __popc(need & lt);
+                if (g < total) {
+                    v = src.locate(g, r);
+                    const TraceArgs& a = src.at(v);
+                    float3 O, dir;
+                    lens_ray(a, __ldg(&a.ray_pix[r]), __ldg(&a.ray_s[r]), O, dir);
+                    ray = make_ray(O, dir);
+                    sh = make_shear(dir);
+                    h.t = INF;
+                    h.slot = -1;
+                    h.id = 0x7fffffff;
+                    h.b0 = h.b1 = h.b2 = 0.f;
+                    cur = a.bvh.root;
+                    sp = 0;
+                    steps = 0;
+                    live = true;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, live)) break;
+        while (true) {
+            if (live) {
+                const TraceArgs& a = src.at(v);
+                const BvhView& bvh = a.bvh;
+                bool fin = false;
+                if (cur >= 0) {
+                    const Node* n = bvh.nodes + cur;
+                    float4 na = __ldg(&n->xy0), nb = __ldg(&n->xy1), nz = __ldg(&n->z01);
+                    int4 ch = __ldg(&n->child);
+                    float t0 = slab(ray, na.x, na.y, na.z, na.w, nz.x, nz.y, h.t);
+                    float t1 = slab(ray, nb.x, nb.y, nb.z, nb.w, nz.z, nz.w, h.t);
+                    bool h0 = t0 < INF, h1 = t1 < INF;
+                    if (h0 && h1) {
+                        int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
+                        if (sp < HDOF_STACK) stack[sp++] = farc;
+                        else atomicOr(a.status, HDOF_STATUS_TIMEOUT);
+                        cur = nearc;
+                    } else if (h0) {
+                        cur = ch.x;
+                    } else if (h1) {
+                        cur = ch.y;
+                    } else if (sp == 0) {
+                        fin = true;
+                    } else {
+                        cur = stack[--sp];
+                    }
+                } else {
+                    int e = ~cur, first = e >> 3, count = (e & 7) + 1;
+                    for (int k = 0; k < count; ++k) hit_tri(bvh, first + k, ray.o, sh, h);
+                    if (sp == 0) fin = true;
+                    else cur = stack[--sp];
+                }
+                if (++steps > a.cap) {
+                    atomicOr(a.status, HDOF_STATUS_TIMEOUT);
+                    fin = true;
+                }
+                if (fin) {
+                    for (int k = 0; k < bvh.big_count; ++k) {
+                        float4 lo = __ldg(&bvh.big_box[2 * k]), hi = __ldg(&bvh.big_box[2 * k + 1]);
+                        if (slab(ray, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, h.t) < INF)
+                            hit_tri(bvh, bvh.big_first + k, ray.o, sh, h);
+                    }
+                    float4 out = make_float4(0.f, 0.f, 0.f, INF);
+                    if (h.slot >= 0) {
+                        float3 nrm, L;
+                        shade(bvh, a.L, h, ray.d, nrm, L);
+                        out = make_float4(L.x, L.y, L.z, h.t);
+                    }
+                    a.recs[r] = out;
+                    live = false;
+                }
+            }
+            if (__popc(__ballot_sync(FULL, live)) < refill) break;
+        }
+    }
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_trace_rays(TraceArgs a, int refill) {
+    trace_rays_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], refill);
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_trace_rays_batch(const TraceArgs* __restrict__ tab,
+                                                         const unsigned* __restrict__ gq, int n, unsigned* head,
+                                                         int refill) {
+    trace_rays_body(ManyViews{tab, gq, n}, __ldcg(&gq[n]), head, refill);
+}
+
+// per traced pixel (queue entry k): its samples' records in sample order ->
+// near/far layer sums -> the normalised rt record (and the adjoint's per-ray
+// (L, z) records when requested)
+__device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
+    const unsigned k = (unsigned)bx * 256u + threadIdx.x;
+    if (k >= __ldcg(&a.totals[0])) return;
+    const unsigned q = __ldg(&a.queue[k]), ro = __ldg(&a.qoff[k]);
+    const int n = min((int)a.spp[q], a.smax);
     float3 SwL = f3(0, 0, 0), SfL = f3(0, 0, 0), SfP = f3(0, 0, 0);
     float Sw = 0.f, Sf = 0.f, Swc = 0.f, Sfc = 0.f;
     for (int smp = 0; smp < n; ++smp) {
-        uint4 x = philox4x32_10(make_uint4(q, (unsigned)smp, 0u, 0u), a.key);
-        float rho = a.A * sqrtf(u01(x.x));
-        float sn, cs;
-        sincospif(2.f * u01(x.y), &sn, &cs);
-        float3 O = a.cam.pos + (rho * cs) * a.cam.right + (rho * sn) * a.cam.up;
-        float3 dir = normalize(Pf - O);
-        Hit h = closest_hit(a.bvh, O, dir, a.cap, a.status);
-        float3 L, P, nrm;
+        float3 O, dir;
+        lens_ray(a, q, (unsigned)smp, O, dir);
+        const float4 rc = a.recs[ro + smp];
+        const bool hit = rc.w < __int_as_float(0x7f800000);
+        const float3 L = f3(rc.x, rc.y, rc.z);
+        float3 P;
         float c;
-        if (h.slot >= 0) {
-            P = O + h.t * dir;
+        if (hit) {
+            P = O + rc.w * dir;
             c = a.coc(dot(P - a.cam.pos, a.cam.fwd));
-            shade(a.bvh, a.L, h, dir, nrm, L);
         } else {
             P = O + a.miss_dist * dir;
             c = a.coc.at_infinity();
-            L = f3(0.f, 0.f, 0.f);
         }
-        if (a.rec) a.rec[a.ray_off[q] + smp] = make_float4(L.x, L.y, L.z, h.slot >= 0 ? dot(P - a.cam.pos, a.cam.fwd)
-                                                                                   : __int_as_float(0x7f800000));
+        if (a.rec)
+            a.rec[ro + smp] = make_float4(L.x, L.y, L.z, hit ? dot(P - a.cam.pos, a.cam.fwd)
+                                                             : __int_as_float(0x7f800000));
         float w = w_near(c), wf = 1.f - w, ac = fabsf(c);
         SwL = SwL + w * L;
         SfL = SfL + wf * L;
@@ -228,24 +409,10 @@ __device__ __forceinline__ void trace_pixel(const TraceArgs& a, unsigned q) {
     o[2] = make_float4(SfP.x * inf_, SfP.y * inf_, SfP.z * inf_, fok ? Sfc * inf_ : -1.f);
 }
 
-#ifndef HDOF_TRACE_MINB
-#define HDOF_TRACE_MINB 1
-#endif
-__global__ void __launch_bounds__(128, HDOF_TRACE_MINB) k_trace(TraceArgs a) {
-    const int lane = threadIdx.x & 31;
-    const unsigned n = __ldcg(&a.totals[0]);
-    while (true) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(&a.totals[1], 32u);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n) break;
-        unsigned k = base + lane;
-        if (k < n) trace_pixel(a, __ldg(&a.queue[k]));
-    }
-}
+__global__ void __launch_bounds__(256) k_resolve(TraceArgs a) { resolve_body(a, blockIdx.x); }
 
 TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
-                     unsigned* st, const uint8_t* spp, const unsigned* queue, unsigned* totals, float* rt, float* rec,
+                     unsigned* st, const uint8_t* spp, const ViewWs& w, float* rt, float* rec,
                      const unsigned* ray_off) {
     TraceArgs a;
     a.bvh = b->view();
@@ -257,10 +424,15 @@ TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens*
     a.miss_dist = p->miss_dist;
     a.key = make_uint2(p->seed, (unsigned)p->view * 65536u + (unsigned)p->frame);
     a.cap = p->trav_cap > 0 ? p->trav_cap : 64 * (b->n_nodes + b->n_tris) + 64;
+    a.smax = p->spp_max;
     a.status = st;
     a.spp = spp;
-    a.queue = queue;
-    a.totals = totals;
+    a.queue = w.queue;
+    a.qoff = w.qoff;
+    a.ray_pix = w.ray_pix;
+    a.ray_s = w.ray_s;
+    a.totals = w.totals;
+    a.recs = w.rec;
     a.rt = reinterpret_cast<float4*>(rt);
     a.rec = reinterpret_cast<float4*>(rec);
     a.ray_off = ray_off;
@@ -280,12 +452,17 @@ __global__ void __launch_bounds__(256) k_scatter_batch(const ScatterArgs* __rest
     g.locate(blockIdx.x, v, bx, by);
     scatter_body(a[v], bx, by);
 }
+__global__ void __launch_bounds__(256) k_resolve_batch(const TraceArgs* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    resolve_body(a[v], bx);
+}
 
-// exclusive prefix of the views' queue lengths: gq[v] is the first entry of
-// view v in the concatenated queue, gq[n] the total; gq[n + 1] (the shared
-// queue head) is reset.  One block.
-__global__ void __launch_bounds__(1024) k_queue_prefix(const ScanArgs* __restrict__ a, int n,
-                                                       unsigned* __restrict__ gq) {
+// exclusive prefix of the views' ray counts: gq[v] is the first ray of view
+// v in the concatenated ray list, gq[n] the total; gq[n + 1] (the shared
+// fetch head) is reset.  One block.
+__global__ void __launch_bounds__(1024) k_ray_prefix(const ScanArgs* __restrict__ a, int n,
+                                                     unsigned* __restrict__ gq) {
     __shared__ unsigned wsum[32];
     __shared__ unsigned carry;
     if (threadIdx.x == 0) carry = 0;
@@ -293,7 +470,7 @@ __global__ void __launch_bounds__(1024) k_queue_prefix(const ScanArgs* __restric
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < n; base += 1024) {
         int v = base + threadIdx.x;
-        unsigned c = v < n ? __ldcg(&a[v].totals[0]) : 0u, x = c;
+        unsigned c = v < n ? __ldcg(&a[v].totals[2]) : 0u, x = c;
         for (int o = 1; o < 32; o <<= 1) {
             unsigned y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
@@ -321,39 +498,32 @@ __global__ void __launch_bounds__(1024) k_queue_prefix(const ScanArgs* __restric
     }
 }
 
-// persistent trace over the concatenated queues of all views: a warp takes
-// 32 * chunk entries per atomic; each entry finds its view by binary search
-// of gq and is traced exactly as the single-view kernel traces it
 template <int BS>
-__global__ void __launch_bounds__(BS) k_trace_batch(const TraceArgs* __restrict__ a, const unsigned* __restrict__ gq,
-                                                    int n, unsigned* head, int chunk) {
-    const int lane = threadIdx.x & 31;
-    const unsigned total = __ldcg(&gq[n]);
-    const unsigned step = 32u * (unsigned)chunk;
-    while (true) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(head, step);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= total) break;
-        for (int c = 0; c < chunk; ++c) {
-            unsigned k = base + 32u * (unsigned)c + (unsigned)lane;
-            if (k >= total) break;
-            int lo = 0, hi = n - 1;  // last view with gq[v] <= k
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (__ldg(&gq[mid]) <= k) lo = mid;
-                else hi = mid - 1;
-            }
-            const TraceArgs& av = a[lo];
-            trace_pixel(av, __ldg(&av.queue[k - __ldg(&gq[lo])]));
-        }
-    }
+int rays_occupancy(bool batch, int* nb) {
+    cudaError_t e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_rays_batch<BS>, BS, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_rays<BS>, BS, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "trace: occupancy");
+    if (*nb < 1) *nb = 1;
+    return HDOF_OK;
 }
 
-template <int BS>
-int trace_batch_occupancy(int* nb) {
-    HDOF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_batch<BS>, BS, 0), "batched trace: occupancy");
-    if (*nb < 1) *nb = 1;
+// resident grid of the persistent trace (cached per device, block size and form)
+int rays_grid(bool batch, int block, int* blocks) {
+    static int cache[64][2][3] = {};
+    int dev = 0;
+    HDOF_CUDA(cudaGetDevice(&dev), "trace: device");
+    const int bi = block == 64 ? 0 : (block == 256 ? 2 : 1);
+    int nb = 0, rc = HDOF_OK;
+    if (dev >= 0 && dev < 64 && cache[dev][batch][bi]) {
+        nb = cache[dev][batch][bi];
+    } else {
+        if (bi == 0) rc = rays_occupancy<64>(batch, &nb);
+        else if (bi == 2) rc = rays_occupancy<256>(batch, &nb);
+        else rc = rays_occupancy<128>(batch, &nb);
+        if (rc) return rc;
+        if (dev >= 0 && dev < 64) cache[dev][batch][bi] = nb;
+    }
+    *blocks = sm_count() * nb;
     return HDOF_OK;
 }
 
@@ -362,7 +532,7 @@ int trace_batch_occupancy(int* nb) {
 size_t count_args_size() { return sizeof(CountArgs); }
 void count_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
     const int W = v.cam.width, H = v.cam.height, ntx = (W + TB - 1) / TB;
-    *reinterpret_cast<CountArgs*>(dst) = CountArgs{v.spp, W, H, ntx, w.counts};
+    *reinterpret_cast<CountArgs*>(dst) = CountArgs{v.spp, W, H, ntx, v.params.spp_max, w.counts};
     *gx = ntx;
     *gy = (H + TB - 1) / TB;
 }
@@ -382,7 +552,9 @@ void scan_launch_batch(const void* args, int n, cudaStream_t s) {
 size_t scatter_args_size() { return sizeof(ScatterArgs); }
 void scatter_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
     const int W = v.cam.width, H = v.cam.height, ntx = (W + TB - 1) / TB;
-    *reinterpret_cast<ScatterArgs*>(dst) = ScatterArgs{v.spp, W, H, ntx, w.offsets, w.roffsets, w.queue, nullptr};
+    *reinterpret_cast<ScatterArgs*>(dst) =
+        ScatterArgs{v.spp, W, H, ntx, v.params.spp_max, w.offsets, w.roffsets, w.queue, w.qoff, w.ray_pix, w.ray_s,
+                    nullptr};
     *gx = ntx;
     *gy = (H + TB - 1) / TB;
 }
@@ -391,35 +563,39 @@ void scatter_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_
 }
 
 size_t trace_args_size() { return sizeof(TraceArgs); }
-void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst) {
-    *reinterpret_cast<TraceArgs*>(dst) =
-        trace_args(v.bvh, &v.cam, &v.lens, &v.params, st, v.spp, w.queue, w.totals, v.rt, nullptr, nullptr);
+void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst, int* gx, int* gy) {
+    *reinterpret_cast<TraceArgs*>(dst) = trace_args(v.bvh, &v.cam, &v.lens, &v.params, st, v.spp, w, v.rt, nullptr,
+                                                    nullptr);
+    *gx = (v.cam.width * v.cam.height + 255) / 256;  // resolve: one thread per possible queue entry
+    *gy = 1;
 }
-int trace_batch_grid(int block, int* blocks) {
-    int nb = 1, rc;
-    if (block == 64) rc = trace_batch_occupancy<64>(&nb);
-    else if (block == 256) rc = trace_batch_occupancy<256>(&nb);
-    else rc = trace_batch_occupancy<128>(&nb);
-    if (rc) return rc;
-    *blocks = sm_count() * nb;
-    return HDOF_OK;
-}
+int trace_batch_grid(int block, int* blocks) { return rays_grid(true, block, blocks); }
 
-int trace_launch_batch(const void* scan_args, const void* trace_args, int n, unsigned* gq, int block, int chunk,
-                       int blocks, cudaStream_t s) {
-    k_queue_prefix<<<1, 1024, 0, s>>>(static_cast<const ScanArgs*>(scan_args), n, gq);
-    HDOF_LAUNCHED("batched trace: queue prefix");
+int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid resolve, int resolve_blocks, int n,
+                       unsigned* gq, int block, int refill, int blocks, cudaStream_t s) {
+    k_ray_prefix<<<1, 1024, 0, s>>>(static_cast<const ScanArgs*>(scan_args), n, gq);
+    HDOF_LAUNCHED("batched trace: ray prefix");
     const TraceArgs* a = static_cast<const TraceArgs*>(trace_args);
-    if (block == 64) k_trace_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, chunk);
-    else if (block == 256) k_trace_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, chunk);
-    else k_trace_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+    if (block == 64) k_trace_rays_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, refill);
+    else if (block == 256) k_trace_rays_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, refill);
+    else k_trace_rays_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, refill);
     HDOF_LAUNCHED("batched trace");
+    k_resolve_batch<<<resolve_blocks, 256, 0, s>>>(a, resolve);
+    HDOF_LAUNCHED("batched trace: resolve");
     return HDOF_OK;
 }
 
 }  // namespace hdof
 
 using namespace hdof;
+
+// launch shape of the single-view trace (the batched frame's is tuned)
+#ifndef HDOF_TRACE_BLOCK
+#define HDOF_TRACE_BLOCK 128
+#endif
+#ifndef HDOF_TRACE_REFILL
+#define HDOF_TRACE_REFILL 8
+#endif
 
 extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
                           const uint8_t* spp, float* rt, uint32_t* stats, float* rec, uint32_t* ray_off,
@@ -434,34 +610,30 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
     HDOF_CHECK_ARG(!rec == !ray_off, "hdof_trace: rec and ray_off go together");
     const int W = cam->width, H = cam->height;
     WsLayout L = ws_layout(W, H, p);
-    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.trace_counts + L.trace_queue,
-                   "hdof_trace: workspace of %zu bytes < %zu", workspace_bytes, L.trace_counts + L.trace_queue);
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.trace, "hdof_trace: workspace of %zu bytes < %zu",
+                   workspace_bytes, L.trace);
     unsigned* st = status_ptr();
     HDOF_CHECK_ARG(st, "hdof_trace: no status word on this device");
     cudaStream_t s = as_stream(stream);
+    hdof_view v = {};
+    v.cam = *cam;
+    v.params = *p;
+    v.workspace = workspace;
+    const ViewWs w = view_ws(v);
     const int ntx = (W + TB - 1) / TB, nty = (H + TB - 1) / TB, ntiles = ntx * nty;
-    unsigned* counts = static_cast<unsigned*>(workspace);            // [2 * ntiles]
-    unsigned* offsets = counts + 2 * ntiles;                        // [ntiles]
-    unsigned* roffsets = offsets + ntiles;                          // [ntiles]
-    unsigned* totals = roffsets + ntiles;                           // [4]
-    unsigned* queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) + L.trace_counts);
     dim3 tg(ntx, nty);
-    k_count<<<tg, 256, 0, s>>>(CountArgs{spp, W, H, ntx, counts});
-    k_scan<<<1, 1024, 0, s>>>(ScanArgs{counts, ntiles, offsets, roffsets, totals, stats});
-    k_scatter<<<tg, 256, 0, s>>>(ScatterArgs{spp, W, H, ntx, offsets, roffsets, queue, ray_off});
+    k_count<<<tg, 256, 0, s>>>(CountArgs{spp, W, H, ntx, p->spp_max, w.counts});
+    k_scan<<<1, 1024, 0, s>>>(ScanArgs{w.counts, ntiles, w.offsets, w.roffsets, w.totals, stats});
+    k_scatter<<<tg, 256, 0, s>>>(
+        ScatterArgs{spp, W, H, ntx, p->spp_max, w.offsets, w.roffsets, w.queue, w.qoff, w.ray_pix, w.ray_s, ray_off});
     HDOF_LAUNCHED("hdof_trace: compaction");
 
-    TraceArgs a = trace_args(b, cam, lens, p, st, spp, queue, totals, rt, rec, ray_off);
-    static int occ[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !occ[dev]) {
-        int nb = 0;
-        HDOF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace, 128, 0), "hdof_trace: occupancy");
-        occ[dev] = nb > 0 ? nb : 1;
-    }
-    int blocks = sm_count() * ((dev >= 0 && dev < 64) ? occ[dev] : 4);
-    k_trace<<<blocks, 128, 0, s>>>(a);
+    TraceArgs a = trace_args(b, cam, lens, p, st, spp, w, rt, rec, ray_off);
+    int blocks = 0;
+    if ((rc = rays_grid(false, HDOF_TRACE_BLOCK, &blocks))) return rc;
+    k_trace_rays<HDOF_TRACE_BLOCK><<<blocks, HDOF_TRACE_BLOCK, 0, s>>>(a, HDOF_TRACE_REFILL);
     HDOF_LAUNCHED("hdof_trace: trace");
+    k_resolve<<<(W * H + 255) / 256, 256, 0, s>>>(a);
+    HDOF_LAUNCHED("hdof_trace: resolve");
     return HDOF_OK;
 }

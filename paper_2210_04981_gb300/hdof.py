@@ -71,7 +71,7 @@ class hdof_view(C.Structure):
 
 
 class hdof_tuning(C.Structure):
-    _fields_ = [("trace_block", C.c_int32), ("trace_chunk", C.c_int32), ("reserved", C.c_int32 * 2)]
+    _fields_ = [("trace_block", C.c_int32), ("trace_refill", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class hdof_post_state(C.Structure):
@@ -409,9 +409,9 @@ class Renderer:
 
 # ------------------------------------------------------ batched multi-view --
 
-def tuning(trace_block=128, trace_chunk=1) -> hdof_tuning:
+def tuning(trace_block=128, trace_refill=8) -> hdof_tuning:
     t = hdof_tuning()
-    t.trace_block, t.trace_chunk = int(trace_block), int(trace_chunk)
+    t.trace_block, t.trace_refill = int(trace_block), int(trace_refill)
     return t
 
 

@@ -63,12 +63,12 @@ def _assert_same(a: H.Renderer, b: H.Renderer, tag):
         assert eq(getattr(ha, name)[tr], getattr(hb, name)[tr]), f"{tag}: history {name}"
 
 
-@pytest.mark.parametrize("block,chunk", [(128, 1), (64, 4), (256, 2)])
-def test_batch_equals_single_view(small, block, chunk):
+@pytest.mark.parametrize("block,refill", [(128, 16), (64, 32), (256, 1)])
+def test_batch_equals_single_view(small, block, refill):
     scenes, bvhs, views = small
     rs = _singles(bvhs, views)
     b = H.Batch([bvhs[v.room] for v in views], [(v.width, v.height) for v in views], [v.params for v in views],
-                tune=H.tuning(block, chunk))
+                tune=H.tuning(block, refill))
     for k in range(3):
         _run_singles(rs, views, k)
         b.frame(*_frame_args(views, k))
@@ -85,7 +85,7 @@ def test_batch_graph_replay(small):
     scenes, bvhs, views = small
     rs = _singles(bvhs, views)
     b = H.Batch([bvhs[v.room] for v in views], [(v.width, v.height) for v in views], [v.params for v in views],
-                tune=H.tuning(128, 2))
+                tune=H.tuning(128, 24))
     # warm-up frame outside the capture (loads every kernel), then start over
     b.frame(*_frame_args(views, 0))
     H.hdof_sync()
@@ -143,7 +143,7 @@ def test_batch_64_views_full_workload(orc):
     bvhs = [bvh_of(s) for s in scenes]
     views = hi.batch_views(64)
     b = H.Batch([bvhs[v.room] for v in views], [(v.width, v.height) for v in views], [v.params for v in views],
-                tune=H.tuning(128, 1))
+                tune=H.tuning(128, 16))
     b.frame(*_frame_args(views, 0))
     H.hdof_sync()
     # single-view calls, a few views at a time (memory)
