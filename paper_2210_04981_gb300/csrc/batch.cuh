@@ -35,6 +35,20 @@ struct BatchGrid {
     }
 };
 
+// A block's launch record, copied once from the table into shared memory:
+// the body then reads it like kernel parameters instead of through a global
+// pointer (which, under a tight register bound, the compiler re-loads
+// inside hot loops).  Every thread of the block must call it.
+template <class T>
+__device__ __forceinline__ const T& batch_record(const T* __restrict__ tab, int v) {
+    static_assert(sizeof(T) % 4 == 0, "launch records are word-sized");
+    __shared__ __align__(16) unsigned s_rec[sizeof(T) / 4];
+    const unsigned* src = reinterpret_cast<const unsigned*>(tab + v);
+    for (int k = threadIdx.x; k < (int)(sizeof(T) / 4); k += blockDim.x) s_rec[k] = __ldg(src + k);
+    __syncthreads();
+    return *reinterpret_cast<const T*>(s_rec);
+}
+
 // one view's workspace carved as the single-view calls carve it (the stages
 // run one after another, so their regions overlap as they do there)
 struct ViewWs {

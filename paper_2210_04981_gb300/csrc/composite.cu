@@ -71,7 +71,7 @@ using CompositeF32 = CompositeArgs<float4, float4>;
 __global__ void __launch_bounds__(256) k_composite_batch(const CompositeF32* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    composite_body(a[v], bx, by);
+    composite_body(batch_record(a, v), bx, by);
 }
 
 template <class ND, class COL>

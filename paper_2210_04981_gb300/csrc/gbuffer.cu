@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(128) k_gbuffer(GbufArgs<ND, COL> a) {
 __global__ void __launch_bounds__(128) k_gbuffer_batch(const GbufArgs<float4, float4>* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    gbuffer_body(a[v], bx, by);
+    gbuffer_body(batch_record(a, v), bx, by);
 }
 
 template <class ND, class COL>

@@ -260,12 +260,12 @@ int launch_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_p
 __global__ void __launch_bounds__(256) k_mask_edge_batch(const EdgeArgs<float4>* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    mask_edge_body(a[v], bx, by);
+    mask_edge_body(batch_record(a, v), bx, by);
 }
 __global__ void __launch_bounds__(256) k_mask_spp_batch(const SppArgs* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    mask_spp_body(a[v], bx, by);
+    mask_spp_body(batch_record(a, v), bx, by);
 }
 
 }  // namespace

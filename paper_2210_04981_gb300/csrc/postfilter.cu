@@ -14,8 +14,8 @@
 //   tile the largest r.  k_pf_gather: per tile the gather window is bounded
 //   by the largest radius among tiles that can reach it; every tap outside
 //   that window has zero weight, so the bounded gather equals the full one.
-//   Each thread gathers two horizontally adjacent pixels so every tap it
-//   loads serves both.
+//   Each thread gathers a 2x2 pixel block so every tap it loads serves four
+//   pixels; the per-tap arithmetic is branch-free (saturating adds).
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -28,6 +28,19 @@ namespace hdof {
 namespace {
 
 constexpr int TP = HDOF_TILE_PF;
+constexpr int GATHER_THREADS = 64;
+#ifndef HDOF_PF_MINB
+#define HDOF_PF_MINB 10  // resident gather blocks per SM the register budget targets
+#endif
+#ifndef HDOF_PF_UNROLL
+#define HDOF_PF_UNROLL 2  // unroll of the gather's tap loop
+#endif
+constexpr int PF_UNROLL = HDOF_PF_UNROLL;
+// Shared-memory carve-out (percent of the maximum) for the gather: the taps
+// are served from L1, so keep L1 large, but every resident block also holds
+// ~1 KB of driver-reserved shared memory; 8% (a 16 KB configuration) admits
+// up to 14 blocks, where the minimum configuration (8 KB) admits only 7.
+constexpr int GATHER_CARVEOUT = 8;
 constexpr int AREA_MAX = 16384;  // breakpoints for radii up to 127.5
 
 // (x_m, a(x_m), slope on [x_m, x_{m+1}], 0)
@@ -103,23 +116,6 @@ struct PfAcc {
     float ka, kb;
 };
 
-__device__ __forceinline__ void pf_tap(PfAcc& a, float d, const float4& e, const float4& c) {
-    float s = e.x - d;  // (r_q + 1/2) - d
-    if (s > 0.f) {
-        s = fminf(s, 1.f);
-        float an = s * e.y;
-        float af = s * e.z * clamp01(fmaf(-e.w, a.kb, a.ka));
-        a.Sn.x = fmaf(an, c.x, a.Sn.x);
-        a.Sn.y = fmaf(an, c.y, a.Sn.y);
-        a.Sn.z = fmaf(an, c.z, a.Sn.z);
-        a.Sf.x = fmaf(af, c.x, a.Sf.x);
-        a.Sf.y = fmaf(af, c.y, a.Sf.y);
-        a.Sf.z = fmaf(af, c.z, a.Sf.z);
-        a.Wn += an;
-        a.Wf += af;
-    }
-}
-
 template <class COL>
 __device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size_t pq, float4* aux) {
     float alpha = clamp01(a.Wn);
@@ -138,8 +134,6 @@ __device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size
     return make_float4(o.x, o.y, o.z, alpha);
 }
 
-// 128 threads per 16x16 tile; thread t gathers pixels (2 (t & 7), t >> 3) and
-// its right neighbour, so a warp covers a 16x4 pixel block.
 template <class COL>
 struct GatherArgs {
     const float4* prep;
@@ -151,6 +145,25 @@ struct GatherArgs {
     float4* aux;
 };
 
+// one tap into one target pixel, branch-free: s = clamp(r_q + 1/2 - d, 0, 1)
+// (zero outside the disk adds exact zeros)
+__device__ __forceinline__ void pf_acc(PfAcc& a, float d, const float4& e, const float4& c) {
+    const float s = __saturatef(e.x - d);
+    const float an = s * e.y;
+    const float af = s * e.z * __saturatef(fmaf(-e.w, a.kb, a.ka));
+    a.Sn.x = fmaf(an, c.x, a.Sn.x);
+    a.Sn.y = fmaf(an, c.y, a.Sn.y);
+    a.Sn.z = fmaf(an, c.z, a.Sn.z);
+    a.Sf.x = fmaf(af, c.x, a.Sf.x);
+    a.Sf.y = fmaf(af, c.y, a.Sf.y);
+    a.Sf.z = fmaf(af, c.z, a.Sf.z);
+    a.Wn += an;
+    a.Wf += af;
+}
+
+// 64 threads per 16x16 tile; thread t gathers the 2x2 pixel block at
+// (2 (t & 7), 2 (t >> 3)), so each loaded tap serves four pixels and a warp
+// covers a 16x8 pixel block.
 template <class COL>
 __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx, int ty) {
     const float4* __restrict__ prep = ar.prep;
@@ -176,50 +189,71 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
     }
     __syncthreads();
     const int G = s_win;
-    const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + (threadIdx.x >> 3);
+    const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + 2 * (threadIdx.x >> 3);
     if (i >= W || j >= H) return;
-    const bool two = i + 1 < W;
+    const bool right = i + 1 < W, down = j + 1 < H;
     const size_t pq = (size_t)j * W + i;
-    PfAcc a0, a1;
+    PfAcc a[4];  // (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1)
     {
-        const float zp0 = __ldg(&prep[pq].w), zp1 = two ? __ldg(&prep[pq + 1].w) : zp0;
-        a0.ka = a1.ka = 1.f + 1.f / kz_rel;  // k_z = clamp(ka - z_q kb), kb = 1 / (kz_rel z_p)
-        a0.kb = 1.f / (kz_rel * zp0);
-        a1.kb = 1.f / (kz_rel * zp1);
-        a0.Sn = a0.Sf = a1.Sn = a1.Sf = f3(0, 0, 0);
-        a0.Wn = a0.Wf = a1.Wn = a1.Wf = 0.f;
-    }
-    const int y0 = max(j - G, 0), y1 = min(j + G, H - 1), x0 = max(i - G, 0), x1 = min(i + 1 + G, W - 1);
-    for (int y = y0; y <= y1; ++y) {
-        const float dy2 = (float)((y - j) * (y - j));
-        const size_t qrow = (size_t)y * W;
-        for (int x = x0; x <= x1; ++x) {
-            float4 e = __ldg(&prep[qrow + x]);
-            const float dx = (float)(x - i);
-            float d0 = sqrt_approx(fmaf(dx, dx, dy2)), d1 = sqrt_approx(fmaf(dx - 1.f, dx - 1.f, dy2));
-            if (e.x > fminf(d0, d1)) {
-                float4 c = ld4(col + qrow + x);
-                pf_tap(a0, d0, e, c);
-                pf_tap(a1, d1, e, c);
-            }
+        const float ka = 1.f + 1.f / kz_rel;  // k_z = clamp(ka - z_q kb), kb = 1 / (kz_rel z_p)
+        const float z00 = __ldg(&prep[pq].w);
+        const float z10 = right ? __ldg(&prep[pq + 1].w) : z00;
+        const float z01 = down ? __ldg(&prep[pq + W].w) : z00;
+        const float z11 = right && down ? __ldg(&prep[pq + W + 1].w) : z00;
+        const float zs[4] = {z00, z10, z01, z11};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[k].ka = ka;
+            a[k].kb = 1.f / (kz_rel * zs[k]);
+            a[k].Sn = a[k].Sf = f3(0, 0, 0);
+            a[k].Wn = a[k].Wf = 0.f;
         }
     }
-    pp[pq] = pf_finish(a0, col, pq, aux);
-    if (two) pp[pq + 1] = pf_finish(a1, col, pq + 1, aux);
+    // every reaching source has r + 1/2 <= G, so only taps closer than G to
+    // one of the four pixels can weigh: per source row, the columns of that
+    // disk (squared distances are exact integers in float)
+    const int y0 = max(j - G, 0), y1 = min(j + 1 + G, H - 1);
+    const float G2 = (float)(G * G);
+    for (int y = y0; y <= y1; ++y) {
+        const float dy = (float)(y - j);
+        const float dy0 = dy * dy, dy1 = (dy - 1.f) * (dy - 1.f);
+        const float rem = G2 - fminf(dy0, dy1);  // > 0: |dy| <= G for the nearer row
+        const int w = (int)ceilf(sqrtf(rem));
+        const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
+        const size_t qrow = (size_t)y * W;
+        float dx = (float)(x0 - i);
+#pragma unroll PF_UNROLL
+        for (int x = x0; x <= x1; ++x, dx += 1.f) {
+            const float4 e = __ldg(&prep[qrow + x]);
+            const float4 c = ld4(col + qrow + x);
+            const float dx0 = dx * dx, dx1 = (dx - 1.f) * (dx - 1.f);
+            pf_acc(a[0], sqrt_approx(dx0 + dy0), e, c);
+            pf_acc(a[1], sqrt_approx(dx1 + dy0), e, c);
+            pf_acc(a[2], sqrt_approx(dx0 + dy1), e, c);
+            pf_acc(a[3], sqrt_approx(dx1 + dy1), e, c);
+        }
+    }
+    pp[pq] = pf_finish(a[0], col, pq, aux);
+    if (right) pp[pq + 1] = pf_finish(a[1], col, pq + 1, aux);
+    if (down) pp[pq + W] = pf_finish(a[2], col, pq + W, aux);
+    if (right && down) pp[pq + W + 1] = pf_finish(a[3], col, pq + W + 1, aux);
 }
 
 template <class COL>
-__global__ void __launch_bounds__(128, 6) k_pf_gather(GatherArgs<COL> a) { pf_gather_body(a, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(GATHER_THREADS, HDOF_PF_MINB) k_pf_gather(GatherArgs<COL> a) {
+    pf_gather_body(a, blockIdx.x, blockIdx.y);
+}
 
 __global__ void __launch_bounds__(256) k_pf_prep_batch(const PrepArgs<float4>* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    pf_prep_body(a[v], bx, by);
+    pf_prep_body(batch_record(a, v), bx, by);
 }
-__global__ void __launch_bounds__(128, 6) k_pf_gather_batch(const GatherArgs<float4>* __restrict__ a, BatchGrid g) {
+__global__ void __launch_bounds__(GATHER_THREADS, HDOF_PF_MINB)
+    k_pf_gather_batch(const GatherArgs<float4>* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    pf_gather_body(a[v], bx, by);
+    pf_gather_body(batch_record(a, v), bx, by);
 }
 
 // tiles of reach around a tile: radii up to r_max (+1/2 soft edge) span this many
@@ -336,15 +370,15 @@ int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p,
             PrepArgs<half4s>{static_cast<const half4s*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax});
     HDOF_LAUNCHED("post-filter prep");
     int kt = gather_tiles(p->r_max);
-    // the taps are served from L1: prefer the largest L1 carve-out
+    // the taps are served from L1: a small shared-memory carve-out
     if (in->dtype_col == HDOF_F32) {
-        cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        k_pf_gather<float4><<<grid, 128, 0, s>>>(GatherArgs<float4>{prep, static_cast<const float4*>(in->col), tmax,
+        cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
+        k_pf_gather<float4><<<grid, GATHER_THREADS, 0, s>>>(GatherArgs<float4>{prep, static_cast<const float4*>(in->col), tmax,
                                                                     W, H, ntx, nty, kt, p->kz_rel,
                                                                     reinterpret_cast<float4*>(pp), aux});
     } else {
-        cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        k_pf_gather<bf164s><<<grid, 128, 0, s>>>(GatherArgs<bf164s>{prep, static_cast<const bf164s*>(in->col), tmax,
+        cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
+        k_pf_gather<bf164s><<<grid, GATHER_THREADS, 0, s>>>(GatherArgs<bf164s>{prep, static_cast<const bf164s*>(in->col), tmax,
                                                                     W, H, ntx, nty, kt, p->kz_rel,
                                                                     reinterpret_cast<float4*>(pp), aux});
     }
@@ -394,10 +428,10 @@ void pf_gather_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, i
                            gather_tiles(v.params.r_max), v.params.kz_rel, reinterpret_cast<float4*>(v.pp), nullptr};
     *gx = ntx;
     *gy = nty;
-    cudaFuncSetAttribute(k_pf_gather_batch, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(k_pf_gather_batch, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
 }
 void pf_gather_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
-    k_pf_gather_batch<<<blocks, 128, 0, s>>>(static_cast<const GatherArgs<float4>*>(args), g);
+    k_pf_gather_batch<<<blocks, GATHER_THREADS, 0, s>>>(static_cast<const GatherArgs<float4>*>(args), g);
 }
 
 }  // namespace hdof

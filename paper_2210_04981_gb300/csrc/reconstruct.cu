@@ -188,7 +188,8 @@ struct TemporalBatch {
 __global__ void __launch_bounds__(256) k_temporal_batch(const TemporalBatch* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    temporal_body(a[v].t, a[v].nd, bx, by);
+    const TemporalBatch& r = batch_record(a, v);
+    temporal_body(r.t, r.nd, bx, by);
 }
 
 struct SpatialArgs {
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(256) k_spatial(SpatialArgs a) { spatial_body(a
 __global__ void __launch_bounds__(256) k_spatial_batch(const SpatialArgs* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    spatial_body(a[v], bx, by);
+    spatial_body(batch_record(a, v), bx, by);
 }
 
 TemporalArgs temporal_args(const float* rt, const hdof_gbuf* in, const uint8_t* spp, const hdof_camera* cam,

@@ -444,18 +444,18 @@ TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens*
 __global__ void __launch_bounds__(256) k_count_batch(const CountArgs* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    count_body(a[v], bx, by);
+    count_body(batch_record(a, v), bx, by);
 }
 __global__ void __launch_bounds__(1024) k_scan_batch(const ScanArgs* __restrict__ a) { scan_body(a[blockIdx.x]); }
 __global__ void __launch_bounds__(256) k_scatter_batch(const ScatterArgs* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    scatter_body(a[v], bx, by);
+    scatter_body(batch_record(a, v), bx, by);
 }
 __global__ void __launch_bounds__(256) k_resolve_batch(const TraceArgs* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    resolve_body(a[v], bx);
+    resolve_body(batch_record(a, v), bx);
 }
 
 // exclusive prefix of the views' ray counts: gq[v] is the first ray of view
