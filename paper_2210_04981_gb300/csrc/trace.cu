@@ -248,10 +248,19 @@ struct ManyViews {
     }
 };
 
-// Persistent ray-level trace with dynamic fetch.  Per lane: one ray's
-// traversal state (same node/leaf steps, stack discipline and tie rule as
-// closest_hit).  The fetch is warp-uniform: every lane takes part in the
-// ballots; idle lanes are predicated off during the steps.
+// Persistent ray-level trace with dynamic fetch and speculative traversal.
+// Per lane: one ray's traversal state (same node steps, stack discipline and
+// tie rule as closest_hit) plus one postponed leaf.  A lane that reaches a
+// leaf parks it and keeps descending; the warp runs node steps until no lane
+// is still searching for a leaf, then tests every parked leaf together
+// (Aila and Laine's speculative while-while), so the node and leaf code do not
+// both run on almost every iteration.  Testing a leaf later than it was
+// reached only delays culling: the closest hit is the same.  The fetch is
+// warp-uniform: every lane takes part in the ballots; idle lanes are
+// predicated off during the steps.
+constexpr int DONE_REF = 0x7fffffff;  // stack exhausted
+constexpr int NO_LEAF = 0;            // empty leaf slot (leaf references are negative)
+
 template <class Src>
 __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, unsigned* head, int refill) {
     const unsigned FULL = 0xffffffffu;
@@ -259,7 +268,7 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     bool live = false, done = false;
-    int v = 0, cur = 0, sp = 0, steps = 0;
+    int v = 0, cur = 0, leaf = NO_LEAF, sp = 0, steps = 0;
     unsigned r = 0;
     Ray ray;
     Shear sh;
@@ -286,6 +295,11 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
                     h.id = 0x7fffffff;
                     h.b0 = h.b1 = h.b2 = 0.f;
                     cur = a.bvh.root;
+                    leaf = NO_LEAF;
+                    if (cur < 0) {  // the whole tree is one leaf
+                        leaf = cur;
+                        cur = DONE_REF;
+                    }
                     sp = 0;
                     steps = 0;
                     live = true;
@@ -296,12 +310,13 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
         }
         if (!__any_sync(FULL, live)) break;
         while (true) {
-            if (live) {
-                const TraceArgs& a = src.at(v);
-                const BvhView& bvh = a.bvh;
-                bool fin = false;
-                if (cur >= 0) {
-                    const Node* n = bvh.nodes + cur;
+            // node phase: descend until no live lane is still looking for a leaf
+            while (true) {
+                // a lane past the step cap stops stepping (it is finished below)
+                const bool can_step = live && cur >= 0 && cur != DONE_REF && steps <= src.at(v).cap;
+                if (can_step) {
+                    const TraceArgs& a = src.at(v);
+                    const Node* n = a.bvh.nodes + cur;
                     float4 na = __ldg(&n->xy0), nb = __ldg(&n->xy1), nz = __ldg(&n->z01);
                     int4 ch = __ldg(&n->child);
                     float t0 = slab(ray, na.x, na.y, na.z, na.w, nz.x, nz.y, h.t);
@@ -316,22 +331,39 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
                         cur = ch.x;
                     } else if (h1) {
                         cur = ch.y;
-                    } else if (sp == 0) {
-                        fin = true;
                     } else {
-                        cur = stack[--sp];
+                        cur = sp ? stack[--sp] : DONE_REF;
                     }
-                } else {
-                    int e = ~cur, first = e >> 3, count = (e & 7) + 1;
-                    for (int k = 0; k < count; ++k) hit_tri(bvh, first + k, ray.o, sh, h);
-                    if (sp == 0) fin = true;
-                    else cur = stack[--sp];
+                    if (cur < 0 && leaf == NO_LEAF) {  // park the leaf, keep descending
+                        leaf = cur;
+                        cur = sp ? stack[--sp] : DONE_REF;
+                    }
+                    ++steps;
                 }
-                if (++steps > a.cap) {
+                const bool searching = can_step && leaf == NO_LEAF && cur >= 0 && cur != DONE_REF;
+                if (!__any_sync(FULL, searching)) break;
+            }
+            // leaf phase: every parked leaf; a leaf waiting in cur moves into the slot
+            if (live && leaf != NO_LEAF) {
+                const TraceArgs& a = src.at(v);
+                int e = ~leaf, first = e >> 3, count = (e & 7) + 1;
+                for (int k = 0; k < count; ++k) hit_tri(a.bvh, first + k, ray.o, sh, h);
+                leaf = NO_LEAF;
+                if (cur < 0) {
+                    leaf = cur;
+                    cur = sp ? stack[--sp] : DONE_REF;
+                }
+                ++steps;
+            }
+            if (live) {
+                const TraceArgs& a = src.at(v);
+                bool fin = leaf == NO_LEAF && cur == DONE_REF;
+                if (steps > a.cap) {
                     atomicOr(a.status, HDOF_STATUS_TIMEOUT);
                     fin = true;
                 }
                 if (fin) {
+                    const BvhView& bvh = a.bvh;
                     for (int k = 0; k < bvh.big_count; ++k) {
                         float4 lo = __ldg(&bvh.big_box[2 * k]), hi = __ldg(&bvh.big_box[2 * k + 1]);
                         if (slab(ray, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, h.t) < INF)
