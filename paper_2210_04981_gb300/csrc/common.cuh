@@ -207,6 +207,14 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     return r;
 }
 
+// hardware approximate square root (relative error ~2^-22): for tap
+// distances that only enter soft weights clamp(r + 1/2 - d, 0, 1)
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Slab test of one box; returns entry distance (or +inf on a miss).  The exit
 // distance is widened by 2 gamma_3 (Ize 2013) so no box the ray touches is culled.
 __device__ __forceinline__ float slab(const Ray& r, float lx, float hx, float ly, float hy, float lz,

@@ -102,14 +102,6 @@ __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND>& a, int bx, int 
 template <class ND>
 __global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND> a) { pf_prep_body(a, blockIdx.x, blockIdx.y); }
 
-// hardware approximate square root (MUFU, relative error ~2^-22): the tap
-// distance only enters the soft weight clamp(r + 1/2 - d, 0, 1)
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 struct PfAcc {
     float3 Sn, Sf;
     float Wn, Wf;

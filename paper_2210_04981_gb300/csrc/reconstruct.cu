@@ -210,30 +210,52 @@ __device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int b
     const float r_s = a.r_s, var_ref = a.var_ref;
     float4* __restrict__ crec = a.crec;
     float4* __restrict__ aux = a.aux;
-    // warp = 8x4 pixel block, block = 16x16 pixels
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int i = bx * 16 + (w & 1) * 8 + (l & 7), j = by * 16 + (w >> 1) * 4 + (l >> 3);
-    if (i >= W || j >= H) return;
+    // block = one 16x16 tile; its traced pixels are compacted (row-major) so
+    // that every warp which runs gathers for traced pixels only
+    __shared__ unsigned char s_list[256];
+    __shared__ int s_wcnt[8];
+    const int t = threadIdx.x, lane = t & 31;
+    bool traced = false;
+    {
+        const int i0 = bx * 16 + (t & 15), j0 = by * 16 + (t >> 4);
+        if (i0 < W && j0 < H) traced = __ldg(&crt[(size_t)j0 * W + i0].w) >= 0.f;
+    }
+    const unsigned tm = __ballot_sync(0xffffffffu, traced);
+    if (lane == 0) s_wcnt[t >> 5] = __popc(tm);
+    __syncthreads();
+    int off = 0, n = 0;
+    for (int k = 0; k < 8; ++k) {
+        off += k < (t >> 5) ? s_wcnt[k] : 0;
+        n += s_wcnt[k];
+    }
+    if (traced) s_list[off + __popc(tm & ((1u << lane) - 1u))] = (unsigned char)t;
+    __syncthreads();
+    if (t >= n) return;
+    const int li = s_list[t];
+    const int i = bx * 16 + (li & 15), j = by * 16 + (li >> 4);
     const size_t q = (size_t)j * W + i;
     const float4 cp = __ldg(&crt[q]);
-    if (cp.w < 0.f) return;  // untraced
     const float rp = fminf(cp.w * 0.5f, r_s);
     const int K = (int)ceilf(rp + 0.5f);
+    // a tap weighs only if d < rp + 1/2 <= K: per row, the columns of that disk
     float3 S = f3(0, 0, 0);
     float Ws = 0.f;
-    const int y0 = max(j - K, 0), y1 = min(j + K, H - 1), x0 = max(i - K, 0), x1 = min(i + K, W - 1);
+    const int y0 = max(j - K, 0), y1 = min(j + K, H - 1);
     for (int y = y0; y <= y1; ++y) {
-        float dy = (float)(y - j);
-        for (int x = x0; x <= x1; ++x) {
-            float dx = (float)(x - i);
-            float4 c = __ldg(&crt[(size_t)y * W + x]);
-            if (c.w < 0.f) continue;
-            float d = sqrtf(fmaf(dx, dx, dy * dy));
+        const float dy = (float)(y - j), dy2 = dy * dy;
+        const int wr = (int)ceilf(sqrtf((float)(K * K) - dy2));
+        const int x0 = max(i - wr, 0), x1 = min(i + wr, W - 1);
+        const float4* row = crt + (size_t)y * W;
+        float dx = (float)(x0 - i);
+        for (int x = x0; x <= x1; ++x, dx += 1.f) {
+            const float4 c = __ldg(&row[x]);
+            const float d = sqrt_approx(fmaf(dx, dx, dy2));
             float wq = soft_step(rp - d) * soft_step(fminf(c.w * 0.5f, r_s) - d);
-            if (wq > 0.f) {
-                S = S + wq * f3(c.x, c.y, c.z);
-                Ws += wq;
-            }
+            wq = c.w < 0.f ? 0.f : wq;  // untraced neighbours carry no sample
+            S.x = fmaf(wq, c.x, S.x);
+            S.y = fmaf(wq, c.y, S.y);
+            S.z = fmaf(wq, c.z, S.z);
+            Ws += wq;
         }
     }
     float2 m = __ldg(&mom[q]);
