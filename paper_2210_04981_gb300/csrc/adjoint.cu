@@ -633,7 +633,7 @@ using namespace hdof;
 
 extern "C" size_t hdof_post_workspace_bytes(int32_t width, int32_t height, const hdof_params* p) {
     if (width <= 0 || height <= 0) return 0;
-    size_t pf = ws_layout(width, height, p).pf_prep + ws_layout(width, height, p).pf_tiles;
+    size_t pf = ws_layout(width, height, p).pf;
     size_t bw = bwd_layout(width, height, nullptr).bytes;
     return pf > bw ? pf : bw;
 }

@@ -123,11 +123,15 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     l.trace_ray_s = align256(nray);
     l.trace_rec = align256(nray * sizeof(float4));
     l.trace = l.trace_counts + l.trace_queue + l.trace_qoff + l.trace_ray_pix + l.trace_ray_s + l.trace_rec;
-    l.pf_prep = align256(npx * sizeof(float4));
-    l.pf_tiles = align256(ptiles * sizeof(float));
+    l.pf_nrec = align256(npx * sizeof(float4));
+    l.pf_frec = align256(npx * sizeof(float4));
+    l.pf_rh = align256(npx * sizeof(float));
+    l.pf_zq = align256(npx * sizeof(float));
+    l.pf_tiles = align256(ptiles * sizeof(float2));
+    l.pf = l.pf_nrec + l.pf_frec + l.pf_rh + l.pf_zq + l.pf_tiles;
     size_t mask = l.mask_tiles;
     size_t trace = l.trace;
-    size_t pf = l.pf_prep + l.pf_tiles;
+    size_t pf = l.pf;
     l.total = mask > trace ? mask : trace;
     if (pf > l.total) l.total = pf;
     return l;

@@ -62,8 +62,11 @@ struct ViewWs {
     unsigned* ray_pix;   // [W * H * spp_max] pixel of each ray
     uint8_t* ray_s;      // [W * H * spp_max] sample index of each ray
     float4* rec;         // [W * H * spp_max] (radiance, hit distance) of each ray
-    float4* prep;        // post-filter per-pixel record
-    float* tmax;         // post-filter per-tile radius
+    float4* nrec;        // post-filter near-layer record per pixel
+    float4* frec;        // post-filter far-layer record per pixel
+    float* rh;           // post-filter r + 1/2 per pixel
+    float* zq;           // post-filter view depth per pixel
+    float2* tmax;        // post-filter per-tile radii (near, far)
 };
 
 inline ViewWs view_ws(const hdof_view& v) {
@@ -82,8 +85,12 @@ inline ViewWs view_ws(const hdof_view& v) {
     w.ray_pix = reinterpret_cast<unsigned*>(base + (o += L.trace_qoff));
     w.ray_s = reinterpret_cast<uint8_t*>(base + (o += L.trace_ray_pix));
     w.rec = reinterpret_cast<float4*>(base + (o += L.trace_ray_s));
-    w.prep = reinterpret_cast<float4*>(base);
-    w.tmax = reinterpret_cast<float*>(base + L.pf_prep);
+    size_t f = 0;
+    w.nrec = reinterpret_cast<float4*>(base + f);
+    w.frec = reinterpret_cast<float4*>(base + (f += L.pf_nrec));
+    w.rh = reinterpret_cast<float*>(base + (f += L.pf_frec));
+    w.zq = reinterpret_cast<float*>(base + (f += L.pf_rh));
+    w.tmax = reinterpret_cast<float2*>(base + (f += L.pf_zq));
     return w;
 }
 

@@ -63,8 +63,12 @@ struct WsLayout {
     size_t trace_ray_s;     // uint8 per possible ray: its sample index
     size_t trace_rec;       // float4 per possible ray: radiance, hit distance
     size_t trace;           // sum of the trace regions (laid out in this order)
-    size_t pf_prep;         // float4 per pixel
-    size_t pf_tiles;        // float per 16x16 tile
+    size_t pf_nrec;         // float4 per pixel: near-layer record
+    size_t pf_frec;         // float4 per pixel: far-layer record
+    size_t pf_rh;           // float per pixel: r + 1/2
+    size_t pf_zq;           // float per pixel: view depth
+    size_t pf_tiles;        // float2 per 16x16 tile
+    size_t pf;              // sum of the post-filter regions (laid out in this order)
     size_t total;
 };
 WsLayout ws_layout(int W, int H, const hdof_params* p);

@@ -10,10 +10,12 @@
 // |o| +- 1/2; a table of its breakpoints is built once per device and
 // evaluated by binary search, which is exact up to float rounding.
 //
-// k_pf_prep: per pixel (r + 1/2, w_near/a, (1-w_near)/a, z) and per 16x16
-//   tile the largest r.  k_pf_gather: per tile the gather window is bounded
-//   by the largest radius among tiles that can reach it; every tap outside
-//   that window has zero weight, so the bounded gather equals the full one.
+// k_pf_prep: per pixel r + 1/2, z and the premultiplied near and far layer
+//   records (c w/a, w/a); per 16x16 tile the largest r feeding each layer.
+// k_pf_gather: near and far are gathered in two loops, each bounded per tile
+//   by the largest radius among the tiles whose pixels feed that layer and
+//   can reach it, and per source row to the columns of that disk; every tap
+//   outside has zero weight, so the bounded gathers equal the full ones.
 //   Each thread gathers a 2x2 pixel block so every tap it loads serves four
 //   pixels; the per-tap arithmetic is branch-free (saturating adds).
 #include <algorithm>
@@ -58,49 +60,64 @@ __device__ __forceinline__ float disk_area(float r) {
     return fmaf(e.z, r - e.x, e.y);
 }
 
-template <class ND>
+// Per source pixel q the gather reads r_q + 1/2, z_q and two premultiplied
+// layer records (c_q w/a, w/a) with w = w_near(q) for the near layer and
+// 1 - w_near(q) for the far layer; per 16x16 tile, the largest r among its
+// pixels that feed each layer (-1: none).  Outside the thin focus zone a
+// pixel feeds one layer only, so near and far are gathered in separate loops
+// with their own windows (in the workloads here the far field's blur is
+// small and the near field's large).
+template <class ND, class COL>
 struct PrepArgs {
     const ND* nd;
+    const COL* col;
     int W, H;
     Coc coc;
     float rmax;
     int ntx;
-    float4* prep;
-    float* tmax;
+    float* rh;      // r + 1/2
+    float* zq;      // view depth
+    float4* nrec;   // (c w/a, w/a), near layer
+    float4* frec;   // (c (1-w)/a, (1-w)/a), far layer
+    float2* tmax;   // per tile: (max r feeding near, max r feeding far)
 };
 
-template <class ND>
-__device__ __forceinline__ void pf_prep_body(const PrepArgs<ND>& a, int bx, int by) {
-    const ND* __restrict__ nd = a.nd;
-    const int W = a.W, H = a.H, ntx = a.ntx;
-    const Coc coc = a.coc;
-    const float rmax = a.rmax;
-    float4* __restrict__ prep = a.prep;
-    float* __restrict__ tmax = a.tmax;
+template <class ND, class COL>
+__device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx, int by) {
+    const int W = a.W, H = a.H;
     int i = bx * TP + (threadIdx.x & 15), j = by * TP + (threadIdx.x >> 4);
-    float r = 0.f;
+    float rn = -1.f, rf = -1.f;
     if (i < W && j < H) {
         size_t q = (size_t)j * W + i;
-        float z = ldz(nd + q);
-        float c = coc(z);
-        r = fminf(fabsf(c) * 0.5f, rmax);
+        float z = ldz(a.nd + q);
+        float c = a.coc(z);
+        float r = fminf(fabsf(c) * 0.5f, a.rmax);
         float ia = 1.f / disk_area(r);
-        float wn = w_near(c);
-        prep[q] = make_float4(r + 0.5f, wn * ia, (1.f - wn) * ia, z);
+        float wn = w_near(c), an = wn * ia, af = (1.f - wn) * ia;
+        float4 col = ld4(a.col + q);
+        a.rh[q] = r + 0.5f;
+        a.zq[q] = z;
+        a.nrec[q] = make_float4(col.x * an, col.y * an, col.z * an, an);
+        a.frec[q] = make_float4(col.x * af, col.y * af, col.z * af, af);
+        rn = wn > 0.f ? r : -1.f;
+        rf = wn < 1.f ? r : -1.f;
     }
-    for (int o = 16; o; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-    __shared__ float red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    for (int o = 16; o; o >>= 1) {
+        rn = fmaxf(rn, __shfl_xor_sync(0xffffffffu, rn, o));
+        rf = fmaxf(rf, __shfl_xor_sync(0xffffffffu, rf, o));
+    }
+    __shared__ float2 red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(rn, rf);
     __syncthreads();
     if (threadIdx.x == 0) {
-        float m = red[0];
-        for (int k = 1; k < 8; ++k) m = fmaxf(m, red[k]);
-        tmax[by * ntx + bx] = m;
+        float2 m = red[0];
+        for (int k = 1; k < 8; ++k) m = make_float2(fmaxf(m.x, red[k].x), fmaxf(m.y, red[k].y));
+        a.tmax[by * a.ntx + bx] = m;
     }
 }
 
-template <class ND>
-__global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND> a) { pf_prep_body(a, blockIdx.x, blockIdx.y); }
+template <class ND, class COL>
+__global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND, COL> a) { pf_prep_body(a, blockIdx.x, blockIdx.y); }
 
 struct PfAcc {
     float3 Sn, Sf;
@@ -128,29 +145,75 @@ __device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size
 
 template <class COL>
 struct GatherArgs {
-    const float4* prep;
-    const COL* col;
-    const float* tmax;
+    const float* rh;
+    const float* zq;
+    const float4* nrec;
+    const float4* frec;
+    const COL* col;  // sharp colour (empty far layer)
+    const float2* tmax;
     int W, H, ntx, nty, kt;
     float kz_rel;
     float4* pp;
     float4* aux;
 };
 
-// one tap into one target pixel, branch-free: s = clamp(r_q + 1/2 - d, 0, 1)
-// (zero outside the disk adds exact zeros)
-__device__ __forceinline__ void pf_acc(PfAcc& a, float d, const float4& e, const float4& c) {
-    const float s = __saturatef(e.x - d);
-    const float an = s * e.y;
-    const float af = s * e.z * __saturatef(fmaf(-e.w, a.kb, a.ka));
-    a.Sn.x = fmaf(an, c.x, a.Sn.x);
-    a.Sn.y = fmaf(an, c.y, a.Sn.y);
-    a.Sn.z = fmaf(an, c.z, a.Sn.z);
-    a.Sf.x = fmaf(af, c.x, a.Sf.x);
-    a.Sf.y = fmaf(af, c.y, a.Sf.y);
-    a.Sf.z = fmaf(af, c.z, a.Sf.z);
-    a.Wn += an;
-    a.Wf += af;
+// one source into one target pixel, branch-free: s = clamp(r_q + 1/2 - d, 0, 1)
+// (zero outside the disk, and zero layer records, add exact zeros)
+__device__ __forceinline__ void acc_near(PfAcc& a, float d, float rh, const float4& n) {
+    const float s = __saturatef(rh - d);
+    a.Sn.x = fmaf(s, n.x, a.Sn.x);
+    a.Sn.y = fmaf(s, n.y, a.Sn.y);
+    a.Sn.z = fmaf(s, n.z, a.Sn.z);
+    a.Wn = fmaf(s, n.w, a.Wn);
+}
+__device__ __forceinline__ void acc_far(PfAcc& a, float d, float rh, float zq, const float4& f) {
+    const float t = __saturatef(rh - d) * __saturatef(fmaf(-zq, a.kb, a.ka));
+    a.Sf.x = fmaf(t, f.x, a.Sf.x);
+    a.Sf.y = fmaf(t, f.y, a.Sf.y);
+    a.Sf.z = fmaf(t, f.z, a.Sf.z);
+    a.Wf = fmaf(t, f.w, a.Wf);
+}
+
+// one layer's loop over a disk-shaped window of radius G around the 2x2
+// block at (i, j): every source feeding the layer within reach has
+// r + 1/2 <= G, so only taps closer than G to one of the four pixels can
+// weigh; per source row, the columns of that disk (squared distances are
+// exact integers in float)
+template <bool NEAR>
+__device__ __forceinline__ void pf_layer(PfAcc (&a)[4], int G, int i, int j, int W, int H,
+                                         const float* __restrict__ rh, const float* __restrict__ zq,
+                                         const float4* __restrict__ rec) {
+    if (G < 0) return;  // nothing within reach feeds this layer
+    const int y0 = max(j - G, 0), y1 = min(j + 1 + G, H - 1);
+    const float G2 = (float)(G * G);
+    for (int y = y0; y <= y1; ++y) {
+        const float dy = (float)(y - j);
+        const float dy0 = dy * dy, dy1 = (dy - 1.f) * (dy - 1.f);
+        const int w = (int)ceilf(sqrtf(fmaxf(G2 - fminf(dy0, dy1), 0.f)));
+        const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
+        const size_t qrow = (size_t)y * W;
+        float dx = (float)(x0 - i);
+#pragma unroll PF_UNROLL
+        for (int x = x0; x <= x1; ++x, dx += 1.f) {
+            const float r = __ldg(&rh[qrow + x]);
+            const float4 e = __ldg(&rec[qrow + x]);
+            const float dx0 = dx * dx, dx1 = (dx - 1.f) * (dx - 1.f);
+            const float d00 = sqrt_approx(dx0 + dy0), d10 = sqrt_approx(dx1 + dy0);
+            const float d01 = sqrt_approx(dx0 + dy1), d11 = sqrt_approx(dx1 + dy1);
+            if (NEAR) {
+                acc_near(a[0], d00, r, e);
+                acc_near(a[1], d10, r, e);
+                acc_near(a[2], d01, r, e);
+                acc_near(a[3], d11, r, e);
+            } else {
+                const float z = __ldg(&zq[qrow + x]);
+                acc_far(a[0], d00, r, z, e);
+                acc_far(a[1], d10, r, z, e);
+                acc_far(a[2], d01, r, z, e);
+                acc_far(a[3], d11, r, z, e);
+            }
+        }
+    }
 }
 
 // 64 threads per 16x16 tile; thread t gathers the 2x2 pixel block at
@@ -158,73 +221,51 @@ __device__ __forceinline__ void pf_acc(PfAcc& a, float d, const float4& e, const
 // covers a 16x8 pixel block.
 template <class COL>
 __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx, int ty) {
-    const float4* __restrict__ prep = ar.prep;
     const COL* __restrict__ col = ar.col;
-    const float* __restrict__ tmax = ar.tmax;
+    const float2* __restrict__ tmax = ar.tmax;
     const int W = ar.W, H = ar.H, ntx = ar.ntx, nty = ar.nty, kt = ar.kt;
-    const float kz_rel = ar.kz_rel;
     float4* __restrict__ pp = ar.pp;
     float4* __restrict__ aux = ar.aux;
-    __shared__ int s_win;
-    if (threadIdx.x == 0) s_win = 0;
+    __shared__ int s_win[2];
+    if (threadIdx.x < 2) s_win[threadIdx.x] = -1;
     __syncthreads();
-    // window: largest r + 1/2 over tiles whose pixels can reach this tile
+    // per layer: largest r + 1/2 over tiles whose feeding pixels can reach this tile
     for (int k = threadIdx.x; k < (2 * kt + 1) * (2 * kt + 1); k += blockDim.x) {
         int ox = k % (2 * kt + 1) - kt, oy = k / (2 * kt + 1) - kt;
         int x = tx + ox, y = ty + oy;
         if (x < 0 || y < 0 || x >= ntx || y >= nty) continue;
-        float r = __ldg(&tmax[y * ntx + x]);
+        const float2 r = __ldg(&tmax[y * ntx + x]);
         // pixel gap between the two tiles along each axis
-        float gx = ox == 0 ? 0.f : (float)((abs(ox) - 1) * TP + 1);
-        float gy = oy == 0 ? 0.f : (float)((abs(oy) - 1) * TP + 1);
-        if (gx * gx + gy * gy < (r + 0.5f) * (r + 0.5f)) atomicMax(&s_win, (int)ceilf(r + 0.5f));
+        const float gx = ox == 0 ? 0.f : (float)((abs(ox) - 1) * TP + 1);
+        const float gy = oy == 0 ? 0.f : (float)((abs(oy) - 1) * TP + 1);
+        const float g2 = gx * gx + gy * gy;
+        if (r.x >= 0.f && g2 < (r.x + 0.5f) * (r.x + 0.5f)) atomicMax(&s_win[0], (int)ceilf(r.x + 0.5f));
+        if (r.y >= 0.f && g2 < (r.y + 0.5f) * (r.y + 0.5f)) atomicMax(&s_win[1], (int)ceilf(r.y + 0.5f));
     }
     __syncthreads();
-    const int G = s_win;
+    const int Gn = s_win[0], Gf = s_win[1];
     const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + 2 * (threadIdx.x >> 3);
     if (i >= W || j >= H) return;
     const bool right = i + 1 < W, down = j + 1 < H;
     const size_t pq = (size_t)j * W + i;
     PfAcc a[4];  // (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1)
     {
-        const float ka = 1.f + 1.f / kz_rel;  // k_z = clamp(ka - z_q kb), kb = 1 / (kz_rel z_p)
-        const float z00 = __ldg(&prep[pq].w);
-        const float z10 = right ? __ldg(&prep[pq + 1].w) : z00;
-        const float z01 = down ? __ldg(&prep[pq + W].w) : z00;
-        const float z11 = right && down ? __ldg(&prep[pq + W + 1].w) : z00;
+        const float ka = 1.f + 1.f / ar.kz_rel;  // k_z = clamp(ka - z_q kb), kb = 1 / (kz_rel z_p)
+        const float z00 = __ldg(&ar.zq[pq]);
+        const float z10 = right ? __ldg(&ar.zq[pq + 1]) : z00;
+        const float z01 = down ? __ldg(&ar.zq[pq + W]) : z00;
+        const float z11 = right && down ? __ldg(&ar.zq[pq + W + 1]) : z00;
         const float zs[4] = {z00, z10, z01, z11};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             a[k].ka = ka;
-            a[k].kb = 1.f / (kz_rel * zs[k]);
+            a[k].kb = 1.f / (ar.kz_rel * zs[k]);
             a[k].Sn = a[k].Sf = f3(0, 0, 0);
             a[k].Wn = a[k].Wf = 0.f;
         }
     }
-    // every reaching source has r + 1/2 <= G, so only taps closer than G to
-    // one of the four pixels can weigh: per source row, the columns of that
-    // disk (squared distances are exact integers in float)
-    const int y0 = max(j - G, 0), y1 = min(j + 1 + G, H - 1);
-    const float G2 = (float)(G * G);
-    for (int y = y0; y <= y1; ++y) {
-        const float dy = (float)(y - j);
-        const float dy0 = dy * dy, dy1 = (dy - 1.f) * (dy - 1.f);
-        const float rem = G2 - fminf(dy0, dy1);  // > 0: |dy| <= G for the nearer row
-        const int w = (int)ceilf(sqrtf(rem));
-        const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
-        const size_t qrow = (size_t)y * W;
-        float dx = (float)(x0 - i);
-#pragma unroll PF_UNROLL
-        for (int x = x0; x <= x1; ++x, dx += 1.f) {
-            const float4 e = __ldg(&prep[qrow + x]);
-            const float4 c = ld4(col + qrow + x);
-            const float dx0 = dx * dx, dx1 = (dx - 1.f) * (dx - 1.f);
-            pf_acc(a[0], sqrt_approx(dx0 + dy0), e, c);
-            pf_acc(a[1], sqrt_approx(dx1 + dy0), e, c);
-            pf_acc(a[2], sqrt_approx(dx0 + dy1), e, c);
-            pf_acc(a[3], sqrt_approx(dx1 + dy1), e, c);
-        }
-    }
+    pf_layer<true>(a, Gn, i, j, W, H, ar.rh, ar.zq, ar.nrec);
+    pf_layer<false>(a, Gf, i, j, W, H, ar.rh, ar.zq, ar.frec);
     pp[pq] = pf_finish(a[0], col, pq, aux);
     if (right) pp[pq + 1] = pf_finish(a[1], col, pq + 1, aux);
     if (down) pp[pq + W] = pf_finish(a[2], col, pq + W, aux);
@@ -236,7 +277,8 @@ __global__ void __launch_bounds__(GATHER_THREADS, HDOF_PF_MINB) k_pf_gather(Gath
     pf_gather_body(a, blockIdx.x, blockIdx.y);
 }
 
-__global__ void __launch_bounds__(256) k_pf_prep_batch(const PrepArgs<float4>* __restrict__ a, BatchGrid g) {
+using PrepF32 = PrepArgs<float4, float4>;
+__global__ void __launch_bounds__(256) k_pf_prep_batch(const PrepF32* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
     pf_prep_body(batch_record(a, v), bx, by);
@@ -349,30 +391,44 @@ int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p,
     int rc;
     if ((rc = ensure_area_table(s))) return rc;
     const int W = in->width, H = in->height;
-    WsLayout L = ws_layout(W, H, p);
-    float4* prep = static_cast<float4*>(workspace);
-    float* tmax = reinterpret_cast<float*>(static_cast<char*>(workspace) + L.pf_prep);
+    hdof_view v = {};
+    v.cam.width = W;
+    v.cam.height = H;
+    v.params = *p;
+    v.workspace = workspace;
+    const ViewWs w = view_ws(v);
     const int ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
     dim3 grid(ntx, nty);
-    if (in->dtype_nd == HDOF_F32)
-        k_pf_prep<float4><<<grid, 256, 0, s>>>(
-            PrepArgs<float4>{static_cast<const float4*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax});
+    const bool f32n = in->dtype_nd == HDOF_F32, f32c = in->dtype_col == HDOF_F32;
+    const float4* nd4 = static_cast<const float4*>(in->nd);
+    const half4s* ndh = static_cast<const half4s*>(in->nd);
+    const float4* col4 = static_cast<const float4*>(in->col);
+    const bf164s* colb = static_cast<const bf164s*>(in->col);
+    const float rm = p->r_max;
+    if (f32n && f32c)
+        k_pf_prep<<<grid, 256, 0, s>>>(
+            PrepArgs<float4, float4>{nd4, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+    else if (f32n)
+        k_pf_prep<<<grid, 256, 0, s>>>(
+            PrepArgs<float4, bf164s>{nd4, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+    else if (f32c)
+        k_pf_prep<<<grid, 256, 0, s>>>(
+            PrepArgs<half4s, float4>{ndh, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
     else
-        k_pf_prep<half4s><<<grid, 256, 0, s>>>(
-            PrepArgs<half4s>{static_cast<const half4s*>(in->nd), W, H, coc, p->r_max, ntx, prep, tmax});
+        k_pf_prep<<<grid, 256, 0, s>>>(
+            PrepArgs<half4s, bf164s>{ndh, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
     HDOF_LAUNCHED("post-filter prep");
-    int kt = gather_tiles(p->r_max);
+    const int kt = gather_tiles(p->r_max);
+    float4* out = reinterpret_cast<float4*>(pp);
     // the taps are served from L1: a small shared-memory carve-out
-    if (in->dtype_col == HDOF_F32) {
+    if (f32c) {
         cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
-        k_pf_gather<float4><<<grid, GATHER_THREADS, 0, s>>>(GatherArgs<float4>{prep, static_cast<const float4*>(in->col), tmax,
-                                                                    W, H, ntx, nty, kt, p->kz_rel,
-                                                                    reinterpret_cast<float4*>(pp), aux});
+        k_pf_gather<float4><<<grid, GATHER_THREADS, 0, s>>>(
+            GatherArgs<float4>{w.rh, w.zq, w.nrec, w.frec, col4, w.tmax, W, H, ntx, nty, kt, p->kz_rel, out, aux});
     } else {
         cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
-        k_pf_gather<bf164s><<<grid, GATHER_THREADS, 0, s>>>(GatherArgs<bf164s>{prep, static_cast<const bf164s*>(in->col), tmax,
-                                                                    W, H, ntx, nty, kt, p->kz_rel,
-                                                                    reinterpret_cast<float4*>(pp), aux});
+        k_pf_gather<bf164s><<<grid, GATHER_THREADS, 0, s>>>(
+            GatherArgs<bf164s>{w.rh, w.zq, w.nrec, w.frec, colb, w.tmax, W, H, ntx, nty, kt, p->kz_rel, out, aux});
     }
     HDOF_LAUNCHED("post-filter gather");
     return HDOF_OK;
@@ -391,32 +447,32 @@ extern "C" int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, cons
     HDOF_CHECK_ARG(pp, "hdof_postfilter: pp output is required");
     HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "hdof_postfilter: gbuf/camera size mismatch");
     WsLayout L = ws_layout(in->width, in->height, p);
-    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.pf_prep + L.pf_tiles,
-                   "hdof_postfilter: workspace of %zu bytes < %zu", workspace_bytes, L.pf_prep + L.pf_tiles);
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.pf, "hdof_postfilter: workspace of %zu bytes < %zu",
+                   workspace_bytes, L.pf);
     return launch_postfilter(in, make_coc(*lens, in->height, cam->tan_half_fovy), p, pp, nullptr, workspace,
                              as_stream(stream));
 }
 
 namespace hdof {
 
-size_t pf_prep_args_size() { return sizeof(PrepArgs<float4>); }
+size_t pf_prep_args_size() { return sizeof(PrepF32); }
 void pf_prep_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
     const int W = v.cam.width, H = v.cam.height, ntx = (W + TP - 1) / TP;
-    *reinterpret_cast<PrepArgs<float4>*>(dst) =
-        PrepArgs<float4>{static_cast<const float4*>(v.g.nd), W, H, make_coc(v.lens, H, v.cam.tan_half_fovy),
-                         v.params.r_max, ntx, w.prep, w.tmax};
+    *reinterpret_cast<PrepF32*>(dst) =
+        PrepF32{static_cast<const float4*>(v.g.nd), static_cast<const float4*>(v.g.col), W, H,
+                make_coc(v.lens, H, v.cam.tan_half_fovy), v.params.r_max, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax};
     *gx = ntx;
     *gy = (H + TP - 1) / TP;
 }
 void pf_prep_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
-    k_pf_prep_batch<<<blocks, 256, 0, s>>>(static_cast<const PrepArgs<float4>*>(args), g);
+    k_pf_prep_batch<<<blocks, 256, 0, s>>>(static_cast<const PrepF32*>(args), g);
 }
 
 size_t pf_gather_args_size() { return sizeof(GatherArgs<float4>); }
 void pf_gather_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
     const int W = v.cam.width, H = v.cam.height, ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
     *reinterpret_cast<GatherArgs<float4>*>(dst) =
-        GatherArgs<float4>{w.prep, static_cast<const float4*>(v.g.col), w.tmax, W, H, ntx, nty,
+        GatherArgs<float4>{w.rh, w.zq, w.nrec, w.frec, static_cast<const float4*>(v.g.col), w.tmax, W, H, ntx, nty,
                            gather_tiles(v.params.r_max), v.params.kz_rel, reinterpret_cast<float4*>(v.pp), nullptr};
     *gx = ntx;
     *gy = nty;
