@@ -127,6 +127,17 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, device):
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------- our kernels ---
 
 def algorithmic_bytes(W, Hh, n_traced, variance_px, nd_b=16, col_b=16):
@@ -249,10 +260,7 @@ def run_ours(args):
     stage_ms = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(len(stages))] for s in range(K)])
     step_ms = stage_ms.sum(1)
     total_ms = float(step_ms.sum())
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, dev)
     clocks = sampler.summary()
 
     st_all = stats_all.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
@@ -422,10 +430,7 @@ def run_batch(args):
     H.hdof_sync()
     step_ms = np.array([a.elapsed_time(c) for a, c in evs])
     total_ms = float(step_ms.sum())
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, dev)
     clocks = sampler.summary()
     st = stats.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
     rays = float(st[:, :, 1].sum(1).mean())

@@ -28,12 +28,15 @@ def cache_path() -> str:
     return os.environ.get("HDOF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "hdof_tuning.json"))
 
 
-def signature(batch: "H.Batch") -> str:
-    """GPU name + every view's (width, height, triangles, spp_max, r_max)."""
-    shape = [torch.cuda.get_device_name()]
-    for r, p in zip(batch.views, batch.params):
-        shape.append((r.W, r.H, int(r.bvh.stats().n_tris), int(p.spp_max), float(p.r_max)))
-    return hashlib.sha1(json.dumps(shape).encode()).hexdigest()[:16]
+def workload_shape(batch: "H.Batch"):
+    """Every view's (width, height, triangles, spp_max, r_max)."""
+    return [(r.W, r.H, int(r.bvh.stats().n_tris), int(p.spp_max), float(p.r_max))
+            for r, p in zip(batch.views, batch.params)]
+
+
+def signature(shape, device_name: str) -> str:
+    """Cache key of a workload shape on a GPU model."""
+    return hashlib.sha1(json.dumps([device_name] + [list(v) for v in shape]).encode()).hexdigest()[:16]
 
 
 def _load() -> dict:
@@ -79,7 +82,7 @@ def tune(batch: "H.Batch", frame_args, candidates=CANDIDATES, reps: int = 5, use
     ``frame_args`` = (cams, prevs, lenses, params) of a representative frame.
     Returns (hdof_tuning, {shape: ms}); the timings are empty on a cache hit.
     """
-    key = signature(batch)
+    key = signature(workload_shape(batch), torch.cuda.get_device_name())
     cache = _load() if use_cache else {}
     if key in cache:
         b, c = cache[key]["best"]

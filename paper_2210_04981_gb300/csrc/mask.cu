@@ -93,25 +93,23 @@ __device__ __forceinline__ void mask_edge_body(const EdgeArgs<ND>& ar, int bx, i
     const int i = x0 + lx, j = y0 + ly;
     if (i >= W || j >= H) return;
     // Sobel on the filtered image with clamp-to-edge (the Sobel's border rule):
-    // an out-of-image neighbour reads the filtered value of the border pixel
-    auto F = [&](int dx, int dy) -> float4 {
-        int x = min(max(i + dx, 0), W - 1), y = min(max(j + dy, 0), H - 1);
-        return fil[y - (y0 - 1)][x - (x0 - 1)];
-    };
-    float gx[4] = {0, 0, 0, 0}, gy[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int k = -1; k <= 1; ++k) {
-        float wk = k == 0 ? 2.f : 1.f;
-        float4 r = F(1, k), l = F(-1, k), dn = F(k, 1), up = F(k, -1);
-        gx[0] += wk * (r.x - l.x);
-        gx[1] += wk * (r.y - l.y);
-        gx[2] += wk * (r.z - l.z);
-        gx[3] += wk * (r.w - l.w);
-        gy[0] += wk * (dn.x - up.x);
-        gy[1] += wk * (dn.y - up.y);
-        gy[2] += wk * (dn.z - up.z);
-        gy[3] += wk * (dn.w - up.w);
-    }
+    // an out-of-image neighbour reads the filtered value of the border pixel.
+    // fil holds filtered rows y0-1 .. y0+16 and columns x0-1 .. x0+16.
+    const int cl = max(i - 1, 0) - (x0 - 1), cc = lx + 1, cr = min(i + 1, W - 1) - (x0 - 1);
+    const int ru = max(j - 1, 0) - (y0 - 1), rc = ly + 1, rd = min(j + 1, H - 1) - (y0 - 1);
+    const float4 f_ul = fil[ru][cl], f_uc = fil[ru][cc], f_ur = fil[ru][cr];
+    const float4 f_cl = fil[rc][cl], f_cr = fil[rc][cr];
+    const float4 f_dl = fil[rd][cl], f_dc = fil[rd][cc], f_dr = fil[rd][cr];
+    float gx[4], gy[4];
+    // gx: right column minus left column, rows weighted 1 2 1; gy: down row minus up row
+    gx[0] = (f_ur.x - f_ul.x) + 2.f * (f_cr.x - f_cl.x) + (f_dr.x - f_dl.x);
+    gx[1] = (f_ur.y - f_ul.y) + 2.f * (f_cr.y - f_cl.y) + (f_dr.y - f_dl.y);
+    gx[2] = (f_ur.z - f_ul.z) + 2.f * (f_cr.z - f_cl.z) + (f_dr.z - f_dl.z);
+    gx[3] = (f_ur.w - f_ul.w) + 2.f * (f_cr.w - f_cl.w) + (f_dr.w - f_dl.w);
+    gy[0] = (f_dl.x - f_ul.x) + 2.f * (f_dc.x - f_uc.x) + (f_dr.x - f_ur.x);
+    gy[1] = (f_dl.y - f_ul.y) + 2.f * (f_dc.y - f_uc.y) + (f_dr.y - f_ur.y);
+    gy[2] = (f_dl.z - f_ul.z) + 2.f * (f_dc.z - f_uc.z) + (f_dr.z - f_ur.z);
+    gy[3] = (f_dl.w - f_ul.w) + 2.f * (f_dc.w - f_uc.w) + (f_dr.w - f_ur.w);
     for (int c = 0; c < 4; ++c) {
         gx[c] *= 0.125f;
         gy[c] *= 0.125f;
@@ -151,22 +149,31 @@ __device__ __forceinline__ void mask_spp_body(const SppArgs& ar, int bx, int by)
     const uint8_t* __restrict__ hhlen = ar.hhlen;
     const float var_tau = ar.var_tau, var_scale = ar.var_scale;
     uint8_t* __restrict__ spp = ar.spp;
-    int i = bx * 32 + (threadIdx.x & 31), j = by * 8 + (threadIdx.x >> 5);
-    if (i >= W || j >= H) return;
-    size_t q = (size_t)j * W + i;
-    int tx = i / tile, ty = j / tile;
-    bool on = false;
-    for (int b = -dil; b <= dil && !on; ++b) {
-        int y = ty + b;
-        if (y < 0 || y >= nty) continue;
-        for (int a = -dil; a <= dil; ++a) {
-            int x = tx + a;
-            if (x >= 0 && x < ntx && __ldg(&tiles[y * ntx + x])) {
-                on = true;
-                break;
-            }
+    // the dilated flag of every mask tile this 32x8 block touches, once, in
+    // shared memory (at most 32 x 8 tiles, for tile = 1)
+    __shared__ unsigned char s_on[8][32];
+    const int x0 = bx * 32, y0 = by * 8;
+    const int tx0 = x0 / tile, ty0 = y0 / tile;
+    const int ntx_b = min(x0 + 31, W - 1) / tile - tx0 + 1, nty_b = min(y0 + 7, H - 1) / tile - ty0 + 1;
+    {
+        const int e = threadIdx.x, ey = e >> 5, ex = e & 31;
+        if (ey < nty_b && ex < ntx_b) {
+            const int tx = tx0 + ex, ty = ty0 + ey;
+            bool any = false;
+            for (int b = max(ty - dil, 0); b <= min(ty + dil, nty - 1) && !any; ++b)
+                for (int a = max(tx - dil, 0); a <= min(tx + dil, ntx - 1); ++a)
+                    if (__ldg(&tiles[b * ntx + a])) {
+                        any = true;
+                        break;
+                    }
+            s_on[ey][ex] = any ? 1 : 0;
         }
     }
+    __syncthreads();
+    int i = x0 + (threadIdx.x & 31), j = y0 + (threadIdx.x >> 5);
+    if (i >= W || j >= H) return;
+    size_t q = (size_t)j * W + i;
+    const bool on = s_on[j / tile - ty0][i / tile - tx0] != 0;
     int s = on ? spp_max : 0;
     if (!on && variance_on) {
         float2 m = __ldg(&mv[q]);

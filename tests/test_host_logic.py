@@ -1,0 +1,80 @@
+"""Host-side logic that needs no GPU: the batch autotuner's choice and cache,
+and the benchmark's multi-rank timing reduction (world size 2 over gloo)."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_autotune_picks_fastest_and_caches(tmp_path, monkeypatch):
+    from paper_2210_04981_gb300 import autotune
+    monkeypatch.setenv("HDOF_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "test-gpu")
+    shape = [(256, 256, 51980, 16, 32.0), (1920, 1080, 502540, 16, 32.0)]
+    monkeypatch.setattr(autotune, "workload_shape", lambda b: shape)
+    calls = []
+
+    def fake_time(batch, frame_args, block, refill, reps=5, warmup=2):
+        calls.append((block, refill))
+        return 1.0 + abs(block - 128) / 64.0 + abs(refill - 4) / 8.0
+
+    monkeypatch.setattr(autotune, "time_shape", fake_time)
+    t, times = autotune.tune(object(), None)
+    assert (t.trace_block, t.trace_refill) == (128, 4)
+    assert sorted(calls) == sorted(autotune.CANDIDATES) and len(times) == len(autotune.CANDIDATES)
+    # second call: a cache hit, nothing timed
+    t2, times2 = autotune.tune(object(), None)
+    assert (t2.trace_block, t2.trace_refill) == (128, 4) and times2 == {}
+    assert len(calls) == len(autotune.CANDIDATES)
+    # the key separates GPUs and workloads
+    assert autotune.signature(shape, "a") != autotune.signature(shape, "b")
+    assert autotune.signature(shape, "a") != autotune.signature(shape[:1], "a")
+    assert autotune.signature(shape, "a") == autotune.signature([tuple(v) for v in shape], "a")
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    env = bench.dist_env()
+    value = bench.max_over_ranks(10.0 + 5.0 * rank, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+    out.put((rank, env, value))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_max_over_ranks_gloo_world_2():
+    """Two CPU ranks: each sees its own rank in the environment and both get
+    the slowest rank's time."""
+    ctx = torch.multiprocessing.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [(2, 0, 0), (2, 1, 1)]
+    assert [r[2] for r in res] == [15.0, 15.0]
+
+
+def test_max_over_ranks_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, "cpu") == 3.5
