@@ -189,7 +189,10 @@ int hdof_gbuffer(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_camera*
 /* Bytes of caller-owned device scratch the calls below need for a
  * width x height frame (the maximum over calls; one buffer serves them all
  * when they run in order on one stream).  The trace's share grows with
- * p->spp_max: 21 bytes per possible ray (pixel, sample index, record). */
+ * p->spp_max: 21 bytes per possible ray (pixel, sample index, record).  The
+ * post-filter's region is disjoint from the mask's and the trace's, so
+ * hdof_postfilter may run on another stream concurrently with hdof_mask and
+ * hdof_trace once hdof_gbuffer has finished. */
 size_t hdof_workspace_bytes(int32_t width, int32_t height, const hdof_params* p);
 
 /* ----------------------------------------------------------- mask -- */

@@ -129,11 +129,8 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     l.pf_zq = align256(npx * sizeof(float));
     l.pf_tiles = align256(ptiles * sizeof(float2));
     l.pf = l.pf_nrec + l.pf_frec + l.pf_rh + l.pf_zq + l.pf_tiles;
-    size_t mask = l.mask_tiles;
-    size_t trace = l.trace;
-    size_t pf = l.pf;
-    l.total = mask > trace ? mask : trace;
-    if (pf > l.total) l.total = pf;
+    l.pf_off = align256(l.mask_tiles > l.trace ? l.mask_tiles : l.trace);
+    l.total = l.pf_off + l.pf;
     return l;
 }
 

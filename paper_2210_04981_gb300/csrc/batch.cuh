@@ -69,6 +69,16 @@ struct ViewWs {
     float2* tmax;        // post-filter per-tile radii (near, far)
 };
 
+// the post-filter regions, laid out from `pf` (ws_layout(...).pf bytes)
+inline void pf_regions(ViewWs& w, char* pf, const WsLayout& L) {
+    size_t f = 0;
+    w.nrec = reinterpret_cast<float4*>(pf + f);
+    w.frec = reinterpret_cast<float4*>(pf + (f += L.pf_nrec));
+    w.rh = reinterpret_cast<float*>(pf + (f += L.pf_frec));
+    w.zq = reinterpret_cast<float*>(pf + (f += L.pf_rh));
+    w.tmax = reinterpret_cast<float2*>(pf + (f += L.pf_zq));
+}
+
 inline ViewWs view_ws(const hdof_view& v) {
     WsLayout L = ws_layout(v.cam.width, v.cam.height, &v.params);
     const int ntx = (v.cam.width + 15) / 16, nty = (v.cam.height + 15) / 16, ntiles = ntx * nty;
@@ -85,12 +95,7 @@ inline ViewWs view_ws(const hdof_view& v) {
     w.ray_pix = reinterpret_cast<unsigned*>(base + (o += L.trace_qoff));
     w.ray_s = reinterpret_cast<uint8_t*>(base + (o += L.trace_ray_pix));
     w.rec = reinterpret_cast<float4*>(base + (o += L.trace_ray_s));
-    size_t f = 0;
-    w.nrec = reinterpret_cast<float4*>(base + f);
-    w.frec = reinterpret_cast<float4*>(base + (f += L.pf_nrec));
-    w.rh = reinterpret_cast<float*>(base + (f += L.pf_frec));
-    w.zq = reinterpret_cast<float*>(base + (f += L.pf_rh));
-    w.tmax = reinterpret_cast<float2*>(base + (f += L.pf_zq));
+    pf_regions(w, base + L.pf_off, L);
     return w;
 }
 

@@ -227,6 +227,16 @@ __device__ __forceinline__ float slab(const Ray& r, float lx, float hx, float ly
     tf *= 1.0000004f;
     return tn <= tf ? tn : __int_as_float(0x7f800000);
 }
+// the same test returning the hit flag, with the entry distance in tn
+__device__ __forceinline__ bool slab_hit(const Ray& r, float lx, float hx, float ly, float hy, float lz, float hz,
+                                         float tmax, float& tn) {
+    float tx0 = fmaf(lx, r.id.x, -r.ood.x), tx1 = fmaf(hx, r.id.x, -r.ood.x);
+    float ty0 = fmaf(ly, r.id.y, -r.ood.y), ty1 = fmaf(hy, r.id.y, -r.ood.y);
+    float tz0 = fmaf(lz, r.id.z, -r.ood.z), tz1 = fmaf(hz, r.id.z, -r.ood.z);
+    tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    return tn <= tf * 1.0000004f;
+}
 
 // Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013).  Edge
 // functions are evaluated without contraction so a shared edge gives exactly
@@ -346,9 +356,9 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
             const Node* n = bvh.nodes + cur;
             float4 a = __ldg(&n->xy0), b = __ldg(&n->xy1), z = __ldg(&n->z01);
             int4 ch = __ldg(&n->child);
-            float t0 = slab(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t);
-            float t1 = slab(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t);
-            bool h0 = t0 < INF, h1 = t1 < INF;
+            float t0, t1;
+            const bool h0 = slab_hit(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t, t0);
+            const bool h1 = slab_hit(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t, t1);
             if (h0 && h1) {
                 int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
                 if (sp < HDOF_STACK) stack[sp++] = farc;

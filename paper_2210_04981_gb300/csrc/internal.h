@@ -69,6 +69,8 @@ struct WsLayout {
     size_t pf_zq;           // float per pixel: view depth
     size_t pf_tiles;        // float2 per 16x16 tile
     size_t pf;              // sum of the post-filter regions (laid out in this order)
+    size_t pf_off;          // where the post-filter regions start: after the mask and trace regions, so
+                            // the post-filter can run concurrently with them
     size_t total;
 };
 WsLayout ws_layout(int W, int H, const hdof_params* p);
@@ -83,8 +85,9 @@ int area_table(const float4** tab, int* n);
 // launches shared by the frame calls and the differentiable post-path (arguments already checked)
 int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, int W, int H, float r_s, float var_ref,
                    float4* crec, float4* aux, cudaStream_t s);
+// scratch: ws_layout(W, H, p).pf bytes (the post-filter regions)
 int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, float4* aux,
-                      void* workspace, cudaStream_t s);
+                      void* scratch, cudaStream_t s);
 int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
                      const float* hacc, const Coc& coc, float h_tau, float* out, cudaStream_t s);
 

@@ -387,16 +387,12 @@ using namespace hdof;
 namespace hdof {
 
 int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, float4* aux,
-                      void* workspace, cudaStream_t s) {
+                      void* scratch, cudaStream_t s) {
     int rc;
     if ((rc = ensure_area_table(s))) return rc;
     const int W = in->width, H = in->height;
-    hdof_view v = {};
-    v.cam.width = W;
-    v.cam.height = H;
-    v.params = *p;
-    v.workspace = workspace;
-    const ViewWs w = view_ws(v);
+    ViewWs w = {};
+    pf_regions(w, static_cast<char*>(scratch), ws_layout(W, H, p));
     const int ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
     dim3 grid(ntx, nty);
     const bool f32n = in->dtype_nd == HDOF_F32, f32c = in->dtype_col == HDOF_F32;
@@ -447,10 +443,10 @@ extern "C" int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, cons
     HDOF_CHECK_ARG(pp, "hdof_postfilter: pp output is required");
     HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "hdof_postfilter: gbuf/camera size mismatch");
     WsLayout L = ws_layout(in->width, in->height, p);
-    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.pf, "hdof_postfilter: workspace of %zu bytes < %zu",
-                   workspace_bytes, L.pf);
-    return launch_postfilter(in, make_coc(*lens, in->height, cam->tan_half_fovy), p, pp, nullptr, workspace,
-                             as_stream(stream));
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.total, "hdof_postfilter: workspace of %zu bytes < %zu",
+                   workspace_bytes, L.total);
+    return launch_postfilter(in, make_coc(*lens, in->height, cam->tan_half_fovy), p, pp, nullptr,
+                             static_cast<char*>(workspace) + L.pf_off, as_stream(stream));
 }
 
 namespace hdof {

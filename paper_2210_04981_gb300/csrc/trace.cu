@@ -319,9 +319,9 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
                     const Node* n = a.bvh.nodes + cur;
                     float4 na = __ldg(&n->xy0), nb = __ldg(&n->xy1), nz = __ldg(&n->z01);
                     int4 ch = __ldg(&n->child);
-                    float t0 = slab(ray, na.x, na.y, na.z, na.w, nz.x, nz.y, h.t);
-                    float t1 = slab(ray, nb.x, nb.y, nb.z, nb.w, nz.z, nz.w, h.t);
-                    bool h0 = t0 < INF, h1 = t1 < INF;
+                    float t0, t1;
+                    const bool h0 = slab_hit(ray, na.x, na.y, na.z, na.w, nz.x, nz.y, h.t, t0);
+                    const bool h1 = slab_hit(ray, nb.x, nb.y, nb.z, nb.w, nz.z, nz.w, h.t, t1);
                     if (h0 && h1) {
                         int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
                         if (sp < HDOF_STACK) stack[sp++] = farc;
