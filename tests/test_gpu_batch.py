@@ -112,6 +112,32 @@ def test_batch_graph_replay(small):
     b.close()
 
 
+def test_batch_degenerate_views(small):
+    """1x1 and 3x2 views, a ragged 17x16 view and a view of a fronto-parallel
+    plane whose mask is empty (no rays at all) in one batch: still equal to
+    the single-view calls."""
+    scenes, bvhs, _ = small
+    plane = bvh_of(hi.plane_scene(2.0))
+    base = hi.batch_views(4, resolutions=((8, 8),))
+    specs = [(bvhs[0], 1, 1), (bvhs[1], 3, 2), (bvhs[2], 17, 16), (plane, 64, 48)]
+    views = []
+    for (b, w, h), v in zip(specs, base):
+        v.width, v.height = w, h
+        views.append(v)
+    views[3].pos, views[3].target = (0.0, 0.0, 0.0), (0.0, 0.0, 5.0)
+    blist = [b for b, _, _ in specs]
+    rs = [H.Renderer(b, v.width, v.height, v.params) for b, v in zip(blist, views)]
+    b = H.Batch(blist, [(v.width, v.height) for v in views], [v.params for v in views], tune=H.tuning(64, 2))
+    for k in range(2):
+        _run_singles(rs, views, k)
+        b.frame(*_frame_args(views, k))
+        H.hdof_sync()
+        for i, (r, rb) in enumerate(zip(rs, b.views)):
+            _assert_same(r, rb, f"frame {k} view {i}")
+    assert int(rs[3].stats[1]) == 0  # the plane view traced nothing
+    b.close()
+
+
 def test_batch_rejects_changed_sizes(small):
     scenes, bvhs, views = small
     b = H.Batch([bvhs[v.room] for v in views[:2]], [(v.width, v.height) for v in views[:2]],

@@ -201,6 +201,21 @@ def test_mask_random_gbuffer(orc, seed, W, Hh):
         assert (spp == 0).sum() > 0
 
 
+@pytest.mark.parametrize("tile,dilate,W,Hh", [(1, 0, 67, 45), (7, 2, 150, 97), (24, 1, 301, 77), (16, 0, 96, 64),
+                                              (5, 8, 83, 59)])
+def test_mask_tile_and_dilation_shapes(orc, tile, dilate, W, Hh):
+    """Mask tiles of other sizes and dilation radii (the per-block dilated
+    flags span up to 32 x 8 tiles) on ragged images."""
+    gb = hi.random_gbuffer(W, Hh, seed=tile + 10 * dilate)
+    p = hi.Params(spp_max=8, tile=tile, dilate=dilate)
+    edge, spp = _mask(gbuf_from(gb["nd"], gb["col"], gb["mv"]), None, p)
+    ref = orc.mask(gb["nd"].astype(np.float64), gb["mv"].astype(np.float64), p)
+    tie, tie_px = _tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
+    assert np.array_equal(edge[~tie], ref["edge"][~tie])
+    assert np.array_equal(spp[~tie_px], ref["spp"][~tie_px])
+    assert edge.sum() > 0 and (spp > 0).sum() > 0
+
+
 def test_mask_variance_term(orc):
     W, Hh = 200, 120
     gb = hi.random_gbuffer(W, Hh, seed=5, n_regions=2)
