@@ -305,12 +305,31 @@ __global__ void __launch_bounds__(256) k_spatial_bwd_prep(const float4* __restri
 // gathered sample of its neighbours and x as a gatherer
 __global__ void __launch_bounds__(256) k_spatial_bwd(const float4* __restrict__ crt, const float4* __restrict__ spb,
                                                      int W, int H, float r_s, float4* __restrict__ gcrt) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7), j = blockIdx.y * 16 + (w >> 1) * 4 + (l >> 3);
-    if (i >= W || j >= H) return;
+    // block = one 16x16 tile; its traced pixels are compacted (row-major) so
+    // that every warp which runs works on traced pixels only
+    __shared__ unsigned char s_list[256];
+    __shared__ int s_wcnt[8];
+    const int t = threadIdx.x, lane = t & 31;
+    bool traced = false;
+    {
+        const int i0 = blockIdx.x * 16 + (t & 15), j0 = blockIdx.y * 16 + (t >> 4);
+        if (i0 < W && j0 < H) traced = __ldg(&crt[(size_t)j0 * W + i0].w) >= 0.f;
+    }
+    const unsigned tm = __ballot_sync(0xffffffffu, traced);
+    if (lane == 0) s_wcnt[t >> 5] = __popc(tm);
+    __syncthreads();
+    int off = 0, n = 0;
+    for (int k = 0; k < 8; ++k) {
+        off += k < (t >> 5) ? s_wcnt[k] : 0;
+        n += s_wcnt[k];
+    }
+    if (traced) s_list[off + __popc(tm & ((1u << lane) - 1u))] = (unsigned char)t;
+    __syncthreads();
+    if (t >= n) return;
+    const int li = s_list[t];
+    const int i = blockIdx.x * 16 + (li & 15), j = blockIdx.y * 16 + (li >> 4);
     const size_t q = (size_t)j * W + i;
     const float4 cx = crt[q];
-    if (cx.w < 0.f) return;
     const float rx = fminf(cx.w * 0.5f, r_s);
     const float rpx = cx.w * 0.5f < r_s ? 0.5f : 0.f;
     const float4 bx = spb[q];
@@ -318,23 +337,27 @@ __global__ void __launch_bounds__(256) k_spatial_bwd(const float4* __restrict__ 
     const int K = (int)ceilf(rx + 0.5f);
     float3 gC = f3(0, 0, 0);
     float gcx = 0.f;
-    const int y0 = max(j - K, 0), y1 = min(j + K, H - 1), x0 = max(i - K, 0), x1 = min(i + K, W - 1);
+    // a neighbour takes part only if d < rx + 1/2 <= K: per row, the columns of that disk
+    const int y0 = max(j - K, 0), y1 = min(j + K, H - 1);
     for (int y = y0; y <= y1; ++y) {
-        float dy = (float)(y - j);
+        const float dy = (float)(y - j), dy2 = dy * dy;
+        const int wr = (int)ceilf(sqrtf(fmaxf((float)(K * K) - dy2, 0.f)));
+        const int x0 = max(i - wr, 0), x1 = min(i + wr, W - 1);
         for (int x = x0; x <= x1; ++x) {
             float dx = (float)(x - i);
             size_t qq = (size_t)y * W + x;
-            float4 cy = __ldg(&crt[qq]);
-            if (cy.w < 0.f) continue;
-            float d = sqrtf(fmaf(dx, dx, dy * dy));
+            // branch-free: untraced neighbours (and their unwritten spb) are
+            // selected away, out-of-disk pairs weigh exactly zero
+            const float4 cy = __ldg(&crt[qq]), by = __ldg(&spb[qq]);
+            const bool ty = cy.w >= 0.f;
+            float d = sqrt_approx(fmaf(dx, dx, dy2));
             float ux = rx - d + 0.5f, uy = fminf(cy.w * 0.5f, r_s) - d + 0.5f;
-            float sx = clamp01(ux), sy = clamp01(uy);
+            float sx = clamp01(ux), sy = ty ? clamp01(uy) : 0.f;
             float spx = (ux > 0.f && ux < 1.f) ? 1.f : 0.f;
-            if (sx <= 0.f && spx == 0.f) continue;
-            float4 by = __ldg(&spb[qq]);
-            float3 ay = ldf3(by);
+            const float3 ay = ty ? ldf3(by) : f3(0.f, 0.f, 0.f);
+            const float byw = ty ? by.w : 0.f;
             gC = gC + (sy * sx) * ay;
-            gcx += sy * spx * (dot3f(ay, Cx) - by.w);              // x gathered by y
+            gcx += sy * spx * (dot3f(ay, Cx) - byw);               // x gathered by y
             gcx += spx * sy * (dot3f(ax, ldf3(cy)) - bx.w);        // x gathering y
         }
     }
@@ -490,63 +513,138 @@ __global__ void __launch_bounds__(256) k_pf_bwd_prep(const float4* __restrict__ 
     pfb[2 * q + 1] = make_float4(Af.x, Af.y, Af.z, Ef);
 }
 
-// post-filter adjoint, part 2 (per source pixel q over the pixels its soft
-// disk reaches): colour gradient and the gradient of q's CoC
-__global__ void __launch_bounds__(256) k_pf_bwd(const float4* __restrict__ nd, const float4* __restrict__ col,
-                                                const float4* __restrict__ pfb, const float4* __restrict__ tab, int ntab,
-                                                int W, int H, LensD L, float rmax, float kz_rel,
-                                                float4* __restrict__ gcol, double2* partial) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7), j = blockIdx.y * 16 + (w >> 1) * 4 + (l >> 3);
+// per source pixel: the radius and the layer weights of the forward map and
+// their slopes with respect to the source's CoC
+struct PfSrc {
+    float R, rp;         // r + 1/2; dr/dc (0 when clipped at r_max)
+    float wnia, fia;     // w/a, (1-w)/a
+    float dwnia, dfia;   // their derivatives with respect to c
+};
+__device__ __forceinline__ PfSrc pf_src(float zq, const LensD& L, float rmax, const float4* tab, int ntab) {
+    PfSrc o;
+    const float c = coc_z(zq, L);
+    const bool clip = fabsf(c) * 0.5f >= rmax;
+    const float r = clip ? rmax : fabsf(c) * 0.5f;
+    o.R = r + 0.5f;
+    o.rp = clip ? 0.f : (c > 0.f ? 0.5f : (c < 0.f ? -0.5f : 0.f));
+    const float2 as = area_and_slope(tab, ntab, r);
+    const float ia = 1.f / as.x, iap = -as.y * ia * ia * o.rp;
+    const float wn = w_near(c), wnp = wn_slope(c);
+    o.wnia = wn * ia;
+    o.fia = (1.f - wn) * ia;
+    o.dwnia = wnp * ia + wn * iap;
+    o.dfia = -wnp * ia + (1.f - wn) * iap;
+    return o;
+}
+
+struct PfBwdAcc {
+    float3 gC;
+    float S1, S2, S3, S4;
+};
+
+// post-filter adjoint, part 2: per source pixel q over the target pixels its
+// soft disk reaches, the colour gradient and the gradient of q's CoC.  One
+// block per 16x16 tile of sources, 64 threads; thread t takes the 2x2 source
+// block at (2 (t & 7), 2 (t >> 3)), so every target it loads serves four
+// sources.  The loop covers, per target row, the columns closer than the
+// tile's largest radius to one of the four (other pairs have zero weight) and
+// is branch-free; the depth test is the forward's clamp(ka - z_q kb_p).
+#ifndef HDOF_PFB_MINB
+#define HDOF_PFB_MINB 10  // resident blocks per SM the post-filter adjoint's register budget targets
+#endif
+__global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __restrict__ nd, const float4* __restrict__ col,
+                                               const float4* __restrict__ pfb, const float4* __restrict__ tab,
+                                               int ntab, int W, int H, LensD L, float rmax, float kz_rel,
+                                               float4* __restrict__ gcol, double2* partial) {
+    __shared__ int s_win;
+    if (threadIdx.x == 0) s_win = 0;
+    __syncthreads();
+    const int i = blockIdx.x * 16 + 2 * (threadIdx.x & 7), j = blockIdx.y * 16 + 2 * (threadIdx.x >> 3);
+    const bool in0 = i < W && j < H;
+    const bool ok[4] = {in0, in0 && i + 1 < W, in0 && j + 1 < H, in0 && i + 1 < W && j + 1 < H};
+    const int ox[4] = {0, 1, 0, 1}, oy[4] = {0, 0, 1, 1};
+    float zq[4], R[4], wnia[4], fia[4];
+    float3 Cq[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        zq[k] = 1.f;
+        R[k] = 0.f;  // an absent source weighs nothing
+        wnia[k] = fia[k] = 0.f;
+        Cq[k] = f3(0, 0, 0);
+        if (ok[k]) {
+            const size_t q = (size_t)(j + oy[k]) * W + (i + ox[k]);
+            zq[k] = __ldg(&nd[q].w);
+            const PfSrc sr = pf_src(zq[k], L, rmax, tab, ntab);
+            R[k] = sr.R;
+            wnia[k] = sr.wnia;
+            fia[k] = sr.fia;
+            Cq[k] = ldf3(__ldg(&col[q]));
+            atomicMax(&s_win, (int)ceilf(sr.R));
+        }
+    }
+    __syncthreads();
     float2 dth = make_float2(0.f, 0.f);
-    if (i < W && j < H) {
-        const size_t q = (size_t)j * W + i;
-        const float zq = __ldg(&nd[q].w);
-        const float c = coc_z(zq, L);
-        const bool clip = fabsf(c) * 0.5f >= rmax;
-        const float r = clip ? rmax : fabsf(c) * 0.5f, R = r + 0.5f;
-        const float rp = clip ? 0.f : (c > 0.f ? 0.5f : (c < 0.f ? -0.5f : 0.f));
-        const float2 as = area_and_slope(tab, ntab, r);
-        const float ia = 1.f / as.x, iap = -as.y * ia * ia * rp;
-        const float wn = w_near(c), wnp = wn_slope(c);
-        const float wnia = wn * ia, fia = (1.f - wn) * ia;
-        const float dwnia = wnp * ia + wn * iap, dfia = -wnp * ia + (1.f - wn) * iap;
-        const float3 Cq = ldf3(__ldg(&col[q]));
+    if (in0) {
+        const int G = s_win;
         const float ka = 1.f + 1.f / kz_rel;
-        float3 gC = f3(0, 0, 0);
-        float S1 = 0.f, S2 = 0.f, S3 = 0.f, S4 = 0.f;
-        const int K = (int)ceilf(R);
-        const int y0 = max(j - K, 0), y1 = min(j + K, H - 1), x0 = max(i - K, 0), x1 = min(i + K, W - 1);
+        PfBwdAcc acc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[k].gC = f3(0, 0, 0);
+            acc[k].S1 = acc[k].S2 = acc[k].S3 = acc[k].S4 = 0.f;
+        }
+        const int y0 = max(j - G, 0), y1 = min(j + 1 + G, H - 1);
+        const float G2 = (float)(G * G);
         for (int y = y0; y <= y1; ++y) {
-            float dy = (float)(y - j);
-            for (int x = x0; x <= x1; ++x) {
-                float dx = (float)(x - i);
-                float u = R - sqrtf(fmaf(dx, dx, dy * dy));
-                if (u <= 0.f) continue;
-                size_t p = (size_t)y * W + x;
-                float s = fminf(u, 1.f), sp = u < 1.f ? 1.f : 0.f;
-                float kz = clamp01(ka - zq / (kz_rel * __ldg(&nd[p].w)));
-                float4 bn = __ldg(&pfb[2 * p]), bf = __ldg(&pfb[2 * p + 1]);
-                float3 An = ldf3(bn), Af = ldf3(bf);
-                gC = gC + (s * wnia) * An + (s * fia * kz) * Af;
-                float tn = dot3f(An, Cq) - bn.w, tf = (dot3f(Af, Cq) - bf.w) * kz;
-                S1 += tn * s;
-                S2 += tn * sp;
-                S3 += tf * s;
-                S4 += tf * sp;
+            const float dy = (float)(y - j);
+            const float dy0 = dy * dy, dy1 = (dy - 1.f) * (dy - 1.f);
+            const int w = (int)ceilf(sqrtf(fmaxf(G2 - fminf(dy0, dy1), 0.f)));
+            const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
+            const size_t prow = (size_t)y * W;
+            float dx = (float)(x0 - i);
+            for (int x = x0; x <= x1; ++x, dx += 1.f) {
+                const size_t p = prow + x;
+                const float kb = 1.f / (kz_rel * __ldg(&nd[p].w));
+                const float4 bn = __ldg(&pfb[2 * p]), bf = __ldg(&pfb[2 * p + 1]);
+                const float3 An = ldf3(bn), Af = ldf3(bf);
+                const float dx0 = dx * dx, dx1 = (dx - 1.f) * (dx - 1.f);
+                const float d2[4] = {dx0 + dy0, dx1 + dy0, dx0 + dy1, dx1 + dy1};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float u = R[k] - sqrt_approx(d2[k]);
+                    const float sw = __saturatef(u), sp = (u > 0.f && u < 1.f) ? 1.f : 0.f;
+                    const float kz = __saturatef(fmaf(-zq[k], kb, ka));
+                    const float an = sw * wnia[k], af = sw * fia[k] * kz;
+                    acc[k].gC.x = fmaf(an, An.x, fmaf(af, Af.x, acc[k].gC.x));
+                    acc[k].gC.y = fmaf(an, An.y, fmaf(af, Af.y, acc[k].gC.y));
+                    acc[k].gC.z = fmaf(an, An.z, fmaf(af, Af.z, acc[k].gC.z));
+                    const float tn = dot3f(An, Cq[k]) - bn.w, tf = (dot3f(Af, Cq[k]) - bf.w) * kz;
+                    acc[k].S1 = fmaf(tn, sw, acc[k].S1);
+                    acc[k].S2 = fmaf(tn, sp, acc[k].S2);
+                    acc[k].S3 = fmaf(tf, sw, acc[k].S3);
+                    acc[k].S4 = fmaf(tf, sp, acc[k].S4);
+                }
             }
         }
-        float4 g0 = gcol[q];
-        gcol[q] = make_float4(g0.x + gC.x, g0.y + gC.y, g0.z + gC.z, 0.f);
-        float gc = S1 * dwnia + S2 * wnia * rp + S3 * dfia + S4 * fia * rp;
-        float2 dc = dcoc(zq, L);
-        dth = make_float2(gc * dc.x, gc * dc.y);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!ok[k]) continue;
+            const size_t q = (size_t)(j + oy[k]) * W + (i + ox[k]);
+            const float4 g0 = gcol[q];
+            gcol[q] = make_float4(g0.x + acc[k].gC.x, g0.y + acc[k].gC.y, g0.z + acc[k].gC.z, 0.f);
+            const PfSrc sr = pf_src(zq[k], L, rmax, tab, ntab);
+            const float gc = acc[k].S1 * sr.dwnia + acc[k].S2 * sr.wnia * sr.rp + acc[k].S3 * sr.dfia +
+                             acc[k].S4 * sr.fia * sr.rp;
+            const float2 dc = dcoc(zq[k], L);
+            dth.x = fmaf(gc, dc.x, dth.x);
+            dth.y = fmaf(gc, dc.y, dth.y);
+        }
     }
     block_partial(dth, partial);
 }
 
-__global__ void k_reduce(const double2* __restrict__ partial, int n, float* out) {
-    __shared__ double red[2][256];
+__global__ void __launch_bounds__(1024) k_reduce(const double2* __restrict__ partial, int n, float* out) {
+    __shared__ double red[2][1024];
     double a = 0.0, b = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         a += partial[k].x;
@@ -708,8 +806,8 @@ extern "C" int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const
                                              reinterpret_cast<const float4*>(hist_samples), b.gcrt, b.ghacc, b.gmom, W,
                                              H, L, p->ema_alpha, p->camera_moved, b.partial + n1);
     k_pf_bwd_prep<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(st->pp_aux), b.gpp, W, H, b.pfb, gcol);
-    k_pf_bwd<<<g2, 256, 0, s>>>(nd, col, b.pfb, tab, ntab, W, H, L, p->r_max, p->kz_rel, gcol, b.partial + 2 * n1);
-    k_reduce<<<1, 256, 0, s>>>(b.partial, b.n_partial, grad_lens);
+    k_pf_bwd<<<g2, 64, 0, s>>>(nd, col, b.pfb, tab, ntab, W, H, L, p->r_max, p->kz_rel, gcol, b.partial + 2 * n1);
+    k_reduce<<<1, 1024, 0, s>>>(b.partial, b.n_partial, grad_lens);
     HDOF_LAUNCHED("hdof_post_backward");
     return HDOF_OK;
 }
