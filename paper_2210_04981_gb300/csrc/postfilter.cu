@@ -30,7 +30,12 @@ namespace hdof {
 namespace {
 
 constexpr int TP = HDOF_TILE_PF;
-constexpr int GATHER_THREADS = 64;
+#ifndef HDOF_PF_RY
+#define HDOF_PF_RY 2  // pixel rows per gather thread (each thread gathers 2 x RY pixels)
+#endif
+constexpr int PF_RY = HDOF_PF_RY;
+constexpr int PF_NPX = 2 * PF_RY;
+constexpr int GATHER_THREADS = 8 * (16 / PF_RY);
 #ifndef HDOF_PF_MINB
 #define HDOF_PF_MINB 10  // resident gather blocks per SM the register budget targets
 #endif
@@ -180,16 +185,20 @@ __device__ __forceinline__ void acc_far(PfAcc& a, float d, float rh, float zq, c
 // weigh; per source row, the columns of that disk (squared distances are
 // exact integers in float)
 template <bool NEAR>
-__device__ __forceinline__ void pf_layer(PfAcc (&a)[4], int G, int i, int j, int W, int H,
+__device__ __forceinline__ void pf_layer(PfAcc (&a)[PF_NPX], int G, int i, int j, int W, int H,
                                          const float* __restrict__ rh, const float* __restrict__ zq,
                                          const float4* __restrict__ rec) {
     if (G < 0) return;  // nothing within reach feeds this layer
-    const int y0 = max(j - G, 0), y1 = min(j + 1 + G, H - 1);
+    const int y0 = max(j - G, 0), y1 = min(j + PF_RY - 1 + G, H - 1);
     const float G2 = (float)(G * G);
     for (int y = y0; y <= y1; ++y) {
         const float dy = (float)(y - j);
-        const float dy0 = dy * dy, dy1 = (dy - 1.f) * (dy - 1.f);
-        const int w = (int)ceilf(sqrtf(fmaxf(G2 - fminf(dy0, dy1), 0.f)));
+        float dyk[PF_RY];
+#pragma unroll
+        for (int k = 0; k < PF_RY; ++k) dyk[k] = (dy - (float)k) * (dy - (float)k);
+        // nearest of the thread's rows to this source row
+        const float dmin = dy >= 0.f && dy <= (float)(PF_RY - 1) ? 0.f : fminf(dyk[0], dyk[PF_RY - 1]);
+        const int w = (int)ceilf(sqrtf(fmaxf(G2 - dmin, 0.f)));
         const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
         const size_t qrow = (size_t)y * W;
         float dx = (float)(x0 - i);
@@ -198,27 +207,24 @@ __device__ __forceinline__ void pf_layer(PfAcc (&a)[4], int G, int i, int j, int
             const float r = __ldg(&rh[qrow + x]);
             const float4 e = __ldg(&rec[qrow + x]);
             const float dx0 = dx * dx, dx1 = (dx - 1.f) * (dx - 1.f);
-            const float d00 = sqrt_approx(dx0 + dy0), d10 = sqrt_approx(dx1 + dy0);
-            const float d01 = sqrt_approx(dx0 + dy1), d11 = sqrt_approx(dx1 + dy1);
-            if (NEAR) {
-                acc_near(a[0], d00, r, e);
-                acc_near(a[1], d10, r, e);
-                acc_near(a[2], d01, r, e);
-                acc_near(a[3], d11, r, e);
-            } else {
-                const float z = __ldg(&zq[qrow + x]);
-                acc_far(a[0], d00, r, z, e);
-                acc_far(a[1], d10, r, z, e);
-                acc_far(a[2], d01, r, z, e);
-                acc_far(a[3], d11, r, z, e);
+            const float z = NEAR ? 0.f : __ldg(&zq[qrow + x]);
+#pragma unroll
+            for (int k = 0; k < PF_RY; ++k) {
+                const float d0 = sqrt_approx(dx0 + dyk[k]), d1 = sqrt_approx(dx1 + dyk[k]);
+                if (NEAR) {
+                    acc_near(a[2 * k], d0, r, e);
+                    acc_near(a[2 * k + 1], d1, r, e);
+                } else {
+                    acc_far(a[2 * k], d0, r, z, e);
+                    acc_far(a[2 * k + 1], d1, r, z, e);
+                }
             }
         }
     }
 }
 
-// 64 threads per 16x16 tile; thread t gathers the 2x2 pixel block at
-// (2 (t & 7), 2 (t >> 3)), so each loaded tap serves four pixels and a warp
-// covers a 16x8 pixel block.
+// 8 x (16 / RY) threads per 16x16 tile; thread t gathers the 2 x RY pixel
+// block at (2 (t & 7), RY (t >> 3)), so each loaded tap serves 2 RY pixels.
 template <class COL>
 __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx, int ty) {
     const COL* __restrict__ col = ar.col;
@@ -244,32 +250,32 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
     }
     __syncthreads();
     const int Gn = s_win[0], Gf = s_win[1];
-    const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + 2 * (threadIdx.x >> 3);
+    const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + PF_RY * (threadIdx.x >> 3);
     if (i >= W || j >= H) return;
-    const bool right = i + 1 < W, down = j + 1 < H;
-    const size_t pq = (size_t)j * W + i;
-    PfAcc a[4];  // (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1)
+    PfAcc a[PF_NPX];  // pixel (i + (k & 1), j + (k >> 1))
     {
         const float ka = 1.f + 1.f / ar.kz_rel;  // k_z = clamp(ka - z_q kb), kb = 1 / (kz_rel z_p)
-        const float z00 = __ldg(&ar.zq[pq]);
-        const float z10 = right ? __ldg(&ar.zq[pq + 1]) : z00;
-        const float z01 = down ? __ldg(&ar.zq[pq + W]) : z00;
-        const float z11 = right && down ? __ldg(&ar.zq[pq + W + 1]) : z00;
-        const float zs[4] = {z00, z10, z01, z11};
+        const float z00 = __ldg(&ar.zq[(size_t)j * W + i]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < PF_NPX; ++k) {
+            const int x = i + (k & 1), y = j + (k >> 1);
+            const float zp = x < W && y < H ? __ldg(&ar.zq[(size_t)y * W + x]) : z00;
             a[k].ka = ka;
-            a[k].kb = 1.f / (ar.kz_rel * zs[k]);
+            a[k].kb = 1.f / (ar.kz_rel * zp);
             a[k].Sn = a[k].Sf = f3(0, 0, 0);
             a[k].Wn = a[k].Wf = 0.f;
         }
     }
     pf_layer<true>(a, Gn, i, j, W, H, ar.rh, ar.zq, ar.nrec);
     pf_layer<false>(a, Gf, i, j, W, H, ar.rh, ar.zq, ar.frec);
-    pp[pq] = pf_finish(a[0], col, pq, aux);
-    if (right) pp[pq + 1] = pf_finish(a[1], col, pq + 1, aux);
-    if (down) pp[pq + W] = pf_finish(a[2], col, pq + W, aux);
-    if (right && down) pp[pq + W + 1] = pf_finish(a[3], col, pq + W + 1, aux);
+#pragma unroll
+    for (int k = 0; k < PF_NPX; ++k) {
+        const int x = i + (k & 1), y = j + (k >> 1);
+        if (x < W && y < H) {
+            const size_t q = (size_t)y * W + x;
+            pp[q] = pf_finish(a[k], col, q, aux);
+        }
+    }
 }
 
 template <class COL>
