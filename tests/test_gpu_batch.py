@@ -138,6 +138,29 @@ def test_batch_degenerate_views(small):
     b.close()
 
 
+def test_batch_stage_ranges_equal_full_render(small):
+    """Running the seven stages one call each (hdof_batch_render_range) gives
+    the same frame as hdof_batch_render; the records upload is counted."""
+    scenes, bvhs, views = small
+    sub = views[:5]
+    a = H.Batch([bvhs[v.room] for v in sub], [(v.width, v.height) for v in sub], [v.params for v in sub])
+    b = H.Batch([bvhs[v.room] for v in sub], [(v.width, v.height) for v in sub], [v.params for v in sub])
+    for k in range(2):
+        a.frame(*_frame_args(sub, k))
+        b.update(*_frame_args(sub, k))
+        for st in range(len(H.BATCH_STAGES)):
+            H.hdof_batch_render_range(b.handle, st, st)
+        b.advance()
+        H.hdof_sync()
+        for i, (ra, rb) in enumerate(zip(a.views, b.views)):
+            _assert_same(ra, rb, f"frame {k} view {i}")
+    assert b.handle_bytes() > 0 and b.handle_bytes() % 256 == 0
+    with pytest.raises(H.HdofError, match="stages"):
+        H.hdof_batch_render_range(b.handle, 3, 7)
+    a.close()
+    b.close()
+
+
 def test_batch_rejects_changed_sizes(small):
     scenes, bvhs, views = small
     b = H.Batch([bvhs[v.room] for v in views[:2]], [(v.width, v.height) for v in views[:2]],
