@@ -315,7 +315,10 @@ __global__ void k_depth(const int* __restrict__ leaf_parent, const Node* __restr
 #ifndef HDOF_BUILDER
 #define HDOF_BUILDER 1  // 1: PLOC, 0: LBVH
 #endif
-constexpr int PLOC_R = 16;
+#ifndef HDOF_PLOC_R
+#define HDOF_PLOC_R 48  // nearest-neighbour search radius of the clustering (measured best of 8..96 overall)
+#endif
+constexpr int PLOC_R = HDOF_PLOC_R;
 constexpr int PLOC_B = 256;
 
 __device__ __forceinline__ float union_area(float4 alo, float4 ahi, float4 blo, float4 bhi) {
