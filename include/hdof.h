@@ -157,7 +157,7 @@ void hdof_default_params(hdof_params* p);
  * the GPU by parallel locally-ordered clustering (Meister and Bittner 2018):
  * 63-bit Morton codes of the triangle centroids, radix sort, then rounds
  * that merge mutual nearest neighbours (smallest union-box surface area
- * within 16 positions) until one cluster remains.  One triangle per leaf.
+ * within 48 positions) until one cluster remains.  One triangle per leaf.
  * verts: float [n_verts][3]; idx: int32 [n_tris][3];
  * mat: float [n_tris][8] = (albedo_a rgb, checker_n, albedo_b rgb, 0);
  * uv: float [n_tris][6] (may be NULL when no material uses a checker).
@@ -187,8 +187,8 @@ int hdof_gbuffer(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_camera*
 
 /* ---------------------------------------------------- scratch memory -- */
 /* Bytes of caller-owned device scratch the calls below need for a
- * width x height frame (the maximum over calls; one buffer serves them all
- * when they run in order on one stream).  The trace's share grows with
+ * width x height frame (one buffer serves them all when they run in order
+ * on one stream).  The trace's share grows with
  * p->spp_max: 21 bytes per possible ray (pixel, sample index, record).  The
  * post-filter's region is disjoint from the mask's and the trace's, so
  * hdof_postfilter may run on another stream concurrently with hdof_mask and
