@@ -338,7 +338,7 @@ typedef struct hdof_batch hdof_batch;
 /* Prepares a batch: validates every view, builds each stage's per-view
  * launch records and block tables and copies them to device memory the
  * handle owns (synchronous).  The views' buffers must stay valid while the
- * handle is used.  tuning may be NULL (defaults 128 / 8). */
+ * handle is used.  tuning may be NULL (defaults 128 / 4). */
 int hdof_batch_create(const hdof_view* views, int32_t n_views, const hdof_tuning* tuning, hdof_batch** out,
                       void* stream);
 int hdof_batch_destroy(hdof_batch* batch);

@@ -179,7 +179,7 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     *out = nullptr;
     HDOF_CHECK_ARG(views && n_views >= 1 && n_views <= 65536, "hdof_batch_create: need 1..65536 views, got %d",
                    (int)n_views);
-    hdof_tuning t = {128, 8, {0, 0}};
+    hdof_tuning t = {128, 4, {0, 0}};
     if (tuning) t = *tuning;
     HDOF_CHECK_ARG(t.trace_block == 64 || t.trace_block == 128 || t.trace_block == 256,
                    "hdof_batch_create: trace_block %d not in {64, 128, 256}", (int)t.trace_block);

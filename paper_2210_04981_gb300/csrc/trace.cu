@@ -626,7 +626,7 @@ using namespace hdof;
 #define HDOF_TRACE_BLOCK 128
 #endif
 #ifndef HDOF_TRACE_REFILL
-#define HDOF_TRACE_REFILL 8
+#define HDOF_TRACE_REFILL 4
 #endif
 
 extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,

@@ -409,7 +409,7 @@ class Renderer:
 
 # ------------------------------------------------------ batched multi-view --
 
-def tuning(trace_block=128, trace_refill=8) -> hdof_tuning:
+def tuning(trace_block=128, trace_refill=4) -> hdof_tuning:
     t = hdof_tuning()
     t.trace_block, t.trace_refill = int(trace_block), int(trace_refill)
     return t
