@@ -689,7 +689,7 @@ def cpu_baseline(args, budget_s=30.0):
     cams = [hi.room_camera(k, W, Hh) for k in range(2)]
     osc = O.OScene(scene)
     hist = O.empty_history(W, Hh)
-    stride = 64
+    stride = 16
     _, t, est = oracle_frame_sample(O, osc, cams, lens, p0, 0, hist, W, Hh, stride)
     return {"value": round(est * 1e3, 1), "unit": "ms/frame", "cores": O.num_threads(), "kind": "oracle",
             "sample": f"frame 0 at {W}x{Hh}: all stages full-frame except post-filter+composite, timed on seeded "
@@ -747,7 +747,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
-    ap.add_argument("--ref-pf-stride", type=int, default=256)
+    ap.add_argument("--ref-pf-stride", type=int, default=16)
     ap.add_argument("--views", type=int, default=64, help="views of the batched workload (--scene batch)")
     args = ap.parse_args()
     if args.warmup < 3:
