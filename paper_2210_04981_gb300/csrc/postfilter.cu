@@ -40,7 +40,7 @@ constexpr int GATHER_THREADS = 8 * (16 / PF_RY);
 #define HDOF_PF_MINB 10  // resident gather blocks per SM the register budget targets
 #endif
 #ifndef HDOF_PF_UNROLL
-#define HDOF_PF_UNROLL 2  // unroll of the gather's tap loop
+#define HDOF_PF_UNROLL 4  // unroll of the gather's tap loop
 #endif
 constexpr int PF_UNROLL = HDOF_PF_UNROLL;
 // Shared-memory carve-out (percent of the maximum) for the gather: the taps
