@@ -192,6 +192,11 @@ __global__ void __launch_bounds__(256) k_temporal_batch(const TemporalBatch* __r
     temporal_body(r.t, r.nd, bx, by);
 }
 
+#ifndef HDOF_SP_UNROLL
+#define HDOF_SP_UNROLL 4  // unroll of the spatial gather's tap loop
+#endif
+constexpr int SP_UNROLL = HDOF_SP_UNROLL;
+
 struct SpatialArgs {
     const float4* crt;
     const float2* mom;
@@ -247,6 +252,7 @@ __device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int b
         const int x0 = max(i - wr, 0), x1 = min(i + wr, W - 1);
         const float4* row = crt + (size_t)y * W;
         float dx = (float)(x0 - i);
+#pragma unroll SP_UNROLL
         for (int x = x0; x <= x1; ++x, dx += 1.f) {
             const float4 c = __ldg(&row[x]);
             const float d = sqrt_approx(fmaf(dx, dx, dy2));
