@@ -434,6 +434,76 @@ __global__ void k_closest(BvhView bvh, int n, const float* __restrict__ org, con
 
 int blocks_for(long n, int bs) { return (int)((n + bs - 1) / bs); }
 
+// ---- depth-first relabelling of the internal nodes --------------------------
+// The clustering numbers nodes in merge order, which scatters a parent and its
+// children over memory.  Relabelling in depth-first pre-order (a node, then
+// its first child's subtree, then its second child's) keeps every subtree in
+// one contiguous range and puts a node's first child right after it, so a
+// descent touches neighbouring cache lines.  The tree itself is unchanged.
+
+__global__ void k_dfs_parent(const Node* __restrict__ nodes, int n, int* parent, int* nint) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 c = nodes[i].child;
+    int k = 0;
+    if (c.x >= 0) {
+        parent[c.x] = i;
+        ++k;
+    }
+    if (c.y >= 0) {
+        parent[c.y] = i;
+        ++k;
+    }
+    nint[i] = k;
+}
+
+// subtree sizes (internal nodes) bottom-up: a node with no internal child
+// starts a walk; the last child to arrive at a parent carries the walk on
+__global__ void k_dfs_size(const Node* __restrict__ nodes, int n, int root, const int* __restrict__ parent,
+                           const int* __restrict__ nint, unsigned* arrived, int* size) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || nint[i] != 0) return;
+    int c = i;
+    size[c] = 1;
+    for (int guard = 0; c != root && guard < n; ++guard) {  // a walk is at most the tree's depth
+        const int p = parent[c];
+        __threadfence();
+        if (atomicAdd(&arrived[p], 1u) + 1 < (unsigned)nint[p]) return;  // the other child is not done yet
+        __threadfence();
+        const int4 ch = nodes[p].child;
+        size[p] = 1 + (ch.x >= 0 ? __ldcg(&size[ch.x]) : 0) + (ch.y >= 0 ? __ldcg(&size[ch.y]) : 0);
+        c = p;
+    }
+}
+
+// pre-order index: 1 per ancestor step, plus the first child's subtree when
+// the path goes through a second child
+__global__ void k_dfs_index(const Node* __restrict__ nodes, int n, int root, const int* __restrict__ parent,
+                            const int* __restrict__ size, int* index) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int idx = 0, c = i;
+    for (int guard = 0; c != root && guard < n; ++guard) {
+        const int p = parent[c];
+        const int4 ch = nodes[p].child;
+        idx += 1;
+        if (c == ch.y && ch.x >= 0) idx += size[ch.x];
+        c = p;
+    }
+    index[i] = idx;
+}
+
+__global__ void k_dfs_permute(const Node* __restrict__ nodes, int n, const int* __restrict__ parent,
+                              const int* __restrict__ index, int root, Node* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Node nd = nodes[i];
+    if (nd.child.x >= 0) nd.child.x = index[nd.child.x];
+    if (nd.child.y >= 0) nd.child.y = index[nd.child.y];
+    nd.child.z = i == root ? -1 : index[parent[i]];
+    out[index[i]] = nd;
+}
+
 }  // namespace
 }  // namespace hdof
 
@@ -639,6 +709,36 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
         depth = h;
         b->n_nodes = m - 1;
         b->root = root_ref;
+        if (root_ref >= 0 && m - 1 > 1) {
+            const int ni = m - 1;
+            // scratch: parent, nint, arrived, size, index (ints) + a node copy
+            size_t q0 = 0, q1 = q0 + up256(4 * (size_t)ni), q2 = q1 + up256(4 * (size_t)ni);
+            size_t q3 = q2 + up256(4 * (size_t)ni), q4 = q3 + up256(4 * (size_t)ni);
+            size_t q5 = q4 + up256(4 * (size_t)ni), qtot = q5 + sizeof(Node) * (size_t)ni;
+            void* rt = nullptr;
+            if ((e = cudaMalloc(&rt, qtot)) != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: cudaMalloc"));
+            char* r8 = static_cast<char*>(rt);
+            int* parent = reinterpret_cast<int*>(r8 + q0);
+            int* nint = reinterpret_cast<int*>(r8 + q1);
+            unsigned* arrived = reinterpret_cast<unsigned*>(r8 + q2);
+            int* size = reinterpret_cast<int*>(r8 + q3);
+            int* index = reinterpret_cast<int*>(r8 + q4);
+            Node* copy = reinterpret_cast<Node*>(r8 + q5);
+            const int nb = blocks_for(ni, 256);
+            if ((e = cudaMemsetAsync(arrived, 0, 4 * (size_t)ni, s)) == cudaSuccess) {
+                k_dfs_parent<<<nb, 256, 0, s>>>(b->nodes, ni, parent, nint);
+                k_dfs_size<<<nb, 256, 0, s>>>(b->nodes, ni, root_ref, parent, nint, arrived, size);
+                k_dfs_index<<<nb, 256, 0, s>>>(b->nodes, ni, root_ref, parent, size, index);
+                k_dfs_permute<<<nb, 256, 0, s>>>(b->nodes, ni, parent, index, root_ref, copy);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->nodes, copy, sizeof(Node) * (size_t)ni, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFree(rt);
+            if (e != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: relabel"));
+            b->root = 0;
+        }
     }
     b->depth = depth;
     if (depth + 1 >= HDOF_STACK) {
