@@ -189,7 +189,7 @@ int hdof_gbuffer(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_camera*
 /* Bytes of caller-owned device scratch the calls below need for a
  * width x height frame (one buffer serves them all when they run in order
  * on one stream).  The trace's share grows with
- * p->spp_max: 21 bytes per possible ray (pixel, sample index, record).  The
+ * p->spp_max: 13 bytes per possible ray (pixel, sample index, record).  The
  * post-filter's region is disjoint from the mask's and the trace's, so
  * hdof_postfilter may run on another stream concurrently with hdof_mask and
  * hdof_trace once hdof_gbuffer has finished. */

@@ -121,7 +121,7 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     l.trace_qoff = align256(npx * sizeof(unsigned));
     l.trace_ray_pix = align256(nray * sizeof(unsigned));
     l.trace_ray_s = align256(nray);
-    l.trace_rec = align256(nray * sizeof(float4));
+    l.trace_rec = align256(nray * sizeof(float2));
     l.trace = l.trace_counts + l.trace_queue + l.trace_qoff + l.trace_ray_pix + l.trace_ray_s + l.trace_rec;
     l.pf_nrec = align256(npx * sizeof(float4));
     l.pf_frec = align256(npx * sizeof(float4));

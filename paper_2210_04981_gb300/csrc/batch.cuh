@@ -61,7 +61,7 @@ struct ViewWs {
     unsigned* qoff;      // [W * H] first ray of each queue entry
     unsigned* ray_pix;   // [W * H * spp_max] pixel of each ray
     uint8_t* ray_s;      // [W * H * spp_max] sample index of each ray
-    float4* rec;         // [W * H * spp_max] (radiance, hit distance) of each ray
+    float2* rec;         // [W * H * spp_max] (hit distance, triangle) of each ray
     float4* nrec;        // post-filter near-layer record per pixel
     float4* frec;        // post-filter far-layer record per pixel
     float* rh;           // post-filter r + 1/2 per pixel
@@ -94,7 +94,7 @@ inline ViewWs view_ws(const hdof_view& v) {
     w.qoff = reinterpret_cast<unsigned*>(base + (o += L.trace_queue));
     w.ray_pix = reinterpret_cast<unsigned*>(base + (o += L.trace_qoff));
     w.ray_s = reinterpret_cast<uint8_t*>(base + (o += L.trace_ray_pix));
-    w.rec = reinterpret_cast<float4*>(base + (o += L.trace_ray_s));
+    w.rec = reinterpret_cast<float2*>(base + (o += L.trace_ray_s));
     pf_regions(w, base + L.pf_off, L);
     return w;
 }

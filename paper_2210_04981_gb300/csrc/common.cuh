@@ -286,16 +286,45 @@ __device__ __forceinline__ bool intersect_tri(float3 o, const Shear& s, float3 v
         W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
     }
     if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
-    float det = U + V + W;
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
     if (det == 0.f) return false;
-    float T = U * (s.Sz * Akz) + V * (s.Sz * Bkz) + W * (s.Sz * Ckz);
+    const float T = __fadd_rn(__fadd_rn(__fmul_rn(U, __fmul_rn(s.Sz, Akz)), __fmul_rn(V, __fmul_rn(s.Sz, Bkz))),
+                              __fmul_rn(W, __fmul_rn(s.Sz, Ckz)));
     if (det > 0.f ? !(T > 0.f) : !(T < 0.f)) return false;
-    float inv = 1.f / det;
-    t = T * inv;
-    b0 = U * inv;
-    b1 = V * inv;
-    b2 = W * inv;
+    const float inv = __frcp_rn(det);
+    t = __fmul_rn(T, inv);
+    b0 = __fmul_rn(U, inv);
+    b1 = __fmul_rn(V, inv);
+    b2 = __fmul_rn(W, inv);
     return true;
+}
+
+// Barycentrics of a known hit, recomputed with the arithmetic of
+// intersect_tri (same inputs give the same values) but without its rejection
+// tests, so a hit found by the traversal is always reproduced.
+__device__ __forceinline__ void tri_bary(float3 o, const Shear& s, float3 v0, float3 v1, float3 v2, float& b0,
+                                         float& b1, float& b2) {
+    float3 A = v0 - o, B = v1 - o, C = v2 - o;
+    float Akz = comp(A, s.kz), Bkz = comp(B, s.kz), Ckz = comp(C, s.kz);
+    float Ax = __fsub_rn(comp(A, s.kx), __fmul_rn(s.Sx, Akz));
+    float Ay = __fsub_rn(comp(A, s.ky), __fmul_rn(s.Sy, Akz));
+    float Bx = __fsub_rn(comp(B, s.kx), __fmul_rn(s.Sx, Bkz));
+    float By = __fsub_rn(comp(B, s.ky), __fmul_rn(s.Sy, Bkz));
+    float Cx = __fsub_rn(comp(C, s.kx), __fmul_rn(s.Sx, Ckz));
+    float Cy = __fsub_rn(comp(C, s.ky), __fmul_rn(s.Sy, Ckz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.f || V == 0.f || W == 0.f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
+    const float inv = det != 0.f ? __frcp_rn(det) : 0.f;
+    b0 = __fmul_rn(U, inv);
+    b1 = __fmul_rn(V, inv);
+    b2 = __fmul_rn(W, inv);
 }
 
 struct Hit {

@@ -61,7 +61,7 @@ struct WsLayout {
     size_t trace_qoff;      // uint32 per pixel: first ray of each queue entry
     size_t trace_ray_pix;   // uint32 per possible ray (pixels x spp_max): its pixel
     size_t trace_ray_s;     // uint8 per possible ray: its sample index
-    size_t trace_rec;       // float4 per possible ray: radiance, hit distance
+    size_t trace_rec;       // float2 per possible ray: hit distance, triangle
     size_t trace;           // sum of the trace regions (laid out in this order)
     size_t pf_nrec;         // float4 per pixel: near-layer record
     size_t pf_frec;         // float4 per pixel: far-layer record

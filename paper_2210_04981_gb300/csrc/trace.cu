@@ -200,7 +200,7 @@ struct TraceArgs {
     const unsigned* ray_pix;
     const uint8_t* ray_s;
     unsigned* totals;  // [0] queue length, [2] ray count, [3] ray head
-    float4* recs;      // per ray (radiance rgb, hit distance t; +inf for a miss)
+    float2* recs;      // per ray (hit distance t, +inf for a miss; sorted triangle slot as int bits)
     float4* rt;        // 3 float4 per pixel
     float4* rec;       // optional per-ray (L rgb, view depth z) records, z = +inf for a miss
     const unsigned* ray_off;
@@ -369,13 +369,9 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
                         if (slab(ray, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, h.t) < INF)
                             hit_tri(bvh, bvh.big_first + k, ray.o, sh, h);
                     }
-                    float4 out = make_float4(0.f, 0.f, 0.f, INF);
-                    if (h.slot >= 0) {
-                        float3 nrm, L;
-                        shade(bvh, a.L, h, ray.d, nrm, L);
-                        out = make_float4(L.x, L.y, L.z, h.t);
-                    }
-                    a.recs[r] = out;
+                    // shading happens per pixel in the resolve, not here where
+                    // few lanes of the warp finish at a time
+                    a.recs[r] = make_float2(h.slot >= 0 ? h.t : INF, __int_as_float(h.slot));
                     live = false;
                 }
             }
@@ -397,8 +393,9 @@ __global__ void __launch_bounds__(BS) k_trace_rays_batch(const TraceArgs* __rest
 }
 
 // per traced pixel (queue entry k): its samples' records in sample order ->
-// near/far layer sums -> the normalised rt record (and the adjoint's per-ray
-// (L, z) records when requested)
+// shading of each hit (its barycentrics recomputed from the recorded
+// triangle) -> near/far layer sums -> the normalised rt record (and the
+// adjoint's per-ray (L, z) records when requested)
 __device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
     const unsigned k = (unsigned)bx * 256u + threadIdx.x;
     if (k >= __ldcg(&a.totals[0])) return;
@@ -409,13 +406,24 @@ __device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
     for (int smp = 0; smp < n; ++smp) {
         float3 O, dir;
         lens_ray(a, q, (unsigned)smp, O, dir);
-        const float4 rc = a.recs[ro + smp];
-        const bool hit = rc.w < __int_as_float(0x7f800000);
-        const float3 L = f3(rc.x, rc.y, rc.z);
+        const float2 rc = a.recs[ro + smp];
+        const int slot = __float_as_int(rc.y);
+        const bool hit = slot >= 0;
+        float3 L = f3(0.f, 0.f, 0.f);
         float3 P;
         float c;
         if (hit) {
-            P = O + rc.w * dir;
+            Hit h;
+            h.t = rc.x;
+            h.slot = slot;
+            const Tri* tr = a.bvh.tris + slot;
+            const float4 p0 = __ldg(&tr->v0), p1 = __ldg(&tr->v1), p2 = __ldg(&tr->v2);
+            h.id = __float_as_int(p0.w);
+            tri_bary(O, make_shear(dir), f3(p0.x, p0.y, p0.z), f3(p1.x, p1.y, p1.z), f3(p2.x, p2.y, p2.z), h.b0, h.b1,
+                     h.b2);
+            float3 nrm;
+            shade(a.bvh, a.L, h, dir, nrm, L);
+            P = O + rc.x * dir;
             c = a.coc(dot(P - a.cam.pos, a.cam.fwd));
         } else {
             P = O + a.miss_dist * dir;
