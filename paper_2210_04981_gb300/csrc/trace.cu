@@ -171,15 +171,29 @@ __device__ __forceinline__ void scatter_body(const ScatterArgs& a, int bx, int b
         base += wcnt[k];
         rbase += wray[k];
     }
+    const unsigned q = (unsigned)(j * W + i);
     if (on) {
-        const unsigned k = base + __popc(m & ((1u << lane) - 1u)), q = (unsigned)(j * W + i), ro = rbase + r - n;
+        const unsigned k = base + __popc(m & ((1u << lane) - 1u)), ro = rbase + r - n;
         queue[k] = q;
         qoff[k] = ro;
-        for (unsigned smp = 0; smp < n; ++smp) {
-            ray_pix[ro + smp] = q;
-            ray_s[ro + smp] = (uint8_t)smp;
-        }
         if (ray_off) ray_off[q] = ro;
+    }
+    // the warp's rays are contiguous from rbase: lanes write them together,
+    // entry e going to the lane whose inclusive spp prefix first exceeds e
+    const unsigned total = __shfl_sync(0xffffffffu, r, 31), first = r - n;
+    for (unsigned e0 = 0; e0 < total; e0 += 32) {
+        const unsigned e = e0 + lane;
+        unsigned owner = 0;  // lanes with prefix <= e
+#pragma unroll
+        for (unsigned b = 16; b > 0; b >>= 1) {
+            const unsigned rt = __shfl_sync(0xffffffffu, r, owner + b - 1);
+            if (rt <= e) owner += b;
+        }
+        const unsigned qo = __shfl_sync(0xffffffffu, q, owner), fo = __shfl_sync(0xffffffffu, first, owner);
+        if (e < total) {
+            ray_pix[rbase + e] = qo;
+            ray_s[rbase + e] = (uint8_t)(e - fo);
+        }
     }
 }
 
