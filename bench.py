@@ -220,7 +220,7 @@ def run_ours(args):
         calls = [
             lambda: H.hdof_gbuffer(bvh, cam, prev, p, r.g),
             lambda: H.hdof_mask(r.g, hin, p, r.edge, r.spp, r.ws),
-            lambda: H.hdof_trace(bvh, cam, lens, p, r.spp, r.rt, r.stats, r.ws),
+            lambda: H.hdof_trace(bvh, cam, lens, p, r.spp, r.rt, r.stats, r.ws, hint=r.g.tri),
             lambda: H.hdof_postfilter(r.g, cam, lens, p, r.pp, r.ws),
             lambda: H.hdof_reconstruct(r.rt, r.g, r.spp, cam, prev, lens, p, hin, hout, r.crt, r.hacc, r.crec),
             lambda: H.hdof_composite(r.g, r.spp, r.pp, r.crt, r.crec, r.hacc, cam, lens, p, r.out),

@@ -242,6 +242,10 @@ int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const 
  * rt: float [H][W][12] = (C_near rgb, h | C_far rgb, c_near | P_far xyz,
  * c_far); h = sum w / n is the hit ratio; an empty layer (weight < 1e-6)
  * has colour 0 and CoC -1.  Untraced pixels are not written.
+ * hint_tri (device, may be NULL): int32 [H][W] original id of each pixel's
+ * primary hit (the G-buffer's tri plane, < 0 for none); each lens ray tests
+ * that triangle first, which only tightens the traversal (results do not
+ * depend on it).
  * stats (device, may be NULL): uint32 [2] = (traced pixels, rays).
  * rec, ray_off (device, both NULL or both set): per-ray hit records
  * rec[ray_off[p] + s] = (L rgb, view depth of the hit, +inf for a miss) of
@@ -249,8 +253,9 @@ int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const 
  * hdof_post_forward/backward re-evaluate at another focus and aperture;
  * rec holds stats[1] float4 entries (at most spp_max x W x H). */
 int hdof_trace(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* lens,
-               const hdof_params* p, const uint8_t* spp, float* rt, uint32_t* stats,
-               float* rec, uint32_t* ray_off, void* workspace, size_t workspace_bytes, void* stream);
+               const hdof_params* p, const uint8_t* spp, const int32_t* hint_tri, float* rt,
+               uint32_t* stats, float* rec, uint32_t* ray_off, void* workspace,
+               size_t workspace_bytes, void* stream);
 
 /* ----------------------------------------------------- post-filter -- */
 /* CoC gather post-filter of the sharp image (Design section; the rejection

@@ -249,10 +249,11 @@ __global__ void k_refit(const float* __restrict__ v, const int* __restrict__ idx
 
 __global__ void k_leaf_data(const float* __restrict__ v, const int* __restrict__ idx, const float* __restrict__ mat,
                             const float* __restrict__ uv, const int* __restrict__ ids, int n, Tri* tris,
-                            float4* mato, float2* uvo) {
+                            float4* mato, float2* uvo, int* slot_of) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int id = ids[k];
+    slot_of[id] = k;
     int a = idx[3 * id], b = idx[3 * id + 1], c = idx[3 * id + 2];
     Tri t;
     t.v0 = make_float4(v[3 * a], v[3 * a + 1], v[3 * a + 2], __int_as_float(id));
@@ -601,7 +602,8 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
     size_t off_mat = off_tris + up256(sizeof(Tri) * (size_t)n);
     size_t off_uv = off_mat + up256(sizeof(float4) * 2 * (size_t)n);
     size_t off_big = off_uv + up256(sizeof(float2) * 3 * (size_t)n);
-    size_t total = off_big + sizeof(float4) * 2 * (size_t)(n_big > 0 ? n_big : 1);
+    size_t off_slot = off_big + up256(sizeof(float4) * 2 * (size_t)(n_big > 0 ? n_big : 1));
+    size_t total = off_slot + sizeof(int) * (size_t)n;
     if ((e = cudaMalloc(&b->pool, total)) != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: cudaMalloc"));
     b->bytes = total;
     char* base = static_cast<char*>(b->pool);
@@ -610,13 +612,15 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
     b->mat = reinterpret_cast<float4*>(base + off_mat);
     b->uv = reinterpret_cast<float2*>(base + off_uv);
     b->big_box = reinterpret_cast<float4*>(base + off_big);
+    b->slot_of = reinterpret_cast<int*>(base + off_slot);
 
     // Morton codes and radix sort (scene-sized triangles keyed last)
     k_morton<<<blocks_for(n, 256), 256, 0, s>>>(verts, idx, n, cbounds, separate ? big : nullptr, keys_in, ids_in);
     e = cub::DeviceRadixSort::SortPairs(sort_tmp, sort_bytes, keys_in, keys_out, ids_in, ids_out, n, 0,
                                         separate ? 64 : 63, s);
     if (e != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: sort"));
-    k_leaf_data<<<blocks_for(n, 256), 256, 0, s>>>(verts, idx, mat, uv, ids_out, n, b->tris, b->mat, b->uv);
+    k_leaf_data<<<blocks_for(n, 256), 256, 0, s>>>(verts, idx, mat, uv, ids_out, n, b->tris, b->mat, b->uv,
+                                                    b->slot_of);
     if (n_big > 0) k_big_boxes<<<1, 64, 0, s>>>(b->tris, n - n_big, n_big, b->big_box);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: leaf data"));
 

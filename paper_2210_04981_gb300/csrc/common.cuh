@@ -188,6 +188,7 @@ struct BvhView {
     int big_first;      // sorted slots [big_first, big_first + big_count) hold scene-sized
     int big_count;      //   triangles tested by every ray after the traversal
     const float4* big_box;  // [2] per scene-sized triangle: (lo xyz, 0), (hi xyz, 0)
+    const int* slot_of;     // sorted slot of each original triangle id
 };
 
 struct Ray {

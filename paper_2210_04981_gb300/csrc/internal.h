@@ -106,6 +106,7 @@ struct hdof_bvh {
     float4* mat;
     float2* uv;
     float4* big_box;  // [2 * n_big]
+    int* slot_of;     // [n_tris] sorted slot of each original triangle id
     void* pool;  // single allocation holding all of the above
     hdof::BvhView view() const {
         hdof::BvhView v;
@@ -118,6 +119,7 @@ struct hdof_bvh {
         v.big_first = n_tris - n_big;
         v.big_count = n_big;
         v.big_box = big_box;
+        v.slot_of = slot_of;
         return v;
     }
 };

@@ -209,6 +209,7 @@ struct TraceArgs {
     int cap, smax;
     unsigned* status;
     const uint8_t* spp;
+    const int* hint;   // optional per-pixel original id of the primary hit (< 0: none)
     const unsigned* queue;
     const unsigned* qoff;
     const unsigned* ray_pix;
@@ -300,14 +301,22 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
                 if (g < total) {
                     v = src.locate(g, r);
                     const TraceArgs& a = src.at(v);
+                    const unsigned qp = __ldg(&a.ray_pix[r]);
                     float3 O, dir;
-                    lens_ray(a, __ldg(&a.ray_pix[r]), __ldg(&a.ray_s[r]), O, dir);
+                    lens_ray(a, qp, __ldg(&a.ray_s[r]), O, dir);
                     ray = make_ray(O, dir);
                     sh = make_shear(dir);
                     h.t = INF;
                     h.slot = -1;
                     h.id = 0x7fffffff;
                     h.b0 = h.b1 = h.b2 = 0.f;
+                    if (a.hint) {
+                        // the pixel's primary hit first: a lens ray often hits the same
+                        // triangle, and the tight distance culls what lies behind it (the
+                        // closest hit, the minimum of (t, id) over all hits, is unchanged)
+                        const int id = __ldg(&a.hint[qp]);
+                        if (id >= 0 && id < a.bvh.n_tris) hit_tri(a.bvh, __ldg(&a.bvh.slot_of[id]), ray.o, sh, h);
+                    }
                     cur = a.bvh.root;
                     leaf = NO_LEAF;
                     if (cur < 0) {  // the whole tree is one leaf
@@ -466,7 +475,7 @@ __device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
 __global__ void __launch_bounds__(256) k_resolve(TraceArgs a) { resolve_body(a, blockIdx.x); }
 
 TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
-                     unsigned* st, const uint8_t* spp, const ViewWs& w, float* rt, float* rec,
+                     unsigned* st, const uint8_t* spp, const int* hint, const ViewWs& w, float* rt, float* rec,
                      const unsigned* ray_off) {
     TraceArgs a;
     a.bvh = b->view();
@@ -481,6 +490,7 @@ TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens*
     a.smax = p->spp_max;
     a.status = st;
     a.spp = spp;
+    a.hint = hint;
     a.queue = w.queue;
     a.qoff = w.qoff;
     a.ray_pix = w.ray_pix;
@@ -618,8 +628,8 @@ void scatter_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_
 
 size_t trace_args_size() { return sizeof(TraceArgs); }
 void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst, int* gx, int* gy) {
-    *reinterpret_cast<TraceArgs*>(dst) = trace_args(v.bvh, &v.cam, &v.lens, &v.params, st, v.spp, w, v.rt, nullptr,
-                                                    nullptr);
+    *reinterpret_cast<TraceArgs*>(dst) =
+        trace_args(v.bvh, &v.cam, &v.lens, &v.params, st, v.spp, v.g.tri, w, v.rt, nullptr, nullptr);
     *gx = (v.cam.width * v.cam.height + 255) / 256;  // resolve: one thread per possible queue entry
     *gy = 1;
 }
@@ -652,8 +662,8 @@ using namespace hdof;
 #endif
 
 extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
-                          const uint8_t* spp, float* rt, uint32_t* stats, float* rec, uint32_t* ray_off,
-                          void* workspace, size_t workspace_bytes, void* stream) {
+                          const uint8_t* spp, const int32_t* hint_tri, float* rt, uint32_t* stats, float* rec,
+                          uint32_t* ray_off, void* workspace, size_t workspace_bytes, void* stream) {
     clear_error();
     HDOF_CHECK_ARG(b, "hdof_trace: bvh is NULL");
     int rc;
@@ -682,7 +692,7 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
         ScatterArgs{spp, W, H, ntx, p->spp_max, w.offsets, w.roffsets, w.queue, w.qoff, w.ray_pix, w.ray_s, ray_off});
     HDOF_LAUNCHED("hdof_trace: compaction");
 
-    TraceArgs a = trace_args(b, cam, lens, p, st, spp, w, rt, rec, ray_off);
+    TraceArgs a = trace_args(b, cam, lens, p, st, spp, hint_tri, w, rt, rec, ray_off);
     int blocks = 0;
     if ((rc = rays_grid(false, HDOF_TRACE_BLOCK, &blocks))) return rc;
     k_trace_rays<HDOF_TRACE_BLOCK><<<blocks, HDOF_TRACE_BLOCK, 0, s>>>(a, HDOF_TRACE_REFILL);

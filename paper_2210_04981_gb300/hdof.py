@@ -110,7 +110,8 @@ def load():
         "hdof_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
         "hdof_mask": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp, sz, vp], C.c_int),
         "hdof_mask_noalloc": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp], C.c_int),
-        "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
+        "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, vp, vp, vp, sz, vp],
+                       C.c_int),
         "hdof_postfilter": ([P(hdof_gbuf), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, sz, vp],
                             C.c_int),
         "hdof_reconstruct": ([vp, P(hdof_gbuf), vp, P(hdof_camera), P(hdof_camera), P(hdof_lens),
@@ -329,11 +330,13 @@ def hdof_mask_noalloc(gbuf: GBuffer, prev_hist, p, edge, spp, stream=None):
                                     _stream(stream)))
 
 
-def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None, rec=None, ray_off=None):
+def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None, rec=None, ray_off=None, hint=None):
     """rec (float [n_rays][4]) and ray_off (int32 [H][W]) optionally receive
-    the per-ray hit records (L rgb, z) and each traced pixel's first ray."""
+    the per-ray hit records (L rgb, z) and each traced pixel's first ray;
+    hint (int32 [H][W], the G-buffer's tri plane) optionally seeds each lens
+    ray with its pixel's primary hit."""
     _check(load().hdof_trace(bvh.handle, C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)),
-                             _ptr(spp), _ptr(rt), _ptr(stats), _ptr(rec), _ptr(ray_off), _ptr(workspace),
+                             _ptr(spp), _ptr(hint), _ptr(rt), _ptr(stats), _ptr(rec), _ptr(ray_off), _ptr(workspace),
                              workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
@@ -398,7 +401,7 @@ class Renderer:
         hout = self.hist[1 - self.cur]
         hdof_gbuffer(self.bvh, cam, prev, p, self.g, stream)
         hdof_mask(self.g, hin if with_history else None, p, self.edge, self.spp, self.ws, stream)
-        hdof_trace(self.bvh, cam, lns, p, self.spp, self.rt, self.stats, self.ws, stream)
+        hdof_trace(self.bvh, cam, lns, p, self.spp, self.rt, self.stats, self.ws, stream, hint=self.g.tri)
         hdof_postfilter(self.g, cam, lns, p, self.pp, self.ws, stream)
         hdof_reconstruct(self.rt, self.g, self.spp, cam, prev, lns, p, hin, hout, self.crt, self.hacc,
                          self.crec, stream)

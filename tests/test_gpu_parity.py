@@ -277,6 +277,31 @@ def test_trace_room(orc):
     assert ok.mean() >= 0.999, f"{(~ok).sum()} of {ok.size}; " + report("rt", rt[traced], ref[traced])
 
 
+def test_trace_hint_does_not_change_results():
+    """Seeding the lens rays with the primary hit (or with arbitrary ids,
+    out-of-range ones included) gives the same trace bit for bit."""
+    W, Hh = 320, 180
+    scene = hi.room_scene(seed=1, aspect=W / Hh)
+    cam = hi.room_camera(1, W, Hh)
+    lens = hi.room_lens()
+    p = hi.room_params(frame=1)
+    bvh = bvh_of(scene)
+    g = H.GBuffer(W, Hh)
+    H.hdof_gbuffer(bvh, cam, cam, p, g)
+    rng = np.random.default_rng(5)
+    spp = dev((rng.integers(0, 9, (Hh, W)) * (rng.uniform(size=(Hh, W)) < 0.7)).astype(np.uint8))
+    junk = dev(rng.integers(-5, scene.n_tris + 50, (Hh, W)).astype(np.int32))
+    outs = []
+    for hint in (None, g.tri, junk):
+        rt = torch.zeros((Hh, W, 12), dtype=torch.float32, device="cuda")
+        stats = torch.zeros(2, dtype=torch.int32, device="cuda")
+        H.hdof_trace(bvh, cam, lens, p, spp, rt, stats, workspace(W, Hh, p), hint=hint)
+        H.hdof_sync()
+        outs.append(rt)
+    assert torch.equal(outs[0].view(torch.int32), outs[1].view(torch.int32))
+    assert torch.equal(outs[0].view(torch.int32), outs[2].view(torch.int32))
+
+
 def test_trace_empty_mask():
     scene, cam, lens, p = hi.tiny_config()
     bvh = bvh_of(scene)
