@@ -218,7 +218,7 @@ def run_ours(args):
         cam, prev, p = cams[k], cams[max(k - 1, 0)], params_of(k)
         hin, hout = r.hist[r.cur], r.hist[1 - r.cur]
         calls = [
-            lambda: H.hdof_gbuffer(bvh, cam, prev, p, r.g),
+            lambda: H.hdof_gbuffer(bvh, cam, prev, p, r.g, hint=r.g.tri),
             lambda: H.hdof_mask(r.g, hin, p, r.edge, r.spp, r.ws),
             lambda: H.hdof_trace(bvh, cam, lens, p, r.spp, r.rt, r.stats, r.ws, hint=r.g.tri),
             lambda: H.hdof_postfilter(r.g, cam, lens, p, r.pp, r.ws),

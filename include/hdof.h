@@ -181,9 +181,14 @@ int hdof_closest_hits(const hdof_bvh* bvh, int32_t n, const float* org, const fl
 /* Deferred-shading G-buffer and sharp image (Design section), rendered as
  * the closest hit of the pinhole ray through each pixel's screen point.
  * Lambert shading: L = albedo (k_a + sum_l E_l max(0, n . w_l)).  prev is
- * the previous frame's camera (pass cam itself for the first frame). */
+ * the previous frame's camera (pass cam itself for the first frame).
+ * hint_tri (device, may be NULL): int32 [H][W] triangle ids likely hit by
+ * each pixel's primary ray, e.g. the previous frame's tri plane; it may be
+ * out->tri itself (each pixel's hint is read before its id is written).
+ * Each primary ray tests its hint first, which only tightens the traversal:
+ * any value, including garbage, gives the same G-buffer. */
 int hdof_gbuffer(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_camera* prev,
-                 const hdof_params* p, const hdof_gbuf* out, void* stream);
+                 const hdof_params* p, const int32_t* hint_tri, const hdof_gbuf* out, void* stream);
 
 /* ---------------------------------------------------- scratch memory -- */
 /* Bytes of caller-owned device scratch the calls below need for a

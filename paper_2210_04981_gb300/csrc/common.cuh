@@ -362,7 +362,11 @@ extern __device__ unsigned long long g_trav_stats[4];
 // (descend the nearer hit child, push the farther); scene-sized triangles
 // (when kept out of the tree) are tested last behind a slab test of their
 // box.  cap bounds the node and leaf steps (watchdog).
-__device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 d, int cap, unsigned* status) {
+// hint_slot >= 0: that triangle is tested first (a likely hit tightens the
+// traversal; the closest hit, the minimum of (t, id) over all hits, is
+// unchanged).
+__device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 d, int cap, unsigned* status,
+                                           int hint_slot = -1) {
     const float INF = __int_as_float(0x7f800000);
     Ray r = make_ray(o, d);
     Shear sh = make_shear(d);
@@ -371,6 +375,7 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
     h.slot = -1;
     h.id = 0x7fffffff;
     h.b0 = h.b1 = h.b2 = 0.f;
+    if (hint_slot >= 0) hit_tri(bvh, hint_slot, o, sh, h);
     int stack[HDOF_STACK];
     int sp = 0;
     int cur = bvh.root;

@@ -20,6 +20,7 @@ struct GbufArgs {
     COL* col;
     float2* mv;
     int* tri;
+    const int* hint;  // optional previous primary-hit ids (may alias tri: read before written)
 };
 
 // 16x8-pixel blocks; warp w covers the 8x4 sub-block ((w & 1) * 8, (w >> 1) * 4)
@@ -32,7 +33,12 @@ __device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx,
     size_t q = (size_t)j * cam.W + i;
     float3 d = pinhole_dir(cam, i + 0.5f + cam.jx, j + 0.5f + cam.jy);
     float3 dn = normalize(d);
-    Hit h = closest_hit(a.bvh, cam.pos, dn, a.cap, a.status);
+    int hint_slot = -1;
+    if (a.hint) {
+        const int id = a.hint[q];
+        if (id >= 0 && id < a.bvh.n_tris) hint_slot = __ldg(&a.bvh.slot_of[id]);
+    }
+    Hit h = closest_hit(a.bvh, cam.pos, dn, a.cap, a.status, hint_slot);
     float3 n, rad, P;
     float z;
     if (h.slot >= 0) {
@@ -68,7 +74,7 @@ __global__ void __launch_bounds__(128) k_gbuffer_batch(const GbufArgs<float4, fl
 
 template <class ND, class COL>
 GbufArgs<ND, COL> gbuf_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_camera* prev, const hdof_params* p,
-                            const hdof_gbuf* g, unsigned* st) {
+                            const hdof_gbuf* g, const int* hint, unsigned* st) {
     GbufArgs<ND, COL> a;
     a.bvh = b->view();
     a.cam = make_cam(*cam);
@@ -81,14 +87,15 @@ GbufArgs<ND, COL> gbuf_args(const hdof_bvh* b, const hdof_camera* cam, const hdo
     a.col = static_cast<COL*>(g->col);
     a.mv = reinterpret_cast<float2*>(g->mv);
     a.tri = g->tri;
+    a.hint = hint;
     return a;
 }
 
 template <class ND, class COL>
 void launch(const hdof_bvh* b, const hdof_camera* cam, const hdof_camera* prev, const hdof_params* p,
-            const hdof_gbuf* g, unsigned* st, cudaStream_t s) {
+            const hdof_gbuf* g, const int* hint, unsigned* st, cudaStream_t s) {
     dim3 grid((cam->width + 15) / 16, (cam->height + 7) / 8);
-    k_gbuffer<ND, COL><<<grid, 128, 0, s>>>(gbuf_args<ND, COL>(b, cam, prev, p, g, st));
+    k_gbuffer<ND, COL><<<grid, 128, 0, s>>>(gbuf_args<ND, COL>(b, cam, prev, p, g, hint, st));
 }
 
 }  // namespace
@@ -97,7 +104,7 @@ void launch(const hdof_bvh* b, const hdof_camera* cam, const hdof_camera* prev, 
 using namespace hdof;
 
 extern "C" int hdof_gbuffer(const hdof_bvh* b, const hdof_camera* cam, const hdof_camera* prev,
-                            const hdof_params* p, const hdof_gbuf* out, void* stream) {
+                            const hdof_params* p, const int32_t* hint_tri, const hdof_gbuf* out, void* stream) {
     clear_error();
     HDOF_CHECK_ARG(b, "hdof_gbuffer: bvh is NULL");
     int rc;
@@ -113,13 +120,13 @@ extern "C" int hdof_gbuffer(const hdof_bvh* b, const hdof_camera* cam, const hdo
     HDOF_CHECK_ARG(st, "hdof_gbuffer: no status word on this device");
     cudaStream_t s = as_stream(stream);
     if (out->dtype_nd == HDOF_F32 && out->dtype_col == HDOF_F32)
-        launch<float4, float4>(b, cam, prev, p, out, st, s);
+        launch<float4, float4>(b, cam, prev, p, out, hint_tri, st, s);
     else if (out->dtype_nd == HDOF_F16 && out->dtype_col == HDOF_BF16)
-        launch<half4s, bf164s>(b, cam, prev, p, out, st, s);
+        launch<half4s, bf164s>(b, cam, prev, p, out, hint_tri, st, s);
     else if (out->dtype_nd == HDOF_F16 && out->dtype_col == HDOF_F32)
-        launch<half4s, float4>(b, cam, prev, p, out, st, s);
+        launch<half4s, float4>(b, cam, prev, p, out, hint_tri, st, s);
     else
-        launch<float4, bf164s>(b, cam, prev, p, out, st, s);
+        launch<float4, bf164s>(b, cam, prev, p, out, hint_tri, st, s);
     HDOF_LAUNCHED("hdof_gbuffer");
     return HDOF_OK;
 }
@@ -130,7 +137,7 @@ size_t gbuffer_args_size() { return sizeof(GbufArgs<float4, float4>); }
 
 void gbuffer_fill(const hdof_view& v, const ViewWs&, unsigned* st, void* dst, int* gx, int* gy) {
     *reinterpret_cast<GbufArgs<float4, float4>*>(dst) =
-        gbuf_args<float4, float4>(v.bvh, &v.cam, &v.prev, &v.params, &v.g, st);
+        gbuf_args<float4, float4>(v.bvh, &v.cam, &v.prev, &v.params, &v.g, v.g.tri, st);
     *gx = (v.cam.width + 15) / 16;
     *gy = (v.cam.height + 7) / 8;
 }

@@ -106,7 +106,7 @@ def load():
         "hdof_bvh_destroy": ([vp], C.c_int),
         "hdof_bvh_info": ([vp, P(hdof_bvh_stats)], C.c_int),
         "hdof_closest_hits": ([vp, i32, vp, vp, vp, vp, vp], C.c_int),
-        "hdof_gbuffer": ([vp, P(hdof_camera), P(hdof_camera), P(hdof_params), P(hdof_gbuf), vp], C.c_int),
+        "hdof_gbuffer": ([vp, P(hdof_camera), P(hdof_camera), P(hdof_params), vp, P(hdof_gbuf), vp], C.c_int),
         "hdof_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
         "hdof_mask": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp, sz, vp], C.c_int),
         "hdof_mask_noalloc": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp], C.c_int),
@@ -311,9 +311,11 @@ def hdof_closest_hits(bvh: Bvh, org, dirs, ids, ts, stream=None):
                                     _stream(stream)))
 
 
-def hdof_gbuffer(bvh: Bvh, cam, prev, p, gbuf: GBuffer, stream=None):
+def hdof_gbuffer(bvh: Bvh, cam, prev, p, gbuf: GBuffer, stream=None, hint=None):
+    """hint (int32 [H][W], e.g. the previous frame's tri plane, possibly
+    gbuf.tri itself) optionally seeds each primary ray with a likely hit."""
     _check(load().hdof_gbuffer(bvh.handle, C.byref(camera(cam)), C.byref(camera(prev)), C.byref(params(p)),
-                               C.byref(gbuf.struct()), _stream(stream)))
+                               _ptr(hint), C.byref(gbuf.struct()), _stream(stream)))
 
 
 def hdof_mask(gbuf: GBuffer, prev_hist, p, edge, spp, workspace, stream=None):
@@ -399,7 +401,7 @@ class Renderer:
     def frame(self, cam, prev, lns, p, stream=None, with_history=True):
         hin = self.hist[self.cur]
         hout = self.hist[1 - self.cur]
-        hdof_gbuffer(self.bvh, cam, prev, p, self.g, stream)
+        hdof_gbuffer(self.bvh, cam, prev, p, self.g, stream, hint=self.g.tri)
         hdof_mask(self.g, hin if with_history else None, p, self.edge, self.spp, self.ws, stream)
         hdof_trace(self.bvh, cam, lns, p, self.spp, self.rt, self.stats, self.ws, stream, hint=self.g.tri)
         hdof_postfilter(self.g, cam, lns, p, self.pp, self.ws, stream)

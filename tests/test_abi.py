@@ -82,7 +82,7 @@ def test_invalid_arguments_rejected_before_launch(H):
     p = H.params(hi.Params())
     g = H.hdof_gbuf(64, 48, 0, 0, None, None, None, None)
     lib = H.load()
-    assert lib.hdof_gbuffer(None, C.byref(cam), C.byref(cam), C.byref(p), C.byref(g), None) == -1
+    assert lib.hdof_gbuffer(None, C.byref(cam), C.byref(cam), C.byref(p), None, C.byref(g), None) == -1
     assert lib.hdof_build_bvh(None, 0, None, 0, None, None, C.byref(C.c_void_p()), None) == -1
     assert lib.hdof_mask(C.byref(g), None, C.byref(p), None, None, None, 0, None) == -1
     assert lib.hdof_postfilter(C.byref(g), C.byref(bad), None, C.byref(p), None, None, 0, None) == -1

@@ -277,6 +277,30 @@ def test_trace_room(orc):
     assert ok.mean() >= 0.999, f"{(~ok).sum()} of {ok.size}; " + report("rt", rt[traced], ref[traced])
 
 
+def test_gbuffer_hint_does_not_change_results():
+    """The G-buffer seeded with the previous frame's ids in place (the tri
+    plane itself), with arbitrary ids, or with none: the same planes bit for
+    bit."""
+    W, Hh = 320, 180
+    scene = hi.room_scene(seed=2, aspect=W / Hh)
+    cams = [hi.room_camera(k, W, Hh) for k in range(2)]
+    p = hi.room_params()
+    bvh = bvh_of(scene)
+    rng = np.random.default_rng(8)
+    outs = []
+    for mode in ("none", "inplace", "junk"):
+        g = H.GBuffer(W, Hh)
+        H.hdof_gbuffer(bvh, cams[0], cams[0], p, g)  # frame 0 fills tri
+        hint = {"none": None, "inplace": g.tri,
+                "junk": dev(rng.integers(-3, scene.n_tris + 9, (Hh, W)).astype(np.int32))}[mode]
+        H.hdof_gbuffer(bvh, cams[1], cams[0], p, g, hint=hint)
+        H.hdof_sync()
+        outs.append([t.clone() for t in (g.nd, g.col, g.mv, g.tri)])
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a.contiguous().view(torch.uint8), b.contiguous().view(torch.uint8))
+
+
 def test_trace_hint_does_not_change_results():
     """Seeding the lens rays with the primary hit (or with arbitrary ids,
     out-of-range ones included) gives the same trace bit for bit."""
