@@ -49,6 +49,12 @@ TRACE_FLOPS_PER_RAY = 24 * TRACE_VISITS_PER_RAY + 40 * TRACE_TESTS_PER_RAY
 # (3 colour FMAs + 1 weight FMA = 8) and, for the far layer, the depth test
 # (~1.5 on average): 12
 PF_FLOPS_PER_TAP = 12
+# DRAM traffic per frame (dram__bytes_read.sum + dram__bytes_write.sum over the
+# stage's kernels, one ncu launch-list capture with caches flushed before each
+# launch) of the current kernels on the 1080p room frame with f32 storage;
+# other workloads report null
+MEASURED_TRAFFIC = {("room", "f32", "trace"): 54.92e6,      # k_count k_scan k_scatter k_trace_rays k_resolve
+                    ("room", "f32", "postfilter"): 186.96e6}  # k_pf_prep k_pf_gather
 
 
 def peaks():
@@ -290,12 +296,15 @@ def run_ours(args):
     if dom == "postfilter":
         ach = taps * PF_FLOPS_PER_TAP / (pf_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                "frac": round(ach / fp32_peak, 3), "traffic": None, "kernel": "postfilter (k_pf_prep + k_pf_gather)",
+                "frac": round(ach / fp32_peak, 3), "kernel": "postfilter (k_pf_prep + k_pf_gather)",
+                "traffic": MEASURED_TRAFFIC.get((args.scene, "mixed" if mixed else "f32", "postfilter")),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock under load"}
     elif dom == "trace":
         ach = TRACE_FLOPS_PER_RAY * float(rays.mean()) / (trace_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                "frac": round(ach / fp32_peak, 3), "traffic": None, "kernel": "trace (k_count, k_scan, k_scatter, k_trace)",
+                "frac": round(ach / fp32_peak, 3),
+                "kernel": "trace stage (k_count, k_scan, k_scatter, k_trace_rays, k_resolve)",
+                "traffic": MEASURED_TRAFFIC.get((args.scene, "mixed" if mixed else "f32", "trace")),
                 "flops_per_ray": TRACE_FLOPS_PER_RAY, "mrays_per_s": round(mrays, 1),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock under load"}
     else:
@@ -505,7 +514,8 @@ def run_batch(args):
         fl = TRACE_FLOPS_PER_RAY * rays
         ach = fl / (stage_ms[dom] * 1e-3) / 1e12
         roof.update(achieved=round(ach, 2), frac=round(ach / fp32_peak, 3),
-                    flops_per_ray=TRACE_FLOPS_PER_RAY, kernel="k_trace_batch")
+                    flops_per_ray=TRACE_FLOPS_PER_RAY,
+                    kernel="trace stage (k_ray_prefix, k_trace_rays_batch, k_resolve_batch)")
     px = sum(v.width * v.height for v in views)
     out = {
         "metric": METRIC, "value": round(batch_ms, 4), "unit": "ms/frame", "n_gpus": ws, "steps": K,
