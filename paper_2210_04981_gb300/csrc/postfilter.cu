@@ -11,7 +11,8 @@
 // evaluated by binary search, which is exact up to float rounding.
 //
 // k_pf_prep: per pixel r + 1/2, z and the premultiplied near and far layer
-//   records (c w/a, w/a); per 16x16 tile the largest r feeding each layer.
+//   records (c w/a, w/a), the records split by pixel-index parity; per 16x16
+//   tile the largest r feeding each layer.
 // k_pf_gather: near and far are gathered in two loops, each bounded per tile
 //   by the largest radius among the tiles whose pixels feed that layer and
 //   can reach it, and per source row to the columns of that disk; every tap
@@ -40,7 +41,7 @@ constexpr int GATHER_THREADS = 8 * (16 / PF_RY);
 #define HDOF_PF_MINB 10  // resident gather blocks per SM the register budget targets
 #endif
 #ifndef HDOF_PF_UNROLL
-#define HDOF_PF_UNROLL 4  // unroll of the gather's tap loop
+#define HDOF_PF_UNROLL 4  // unroll of the gather's tap-pair loop
 #endif
 constexpr int PF_UNROLL = HDOF_PF_UNROLL;
 // Shared-memory carve-out (percent of the maximum) for the gather: the taps
@@ -102,8 +103,10 @@ __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx,
         float4 col = ld4(a.col + q);
         a.rh[q] = r + 0.5f;
         a.zq[q] = z;
-        a.nrec[q] = make_float4(col.x * an, col.y * an, col.z * an, an);
-        a.frec[q] = make_float4(col.x * af, col.y * af, col.z * af, af);
+        // records split by pixel-index parity: even pixels, then odd ones
+        const size_t qs = (q >> 1) + (q & 1) * (((size_t)W * H + 1) >> 1);
+        a.nrec[qs] = make_float4(col.x * an, col.y * an, col.z * an, an);
+        a.frec[qs] = make_float4(col.x * af, col.y * af, col.z * af, af);
         rn = wn > 0.f ? r : -1.f;
         rf = wn < 1.f ? r : -1.f;
     }
@@ -179,46 +182,84 @@ __device__ __forceinline__ void acc_far(PfAcc& a, float d, float rh, float zq, c
     a.Wf = fmaf(t, f.w, a.Wf);
 }
 
+// one (source, thread) tap: the thread's left pixels get fresh distances,
+// its right pixels the left pixels' distances of the previous tap (the same
+// offsets, so the same floats), carried in c
+template <bool NEAR>
+__device__ __forceinline__ void pf_tap(PfAcc (&a)[PF_NPX], float (&c)[PF_RY], const float (&dyk)[PF_RY], float dx,
+                                       float r, float z, const float4& e) {
+    const float dx2 = dx * dx;
+#pragma unroll
+    for (int k = 0; k < PF_RY; ++k) {
+        const float d0 = sqrt_approx(dx2 + dyk[k]);
+        if (NEAR) {
+            acc_near(a[2 * k], d0, r, e);
+            acc_near(a[2 * k + 1], c[k], r, e);
+        } else {
+            acc_far(a[2 * k], d0, r, z, e);
+            acc_far(a[2 * k + 1], c[k], r, z, e);
+        }
+        c[k] = d0;
+    }
+}
+
 // one layer's loop over a disk-shaped window of radius G around the 2x2
 // block at (i, j): every source feeding the layer within reach has
 // r + 1/2 <= G, so only taps closer than G to one of the four pixels can
 // weigh; per source row, the columns of that disk (squared distances are
-// exact integers in float)
+// exact integers in float).  Records are split by the parity of the pixel
+// index (even pixels first), so at each tap the threads of a row, two
+// columns apart, read consecutive records; taps go in pairs (even, odd
+// index) with one float2 load of r + 1/2 (and z) per pair.
 template <bool NEAR>
 __device__ __forceinline__ void pf_layer(PfAcc (&a)[PF_NPX], int G, int i, int j, int W, int H,
                                          const float* __restrict__ rh, const float* __restrict__ zq,
                                          const float4* __restrict__ rec) {
     if (G < 0) return;  // nothing within reach feeds this layer
+    const size_t half = ((size_t)W * H + 1) >> 1;
+    const float4* __restrict__ rec_e = rec;
+    const float4* __restrict__ rec_o = rec + half;
+    const float2* __restrict__ rh2 = reinterpret_cast<const float2*>(rh);
+    const float2* __restrict__ zq2 = reinterpret_cast<const float2*>(zq);
     const int y0 = max(j - G, 0), y1 = min(j + PF_RY - 1 + G, H - 1);
     const float G2 = (float)(G * G);
     for (int y = y0; y <= y1; ++y) {
         const float dy = (float)(y - j);
-        float dyk[PF_RY];
+        float dyk[PF_RY], c[PF_RY];
 #pragma unroll
         for (int k = 0; k < PF_RY; ++k) dyk[k] = (dy - (float)k) * (dy - (float)k);
         // nearest of the thread's rows to this source row
         const float dmin = dy >= 0.f && dy <= (float)(PF_RY - 1) ? 0.f : fminf(dyk[0], dyk[PF_RY - 1]);
         const int w = (int)ceilf(sqrtf(fmaxf(G2 - dmin, 0.f)));
         const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
-        const size_t qrow = (size_t)y * W;
         float dx = (float)(x0 - i);
-#pragma unroll PF_UNROLL
-        for (int x = x0; x <= x1; ++x, dx += 1.f) {
-            const float r = __ldg(&rh[qrow + x]);
-            const float4 e = __ldg(&rec[qrow + x]);
-            const float dx0 = dx * dx, dx1 = (dx - 1.f) * (dx - 1.f);
-            const float z = NEAR ? 0.f : __ldg(&zq[qrow + x]);
+        {
+            const float dm = (dx - 1.f) * (dx - 1.f);
 #pragma unroll
-            for (int k = 0; k < PF_RY; ++k) {
-                const float d0 = sqrt_approx(dx0 + dyk[k]), d1 = sqrt_approx(dx1 + dyk[k]);
-                if (NEAR) {
-                    acc_near(a[2 * k], d0, r, e);
-                    acc_near(a[2 * k + 1], d1, r, e);
-                } else {
-                    acc_far(a[2 * k], d0, r, z, e);
-                    acc_far(a[2 * k + 1], d1, r, z, e);
-                }
-            }
+            for (int k = 0; k < PF_RY; ++k) c[k] = sqrt_approx(dm + dyk[k]);
+        }
+        size_t g = (size_t)y * W + x0;  // pixel index of the next tap
+        const size_t gend = (size_t)y * W + x1 + 1;
+        if (g & 1) {  // an odd first tap on its own
+            const float z = NEAR ? 0.f : __ldg(&zq[g]);
+            pf_tap<NEAR>(a, c, dyk, dx, __ldg(&rh[g]), z, __ldg(&rec_o[g >> 1]));
+            ++g;
+            dx += 1.f;
+        }
+        size_t m = g >> 1;
+        const size_t mend = gend >> 1;  // pairs (2m, 2m + 1) with 2m + 1 < gend
+#pragma unroll PF_UNROLL
+        for (; m < mend; ++m, dx += 2.f) {
+            const float2 r2 = __ldg(&rh2[m]);
+            const float4 e0 = __ldg(&rec_e[m]), e1 = __ldg(&rec_o[m]);
+            const float2 z2 = NEAR ? make_float2(0.f, 0.f) : __ldg(&zq2[m]);
+            pf_tap<NEAR>(a, c, dyk, dx, r2.x, z2.x, e0);
+            pf_tap<NEAR>(a, c, dyk, dx + 1.f, r2.y, z2.y, e1);
+        }
+        if (gend & 1) {  // an even last tap on its own
+            const size_t gl = gend - 1;
+            const float z = NEAR ? 0.f : __ldg(&zq[gl]);
+            pf_tap<NEAR>(a, c, dyk, dx, __ldg(&rh[gl]), z, __ldg(&rec_e[gl >> 1]));
         }
     }
 }
@@ -266,8 +307,9 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
             a[k].Wn = a[k].Wf = 0.f;
         }
     }
-    pf_layer<true>(a, Gn, i, j, W, H, ar.rh, ar.zq, ar.nrec);
+    // far first: its depth-test constants are dead before the (longer) near loop
     pf_layer<false>(a, Gf, i, j, W, H, ar.rh, ar.zq, ar.frec);
+    pf_layer<true>(a, Gn, i, j, W, H, ar.rh, ar.zq, ar.nrec);
 #pragma unroll
     for (int k = 0; k < PF_NPX; ++k) {
         const int x = i + (k & 1), y = j + (k >> 1);
