@@ -488,11 +488,18 @@ __device__ __forceinline__ float2 area_and_slope(const float4* tab, int n, float
 // post-filter adjoint, part 1 (per pixel p): factors of dL/d(near weight) =
 // A . C_q - E and dL/d(far weight) = Af . C_q - Ef, and the sharp-colour
 // fallback of an empty far layer
+// Written per pixel q: (A, E) and (Af, Ef) in two planes, each split by
+// pixel-index parity (even pixels, then odd), and kb_q = 1 / (kz_rel z_q) of
+// the forward's depth test, row-major.
 __global__ void __launch_bounds__(256) k_pf_bwd_prep(const float4* __restrict__ aux, const float4* __restrict__ gpp,
-                                                     int W, int H, float4* __restrict__ pfb, float4* __restrict__ gcol) {
+                                                     const float4* __restrict__ nd, float kz_rel, int W, int H,
+                                                     float4* __restrict__ pfb, float* __restrict__ kbp,
+                                                     float4* __restrict__ gcol) {
     int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (i >= W || j >= H) return;
     size_t q = (size_t)j * W + i;
+    const size_t px = (size_t)W * H, qs = (q >> 1) + (q & 1) * ((px + 1) >> 1);
+    kbp[q] = 1.f / (kz_rel * __ldg(&nd[q].w));
     float4 an = aux[2 * q], af = aux[2 * q + 1];
     float3 g = ldf3(gpp[q]), N = ldf3(an), F = ldf3(af);
     float Wn = an.w, Wf = af.w;
@@ -509,8 +516,8 @@ __global__ void __launch_bounds__(256) k_pf_bwd_prep(const float4* __restrict__ 
         float4 gc = gcol[q];  // F is this pixel's sharp colour
         gcol[q] = make_float4(gc.x + (1.f - alpha) * g.x, gc.y + (1.f - alpha) * g.y, gc.z + (1.f - alpha) * g.z, 0.f);
     }
-    pfb[2 * q] = make_float4(A.x, A.y, A.z, E);
-    pfb[2 * q + 1] = make_float4(Af.x, Af.y, Af.z, Ef);
+    pfb[qs] = make_float4(A.x, A.y, A.z, E);
+    pfb[px + qs] = make_float4(Af.x, Af.y, Af.z, Ef);
 }
 
 // per source pixel: the radius and the layer weights of the forward map and
@@ -542,6 +549,39 @@ struct PfBwdAcc {
     float S1, S2, S3, S4;
 };
 
+// the four sources of a thread against one target: sources (i, j) and
+// (i, j + 1) get fresh distances, sources (i + 1, j) and (i + 1, j + 1) the
+// previous target's (the same offsets, so the same floats), carried in c
+struct PfBwdSrc {
+    float zq[4], R[4], wnia[4], fia[4];
+    float3 Cq[4];
+};
+__device__ __forceinline__ void pf_bwd_tap(PfBwdAcc (&acc)[4], float (&c)[2], const PfBwdSrc& src, float dx,
+                                           float dy0, float dy1, float ka, float kb, const float4& bn,
+                                           const float4& bf) {
+    const float3 An = ldf3(bn), Af = ldf3(bf);
+    const float dx2 = dx * dx;
+    const float e0 = sqrt_approx(dx2 + dy0), e2 = sqrt_approx(dx2 + dy1);
+    const float d[4] = {e0, c[0], e2, c[1]};
+    c[0] = e0;
+    c[1] = e2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float u = src.R[k] - d[k];
+        const float sw = __saturatef(u), sp = (u > 0.f && u < 1.f) ? 1.f : 0.f;
+        const float kz = __saturatef(fmaf(-src.zq[k], kb, ka));
+        const float an = sw * src.wnia[k], af = sw * src.fia[k] * kz;
+        acc[k].gC.x = fmaf(an, An.x, fmaf(af, Af.x, acc[k].gC.x));
+        acc[k].gC.y = fmaf(an, An.y, fmaf(af, Af.y, acc[k].gC.y));
+        acc[k].gC.z = fmaf(an, An.z, fmaf(af, Af.z, acc[k].gC.z));
+        const float tn = dot3f(An, src.Cq[k]) - bn.w, tf = (dot3f(Af, src.Cq[k]) - bf.w) * kz;
+        acc[k].S1 = fmaf(tn, sw, acc[k].S1);
+        acc[k].S2 = fmaf(tn, sp, acc[k].S2);
+        acc[k].S3 = fmaf(tf, sw, acc[k].S3);
+        acc[k].S4 = fmaf(tf, sp, acc[k].S4);
+    }
+}
+
 // post-filter adjoint, part 2: per source pixel q over the target pixels its
 // soft disk reaches, the colour gradient and the gradient of q's CoC.  One
 // block per 16x16 tile of sources, 64 threads; thread t takes the 2x2 source
@@ -550,12 +590,13 @@ struct PfBwdAcc {
 // tile's largest radius to one of the four (other pairs have zero weight) and
 // is branch-free; the depth test is the forward's clamp(ka - z_q kb_p).
 #ifndef HDOF_PFB_MINB
-#define HDOF_PFB_MINB 10  // resident blocks per SM the post-filter adjoint's register budget targets
+#define HDOF_PFB_MINB 8  // resident blocks per SM the post-filter adjoint's register budget targets (128 registers)
 #endif
 __global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __restrict__ nd, const float4* __restrict__ col,
-                                               const float4* __restrict__ pfb, const float4* __restrict__ tab,
-                                               int ntab, int W, int H, LensD L, float rmax, float kz_rel,
-                                               float4* __restrict__ gcol, double2* partial) {
+                                               const float4* __restrict__ pfb, const float* __restrict__ kbp,
+                                               const float4* __restrict__ tab, int ntab, int W, int H, LensD L,
+                                               float rmax, float kz_rel, float4* __restrict__ gcol,
+                                               double2* partial) {
     __shared__ int s_win;
     if (threadIdx.x == 0) s_win = 0;
     __syncthreads();
@@ -563,22 +604,21 @@ __global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __re
     const bool in0 = i < W && j < H;
     const bool ok[4] = {in0, in0 && i + 1 < W, in0 && j + 1 < H, in0 && i + 1 < W && j + 1 < H};
     const int ox[4] = {0, 1, 0, 1}, oy[4] = {0, 0, 1, 1};
-    float zq[4], R[4], wnia[4], fia[4];
-    float3 Cq[4];
+    PfBwdSrc src;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        zq[k] = 1.f;
-        R[k] = 0.f;  // an absent source weighs nothing
-        wnia[k] = fia[k] = 0.f;
-        Cq[k] = f3(0, 0, 0);
+        src.zq[k] = 1.f;
+        src.R[k] = 0.f;  // an absent source weighs nothing
+        src.wnia[k] = src.fia[k] = 0.f;
+        src.Cq[k] = f3(0, 0, 0);
         if (ok[k]) {
             const size_t q = (size_t)(j + oy[k]) * W + (i + ox[k]);
-            zq[k] = __ldg(&nd[q].w);
-            const PfSrc sr = pf_src(zq[k], L, rmax, tab, ntab);
-            R[k] = sr.R;
-            wnia[k] = sr.wnia;
-            fia[k] = sr.fia;
-            Cq[k] = ldf3(__ldg(&col[q]));
+            src.zq[k] = __ldg(&nd[q].w);
+            const PfSrc sr = pf_src(src.zq[k], L, rmax, tab, ntab);
+            src.R[k] = sr.R;
+            src.wnia[k] = sr.wnia;
+            src.fia[k] = sr.fia;
+            src.Cq[k] = ldf3(__ldg(&col[q]));
             atomicMax(&s_win, (int)ceilf(sr.R));
         }
     }
@@ -587,6 +627,12 @@ __global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __re
     if (in0) {
         const int G = s_win;
         const float ka = 1.f + 1.f / kz_rel;
+        const size_t px = (size_t)W * H, half = (px + 1) >> 1;
+        const float4* __restrict__ pn_e = pfb;
+        const float4* __restrict__ pn_o = pfb + half;
+        const float4* __restrict__ pf_e = pfb + px;
+        const float4* __restrict__ pf_o = pfb + px + half;
+        const float2* __restrict__ kb2 = reinterpret_cast<const float2*>(kbp);
         PfBwdAcc acc[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -600,30 +646,32 @@ __global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __re
             const float dy0 = dy * dy, dy1 = (dy - 1.f) * (dy - 1.f);
             const int w = (int)ceilf(sqrtf(fmaxf(G2 - fminf(dy0, dy1), 0.f)));
             const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
-            const size_t prow = (size_t)y * W;
             float dx = (float)(x0 - i);
-            for (int x = x0; x <= x1; ++x, dx += 1.f) {
-                const size_t p = prow + x;
-                const float kb = 1.f / (kz_rel * __ldg(&nd[p].w));
-                const float4 bn = __ldg(&pfb[2 * p]), bf = __ldg(&pfb[2 * p + 1]);
-                const float3 An = ldf3(bn), Af = ldf3(bf);
-                const float dx0 = dx * dx, dx1 = (dx - 1.f) * (dx - 1.f);
-                const float d2[4] = {dx0 + dy0, dx1 + dy0, dx0 + dy1, dx1 + dy1};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float u = R[k] - sqrt_approx(d2[k]);
-                    const float sw = __saturatef(u), sp = (u > 0.f && u < 1.f) ? 1.f : 0.f;
-                    const float kz = __saturatef(fmaf(-zq[k], kb, ka));
-                    const float an = sw * wnia[k], af = sw * fia[k] * kz;
-                    acc[k].gC.x = fmaf(an, An.x, fmaf(af, Af.x, acc[k].gC.x));
-                    acc[k].gC.y = fmaf(an, An.y, fmaf(af, Af.y, acc[k].gC.y));
-                    acc[k].gC.z = fmaf(an, An.z, fmaf(af, Af.z, acc[k].gC.z));
-                    const float tn = dot3f(An, Cq[k]) - bn.w, tf = (dot3f(Af, Cq[k]) - bf.w) * kz;
-                    acc[k].S1 = fmaf(tn, sw, acc[k].S1);
-                    acc[k].S2 = fmaf(tn, sp, acc[k].S2);
-                    acc[k].S3 = fmaf(tf, sw, acc[k].S3);
-                    acc[k].S4 = fmaf(tf, sp, acc[k].S4);
-                }
+            float c[2];
+            {
+                const float dm = (dx - 1.f) * (dx - 1.f);
+                c[0] = sqrt_approx(dm + dy0);
+                c[1] = sqrt_approx(dm + dy1);
+            }
+            // targets in (even, odd) index pairs; a lone odd first and even last on their own
+            size_t g = (size_t)y * W + x0;
+            const size_t gend = (size_t)y * W + x1 + 1;
+            if (g & 1) {
+                pf_bwd_tap(acc, c, src, dx, dy0, dy1, ka, __ldg(&kbp[g]), __ldg(&pn_o[g >> 1]), __ldg(&pf_o[g >> 1]));
+                ++g;
+                dx += 1.f;
+            }
+            const size_t mend = gend >> 1;
+#pragma unroll 1
+            for (size_t m = g >> 1; m < mend; ++m, dx += 2.f) {
+                const float2 kb = __ldg(&kb2[m]);
+                pf_bwd_tap(acc, c, src, dx, dy0, dy1, ka, kb.x, __ldg(&pn_e[m]), __ldg(&pf_e[m]));
+                pf_bwd_tap(acc, c, src, dx + 1.f, dy0, dy1, ka, kb.y, __ldg(&pn_o[m]), __ldg(&pf_o[m]));
+            }
+            if (gend & 1) {
+                const size_t gl = gend - 1;
+                pf_bwd_tap(acc, c, src, dx, dy0, dy1, ka, __ldg(&kbp[gl]), __ldg(&pn_e[gl >> 1]),
+                           __ldg(&pf_e[gl >> 1]));
             }
         }
 #pragma unroll
@@ -632,10 +680,10 @@ __global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __re
             const size_t q = (size_t)(j + oy[k]) * W + (i + ox[k]);
             const float4 g0 = gcol[q];
             gcol[q] = make_float4(g0.x + acc[k].gC.x, g0.y + acc[k].gC.y, g0.z + acc[k].gC.z, 0.f);
-            const PfSrc sr = pf_src(zq[k], L, rmax, tab, ntab);
+            const PfSrc sr = pf_src(src.zq[k], L, rmax, tab, ntab);
             const float gc = acc[k].S1 * sr.dwnia + acc[k].S2 * sr.wnia * sr.rp + acc[k].S3 * sr.dfia +
                              acc[k].S4 * sr.fia * sr.rp;
-            const float2 dc = dcoc(zq[k], L);
+            const float2 dc = dcoc(src.zq[k], L);
             dth.x = fmaf(gc, dc.x, dth.x);
             dth.y = fmaf(gc, dc.y, dth.y);
         }
@@ -678,7 +726,7 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct BwdWs {
     float4 *gpp, *gcrec, *gcrt, *spb, *pfb;
-    float* ghacc;
+    float *ghacc, *kbp;
     float2* gmom;
     double2* partial;
     int n_partial;
@@ -698,6 +746,7 @@ BwdWs bwd_layout(int W, int H, char* base) {
     b.gcrt = reinterpret_cast<float4*>(take(16 * px));
     b.spb = reinterpret_cast<float4*>(take(16 * px));
     b.pfb = reinterpret_cast<float4*>(take(32 * px));
+    b.kbp = reinterpret_cast<float*>(take(4 * px));
     b.ghacc = reinterpret_cast<float*>(take(4 * px));
     b.gmom = reinterpret_cast<float2*>(take(8 * px));
     int n1 = ((W + 31) / 32) * ((H + 7) / 8), n2 = ((W + 15) / 16) * ((H + 15) / 16);
@@ -805,8 +854,10 @@ extern "C" int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const
     k_temporal_replay_bwd<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(rec), ray_off, spp,
                                              reinterpret_cast<const float4*>(hist_samples), b.gcrt, b.ghacc, b.gmom, W,
                                              H, L, p->ema_alpha, p->camera_moved, b.partial + n1);
-    k_pf_bwd_prep<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(st->pp_aux), b.gpp, W, H, b.pfb, gcol);
-    k_pf_bwd<<<g2, 64, 0, s>>>(nd, col, b.pfb, tab, ntab, W, H, L, p->r_max, p->kz_rel, gcol, b.partial + 2 * n1);
+    k_pf_bwd_prep<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(st->pp_aux), b.gpp, nd, p->kz_rel, W, H, b.pfb,
+                                     b.kbp, gcol);
+    k_pf_bwd<<<g2, 64, 0, s>>>(nd, col, b.pfb, b.kbp, tab, ntab, W, H, L, p->r_max, p->kz_rel, gcol,
+                               b.partial + 2 * n1);
     k_reduce<<<1, 1024, 0, s>>>(b.partial, b.n_partial, grad_lens);
     HDOF_LAUNCHED("hdof_post_backward");
     return HDOF_OK;
