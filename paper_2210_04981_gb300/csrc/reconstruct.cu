@@ -207,37 +207,11 @@ struct SpatialArgs {
     float4* aux;
 };
 
-__device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int by) {
+// the spatial gather of one traced pixel (i, j)
+__device__ __forceinline__ void spatial_pixel(const SpatialArgs& a, int i, int j) {
     const float4* __restrict__ crt = a.crt;
-    const float2* __restrict__ mom = a.mom;
-    const uint8_t* __restrict__ hlen = a.hlen;
     const int W = a.W, H = a.H;
-    const float r_s = a.r_s, var_ref = a.var_ref;
-    float4* __restrict__ crec = a.crec;
-    float4* __restrict__ aux = a.aux;
-    // block = one 16x16 tile; its traced pixels are compacted (row-major) so
-    // that every warp which runs gathers for traced pixels only
-    __shared__ unsigned char s_list[256];
-    __shared__ int s_wcnt[8];
-    const int t = threadIdx.x, lane = t & 31;
-    bool traced = false;
-    {
-        const int i0 = bx * 16 + (t & 15), j0 = by * 16 + (t >> 4);
-        if (i0 < W && j0 < H) traced = __ldg(&crt[(size_t)j0 * W + i0].w) >= 0.f;
-    }
-    const unsigned tm = __ballot_sync(0xffffffffu, traced);
-    if (lane == 0) s_wcnt[t >> 5] = __popc(tm);
-    __syncthreads();
-    int off = 0, n = 0;
-    for (int k = 0; k < 8; ++k) {
-        off += k < (t >> 5) ? s_wcnt[k] : 0;
-        n += s_wcnt[k];
-    }
-    if (traced) s_list[off + __popc(tm & ((1u << lane) - 1u))] = (unsigned char)t;
-    __syncthreads();
-    if (t >= n) return;
-    const int li = s_list[t];
-    const int i = bx * 16 + (li & 15), j = by * 16 + (li >> 4);
+    const float r_s = a.r_s;
     const size_t q = (size_t)j * W + i;
     const float4 cp = __ldg(&crt[q]);
     const float rp = fminf(cp.w * 0.5f, r_s);
@@ -264,17 +238,45 @@ __device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int b
             Ws += wq;
         }
     }
-    float2 m = __ldg(&mom[q]);
+    float2 m = __ldg(&a.mom[q]);
     float sig = sqrtf(fmaxf(0.f, m.y - m.x * m.x));
-    float beta = __ldg(&hlen[q]) < 2 ? 1.f : clamp01(sig / var_ref);
+    float beta = __ldg(&a.hlen[q]) < 2 ? 1.f : clamp01(sig / a.var_ref);
     float3 Csp = (1.f / Ws) * S;
-    if (aux) aux[q] = make_float4(Csp.x, Csp.y, Csp.z, Ws);  // kept for the adjoint
-    crec[q] = make_float4(cp.x + beta * (Csp.x - cp.x), cp.y + beta * (Csp.y - cp.y), cp.z + beta * (Csp.z - cp.z),
-                          0.f);
+    if (a.aux) a.aux[q] = make_float4(Csp.x, Csp.y, Csp.z, Ws);  // kept for the adjoint
+    a.crec[q] = make_float4(cp.x + beta * (Csp.x - cp.x), cp.y + beta * (Csp.y - cp.y), cp.z + beta * (Csp.z - cp.z),
+                            0.f);
 }
 
-__global__ void __launch_bounds__(256) k_spatial(SpatialArgs a) { spatial_body(a, blockIdx.x, blockIdx.y); }
-__global__ void __launch_bounds__(256) k_spatial_batch(const SpatialArgs* __restrict__ a, BatchGrid g) {
+// block = one 8x8 tile, one thread per pixel: the tile's traced pixels are
+// compacted (row-major) so the threads that run all gather for traced
+// pixels, in one round; small blocks keep many tiles resident where few of
+// their pixels are traced
+constexpr int SP_TILE = 8, SP_THREADS = SP_TILE * SP_TILE;
+__device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int by) {
+    __shared__ unsigned char s_list[SP_THREADS];
+    __shared__ int s_cnt[SP_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int i0 = bx * SP_TILE + (t % SP_TILE), j0 = by * SP_TILE + (t / SP_TILE);
+    const bool traced = i0 < a.W && j0 < a.H && __ldg(&a.crt[(size_t)j0 * a.W + i0].w) >= 0.f;
+    const unsigned tm = __ballot_sync(0xffffffffu, traced);
+    if (lane == 0) s_cnt[w] = __popc(tm);
+    __syncthreads();
+    int off = 0, n = 0;
+#pragma unroll
+    for (int c = 0; c < SP_THREADS / 32; ++c) {
+        off += c < w ? s_cnt[c] : 0;
+        n += s_cnt[c];
+    }
+    if (traced) s_list[off + __popc(tm & ((1u << lane) - 1u))] = (unsigned char)t;
+    __syncthreads();
+    if (t < n) {
+        const int li = s_list[t];
+        spatial_pixel(a, bx * SP_TILE + (li % SP_TILE), by * SP_TILE + (li / SP_TILE));
+    }
+}
+
+__global__ void __launch_bounds__(SP_THREADS) k_spatial(SpatialArgs a) { spatial_body(a, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(SP_THREADS) k_spatial_batch(const SpatialArgs* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
     spatial_body(batch_record(a, v), bx, by);
@@ -310,8 +312,8 @@ TemporalArgs temporal_args(const float* rt, const hdof_gbuf* in, const uint8_t* 
 
 int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, int W, int H, float r_s, float var_ref,
                    float4* crec, float4* aux, cudaStream_t s) {
-    dim3 g2((W + 15) / 16, (H + 15) / 16);
-    k_spatial<<<g2, 256, 0, s>>>(SpatialArgs{crt, mom, hlen, W, H, r_s, var_ref, crec, aux});
+    dim3 g2((W + SP_TILE - 1) / SP_TILE, (H + SP_TILE - 1) / SP_TILE);
+    k_spatial<<<g2, SP_THREADS, 0, s>>>(SpatialArgs{crt, mom, hlen, W, H, r_s, var_ref, crec, aux});
     HDOF_LAUNCHED("spatial reconstruction");
     return HDOF_OK;
 }
@@ -373,11 +375,11 @@ void spatial_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int* 
         SpatialArgs{reinterpret_cast<const float4*>(v.crt), reinterpret_cast<const float2*>(v.hist_out.mom),
                     v.hist_out.hlen, v.cam.width, v.cam.height, v.params.r_s, v.params.var_ref,
                     reinterpret_cast<float4*>(v.crec), nullptr};
-    *gx = (v.cam.width + 15) / 16;
-    *gy = (v.cam.height + 15) / 16;
+    *gx = (v.cam.width + SP_TILE - 1) / SP_TILE;
+    *gy = (v.cam.height + SP_TILE - 1) / SP_TILE;
 }
 void spatial_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
-    k_spatial_batch<<<blocks, 256, 0, s>>>(static_cast<const SpatialArgs*>(args), g);
+    k_spatial_batch<<<blocks, SP_THREADS, 0, s>>>(static_cast<const SpatialArgs*>(args), g);
 }
 
 }  // namespace hdof
