@@ -234,11 +234,26 @@ int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const 
                       uint8_t* edge, uint8_t* spp, void* stream);
 
 /* ---------------------------------------------------------- trace */
+/* Form and launch shape of the persistent trace (results do not depend on
+ * them; hdof_trace takes one optionally, a batch one chosen by an autotuner).
+ * trace_block: threads per block (64, 128 or 256);
+ * trace_refill: 0 = warp packets (a warp takes 32 consecutive rays of the
+ *   list and finds their closest hits in one shared traversal, each lane
+ *   culling with its own hit: fast when the rays of neighbouring pixels stay
+ *   close, i.e. for small lens apertures); 1..32 = ray level (one ray per
+ *   lane; a warp fetches new rays for its idle lanes once fewer than this
+ *   many of its 32 lanes still trace). */
+typedef struct hdof_tuning {
+    int32_t trace_block;
+    int32_t trace_refill;
+    int32_t reserved[2];
+} hdof_tuning;
+
 /* Thin-lens distributed ray trace of the masked pixels (Ray Trace section).
  * Compacts the pixels with spp > 0 into a queue (tile order) and lists
- * their rays; a persistent kernel traces the ray list (idle lanes of a warp
- * fetch new rays as others finish), then each queued pixel sums its
- * samples' records in sample order.  min(spp[p], p->spp_max) lens rays
+ * their rays; a persistent kernel traces the ray list (as warp packets or
+ * ray by ray, see hdof_tuning), then each queued pixel sums its samples'
+ * records in sample order.  min(spp[p], p->spp_max) lens rays
  * per pixel (the ray lists are sized for spp_max): Philox4x32-10
  * (key = (seed, view*65536+frame), counter = (pixel, sample, 0, 0)) gives
  * u1, u2 -> lens point rho = A sqrt(u1), theta = 2 pi u2; the ray aims at
@@ -256,11 +271,16 @@ int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const 
  * rec[ray_off[p] + s] = (L rgb, view depth of the hit, +inf for a miss) of
  * sample s of traced pixel p -- the frozen visibility that
  * hdof_post_forward/backward re-evaluate at another focus and aperture;
- * rec holds stats[1] float4 entries (at most spp_max x W x H). */
+ * rec holds stats[1] float4 entries (at most spp_max x W x H).
+ * tune (host, may be NULL): the trace's form and block size (out-of-range
+ * values are rejected with HDOF_EINVAL); NULL takes 128 threads and warp
+ * packets when the lens's CoC scale K = A H / (zf tan(fovy/2)) is below 20
+ * pixels (|c(z)| = K |zf/z - 1|: the lens rays of neighbouring pixels stay
+ * close), ray level with refill 4 otherwise. */
 int hdof_trace(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* lens,
                const hdof_params* p, const uint8_t* spp, const int32_t* hint_tri, float* rt,
                uint32_t* stats, float* rec, uint32_t* ray_off, void* workspace,
-               size_t workspace_bytes, void* stream);
+               size_t workspace_bytes, const hdof_tuning* tune, void* stream);
 
 /* ----------------------------------------------------- post-filter -- */
 /* CoC gather post-filter of the sharp image (Design section; the rejection
@@ -332,16 +352,6 @@ typedef struct hdof_view {
     size_t workspace_bytes;
 } hdof_view;
 
-/* Launch shape of the batched frame's persistent trace (chosen by an
- * autotuner; results do not depend on it).
- * trace_block: threads per block (64, 128 or 256);
- * trace_refill: a warp fetches new rays for its idle lanes once fewer than
- *   this many of its 32 lanes still trace (1..32). */
-typedef struct hdof_tuning {
-    int32_t trace_block;
-    int32_t trace_refill;
-    int32_t reserved[2];
-} hdof_tuning;
 
 typedef struct hdof_batch hdof_batch;
 

@@ -1,9 +1,10 @@
 """Launch-shape autotuner of the batched multi-view frame.
 
-The batched frame has one free launch shape that changes its speed but not
-its results: the persistent trace's block size (64, 128 or 256 threads) and
-its refill threshold (a warp fetches new rays for its idle lanes once fewer
-than that many lanes still trace: 2, 4, 8 or 16).  Every
+The batched frame has one free choice that changes its speed but not its
+results: the persistent trace's block size (64, 128 or 256 threads) and its
+form: warp packets (refill 0: a warp traverses for 32 coherent rays at once)
+or ray level with a refill threshold (a warp fetches new rays for its idle
+lanes once fewer than that many lanes still trace: 4 or 8).  Every
 candidate renders bit-identical images, so the tuner only times them: it
 builds one batch handle per candidate over the caller's own buffers, times
 whole batched frames with CUDA events on the current stream (warm-up first,
@@ -21,7 +22,7 @@ import torch
 
 from . import hdof as H
 
-CANDIDATES = tuple((b, c) for b in (64, 128, 256) for c in (2, 4, 8, 16))
+CANDIDATES = tuple((b, c) for b in (64, 128, 256) for c in (0, 4, 8))
 
 
 def cache_path() -> str:

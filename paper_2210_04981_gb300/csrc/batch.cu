@@ -183,7 +183,7 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     if (tuning) t = *tuning;
     HDOF_CHECK_ARG(t.trace_block == 64 || t.trace_block == 128 || t.trace_block == 256,
                    "hdof_batch_create: trace_block %d not in {64, 128, 256}", (int)t.trace_block);
-    HDOF_CHECK_ARG(t.trace_refill >= 1 && t.trace_refill <= 32, "hdof_batch_create: trace_refill %d not in 1..32",
+    HDOF_CHECK_ARG(t.trace_refill >= 0 && t.trace_refill <= 32, "hdof_batch_create: trace_refill %d not in 0..32",
                    (int)t.trace_refill);
     int dev = 0;
     HDOF_CUDA(cudaGetDevice(&dev), "hdof_batch_create: device");
@@ -198,7 +198,7 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     int rc;
     if ((rc = ensure_area_table(s))) return rc;
     int trace_blocks = 0;
-    if ((rc = trace_batch_grid(t.trace_block, &trace_blocks))) return rc;
+    if ((rc = trace_batch_grid(t.trace_block, t.trace_refill, &trace_blocks))) return rc;
 
     Layout L = layout(n);
     char* host = nullptr;

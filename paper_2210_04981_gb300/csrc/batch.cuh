@@ -123,7 +123,7 @@ void scan_launch_batch(const void* args, int n, cudaStream_t s);  // one block p
 size_t trace_args_size();
 void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst, int* gx, int* gy);
 // resident grid of the persistent batched trace for a block size
-int trace_batch_grid(int block, int* blocks);
+int trace_batch_grid(int block, int refill, int* blocks);
 // ray-count prefix over the views (gq[0..n], gq[n + 1] = head), the
 // persistent trace over the concatenated ray lists, and the per-pixel
 // resolve (grid of the trace records' gx x gy blocks per view)

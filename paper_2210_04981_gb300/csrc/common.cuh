@@ -193,18 +193,32 @@ struct BvhView {
 
 struct Ray {
     float3 o, d, id;  // id = 1 / d (finite)
-    float3 ood;       // o * id
+    float3 cl, ch;    // per axis: o id shifted so the l- and h-plane distances err outwards
 };
 
+// Plane distances are fma(l, id, -o id): (l - o) id (1 + d1) - (o id) d2 with
+// |d1|, |d2| of a few units of 2^-24.  The relative part is covered by
+// widening the exit distance relatively; the absolute part, below
+// 2^-23 |o id| on that axis, by shifting each axis's offset by
+// e = 2^-22 |o id| so that its entry plane reads early and its exit plane
+// late (which plane is which follows the sign of d).  A ray nearly parallel
+// to an axis has huge distances on it and a large e there: they stay huge,
+// so the shift costs no culling.
 __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     Ray r;
     r.o = o;
     r.d = d;
-    const float eps = 1e-20f;
-    r.id = f3(1.f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
-              1.f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
-              1.f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
-    r.ood = f3(o.x * r.id.x, o.y * r.id.y, o.z * r.id.z);
+    const float tiny = 1e-20f;
+    r.id = f3(1.f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
+              1.f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
+              1.f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+    const float3 ood = f3(o.x * r.id.x, o.y * r.id.y, o.z * r.id.z);
+    const float3 e = f3(ldexpf(fabsf(ood.x), -22), ldexpf(fabsf(ood.y), -22), ldexpf(fabsf(ood.z), -22));
+    // id > 0: l is the entry plane (distance lowered: offset raised), h the exit
+    r.cl = f3(r.id.x > 0.f ? ood.x + e.x : ood.x - e.x, r.id.y > 0.f ? ood.y + e.y : ood.y - e.y,
+              r.id.z > 0.f ? ood.z + e.z : ood.z - e.z);
+    r.ch = f3(r.id.x > 0.f ? ood.x - e.x : ood.x + e.x, r.id.y > 0.f ? ood.y - e.y : ood.y + e.y,
+              r.id.z > 0.f ? ood.z - e.z : ood.z + e.z);
     return r;
 }
 
@@ -216,27 +230,30 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
-// Slab test of one box; returns entry distance (or +inf on a miss).  The exit
-// distance is widened by 2 gamma_3 (Ize 2013) so no box the ray touches is culled.
+// Slab test of one box; returns entry distance (or +inf on a miss).  With
+// the outward plane offsets of make_ray and the exit distance widened by
+// 2^-19 (relative rounding of the planes and of a triangle's hit distance,
+// which tmax may be), a box that holds a point of the ray at a distance
+// <= tmax is not culled: the closest hit, the minimum of (t, id) over the
+// triangles the ray hits, does not depend on the order boxes are visited.
 __device__ __forceinline__ float slab(const Ray& r, float lx, float hx, float ly, float hy, float lz,
                                       float hz, float tmax) {
-    float tx0 = fmaf(lx, r.id.x, -r.ood.x), tx1 = fmaf(hx, r.id.x, -r.ood.x);
-    float ty0 = fmaf(ly, r.id.y, -r.ood.y), ty1 = fmaf(hy, r.id.y, -r.ood.y);
-    float tz0 = fmaf(lz, r.id.z, -r.ood.z), tz1 = fmaf(hz, r.id.z, -r.ood.z);
+    float tx0 = fmaf(lx, r.id.x, -r.cl.x), tx1 = fmaf(hx, r.id.x, -r.ch.x);
+    float ty0 = fmaf(ly, r.id.y, -r.cl.y), ty1 = fmaf(hy, r.id.y, -r.ch.y);
+    float tz0 = fmaf(lz, r.id.z, -r.cl.z), tz1 = fmaf(hz, r.id.z, -r.ch.z);
     float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
     float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    tf *= 1.0000004f;
-    return tn <= tf ? tn : __int_as_float(0x7f800000);
+    return tn <= tf * 1.0000019f ? tn : __int_as_float(0x7f800000);
 }
 // the same test returning the hit flag, with the entry distance in tn
 __device__ __forceinline__ bool slab_hit(const Ray& r, float lx, float hx, float ly, float hy, float lz, float hz,
                                          float tmax, float& tn) {
-    float tx0 = fmaf(lx, r.id.x, -r.ood.x), tx1 = fmaf(hx, r.id.x, -r.ood.x);
-    float ty0 = fmaf(ly, r.id.y, -r.ood.y), ty1 = fmaf(hy, r.id.y, -r.ood.y);
-    float tz0 = fmaf(lz, r.id.z, -r.ood.z), tz1 = fmaf(hz, r.id.z, -r.ood.z);
+    float tx0 = fmaf(lx, r.id.x, -r.cl.x), tx1 = fmaf(hx, r.id.x, -r.ch.x);
+    float ty0 = fmaf(ly, r.id.y, -r.cl.y), ty1 = fmaf(hy, r.id.y, -r.ch.y);
+    float tz0 = fmaf(lz, r.id.z, -r.cl.z), tz1 = fmaf(hz, r.id.z, -r.ch.z);
     tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
     float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    return tn <= tf * 1.0000004f;
+    return tn <= tf * 1.0000019f;
 }
 
 // Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013).  Edge
@@ -432,6 +449,86 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
 #endif
     if (h.slot < 0) h.id = -1;
     return h;
+}
+
+// Warp-wide closest hits: all 32 lanes call this together; the active lanes'
+// rays share one traversal (node references and the stack are warp-uniform,
+// the stack lives in the caller's shared memory, one per warp).  A node is
+// entered when any active lane's ray enters one of its children before that
+// lane's own closest hit so far; each lane tests the triangles of every leaf
+// the warp reaches.  A lane's own closest hit lies in a leaf whose every
+// ancestor box that lane enters, so the warp reaches it: every lane gets the
+// same (t, id) minimum as closest_hit.  Coherent rays (the lens samples of
+// neighbouring pixels, the primary rays of a pixel block) visit nearly the
+// same nodes, so one broadcast node fetch and one box test per lane serve
+// the warp without divergence.  h holds each lane's hit so far (a hint hit
+// or a miss); scene-sized triangles are left to the caller.  Returns false
+// when the step cap was reached (the warp stops; status is flagged).
+__device__ __forceinline__ bool closest_hit_warp(const BvhView& bvh, bool act, const Ray& r, float3 o,
+                                                 const Shear& sh, Hit& h, int cap, unsigned* status,
+                                                 int* __restrict__ stack) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int cur = bvh.root, sp = 0, steps = 0;
+#if HDOF_TRAV_STATS
+    unsigned nv = 0, nt = 0;
+#endif
+    while (true) {
+        bool pop = true;
+        if (cur >= 0) {
+#if HDOF_TRAV_STATS
+            ++nv;
+#endif
+            const Node* n = bvh.nodes + cur;
+            const float4 a = __ldg(&n->xy0), b = __ldg(&n->xy1), z = __ldg(&n->z01);
+            const int4 ch = __ldg(&n->child);
+            float t0 = 0.f, t1 = 0.f;
+            const bool h0 = act && slab_hit(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t, t0);
+            const bool h1 = act && slab_hit(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t, t1);
+            const unsigned b0 = __ballot_sync(FULL, h0), b1 = __ballot_sync(FULL, h1);
+            if (b0 && b1) {
+                // first the child nearer for most of the lanes that enter both
+                // (or entered by more lanes): only the culling depends on it
+                const unsigned both = b0 & b1, nx = __ballot_sync(FULL, h0 && h1 && t0 <= t1);
+                const bool x_first = both ? 2 * __popc(nx) >= __popc(both) : __popc(b0) >= __popc(b1);
+                if (sp < HDOF_STACK) {
+                    if (lane == 0) stack[sp] = x_first ? ch.y : ch.x;
+                    ++sp;
+                } else if (lane == 0) {
+                    atomicOr(status, HDOF_STATUS_TIMEOUT);
+                }
+                cur = x_first ? ch.x : ch.y;
+                pop = false;
+            } else if (b0 | b1) {
+                cur = b0 ? ch.x : ch.y;
+                pop = false;
+            }
+        } else {
+            const int e = ~cur, first = e >> 3, count = (e & 7) + 1;
+            if (act)
+                for (int k = 0; k < count; ++k) hit_tri(bvh, first + k, o, sh, h);
+#if HDOF_TRAV_STATS
+            nt += count;
+#endif
+        }
+        if (pop) {
+            if (sp == 0) break;
+            __syncwarp();
+            cur = stack[--sp];
+        }
+        if (++steps > cap) {
+            if (lane == 0) atomicOr(status, HDOF_STATUS_TIMEOUT);
+            return false;
+        }
+    }
+#if HDOF_TRAV_STATS
+    if (lane == 0) {
+        atomicAdd(&g_trav_stats[1], (unsigned long long)nv);
+        atomicAdd(&g_trav_stats[2], (unsigned long long)nt);
+    }
+    if (act) atomicAdd(&g_trav_stats[0], 1ull);
+#endif
+    return true;
 }
 
 // Lambert shading at a hit: face normal turned towards the ray, albedo from

@@ -403,6 +403,79 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
     }
 }
 
+// Packet form of the trace: a warp takes 32 consecutive rays of the list
+// (the lens samples of a few neighbouring pixels: nearly the same path
+// through the tree) and finds their closest hits in one shared traversal
+// (closest_hit_warp); in a batched list the rays of one view go together.
+// Same records as the ray-level form.
+template <class Src>
+__device__ __forceinline__ void trace_packets_body(const Src& src, unsigned total, unsigned* head, int* stack) {
+    const unsigned FULL = 0xffffffffu;
+    const float INF = __int_as_float(0x7f800000);
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(head, 32u);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= total) break;
+        const unsigned g = base + lane;
+        bool pending = g < total;
+        unsigned r = 0;
+        int v = 0;
+        if (pending) v = src.locate(g, r);
+        while (true) {
+            const unsigned pm = __ballot_sync(FULL, pending);
+            if (!pm) break;
+            const int v0 = __shfl_sync(FULL, v, __ffs(pm) - 1);
+            const bool act = pending && v == v0;
+            const TraceArgs& a = src.at(v0);
+            Ray ray;
+            Shear sh;
+            Hit h;
+            h.t = INF;
+            h.slot = -1;
+            h.id = 0x7fffffff;
+            h.b0 = h.b1 = h.b2 = 0.f;
+            float3 O = f3(0.f, 0.f, 0.f), dir = f3(0.f, 0.f, 1.f);
+            if (act) {
+                const unsigned qp = __ldg(&a.ray_pix[r]);
+                lens_ray(a, qp, __ldg(&a.ray_s[r]), O, dir);
+                if (a.hint) {  // the pixel's primary hit first (see trace_rays_body)
+                    sh = make_shear(dir);
+                    const int id = __ldg(&a.hint[qp]);
+                    if (id >= 0 && id < a.bvh.n_tris) hit_tri(a.bvh, __ldg(&a.bvh.slot_of[id]), O, sh, h);
+                }
+            }
+            ray = make_ray(O, dir);
+            sh = make_shear(dir);
+            closest_hit_warp(a.bvh, act, ray, O, sh, h, a.cap, a.status, stack);
+            if (act) {
+                const BvhView& bvh = a.bvh;
+                for (int k = 0; k < bvh.big_count; ++k) {
+                    float4 lo = __ldg(&bvh.big_box[2 * k]), hi = __ldg(&bvh.big_box[2 * k + 1]);
+                    if (slab(ray, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, h.t) < INF)
+                        hit_tri(bvh, bvh.big_first + k, O, sh, h);
+                }
+                a.recs[r] = make_float2(h.slot >= 0 ? h.t : INF, __int_as_float(h.slot));
+            }
+            pending = pending && !act;
+        }
+    }
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_trace_packets(TraceArgs a) {
+    __shared__ int s_stack[BS / 32][HDOF_STACK];
+    trace_packets_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], s_stack[threadIdx.x >> 5]);
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_trace_packets_batch(const TraceArgs* __restrict__ tab,
+                                                            const unsigned* __restrict__ gq, int n, unsigned* head) {
+    __shared__ int s_stack[BS / 32][HDOF_STACK];
+    trace_packets_body(ManyViews{tab, gq, n}, __ldcg(&gq[n]), head, s_stack[threadIdx.x >> 5]);
+}
+
 template <int BS>
 __global__ void __launch_bounds__(BS) k_trace_rays(TraceArgs a, int refill) {
     trace_rays_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], refill);
@@ -563,29 +636,34 @@ __global__ void __launch_bounds__(1024) k_ray_prefix(const ScanArgs* __restrict_
 }
 
 template <int BS>
-int rays_occupancy(bool batch, int* nb) {
-    cudaError_t e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_rays_batch<BS>, BS, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_rays<BS>, BS, 0);
+int rays_occupancy(bool batch, bool packets, int* nb) {
+    cudaError_t e;
+    if (packets)
+        e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_packets_batch<BS>, BS, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_packets<BS>, BS, 0);
+    else
+        e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_rays_batch<BS>, BS, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_trace_rays<BS>, BS, 0);
     if (e != cudaSuccess) return cuda_fail(e, "trace: occupancy");
     if (*nb < 1) *nb = 1;
     return HDOF_OK;
 }
 
-// resident grid of the persistent trace (cached per device, block size and form)
-int rays_grid(bool batch, int block, int* blocks) {
-    static int cache[64][2][3] = {};
+// resident grid of the persistent trace (cached per device, form and block size)
+int rays_grid(bool batch, bool packets, int block, int* blocks) {
+    static int cache[64][2][2][3] = {};
     int dev = 0;
     HDOF_CUDA(cudaGetDevice(&dev), "trace: device");
     const int bi = block == 64 ? 0 : (block == 256 ? 2 : 1);
     int nb = 0, rc = HDOF_OK;
-    if (dev >= 0 && dev < 64 && cache[dev][batch][bi]) {
-        nb = cache[dev][batch][bi];
+    if (dev >= 0 && dev < 64 && cache[dev][batch][packets][bi]) {
+        nb = cache[dev][batch][packets][bi];
     } else {
-        if (bi == 0) rc = rays_occupancy<64>(batch, &nb);
-        else if (bi == 2) rc = rays_occupancy<256>(batch, &nb);
-        else rc = rays_occupancy<128>(batch, &nb);
+        if (bi == 0) rc = rays_occupancy<64>(batch, packets, &nb);
+        else if (bi == 2) rc = rays_occupancy<256>(batch, packets, &nb);
+        else rc = rays_occupancy<128>(batch, packets, &nb);
         if (rc) return rc;
-        if (dev >= 0 && dev < 64) cache[dev][batch][bi] = nb;
+        if (dev >= 0 && dev < 64) cache[dev][batch][packets][bi] = nb;
     }
     *blocks = sm_count() * nb;
     return HDOF_OK;
@@ -633,16 +711,22 @@ void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst, in
     *gx = (v.cam.width * v.cam.height + 255) / 256;  // resolve: one thread per possible queue entry
     *gy = 1;
 }
-int trace_batch_grid(int block, int* blocks) { return rays_grid(true, block, blocks); }
+int trace_batch_grid(int block, int refill, int* blocks) { return rays_grid(true, refill == 0, block, blocks); }
 
 int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid resolve, int resolve_blocks, int n,
                        unsigned* gq, int block, int refill, int blocks, cudaStream_t s) {
     k_ray_prefix<<<1, 1024, 0, s>>>(static_cast<const ScanArgs*>(scan_args), n, gq);
     HDOF_LAUNCHED("batched trace: ray prefix");
     const TraceArgs* a = static_cast<const TraceArgs*>(trace_args);
-    if (block == 64) k_trace_rays_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, refill);
-    else if (block == 256) k_trace_rays_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, refill);
-    else k_trace_rays_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, refill);
+    if (refill == 0) {  // warp packets
+        if (block == 64) k_trace_packets_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1);
+        else if (block == 256) k_trace_packets_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1);
+        else k_trace_packets_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1);
+    } else {  // ray level, dynamic fetch
+        if (block == 64) k_trace_rays_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, refill);
+        else if (block == 256) k_trace_rays_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, refill);
+        else k_trace_rays_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, refill);
+    }
     HDOF_LAUNCHED("batched trace");
     k_resolve_batch<<<resolve_blocks, 256, 0, s>>>(a, resolve);
     HDOF_LAUNCHED("batched trace: resolve");
@@ -653,17 +737,20 @@ int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid 
 
 using namespace hdof;
 
-// launch shape of the single-view trace (the batched frame's is tuned)
-#ifndef HDOF_TRACE_BLOCK
-#define HDOF_TRACE_BLOCK 128
-#endif
-#ifndef HDOF_TRACE_REFILL
-#define HDOF_TRACE_REFILL 4
-#endif
+// default form of the single-view trace: warp packets below this CoC scale
+// (pixels of CoC per unit of zf/z - 1), ray level with refill 4 above
+constexpr float PACKET_K_MAX = 20.f;
+
+template <int BS>
+void launch_trace(const TraceArgs& a, int refill, int blocks, cudaStream_t s) {
+    if (refill == 0) k_trace_packets<BS><<<blocks, BS, 0, s>>>(a);
+    else k_trace_rays<BS><<<blocks, BS, 0, s>>>(a, refill);
+}
 
 extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
                           const uint8_t* spp, const int32_t* hint_tri, float* rt, uint32_t* stats, float* rec,
-                          uint32_t* ray_off, void* workspace, size_t workspace_bytes, void* stream) {
+                          uint32_t* ray_off, void* workspace, size_t workspace_bytes, const hdof_tuning* tune,
+                          void* stream) {
     clear_error();
     HDOF_CHECK_ARG(b, "hdof_trace: bvh is NULL");
     int rc;
@@ -672,6 +759,18 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
         return rc;
     HDOF_CHECK_ARG(spp && rt, "hdof_trace: spp and rt are required");
     HDOF_CHECK_ARG(!rec == !ray_off, "hdof_trace: rec and ray_off go together");
+    hdof_tuning t = {};
+    if (tune) {
+        t = *tune;
+        HDOF_CHECK_ARG(t.trace_block == 64 || t.trace_block == 128 || t.trace_block == 256,
+                       "hdof_trace: trace_block %d not in {64, 128, 256}", (int)t.trace_block);
+        HDOF_CHECK_ARG(t.trace_refill >= 0 && t.trace_refill <= 32, "hdof_trace: trace_refill %d not in 0..32",
+                       (int)t.trace_refill);
+    } else {
+        const float K = lens->aperture_radius * (float)cam->height / (lens->focus_dist * cam->tan_half_fovy);
+        t.trace_block = 128;
+        t.trace_refill = K < PACKET_K_MAX ? 0 : 4;
+    }
     const int W = cam->width, H = cam->height;
     WsLayout L = ws_layout(W, H, p);
     HDOF_CHECK_ARG(workspace && workspace_bytes >= L.trace, "hdof_trace: workspace of %zu bytes < %zu",
@@ -694,8 +793,10 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
 
     TraceArgs a = trace_args(b, cam, lens, p, st, spp, hint_tri, w, rt, rec, ray_off);
     int blocks = 0;
-    if ((rc = rays_grid(false, HDOF_TRACE_BLOCK, &blocks))) return rc;
-    k_trace_rays<HDOF_TRACE_BLOCK><<<blocks, HDOF_TRACE_BLOCK, 0, s>>>(a, HDOF_TRACE_REFILL);
+    if ((rc = rays_grid(false, t.trace_refill == 0, t.trace_block, &blocks))) return rc;
+    if (t.trace_block == 64) launch_trace<64>(a, t.trace_refill, blocks, s);
+    else if (t.trace_block == 256) launch_trace<256>(a, t.trace_refill, blocks, s);
+    else launch_trace<128>(a, t.trace_refill, blocks, s);
     HDOF_LAUNCHED("hdof_trace: trace");
     k_resolve<<<(W * H + 255) / 256, 256, 0, s>>>(a);
     HDOF_LAUNCHED("hdof_trace: resolve");

@@ -110,7 +110,7 @@ def load():
         "hdof_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
         "hdof_mask": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp, sz, vp], C.c_int),
         "hdof_mask_noalloc": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp], C.c_int),
-        "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, vp, vp, vp, sz, vp],
+        "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, vp, vp, vp, sz, P(hdof_tuning), vp],
                        C.c_int),
         "hdof_postfilter": ([P(hdof_gbuf), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, sz, vp],
                             C.c_int),
@@ -332,14 +332,17 @@ def hdof_mask_noalloc(gbuf: GBuffer, prev_hist, p, edge, spp, stream=None):
                                     _stream(stream)))
 
 
-def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None, rec=None, ray_off=None, hint=None):
+def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None, rec=None, ray_off=None, hint=None,
+               tune=None):
     """rec (float [n_rays][4]) and ray_off (int32 [H][W]) optionally receive
     the per-ray hit records (L rgb, z) and each traced pixel's first ray;
     hint (int32 [H][W], the G-buffer's tri plane) optionally seeds each lens
-    ray with its pixel's primary hit."""
+    ray with its pixel's primary hit; tune (hdof_tuning) optionally fixes the
+    trace's form and block size (default: chosen from the lens)."""
     _check(load().hdof_trace(bvh.handle, C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)),
                              _ptr(spp), _ptr(hint), _ptr(rt), _ptr(stats), _ptr(rec), _ptr(ray_off), _ptr(workspace),
-                             workspace.numel() * workspace.element_size(), _stream(stream)))
+                             workspace.numel() * workspace.element_size(),
+                             C.byref(tune) if tune is not None else None, _stream(stream)))
 
 
 def hdof_postfilter(gbuf: GBuffer, cam, lns, p, pp, workspace, stream=None):
@@ -414,7 +417,7 @@ class Renderer:
 
 # ------------------------------------------------------ batched multi-view --
 
-def tuning(trace_block=128, trace_refill=4) -> hdof_tuning:
+def tuning(trace_block=128, trace_refill=0) -> hdof_tuning:
     t = hdof_tuning()
     t.trace_block, t.trace_refill = int(trace_block), int(trace_refill)
     return t

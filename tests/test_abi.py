@@ -91,7 +91,7 @@ def test_invalid_arguments_rejected_before_launch(H):
     assert b"image size" in buf.value
     p_bad = H.params(hi.Params(spp_max=300))
     assert lib.hdof_trace(C.c_void_p(1), C.byref(cam), C.byref(H.lens(hi.Lens())), C.byref(p_bad), None, None, None,
-                          None, None, None, None, 0, None) == -1
+                          None, None, None, None, 0, None, None) == -1
     lib.hdof_last_error(buf, 256)
     assert b"spp_max" in buf.value
     # batched calls: empty batch, unsupported launch shape, NULL handle
@@ -101,7 +101,7 @@ def test_invalid_arguments_rejected_before_launch(H):
     assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(96, 1)), C.byref(h), None) == -1
     lib.hdof_last_error(buf, 256)
     assert b"trace_block" in buf.value
-    assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(128, 0)), C.byref(h), None) == -1
+    assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(128, -1)), C.byref(h), None) == -1
     assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(128, 33)), C.byref(h), None) == -1
     assert lib.hdof_batch_render(None, None) == -1
     assert lib.hdof_batch_update(None, views, 1, None) == -1

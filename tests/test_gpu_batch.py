@@ -63,7 +63,7 @@ def _assert_same(a: H.Renderer, b: H.Renderer, tag):
         assert eq(getattr(ha, name)[tr], getattr(hb, name)[tr]), f"{tag}: history {name}"
 
 
-@pytest.mark.parametrize("block,refill", [(128, 16), (64, 32), (256, 1)])
+@pytest.mark.parametrize("block,refill", [(128, 0), (64, 0), (256, 0), (128, 16), (64, 32), (256, 1)])
 def test_batch_equals_single_view(small, block, refill):
     scenes, bvhs, views = small
     rs = _singles(bvhs, views)

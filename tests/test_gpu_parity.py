@@ -326,6 +326,45 @@ def test_trace_hint_does_not_change_results():
     assert torch.equal(outs[0].view(torch.int32), outs[2].view(torch.int32))
 
 
+@pytest.mark.parametrize("aperture", [None, 0.08])
+def test_trace_forms_agree(aperture):
+    """Warp packets and the ray-level trace (every block size, several refill
+    thresholds, with and without the hint) give the same trace bit for bit:
+    the box test never culls a box that could hold the closest hit, so the
+    (t, id) minimum does not depend on the traversal order.  The small
+    aperture is the room's (packets by default), 0.08 a wide one."""
+    W, Hh = 333, 190
+    scene = hi.room_scene(seed=2, aspect=W / Hh)
+    cam = hi.room_camera(2, W, Hh)
+    lens = hi.room_lens() if aperture is None else hi.Lens(1.5, aperture, 0.05).f32()
+    p = hi.room_params(frame=2)
+    bvh = bvh_of(scene)
+    g = H.GBuffer(W, Hh)
+    H.hdof_gbuffer(bvh, cam, cam, p, g)
+    rng = np.random.default_rng(6)
+    spp = dev((rng.integers(0, 9, (Hh, W)) * (rng.uniform(size=(Hh, W)) < 0.6)).astype(np.uint8))
+    outs = []
+    for tune, hint in [(None, g.tri), (H.tuning(128, 0), None), (H.tuning(64, 0), g.tri), (H.tuning(256, 0), g.tri),
+                       (H.tuning(128, 4), g.tri), (H.tuning(64, 1), None), (H.tuning(256, 32), g.tri)]:
+        rt = torch.zeros((Hh, W, 12), dtype=torch.float32, device="cuda")
+        stats = torch.zeros(2, dtype=torch.int32, device="cuda")
+        H.hdof_trace(bvh, cam, lens, p, spp, rt, stats, workspace(W, Hh, p), hint=hint, tune=tune)
+        H.hdof_sync()
+        outs.append(rt)
+    for o in outs[1:]:
+        assert torch.equal(outs[0].view(torch.int32), o.view(torch.int32))
+
+
+def test_trace_rejects_bad_tuning():
+    scene, cam, lens, p = hi.tiny_config()
+    bvh = bvh_of(scene)
+    spp = dev(np.ones((128, 128), np.uint8))
+    rt = torch.zeros((128, 128, 12), dtype=torch.float32, device="cuda")
+    for t in (H.tuning(96, 0), H.tuning(128, -1), H.tuning(128, 33)):
+        with pytest.raises(H.HdofError):
+            H.hdof_trace(bvh, cam, lens, p, spp, rt, None, workspace(128, 128, p), tune=t)
+
+
 def test_trace_empty_mask():
     scene, cam, lens, p = hi.tiny_config()
     bvh = bvh_of(scene)
