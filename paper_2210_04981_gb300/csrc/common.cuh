@@ -451,6 +451,27 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
     return h;
 }
 
+// Box test for rays of a known octant (OCT bit k set: direction component k
+// negative), so the entry and exit plane of each axis are known and need no
+// per-axis min/max; OCT < 0: any direction (slab_hit).  With the outward
+// offsets of make_ray an axis's entry distance never exceeds its exit
+// distance (rounding is monotone), so the decisions and tn equal slab_hit's.
+template <int OCT>
+__device__ __forceinline__ bool slab_hit_oct(const Ray& r, float lx, float hx, float ly, float hy, float lz,
+                                             float hz, float tmax, float& tn) {
+    if (OCT < 0) return slab_hit(r, lx, hx, ly, hy, lz, hz, tmax, tn);
+    const bool nx = OCT & 1, ny = OCT & 2, nz = OCT & 4;
+    const float ex = fmaf(nx ? hx : lx, r.id.x, -(nx ? r.ch.x : r.cl.x));
+    const float fx = fmaf(nx ? lx : hx, r.id.x, -(nx ? r.cl.x : r.ch.x));
+    const float ey = fmaf(ny ? hy : ly, r.id.y, -(ny ? r.ch.y : r.cl.y));
+    const float fy = fmaf(ny ? ly : hy, r.id.y, -(ny ? r.cl.y : r.ch.y));
+    const float ez = fmaf(nz ? hz : lz, r.id.z, -(nz ? r.ch.z : r.cl.z));
+    const float fz = fmaf(nz ? lz : hz, r.id.z, -(nz ? r.cl.z : r.ch.z));
+    tn = fmaxf(fmaxf(ex, ey), fmaxf(ez, 0.f));
+    const float tf = fminf(fminf(fx, fy), fminf(fz, tmax));
+    return tn <= tf * 1.0000019f;
+}
+
 // Warp-wide closest hits: all 32 lanes call this together; the active lanes'
 // rays share one traversal (node references and the stack are warp-uniform,
 // the stack lives in the caller's shared memory, one per warp).  A node is
@@ -464,9 +485,10 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
 // the warp without divergence.  h holds each lane's hit so far (a hint hit
 // or a miss); scene-sized triangles are left to the caller.  Returns false
 // when the step cap was reached (the warp stops; status is flagged).
-__device__ __forceinline__ bool closest_hit_warp(const BvhView& bvh, bool act, const Ray& r, float3 o,
-                                                 const Shear& sh, Hit& h, int cap, unsigned* status,
-                                                 int* __restrict__ stack) {
+template <int OCT>
+__device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool act, const Ray& r, float3 o,
+                                                     const Shear& sh, Hit& h, int cap, unsigned* status,
+                                                     int* __restrict__ stack) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     int cur = bvh.root, sp = 0, steps = 0;
@@ -483,8 +505,8 @@ __device__ __forceinline__ bool closest_hit_warp(const BvhView& bvh, bool act, c
             const float4 a = __ldg(&n->xy0), b = __ldg(&n->xy1), z = __ldg(&n->z01);
             const int4 ch = __ldg(&n->child);
             float t0 = 0.f, t1 = 0.f;
-            const bool h0 = act && slab_hit(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t, t0);
-            const bool h1 = act && slab_hit(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t, t1);
+            const bool h0 = act && slab_hit_oct<OCT>(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t, t0);
+            const bool h1 = act && slab_hit_oct<OCT>(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t, t1);
             const unsigned b0 = __ballot_sync(FULL, h0), b1 = __ballot_sync(FULL, h1);
             if (b0 && b1) {
                 // first the child nearer for most of the lanes that enter both
@@ -529,6 +551,29 @@ __device__ __forceinline__ bool closest_hit_warp(const BvhView& bvh, bool act, c
     if (act) atomicAdd(&g_trav_stats[0], 1ull);
 #endif
     return true;
+}
+
+// the traversal specialised to the packet's octant when all its active rays
+// share one (the usual case for coherent rays), the general one otherwise
+__device__ __forceinline__ bool closest_hit_warp(const BvhView& bvh, bool act, const Ray& r, float3 o,
+                                                 const Shear& sh, Hit& h, int cap, unsigned* status,
+                                                 int* __restrict__ stack) {
+    const unsigned FULL = 0xffffffffu;
+    const int oct = (r.id.x < 0.f ? 1 : 0) | (r.id.y < 0.f ? 2 : 0) | (r.id.z < 0.f ? 4 : 0);
+    const unsigned am = __ballot_sync(FULL, act);
+    const int o0 = __shfl_sync(FULL, oct, am ? __ffs(am) - 1 : 0);
+    const int u = __all_sync(FULL, !act || oct == o0) ? o0 : -1;
+    switch (u) {
+        case 0: return closest_hit_warp_oct<0>(bvh, act, r, o, sh, h, cap, status, stack);
+        case 1: return closest_hit_warp_oct<1>(bvh, act, r, o, sh, h, cap, status, stack);
+        case 2: return closest_hit_warp_oct<2>(bvh, act, r, o, sh, h, cap, status, stack);
+        case 3: return closest_hit_warp_oct<3>(bvh, act, r, o, sh, h, cap, status, stack);
+        case 4: return closest_hit_warp_oct<4>(bvh, act, r, o, sh, h, cap, status, stack);
+        case 5: return closest_hit_warp_oct<5>(bvh, act, r, o, sh, h, cap, status, stack);
+        case 6: return closest_hit_warp_oct<6>(bvh, act, r, o, sh, h, cap, status, stack);
+        case 7: return closest_hit_warp_oct<7>(bvh, act, r, o, sh, h, cap, status, stack);
+        default: return closest_hit_warp_oct<-1>(bvh, act, r, o, sh, h, cap, status, stack);
+    }
 }
 
 // Lambert shading at a hit: face normal turned towards the ray, albedo from
