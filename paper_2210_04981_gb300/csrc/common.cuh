@@ -375,6 +375,27 @@ __device__ __forceinline__ void hit_tri(const BvhView& bvh, int slot, float3 o, 
 extern __device__ unsigned long long g_trav_stats[4];
 #endif
 
+// Box test for rays of a known octant (OCT bit k set: direction component k
+// negative), so the entry and exit plane of each axis are known and need no
+// per-axis min/max; OCT < 0: any direction (slab_hit).  With the outward
+// offsets of make_ray an axis's entry distance never exceeds its exit
+// distance (rounding is monotone), so the decisions and tn equal slab_hit's.
+template <int OCT>
+__device__ __forceinline__ bool slab_hit_oct(const Ray& r, float lx, float hx, float ly, float hy, float lz,
+                                             float hz, float tmax, float& tn) {
+    if (OCT < 0) return slab_hit(r, lx, hx, ly, hy, lz, hz, tmax, tn);
+    const bool nx = OCT & 1, ny = OCT & 2, nz = OCT & 4;
+    const float ex = fmaf(nx ? hx : lx, r.id.x, -(nx ? r.ch.x : r.cl.x));
+    const float fx = fmaf(nx ? lx : hx, r.id.x, -(nx ? r.cl.x : r.ch.x));
+    const float ey = fmaf(ny ? hy : ly, r.id.y, -(ny ? r.ch.y : r.cl.y));
+    const float fy = fmaf(ny ? ly : hy, r.id.y, -(ny ? r.cl.y : r.ch.y));
+    const float ez = fmaf(nz ? hz : lz, r.id.z, -(nz ? r.ch.z : r.cl.z));
+    const float fz = fmaf(nz ? lz : hz, r.id.z, -(nz ? r.cl.z : r.ch.z));
+    tn = fmaxf(fmaxf(ex, ey), fmaxf(ez, 0.f));
+    const float tf = fminf(fminf(fx, fy), fminf(fz, tmax));
+    return tn <= tf * 1.0000019f;
+}
+
 // Closest hit: smallest t, equal t -> lower original id.  Stack traversal
 // (descend the nearer hit child, push the farther); scene-sized triangles
 // (when kept out of the tree) are tested last behind a slab test of their
@@ -382,8 +403,9 @@ extern __device__ unsigned long long g_trav_stats[4];
 // hint_slot >= 0: that triangle is tested first (a likely hit tightens the
 // traversal; the closest hit, the minimum of (t, id) over all hits, is
 // unchanged).
-__device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 d, int cap, unsigned* status,
-                                           int hint_slot = -1) {
+template <int OCT>
+__device__ __forceinline__ Hit closest_hit_oct(const BvhView& bvh, float3 o, float3 d, int cap, unsigned* status,
+                                               int hint_slot) {
     const float INF = __int_as_float(0x7f800000);
     Ray r = make_ray(o, d);
     Shear sh = make_shear(d);
@@ -409,8 +431,8 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
             float4 a = __ldg(&n->xy0), b = __ldg(&n->xy1), z = __ldg(&n->z01);
             int4 ch = __ldg(&n->child);
             float t0, t1;
-            const bool h0 = slab_hit(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t, t0);
-            const bool h1 = slab_hit(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t, t1);
+            const bool h0 = slab_hit_oct<OCT>(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t, t0);
+            const bool h1 = slab_hit_oct<OCT>(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t, t1);
             if (h0 && h1) {
                 int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
                 if (sp < HDOF_STACK) stack[sp++] = farc;
@@ -451,25 +473,28 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
     return h;
 }
 
-// Box test for rays of a known octant (OCT bit k set: direction component k
-// negative), so the entry and exit plane of each axis are known and need no
-// per-axis min/max; OCT < 0: any direction (slab_hit).  With the outward
-// offsets of make_ray an axis's entry distance never exceeds its exit
-// distance (rounding is monotone), so the decisions and tn equal slab_hit's.
-template <int OCT>
-__device__ __forceinline__ bool slab_hit_oct(const Ray& r, float lx, float hx, float ly, float hy, float lz,
-                                             float hz, float tmax, float& tn) {
-    if (OCT < 0) return slab_hit(r, lx, hx, ly, hy, lz, hz, tmax, tn);
-    const bool nx = OCT & 1, ny = OCT & 2, nz = OCT & 4;
-    const float ex = fmaf(nx ? hx : lx, r.id.x, -(nx ? r.ch.x : r.cl.x));
-    const float fx = fmaf(nx ? lx : hx, r.id.x, -(nx ? r.cl.x : r.ch.x));
-    const float ey = fmaf(ny ? hy : ly, r.id.y, -(ny ? r.ch.y : r.cl.y));
-    const float fy = fmaf(ny ? ly : hy, r.id.y, -(ny ? r.cl.y : r.ch.y));
-    const float ez = fmaf(nz ? hz : lz, r.id.z, -(nz ? r.ch.z : r.cl.z));
-    const float fz = fmaf(nz ? lz : hz, r.id.z, -(nz ? r.cl.z : r.ch.z));
-    tn = fmaxf(fmaxf(ex, ey), fmaxf(ez, 0.f));
-    const float tf = fminf(fminf(fx, fy), fminf(fz, tmax));
-    return tn <= tf * 1.0000019f;
+
+// Closest hit of each calling lane's own ray; when the lanes that call
+// together share a direction octant (primary rays of a pixel block) the
+// traversal specialised to it runs (same results, fewer box-test steps).
+__device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 d, int cap, unsigned* status,
+                                           int hint_slot = -1) {
+    const unsigned m = __activemask();
+    // the signs of 1/d as make_ray forms it (a -0 component gives -1e20)
+    const int oct = (signbit(d.x) ? 1 : 0) | (signbit(d.y) ? 2 : 0) | (signbit(d.z) ? 4 : 0);
+    const int o0 = __shfl_sync(m, oct, __ffs(m) - 1);
+    const int u = __all_sync(m, oct == o0) ? o0 : -1;
+    switch (u) {
+        case 0: return closest_hit_oct<0>(bvh, o, d, cap, status, hint_slot);
+        case 1: return closest_hit_oct<1>(bvh, o, d, cap, status, hint_slot);
+        case 2: return closest_hit_oct<2>(bvh, o, d, cap, status, hint_slot);
+        case 3: return closest_hit_oct<3>(bvh, o, d, cap, status, hint_slot);
+        case 4: return closest_hit_oct<4>(bvh, o, d, cap, status, hint_slot);
+        case 5: return closest_hit_oct<5>(bvh, o, d, cap, status, hint_slot);
+        case 6: return closest_hit_oct<6>(bvh, o, d, cap, status, hint_slot);
+        case 7: return closest_hit_oct<7>(bvh, o, d, cap, status, hint_slot);
+        default: return closest_hit_oct<-1>(bvh, o, d, cap, status, hint_slot);
+    }
 }
 
 // Warp-wide closest hits: all 32 lanes call this together; the active lanes'

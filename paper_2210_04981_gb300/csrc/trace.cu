@@ -276,129 +276,166 @@ struct ManyViews {
 constexpr int DONE_REF = 0x7fffffff;  // stack exhausted
 constexpr int NO_LEAF = 0;            // empty leaf slot (leaf references are negative)
 
+// One lane's traversal state in the ray-level trace.
+struct RayLane {
+    bool live, done;
+    int v, cur, leaf, sp, steps;
+    unsigned r;
+    Ray ray;
+    Shear sh;
+    Hit h;
+};
+
+// Steps of the ray-level trace between two fetches: node phases and leaf
+// phases until fewer than `refill` lanes are still live.  OCT >= 0: every
+// live lane's ray lies in that direction octant (box tests without per-axis
+// min/max, same decisions); rays are fetched only between calls, so it holds
+// throughout.
+template <int OCT, class Src>
+__device__ __forceinline__ void trace_rays_steps(const Src& src, RayLane& L, int (&stack)[HDOF_STACK], int refill) {
+    const unsigned FULL = 0xffffffffu;
+    const float INF = __int_as_float(0x7f800000);
+    while (true) {
+        // node phase: descend until no live lane is still looking for a leaf
+        while (true) {
+            // a lane past the step cap stops stepping (it is finished below)
+            const bool can_step = L.live && L.cur >= 0 && L.cur != DONE_REF && L.steps <= src.at(L.v).cap;
+            if (can_step) {
+                const TraceArgs& a = src.at(L.v);
+                const Node* n = a.bvh.nodes + L.cur;
+                float4 na = __ldg(&n->xy0), nb = __ldg(&n->xy1), nz = __ldg(&n->z01);
+                int4 ch = __ldg(&n->child);
+                float t0, t1;
+                const bool h0 = slab_hit_oct<OCT>(L.ray, na.x, na.y, na.z, na.w, nz.x, nz.y, L.h.t, t0);
+                const bool h1 = slab_hit_oct<OCT>(L.ray, nb.x, nb.y, nb.z, nb.w, nz.z, nz.w, L.h.t, t1);
+                if (h0 && h1) {
+                    int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
+                    if (L.sp < HDOF_STACK) stack[L.sp++] = farc;
+                    else atomicOr(a.status, HDOF_STATUS_TIMEOUT);
+                    L.cur = nearc;
+                } else if (h0) {
+                    L.cur = ch.x;
+                } else if (h1) {
+                    L.cur = ch.y;
+                } else {
+                    L.cur = L.sp ? stack[--L.sp] : DONE_REF;
+                }
+                if (L.cur < 0 && L.leaf == NO_LEAF) {  // park the leaf, keep descending
+                    L.leaf = L.cur;
+                    L.cur = L.sp ? stack[--L.sp] : DONE_REF;
+                }
+                ++L.steps;
+            }
+            const bool searching = can_step && L.leaf == NO_LEAF && L.cur >= 0 && L.cur != DONE_REF;
+            if (!__any_sync(FULL, searching)) break;
+        }
+        // leaf phase: every parked leaf; a leaf waiting in cur moves into the slot
+        if (L.live && L.leaf != NO_LEAF) {
+            const TraceArgs& a = src.at(L.v);
+            int e = ~L.leaf, first = e >> 3, count = (e & 7) + 1;
+            for (int k = 0; k < count; ++k) hit_tri(a.bvh, first + k, L.ray.o, L.sh, L.h);
+            L.leaf = NO_LEAF;
+            if (L.cur < 0) {
+                L.leaf = L.cur;
+                L.cur = L.sp ? stack[--L.sp] : DONE_REF;
+            }
+            ++L.steps;
+        }
+        if (L.live) {
+            const TraceArgs& a = src.at(L.v);
+            bool fin = L.leaf == NO_LEAF && L.cur == DONE_REF;
+            if (L.steps > a.cap) {
+                atomicOr(a.status, HDOF_STATUS_TIMEOUT);
+                fin = true;
+            }
+            if (fin) {
+                const BvhView& bvh = a.bvh;
+                for (int k = 0; k < bvh.big_count; ++k) {
+                    float4 lo = __ldg(&bvh.big_box[2 * k]), hi = __ldg(&bvh.big_box[2 * k + 1]);
+                    if (slab(L.ray, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, L.h.t) < INF)
+                        hit_tri(bvh, bvh.big_first + k, L.ray.o, L.sh, L.h);
+                }
+                // shading happens per pixel in the resolve, not here where
+                // few lanes of the warp finish at a time
+                a.recs[L.r] = make_float2(L.h.slot >= 0 ? L.h.t : INF, __int_as_float(L.h.slot));
+                L.live = false;
+            }
+        }
+        if (__popc(__ballot_sync(FULL, L.live)) < refill) break;
+    }
+}
+
 template <class Src>
 __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, unsigned* head, int refill) {
     const unsigned FULL = 0xffffffffu;
     const float INF = __int_as_float(0x7f800000);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    bool live = false, done = false;
-    int v = 0, cur = 0, leaf = NO_LEAF, sp = 0, steps = 0;
-    unsigned r = 0;
-    Ray ray;
-    Shear sh;
-    Hit h;
+    RayLane L;
+    L.live = L.done = false;
+    L.v = L.cur = L.sp = L.steps = 0;
+    L.leaf = NO_LEAF;
+    L.r = 0;
     int stack[HDOF_STACK];
     while (true) {
-        const unsigned need = __ballot_sync(FULL, !live && !done);
+        const unsigned need = __ballot_sync(FULL, !L.live && !L.done);
         if (need) {
             const int leader = __ffs(need) - 1;
             unsigned base = 0;
             if (lane == leader) base = atomicAdd(head, (unsigned)__popc(need));
             base = __shfl_sync(FULL, base, leader);
-            if (!live && !done) {
+            if (!L.live && !L.done) {
                 const unsigned g = base + __popc(need & lt);
                 if (g < total) {
-                    v = src.locate(g, r);
-                    const TraceArgs& a = src.at(v);
-                    const unsigned qp = __ldg(&a.ray_pix[r]);
+                    L.v = src.locate(g, L.r);
+                    const TraceArgs& a = src.at(L.v);
+                    const unsigned qp = __ldg(&a.ray_pix[L.r]);
                     float3 O, dir;
-                    lens_ray(a, qp, __ldg(&a.ray_s[r]), O, dir);
-                    ray = make_ray(O, dir);
-                    sh = make_shear(dir);
-                    h.t = INF;
-                    h.slot = -1;
-                    h.id = 0x7fffffff;
-                    h.b0 = h.b1 = h.b2 = 0.f;
+                    lens_ray(a, qp, __ldg(&a.ray_s[L.r]), O, dir);
+                    L.ray = make_ray(O, dir);
+                    L.sh = make_shear(dir);
+                    L.h.t = INF;
+                    L.h.slot = -1;
+                    L.h.id = 0x7fffffff;
+                    L.h.b0 = L.h.b1 = L.h.b2 = 0.f;
                     if (a.hint) {
                         // the pixel's primary hit first: a lens ray often hits the same
                         // triangle, and the tight distance culls what lies behind it (the
                         // closest hit, the minimum of (t, id) over all hits, is unchanged)
                         const int id = __ldg(&a.hint[qp]);
-                        if (id >= 0 && id < a.bvh.n_tris) hit_tri(a.bvh, __ldg(&a.bvh.slot_of[id]), ray.o, sh, h);
+                        if (id >= 0 && id < a.bvh.n_tris)
+                            hit_tri(a.bvh, __ldg(&a.bvh.slot_of[id]), L.ray.o, L.sh, L.h);
                     }
-                    cur = a.bvh.root;
-                    leaf = NO_LEAF;
-                    if (cur < 0) {  // the whole tree is one leaf
-                        leaf = cur;
-                        cur = DONE_REF;
+                    L.cur = a.bvh.root;
+                    L.leaf = NO_LEAF;
+                    if (L.cur < 0) {  // the whole tree is one leaf
+                        L.leaf = L.cur;
+                        L.cur = DONE_REF;
                     }
-                    sp = 0;
-                    steps = 0;
-                    live = true;
+                    L.sp = 0;
+                    L.steps = 0;
+                    L.live = true;
                 } else {
-                    done = true;
+                    L.done = true;
                 }
             }
         }
-        if (!__any_sync(FULL, live)) break;
-        while (true) {
-            // node phase: descend until no live lane is still looking for a leaf
-            while (true) {
-                // a lane past the step cap stops stepping (it is finished below)
-                const bool can_step = live && cur >= 0 && cur != DONE_REF && steps <= src.at(v).cap;
-                if (can_step) {
-                    const TraceArgs& a = src.at(v);
-                    const Node* n = a.bvh.nodes + cur;
-                    float4 na = __ldg(&n->xy0), nb = __ldg(&n->xy1), nz = __ldg(&n->z01);
-                    int4 ch = __ldg(&n->child);
-                    float t0, t1;
-                    const bool h0 = slab_hit(ray, na.x, na.y, na.z, na.w, nz.x, nz.y, h.t, t0);
-                    const bool h1 = slab_hit(ray, nb.x, nb.y, nb.z, nb.w, nz.z, nz.w, h.t, t1);
-                    if (h0 && h1) {
-                        int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
-                        if (sp < HDOF_STACK) stack[sp++] = farc;
-                        else atomicOr(a.status, HDOF_STATUS_TIMEOUT);
-                        cur = nearc;
-                    } else if (h0) {
-                        cur = ch.x;
-                    } else if (h1) {
-                        cur = ch.y;
-                    } else {
-                        cur = sp ? stack[--sp] : DONE_REF;
-                    }
-                    if (cur < 0 && leaf == NO_LEAF) {  // park the leaf, keep descending
-                        leaf = cur;
-                        cur = sp ? stack[--sp] : DONE_REF;
-                    }
-                    ++steps;
-                }
-                const bool searching = can_step && leaf == NO_LEAF && cur >= 0 && cur != DONE_REF;
-                if (!__any_sync(FULL, searching)) break;
-            }
-            // leaf phase: every parked leaf; a leaf waiting in cur moves into the slot
-            if (live && leaf != NO_LEAF) {
-                const TraceArgs& a = src.at(v);
-                int e = ~leaf, first = e >> 3, count = (e & 7) + 1;
-                for (int k = 0; k < count; ++k) hit_tri(a.bvh, first + k, ray.o, sh, h);
-                leaf = NO_LEAF;
-                if (cur < 0) {
-                    leaf = cur;
-                    cur = sp ? stack[--sp] : DONE_REF;
-                }
-                ++steps;
-            }
-            if (live) {
-                const TraceArgs& a = src.at(v);
-                bool fin = leaf == NO_LEAF && cur == DONE_REF;
-                if (steps > a.cap) {
-                    atomicOr(a.status, HDOF_STATUS_TIMEOUT);
-                    fin = true;
-                }
-                if (fin) {
-                    const BvhView& bvh = a.bvh;
-                    for (int k = 0; k < bvh.big_count; ++k) {
-                        float4 lo = __ldg(&bvh.big_box[2 * k]), hi = __ldg(&bvh.big_box[2 * k + 1]);
-                        if (slab(ray, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, h.t) < INF)
-                            hit_tri(bvh, bvh.big_first + k, ray.o, sh, h);
-                    }
-                    // shading happens per pixel in the resolve, not here where
-                    // few lanes of the warp finish at a time
-                    a.recs[r] = make_float2(h.slot >= 0 ? h.t : INF, __int_as_float(h.slot));
-                    live = false;
-                }
-            }
-            if (__popc(__ballot_sync(FULL, live)) < refill) break;
+        const unsigned lm = __ballot_sync(FULL, L.live);
+        if (!lm) break;
+        // the live lanes' common direction octant, if they share one
+        const int oct = (L.ray.id.x < 0.f ? 1 : 0) | (L.ray.id.y < 0.f ? 2 : 0) | (L.ray.id.z < 0.f ? 4 : 0);
+        const int o0 = __shfl_sync(FULL, oct, __ffs(lm) - 1);
+        const int u = __all_sync(FULL, !L.live || oct == o0) ? o0 : -1;
+        switch (u) {
+            case 0: trace_rays_steps<0>(src, L, stack, refill); break;
+            case 1: trace_rays_steps<1>(src, L, stack, refill); break;
+            case 2: trace_rays_steps<2>(src, L, stack, refill); break;
+            case 3: trace_rays_steps<3>(src, L, stack, refill); break;
+            case 4: trace_rays_steps<4>(src, L, stack, refill); break;
+            case 5: trace_rays_steps<5>(src, L, stack, refill); break;
+            case 6: trace_rays_steps<6>(src, L, stack, refill); break;
+            case 7: trace_rays_steps<7>(src, L, stack, refill); break;
+            default: trace_rays_steps<-1>(src, L, stack, refill); break;
         }
     }
 }
