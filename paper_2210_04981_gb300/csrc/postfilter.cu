@@ -127,25 +127,43 @@ __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx,
 template <class ND, class COL>
 __global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND, COL> a) { pf_prep_body(a, blockIdx.x, blockIdx.y); }
 
+// Per target pixel: near sums (S.x, S.y) and (S.z, W), far sums likewise,
+// as register pairs so one packed FMA updates two of them; the far depth
+// test's constants ka, kb.
 struct PfAcc {
-    float3 Sn, Sf;
-    float Wn, Wf;
+    float2 nxy, nzw, fxy, fzw;
     float ka, kb;
 };
 
+// (c.x, c.y) + s (e.x, e.y), each lane rounded once as fmaf would
+__device__ __forceinline__ float2 fma2(float s, float ex, float ey, float2 c) {
+    float2 r;
+    asm("{\n\t.reg .b64 ps, pe, pc, pr;\n\t"
+        "mov.b64 ps, {%2, %2};\n\t"
+        "mov.b64 pe, {%3, %4};\n\t"
+        "mov.b64 pc, {%5, %6};\n\t"
+        "fma.rn.f32x2 pr, ps, pe, pc;\n\t"
+        "mov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(s), "f"(ex), "f"(ey), "f"(c.x), "f"(c.y));
+    return r;
+}
+
 template <class COL>
 __device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size_t pq, float4* aux) {
-    float alpha = clamp01(a.Wn);
-    float3 N = a.Wn > HDOF_PP_MIN_W ? (1.f / a.Wn) * a.Sn : f3(0, 0, 0);
+    const float3 Sn = f3(a.nxy.x, a.nxy.y, a.nzw.x), Sf = f3(a.fxy.x, a.fxy.y, a.fzw.x);
+    const float Wn = a.nzw.y, Wf = a.fzw.y;
+    float alpha = clamp01(Wn);
+    float3 N = Wn > HDOF_PP_MIN_W ? (1.f / Wn) * Sn : f3(0, 0, 0);
     float3 F;
-    if (a.Wf > HDOF_PP_MIN_W) F = (1.f / a.Wf) * a.Sf;
+    if (Wf > HDOF_PP_MIN_W) F = (1.f / Wf) * Sf;
     else {
         float4 c = ld4(col + pq);
         F = f3(c.x, c.y, c.z);
     }
     if (aux) {  // layer colours and weights, kept for the adjoint
-        aux[2 * pq] = make_float4(N.x, N.y, N.z, a.Wn);
-        aux[2 * pq + 1] = make_float4(F.x, F.y, F.z, a.Wf);
+        aux[2 * pq] = make_float4(N.x, N.y, N.z, Wn);
+        aux[2 * pq + 1] = make_float4(F.x, F.y, F.z, Wf);
     }
     float3 o = alpha * N + (1.f - alpha) * F;
     return make_float4(o.x, o.y, o.z, alpha);
@@ -169,17 +187,13 @@ struct GatherArgs {
 // (zero outside the disk, and zero layer records, add exact zeros)
 __device__ __forceinline__ void acc_near(PfAcc& a, float d, float rh, const float4& n) {
     const float s = __saturatef(rh - d);
-    a.Sn.x = fmaf(s, n.x, a.Sn.x);
-    a.Sn.y = fmaf(s, n.y, a.Sn.y);
-    a.Sn.z = fmaf(s, n.z, a.Sn.z);
-    a.Wn = fmaf(s, n.w, a.Wn);
+    a.nxy = fma2(s, n.x, n.y, a.nxy);
+    a.nzw = fma2(s, n.z, n.w, a.nzw);
 }
 __device__ __forceinline__ void acc_far(PfAcc& a, float d, float rh, float zq, const float4& f) {
     const float t = __saturatef(rh - d) * __saturatef(fmaf(-zq, a.kb, a.ka));
-    a.Sf.x = fmaf(t, f.x, a.Sf.x);
-    a.Sf.y = fmaf(t, f.y, a.Sf.y);
-    a.Sf.z = fmaf(t, f.z, a.Sf.z);
-    a.Wf = fmaf(t, f.w, a.Wf);
+    a.fxy = fma2(t, f.x, f.y, a.fxy);
+    a.fzw = fma2(t, f.z, f.w, a.fzw);
 }
 
 // one (source, thread) tap: the thread's left pixels get fresh distances,
@@ -303,8 +317,7 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
             const float zp = x < W && y < H ? __ldg(&ar.zq[(size_t)y * W + x]) : z00;
             a[k].ka = ka;
             a[k].kb = 1.f / (ar.kz_rel * zp);
-            a[k].Sn = a[k].Sf = f3(0, 0, 0);
-            a[k].Wn = a[k].Wf = 0.f;
+            a[k].nxy = a[k].nzw = a[k].fxy = a[k].fzw = make_float2(0.f, 0.f);
         }
     }
     // far first: its depth-test constants are dead before the (longer) near loop
