@@ -217,26 +217,28 @@ __device__ __forceinline__ void pf_tap(PfAcc (&a)[PF_NPX], float (&c)[PF_RY], co
     }
 }
 
-// one layer's loop over a disk-shaped window of radius G around the 2x2
+// one layer's loop over a disk-shaped window of radius R around the 2x2
 // block at (i, j): every source feeding the layer within reach has
-// r + 1/2 <= G, so only taps closer than G to one of the four pixels can
+// r + 1/2 <= R, so only taps closer than R to one of the four pixels can
 // weigh; per source row, the columns of that disk (squared distances are
 // exact integers in float).  Records are split by the parity of the pixel
 // index (even pixels first), so at each tap the threads of a row, two
 // columns apart, read consecutive records; taps go in pairs (even, odd
 // index) with one float2 load of r + 1/2 (and z) per pair.
 template <bool NEAR>
-__device__ __forceinline__ void pf_layer(PfAcc (&a)[PF_NPX], int G, int i, int j, int W, int H,
+__device__ __forceinline__ void pf_layer(PfAcc (&a)[PF_NPX], float R, int i, int j, int W, int H,
                                          const float* __restrict__ rh, const float* __restrict__ zq,
                                          const float4* __restrict__ rec) {
-    if (G < 0) return;  // nothing within reach feeds this layer
+    if (R < 0.f) return;  // nothing within reach feeds this layer
+    // bounds lean outwards by 1e-3 pixel (float rounding); taps they add weigh 0
+    const int G = (int)floorf(R + 1e-3f);
     const size_t half = ((size_t)W * H + 1) >> 1;
     const float4* __restrict__ rec_e = rec;
     const float4* __restrict__ rec_o = rec + half;
     const float2* __restrict__ rh2 = reinterpret_cast<const float2*>(rh);
     const float2* __restrict__ zq2 = reinterpret_cast<const float2*>(zq);
     const int y0 = max(j - G, 0), y1 = min(j + PF_RY - 1 + G, H - 1);
-    const float G2 = (float)(G * G);
+    const float R2 = R * R;
     for (int y = y0; y <= y1; ++y) {
         const float dy = (float)(y - j);
         float dyk[PF_RY], c[PF_RY];
@@ -244,7 +246,7 @@ __device__ __forceinline__ void pf_layer(PfAcc (&a)[PF_NPX], int G, int i, int j
         for (int k = 0; k < PF_RY; ++k) dyk[k] = (dy - (float)k) * (dy - (float)k);
         // nearest of the thread's rows to this source row
         const float dmin = dy >= 0.f && dy <= (float)(PF_RY - 1) ? 0.f : fminf(dyk[0], dyk[PF_RY - 1]);
-        const int w = (int)ceilf(sqrtf(fmaxf(G2 - dmin, 0.f)));
+        const int w = (int)floorf(sqrtf(fmaxf(R2 - dmin, 0.f)) + 1e-3f);
         const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
         float dx = (float)(x0 - i);
         {
@@ -300,11 +302,14 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
         const float gx = ox == 0 ? 0.f : (float)((abs(ox) - 1) * TP + 1);
         const float gy = oy == 0 ? 0.f : (float)((abs(oy) - 1) * TP + 1);
         const float g2 = gx * gx + gy * gy;
-        if (r.x >= 0.f && g2 < (r.x + 0.5f) * (r.x + 0.5f)) atomicMax(&s_win[0], (int)ceilf(r.x + 0.5f));
-        if (r.y >= 0.f && g2 < (r.y + 0.5f) * (r.y + 0.5f)) atomicMax(&s_win[1], (int)ceilf(r.y + 0.5f));
+        // positive floats order as their bit patterns
+        if (r.x >= 0.f && g2 < (r.x + 0.5f) * (r.x + 0.5f)) atomicMax(&s_win[0], __float_as_int(r.x + 0.5f));
+        if (r.y >= 0.f && g2 < (r.y + 0.5f) * (r.y + 0.5f)) atomicMax(&s_win[1], __float_as_int(r.y + 0.5f));
     }
     __syncthreads();
-    const int Gn = s_win[0], Gf = s_win[1];
+    // the layer's reach R (-1: none); a source weighs only closer than R
+    const float Gn = s_win[0] < 0 ? -1.f : __int_as_float(s_win[0]);
+    const float Gf = s_win[1] < 0 ? -1.f : __int_as_float(s_win[1]);
     const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + PF_RY * (threadIdx.x >> 3);
     if (i >= W || j >= H) return;
     PfAcc a[PF_NPX];  // pixel (i + (k & 1), j + (k >> 1))

@@ -215,14 +215,16 @@ __device__ __forceinline__ void spatial_pixel(const SpatialArgs& a, int i, int j
     const size_t q = (size_t)j * W + i;
     const float4 cp = __ldg(&crt[q]);
     const float rp = fminf(cp.w * 0.5f, r_s);
-    const int K = (int)ceilf(rp + 0.5f);
-    // a tap weighs only if d < rp + 1/2 <= K: per row, the columns of that disk
+    // a tap weighs only if d < R = rp + 1/2: per row, the columns of that
+    // disk (the bounds lean outwards by 1e-3 pixel; the taps they add weigh 0)
+    const float R = rp + 0.5f, R2 = R * R;
+    const int K = (int)floorf(R + 1e-3f);
     float3 S = f3(0, 0, 0);
     float Ws = 0.f;
     const int y0 = max(j - K, 0), y1 = min(j + K, H - 1);
     for (int y = y0; y <= y1; ++y) {
         const float dy = (float)(y - j), dy2 = dy * dy;
-        const int wr = (int)ceilf(sqrtf((float)(K * K) - dy2));
+        const int wr = (int)floorf(sqrtf(fmaxf(R2 - dy2, 0.f)) + 1e-3f);
         const int x0 = max(i - wr, 0), x1 = min(i + wr, W - 1);
         const float4* row = crt + (size_t)y * W;
         float dx = (float)(x0 - i);
@@ -230,8 +232,9 @@ __device__ __forceinline__ void spatial_pixel(const SpatialArgs& a, int i, int j
         for (int x = x0; x <= x1; ++x, dx += 1.f) {
             const float4 c = __ldg(&row[x]);
             const float d = sqrt_approx(fmaf(dx, dx, dy2));
-            float wq = soft_step(rp - d) * soft_step(fminf(c.w * 0.5f, r_s) - d);
-            wq = c.w < 0.f ? 0.f : wq;  // untraced neighbours carry no sample
+            // an untraced neighbour (written as (0, 0, 0, -1)) weighs
+            // clamp(-d, 0, 1) = 0 times colour 0: it adds nothing
+            const float wq = soft_step(rp - d) * soft_step(fminf(c.w * 0.5f, r_s) - d);
             S.x = fmaf(wq, c.x, S.x);
             S.y = fmaf(wq, c.y, S.y);
             S.z = fmaf(wq, c.z, S.z);
