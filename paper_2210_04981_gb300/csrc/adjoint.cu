@@ -334,14 +334,16 @@ __global__ void __launch_bounds__(256) k_spatial_bwd(const float4* __restrict__ 
     const float rpx = cx.w * 0.5f < r_s ? 0.5f : 0.f;
     const float4 bx = spb[q];
     const float3 Cx = ldf3(cx), ax = ldf3(bx);
-    const int K = (int)ceilf(rx + 0.5f);
+    // a neighbour takes part only if d < R = rx + 1/2: per row, the columns
+    // of that disk (bounds lean outwards by 1e-3 pixel; taps they add weigh 0)
+    const float R = rx + 0.5f, R2 = R * R;
+    const int K = (int)floorf(R + 1e-3f);
     float3 gC = f3(0, 0, 0);
     float gcx = 0.f;
-    // a neighbour takes part only if d < rx + 1/2 <= K: per row, the columns of that disk
     const int y0 = max(j - K, 0), y1 = min(j + K, H - 1);
     for (int y = y0; y <= y1; ++y) {
         const float dy = (float)(y - j), dy2 = dy * dy;
-        const int wr = (int)ceilf(sqrtf(fmaxf((float)(K * K) - dy2, 0.f)));
+        const int wr = (int)floorf(sqrtf(fmaxf(R2 - dy2, 0.f)) + 1e-3f);
         const int x0 = max(i - wr, 0), x1 = min(i + wr, W - 1);
         for (int x = x0; x <= x1; ++x) {
             float dx = (float)(x - i);
@@ -619,13 +621,16 @@ __global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __re
             src.wnia[k] = sr.wnia;
             src.fia[k] = sr.fia;
             src.Cq[k] = ldf3(__ldg(&col[q]));
-            atomicMax(&s_win, (int)ceilf(sr.R));
+            atomicMax(&s_win, __float_as_int(sr.R));  // positive floats order as their bits
         }
     }
     __syncthreads();
     float2 dth = make_float2(0.f, 0.f);
     if (in0) {
-        const int G = s_win;
+        // the block's reach R = max(r) + 1/2: a pair weighs (and its rim term
+        // counts) only closer than that; bounds lean outwards by 1e-3 pixel
+        const float Rw = __int_as_float(s_win), R2w = Rw * Rw;
+        const int G = (int)floorf(Rw + 1e-3f);
         const float ka = 1.f + 1.f / kz_rel;
         const size_t px = (size_t)W * H, half = (px + 1) >> 1;
         const float4* __restrict__ pn_e = pfb;
@@ -640,11 +645,11 @@ __global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __re
             acc[k].S1 = acc[k].S2 = acc[k].S3 = acc[k].S4 = 0.f;
         }
         const int y0 = max(j - G, 0), y1 = min(j + 1 + G, H - 1);
-        const float G2 = (float)(G * G);
         for (int y = y0; y <= y1; ++y) {
             const float dy = (float)(y - j);
             const float dy0 = dy * dy, dy1 = (dy - 1.f) * (dy - 1.f);
-            const int w = (int)ceilf(sqrtf(fmaxf(G2 - fminf(dy0, dy1), 0.f)));
+            const float dmin = dy >= 0.f && dy <= 1.f ? 0.f : fminf(dy0, dy1);
+            const int w = (int)floorf(sqrtf(fmaxf(R2w - dmin, 0.f)) + 1e-3f);
             const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
             float dx = (float)(x0 - i);
             float c[2];
