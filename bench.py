@@ -53,8 +53,8 @@ PF_FLOPS_PER_TAP = 12
 # stage's kernels, one ncu launch-list capture with caches flushed before each
 # launch) of the current kernels on the 1080p room frame with f32 storage;
 # other workloads report null
-MEASURED_TRAFFIC = {("room", "f32", "trace"): 54.92e6,      # k_count k_scan k_scatter k_trace_rays k_resolve
-                    ("room", "f32", "postfilter"): 186.96e6}  # k_pf_prep k_pf_gather
+MEASURED_TRAFFIC = {("room", "f32", "trace"): None,     # k_count k_scan k_scatter k_trace_packets k_resolve
+                    ("room", "f32", "postfilter"): None}  # k_pf_prep k_pf_gather
 
 
 def peaks():
@@ -303,7 +303,7 @@ def run_ours(args):
         ach = TRACE_FLOPS_PER_RAY * float(rays.mean()) / (trace_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                 "frac": round(ach / fp32_peak, 3),
-                "kernel": "trace stage (k_count, k_scan, k_scatter, k_trace_rays, k_resolve)",
+                "kernel": "trace stage (k_count, k_scan, k_scatter, k_trace_packets or k_trace_rays by lens, k_resolve)",
                 "traffic": MEASURED_TRAFFIC.get((args.scene, "mixed" if mixed else "f32", "trace")),
                 "flops_per_ray": TRACE_FLOPS_PER_RAY, "mrays_per_s": round(mrays, 1),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock under load"}
