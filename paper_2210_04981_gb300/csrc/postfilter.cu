@@ -38,7 +38,7 @@ constexpr int PF_RY = HDOF_PF_RY;
 constexpr int PF_NPX = 2 * PF_RY;
 constexpr int GATHER_THREADS = 8 * (16 / PF_RY);
 #ifndef HDOF_PF_MINB
-#define HDOF_PF_MINB 10  // resident gather blocks per SM the register budget targets
+#define HDOF_PF_MINB 12  // resident gather blocks per SM the register budget targets
 #endif
 #ifndef HDOF_PF_UNROLL
 #define HDOF_PF_UNROLL 4  // unroll of the gather's tap-pair loop
@@ -127,11 +127,14 @@ __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx,
 template <class ND, class COL>
 __global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND, COL> a) { pf_prep_body(a, blockIdx.x, blockIdx.y); }
 
-// Per target pixel: near sums (S.x, S.y) and (S.z, W), far sums likewise,
-// as register pairs so one packed FMA updates two of them; the far depth
-// test's constants ka, kb.
-struct PfAcc {
-    float2 nxy, nzw, fxy, fzw;
+// Per target pixel: a layer's sums (S.x, S.y) and (S.z, W) as register
+// pairs so one packed FMA updates two of them; the far layer also holds its
+// depth test's constants ka, kb.
+struct NearAcc {
+    float2 xy, zw;
+};
+struct FarAcc {
+    float2 xy, zw;
     float ka, kb;
 };
 
@@ -149,10 +152,12 @@ __device__ __forceinline__ float2 fma2(float s, float ex, float ey, float2 c) {
     return r;
 }
 
+// far = (S.x, S.y, S.z, W) of the far layer
 template <class COL>
-__device__ __forceinline__ float4 pf_finish(const PfAcc& a, const COL* col, size_t pq, float4* aux) {
-    const float3 Sn = f3(a.nxy.x, a.nxy.y, a.nzw.x), Sf = f3(a.fxy.x, a.fxy.y, a.fzw.x);
-    const float Wn = a.nzw.y, Wf = a.fzw.y;
+__device__ __forceinline__ float4 pf_finish(const NearAcc& a, const float4& far, const COL* col, size_t pq,
+                                            float4* aux) {
+    const float3 Sn = f3(a.xy.x, a.xy.y, a.zw.x), Sf = f3(far.x, far.y, far.z);
+    const float Wn = a.zw.y, Wf = far.w;
     float alpha = clamp01(Wn);
     float3 N = Wn > HDOF_PP_MIN_W ? (1.f / Wn) * Sn : f3(0, 0, 0);
     float3 F;
@@ -185,34 +190,29 @@ struct GatherArgs {
 
 // one source into one target pixel, branch-free: s = clamp(r_q + 1/2 - d, 0, 1)
 // (zero outside the disk, and zero layer records, add exact zeros)
-__device__ __forceinline__ void acc_near(PfAcc& a, float d, float rh, const float4& n) {
+__device__ __forceinline__ void acc(NearAcc& a, float d, float rh, float, const float4& n) {
     const float s = __saturatef(rh - d);
-    a.nxy = fma2(s, n.x, n.y, a.nxy);
-    a.nzw = fma2(s, n.z, n.w, a.nzw);
+    a.xy = fma2(s, n.x, n.y, a.xy);
+    a.zw = fma2(s, n.z, n.w, a.zw);
 }
-__device__ __forceinline__ void acc_far(PfAcc& a, float d, float rh, float zq, const float4& f) {
+__device__ __forceinline__ void acc(FarAcc& a, float d, float rh, float zq, const float4& f) {
     const float t = __saturatef(rh - d) * __saturatef(fmaf(-zq, a.kb, a.ka));
-    a.fxy = fma2(t, f.x, f.y, a.fxy);
-    a.fzw = fma2(t, f.z, f.w, a.fzw);
+    a.xy = fma2(t, f.x, f.y, a.xy);
+    a.zw = fma2(t, f.z, f.w, a.zw);
 }
 
 // one (source, thread) tap: the thread's left pixels get fresh distances,
 // its right pixels the left pixels' distances of the previous tap (the same
 // offsets, so the same floats), carried in c
-template <bool NEAR>
-__device__ __forceinline__ void pf_tap(PfAcc (&a)[PF_NPX], float (&c)[PF_RY], const float (&dyk)[PF_RY], float dx,
+template <class A>
+__device__ __forceinline__ void pf_tap(A (&a)[PF_NPX], float (&c)[PF_RY], const float (&dyk)[PF_RY], float dx,
                                        float r, float z, const float4& e) {
     const float dx2 = dx * dx;
 #pragma unroll
     for (int k = 0; k < PF_RY; ++k) {
         const float d0 = sqrt_approx(dx2 + dyk[k]);
-        if (NEAR) {
-            acc_near(a[2 * k], d0, r, e);
-            acc_near(a[2 * k + 1], c[k], r, e);
-        } else {
-            acc_far(a[2 * k], d0, r, z, e);
-            acc_far(a[2 * k + 1], c[k], r, z, e);
-        }
+        acc(a[2 * k], d0, r, z, e);
+        acc(a[2 * k + 1], c[k], r, z, e);
         c[k] = d0;
     }
 }
@@ -225,8 +225,8 @@ __device__ __forceinline__ void pf_tap(PfAcc (&a)[PF_NPX], float (&c)[PF_RY], co
 // index (even pixels first), so at each tap the threads of a row, two
 // columns apart, read consecutive records; taps go in pairs (even, odd
 // index) with one float2 load of r + 1/2 (and z) per pair.
-template <bool NEAR>
-__device__ __forceinline__ void pf_layer(PfAcc (&a)[PF_NPX], float R, int i, int j, int W, int H,
+template <bool NEAR, class A>
+__device__ __forceinline__ void pf_layer(A (&a)[PF_NPX], float R, int i, int j, int W, int H,
                                          const float* __restrict__ rh, const float* __restrict__ zq,
                                          const float4* __restrict__ rec) {
     if (R < 0.f) return;  // nothing within reach feeds this layer
@@ -258,7 +258,7 @@ __device__ __forceinline__ void pf_layer(PfAcc (&a)[PF_NPX], float R, int i, int
         const size_t gend = (size_t)y * W + x1 + 1;
         if (g & 1) {  // an odd first tap on its own
             const float z = NEAR ? 0.f : __ldg(&zq[g]);
-            pf_tap<NEAR>(a, c, dyk, dx, __ldg(&rh[g]), z, __ldg(&rec_o[g >> 1]));
+            pf_tap(a, c, dyk, dx, __ldg(&rh[g]), z, __ldg(&rec_o[g >> 1]));
             ++g;
             dx += 1.f;
         }
@@ -269,13 +269,13 @@ __device__ __forceinline__ void pf_layer(PfAcc (&a)[PF_NPX], float R, int i, int
             const float2 r2 = __ldg(&rh2[m]);
             const float4 e0 = __ldg(&rec_e[m]), e1 = __ldg(&rec_o[m]);
             const float2 z2 = NEAR ? make_float2(0.f, 0.f) : __ldg(&zq2[m]);
-            pf_tap<NEAR>(a, c, dyk, dx, r2.x, z2.x, e0);
-            pf_tap<NEAR>(a, c, dyk, dx + 1.f, r2.y, z2.y, e1);
+            pf_tap(a, c, dyk, dx, r2.x, z2.x, e0);
+            pf_tap(a, c, dyk, dx + 1.f, r2.y, z2.y, e1);
         }
         if (gend & 1) {  // an even last tap on its own
             const size_t gl = gend - 1;
             const float z = NEAR ? 0.f : __ldg(&zq[gl]);
-            pf_tap<NEAR>(a, c, dyk, dx, __ldg(&rh[gl]), z, __ldg(&rec_e[gl >> 1]));
+            pf_tap(a, c, dyk, dx, __ldg(&rh[gl]), z, __ldg(&rec_e[gl >> 1]));
         }
     }
 }
@@ -312,28 +312,38 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
     const float Gf = s_win[1] < 0 ? -1.f : __int_as_float(s_win[1]);
     const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + PF_RY * (threadIdx.x >> 3);
     if (i >= W || j >= H) return;
-    PfAcc a[PF_NPX];  // pixel (i + (k & 1), j + (k >> 1))
-    {
+    // far layer first; its sums wait in the pixels' own pp slots (each pixel
+    // is this thread's alone) so they hold no registers during the near loop
+    if (Gf >= 0.f) {
+        FarAcc f[PF_NPX];  // pixel (i + (k & 1), j + (k >> 1))
         const float ka = 1.f + 1.f / ar.kz_rel;  // k_z = clamp(ka - z_q kb), kb = 1 / (kz_rel z_p)
         const float z00 = __ldg(&ar.zq[(size_t)j * W + i]);
 #pragma unroll
         for (int k = 0; k < PF_NPX; ++k) {
             const int x = i + (k & 1), y = j + (k >> 1);
             const float zp = x < W && y < H ? __ldg(&ar.zq[(size_t)y * W + x]) : z00;
-            a[k].ka = ka;
-            a[k].kb = 1.f / (ar.kz_rel * zp);
-            a[k].nxy = a[k].nzw = a[k].fxy = a[k].fzw = make_float2(0.f, 0.f);
+            f[k].ka = ka;
+            f[k].kb = 1.f / (ar.kz_rel * zp);
+            f[k].xy = f[k].zw = make_float2(0.f, 0.f);
+        }
+        pf_layer<false>(f, Gf, i, j, W, H, ar.rh, ar.zq, ar.frec);
+#pragma unroll
+        for (int k = 0; k < PF_NPX; ++k) {
+            const int x = i + (k & 1), y = j + (k >> 1);
+            if (x < W && y < H) pp[(size_t)y * W + x] = make_float4(f[k].xy.x, f[k].xy.y, f[k].zw.x, f[k].zw.y);
         }
     }
-    // far first: its depth-test constants are dead before the (longer) near loop
-    pf_layer<false>(a, Gf, i, j, W, H, ar.rh, ar.zq, ar.frec);
+    NearAcc a[PF_NPX];
+#pragma unroll
+    for (int k = 0; k < PF_NPX; ++k) a[k].xy = a[k].zw = make_float2(0.f, 0.f);
     pf_layer<true>(a, Gn, i, j, W, H, ar.rh, ar.zq, ar.nrec);
 #pragma unroll
     for (int k = 0; k < PF_NPX; ++k) {
         const int x = i + (k & 1), y = j + (k >> 1);
         if (x < W && y < H) {
             const size_t q = (size_t)y * W + x;
-            pp[q] = pf_finish(a[k], col, q, aux);
+            const float4 far = Gf >= 0.f ? pp[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            pp[q] = pf_finish(a[k], far, col, q, aux);
         }
     }
 }
