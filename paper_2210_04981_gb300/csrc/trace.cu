@@ -6,16 +6,18 @@
 //
 // Compaction (deterministic, tile order): k_count counts traced pixels and
 // rays per 16x16 tile, k_scan turns the counts into queue and ray offsets,
-// k_scatter writes the traced pixels in row-major order within each tile
-// and lists every ray as (pixel, sample).
+// k_scatter writes the traced pixels in Z order within each tile and lists
+// every ray as (pixel, sample).
 //
-// Trace: k_trace_rays is persistent over the ray list.  Each lane holds one
-// ray; when it finishes, its (radiance, hit distance) record is written and,
-// once fewer than `refill` lanes of the warp are still busy, the idle lanes
-// take the next rays with one atomic per warp (dynamic fetch), so warps stay
-// full whatever the per-pixel ray counts and traversal lengths.  k_resolve
-// then sums each pixel's records in sample order, so the output does not
-// depend on scheduling.
+// Trace: two persistent forms over the ray list, each writing a (hit
+// distance, triangle slot) record per ray.  k_trace_packets: a warp takes 32
+// consecutive rays and finds their closest hits in one shared traversal
+// (narrow lenses: the rays stay close).  k_trace_rays: each lane holds one
+// ray and, once fewer than `refill` lanes of the warp are still busy, the
+// idle lanes take the next rays with one atomic per warp (dynamic fetch), so
+// warps stay full whatever the per-pixel ray counts and traversal lengths.
+// k_resolve then shades each pixel's hits and sums them in sample order, so
+// the output does not depend on scheduling.
 #include "batch.cuh"
 #include "internal.h"
 
@@ -127,8 +129,10 @@ __device__ __forceinline__ void scan_body(const ScanArgs& a) {
 
 __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) { scan_body(a); }
 
-// queue entries in row-major order within each tile; optionally the first
-// ray of every traced pixel (tile ray offset + prefix of spp in queue order)
+// queue entries in Z (Morton) order within each tile, so four consecutive
+// pixels form a 2x2 square and a warp's 32 an 8x4 block (the rays that one
+// packet or one warp traces together stay close); optionally the first ray
+// of every traced pixel (tile ray offset + prefix of spp in queue order)
 struct ScatterArgs {
     const uint8_t* spp;
     int W, H, ntx, smax;
@@ -151,7 +155,10 @@ __device__ __forceinline__ void scatter_body(const ScatterArgs& a, int bx, int b
     unsigned* __restrict__ ray_pix = a.ray_pix;
     uint8_t* __restrict__ ray_s = a.ray_s;
     unsigned* __restrict__ ray_off = a.ray_off;
-    int i = bx * TB + (threadIdx.x & 15), j = by * TB + (threadIdx.x >> 4);
+    const int t = threadIdx.x;  // Z-order index: x from the even bits, y from the odd bits
+    const int mx = (t & 1) | ((t >> 1) & 2) | ((t >> 2) & 4) | ((t >> 3) & 8);
+    const int my = ((t >> 1) & 1) | ((t >> 2) & 2) | ((t >> 3) & 4) | ((t >> 4) & 8);
+    int i = bx * TB + mx, j = by * TB + my;
     unsigned n = (i < W && j < H) ? min((unsigned)spp[(size_t)j * W + i], (unsigned)a.smax) : 0u;
     bool on = n > 0;
     unsigned m = __ballot_sync(0xffffffffu, on);
