@@ -54,7 +54,7 @@ PF_FLOPS_PER_TAP = 12
 # launch) of the current kernels on the 1080p room frame with f32 storage;
 # other workloads report null
 MEASURED_TRAFFIC = {("room", "f32", "trace"): 53.13e6,      # k_count k_scan k_scatter k_trace_packets k_resolve
-                    ("room", "f32", "postfilter"): 178.81e6}  # k_pf_prep k_pf_gather
+                    ("room", "f32", "postfilter"): None}  # k_pf_prep k_pf_rowscan k_pf_gather
 
 
 def peaks():
@@ -296,7 +296,7 @@ def run_ours(args):
     if dom == "postfilter":
         ach = taps * PF_FLOPS_PER_TAP / (pf_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                "frac": round(ach / fp32_peak, 3), "kernel": "postfilter (k_pf_prep + k_pf_gather)",
+                "frac": round(ach / fp32_peak, 3), "kernel": "postfilter (k_pf_prep + k_pf_rowscan + k_pf_gather)",
                 "traffic": MEASURED_TRAFFIC.get((args.scene, "mixed" if mixed else "f32", "postfilter")),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock under load"}
     elif dom == "trace":
@@ -352,7 +352,7 @@ def run_ours(args):
         "traced_px_per_frame": int(traced.mean()), "trace_ms": round(trace_ms, 4),
         "stages": per_stage, "bvh_build_ms": round(bvh_ms, 3), "scene_upload_ms": round(upload_ms, 3),
         "wall_s_timed": round(wall, 3),
-        "roofline": roof, "e2e": e2e, "gpu_launches": 13 * K, "clocks": clocks,
+        "roofline": roof, "e2e": e2e, "gpu_launches": 14 * K, "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
@@ -533,7 +533,7 @@ def run_batch(args):
         "mrays_per_s_trace": round(rays / (stage_ms[3] * 1e-3) / 1e6, 1),
         "rays_per_frame": int(rays), "traced_px_per_frame": int(traced),
         "stages": {n: round(float(t), 4) for n, t in zip(H.BATCH_STAGES, stage_ms)},
-        "bvh_build_ms": round(bvh_ms, 3), "roofline": roof, "e2e": e2e, "gpu_launches": 15 * K, "clocks": clocks,
+        "bvh_build_ms": round(bvh_ms, 3), "roofline": roof, "e2e": e2e, "gpu_launches": 16 * K, "clocks": clocks,
     }
     b.close()
     if rank == 0:
@@ -636,7 +636,7 @@ def run_diff(args):
                      "flops_per_tap": PF_BWD_FLOPS_PER_TAP},
         "e2e": {"value": round(e_ms / K, 4), "unit": "ms/step", "h2d_bytes_per_step": int(hC.numel() * 4),
                 "d2h_bytes_per_step": int(hg.numel() * 4 + 8)},
-        "gpu_launches": 13 * K, "clocks": clocks,
+        "gpu_launches": 14 * K, "clocks": clocks,
     }
     print(json.dumps(out), flush=True)
 

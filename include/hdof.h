@@ -289,7 +289,9 @@ int hdof_trace(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* len
  * normalised by the disk's lattice area; near layer weighted by w_near(q),
  * far layer by 1 - w_near(q) and the depth test clamp(1 - (z_q - z_p) /
  * (kz_rel z_p), 0, 1).  pp: float [H][W][4] = (alpha N + (1-alpha) F, alpha).
- * Gathers are bounded per 16x16 tile by the largest reaching CoC. */
+ * Gathers are bounded per 16x16 tile by the largest reaching CoC; where every
+ * near source close to a tile has a large CoC, the taps of weight exactly 1
+ * are summed from row prefix sums (the same sum, another rounding order). */
 int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, const hdof_lens* lens,
                     const hdof_params* p, float* pp, void* workspace, size_t workspace_bytes,
                     void* stream);
@@ -385,7 +387,7 @@ enum {
     HDOF_STAGE_MASK = 1,        /* tile clear, edge, spp: 3 launches */
     HDOF_STAGE_COMPACT = 2,     /* count, scan, scatter: 3 launches */
     HDOF_STAGE_TRACE = 3,       /* ray prefix, persistent trace, resolve: 3 launches */
-    HDOF_STAGE_POSTFILTER = 4,  /* prep, gather: 2 launches */
+    HDOF_STAGE_POSTFILTER = 4,  /* prep, row prefix, gather: 3 launches */
     HDOF_STAGE_RECONSTRUCT = 5, /* temporal, spatial: 2 launches */
     HDOF_STAGE_COMPOSITE = 6,   /* 1 launch */
     HDOF_BATCH_STAGES = 7

@@ -127,8 +127,9 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     l.pf_frec = align256(npx * sizeof(float4));
     l.pf_rh = align256(npx * sizeof(float));
     l.pf_zq = align256(npx * sizeof(float));
-    l.pf_tiles = align256(ptiles * sizeof(float2));
-    l.pf = l.pf_nrec + l.pf_frec + l.pf_rh + l.pf_zq + l.pf_tiles;
+    l.pf_tiles = align256(ptiles * sizeof(float4));
+    l.pf_pre = align256(npx * sizeof(float4));
+    l.pf = l.pf_nrec + l.pf_frec + l.pf_rh + l.pf_zq + l.pf_tiles + l.pf_pre;
     l.pf_off = align256(l.mask_tiles > l.trace ? l.mask_tiles : l.trace);
     l.total = l.pf_off + l.pf;
     return l;

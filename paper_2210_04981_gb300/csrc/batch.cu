@@ -41,7 +41,7 @@ struct StageDef {
 
 // per-view records in launch order (the tile clear, the scan and the
 // persistent trace are launched between the grid stages by hand)
-enum { S_GBUF, S_MASK_EDGE, S_MASK_SPP, S_COUNT, S_SCATTER, S_TRACE, S_PF_PREP, S_PF_GATHER, S_TEMPORAL,
+enum { S_GBUF, S_MASK_EDGE, S_MASK_SPP, S_COUNT, S_SCATTER, S_TRACE, S_PF_PREP, S_PF_ROWSCAN, S_PF_GATHER, S_TEMPORAL,
        S_SPATIAL, S_COMPOSITE, N_STAGES };
 
 const StageDef kStages[N_STAGES] = {
@@ -52,6 +52,7 @@ const StageDef kStages[N_STAGES] = {
     {"scatter", scatter_args_size, scatter_fill, scatter_launch_batch},
     {"trace", trace_args_size, trace_fill, nullptr},  // its grid is the per-pixel resolve
     {"post-filter prep", pf_prep_args_size, pf_prep_fill, pf_prep_launch_batch},
+    {"post-filter row prefix", pf_rowscan_args_size, pf_rowscan_fill, pf_rowscan_launch_batch},
     {"post-filter gather", pf_gather_args_size, pf_gather_fill, pf_gather_launch_batch},
     {"temporal", temporal_args_size, temporal_fill, temporal_launch_batch},
     {"spatial", spatial_args_size, spatial_fill, spatial_launch_batch},
@@ -330,6 +331,7 @@ extern "C" int hdof_batch_render_range(const hdof_batch* b, int32_t first, int32
             }
             case HDOF_STAGE_POSTFILTER:
                 run(S_PF_PREP);
+                run(S_PF_ROWSCAN);
                 run(S_PF_GATHER);
                 break;
             case HDOF_STAGE_RECONSTRUCT:

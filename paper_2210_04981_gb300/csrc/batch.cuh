@@ -66,7 +66,8 @@ struct ViewWs {
     float4* frec;        // post-filter far-layer record per pixel
     float* rh;           // post-filter r + 1/2 per pixel
     float* zq;           // post-filter view depth per pixel
-    float2* tmax;        // post-filter per-tile radii (near, far)
+    float4* tmax;        // post-filter per-tile radii (largest near, largest far, smallest near)
+    float4* pre;         // post-filter row prefix of the near records (row-major)
 };
 
 // the post-filter regions, laid out from `pf` (ws_layout(...).pf bytes)
@@ -76,7 +77,8 @@ inline void pf_regions(ViewWs& w, char* pf, const WsLayout& L) {
     w.frec = reinterpret_cast<float4*>(pf + (f += L.pf_nrec));
     w.rh = reinterpret_cast<float*>(pf + (f += L.pf_frec));
     w.zq = reinterpret_cast<float*>(pf + (f += L.pf_rh));
-    w.tmax = reinterpret_cast<float2*>(pf + (f += L.pf_zq));
+    w.tmax = reinterpret_cast<float4*>(pf + (f += L.pf_zq));
+    w.pre = reinterpret_cast<float4*>(pf + (f += L.pf_tiles));
 }
 
 inline ViewWs view_ws(const hdof_view& v) {
@@ -110,6 +112,7 @@ HDOF_BATCH_STAGE(mask_spp)
 HDOF_BATCH_STAGE(count)
 HDOF_BATCH_STAGE(scatter)
 HDOF_BATCH_STAGE(pf_prep)
+HDOF_BATCH_STAGE(pf_rowscan)
 HDOF_BATCH_STAGE(pf_gather)
 HDOF_BATCH_STAGE(temporal)
 HDOF_BATCH_STAGE(spatial)

@@ -67,7 +67,8 @@ struct WsLayout {
     size_t pf_frec;         // float4 per pixel: far-layer record
     size_t pf_rh;           // float per pixel: r + 1/2
     size_t pf_zq;           // float per pixel: view depth
-    size_t pf_tiles;        // float2 per 16x16 tile
+    size_t pf_tiles;        // float4 per 16x16 tile: largest r near, far; smallest r near
+    size_t pf_pre;          // float4 per pixel: row-major inclusive row prefix of the near records
     size_t pf;              // sum of the post-filter regions (laid out in this order)
     size_t pf_off;          // where the post-filter regions start: after the mask and trace regions, so
                             // the post-filter can run concurrently with them

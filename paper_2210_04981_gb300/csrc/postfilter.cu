@@ -85,14 +85,15 @@ struct PrepArgs {
     float* zq;      // view depth
     float4* nrec;   // (c w/a, w/a), near layer
     float4* frec;   // (c (1-w)/a, (1-w)/a), far layer
-    float2* tmax;   // per tile: (max r feeding near, max r feeding far)
+    float4* tmax;   // per tile: (max r feeding near, max r feeding far, min r feeding near (+inf: none), 0)
 };
 
 template <class ND, class COL>
 __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx, int by) {
     const int W = a.W, H = a.H;
     int i = bx * TP + (threadIdx.x & 15), j = by * TP + (threadIdx.x >> 4);
-    float rn = -1.f, rf = -1.f;
+    const float INF = __int_as_float(0x7f800000);
+    float rn = -1.f, rf = -1.f, rnmin = INF;
     if (i < W && j < H) {
         size_t q = (size_t)j * W + i;
         float z = ldz(a.nd + q);
@@ -109,23 +110,73 @@ __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx,
         a.frec[qs] = make_float4(col.x * af, col.y * af, col.z * af, af);
         rn = wn > 0.f ? r : -1.f;
         rf = wn < 1.f ? r : -1.f;
+        rnmin = wn > 0.f ? r : INF;
     }
     for (int o = 16; o; o >>= 1) {
         rn = fmaxf(rn, __shfl_xor_sync(0xffffffffu, rn, o));
         rf = fmaxf(rf, __shfl_xor_sync(0xffffffffu, rf, o));
+        rnmin = fminf(rnmin, __shfl_xor_sync(0xffffffffu, rnmin, o));
     }
-    __shared__ float2 red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(rn, rf);
+    __shared__ float4 red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float4(rn, rf, rnmin, 0.f);
     __syncthreads();
     if (threadIdx.x == 0) {
-        float2 m = red[0];
-        for (int k = 1; k < 8; ++k) m = make_float2(fmaxf(m.x, red[k].x), fmaxf(m.y, red[k].y));
+        float4 m = red[0];
+        for (int k = 1; k < 8; ++k)
+            m = make_float4(fmaxf(m.x, red[k].x), fmaxf(m.y, red[k].y), fminf(m.z, red[k].z), 0.f);
         a.tmax[by * a.ntx + bx] = m;
     }
 }
 
 template <class ND, class COL>
 __global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND, COL> a) { pf_prep_body(a, blockIdx.x, blockIdx.y); }
+
+// Row prefix of the near records: pre[y][x] = sum over x' <= x of the near
+// record of pixel (x', y), row-major.  The gather sums a pixel's interior
+// taps (all of weight exactly 1) as differences of it.  One block per row,
+// in rounds of 256 consecutive pixels (a block scan per round plus the
+// running total): the summation order is fixed.
+struct RowScanArgs {
+    const float4* nrec;  // split by pixel-index parity
+    int W, H;
+    float4* pre;
+};
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ void pf_rowscan_body(const RowScanArgs& a, int y) {
+    const int W = a.W, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const size_t half = ((size_t)W * a.H + 1) >> 1, row = (size_t)y * W;
+    __shared__ float4 s_warp[8];
+    float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int x0 = 0; x0 < W; x0 += 256) {
+        const int x = x0 + t;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (x < W) {
+            const size_t q = row + x;
+            v = __ldg(&a.nrec[(q >> 1) + (q & 1) * half]);
+        }
+        // inclusive warp scan, then the warps' totals
+        for (int o = 1; o < 32; o <<= 1) {
+            const float4 u = make_float4(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o),
+                                         __shfl_up_sync(0xffffffffu, v.z, o), __shfl_up_sync(0xffffffffu, v.w, o));
+            if (lane >= o) v = add4(v, u);
+        }
+        if (lane == 31) s_warp[w] = v;
+        __syncthreads();
+        float4 before = carry;
+        for (int k = 0; k < w; ++k) before = add4(before, s_warp[k]);
+        if (x < W) a.pre[row + x] = add4(before, v);
+        float4 total = carry;
+        for (int k = 0; k < 8; ++k) total = add4(total, s_warp[k]);
+        carry = total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pf_rowscan(RowScanArgs a) { pf_rowscan_body(a, blockIdx.x); }
 
 // Per target pixel: a layer's sums (S.x, S.y) and (S.z, W) as register
 // pairs so one packed FMA updates two of them; the far layer also holds its
@@ -181,7 +232,8 @@ struct GatherArgs {
     const float4* nrec;
     const float4* frec;
     const COL* col;  // sharp colour (empty far layer)
-    const float2* tmax;
+    const float4* tmax;
+    const float4* pre;  // row prefix of the near records
     int W, H, ntx, nty, kt;
     float kz_rel;
     float4* pp;
@@ -189,93 +241,153 @@ struct GatherArgs {
 };
 
 // one source into one target pixel, branch-free: s = clamp(r_q + 1/2 - d, 0, 1)
-// (zero outside the disk, and zero layer records, add exact zeros)
-__device__ __forceinline__ void acc(NearAcc& a, float d, float rh, float, const float4& n) {
-    const float s = __saturatef(rh - d);
+// (zero outside the disk, and zero layer records, add exact zeros); `in`
+// false: the tap lies in the pixel's interior, already summed (weight 0 here)
+__device__ __forceinline__ void acc(NearAcc& a, float d, float rh, float, const float4& n, bool in) {
+    const float s = in ? __saturatef(rh - d) : 0.f;
     a.xy = fma2(s, n.x, n.y, a.xy);
     a.zw = fma2(s, n.z, n.w, a.zw);
 }
-__device__ __forceinline__ void acc(FarAcc& a, float d, float rh, float zq, const float4& f) {
+__device__ __forceinline__ void acc(FarAcc& a, float d, float rh, float zq, const float4& f, bool) {
     const float t = __saturatef(rh - d) * __saturatef(fmaf(-zq, a.kb, a.ka));
     a.xy = fma2(t, f.x, f.y, a.xy);
     a.zw = fma2(t, f.z, f.w, a.zw);
 }
 
-// one (source, thread) tap: the thread's left pixels get fresh distances,
+// One (source, thread) tap: the thread's left pixels get fresh distances,
 // its right pixels the left pixels' distances of the previous tap (the same
-// offsets, so the same floats), carried in c
-template <class A>
-__device__ __forceinline__ void pf_tap(A (&a)[PF_NPX], float (&c)[PF_RY], const float (&dyk)[PF_RY], float dx,
-                                       float r, float z, const float4& e) {
+// offsets, so the same floats), carried in c (and the squared column offset
+// in pdx2).  MASK: a pixel takes the tap only if its column offset exceeds
+// its interior half-width for that row (squared: win2).
+template <bool MASK, class A>
+__device__ __forceinline__ void pf_tap(A (&a)[PF_NPX], float (&c)[PF_RY], float& pdx2, const float (&dyk)[PF_RY],
+                                       const float (&win2)[PF_RY], float dx, float r, float z, const float4& e) {
     const float dx2 = dx * dx;
 #pragma unroll
     for (int k = 0; k < PF_RY; ++k) {
         const float d0 = sqrt_approx(dx2 + dyk[k]);
-        acc(a[2 * k], d0, r, z, e);
-        acc(a[2 * k + 1], c[k], r, z, e);
+        acc(a[2 * k], d0, r, z, e, !MASK || dx2 > win2[k]);
+        acc(a[2 * k + 1], c[k], r, z, e, !MASK || pdx2 > win2[k]);
         c[k] = d0;
     }
+    pdx2 = dx2;
 }
 
-// one layer's loop over a disk-shaped window of radius R around the 2x2
-// block at (i, j): every source feeding the layer within reach has
-// r + 1/2 <= R, so only taps closer than R to one of the four pixels can
-// weigh; per source row, the columns of that disk (squared distances are
-// exact integers in float).  Records are split by the parity of the pixel
-// index (even pixels first), so at each tap the threads of a row, two
-// columns apart, read consecutive records; taps go in pairs (even, odd
-// index) with one float2 load of r + 1/2 (and z) per pair.
-template <bool NEAR, class A>
-__device__ __forceinline__ void pf_layer(A (&a)[PF_NPX], float R, int i, int j, int W, int H,
-                                         const float* __restrict__ rh, const float* __restrict__ zq,
-                                         const float4* __restrict__ rec) {
-    if (R < 0.f) return;  // nothing within reach feeds this layer
-    // bounds lean outwards by 1e-3 pixel (float rounding); taps they add weigh 0
-    const int G = (int)floorf(R + 1e-3f);
-    const size_t half = ((size_t)W * H + 1) >> 1;
+// The taps of source row y from column xs to xe (inclusive) for the 2 x RY
+// block at (i, j).  Records are split by the parity of the pixel index (even
+// pixels first), so at each tap the threads of a row, two columns apart,
+// read consecutive records; taps go in pairs (even, odd index) with one
+// float2 load of r + 1/2 (and z) per pair.
+template <bool NEAR, bool MASK, class A>
+__device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF_RY], const float (&win2)[PF_RY],
+                                           int xs, int xe, int i, int y, int W, size_t half,
+                                           const float* __restrict__ rh, const float* __restrict__ zq,
+                                           const float4* __restrict__ rec) {
     const float4* __restrict__ rec_e = rec;
     const float4* __restrict__ rec_o = rec + half;
     const float2* __restrict__ rh2 = reinterpret_cast<const float2*>(rh);
     const float2* __restrict__ zq2 = reinterpret_cast<const float2*>(zq);
+    float dx = (float)(xs - i);
+    float c[PF_RY], pdx2 = (dx - 1.f) * (dx - 1.f);
+#pragma unroll
+    for (int k = 0; k < PF_RY; ++k) c[k] = sqrt_approx(pdx2 + dyk[k]);
+    size_t g = (size_t)y * W + xs;  // pixel index of the next tap
+    const size_t gend = (size_t)y * W + xe + 1;
+    if (g & 1) {  // an odd first tap on its own
+        const float z = NEAR ? 0.f : __ldg(&zq[g]);
+        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[g]), z, __ldg(&rec_o[g >> 1]));
+        ++g;
+        dx += 1.f;
+    }
+    size_t m = g >> 1;
+    const size_t mend = gend >> 1;  // pairs (2m, 2m + 1) with 2m + 1 < gend
+#pragma unroll PF_UNROLL
+    for (; m < mend; ++m, dx += 2.f) {
+        const float2 r2 = __ldg(&rh2[m]);
+        const float4 e0 = __ldg(&rec_e[m]), e1 = __ldg(&rec_o[m]);
+        const float2 z2 = NEAR ? make_float2(0.f, 0.f) : __ldg(&zq2[m]);
+        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, r2.x, z2.x, e0);
+        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx + 1.f, r2.y, z2.y, e1);
+    }
+    if (gend & 1) {  // an even last tap on its own
+        const size_t gl = gend - 1;
+        const float z = NEAR ? 0.f : __ldg(&zq[gl]);
+        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[gl]), z, __ldg(&rec_e[gl >> 1]));
+    }
+}
+
+// One layer's loop over a disk-shaped window of radius R around the 2x2
+// block at (i, j): every source feeding the layer within reach has
+// r + 1/2 <= R, so only taps closer than R to one of the four pixels can
+// weigh; per source row, the columns of that disk (squared distances are
+// exact integers in float).
+// Near layer with Rin >= 0: every source that feeds the near layer and lies
+// within Rin of the block has r - 1/2 >= Rin, so a tap closer than Rin
+// weighs exactly 1.  Per row, a pixel's taps within its interior half-width
+// floor(sqrt(Rin^2 - dy^2)) are summed from the row prefix `pre` (two
+// loads); the columns inside every pixel's interior are skipped, the rest
+// are tapped with that interior masked out.
+template <bool NEAR, class A>
+__device__ __forceinline__ void pf_layer(A (&a)[PF_NPX], float R, float Rin, int i, int j, int W, int H,
+                                         const float* __restrict__ rh, const float* __restrict__ zq,
+                                         const float4* __restrict__ rec, const float4* __restrict__ pre) {
+    if (R < 0.f) return;  // nothing within reach feeds this layer
+    // bounds lean outwards by 1e-3 pixel (float rounding); taps they add weigh 0
+    const int G = (int)floorf(R + 1e-3f);
+    const size_t half = ((size_t)W * H + 1) >> 1;
     const int y0 = max(j - G, 0), y1 = min(j + PF_RY - 1 + G, H - 1);
-    const float R2 = R * R;
+    const float R2 = R * R, Rin2 = Rin * Rin;
     for (int y = y0; y <= y1; ++y) {
         const float dy = (float)(y - j);
-        float dyk[PF_RY], c[PF_RY];
+        float dyk[PF_RY], win2[PF_RY];
 #pragma unroll
         for (int k = 0; k < PF_RY; ++k) dyk[k] = (dy - (float)k) * (dy - (float)k);
         // nearest of the thread's rows to this source row
         const float dmin = dy >= 0.f && dy <= (float)(PF_RY - 1) ? 0.f : fminf(dyk[0], dyk[PF_RY - 1]);
         const int w = (int)floorf(sqrtf(fmaxf(R2 - dmin, 0.f)) + 1e-3f);
         const int x0 = max(i - w, 0), x1 = min(i + 1 + w, W - 1);
-        float dx = (float)(x0 - i);
-        {
-            const float dm = (dx - 1.f) * (dx - 1.f);
 #pragma unroll
-            for (int k = 0; k < PF_RY; ++k) c[k] = sqrt_approx(dm + dyk[k]);
+        for (int k = 0; k < PF_RY; ++k) win2[k] = -1.f;
+        int wmin = -1;        // interior half-width common to the thread's rows (-1: none)
+        bool masked = false;  // some row of the thread has an interior
+        if (NEAR && Rin >= 0.f) {
+            const float4* prow = pre + (size_t)y * W;
+            wmin = 1 << 30;
+#pragma unroll
+            for (int k = 0; k < PF_RY; ++k) {
+                // inward: no outward lean here (Rin already has its margin)
+                const int wi = dyk[k] <= Rin2 ? (int)floorf(sqrtf(Rin2 - dyk[k])) : -1;
+                win2[k] = wi >= 0 ? (float)(wi * wi) : -1.f;
+                wmin = min(wmin, wi);
+                if (wi >= 0) {
+                    masked = true;
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int xa = i + b;
+                        if (xa < W) {
+                            const int lo = max(xa - wi, 0), hi = min(xa + wi, W - 1);
+                            float4 sum = __ldg(&prow[hi]);
+                            if (lo > 0) {
+                                const float4 l = __ldg(&prow[lo - 1]);
+                                sum = make_float4(sum.x - l.x, sum.y - l.y, sum.z - l.z, sum.w - l.w);
+                            }
+                            A& t = a[2 * k + b];
+                            t.xy = make_float2(t.xy.x + sum.x, t.xy.y + sum.y);
+                            t.zw = make_float2(t.zw.x + sum.z, t.zw.y + sum.w);
+                        }
+                    }
+                }
+            }
         }
-        size_t g = (size_t)y * W + x0;  // pixel index of the next tap
-        const size_t gend = (size_t)y * W + x1 + 1;
-        if (g & 1) {  // an odd first tap on its own
-            const float z = NEAR ? 0.f : __ldg(&zq[g]);
-            pf_tap(a, c, dyk, dx, __ldg(&rh[g]), z, __ldg(&rec_o[g >> 1]));
-            ++g;
-            dx += 1.f;
-        }
-        size_t m = g >> 1;
-        const size_t mend = gend >> 1;  // pairs (2m, 2m + 1) with 2m + 1 < gend
-#pragma unroll PF_UNROLL
-        for (; m < mend; ++m, dx += 2.f) {
-            const float2 r2 = __ldg(&rh2[m]);
-            const float4 e0 = __ldg(&rec_e[m]), e1 = __ldg(&rec_o[m]);
-            const float2 z2 = NEAR ? make_float2(0.f, 0.f) : __ldg(&zq2[m]);
-            pf_tap(a, c, dyk, dx, r2.x, z2.x, e0);
-            pf_tap(a, c, dyk, dx + 1.f, r2.y, z2.y, e1);
-        }
-        if (gend & 1) {  // an even last tap on its own
-            const size_t gl = gend - 1;
-            const float z = NEAR ? 0.f : __ldg(&zq[gl]);
-            pf_tap(a, c, dyk, dx, __ldg(&rh[gl]), z, __ldg(&rec_e[gl >> 1]));
+        if (wmin >= 1) {
+            // columns [i + 1 - wmin, i + wmin] lie in every pixel's interior
+            const int ls = min(x1, i - wmin), rs = max(x0, i + wmin + 1);
+            if (x0 <= ls) pf_segment<NEAR, true>(a, dyk, win2, x0, ls, i, y, W, half, rh, zq, rec);
+            if (rs <= x1) pf_segment<NEAR, true>(a, dyk, win2, rs, x1, i, y, W, half, rh, zq, rec);
+        } else if (masked) {
+            pf_segment<NEAR, true>(a, dyk, win2, x0, x1, i, y, W, half, rh, zq, rec);
+        } else {
+            pf_segment<NEAR, false>(a, dyk, win2, x0, x1, i, y, W, half, rh, zq, rec);
         }
     }
 }
@@ -285,19 +397,21 @@ __device__ __forceinline__ void pf_layer(A (&a)[PF_NPX], float R, int i, int j, 
 template <class COL>
 __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx, int ty) {
     const COL* __restrict__ col = ar.col;
-    const float2* __restrict__ tmax = ar.tmax;
+    const float4* __restrict__ tmax = ar.tmax;
     const int W = ar.W, H = ar.H, ntx = ar.ntx, nty = ar.nty, kt = ar.kt;
+    const int nk = (2 * kt + 1) * (2 * kt + 1);
     float4* __restrict__ pp = ar.pp;
     float4* __restrict__ aux = ar.aux;
-    __shared__ int s_win[2];
+    __shared__ int s_win[3];
     if (threadIdx.x < 2) s_win[threadIdx.x] = -1;
+    if (threadIdx.x == 2) s_win[2] = 0x7f800000;  // +inf
     __syncthreads();
     // per layer: largest r + 1/2 over tiles whose feeding pixels can reach this tile
-    for (int k = threadIdx.x; k < (2 * kt + 1) * (2 * kt + 1); k += blockDim.x) {
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
         int ox = k % (2 * kt + 1) - kt, oy = k / (2 * kt + 1) - kt;
         int x = tx + ox, y = ty + oy;
         if (x < 0 || y < 0 || x >= ntx || y >= nty) continue;
-        const float2 r = __ldg(&tmax[y * ntx + x]);
+        const float4 r = __ldg(&tmax[y * ntx + x]);
         // pixel gap between the two tiles along each axis
         const float gx = ox == 0 ? 0.f : (float)((abs(ox) - 1) * TP + 1);
         const float gy = oy == 0 ? 0.f : (float)((abs(oy) - 1) * TP + 1);
@@ -310,6 +424,29 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
     // the layer's reach R (-1: none); a source weighs only closer than R
     const float Gn = s_win[0] < 0 ? -1.f : __int_as_float(s_win[0]);
     const float Gf = s_win[1] < 0 ? -1.f : __int_as_float(s_win[1]);
+    // Near interior radius of the tile: a near source q at distance d weighs
+    // exactly 1 if d <= r_q - 1/2, so Rin may grow while every tile T that
+    // feeds the near layer and lies closer than Rin to this one has
+    // r_min(T) - 1/2 >= Rin: Rin = min over T of max(r_min(T) - 1/2, gap(T)),
+    // less a margin, at most Gn.  The interior path (two prefix loads per
+    // pixel and row, masked taps around it) pays only when the interior is
+    // most of the window: below Rin = Gn / 2 the plain loop runs.
+    if (Gn >= 0.f) {
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            int ox = k % (2 * kt + 1) - kt, oy = k / (2 * kt + 1) - kt;
+            int x = tx + ox, y = ty + oy;
+            if (x < 0 || y < 0 || x >= ntx || y >= nty) continue;
+            const float4 r = __ldg(&tmax[y * ntx + x]);
+            if (r.x < 0.f) continue;  // feeds no near layer
+            const float gx = ox == 0 ? 0.f : (float)((abs(ox) - 1) * TP + 1);
+            const float gy = oy == 0 ? 0.f : (float)((abs(oy) - 1) * TP + 1);
+            const float lim = fmaxf(fmaxf(r.z - 0.5f, sqrtf(gx * gx + gy * gy) - 1e-3f), 0.f);
+            atomicMin(&s_win[2], __float_as_int(lim));  // non-negative floats order as their bits
+        }
+        __syncthreads();
+    }
+    float Rin = Gn >= 0.f ? fminf(__int_as_float(s_win[2]), Gn) - 1e-3f : -1.f;
+    if (Rin < 0.5f * Gn) Rin = -1.f;
     const int i = tx * TP + 2 * (threadIdx.x & 7), j = ty * TP + PF_RY * (threadIdx.x >> 3);
     if (i >= W || j >= H) return;
     // far layer first; its sums wait in the pixels' own pp slots (each pixel
@@ -326,7 +463,7 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
             f[k].kb = 1.f / (ar.kz_rel * zp);
             f[k].xy = f[k].zw = make_float2(0.f, 0.f);
         }
-        pf_layer<false>(f, Gf, i, j, W, H, ar.rh, ar.zq, ar.frec);
+        pf_layer<false>(f, Gf, -1.f, i, j, W, H, ar.rh, ar.zq, ar.frec, nullptr);
 #pragma unroll
         for (int k = 0; k < PF_NPX; ++k) {
             const int x = i + (k & 1), y = j + (k >> 1);
@@ -336,7 +473,7 @@ __device__ __forceinline__ void pf_gather_body(const GatherArgs<COL>& ar, int tx
     NearAcc a[PF_NPX];
 #pragma unroll
     for (int k = 0; k < PF_NPX; ++k) a[k].xy = a[k].zw = make_float2(0.f, 0.f);
-    pf_layer<true>(a, Gn, i, j, W, H, ar.rh, ar.zq, ar.nrec);
+    pf_layer<true>(a, Gn, Rin, i, j, W, H, ar.rh, ar.zq, ar.nrec, ar.pre);
 #pragma unroll
     for (int k = 0; k < PF_NPX; ++k) {
         const int x = i + (k & 1), y = j + (k >> 1);
@@ -354,6 +491,11 @@ __global__ void __launch_bounds__(GATHER_THREADS, HDOF_PF_MINB) k_pf_gather(Gath
 }
 
 using PrepF32 = PrepArgs<float4, float4>;
+__global__ void __launch_bounds__(256) k_pf_rowscan_batch(const RowScanArgs* __restrict__ a, BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    pf_rowscan_body(batch_record(a, v), by);
+}
 __global__ void __launch_bounds__(256) k_pf_prep_batch(const PrepF32* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
@@ -490,17 +632,21 @@ int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p,
         k_pf_prep<<<grid, 256, 0, s>>>(
             PrepArgs<half4s, bf164s>{ndh, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
     HDOF_LAUNCHED("post-filter prep");
+    k_pf_rowscan<<<H, 256, 0, s>>>(RowScanArgs{w.nrec, W, H, w.pre});
+    HDOF_LAUNCHED("post-filter row prefix");
     const int kt = gather_tiles(p->r_max);
     float4* out = reinterpret_cast<float4*>(pp);
     // the taps are served from L1: a small shared-memory carve-out
     if (f32c) {
         cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
         k_pf_gather<float4><<<grid, GATHER_THREADS, 0, s>>>(
-            GatherArgs<float4>{w.rh, w.zq, w.nrec, w.frec, col4, w.tmax, W, H, ntx, nty, kt, p->kz_rel, out, aux});
+            GatherArgs<float4>{w.rh, w.zq, w.nrec, w.frec, col4, w.tmax, w.pre, W, H, ntx, nty, kt, p->kz_rel, out,
+                               aux});
     } else {
         cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
         k_pf_gather<bf164s><<<grid, GATHER_THREADS, 0, s>>>(
-            GatherArgs<bf164s>{w.rh, w.zq, w.nrec, w.frec, colb, w.tmax, W, H, ntx, nty, kt, p->kz_rel, out, aux});
+            GatherArgs<bf164s>{w.rh, w.zq, w.nrec, w.frec, colb, w.tmax, w.pre, W, H, ntx, nty, kt, p->kz_rel, out,
+                               aux});
     }
     HDOF_LAUNCHED("post-filter gather");
     return HDOF_OK;
@@ -540,12 +686,23 @@ void pf_prep_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_
     k_pf_prep_batch<<<blocks, 256, 0, s>>>(static_cast<const PrepF32*>(args), g);
 }
 
+size_t pf_rowscan_args_size() { return sizeof(RowScanArgs); }
+void pf_rowscan_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
+    *reinterpret_cast<RowScanArgs*>(dst) = RowScanArgs{w.nrec, v.cam.width, v.cam.height, w.pre};
+    *gx = 1;  // one block per row
+    *gy = v.cam.height;
+}
+void pf_rowscan_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    k_pf_rowscan_batch<<<blocks, 256, 0, s>>>(static_cast<const RowScanArgs*>(args), g);
+}
+
 size_t pf_gather_args_size() { return sizeof(GatherArgs<float4>); }
 void pf_gather_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
     const int W = v.cam.width, H = v.cam.height, ntx = (W + TP - 1) / TP, nty = (H + TP - 1) / TP;
     *reinterpret_cast<GatherArgs<float4>*>(dst) =
-        GatherArgs<float4>{w.rh, w.zq, w.nrec, w.frec, static_cast<const float4*>(v.g.col), w.tmax, W, H, ntx, nty,
-                           gather_tiles(v.params.r_max), v.params.kz_rel, reinterpret_cast<float4*>(v.pp), nullptr};
+        GatherArgs<float4>{w.rh, w.zq, w.nrec, w.frec, static_cast<const float4*>(v.g.col), w.tmax, w.pre, W, H, ntx,
+                           nty, gather_tiles(v.params.r_max), v.params.kz_rel, reinterpret_cast<float4*>(v.pp),
+                           nullptr};
     *gx = ntx;
     *gy = nty;
     cudaFuncSetAttribute(k_pf_gather_batch, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
