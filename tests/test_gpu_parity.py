@@ -389,6 +389,34 @@ def test_postfilter(orc, seed, W, Hh, rmax, A):
     assert frac_close(got, ref, 1e-4) == 1.0, report("pp", got, ref)
 
 
+@pytest.mark.parametrize("tilt,far_block", [(0.0, False), (0.004, True)])
+def test_postfilter_interior_prefix(orc, tilt, far_block):
+    """A smooth near field with radii around 20 px: most of each window lies
+    inside every nearby source's disk, so the gather sums those taps from row
+    prefixes; the result matches the oracle's tap-by-tap sums (a far block
+    adds tiles where the plain loop runs next to interior tiles)."""
+    W, Hh = 160, 120
+    rng = np.random.default_rng(11)
+    yy, xx = np.mgrid[0:Hh, 0:W].astype(np.float64)
+    nd = np.zeros((Hh, W, 4))
+    nd[..., 2] = -1.0
+    nd[..., 3] = 0.8 + tilt * xx
+    if far_block:
+        nd[40:80, 100:140, 3] = 6.0
+    col = np.zeros((Hh, W, 4))
+    col[..., :3] = rng.uniform(0.2, 0.9, (Hh, W, 3))
+    nd, col = nd.astype(np.float32), col.astype(np.float32)
+    cam = hi.Camera(width=W, height=Hh).f32()
+    lens = hi.Lens(3.0, 0.2, 0.05).f32()
+    p = hi.Params(r_max=32.0)
+    pp = torch.empty((Hh, W, 4), dtype=torch.float32, device="cuda")
+    H.hdof_postfilter(gbuf_from(nd, col), cam, lens, p, pp, workspace(W, Hh, p))
+    H.hdof_sync()
+    ref = orc.postfilter(nd.astype(np.float64), col.astype(np.float64), lens, cam.tan_half_fovy, p)
+    got = host(pp)
+    assert frac_close(got, ref, 1e-4) == 1.0, report("pp", got, ref)
+
+
 # -------------------------------------------------------- reconstruction ----
 
 def _reconstruct_inputs(W, Hh, seed):
