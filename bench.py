@@ -54,7 +54,7 @@ PF_FLOPS_PER_TAP = 12
 # launch) of the current kernels on the 1080p room frame with f32 storage;
 # other workloads report null
 MEASURED_TRAFFIC = {("room", "f32", "trace"): 53.13e6,      # k_count k_scan k_scatter k_trace_packets k_resolve
-                    ("room", "f32", "postfilter"): None}  # k_pf_prep k_pf_rowscan k_pf_gather
+                    ("room", "f32", "postfilter"): 251.66e6}  # k_pf_prep k_pf_rowscan k_pf_gather
 
 
 def peaks():
@@ -181,6 +181,70 @@ def contributing_taps(z, lens, Hh, t, r_max):
     return int(np.searchsorted(d, r.ravel() + 0.5, side="left").sum())
 
 
+def gather_work(z, lens, Hh, t, r_max):
+    """Work the near-layer post-filter gather executes on depth plane z, by
+    the kernel's own window rules: per 16x16 tile the reach R (largest r +
+    1/2 of the tiles that reach it) and the interior radius R_in (smallest
+    max(r_min(T) - 1/2, gap(T)) over the tiles that feed the near layer, used
+    when >= R/2); per 2x2-pixel thread and source row, the columns it taps
+    (interior columns of all four pixels skipped) and its prefix lookups (two
+    per pixel row with an interior).  Returns (tap iterations, each of four
+    pixel-taps, prefix lookups)."""
+    H, W = z.shape
+    c = lens.aperture_radius * Hh * (lens.focus_dist - z) / (z * lens.focus_dist * t)
+    r = np.minimum(np.abs(c) * 0.5, r_max)
+    wn = np.clip((c + math.sqrt(2.0)) / (2.0 * math.sqrt(2.0)), 0.0, 1.0)
+    TP = 16
+    ntx, nty = (W + TP - 1) // TP, (H + TP - 1) // TP
+
+    def tiles(a, fill, red):
+        a = np.pad(a, ((0, nty * TP - H), (0, ntx * TP - W)), constant_values=fill)
+        return red(a.reshape(nty, TP, ntx, TP), axis=(1, 3))
+
+    tmax = tiles(np.where(wn > 0, r, -1.0), -1.0, np.max)
+    tmin = tiles(np.where(wn > 0, r, np.inf), np.inf, np.min)
+    kt = math.ceil((r_max + 0.5) / TP) + 1
+    offs = np.arange(-kt, kt + 1)
+    gap = np.where(offs == 0, 0.0, (np.abs(offs) - 1) * TP + 1.0)
+    th = np.arange(64)
+    taps = pre = 0
+    for ty in range(nty):
+        for tx in range(ntx):
+            vy, vx = (ty + offs >= 0) & (ty + offs < nty), (tx + offs >= 0) & (tx + offs < ntx)
+            sub = tmax[np.ix_(ty + offs[vy], tx + offs[vx])]
+            subm = tmin[np.ix_(ty + offs[vy], tx + offs[vx])]
+            g2 = gap[vy][:, None] ** 2 + gap[vx][None, :] ** 2
+            reach = (sub >= 0) & (g2 < (sub + 0.5) ** 2)
+            if not reach.any():
+                continue
+            R = float((sub + 0.5)[reach].max())
+            lim = np.maximum(np.maximum(subm - 0.5, np.sqrt(g2) - 1e-3), 0.0)[sub >= 0]
+            Rin = min(float(lim.min()), R) - 1e-3
+            if Rin < 0.5 * R:
+                Rin = -1.0
+            G = math.floor(R + 1e-3)
+            i, j = tx * TP + 2 * (th & 7), ty * TP + 2 * (th >> 3)
+            ok = (i < W) & (j < H)
+            i, j = i[ok][:, None], j[ok][:, None]
+            dy = np.arange(-G, G + 2, dtype=np.float64)[None, :]
+            rows = (j + dy >= 0) & (j + dy < H)
+            d0, d1 = dy ** 2, (dy - 1) ** 2
+            dmin = np.where((dy >= 0) & (dy <= 1), 0.0, np.minimum(d0, d1))
+            w = np.floor(np.sqrt(np.maximum(R * R - dmin, 0.0)) + 1e-3).astype(np.int64)
+            x0, x1 = np.maximum(i - w, 0), np.minimum(i + 1 + w, W - 1)
+            span = x1 - x0 + 1
+            if Rin >= 0:
+                R2 = Rin * Rin
+                w0 = np.where(d0 <= R2, np.floor(np.sqrt(np.maximum(R2 - d0, 0.0))), -1).astype(np.int64)
+                w1 = np.where(d1 <= R2, np.floor(np.sqrt(np.maximum(R2 - d1, 0.0))), -1).astype(np.int64)
+                wm = np.minimum(w0, w1)
+                ls, rs = np.minimum(x1, i - wm), np.maximum(x0, i + wm + 1)
+                span = np.where(wm >= 1, np.maximum(ls - x0 + 1, 0) + np.maximum(x1 - rs + 1, 0), span)
+                pre += int((((w0 >= 0).astype(np.int64) + (w1 >= 0)) * 2 * rows).sum())
+            taps += int((span * rows).sum())
+    return taps, pre
+
+
 def run_ours(args):
     import torch
 
@@ -285,18 +349,24 @@ def run_ours(args):
         gbs = ab[n] / (mean_stage[i] * 1e-3) / 1e9
         per_stage[n] = {"ms": round(float(mean_stage[i]), 4), "alg_bytes": int(ab[n]),
                         "alg_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3)}
-    # post-filter gather as arithmetic: contributing taps x PF_FLOPS_PER_TAP FP32 ops
+    # post-filter gather as arithmetic: the taps it executes (each pixel-tap
+    # PF_FLOPS_PER_TAP FP32 ops) and its interior prefix lookups (float4
+    # difference + accumulation: 8 ops); contributing taps for reference
     z = r.g.nd[..., 3].float().cpu().numpy().astype(np.float64)
     taps = contributing_taps(z, lens, Hh, cams[0].tan_half_fovy, p0.r_max)
     fp32_peak = FP32_LANES * 2 * (clocks["sm_mhz"] or sm_med) * 1e6 / 1e12
     pf_ms = float(mean_stage[stages.index("postfilter")])
-    per_stage["postfilter"]["contributing_taps"] = taps
-    per_stage["postfilter"]["alg_TFLOPs"] = round(taps * PF_FLOPS_PER_TAP / (pf_ms * 1e-3) / 1e12, 2)
     dom = stages[int(np.argmax(mean_stage))]
+    per_stage["postfilter"]["contributing_taps"] = taps
     if dom == "postfilter":
-        ach = taps * PF_FLOPS_PER_TAP / (pf_ms * 1e-3) / 1e12
+        tap_it, lookups = gather_work(z, lens, Hh, cams[0].tan_half_fovy, p0.r_max)
+        flops = 4 * tap_it * PF_FLOPS_PER_TAP + 8 * lookups
+        ach = flops / (pf_ms * 1e-3) / 1e12
+        per_stage["postfilter"].update(executed_pixel_taps=4 * tap_it, prefix_lookups=lookups,
+                                       executed_TFLOPs=round(ach, 2))
         roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                 "frac": round(ach / fp32_peak, 3), "kernel": "postfilter (k_pf_prep + k_pf_rowscan + k_pf_gather)",
+                "flops_per_frame": int(flops),
                 "traffic": MEASURED_TRAFFIC.get((args.scene, "mixed" if mixed else "f32", "postfilter")),
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock under load"}
     elif dom == "trace":
