@@ -38,7 +38,7 @@ constexpr int PF_RY = HDOF_PF_RY;
 constexpr int PF_NPX = 2 * PF_RY;
 constexpr int GATHER_THREADS = 8 * (16 / PF_RY);
 #ifndef HDOF_PF_MINB
-#define HDOF_PF_MINB 12  // resident gather blocks per SM the register budget targets
+#define HDOF_PF_MINB 16  // resident gather blocks per SM the register budget targets
 #endif
 #ifndef HDOF_PF_UNROLL
 #define HDOF_PF_UNROLL 4  // unroll of the gather's tap-pair loop
@@ -47,8 +47,12 @@ constexpr int PF_UNROLL = HDOF_PF_UNROLL;
 // Shared-memory carve-out (percent of the maximum) for the gather: the taps
 // are served from L1, so keep L1 large, but every resident block also holds
 // ~1 KB of driver-reserved shared memory; 8% (a 16 KB configuration) admits
-// up to 14 blocks, where the minimum configuration (8 KB) admits only 7.
-constexpr int GATHER_CARVEOUT = 8;
+// about 14-15 blocks, where the minimum configuration (8 KB) admits only 7
+// and a 32 KB one leaves too little L1 for the taps.
+#ifndef HDOF_PF_CARVEOUT
+#define HDOF_PF_CARVEOUT 8
+#endif
+constexpr int GATHER_CARVEOUT = HDOF_PF_CARVEOUT;
 constexpr int AREA_MAX = 16384;  // breakpoints for radii up to 127.5
 
 // (x_m, a(x_m), slope on [x_m, x_{m+1}], 0)
