@@ -53,7 +53,7 @@ PF_FLOPS_PER_TAP = 12
 # stage's kernels, one ncu launch-list capture with caches flushed before each
 # launch) of the current kernels on the 1080p room frame with f32 storage;
 # other workloads report null
-MEASURED_TRAFFIC = {("room", "f32", "trace"): 53.08e6,      # k_count k_scan k_scatter k_trace_packets k_resolve
+MEASURED_TRAFFIC = {("room", "f32", "trace"): 53.15e6,      # k_count k_scan k_scatter k_trace_packets k_resolve
                     ("room", "f32", "postfilter"): 252.53e6}  # k_pf_prep k_pf_rowscan k_pf_gather
 
 
