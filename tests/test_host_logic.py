@@ -1,9 +1,12 @@
 """Host-side logic that needs no GPU: the batch autotuner's choice and cache,
-and the benchmark's multi-rank timing reduction (world size 2 over gloo)."""
+the benchmark's multi-rank timing reduction (world size 2 over gloo) and its
+model of the post-filter gather's executed work."""
+import math
 import os
 import socket
 import sys
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -78,3 +81,26 @@ def test_max_over_ranks_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.5, "cpu") == 3.5
+
+
+def test_gather_work_model():
+    """The executed-work model of the post-filter gather (the bench's roofline
+    for it): a uniform near field engages the interior prefix sums and taps far
+    fewer pixel-taps than contribute; an all-far frame gathers nothing in the
+    near layer; a near field whose radii jump from pixel to pixel (interior
+    below half the reach) falls back to tapping every column, with no lookups."""
+    import bench
+    import hdof_inputs as hi
+
+    lens = hi.Lens(3.0, 0.2, 0.05).f32()
+    t = math.tan(math.radians(30.0))
+    W, Hh = 96, 64
+    z_uniform = np.full((Hh, W), 0.8)
+    taps, pre = bench.gather_work(z_uniform, lens, Hh, t, 32.0)
+    contributing = bench.contributing_taps(z_uniform, lens, Hh, t, 32.0)
+    assert pre > 0 and 0 < 4 * taps < contributing / 2
+    z_far = np.full((Hh, W), 20.0)
+    assert bench.gather_work(z_far, lens, Hh, t, 32.0) == (0, 0)
+    z_mixed = np.where((np.arange(W)[None, :] + np.arange(Hh)[:, None]) % 2 == 0, 0.8, 2.9)
+    taps_m, pre_m = bench.gather_work(z_mixed, lens, Hh, t, 32.0)
+    assert pre_m == 0 and 4 * taps_m >= bench.contributing_taps(z_mixed, lens, Hh, t, 32.0) * 0.5
