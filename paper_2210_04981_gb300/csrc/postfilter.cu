@@ -12,13 +12,18 @@
 //
 // k_pf_prep: per pixel r + 1/2, z and the premultiplied near and far layer
 //   records (c w/a, w/a), the records split by pixel-index parity; per 16x16
-//   tile the largest r feeding each layer.
+//   tile the largest r feeding each layer and the smallest r feeding the near
+//   layer.
+// k_pf_rowscan: the row prefix of the near records (row-major).
 // k_pf_gather: near and far are gathered in two loops, each bounded per tile
 //   by the largest radius among the tiles whose pixels feed that layer and
 //   can reach it, and per source row to the columns of that disk; every tap
 //   outside has zero weight, so the bounded gathers equal the full ones.
-//   Each thread gathers a 2x2 pixel block so every tap it loads serves four
-//   pixels; the per-tap arithmetic is branch-free (saturating adds).
+//   Where every near source close to the tile has a large radius, the near
+//   taps of weight exactly 1 (the interior) are summed as differences of the
+//   row prefix and only the ring around them is tapped.  Each thread gathers
+//   a 2x2 pixel block so every tap it loads serves four pixels; the per-tap
+//   arithmetic is branch-free (saturating adds).
 #include <algorithm>
 #include <cmath>
 #include <mutex>
