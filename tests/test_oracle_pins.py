@@ -3,7 +3,7 @@
 Each test checks the oracle against something the paper, the thin-lens
 geometry or plain mathematics fixes: the closed-form CoC against a ray
 construction, the ray-traced image of a fronto-parallel plane against an
-independent disk-convolution quadrature, BVH closest hits against brute force,
+exact disk convolution (test_oracle_pins_stages.py), BVH closest hits against brute force,
 filter identities on constant and linear images, and the stage invariants.
 """
 import math
@@ -90,66 +90,6 @@ def test_project_inverts_pinhole_dir(orc):
         uv = orc.project(cam, P)
         assert abs(uv[0] - i) < 1e-9 and abs(uv[1] - j) < 1e-9
         assert abs(np.dot(d, f) - 1.0) < 1e-12
-
-
-# ------------------------------------------------------ fronto-parallel plane
-
-def _disk_average_checker(cam, z, r_px, cells, half, nr=160, nt=320):
-    """Independent quadrature: average pinhole radiance over a disk of radius
-    r_px pixels (equal-area polar nodes) for a checker plane at depth z."""
-    W, H = cam.width, cam.height
-    k = (np.arange(nr) + 0.5) / nr
-    rho = r_px * np.sqrt(k)
-    th = 2 * np.pi * (np.arange(nt) + 0.5) / nt
-    ox = (rho[:, None] * np.cos(th)[None, :]).ravel()
-    oy = (rho[:, None] * np.sin(th)[None, :]).ravel()
-    t = cam.tan_half_fovy
-    a = W / H
-    n = np.array([0, 0, -1.0])
-    ldir = np.array([0.3, 0.5, -1.0]) / np.linalg.norm([0.3, 0.5, -1.0])
-    irr = 0.05 + max(0.0, float(n @ ldir))
-    mean = np.zeros((H, W))
-    var = np.zeros((H, W))
-    for j in range(H):
-        for i in range(W):
-            sx = i + 0.5 + ox
-            sy = j + 0.5 + oy
-            X = (2 * sx / W - 1) * a * t * z
-            Y = (1 - 2 * sy / H) * t * z
-            u = (X + half) / (2 * half)
-            v = (Y + half) / (2 * half)
-            cell = np.floor(cells * u) + np.floor(cells * v)
-            L = np.where(cell % 2 == 0, 0.2, 0.8) * irr
-            mean[j, i] = L.mean()
-            var[j, i] = L.var()
-    return mean, np.sqrt(var)
-
-
-def test_fronto_plane_converges_to_disk_convolution(orc):
-    """Fact 2: the thin-lens image of a fronto-parallel Lambert plane is its
-    pinhole image convolved with a uniform disk of radius |c(z)|/2."""
-    z, zf, A = 1.0, 2.0, 0.2
-    W = H = 24
-    cam = hi.Camera(width=W, height=H).f32()
-    lens = hi.Lens(zf, A, 0.05).f32()
-    scene = hi.plane_scene(z, half=50.0, cells=400.0)
-    osc = orc.OScene(scene)
-    c = orc.coc(z, lens, H, cam.tan_half_fovy)
-    assert c > SQRT2  # whole plane in the near field
-    exp_mean, sig = _disk_average_checker(cam, z, abs(c) / 2, 400.0, 50.0)
-    p = hi.Params(spp_max=128)
-    spp = np.full((H, W), 128, np.uint8)
-    est = []
-    for fr in range(8):  # 8 independent keys x 128 spp = 1024 samples
-        rt = orc.trace(osc, cam, lens, p.replace(frame=fr), spp)
-        assert np.all(rt[..., 3] == 1.0)  # hit ratio: every ray in the near field
-        est.append(rt[..., 0])
-    est = np.array(est)
-    e1024 = np.abs(est.mean(0) - exp_mean)
-    tol = 4 * sig / math.sqrt(1024) + 2e-3
-    assert (e1024 <= tol).mean() >= 0.99
-    e128 = np.abs(est[0] - exp_mean).mean()
-    assert e1024.mean() < 0.6 * e128  # error shrinks with N (~1/sqrt(8))
 
 
 # ------------------------------------------------------ closest hit / BVH ---
