@@ -151,6 +151,34 @@ int hdof_sync(void* stream);
 /* Fills *p with the library defaults (the tiny-scene values). */
 void hdof_default_params(hdof_params* p);
 
+/* Kernel timing (not in the paper; a measurement facility).  With
+ * hdof_profile(1) every compute call records a pair of CUDA events on its
+ * stream around each of its kernels (names: "gbuffer", "mask",
+ * "trace_compact", "trace_packets" or "trace_rays", "trace_resolve",
+ * "pf_prep", "pf_rowscan", "pf_gather", "temporal", "spatial", "composite",
+ * and the batched forms with a "batch_" prefix); hdof_profile(0) stops.
+ * Do not profile while a stream is being captured into a graph.
+ * hdof_profile_read waits for the recorded events, writes up to max_out
+ * entries (one per kernel name: launches and summed device milliseconds
+ * since the previous read) and returns the number of names (or a negative
+ * HDOF_E* code); the record is cleared. */
+typedef struct hdof_kernel_time {
+    char name[32];
+    int32_t launches;
+    float total_ms;
+} hdof_kernel_time;
+int hdof_profile(int32_t on);
+int hdof_profile_read(hdof_kernel_time* out, int32_t max_out);
+
+/* FP32 arithmetic probe (not in the paper; the measured peak that the
+ * ALU-bound kernels are compared against).  Enqueues one kernel of
+ * SMs x blocks_per_sm blocks of 256 threads, each running eight independent
+ * fused multiply-add chains for iters x 16 steps; *lane_ops (host) receives
+ * the number of FMA lane-instructions it executes (blocks x 256 x iters x
+ * 128).  Time it with events on `stream`.  sink: device float [256], never
+ * written in practice (it keeps the chains from being optimised away). */
+int hdof_probe_fma(int32_t blocks_per_sm, int32_t iters, float* sink, double* lane_ops, void* stream);
+
 /* ------------------------------------------------------------ BVH -- */
 /* Builds the ray-tracing acceleration structure that stands in for the
  * paper's hardware ray-tracing acceleration (Abstract): a binary BVH built on
@@ -281,6 +309,19 @@ int hdof_trace(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* len
                const hdof_params* p, const uint8_t* spp, const int32_t* hint_tri, float* rt,
                uint32_t* stats, float* rec, uint32_t* ray_off, void* workspace,
                size_t workspace_bytes, const hdof_tuning* tune, void* stream);
+
+/* Per-ray closest hits of the thin-lens samples (Ray Trace section: each
+ * lens ray's closest hit), for checking visibility ray by ray.  Reads the
+ * hit records that the last hdof_trace call with this workspace, camera,
+ * params and spp left in the workspace (run it on the same stream, before
+ * anything else reuses the workspace).  ids: int32 written at
+ * [ray_off[p] + s] for sample s of each traced pixel p, where ray_off is the
+ * plane that hdof_trace wrote (pass rec/ray_off to it): the original
+ * triangle id, or -1 for a miss.  ts (may be NULL): float at the same index,
+ * the ray parameter of the hit along the unit direction (+inf for a miss).
+ * Both hold at least stats[1] (rays of that trace) entries. */
+int hdof_trace_hits(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_params* p, const uint8_t* spp,
+                    const void* workspace, size_t workspace_bytes, int32_t* ids, float* ts, void* stream);
 
 /* ----------------------------------------------------- post-filter -- */
 /* CoC gather post-filter of the sharp image (Design section; the rejection

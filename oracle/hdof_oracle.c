@@ -553,24 +553,37 @@ void orc_mask(int32_t W, int32_t H, const double* nd, const double* mv, const do
  * h = sum w / n (hit ratio); empty layers (weight < 1e-6) give colour 0 and
  * CoC -1.
  * ---------------------------------------------------------------------- */
-static void trace_pixel(const oscene* s, const orc_camera* cam, const orc_lens* lens,
-                        const orc_params* p, int32_t i, int32_t j, int n, double* rt) {
-    int32_t W = cam->width, H = cam->height;
-    double A = lens->aperture_radius, zf = lens->focus_dist, t = cam->tan_half_fovy;
+/* Lens sample `smp` of pixel q (Ray Trace section: rays through random
+ * points of the lens aperture, aimed at the pixel's point on the focus
+ * plane): Philox(key = (seed, view*65536 + frame), ctr = (q, smp, 0, 0)) ->
+ * u1, u2; lens point rho = A sqrt(u1), theta = 2 pi u2 in the (right, up)
+ * plane; unit direction towards the focus-plane point of the pixel's pinhole
+ * ray. */
+void orc_lens_ray(const orc_camera* cam, const orc_lens* lens, const orc_params* p, int64_t q, int32_t smp,
+                  double O[3], double dir[3]) {
+    int32_t W = cam->width, i = (int32_t)(q % W), j = (int32_t)(q / W);
+    double A = lens->aperture_radius, zf = lens->focus_dist;
     uint32_t key[2] = {p->seed, (uint32_t)p->view * 65536u + (uint32_t)p->frame};
     double d[3], Pf[3];
     orc_pinhole_dir(cam, i + 0.5 + cam->jitter[0], j + 0.5 + cam->jitter[1], d);
     for (int k = 0; k < 3; ++k) Pf[k] = cam->pos[k] + zf * d[k];
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)smp, 0u, 0u}, x[4];
+    orc_philox(ctr, key, x);
+    double rho = A * sqrt(u01(x[0])), th = 2.0 * PI_D * u01(x[1]);
+    for (int k = 0; k < 3; ++k) O[k] = cam->pos[k] + rho * cos(th) * cam->right[k] + rho * sin(th) * cam->up[k];
+    sub3(Pf, O, dir);
+    normalize3(dir);
+}
+
+static void trace_pixel(const oscene* s, const orc_camera* cam, const orc_lens* lens,
+                        const orc_params* p, int32_t i, int32_t j, int n, double* rt) {
+    int32_t W = cam->width, H = cam->height;
+    double t = cam->tan_half_fovy;
     double SwL[3] = {0, 0, 0}, SfL[3] = {0, 0, 0}, SfP[3] = {0, 0, 0};
     double Sw = 0, Sf = 0, Swc = 0, Sfc = 0;
     for (int smp = 0; smp < n; ++smp) {
-        uint32_t ctr[4] = {(uint32_t)((size_t)j * W + i), (uint32_t)smp, 0u, 0u}, x[4];
-        orc_philox(ctr, key, x);
-        double rho = A * sqrt(u01(x[0])), th = 2.0 * PI_D * u01(x[1]);
         double O[3], dir[3];
-        for (int k = 0; k < 3; ++k) O[k] = cam->pos[k] + rho * cos(th) * cam->right[k] + rho * sin(th) * cam->up[k];
-        sub3(Pf, O, dir);
-        normalize3(dir);
+        orc_lens_ray(cam, lens, p, (int64_t)j * W + i, smp, O, dir);
         double th_, bary[3], n_[3], L[3], P[3], c;
         int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
         if (id >= 0) {
@@ -930,8 +943,6 @@ void orc_trace_records(const void* sp, const orc_camera* cam, const orc_lens* le
                        const uint8_t* spp, const int64_t* off, double* rec) {
     const oscene* s = (const oscene*)sp;
     int32_t W = cam->width, H = cam->height;
-    double A = lens->aperture_radius, zf = lens->focus_dist;
-    uint32_t key[2] = {p->seed, (uint32_t)p->view * 65536u + (uint32_t)p->frame};
     (void)H;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t j = 0; j < cam->height; ++j)
@@ -939,18 +950,9 @@ void orc_trace_records(const void* sp, const orc_camera* cam, const orc_lens* le
             size_t q = (size_t)j * W + i;
             int n = spp[q];
             if (!n) continue;
-            double d[3], Pf[3];
-            orc_pinhole_dir(cam, i + 0.5 + cam->jitter[0], j + 0.5 + cam->jitter[1], d);
-            for (int k = 0; k < 3; ++k) Pf[k] = cam->pos[k] + zf * d[k];
             for (int smp = 0; smp < n; ++smp) {
-                uint32_t ctr[4] = {(uint32_t)q, (uint32_t)smp, 0u, 0u}, x[4];
-                orc_philox(ctr, key, x);
-                double rho = A * sqrt(u01(x[0])), th = 2.0 * PI_D * u01(x[1]);
                 double O[3], dir[3];
-                for (int k = 0; k < 3; ++k)
-                    O[k] = cam->pos[k] + rho * cos(th) * cam->right[k] + rho * sin(th) * cam->up[k];
-                sub3(Pf, O, dir);
-                normalize3(dir);
+                orc_lens_ray(cam, lens, p, (int64_t)q, smp, O, dir);
                 double th_, bary[3], n_[3], L[3], P[3], z;
                 int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
                 if (id >= 0) {
@@ -965,6 +967,46 @@ void orc_trace_records(const void* sp, const orc_camera* cam, const orc_lens* le
                 }
                 double* r = rec + 4 * (size_t)(off[q] + smp);
                 r[0] = L[0]; r[1] = L[1]; r[2] = L[2]; r[3] = z;
+            }
+        }
+}
+
+/* Closest hit of every thin-lens sample (the visibility the trace shades):
+ * for sample s of pixel q, ids[off[q] + s] = hit triangle (-1 = miss),
+ * ts[...] = ray parameter along the unit direction, margin[...] = distance
+ * of the hit point from the nearest edge of its triangle (world units,
+ * +inf for a miss): a small margin marks a hit a slightly different ray can
+ * miss (an epsilon-tie of the closest-hit decision). */
+void orc_trace_hits(const void* sp, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
+                    const uint8_t* spp, const int64_t* off, int32_t* ids, double* ts, double* margin) {
+    const oscene* s = (const oscene*)sp;
+    int32_t W = cam->width;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t j = 0; j < cam->height; ++j)
+        for (int32_t i = 0; i < W; ++i) {
+            size_t q = (size_t)j * W + i;
+            for (int smp = 0; smp < spp[q]; ++smp) {
+                double O[3], dir[3], th_, bary[3];
+                orc_lens_ray(cam, lens, p, (int64_t)q, smp, O, dir);
+                int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
+                size_t r = (size_t)(off[q] + smp);
+                ids[r] = id;
+                ts[r] = id >= 0 ? th_ : INFINITY;
+                margin[r] = INFINITY;
+                if (id >= 0) {
+                    /* distance to the edge opposite vertex k = bary_k * 2 area / |edge_k| */
+                    const double* v = s->v + 9 * (size_t)id;
+                    double e1[3], e2[3], nrm[3], ek[3];
+                    sub3(v + 3, v, e1);
+                    sub3(v + 6, v, e2);
+                    cross3(e1, e2, nrm);
+                    double twice_area = sqrt(dot3(nrm, nrm));
+                    for (int k = 0; k < 3; ++k) {
+                        sub3(v + 3 * ((k + 2) % 3), v + 3 * ((k + 1) % 3), ek);
+                        double m = fabs(bary[k]) * twice_area / sqrt(dot3(ek, ek));
+                        if (m < margin[r]) margin[r] = m;
+                    }
+                }
             }
         }
 }

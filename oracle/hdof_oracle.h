@@ -99,5 +99,9 @@ void orc_replay(int32_t W, int32_t H, const orc_lens* lens, double tan_half_fovy
                 const int64_t* off, const double* rec, double* rt);
 void orc_temporal_frozen(int32_t W, int32_t H, const orc_params* p, const double* rt, const uint8_t* spp,
                          const double* hs, double* crt, double* hacc, double* mom, uint8_t* hlen);
+void orc_lens_ray(const orc_camera* cam, const orc_lens* lens, const orc_params* p, int64_t q, int32_t smp,
+                  double O[3], double dir[3]);
+void orc_trace_hits(const void* s, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
+                    const uint8_t* spp, const int64_t* off, int32_t* ids, double* ts, double* margin);
 int32_t orc_num_threads(void);
 #endif

@@ -102,6 +102,8 @@ def lib():
         L.orc_replay.argtypes = [C.c_int32, C.c_int32, C.POINTER(Lens), C.c_double, up8, i64p, dp, dp]
         L.orc_temporal_frozen.argtypes = [C.c_int32, C.c_int32, C.POINTER(Params), dp, up8, dp, dp, dp, dp, up8]
         L.orc_disk_area.restype = C.c_double
+        L.orc_lens_ray.argtypes = [C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), C.c_int64, C.c_int32, dp, dp]
+        L.orc_trace_hits.argtypes = [vp, C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), up8, i64p, ip, dp, dp]
         _lib = L
     return _lib
 
@@ -362,6 +364,28 @@ def trace_records(oscene: OScene, cam_, lens_, params_, spp):
                             spp.ctypes.data_as(C.POINTER(C.c_uint8)), off.ctypes.data_as(C.POINTER(C.c_int64)),
                             _d(rec)[1])
     return rec, off
+
+
+def lens_ray(cam_, lens_, params_, q, smp):
+    """FP64 origin and unit direction of lens sample smp of pixel q."""
+    O = (C.c_double * 3)()
+    d = (C.c_double * 3)()
+    lib().orc_lens_ray(C.byref(cam(cam_)), C.byref(lens(lens_)), C.byref(params(params_)), int(q), int(smp), O, d)
+    return np.array(list(O)), np.array(list(d))
+
+
+def trace_hits(oscene: OScene, cam_, lens_, params_, spp):
+    """Per-ray closest hits of the thin-lens samples at the row-major ray
+    offsets: (ids, t, edge margin, off)."""
+    spp = np.ascontiguousarray(spp, np.uint8)
+    off, n = ray_offsets(spp)
+    ids = np.full(max(n, 1), -1, np.int32)
+    ts = np.full(max(n, 1), np.inf)
+    mg = np.full(max(n, 1), np.inf)
+    lib().orc_trace_hits(oscene.h, C.byref(cam(cam_)), C.byref(lens(lens_)), C.byref(params(params_)),
+                         spp.ctypes.data_as(C.POINTER(C.c_uint8)), off.ctypes.data_as(C.POINTER(C.c_int64)),
+                         ids.ctypes.data_as(C.POINTER(C.c_int32)), _d(ts)[1], _d(mg)[1])
+    return ids[:n], ts[:n], mg[:n], off
 
 
 def replay(lens_, tan_half_fovy, spp, rec, off):

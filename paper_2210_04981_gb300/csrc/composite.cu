@@ -78,6 +78,7 @@ template <class ND, class COL>
 void launch(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
             const float* hacc, Coc coc, float h_tau, float* out, cudaStream_t s) {
     dim3 g((in->width + 31) / 32, (in->height + 7) / 8);
+    ProfScope ps_("composite", s);
     k_composite<ND, COL><<<g, 256, 0, s>>>(CompositeArgs<ND, COL>{
         static_cast<const ND*>(in->nd), static_cast<const COL*>(in->col), spp, reinterpret_cast<const float4*>(pp),
         reinterpret_cast<const float4*>(crt), reinterpret_cast<const float4*>(crec), hacc, in->width, in->height, coc,
@@ -138,6 +139,7 @@ void composite_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int
     *gy = (v.cam.height + 7) / 8;
 }
 void composite_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_composite", s);
     k_composite_batch<<<blocks, 256, 0, s>>>(static_cast<const CompositeF32*>(args), g);
 }
 

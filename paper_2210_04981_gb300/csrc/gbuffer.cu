@@ -95,6 +95,7 @@ template <class ND, class COL>
 void launch(const hdof_bvh* b, const hdof_camera* cam, const hdof_camera* prev, const hdof_params* p,
             const hdof_gbuf* g, const int* hint, unsigned* st, cudaStream_t s) {
     dim3 grid((cam->width + 15) / 16, (cam->height + 7) / 8);
+    ProfScope ps_("gbuffer", s);
     k_gbuffer<ND, COL><<<grid, 128, 0, s>>>(gbuf_args<ND, COL>(b, cam, prev, p, g, hint, st));
 }
 
@@ -143,6 +144,7 @@ void gbuffer_fill(const hdof_view& v, const ViewWs&, unsigned* st, void* dst, in
 }
 
 void gbuffer_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_gbuffer", s);
     k_gbuffer_batch<<<blocks, 128, 0, s>>>(static_cast<const GbufArgs<float4, float4>*>(args), g);
 }
 

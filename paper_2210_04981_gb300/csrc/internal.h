@@ -46,6 +46,19 @@ int check_lens(const hdof_lens* l, const char* who);
 int check_params(const hdof_params* p, const char* who);
 int check_gbuf(const hdof_gbuf* g, const char* who, bool need_mv);
 
+// Kernel timing (hdof_profile): a scope records CUDA events on its stream
+// around the launches inside it while profiling is on; nothing otherwise.
+bool prof_enabled();
+struct ProfScope {
+    int idx = -1;
+    unsigned gen = 0;
+    cudaStream_t s;
+    ProfScope(const char* name, cudaStream_t s_);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+};
+
 // number of SMs of the current device (cached per device)
 int sm_count();
 

@@ -253,6 +253,7 @@ int launch_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_p
                 uint8_t* tiles, cudaStream_t s) {
     const int W = in->width, H = in->height;
     dim3 grid((W + B - 1) / B, (H + B - 1) / B);
+    ProfScope ps_("mask", s);
     if (in->dtype_nd == HDOF_F32)
         k_mask_edge<float4><<<grid, 256, 0, s>>>(edge_args<float4>(in, p, edge, tiles));
     else
@@ -373,6 +374,7 @@ void mask_edge_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, i
     *gy = (v.g.height + B - 1) / B;
 }
 void mask_edge_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_mask_edge", s);
     k_mask_edge_batch<<<blocks, 256, 0, s>>>(static_cast<const EdgeArgs<float4>*>(args), g);
 }
 
@@ -383,6 +385,7 @@ void mask_spp_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, in
     *gy = (v.g.height + 7) / 8;
 }
 void mask_spp_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_mask_spp", s);
     k_mask_spp_batch<<<blocks, 256, 0, s>>>(static_cast<const SppArgs*>(args), g);
 }
 

@@ -628,24 +628,31 @@ int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p,
     const float4* col4 = static_cast<const float4*>(in->col);
     const bf164s* colb = static_cast<const bf164s*>(in->col);
     const float rm = p->r_max;
-    if (f32n && f32c)
-        k_pf_prep<<<grid, 256, 0, s>>>(
-            PrepArgs<float4, float4>{nd4, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
-    else if (f32n)
-        k_pf_prep<<<grid, 256, 0, s>>>(
-            PrepArgs<float4, bf164s>{nd4, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
-    else if (f32c)
-        k_pf_prep<<<grid, 256, 0, s>>>(
-            PrepArgs<half4s, float4>{ndh, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
-    else
-        k_pf_prep<<<grid, 256, 0, s>>>(
-            PrepArgs<half4s, bf164s>{ndh, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
-    HDOF_LAUNCHED("post-filter prep");
-    k_pf_rowscan<<<H, 256, 0, s>>>(RowScanArgs{w.nrec, W, H, w.pre});
-    HDOF_LAUNCHED("post-filter row prefix");
+    {
+        ProfScope ps_("pf_prep", s);
+        if (f32n && f32c)
+            k_pf_prep<<<grid, 256, 0, s>>>(
+                PrepArgs<float4, float4>{nd4, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+        else if (f32n)
+            k_pf_prep<<<grid, 256, 0, s>>>(
+                PrepArgs<float4, bf164s>{nd4, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+        else if (f32c)
+            k_pf_prep<<<grid, 256, 0, s>>>(
+                PrepArgs<half4s, float4>{ndh, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+        else
+            k_pf_prep<<<grid, 256, 0, s>>>(
+                PrepArgs<half4s, bf164s>{ndh, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+        HDOF_LAUNCHED("post-filter prep");
+    }
+    {
+        ProfScope ps_("pf_rowscan", s);
+        k_pf_rowscan<<<H, 256, 0, s>>>(RowScanArgs{w.nrec, W, H, w.pre});
+        HDOF_LAUNCHED("post-filter row prefix");
+    }
     const int kt = gather_tiles(p->r_max);
     float4* out = reinterpret_cast<float4*>(pp);
     // the taps are served from L1: a small shared-memory carve-out
+    ProfScope ps_("pf_gather", s);
     if (f32c) {
         cudaFuncSetAttribute(k_pf_gather<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
         k_pf_gather<float4><<<grid, GATHER_THREADS, 0, s>>>(
@@ -692,6 +699,7 @@ void pf_prep_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int
     *gy = (H + TP - 1) / TP;
 }
 void pf_prep_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_pf_prep", s);
     k_pf_prep_batch<<<blocks, 256, 0, s>>>(static_cast<const PrepF32*>(args), g);
 }
 
@@ -702,6 +710,7 @@ void pf_rowscan_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, 
     *gy = v.cam.height;
 }
 void pf_rowscan_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_pf_rowscan", s);
     k_pf_rowscan_batch<<<blocks, 256, 0, s>>>(static_cast<const RowScanArgs*>(args), g);
 }
 
@@ -717,6 +726,7 @@ void pf_gather_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, i
     cudaFuncSetAttribute(k_pf_gather_batch, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
 }
 void pf_gather_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_pf_gather", s);
     k_pf_gather_batch<<<blocks, GATHER_THREADS, 0, s>>>(static_cast<const GatherArgs<float4>*>(args), g);
 }
 

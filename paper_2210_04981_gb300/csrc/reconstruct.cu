@@ -316,6 +316,7 @@ TemporalArgs temporal_args(const float* rt, const hdof_gbuf* in, const uint8_t* 
 int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, int W, int H, float r_s, float var_ref,
                    float4* crec, float4* aux, cudaStream_t s) {
     dim3 g2((W + SP_TILE - 1) / SP_TILE, (H + SP_TILE - 1) / SP_TILE);
+    ProfScope ps_("spatial", s);
     k_spatial<<<g2, SP_THREADS, 0, s>>>(SpatialArgs{crt, mom, hlen, W, H, r_s, var_ref, crec, aux});
     HDOF_LAUNCHED("spatial reconstruction");
     return HDOF_OK;
@@ -349,11 +350,14 @@ extern "C" int hdof_reconstruct(const float* rt, const hdof_gbuf* in, const uint
     const int W = cam->width, H = cam->height;
     TemporalArgs a = temporal_args(rt, in, spp, cam, prev, p, hist_in, hist_out, crt, hacc);
     dim3 g1((W + 31) / 32, (H + 7) / 8);
-    if (in->dtype_nd == HDOF_F32)
-        k_temporal<float4><<<g1, 256, 0, s>>>(a, static_cast<const float4*>(in->nd));
-    else
-        k_temporal<half4s><<<g1, 256, 0, s>>>(a, static_cast<const half4s*>(in->nd));
-    HDOF_LAUNCHED("hdof_reconstruct: temporal");
+    {
+        ProfScope ps_("temporal", s);
+        if (in->dtype_nd == HDOF_F32)
+            k_temporal<float4><<<g1, 256, 0, s>>>(a, static_cast<const float4*>(in->nd));
+        else
+            k_temporal<half4s><<<g1, 256, 0, s>>>(a, static_cast<const half4s*>(in->nd));
+        HDOF_LAUNCHED("hdof_reconstruct: temporal");
+    }
     return launch_spatial(reinterpret_cast<const float4*>(crt), reinterpret_cast<const float2*>(hist_out->mom),
                           hist_out->hlen, W, H, p->r_s, p->var_ref, reinterpret_cast<float4*>(crec), nullptr, s);
 }
@@ -369,6 +373,7 @@ void temporal_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int*
     *gy = (v.cam.height + 7) / 8;
 }
 void temporal_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_temporal", s);
     k_temporal_batch<<<blocks, 256, 0, s>>>(static_cast<const TemporalBatch*>(args), g);
 }
 
@@ -382,6 +387,7 @@ void spatial_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int* 
     *gy = (v.cam.height + SP_TILE - 1) / SP_TILE;
 }
 void spatial_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_spatial", s);
     k_spatial_batch<<<blocks, SP_THREADS, 0, s>>>(static_cast<const SpatialArgs*>(args), g);
 }
 

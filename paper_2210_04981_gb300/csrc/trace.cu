@@ -591,6 +591,33 @@ __device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
 
 __global__ void __launch_bounds__(256) k_resolve(TraceArgs a) { resolve_body(a, blockIdx.x); }
 
+// Per-ray closest hits of the last trace on this workspace, in the order of
+// its hit records: ids[qoff[k] + s] = original id of sample s of queue entry
+// k (-1 for a miss), ts[...] = ray parameter of the hit (+inf for a miss).
+struct HitsArgs {
+    const Tri* tris;
+    const uint8_t* spp;
+    const unsigned* queue;
+    const unsigned* qoff;
+    const unsigned* totals;
+    const float2* recs;
+    int smax;
+    int* ids;
+    float* ts;
+};
+__global__ void __launch_bounds__(256) k_hits(HitsArgs a) {
+    const unsigned k = blockIdx.x * 256u + threadIdx.x;
+    if (k >= __ldg(&a.totals[0])) return;
+    const unsigned q = __ldg(&a.queue[k]), ro = __ldg(&a.qoff[k]);
+    const int n = min((int)__ldg(&a.spp[q]), a.smax);
+    for (int smp = 0; smp < n; ++smp) {
+        const float2 rc = a.recs[ro + smp];
+        const int slot = __float_as_int(rc.y);
+        a.ids[ro + smp] = slot >= 0 ? __float_as_int(__ldg(&a.tris[slot].v0.w)) : -1;
+        if (a.ts) a.ts[ro + smp] = rc.x;
+    }
+}
+
 TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
                      unsigned* st, const uint8_t* spp, const int* hint, const ViewWs& w, float* rt, float* rec,
                      const unsigned* ray_off) {
@@ -723,6 +750,7 @@ void count_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* 
     *gy = (H + TB - 1) / TB;
 }
 void count_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_trace_count", s);
     k_count_batch<<<blocks, 256, 0, s>>>(static_cast<const CountArgs*>(args), g);
 }
 
@@ -732,6 +760,7 @@ void scan_fill(const hdof_view& v, const ViewWs& w, void* dst) {
     *reinterpret_cast<ScanArgs*>(dst) = ScanArgs{w.counts, ntiles, w.offsets, w.roffsets, w.totals, v.stats};
 }
 void scan_launch_batch(const void* args, int n, cudaStream_t s) {
+    ProfScope ps_("batch_trace_scan", s);
     k_scan_batch<<<n, 1024, 0, s>>>(static_cast<const ScanArgs*>(args));
 }
 
@@ -745,6 +774,7 @@ void scatter_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int
     *gy = (H + TB - 1) / TB;
 }
 void scatter_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    ProfScope ps_("batch_trace_scatter", s);
     k_scatter_batch<<<blocks, 256, 0, s>>>(static_cast<const ScatterArgs*>(args), g);
 }
 
@@ -762,16 +792,20 @@ int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid 
     k_ray_prefix<<<1, 1024, 0, s>>>(static_cast<const ScanArgs*>(scan_args), n, gq);
     HDOF_LAUNCHED("batched trace: ray prefix");
     const TraceArgs* a = static_cast<const TraceArgs*>(trace_args);
-    if (refill == 0) {  // warp packets
-        if (block == 64) k_trace_packets_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1);
-        else if (block == 256) k_trace_packets_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1);
-        else k_trace_packets_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1);
-    } else {  // ray level, dynamic fetch
-        if (block == 64) k_trace_rays_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, refill);
-        else if (block == 256) k_trace_rays_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, refill);
-        else k_trace_rays_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, refill);
+    {
+        ProfScope ps_(refill == 0 ? "batch_trace_packets" : "batch_trace_rays", s);
+        if (refill == 0) {  // warp packets
+            if (block == 64) k_trace_packets_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1);
+            else if (block == 256) k_trace_packets_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1);
+            else k_trace_packets_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1);
+        } else {  // ray level, dynamic fetch
+            if (block == 64) k_trace_rays_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, refill);
+            else if (block == 256) k_trace_rays_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, refill);
+            else k_trace_rays_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, refill);
     }
     HDOF_LAUNCHED("batched trace");
+    }
+    ProfScope ps_("batch_trace_resolve", s);
     k_resolve_batch<<<resolve_blocks, 256, 0, s>>>(a, resolve);
     HDOF_LAUNCHED("batched trace: resolve");
     return HDOF_OK;
@@ -829,20 +863,50 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
     const ViewWs w = view_ws(v);
     const int ntx = (W + TB - 1) / TB, nty = (H + TB - 1) / TB, ntiles = ntx * nty;
     dim3 tg(ntx, nty);
-    k_count<<<tg, 256, 0, s>>>(CountArgs{spp, W, H, ntx, p->spp_max, w.counts});
-    k_scan<<<1, 1024, 0, s>>>(ScanArgs{w.counts, ntiles, w.offsets, w.roffsets, w.totals, stats});
-    k_scatter<<<tg, 256, 0, s>>>(
-        ScatterArgs{spp, W, H, ntx, p->spp_max, w.offsets, w.roffsets, w.queue, w.qoff, w.ray_pix, w.ray_s, ray_off});
-    HDOF_LAUNCHED("hdof_trace: compaction");
+    {
+        ProfScope ps_("trace_compact", s);
+        k_count<<<tg, 256, 0, s>>>(CountArgs{spp, W, H, ntx, p->spp_max, w.counts});
+        k_scan<<<1, 1024, 0, s>>>(ScanArgs{w.counts, ntiles, w.offsets, w.roffsets, w.totals, stats});
+        k_scatter<<<tg, 256, 0, s>>>(
+            ScatterArgs{spp, W, H, ntx, p->spp_max, w.offsets, w.roffsets, w.queue, w.qoff, w.ray_pix, w.ray_s, ray_off});
+        HDOF_LAUNCHED("hdof_trace: compaction");
+    }
 
     TraceArgs a = trace_args(b, cam, lens, p, st, spp, hint_tri, w, rt, rec, ray_off);
     int blocks = 0;
     if ((rc = rays_grid(false, t.trace_refill == 0, t.trace_block, &blocks))) return rc;
-    if (t.trace_block == 64) launch_trace<64>(a, t.trace_refill, blocks, s);
-    else if (t.trace_block == 256) launch_trace<256>(a, t.trace_refill, blocks, s);
-    else launch_trace<128>(a, t.trace_refill, blocks, s);
-    HDOF_LAUNCHED("hdof_trace: trace");
+    {
+        ProfScope ps_(t.trace_refill == 0 ? "trace_packets" : "trace_rays", s);
+        if (t.trace_block == 64) launch_trace<64>(a, t.trace_refill, blocks, s);
+        else if (t.trace_block == 256) launch_trace<256>(a, t.trace_refill, blocks, s);
+        else launch_trace<128>(a, t.trace_refill, blocks, s);
+        HDOF_LAUNCHED("hdof_trace: trace");
+    }
+    ProfScope ps_("trace_resolve", s);
     k_resolve<<<(W * H + 255) / 256, 256, 0, s>>>(a);
     HDOF_LAUNCHED("hdof_trace: resolve");
+    return HDOF_OK;
+}
+
+extern "C" int hdof_trace_hits(const hdof_bvh* b, const hdof_camera* cam, const hdof_params* p, const uint8_t* spp,
+                               const void* workspace, size_t workspace_bytes, int32_t* ids, float* ts,
+                               void* stream) {
+    clear_error();
+    HDOF_CHECK_ARG(b, "hdof_trace_hits: bvh is NULL");
+    int rc;
+    if ((rc = check_camera(cam, "hdof_trace_hits")) || (rc = check_params(p, "hdof_trace_hits"))) return rc;
+    HDOF_CHECK_ARG(spp && ids, "hdof_trace_hits: spp and ids are required");
+    const int W = cam->width, H = cam->height;
+    WsLayout L = ws_layout(W, H, p);
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.trace, "hdof_trace_hits: workspace of %zu bytes < %zu",
+                   workspace_bytes, L.trace);
+    hdof_view v = {};
+    v.cam = *cam;
+    v.params = *p;
+    v.workspace = const_cast<void*>(workspace);
+    const ViewWs w = view_ws(v);
+    HitsArgs a{b->tris, spp, w.queue, w.qoff, w.totals, w.rec, p->spp_max, ids, ts};
+    k_hits<<<(W * H + 255) / 256, 256, 0, as_stream(stream)>>>(a);
+    HDOF_LAUNCHED("hdof_trace_hits");
     return HDOF_OK;
 }

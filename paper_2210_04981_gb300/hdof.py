@@ -79,6 +79,10 @@ class hdof_post_state(C.Structure):
                                           "out")]
 
 
+class hdof_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int32), ("total_ms", C.c_float)]
+
+
 class hdof_bvh_stats(C.Structure):
     _fields_ = [("n_tris", C.c_int32), ("n_nodes", C.c_int32), ("depth", C.c_int32),
                 ("n_big", C.c_int32), ("device_bytes", C.c_int64)]
@@ -112,6 +116,10 @@ def load():
         "hdof_mask_noalloc": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp], C.c_int),
         "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, vp, vp, vp, sz, P(hdof_tuning), vp],
                        C.c_int),
+        "hdof_profile": ([i32], C.c_int),
+        "hdof_profile_read": ([P(hdof_kernel_time), i32], C.c_int),
+        "hdof_probe_fma": ([i32, i32, vp, P(C.c_double), vp], C.c_int),
+        "hdof_trace_hits": ([vp, P(hdof_camera), P(hdof_params), vp, vp, sz, vp, vp, vp], C.c_int),
         "hdof_postfilter": ([P(hdof_gbuf), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, sz, vp],
                             C.c_int),
         "hdof_reconstruct": ([vp, P(hdof_gbuf), vp, P(hdof_camera), P(hdof_camera), P(hdof_lens),
@@ -142,10 +150,11 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["hdof_version", "hdof_last_error", "hdof_sync", "hdof_default_params", "hdof_build_bvh",
             "hdof_bvh_destroy", "hdof_bvh_info", "hdof_closest_hits", "hdof_gbuffer", "hdof_workspace_bytes",
-            "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_postfilter", "hdof_reconstruct", "hdof_composite",
+            "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_trace_hits", "hdof_postfilter", "hdof_reconstruct", "hdof_composite",
             "hdof_batch_create", "hdof_batch_update", "hdof_batch_render", "hdof_batch_render_range",
             "hdof_batch_destroy", "hdof_batch_bytes",
-            "hdof_post_workspace_bytes", "hdof_post_forward", "hdof_post_backward"]
+            "hdof_post_workspace_bytes", "hdof_post_forward", "hdof_post_backward", "hdof_profile",
+            "hdof_profile_read", "hdof_probe_fma"]
 
 
 def _check(rc):
@@ -295,6 +304,27 @@ def hdof_sync(stream=None):
     _check(load().hdof_sync(_stream(stream)))
 
 
+def hdof_profile(on: bool):
+    """Switch per-kernel event timing of the compute calls on or off."""
+    _check(load().hdof_profile(int(bool(on))))
+
+
+def hdof_profile_read(max_out=64) -> dict:
+    """{kernel name: (launches, summed device ms)} since the previous read."""
+    arr = (hdof_kernel_time * max_out)()
+    n = load().hdof_profile_read(arr, max_out)
+    if n < 0:
+        _check(n)
+    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms)) for k in range(min(n, max_out))}
+
+
+def hdof_probe_fma(blocks_per_sm, iters, sink, stream=None) -> float:
+    """Enqueue the FMA-throughput probe; returns its FMA lane-instruction count."""
+    ops = C.c_double()
+    _check(load().hdof_probe_fma(int(blocks_per_sm), int(iters), _ptr(sink), C.byref(ops), _stream(stream)))
+    return ops.value
+
+
 def hdof_workspace_bytes(width, height, p=None) -> int:
     return int(load().hdof_workspace_bytes(int(width), int(height), C.byref(params(p))))
 
@@ -343,6 +373,14 @@ def hdof_trace(bvh: Bvh, cam, lns, p, spp, rt, stats, workspace, stream=None, re
                              _ptr(spp), _ptr(hint), _ptr(rt), _ptr(stats), _ptr(rec), _ptr(ray_off), _ptr(workspace),
                              workspace.numel() * workspace.element_size(),
                              C.byref(tune) if tune is not None else None, _stream(stream)))
+
+
+def hdof_trace_hits(bvh: Bvh, cam, p, spp, workspace, ids, ts=None, stream=None):
+    """Per-ray hit ids (int32, -1 = miss) and hit distances of the last
+    hdof_trace on this workspace, at that call's ray_off[p] + s."""
+    _check(load().hdof_trace_hits(bvh.handle, C.byref(camera(cam)), C.byref(params(p)), _ptr(spp),
+                                  _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(ids),
+                                  _ptr(ts), _stream(stream)))
 
 
 def hdof_postfilter(gbuf: GBuffer, cam, lns, p, pp, workspace, stream=None):

@@ -53,7 +53,8 @@ def test_struct_layout_matches_header(H, tmp_path):
     import subprocess
     recs = {"hdof_camera": H.hdof_camera, "hdof_lens": H.hdof_lens, "hdof_params": H.hdof_params,
             "hdof_gbuf": H.hdof_gbuf, "hdof_history": H.hdof_history, "hdof_bvh_stats": H.hdof_bvh_stats,
-            "hdof_post_state": H.hdof_post_state, "hdof_view": H.hdof_view, "hdof_tuning": H.hdof_tuning}
+            "hdof_post_state": H.hdof_post_state, "hdof_view": H.hdof_view, "hdof_tuning": H.hdof_tuning,
+            "hdof_kernel_time": H.hdof_kernel_time}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hdof.h"', "int main(void) {"]
     for name, rec in recs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')

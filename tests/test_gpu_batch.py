@@ -16,7 +16,8 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_2210_04981_gb300.hdof as H  # noqa: E402
-from gpu_util import bvh_of, frac_close, host, report, rt_close  # noqa: E402
+from gpu_util import (bvh_of, check_gbuffer_ids, check_mask_stage, frac_close, history_host, host, report,  # noqa: E402
+                      rt_close)
 
 SMALL_RES = ((64, 64), (160, 120), (320, 180), (200, 150), (33, 17))
 
@@ -215,7 +216,9 @@ def test_batch_64_views_full_workload(orc):
         pix = np.random.default_rng(i).choice(W * Hh, min(4000, W * Hh), replace=False).astype(np.int32)
         ref = orc.frame(orc.OScene(scenes[v.room]), cams[i], prevs[i], lenses[i], ps[i], pp_pix=pix)
         spp = host(r.spp)
-        assert (spp == ref["mask"]["spp"]).mean() >= 0.999, f"view {i}"
+        check_gbuffer_ids(orc, scenes[v.room], cams[i], host(r.g.tri), ref["g"]["tri"], f"view {i}")
+        check_mask_stage(orc, ps[i], host(r.g.nd), host(r.g.mv), host(r.edge), spp, history_host(r.hist[1 - r.cur]),
+                         f"view {i}")
         tr = (spp > 0) & (spp == ref["mask"]["spp"])
         assert tr.any()
         ok = rt_close(host(r.rt), ref["rt"], tr)

@@ -21,7 +21,9 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_2210_04981_gb300.hdof as H  # noqa: E402
-from gpu_util import bvh_of, dev, frac_close, gbuf_from, history_from, host, report, rt_close, workspace  # noqa: E402,E501
+from gpu_util import (bvh_of, check_gbuffer_ids, check_mask_stage, classify_hits, dev, frac_close,  # noqa: E402
+                      gbuf_from, history_from, history_host, host, report, reprojection_ties, rt_close,
+                      tie_tiles, workspace)
 
 T30 = math.tan(math.radians(30.0))
 
@@ -144,14 +146,14 @@ def test_gbuffer_room_moving_camera(orc):
     _, g = _gbuffer(scene, cam1, cam0, p)
     ref = orc.gbuffer(orc.OScene(scene), cam1, cam0, p)
     tri, rtri = host(g.tri), ref["tri"]
-    mism = tri != rtri
-    assert mism.mean() < 2e-3, f"{mism.sum()} hit-id mismatches"
-    # mismatched pixels must be ties: same depth (shared edge of one surface) or a silhouette graze
+    # every differing id is an epsilon-tie of the primary ray (grazed edge, equal t)
+    ties = check_gbuffer_ids(orc, scene, cam1, tri, rtri, "room 320x180")
+    same = tri == rtri
+    print(f"room 320x180 G-buffer: {ties} hit-id ties of {tri.size} pixels")
     z, rz = host(g.nd)[..., 3], ref["nd"][..., 3]
-    same = ~mism
     assert np.allclose(z[same], rz[same], rtol=1e-5)
-    assert frac_close(host(g.col)[same], ref["col"][same], 1e-4, axis=-1) >= 0.999
-    assert frac_close(host(g.mv)[same], ref["mv"][same], 1e-3, axis=-1) >= 0.999
+    assert frac_close(host(g.col)[same], ref["col"][same], 1e-4, axis=-1) == 1.0
+    assert frac_close(host(g.mv)[same], ref["mv"][same], 1e-3, axis=-1) == 1.0
 
 
 # ------------------------------------------------------------------ mask ----
@@ -165,35 +167,13 @@ def _mask(g, hist, p):
     return host(edge), host(spp)
 
 
-def _tie_tiles(emetric, tau, tile, dilate, tol=1e-4):
-    """Pixels whose spp may legitimately differ: inside (dilated) tiles whose
-    edge OR involves a pixel at the threshold."""
-    Hh, W = emetric.shape
-    tie = np.abs(emetric - tau) < tol * max(1.0, tau)
-    nty, ntx = (Hh + tile - 1) // tile, (W + tile - 1) // tile
-    tt = np.zeros((nty, ntx), bool)
-    ys, xs = np.nonzero(tie)
-    tt[ys // tile, xs // tile] = True
-    dil = np.zeros_like(tt)
-    for dy in range(-dilate, dilate + 1):
-        for dx in range(-dilate, dilate + 1):
-            sh = np.zeros_like(tt)
-            sy = slice(max(0, dy), nty + min(0, dy))
-            sx = slice(max(0, dx), ntx + min(0, dx))
-            ty = slice(max(0, -dy), nty + min(0, -dy))
-            tx = slice(max(0, -dx), ntx + min(0, -dx))
-            sh[ty, tx] = tt[sy, sx]
-            dil |= sh
-    return tie, np.kron(dil, np.ones((tile, tile), bool))[:Hh, :W]
-
-
 @pytest.mark.parametrize("seed,W,Hh", [(0, 128, 128), (1, 257, 131), (2, 64, 40)])
 def test_mask_random_gbuffer(orc, seed, W, Hh):
     gb = hi.random_gbuffer(W, Hh, seed=seed)
     p = hi.Params(spp_max=8)
     edge, spp = _mask(gbuf_from(gb["nd"], gb["col"], gb["mv"]), None, p)
     ref = orc.mask(gb["nd"].astype(np.float64), gb["mv"].astype(np.float64), p)
-    tie, tie_px = _tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
+    tie, tie_px = tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
     assert np.array_equal(edge[~tie], ref["edge"][~tie])
     assert np.array_equal(spp[~tie_px], ref["spp"][~tie_px])
     assert edge.sum() > 0
@@ -210,7 +190,7 @@ def test_mask_tile_and_dilation_shapes(orc, tile, dilate, W, Hh):
     p = hi.Params(spp_max=8, tile=tile, dilate=dilate)
     edge, spp = _mask(gbuf_from(gb["nd"], gb["col"], gb["mv"]), None, p)
     ref = orc.mask(gb["nd"].astype(np.float64), gb["mv"].astype(np.float64), p)
-    tie, tie_px = _tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
+    tie, tie_px = tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
     assert np.array_equal(edge[~tie], ref["edge"][~tie])
     assert np.array_equal(spp[~tie_px], ref["spp"][~tie_px])
     assert edge.sum() > 0 and (spp > 0).sum() > 0
@@ -224,12 +204,9 @@ def test_mask_variance_term(orc):
     edge, spp = _mask(gbuf_from(gb["nd"], gb["col"], gb["mv"]), history_from(hist), p)
     ref = orc.mask(gb["nd"].astype(np.float64), gb["mv"].astype(np.float64), p, hist["mom"].astype(np.float64),
                    hist["hlen"])
-    tie, tie_px = _tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
+    tie, tie_px = tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
     # nearest-pixel reprojection ties: u within 1e-4 of a half-integer
-    jj, ii = np.mgrid[0:Hh, 0:W]
-    ux, uy = ii - gb["mv"][..., 0].astype(np.float64), jj - gb["mv"][..., 1].astype(np.float64)
-    near_half = (np.abs((ux + 0.5) - np.round(ux + 0.5)) < 1e-4) | (np.abs((uy + 0.5) - np.round(uy + 0.5)) < 1e-4)
-    ok = ~(tie_px | near_half)
+    ok = ~(tie_px | reprojection_ties(gb["mv"]))
     assert np.array_equal(spp[ok], ref["spp"][ok])
     assert len(np.unique(spp)) > 3  # variance term produced intermediate ray counts
 
@@ -353,6 +330,31 @@ def test_trace_forms_agree(aperture):
         outs.append(rt)
     for o in outs[1:]:
         assert torch.equal(outs[0].view(torch.int32), o.view(torch.int32))
+
+
+@pytest.mark.parametrize("refill", [0, 4])
+def test_trace_watchdog_reports_timeout(refill):
+    """A traversal step cap of 1 stops every lens ray after one step (the
+    lane or packet gives up and the kernel returns; nothing waits):
+    hdof_sync reports HDOF_ETIMEOUT once and clears the status word, and a
+    trace with the default cap afterwards is clean."""
+    scene, cam, lens, p = hi.tiny_config()
+    bvh = bvh_of(scene)
+    W, Hh = cam.width, cam.height
+    spp = dev(np.full((Hh, W), 4, np.uint8))
+    rt = torch.empty((Hh, W, 12), dtype=torch.float32, device="cuda")
+    stats = torch.zeros(2, dtype=torch.int32, device="cuda")
+    ws = workspace(W, Hh, p)
+    tune = H.tuning(128, refill)
+    H.hdof_sync()
+    H.hdof_trace(bvh, cam, lens, p.replace(trav_cap=1), spp, rt, stats, ws, tune=tune)
+    with pytest.raises(H.HdofError) as e:
+        H.hdof_sync()
+    assert e.value.code == -4
+    H.hdof_sync()  # cleared
+    H.hdof_trace(bvh, cam, lens, p, spp, rt, stats, ws, tune=tune)
+    H.hdof_sync()
+    assert int(host(stats)[1]) == 4 * W * Hh
 
 
 def test_trace_rejects_bad_tuning():
@@ -487,11 +489,23 @@ def test_composite(orc):
 
 # ------------------------------------------------------------ full frames --
 
-def _frame_check(r, ref, name):
+def _stage_check(orc, scene, cam, p, r, ref, name):
+    """The frame's integer decisions stage by stage: G-buffer hit ids against
+    the oracle's up to primary-ray epsilon-ties; edge bits and spp against
+    the oracle's mask of the GPU's own G-buffer and input history, identical
+    outside threshold and reprojection ties.  Prints the tie counts."""
+    gt = check_gbuffer_ids(orc, scene, cam, host(r.g.tri), ref["g"]["tri"], name)
+    hin = history_host(r.hist[1 - r.cur])
+    mt = check_mask_stage(orc, p, host(r.g.nd), host(r.g.mv), host(r.edge), host(r.spp), hin, name)
+    spp_eq = float((host(r.spp) == ref["mask"]["spp"]).mean())
+    print(f"{name}: {gt} G-buffer hit-id ties, {mt} mask pixels at ties; spp equal to the oracle frame's on "
+          f"{spp_eq:.6f} of pixels")
+
+
+def _frame_check(orc, scene, cam, p, r, ref, name):
+    _stage_check(orc, scene, cam, p, r, ref, name)
     out = host(r.out)[..., :3]
     ok = frac_close(out, ref["out"][..., :3], 1e-3)
-    spp_eq = float((host(r.spp) == ref["mask"]["spp"]).mean())
-    assert spp_eq >= 0.999, f"{name}: spp agrees on {spp_eq:.5f}"
     assert ok >= 0.999, f"{name}: {ok:.5f} within 1e-3; " + report("out", out, ref["out"][..., :3])
 
 
@@ -503,7 +517,7 @@ def test_frame_tiny(orc):
     ref = orc.frame(orc.OScene(scene), cam, cam, lens, p)
     assert np.array_equal(host(r.spp), ref["mask"]["spp"])
     assert np.array_equal(host(r.edge), ref["mask"]["edge"])
-    _frame_check(r, ref, "tiny")
+    _frame_check(orc, scene, cam, p, r, ref, "tiny")
 
 
 def test_room_sequence_8_frames(orc):
@@ -521,7 +535,7 @@ def test_room_sequence_8_frames(orc):
         H.hdof_sync()
         ref = orc.frame(osc, cams[k], prev, lens, p, hist=hist)
         hist = ref["hist"]
-        _frame_check(r, ref, f"frame {k}")
+        _frame_check(orc, scene, cams[k], p, r, ref, f"frame {k}")
 
 
 def test_room_1080p_bench_config_sampled(orc):
@@ -542,8 +556,8 @@ def test_room_1080p_bench_config_sampled(orc):
         H.hdof_sync()
         ref = orc.frame(osc, cams[k], prev, lens, p, hist=hist, pp_pix=pix)
         hist = ref["hist"]
+        _stage_check(orc, scene, cams[k], p, r, ref, f"1080p frame {k}")
         spp = host(r.spp)
-        assert (spp == ref["mask"]["spp"]).mean() >= 0.999
         same = spp == ref["mask"]["spp"]
         tr = (spp > 0) & same
         ok = rt_close(host(r.rt), ref["rt"], tr)
@@ -553,3 +567,52 @@ def test_room_1080p_bench_config_sampled(orc):
         assert frac_close(pp, ref["pp"], 1e-4) >= 0.999, report("pp", pp, ref["pp"])
         out = host(r.out).reshape(-1, 4)[pix][:, :3]
         assert frac_close(out, ref["out"][:, :3], 1e-3) >= 0.999, report("out", out, ref["out"][:, :3])
+
+
+def test_lens_ray_hit_ids_room_1080p(orc):
+    """Visibility ray by ray at the benchmark's workload (1920x1080 room,
+    frame 0, packet trace as the benchmark launches it): the closest hit of
+    every lens sample of 20000 sampled traced pixels equals the oracle's
+    (same pixel, sample, lens point and aim), except at epsilon-ties of the
+    float32 ray against the float64 one (a hit within 2^-16 t of an edge, or
+    two hits at equal t); hit distances agree to 1e-5 relative."""
+    W, Hh = 1920, 1080
+    scene, cams, lens, p0 = hi.room_config(W, Hh, frames=1)
+    cam, p = cams[0], p0.replace(frame=0)
+    osc = orc.OScene(scene)
+    bvh = bvh_of(scene)
+    r = H.Renderer(bvh, W, Hh, p)
+    r.frame(cam, cam, lens, p)
+    H.hdof_sync()
+    n_rays = int(host(r.stats)[1])
+    rec = torch.empty((n_rays, 4), dtype=torch.float32, device="cuda")
+    ray_off = torch.empty((Hh, W), dtype=torch.int32, device="cuda")
+    rt = torch.empty_like(r.rt)
+    stats = torch.zeros(2, dtype=torch.int32, device="cuda")
+    H.hdof_trace(bvh, cam, lens, p, r.spp, rt, stats, r.ws, rec=rec, ray_off=ray_off, hint=r.g.tri)
+    ids = torch.empty(n_rays, dtype=torch.int32, device="cuda")
+    ts = torch.empty(n_rays, dtype=torch.float32, device="cuda")
+    H.hdof_trace_hits(bvh, cam, p, r.spp, r.ws, ids, ts)
+    H.hdof_sync()
+    assert np.array_equal(host(rt), host(r.rt)) and int(host(stats)[1]) == n_rays
+    spp = host(r.spp)
+    traced = np.nonzero(spp.ravel())[0]
+    pick = np.sort(np.random.default_rng(5).choice(traced, min(20000, traced.size), replace=False))
+    spp_s = np.zeros_like(spp)
+    spp_s.ravel()[pick] = spp.ravel()[pick]
+    oids, ots, _, ooff = orc.trace_hits(osc, cam, lens, p, spp_s)
+    n = spp.ravel()[pick].astype(np.int64)
+    qs = np.repeat(pick, n)
+    ss = np.concatenate([np.arange(k) for k in n])
+    gidx = host(ray_off).ravel()[qs].astype(np.int64) + ss
+    oidx = ooff[qs] + ss
+    gid, gt = host(ids)[gidx], host(ts)[gidx]
+    oid, ot = oids[oidx], ots[oidx]
+    tris = scene.tri_verts().astype(np.float64).reshape(-1, 3, 3)
+    bad, ties = classify_hits(tris, lambda k: orc.lens_ray(cam, lens, p, qs[k], ss[k]), gid, oid)
+    assert not bad, f"{len(bad)} of {gid.size} lens-ray hit ids differ beyond ties (first: {bad[:5]})"
+    hit = (gid == oid) & (oid >= 0)
+    assert np.all(np.abs(gt[hit] - ot[hit]) <= 1e-5 * ot[hit])
+    assert np.all(np.isinf(gt[(gid == oid) & (oid < 0)]))
+    assert ties <= 1e-3 * gid.size
+    print(f"lens rays 1080p: {gid.size} rays compared, {ties} epsilon-ties, {int((oid < 0).sum())} misses")
