@@ -310,9 +310,6 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(K)]
     stats_all = torch.zeros((K, 2), dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
-    if profile:
-        H.hdof_profile_read()  # drop anything recorded before
-        H.hdof_profile(True)
     wall0 = time.perf_counter()
     for s in range(K):
         flush.zero_()  # evict L2 between steps (outside the step's events)
@@ -322,6 +319,15 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
     wall = time.perf_counter() - wall0
     kern = {}
     if profile:
+        # the next K frames again with the library's per-kernel events (they
+        # add ~0.05 ms per frame, so the stage times above are taken without)
+        H.hdof_sync()
+        H.hdof_profile_read()  # drop anything recorded before
+        H.hdof_profile(True)
+        for s in range(K):
+            flush.zero_()
+            frame(warmup + K + s)
+        torch.cuda.synchronize()
         H.hdof_profile(False)
         kern = {n: t / K for n, (_, t) in H.hdof_profile_read().items()}
     H.hdof_sync()
@@ -362,7 +368,7 @@ def kernel_roofline(name, kms, rays, z, lens, Hh, t, r_max, lane_peak, clock_mhz
     peak_t = lane_peak / 1e12
     src = (f"measured: FFMA lane-instruction rate of hdof_probe_fma (8 chains x 256 threads x 8 blocks per SM) "
            f"at {clock_mhz or 'unsampled'} MHz")
-    if name.startswith("trace_"):
+    if name in ("trace_packets", "trace_rays"):
         ops = TRACE_OPS_PER_RAY * rays
         ach = ops / (kms * 1e-3) / 1e12
         return {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak_t, 2), "unit": "Tlane-op/s",
@@ -382,6 +388,36 @@ def kernel_roofline(name, kms, rays, z, lens, Hh, t, r_max, lane_peak, clock_mhz
     return None
 
 
+def quality(H, bvh, r, cam, lens, p, passes):
+    """The paper's Fig. 1 comparison on the renderer's last frame: a full
+    ray-traced frame (every pixel, passes x spp_max lens samples, timed), the
+    post-process-only frame (the composite with no traced pixels), and the
+    error of the hybrid and post-process frames against the ray-traced one,
+    over all pixels and over the traced pixels (the blurry silhouettes)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    zero = torch.zeros_like(r.spp)
+    pp_only = torch.empty_like(r.out)
+    H.hdof_composite(r.g, zero, r.pp, r.crt, r.crec, r.hacc, cam, lens, p, pp_only)
+    rt = torch.empty_like(r.out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    H.hdof_reference_rt(bvh, cam, lens, p, passes, rt, r.ws, hint=r.g.tri)
+    e1.record(stream)
+    e1.synchronize()
+    rt_ms = e0.elapsed_time(e1)
+    stats = torch.empty(H.ERR_SCRATCH, dtype=torch.float64, device=r.out.device)
+    traced = (r.spp > 0).to(torch.uint8)
+    res = {"reference": f"full ray trace, {passes * p.spp_max} lens samples per pixel",
+           "reference_ms": round(rt_ms, 3), "traced_pixels": int(traced.sum())}
+    for name, a, b in (("hybrid_vs_rt", r.out, rt), ("pp_vs_rt", pp_only, rt), ("hybrid_vs_pp", r.out, pp_only)):
+        H.hdof_error_map(a, b, stats, region=traced)
+        sm = H.error_summary(stats)
+        res[name] = {part: {k: (round(v, 6) if isinstance(v, float) else v) for k, v in sm[part].items()}
+                     for part in ("all", "region")}
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -399,7 +435,7 @@ def run_ours(args):
     scene = make_scene(W / Hh)
     lens = hi.room_lens()
     p0 = hi.room_params(**over)
-    cams = [hi.room_camera(k, W, Hh) for k in range(args.warmup + args.steps + 1)]
+    cams = [hi.room_camera(k, W, Hh) for k in range(args.warmup + 2 * args.steps + 1)]
     mixed = args.precision == "mixed"
     nd_dt, col_dt = (torch.float16, torch.bfloat16) if mixed else (torch.float32, torch.float32)
     t0 = time.perf_counter()
@@ -464,6 +500,8 @@ def run_ours(args):
         gbs = ab[stg] / (mean_stage[STAGES.index(stg)] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 3),
                 "traffic": MEASURED_TRAFFIC.get((args.scene, storage, dom)), "kernel": dom, "peak_source": peak_src}
+    last = args.warmup + 2 * K - 1
+    qual = quality(H, bvh, r, cams[last], lens, p0.replace(frame=last % 65536, camera_moved=1), args.rt_passes)
     e2e = None
     if not args.no_e2e:
         e_ms, h2d, d2h = e2e_frames(H, r, Hh, W, args.warmup, K, flush)
@@ -486,7 +524,7 @@ def run_ours(args):
         "roofline": roof, "roofline_alu_kernels": roofs,
         "fp32_peak": {"lane_ops_per_s": round(lane_peak / 1e12, 3), "unit": "T", "clocks": pclk,
                       "sms": torch.cuda.get_device_properties(dev).multi_processor_count},
-        "e2e": e2e, "gpu_launches": 14 * K, "clocks": clocks,
+        "quality": qual, "e2e": e2e, "gpu_launches": 14 * K, "clocks": clocks,
     }
     # "vs plain form": the same frames with mixed-precision storage, and the
     # 64-view batched frame against its single-view calls
@@ -935,6 +973,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--ref-pf-stride", type=int, default=16)
     ap.add_argument("--views", type=int, default=64, help="views of the batched workload")
+    ap.add_argument("--rt-passes", type=int, default=32,
+                    help="passes of spp_max lens samples of the full ray-traced quality reference")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the mixed-precision and batched comparisons of the default line")
     args = ap.parse_args()

@@ -323,6 +323,30 @@ int hdof_trace(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* len
 int hdof_trace_hits(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_params* p, const uint8_t* spp,
                     const void* workspace, size_t workspace_bytes, int32_t* ids, float* ts, void* stream);
 
+/* Full ray-traced depth of field: the quality reference that the paper's
+ * Fig. 1 sets beside the hybrid frame (distributed ray tracing of every
+ * pixel, no mask, no post-process).  Every pixel is traced with spp_max lens
+ * samples per pass (the sampling of hdof_trace); pass k draws its samples
+ * with the Philox key of frame (p->frame + k) mod 65536.  out: float
+ * [H][W][4] = (mean radiance over all passes x spp_max samples rgb, 0).
+ * workspace: hdof_workspace_bytes(width, height, p) bytes (the post-filter
+ * region holds each pass's trace output).  hint_tri as for hdof_trace. */
+int hdof_reference_rt(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
+                      int32_t passes, const int32_t* hint_tri, float* out, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Error map between two images a, b (float [H][W][4], rgb compared): err
+ * (may be NULL) float [H][W] = mean over rgb of |a - b|; stats: device
+ * double [HDOF_ERR_SCRATCH], whose first HDOF_ERR_STATS entries receive
+ * (pixels, sum |d|, sum d^2, max |d|) over all pixels, then the same over
+ * the pixels where region (uint8 [H][W], may be NULL) is non-zero; sums run
+ * over the three channels.  The rest is scratch.  Reduced in a fixed order:
+ * the same inputs give the same bits. */
+#define HDOF_ERR_STATS 8
+#define HDOF_ERR_SCRATCH (HDOF_ERR_STATS + 8 * 1024)
+int hdof_error_map(const float* a, const float* b, const uint8_t* region, int32_t width, int32_t height,
+                   float* err, double* stats, void* stream);
+
 /* ----------------------------------------------------- post-filter -- */
 /* CoC gather post-filter of the sharp image (Design section; the rejection
  * rule of the Reconstruction section).  Scatter-as-gather over soft disks

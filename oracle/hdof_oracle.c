@@ -1011,6 +1011,38 @@ void orc_trace_hits(const void* sp, const orc_camera* cam, const orc_lens* lens,
         }
 }
 
+/* Full ray-traced depth of field (the reference the paper's Fig. 1 sets
+ * beside the hybrid frame): the thin-lens image by distributed ray tracing,
+ * every pixel, no mask.  out[q] = mean Lambert radiance of the closest hits
+ * of passes x spp_max lens samples; pass k draws its samples with the key of
+ * frame (frame + k) mod 65536.  Misses contribute 0. */
+void orc_reference_rt(const void* sp, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
+                      int32_t passes, double* out) {
+    const oscene* s = (const oscene*)sp;
+    int32_t W = cam->width, H = cam->height;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t j = 0; j < H; ++j)
+        for (int32_t i = 0; i < W; ++i) {
+            size_t q = (size_t)j * W + i;
+            double S[3] = {0, 0, 0};
+            for (int32_t k = 0; k < passes; ++k) {
+                orc_params pk = *p;
+                pk.frame = (int32_t)(((uint32_t)p->frame + (uint32_t)k) & 0xFFFFu);
+                for (int smp = 0; smp < p->spp_max; ++smp) {
+                    double O[3], dir[3], th_, bary[3], n_[3], L[3];
+                    orc_lens_ray(cam, lens, &pk, (int64_t)q, smp, O, dir);
+                    int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
+                    if (id < 0) continue;
+                    shade_hit(s, id, bary, dir, p, n_, L);
+                    for (int c = 0; c < 3; ++c) S[c] += L[c];
+                }
+            }
+            double n = (double)passes * p->spp_max;
+            for (int c = 0; c < 3; ++c) out[4 * q + c] = S[c] / n;
+            out[4 * q + 3] = 0.0;
+        }
+}
+
 /* The trace accumulation (same definitions as orc_trace) from recorded hits;
  * P_far is not recorded and is left 0. */
 void orc_replay(int32_t W, int32_t H, const orc_lens* lens, double t, const uint8_t* spp, const int64_t* off,

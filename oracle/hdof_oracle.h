@@ -103,5 +103,7 @@ void orc_lens_ray(const orc_camera* cam, const orc_lens* lens, const orc_params*
                   double O[3], double dir[3]);
 void orc_trace_hits(const void* s, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
                     const uint8_t* spp, const int64_t* off, int32_t* ids, double* ts, double* margin);
+void orc_reference_rt(const void* s, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
+                      int32_t passes, double* out);
 int32_t orc_num_threads(void);
 #endif

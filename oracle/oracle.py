@@ -102,6 +102,7 @@ def lib():
         L.orc_replay.argtypes = [C.c_int32, C.c_int32, C.POINTER(Lens), C.c_double, up8, i64p, dp, dp]
         L.orc_temporal_frozen.argtypes = [C.c_int32, C.c_int32, C.POINTER(Params), dp, up8, dp, dp, dp, dp, up8]
         L.orc_disk_area.restype = C.c_double
+        L.orc_reference_rt.argtypes = [vp, C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), C.c_int32, dp]
         L.orc_lens_ray.argtypes = [C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), C.c_int64, C.c_int32, dp, dp]
         L.orc_trace_hits.argtypes = [vp, C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), up8, i64p, ip, dp, dp]
         _lib = L
@@ -364,6 +365,15 @@ def trace_records(oscene: OScene, cam_, lens_, params_, spp):
                             spp.ctypes.data_as(C.POINTER(C.c_uint8)), off.ctypes.data_as(C.POINTER(C.c_int64)),
                             _d(rec)[1])
     return rec, off
+
+
+def reference_rt(oscene: OScene, cam_, lens_, params_, passes):
+    """Full ray-traced thin-lens image [H,W,4]: mean radiance of passes x
+    spp_max lens samples per pixel (pass k keyed with frame + k)."""
+    out = np.empty((cam_.height, cam_.width, 4))
+    lib().orc_reference_rt(oscene.h, C.byref(cam(cam_)), C.byref(lens(lens_)), C.byref(params(params_)),
+                           int(passes), _d(out)[1])
+    return out
 
 
 def lens_ray(cam_, lens_, params_, q, smp):

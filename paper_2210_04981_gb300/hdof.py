@@ -119,6 +119,9 @@ def load():
         "hdof_profile": ([i32], C.c_int),
         "hdof_profile_read": ([P(hdof_kernel_time), i32], C.c_int),
         "hdof_probe_fma": ([i32, i32, vp, P(C.c_double), vp], C.c_int),
+        "hdof_reference_rt": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), i32, vp, vp, vp, sz, vp],
+                              C.c_int),
+        "hdof_error_map": ([vp, vp, vp, i32, i32, vp, vp, vp], C.c_int),
         "hdof_trace_hits": ([vp, P(hdof_camera), P(hdof_params), vp, vp, sz, vp, vp, vp], C.c_int),
         "hdof_postfilter": ([P(hdof_gbuf), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, sz, vp],
                             C.c_int),
@@ -150,7 +153,8 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["hdof_version", "hdof_last_error", "hdof_sync", "hdof_default_params", "hdof_build_bvh",
             "hdof_bvh_destroy", "hdof_bvh_info", "hdof_closest_hits", "hdof_gbuffer", "hdof_workspace_bytes",
-            "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_trace_hits", "hdof_postfilter", "hdof_reconstruct", "hdof_composite",
+            "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_trace_hits", "hdof_reference_rt", "hdof_error_map",
+            "hdof_postfilter", "hdof_reconstruct", "hdof_composite",
             "hdof_batch_create", "hdof_batch_update", "hdof_batch_render", "hdof_batch_render_range",
             "hdof_batch_destroy", "hdof_batch_bytes",
             "hdof_post_workspace_bytes", "hdof_post_forward", "hdof_post_backward", "hdof_profile",
@@ -381,6 +385,39 @@ def hdof_trace_hits(bvh: Bvh, cam, p, spp, workspace, ids, ts=None, stream=None)
     _check(load().hdof_trace_hits(bvh.handle, C.byref(camera(cam)), C.byref(params(p)), _ptr(spp),
                                   _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(ids),
                                   _ptr(ts), _stream(stream)))
+
+
+def hdof_reference_rt(bvh: Bvh, cam, lns, p, passes, out, workspace, hint=None, stream=None):
+    """Full ray-traced frame: mean radiance of passes x spp_max lens samples per pixel."""
+    _check(load().hdof_reference_rt(bvh.handle, C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)),
+                                    int(passes), _ptr(hint), _ptr(out), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+ERR_STATS, ERR_SCRATCH = 8, 8 + 8 * 1024
+
+
+def hdof_error_map(a, b, stats, region=None, err=None, stream=None):
+    """Per-pixel mean |a - b| over rgb into err (optional) and, into the
+    device double tensor stats [ERR_SCRATCH], the summary sums."""
+    Hh, W = a.shape[:2]
+    _check(load().hdof_error_map(_ptr(a), _ptr(b), _ptr(region), int(W), int(Hh), _ptr(err), _ptr(stats),
+                                 _stream(stream)))
+
+
+def error_summary(stats) -> dict:
+    """Mean absolute error, RMSE, PSNR (peak 1) and max |d| per channel, over
+    all pixels and over the region, from hdof_error_map's stats."""
+    v = stats[:ERR_STATS].double().cpu().tolist()
+
+    def one(n, s1, s2, mx):
+        if n <= 0:
+            return {"pixels": 0}
+        mse = s2 / (3 * n)
+        return {"pixels": int(n), "mae": s1 / (3 * n), "rmse": mse ** 0.5,
+                "psnr_db": (10 * math.log10(1.0 / mse)) if mse > 0 else float("inf"), "max": mx}
+
+    return {"all": one(*v[0:4]), "region": one(*v[4:8])}
 
 
 def hdof_postfilter(gbuf: GBuffer, cam, lns, p, pp, workspace, stream=None):

@@ -482,3 +482,53 @@ def test_fronto_plane_matches_exact_disk_convolution(orc):
     assert e1024[sig == 0].max(initial=0.0) < 1e-12
     e128 = np.abs(est[0] - exp_mean).mean()
     assert e1024.mean() < 0.6 * e128
+
+
+# ------------------------------------------- full ray-traced reference -----
+
+def test_reference_rt_of_a_plane_is_the_disk_convolution(orc):
+    """The full ray-traced frame of a fronto-parallel checker plane converges
+    to the exact disk convolution (passes x spp_max = 8 x 128 samples), within
+    4 sigma_p / sqrt(N) on >= 99% of pixels, as the trace's own estimate
+    does."""
+    z, zf, A = 1.0, 2.0, 0.2
+    W = H = 24
+    cam = hi.Camera(width=W, height=H).f32()
+    lens = hi.Lens(zf, A, 0.05).f32()
+    osc = orc.OScene(hi.plane_scene(z, half=50.0, cells=400.0))
+    t = cam.tan_half_fovy
+    c = lens.aperture_radius * H * (lens.focus_dist - z) / (z * lens.focus_dist * t)
+    p = hi.Params(spp_max=128)
+    irr = p.k_ambient + max(0.0, -p.unit_lights()[0][2])
+    exp_mean, sig = _exact_disk_average_checker(cam, z, c / 2, 400.0, 50.0,
+                                                (float(np.float32(0.2)), float(np.float32(0.8))), irr)
+    out = orc.reference_rt(osc, cam, lens, p, 8)
+    e = np.abs(out[..., 0] - exp_mean)
+    assert (e <= 4 * sig / math.sqrt(1024) + 1e-12).mean() >= 0.99
+    # the same samples as eight traces keyed frame 0..7 (pass k = frame k)
+    spp = np.full((H, W), 128, np.uint8)
+    est = np.mean([orc.trace(osc, cam, lens, p.replace(frame=k), spp)[..., 0] for k in range(8)], 0)
+    np.testing.assert_allclose(out[..., 0], est, atol=1e-12)
+
+
+def test_hybrid_is_closer_to_ray_tracing_than_post_processing(orc):
+    """The paper's claim (Abstract; Fig. 1) on the tiny scene: against the
+    full ray-traced frame (16 passes x 16 samples), after four frames of a
+    static camera, the hybrid frame's mean error on the traced pixels (the
+    blurry occluder's silhouette) is below half the post-process-only frame's
+    (the same composite with no traced pixels); elsewhere they are equal."""
+    scene, cam, lens, p = hi.tiny_config()
+    osc = orc.OScene(scene)
+    hist = None
+    for k in range(4):
+        r = orc.frame(osc, cam, cam, lens, p.replace(frame=k), hist=hist)
+        hist = r["hist"]
+    spp = r["mask"]["spp"]
+    pp_only = orc.composite(r["g"]["nd"], r["g"]["col"], np.zeros_like(spp), r["pp"], r["crt"], r["crec"],
+                            r["hacc"], lens, cam.tan_half_fovy, p, cam.height)
+    rt = orc.reference_rt(osc, cam, lens, p, 16)
+    tr = spp > 0
+    hyb = np.abs(r["out"][..., :3] - rt[..., :3])[tr].mean()
+    pp = np.abs(pp_only[..., :3] - rt[..., :3])[tr].mean()
+    assert hyb < 0.5 * pp, (hyb, pp)
+    assert np.array_equal(r["out"][~tr, :3], pp_only[~tr, :3])
