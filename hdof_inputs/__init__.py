@@ -96,6 +96,12 @@ class Params:
     kz_rel: float = 0.05
     # composite
     h_tau: float = 0.25
+    # extensions named as future work in the paper's Discussion (0 = off)
+    alpha_k: float = 0.0      # per-pixel temporal blend factor threshold (history std-devs)
+    mask_coc: int = 0         # edge tiles dilate over their largest CoC radius
+    blades: int = 0           # aperture polygon blades (0 = circle)
+    blade_rot: float = 0.0    # polygon rotation (radians)
+    aberration: float = 0.0   # radial weight of the lens samples, 1 + a (2 rho^2 / A^2 - 1)
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -99,6 +99,13 @@ typedef struct hdof_params {
     float kz_rel;        /* relative depth band of the far-field depth test */
     /* composite (Composite section) */
     float h_tau;         /* hit ratio above which far pixels take the post-process */
+    /* extensions the paper's Discussion names as future work; 0 = off */
+    float alpha_k;       /* per-pixel temporal blend factor: luminance change beyond alpha_k
+                            history std-devs raises the pixel's EMA weight towards 1 */
+    int32_t mask_coc;    /* 1: an edge tile's dilation reaches its pixels' largest CoC radius */
+    int32_t blades;      /* aperture: 0 = circle, 3..16 = regular polygon of that many blades */
+    float blade_rot;     /* polygon rotation, radians */
+    float aberration;    /* lens sample weight 1 + aberration (2 rho^2 / A^2 - 1), in [-1, 1] */
 } hdof_params;
 
 /* G-buffer of one frame.  nd: (nx, ny, nz, z) per pixel, n the geometric
@@ -366,7 +373,13 @@ int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, const hdof_lens
  * terms and moments reprojected by mv, far terms by the previous-frame
  * projection of the far position (own far hits, else the 3x3 neighbours',
  * else the G-buffer point); bilinear over taps with history, invalid below
- * weight 1e-3; EMA with ema_alpha; layer colours normalised by their
+ * weight 1e-3; EMA with ema_alpha, or with alpha_k > 0 a per-pixel weight
+ * (the Discussion's per-pixel blend factors against ghosting): lambda = the
+ * larger of clamp((|Y - mu1| - alpha_k sigma_L) / max(Y, mu1, 1e-3), 0, 1)
+ * (this frame's ray-traced luminance Y against the reprojected history
+ * moments) and clamp(|h - B_near| - alpha_k sqrt(B_near (1 - B_near) / spp),
+ * 0, 1) (the hit ratio against its reprojected EMA), alpha = ema_alpha +
+ * (1 - ema_alpha) lambda; layer colours normalised by their
  * accumulated hit ratio; composed with this frame's hit ratio when
  * camera_moved, else the accumulated one; CoC = H_acc c_near + (1-H_acc)
  * c_far.  Spatial: for traced pixels, gather of traced neighbours with
@@ -507,7 +520,9 @@ int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const float* rec,
  * grad_lens (device float [2] = d/d focus_dist, d/d aperture_radius).  Gather
  * weights are recomputed, not stored; the lens gradient is reduced per block
  * in double precision and summed in a fixed order (deterministic).  Needs
- * aperture_radius > 0. */
+ * aperture_radius > 0.  Both calls take the fixed EMA weight and the uniform
+ * circular lens: alpha_k, blades and aberration other than 0 return
+ * HDOF_EUNSUPPORTED. */
 int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
                        const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
                        const hdof_params* p, const hdof_post_state* st, const float* grad_out,

@@ -682,7 +682,6 @@ void orc_temporal(const orc_camera* cam, const orc_camera* prev, const orc_param
                   const uint8_t* h_hlen, double* o_near, double* o_far, double* o_mom,
                   uint8_t* o_hlen, double* crt, double* hacc) {
     int32_t W = cam->width, H = cam->height;
-    double al = p->ema_alpha;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t j = 0; j < H; ++j)
         for (int32_t i = 0; i < W; ++i) {
@@ -736,6 +735,22 @@ void orc_temporal(const orc_camera* cam, const orc_camera* prev, const orc_param
             }
             double uf[2], hf[4];
             int vf_ok = orc_project(prev, P, uf) && hist_bilinear(W, H, uf[0], uf[1], h_hlen, h_far, 4, hf, NULL);
+            /* EMA weight: fixed, or per pixel (Discussion: per-pixel blend factors against ghosting, after
+             * Schied et al.'s gradient-estimated temporal filtering): the normalised temporal gradient
+             * lambda = clamp((|Y - mu1| - alpha_k sigma_L) / max(Y, mu1, 1e-3), 0, 1) of this frame's
+             * luminance against the reprojected history, whose per-frame spread sigma_L counts as noise;
+             * alpha = alpha_min + (1 - alpha_min) lambda */
+            double al = p->ema_alpha;
+            if (p->alpha_k > 0.0 && vn_ok) {
+                double sg = sqrt(fmax(0.0, hm[1] - hm[0] * hm[0]));
+                double den = fmax(fmax(Y, hm[0]), 1e-3);
+                double lam = clampd((fabs(Y - hm[0]) - p->alpha_k * sg) / den, 0.0, 1.0);
+                /* the hit ratio's change beyond alpha_k binomial standard errors of n samples */
+                double hb = hn[3], se = sqrt(fmax(hb * (1.0 - hb), 0.0) / spp[q]);
+                double lh = clampd(fabs(h - hb) - p->alpha_k * se, 0.0, 1.0);
+                if (lh > lam) lam = lh;
+                al += (1.0 - al) * lam;
+            }
             /* EMA */
             double cur_n[4] = {h * r[0], h * r[1], h * r[2], h};
             double cur_f[4] = {(1 - h) * r[4], (1 - h) * r[5], (1 - h) * r[6], 1 - h};

@@ -46,6 +46,9 @@ typedef struct {
     double r_s, var_ref;
     double r_max, kz_rel;
     double h_tau;
+    double alpha_k;
+    int32_t mask_coc, blades;
+    double blade_rot, aberration;
 } orc_params;
 
 /* ---- counter-based RNG (Philox4x32-10, Salmon et al. SC'11) ---- */

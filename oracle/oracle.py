@@ -53,7 +53,8 @@ class Params(C.Structure):
                 ("light_dir", (C.c_double * 3) * 4), ("light_E", C.c_double * 4),
                 ("miss_dist", C.c_double), ("ema_alpha", C.c_double), ("camera_moved", C.c_int32),
                 ("r_s", C.c_double), ("var_ref", C.c_double), ("r_max", C.c_double),
-                ("kz_rel", C.c_double), ("h_tau", C.c_double)]
+                ("kz_rel", C.c_double), ("h_tau", C.c_double), ("alpha_k", C.c_double), ("mask_coc", C.c_int32),
+                ("blades", C.c_int32), ("blade_rot", C.c_double), ("aberration", C.c_double)]
 
 
 _lib = None
@@ -148,7 +149,8 @@ def params(p) -> Params:
     o = Params()
     for name in ("gauss_sigma", "edge_tau", "tile", "dilate", "spp_max", "variance_on", "var_tau",
                  "var_scale", "hlen_young", "seed", "frame", "view", "k_ambient", "miss_dist",
-                 "ema_alpha", "camera_moved", "r_s", "var_ref", "r_max", "kz_rel", "h_tau"):
+                 "ema_alpha", "camera_moved", "r_s", "var_ref", "r_max", "kz_rel", "h_tau", "alpha_k", "mask_coc",
+                 "blades", "blade_rot", "aberration"):
         setattr(o, name, getattr(p, name))
     lights = p.unit_lights()
     o.n_lights = len(lights)

@@ -775,6 +775,11 @@ int check_post(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const 
                        st->pp_aux && st->out,
                    "%s: every state buffer is required", who);
     HDOF_CHECK_ARG(lens->aperture_radius > 0.f, "%s: the lens gradient needs an aperture > 0", who);
+    if (p->alpha_k != 0.f || p->blades != 0 || p->aberration != 0.f) {
+        set_error("%s: the differentiable path takes the fixed EMA weight and the uniform circular lens "
+                  "(alpha_k, blades and aberration must be 0)", who);
+        return HDOF_EUNSUPPORTED;
+    }
     return HDOF_OK;
 }
 

@@ -78,6 +78,12 @@ int check_params(const hdof_params* p, const char* who) {
     HDOF_CHECK_ARG(p->trav_cap >= 0, "%s: trav_cap must be >= 0", who);
     HDOF_CHECK_ARG(p->frame >= 0 && p->frame < 65536 && p->view >= 0 && p->view < 65536,
                    "%s: frame and view must be 0..65535", who);
+    HDOF_CHECK_ARG(std::isfinite(p->alpha_k) && p->alpha_k >= 0.f, "%s: alpha_k must be >= 0", who);
+    HDOF_CHECK_ARG(p->mask_coc == 0 || p->mask_coc == 1, "%s: mask_coc must be 0 or 1", who);
+    HDOF_CHECK_ARG(p->blades == 0 || (p->blades >= 3 && p->blades <= 16), "%s: blades must be 0 or 3..16", who);
+    HDOF_CHECK_ARG(std::isfinite(p->blade_rot) && std::isfinite(p->aberration) && p->aberration >= -1.f &&
+                       p->aberration <= 1.f,
+                   "%s: blade_rot must be finite and aberration in [-1, 1]", who);
     return HDOF_OK;
 }
 

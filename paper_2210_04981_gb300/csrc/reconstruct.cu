@@ -25,7 +25,7 @@ namespace {
 struct TemporalArgs {
     Cam cam, prev;
     int W, H;
-    float alpha;
+    float alpha, alpha_k;  // EMA weight; per-pixel blend factor threshold (0 = fixed weight)
     int moved;
     const float4* rt;  // 3 per pixel
     const uint8_t* spp;
@@ -147,8 +147,21 @@ __device__ __forceinline__ void temporal_body(const TemporalArgs& a, const ND* _
     float uf, vf;
     float4 hf;
     bool vf_ok = project(a.prev, P, uf, vf) && hist_sample(a, uf, vf, a.hf, hf, (int*)nullptr);
-    // EMA
-    const float al = a.alpha;
+    // EMA weight: fixed, or per pixel from the temporal gradient (the paper's
+    // per-pixel blend factors against ghosting): the larger of this frame's
+    // luminance change against the reprojected history beyond alpha_k of its
+    // per-frame spread (relative to the larger luminance) and the hit ratio's
+    // change beyond alpha_k binomial standard errors; alpha rises towards 1
+    float al = a.alpha;
+    if (a.alpha_k > 0.f && vn_ok) {
+        const float sg = sqrtf(fmaxf(0.f, hm.y - hm.x * hm.x));
+        const float den = fmaxf(fmaxf(Y, hm.x), 1e-3f);
+        float lam = fminf(fmaxf((fabsf(Y - hm.x) - a.alpha_k * sg) / den, 0.f), 1.f);
+        const float hb = hn.w, se = sqrtf(fmaxf(hb * (1.f - hb), 0.f) / (float)a.spp[q]);
+        const float lh = fminf(fmaxf(fabsf(h - hb) - a.alpha_k * se, 0.f), 1.f);
+        lam = fmaxf(lam, lh);
+        al = fmaf(1.f - al, lam, al);
+    }
     float4 cur_n = make_float4(h * Cn.x, h * Cn.y, h * Cn.z, h);
     float4 cur_f = make_float4((1.f - h) * Cf.x, (1.f - h) * Cf.y, (1.f - h) * Cf.z, 1.f - h);
     float4 on = vn_ok ? make_float4(fmaf(al, cur_n.x - hn.x, hn.x), fmaf(al, cur_n.y - hn.y, hn.y),
@@ -294,6 +307,7 @@ TemporalArgs temporal_args(const float* rt, const hdof_gbuf* in, const uint8_t* 
     a.W = cam->width;
     a.H = cam->height;
     a.alpha = p->ema_alpha;
+    a.alpha_k = p->alpha_k;
     a.moved = p->camera_moved;
     a.rt = reinterpret_cast<const float4*>(rt);
     a.spp = spp;

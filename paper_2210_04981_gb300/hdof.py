@@ -48,7 +48,9 @@ class hdof_params(C.Structure):
                 ("light_dir", (C.c_float * 3) * 4), ("light_E", C.c_float * 4),
                 ("miss_dist", C.c_float), ("trav_cap", C.c_int32), ("ema_alpha", C.c_float),
                 ("camera_moved", C.c_int32), ("r_s", C.c_float), ("var_ref", C.c_float),
-                ("r_max", C.c_float), ("kz_rel", C.c_float), ("h_tau", C.c_float)]
+                ("r_max", C.c_float), ("kz_rel", C.c_float), ("h_tau", C.c_float),
+                ("alpha_k", C.c_float), ("mask_coc", C.c_int32), ("blades", C.c_int32), ("blade_rot", C.c_float),
+                ("aberration", C.c_float)]
 
 
 class hdof_gbuf(C.Structure):
@@ -206,7 +208,8 @@ def lens(l) -> hdof_lens:
 
 _PARAM_NAMES = ("gauss_sigma", "edge_tau", "tile", "dilate", "spp_max", "variance_on", "var_tau", "var_scale",
                 "hlen_young", "seed", "frame", "view", "k_ambient", "miss_dist", "trav_cap", "ema_alpha",
-                "camera_moved", "r_s", "var_ref", "r_max", "kz_rel", "h_tau")
+                "camera_moved", "r_s", "var_ref", "r_max", "kz_rel", "h_tau", "alpha_k", "mask_coc", "blades",
+                "blade_rot", "aberration")
 
 
 def params(p=None) -> hdof_params:

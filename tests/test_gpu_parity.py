@@ -432,11 +432,14 @@ def _reconstruct_inputs(W, Hh, seed):
     return spp, cam0, cam1, rt, gb, hist
 
 
-@pytest.mark.parametrize("seed,W,Hh,moved", [(0, 96, 64, 1), (1, 131, 77, 0)])
-def test_reconstruct(orc, seed, W, Hh, moved):
+@pytest.mark.parametrize("seed,W,Hh,moved,alpha_k", [(0, 96, 64, 1, 0.0), (1, 131, 77, 0, 0.0), (2, 120, 70, 1, 1.0),
+                                                     (3, 64, 48, 0, 0.5)])
+def test_reconstruct(orc, seed, W, Hh, moved, alpha_k):
+    """Temporal + spatial reconstruction against the oracle, with the fixed
+    EMA weight and with per-pixel blend factors (alpha_k > 0)."""
     spp, cam0, cam1, rt, gb, hist = _reconstruct_inputs(W, Hh, seed)
     lens = hi.Lens(3.0, 0.02, 0.05).f32()
-    p = hi.room_params(camera_moved=moved, r_s=8.0)
+    p = hi.room_params(camera_moved=moved, r_s=8.0, alpha_k=alpha_k)
     hin = history_from(hist)
     hout = H.History(W, Hh)
     crt = torch.empty((Hh, W, 4), dtype=torch.float32, device="cuda")

@@ -532,3 +532,60 @@ def test_hybrid_is_closer_to_ray_tracing_than_post_processing(orc):
     pp = np.abs(pp_only[..., :3] - rt[..., :3])[tr].mean()
     assert hyb < 0.5 * pp, (hyb, pp)
     assert np.array_equal(r["out"][~tr, :3], pp_only[~tr, :3])
+
+
+# --------------------------------------- per-pixel temporal blend factor ----
+
+def _one_pixel_temporal(orc, h, grey, hist_B, hist_grey, mu1, sigma, spp_n, alpha_k):
+    """A 3x3 static frame whose pixels are all traced alike: this frame's
+    layers both grey `grey` with hit ratio h, the history's near layer (B,
+    B hist_grey) and moments (mu1, mu1^2 + sigma^2); returns the centre
+    pixel's new near history and the trace record."""
+    W = H = 3
+    cam = hi.Camera(width=W, height=H)
+    spp = np.full((H, W), spp_n, np.uint8)
+    rt = np.zeros((H, W, 12))
+    rt[..., 0:3] = grey
+    rt[..., 3] = h
+    rt[..., 4:7] = grey
+    rt[..., 7] = 4.0
+    rt[..., 11] = 1.0
+    for j in range(H):
+        for i in range(W):
+            d = orc.pinhole_dir(cam, i + 0.5, j + 0.5)
+            rt[j, i, 8:11] = 3.0 * d
+    hist = orc.empty_history(W, H)
+    hist["near"][..., :3] = hist_B * hist_grey
+    hist["near"][..., 3] = hist_B
+    hist["far"][..., :3] = (1 - hist_B) * hist_grey
+    hist["far"][..., 3] = 1 - hist_B
+    hist["mom"][..., 0] = mu1
+    hist["mom"][..., 1] = mu1 * mu1 + sigma * sigma
+    hist["hlen"][:] = 6
+    g = hi.random_gbuffer(W, H, seed=0)
+    p = hi.Params(ema_alpha=0.2, alpha_k=alpha_k)
+    out, _, _ = orc.temporal(cam, cam, p, rt, spp, g["nd"], np.zeros((H, W, 2)), hist)
+    return out["near"][1, 1], rt[1, 1]
+
+
+@pytest.mark.parametrize("case", ["luminance", "hit_ratio", "noise", "off"])
+def test_temporal_per_pixel_blend_factor(orc, case):
+    """alpha = alpha_min + (1 - alpha_min) lambda with lambda the larger of
+    the luminance change beyond alpha_k history std-devs (relative to the
+    larger luminance) and the hit-ratio change beyond alpha_k binomial
+    standard errors; the near history moves by alpha towards this frame."""
+    if case == "luminance":   # Y 0.8 against mu1 0.5, sigma 0.01: (0.3 - 0.02) / 0.8 = 0.35
+        args, lam = dict(h=0.5, grey=0.8, hist_B=0.5, hist_grey=0.5, mu1=0.5, sigma=0.01, spp_n=4, alpha_k=2.0), 0.35
+    elif case == "hit_ratio":  # h 0.9 against B 0.1 at 4 samples: 0.8 - 2 sqrt(0.09 / 4) = 0.5
+        args, lam = dict(h=0.9, grey=0.6, hist_B=0.1, hist_grey=0.6, mu1=0.6, sigma=0.0, spp_n=4, alpha_k=2.0), 0.5
+    elif case == "noise":      # both changes inside the noise bands
+        args, lam = dict(h=0.5, grey=0.52, hist_B=0.45, hist_grey=0.5, mu1=0.5, sigma=0.02, spp_n=4,
+                         alpha_k=2.0), 0.0
+    else:                      # alpha_k = 0: the fixed weight, whatever the change
+        args, lam = dict(h=0.9, grey=0.8, hist_B=0.1, hist_grey=0.5, mu1=0.5, sigma=0.0, spp_n=4, alpha_k=0.0), 0.0
+    near, r = _one_pixel_temporal(orc, **args)
+    al = 0.2 + 0.8 * lam
+    B = args["hist_B"]
+    hn = np.array([B * args["hist_grey"]] * 3 + [B])
+    cur = np.array([r[3] * r[0], r[3] * r[1], r[3] * r[2], r[3]])
+    np.testing.assert_allclose(near, hn + al * (cur - hn), atol=1e-12)
