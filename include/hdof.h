@@ -248,6 +248,20 @@ size_t hdof_workspace_bytes(int32_t width, int32_t height, const hdof_params* p)
 int hdof_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p,
               uint8_t* edge, uint8_t* spp, void* workspace, size_t workspace_bytes, void* stream);
 
+/* hdof_mask with the ray mask's reach scaled by the CoC (the Discussion's
+ * mask resolution scaled by the maximum CoC, against tiling artifacts).
+ * With p->mask_coc = 1, each mask tile holding an edge covers the tiles
+ * within max(dilate, ceil(r / tile)) tiles of it (Chebyshev distance, at
+ * most 8), r = the largest min(|c(z)| / 2, r_max) over the tile's pixels
+ * (G-buffer depth, the lens's CoC): every pixel within the blur radius of an
+ * edge tile is traced.  With p->mask_coc = 0 it computes what hdof_mask does.
+ * cam gives the CoC's image height and tan(fovy/2).  The workspace holds the
+ * tile flags and one float per tile (hdof_workspace_bytes covers both).
+ * hdof_mask and hdof_mask_noalloc reject mask_coc = 1 (they take no lens). */
+int hdof_mask_coc(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_camera* cam, const hdof_lens* lens,
+                  const hdof_params* p, uint8_t* edge, uint8_t* spp, void* workspace, size_t workspace_bytes,
+                  void* stream);
+
 /* hdof_mask without caller scratch memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * for the library -- for instance a real-time render thread that must not

@@ -448,9 +448,12 @@ void orc_gaussian_weights(double sigma, double w[5]) {
 
 static int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-void orc_mask(int32_t W, int32_t H, const double* nd, const double* mv, const double* hist_mom,
-              const uint8_t* hist_hlen, const orc_params* p, uint8_t* edge, uint8_t* spp,
-              double* emetric) {
+/* lens, t: the CoC-scaled mask (p->mask_coc = 1; the Discussion's mask resolution scaled by the CoC):
+ * an edge tile reaches max(dilate, ceil(r / tile)) tiles (Chebyshev distance, at most 8), r = the
+ * largest min(|c(z)| / 2, r_max) over its pixels; lens = NULL: every edge tile reaches `dilate` tiles. */
+static void mask_impl(int32_t W, int32_t H, const double* nd, const double* mv, const double* hist_mom,
+                      const uint8_t* hist_hlen, const orc_params* p, const orc_lens* lens, double t, uint8_t* edge,
+                      uint8_t* spp, double* emetric) {
     size_t N = (size_t)W * H;
     double g[5];
     orc_gaussian_weights(p->gauss_sigma, g);
@@ -496,20 +499,41 @@ void orc_mask(int32_t W, int32_t H, const double* nd, const double* mv, const do
             if (emetric) emetric[pix] = e;
             edge[pix] = e > p->edge_tau ? 1 : 0;
         }
-    /* tile OR, then dilation by `dilate` tiles in each direction */
+    /* tile OR; each edge tile's reach in tiles (fixed `dilate`, or from its pixels' largest CoC radius) */
     int32_t T = p->tile, ntx = (W + T - 1) / T, nty = (H + T - 1) / T;
     uint8_t* ton = (uint8_t*)calloc((size_t)ntx * nty, 1);
+    int* reach = (int*)malloc(sizeof(int) * (size_t)ntx * nty);
+    double* rt_ = (double*)calloc((size_t)ntx * nty, sizeof(double));
     for (int32_t j = 0; j < H; ++j)
-        for (int32_t i = 0; i < W; ++i)
-            if (edge[(size_t)j * W + i]) ton[(size_t)(j / T) * ntx + i / T] = 1;
+        for (int32_t i = 0; i < W; ++i) {
+            size_t k = (size_t)(j / T) * ntx + i / T;
+            if (edge[(size_t)j * W + i]) ton[k] = 1;
+            if (lens && p->mask_coc) {
+                double r = fmin(fabs(orc_coc(nd[4 * ((size_t)j * W + i) + 3], lens, H, t)) * 0.5, p->r_max);
+                if (r > rt_[k]) rt_[k] = r;
+            }
+        }
+    for (size_t k = 0; k < (size_t)ntx * nty; ++k) {
+        int rc = p->dilate;
+        if (lens && p->mask_coc) {
+            int c = (int)ceil(rt_[k] / T);
+            if (c > rc) rc = c;
+            if (rc > 8) rc = 8;
+        }
+        reach[k] = rc;
+    }
+    int dmax = (lens && p->mask_coc) ? 8 : p->dilate;
     for (int32_t j = 0; j < H; ++j)
         for (int32_t i = 0; i < W; ++i) {
             size_t pix = (size_t)j * W + i;
             int tx = i / T, ty = j / T, on = 0;
-            for (int b = -p->dilate; b <= p->dilate && !on; ++b)
-                for (int a = -p->dilate; a <= p->dilate; ++a) {
+            for (int b = -dmax; b <= dmax && !on; ++b)
+                for (int a = -dmax; a <= dmax; ++a) {
                     int x = tx + a, y = ty + b;
-                    if (x >= 0 && y >= 0 && x < ntx && y < nty && ton[(size_t)y * ntx + x]) { on = 1; break; }
+                    if (x < 0 || y < 0 || x >= ntx || y >= nty) continue;
+                    size_t k = (size_t)y * ntx + x;
+                    int cheb = abs(a) > abs(b) ? abs(a) : abs(b);
+                    if (ton[k] && cheb <= reach[k]) { on = 1; break; }
                 }
             int s = on ? p->spp_max : 0;
             if (!on && p->variance_on && hist_hlen && hist_mom) {
@@ -537,7 +561,20 @@ void orc_mask(int32_t W, int32_t H, const double* nd, const double* mv, const do
             spp[pix] = (uint8_t)s;
         }
     free(ton);
+    free(reach);
+    free(rt_);
     free(f);
+}
+
+void orc_mask(int32_t W, int32_t H, const double* nd, const double* mv, const double* hist_mom,
+              const uint8_t* hist_hlen, const orc_params* p, uint8_t* edge, uint8_t* spp, double* emetric) {
+    mask_impl(W, H, nd, mv, hist_mom, hist_hlen, p, NULL, 0.0, edge, spp, emetric);
+}
+
+void orc_mask_coc(int32_t W, int32_t H, const double* nd, const double* mv, const double* hist_mom,
+                  const uint8_t* hist_hlen, const orc_params* p, const orc_lens* lens, double tan_half_fovy,
+                  uint8_t* edge, uint8_t* spp, double* emetric) {
+    mask_impl(W, H, nd, mv, hist_mom, hist_hlen, p, lens, tan_half_fovy, edge, spp, emetric);
 }
 
 /* ------------------------------------------------------------------------

@@ -77,6 +77,9 @@ void orc_gaussian_weights(double sigma, double w[5]);
 void orc_mask(int32_t W, int32_t H, const double* nd, const double* mv, const double* hist_mom,
               const uint8_t* hist_hlen, const orc_params* p, uint8_t* edge, uint8_t* spp,
               double* emetric);
+void orc_mask_coc(int32_t W, int32_t H, const double* nd, const double* mv, const double* hist_mom,
+                  const uint8_t* hist_hlen, const orc_params* p, const orc_lens* lens, double tan_half_fovy,
+                  uint8_t* edge, uint8_t* spp, double* emetric);
 void orc_trace(const void* s, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
                const uint8_t* spp, double* rt, int32_t n_pix, const int32_t* pix);
 void orc_temporal(const orc_camera* cam, const orc_camera* prev, const orc_params* p,

@@ -86,6 +86,8 @@ def lib():
         L.orc_gbuffer.argtypes = [vp, C.POINTER(Cam), C.POINTER(Cam), C.POINTER(Params), dp, dp, dp, ip]
         L.orc_gaussian_weights.argtypes = [C.c_double, dp]
         L.orc_mask.argtypes = [C.c_int32, C.c_int32, dp, dp, dp, up8, C.POINTER(Params), up8, up8, dp]
+        L.orc_mask_coc.argtypes = [C.c_int32, C.c_int32, dp, dp, dp, up8, C.POINTER(Params), C.POINTER(Lens),
+                                   C.c_double, up8, up8, dp]
         L.orc_trace.argtypes = [vp, C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), up8, dp,
                                 C.c_int32, ip]
         L.orc_temporal.argtypes = [C.POINTER(Cam), C.POINTER(Cam), C.POINTER(Params), dp, up8, dp, dp,
@@ -228,7 +230,9 @@ def gbuffer(oscene: OScene, cam_, prev_cam, params_):
     return dict(nd=nd, col=col, mv=mv, tri=tri)
 
 
-def mask(nd, mv, params_, hist_mom=None, hist_hlen=None):
+def mask(nd, mv, params_, hist_mom=None, hist_hlen=None, lens_=None, tan_half_fovy=None):
+    """Edge bits, spp and the edge metric; with lens_ (and tan_half_fovy) the
+    CoC-scaled mask of params_.mask_coc."""
     H, W = nd.shape[:2]
     nd, pnd = _d(nd)
     mv, pmv = _d(mv)
@@ -240,8 +244,12 @@ def mask(nd, mv, params_, hist_mom=None, hist_hlen=None):
         hh, phh = _u8(hist_hlen)
     else:
         phm, phh = None, None
-    lib().orc_mask(W, H, pnd, pmv, phm, phh, C.byref(params(params_)), _u8(edge)[1], _u8(spp)[1],
-                   _d(em)[1])
+    if lens_ is None:
+        lib().orc_mask(W, H, pnd, pmv, phm, phh, C.byref(params(params_)), _u8(edge)[1], _u8(spp)[1],
+                       _d(em)[1])
+    else:
+        lib().orc_mask_coc(W, H, pnd, pmv, phm, phh, C.byref(params(params_)), C.byref(lens(lens_)),
+                           float(tan_half_fovy), _u8(edge)[1], _u8(spp)[1], _d(em)[1])
     return dict(edge=edge, spp=spp, emetric=em)
 
 
@@ -333,7 +341,7 @@ def frame(oscene, cam_, prev_cam, lens_, params_, hist=None, pp_pix=None):
     g = gbuffer(oscene, cam_, prev_cam, params_)
     if hist is None:
         hist = empty_history(W, H)
-    m = mask(g["nd"], g["mv"], params_, hist["mom"], hist["hlen"])
+    m = mask(g["nd"], g["mv"], params_, hist["mom"], hist["hlen"], lens_, cam_.tan_half_fovy)
     rt = trace(oscene, cam_, lens_, params_, m["spp"])
     newh, crt, hacc = temporal(cam_, prev_cam, params_, rt, m["spp"], g["nd"], g["mv"], hist)
     crec = spatial(params_, crt, m["spp"], newh["mom"], newh["hlen"])

@@ -121,6 +121,7 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     size_t mtiles = (size_t)((W + T - 1) / T) * ((H + T - 1) / T);
     size_t ptiles = (size_t)((W + HDOF_TILE_PF - 1) / HDOF_TILE_PF) * ((H + HDOF_TILE_PF - 1) / HDOF_TILE_PF);
     l.mask_tiles = align256(mtiles);
+    l.mask_tile_r = align256(mtiles * sizeof(float));
     size_t nray = npx * (size_t)(p ? p->spp_max : 16);
     l.trace_counts = align256(ptiles * 4 * sizeof(unsigned) + 4 * sizeof(unsigned));
     l.trace_queue = align256(npx * sizeof(unsigned));
@@ -136,7 +137,8 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     l.pf_tiles = align256(ptiles * sizeof(float4));
     l.pf_pre = align256(npx * sizeof(float4));
     l.pf = l.pf_nrec + l.pf_frec + l.pf_rh + l.pf_zq + l.pf_tiles + l.pf_pre;
-    l.pf_off = align256(l.mask_tiles > l.trace ? l.mask_tiles : l.trace);
+    const size_t mask = l.mask_tiles + l.mask_tile_r;
+    l.pf_off = align256(mask > l.trace ? mask : l.trace);
     l.total = l.pf_off + l.pf;
     return l;
 }

@@ -143,6 +143,10 @@ int fill_image(const hdof_view* views, int n, unsigned* st, const Layout& L, cha
         z.ptr = w.tiles;
         z.bytes = (unsigned long long)((views[v].cam.width + p.tile - 1) / p.tile) *
                   (unsigned long long)((views[v].cam.height + p.tile - 1) / p.tile);
+        if (p.mask_coc) {  // the per-tile radii follow the flags (and their padding)
+            const WsLayout Lv = ws_layout(views[v].cam.width, views[v].cam.height, &p);
+            z.bytes = Lv.mask_tiles + z.bytes * sizeof(float);
+        }
         std::memcpy(img + L.zero + (size_t)v * sizeof(ZeroRec), &z, sizeof z);
     }
     return HDOF_OK;

@@ -53,6 +53,7 @@ __device__ __forceinline__ const T& batch_record(const T* __restrict__ tab, int 
 // run one after another, so their regions overlap as they do there)
 struct ViewWs {
     uint8_t* tiles;      // mask tile flags
+    float* tile_r;       // largest CoC radius per mask tile (CoC-scaled mask)
     unsigned* counts;    // [2 * ntiles] traced pixels, rays per 16x16 tile
     unsigned* offsets;   // [ntiles]
     unsigned* roffsets;  // [ntiles]
@@ -87,6 +88,7 @@ inline ViewWs view_ws(const hdof_view& v) {
     char* base = static_cast<char*>(v.workspace);
     ViewWs w;
     w.tiles = reinterpret_cast<uint8_t*>(base);
+    w.tile_r = reinterpret_cast<float*>(base + L.mask_tiles);
     w.counts = reinterpret_cast<unsigned*>(base);
     w.offsets = w.counts + 2 * ntiles;
     w.roffsets = w.offsets + ntiles;

@@ -69,6 +69,7 @@ unsigned* status_ptr();
 // workspace layout (bytes) for a width x height frame
 struct WsLayout {
     size_t mask_tiles;      // uint8 per mask tile
+    size_t mask_tile_r;     // float per mask tile: largest CoC radius of its pixels (CoC-scaled mask)
     size_t trace_counts;    // uint32 per 16x16 tile: traced pixels, rays; + scan output
     size_t trace_queue;     // uint32 per pixel: traced pixels in queue order
     size_t trace_qoff;      // uint32 per pixel: first ray of each queue entry

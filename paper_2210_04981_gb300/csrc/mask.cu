@@ -37,6 +37,9 @@ struct EdgeArgs {
     int tile, ntx;
     uint8_t* edge;
     uint8_t* tiles;
+    Coc coc;        // CoC-scaled mask: the lens's CoC in pixels
+    float rmax;     // CoC radius cap (the post-filter's r_max)
+    float* tile_r;  // largest CoC radius per mask tile (atomic max of float bits); NULL: fixed dilation
 };
 
 template <class ND>
@@ -59,6 +62,27 @@ __device__ __forceinline__ void mask_edge_body(const EdgeArgs<ND>& ar, int bx, i
         src[r][c] = ld4(nd + (size_t)y * W + x);
     }
     __syncthreads();
+    if (ar.tile_r) {
+        // largest CoC radius min(|c(z)| / 2, r_max) of each mask tile's pixels:
+        // a shared-memory maximum per tile this block touches, then one global
+        // atomic maximum per tile (non-negative floats order as their bits)
+        __shared__ unsigned s_r[B][B];
+        const int tx0 = x0 / tile, ty0 = y0 / tile;
+        s_r[tid >> 4][tid & 15] = 0u;
+        __syncthreads();
+        const int i = x0 + (tid & 15), j = y0 + (tid >> 4);
+        if (i < W && j < H) {
+            const float r = fminf(fabsf(ar.coc(src[(tid >> 4) + HALO][(tid & 15) + HALO].w)) * 0.5f, ar.rmax);
+            atomicMax(&s_r[j / tile - ty0][i / tile - tx0], __float_as_uint(r));
+        }
+        __syncthreads();
+        const int nbx = min(x0 + B - 1, W - 1) / tile - tx0 + 1, nby = min(y0 + B - 1, H - 1) / tile - ty0 + 1;
+        if (tid < nbx * nby) {
+            const int a = tid % nbx, b = tid / nbx;
+            const unsigned v = s_r[b][a];
+            if (v) atomicMax(reinterpret_cast<unsigned*>(ar.tile_r) + (ty0 + b) * ntx + tx0 + a, v);
+        }
+    }
     // row pass: filtered columns x0-1 .. x0+16 for all 22 staged rows
     for (int k = tid; k < SRC * FIL; k += 256) {
         int r = k / FIL, c = k % FIL;
@@ -138,6 +162,7 @@ struct SppArgs {
     float var_tau, var_scale;
     int hlen_young;
     uint8_t* spp;
+    const float* tile_r;  // CoC-scaled mask: largest CoC radius per tile; NULL: fixed dilation
 };
 
 __device__ __forceinline__ void mask_spp_body(const SppArgs& ar, int bx, int by) {
@@ -160,12 +185,28 @@ __device__ __forceinline__ void mask_spp_body(const SppArgs& ar, int bx, int by)
         if (ey < nty_b && ex < ntx_b) {
             const int tx = tx0 + ex, ty = ty0 + ey;
             bool any = false;
-            for (int b = max(ty - dil, 0); b <= min(ty + dil, nty - 1) && !any; ++b)
-                for (int a = max(tx - dil, 0); a <= min(tx + dil, ntx - 1); ++a)
-                    if (__ldg(&tiles[b * ntx + a])) {
-                        any = true;
-                        break;
+            if (!ar.tile_r) {
+                for (int b = max(ty - dil, 0); b <= min(ty + dil, nty - 1) && !any; ++b)
+                    for (int a = max(tx - dil, 0); a <= min(tx + dil, ntx - 1); ++a)
+                        if (__ldg(&tiles[b * ntx + a])) {
+                            any = true;
+                            break;
+                        }
+            } else {
+                // an edge tile reaches max(dil, ceil(r / tile)) tiles (at most 8),
+                // r its pixels' largest CoC radius
+                const float inv_tile = 1.f / (float)tile;
+                for (int b = max(ty - 8, 0); b <= min(ty + 8, nty - 1) && !any; ++b)
+                    for (int a = max(tx - 8, 0); a <= min(tx + 8, ntx - 1); ++a) {
+                        if (!__ldg(&tiles[b * ntx + a])) continue;
+                        const int reach =
+                            min(8, max(dil, (int)ceilf(__ldg(&ar.tile_r[b * ntx + a]) * inv_tile)));
+                        if (max(abs(a - tx), abs(b - ty)) <= reach) {
+                            any = true;
+                            break;
+                        }
                     }
+            }
             s_on[ey][ex] = any ? 1 : 0;
         }
     }
@@ -211,7 +252,8 @@ GaussW gauss_weights(float sigma) {
 }
 
 template <class ND>
-EdgeArgs<ND> edge_args(const hdof_gbuf* in, const hdof_params* p, uint8_t* edge, uint8_t* tiles) {
+EdgeArgs<ND> edge_args(const hdof_gbuf* in, const hdof_params* p, uint8_t* edge, uint8_t* tiles,
+                       const Coc* coc = nullptr, float* tile_r = nullptr) {
     EdgeArgs<ND> a;
     a.nd = static_cast<const ND*>(in->nd);
     a.W = in->width;
@@ -222,11 +264,14 @@ EdgeArgs<ND> edge_args(const hdof_gbuf* in, const hdof_params* p, uint8_t* edge,
     a.ntx = (in->width + p->tile - 1) / p->tile;
     a.edge = edge;
     a.tiles = tiles;
+    a.coc = coc ? *coc : Coc{0.f, 0.f};
+    a.rmax = p->r_max;
+    a.tile_r = coc ? tile_r : nullptr;
     return a;
 }
 
 SppArgs spp_args(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p, const uint8_t* tiles,
-                 uint8_t* spp) {
+                 uint8_t* spp, const float* tile_r = nullptr) {
     bool var = p->variance_on && prev_hist;
     SppArgs a;
     a.W = in->width;
@@ -245,22 +290,24 @@ SppArgs spp_args(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_
     a.var_scale = p->var_scale;
     a.hlen_young = p->hlen_young;
     a.spp = spp;
+    a.tile_r = tile_r;
     return a;
 }
 
 // launches of both kernels for one view (tiles already cleared)
+// coc, tile_r: the CoC-scaled mask (both set) or the fixed dilation (both NULL)
 int launch_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p, uint8_t* edge, uint8_t* spp,
-                uint8_t* tiles, cudaStream_t s) {
+                uint8_t* tiles, cudaStream_t s, const Coc* coc = nullptr, float* tile_r = nullptr) {
     const int W = in->width, H = in->height;
     dim3 grid((W + B - 1) / B, (H + B - 1) / B);
     ProfScope ps_("mask", s);
     if (in->dtype_nd == HDOF_F32)
-        k_mask_edge<float4><<<grid, 256, 0, s>>>(edge_args<float4>(in, p, edge, tiles));
+        k_mask_edge<float4><<<grid, 256, 0, s>>>(edge_args<float4>(in, p, edge, tiles, coc, tile_r));
     else
-        k_mask_edge<half4s><<<grid, 256, 0, s>>>(edge_args<half4s>(in, p, edge, tiles));
+        k_mask_edge<half4s><<<grid, 256, 0, s>>>(edge_args<half4s>(in, p, edge, tiles, coc, tile_r));
     HDOF_LAUNCHED("mask: edge");
     dim3 g2((W + 31) / 32, (H + 7) / 8);
-    k_mask_spp<<<g2, 256, 0, s>>>(spp_args(in, prev_hist, p, tiles, spp));
+    k_mask_spp<<<g2, 256, 0, s>>>(spp_args(in, prev_hist, p, tiles, spp, coc ? tile_r : nullptr));
     HDOF_LAUNCHED("mask: spp");
     return HDOF_OK;
 }
@@ -286,6 +333,7 @@ extern "C" int hdof_mask(const hdof_gbuf* in, const hdof_history* prev_hist, con
     clear_error();
     int rc;
     if ((rc = check_params(p, "hdof_mask")) || (rc = check_gbuf(in, "hdof_mask", false))) return rc;
+    HDOF_CHECK_ARG(!p->mask_coc, "hdof_mask: the CoC-scaled mask (mask_coc) needs the lens: call hdof_mask_coc");
     HDOF_CHECK_ARG(edge && spp, "hdof_mask: edge and spp outputs are required");
     const int W = in->width, H = in->height;
     bool var = p->variance_on && prev_hist;
@@ -299,6 +347,35 @@ extern "C" int hdof_mask(const hdof_gbuf* in, const hdof_history* prev_hist, con
     uint8_t* tiles = static_cast<uint8_t*>(workspace);
     HDOF_CUDA(cudaMemsetAsync(tiles, 0, (size_t)ntx * nty, s), "hdof_mask: clear tiles");
     return launch_mask(in, prev_hist, p, edge, spp, tiles, s);
+}
+
+extern "C" int hdof_mask_coc(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_camera* cam,
+                             const hdof_lens* lens, const hdof_params* p, uint8_t* edge, uint8_t* spp,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_params(p, "hdof_mask_coc")) || (rc = check_gbuf(in, "hdof_mask_coc", false)) ||
+        (rc = check_camera(cam, "hdof_mask_coc")) || (rc = check_lens(lens, "hdof_mask_coc")))
+        return rc;
+    HDOF_CHECK_ARG(edge && spp, "hdof_mask_coc: edge and spp outputs are required");
+    HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "hdof_mask_coc: gbuf/camera size mismatch");
+    const int W = in->width, H = in->height;
+    bool var = p->variance_on && prev_hist;
+    HDOF_CHECK_ARG(!var || (prev_hist->mom && prev_hist->hlen && in->mv),
+                   "hdof_mask_coc: the variance term needs mv and the history mom/hlen planes");
+    WsLayout L = ws_layout(W, H, p);
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.mask_tiles + L.mask_tile_r,
+                   "hdof_mask_coc: workspace of %zu bytes < %zu", workspace_bytes, L.mask_tiles + L.mask_tile_r);
+    cudaStream_t s = as_stream(stream);
+    const int T = p->tile, ntx = (W + T - 1) / T, nty = (H + T - 1) / T;
+    uint8_t* tiles = static_cast<uint8_t*>(workspace);
+    float* tile_r = reinterpret_cast<float*>(static_cast<char*>(workspace) + L.mask_tiles);
+    HDOF_CUDA(cudaMemsetAsync(tiles, 0, p->mask_coc ? L.mask_tiles + (size_t)ntx * nty * sizeof(float)
+                                                    : (size_t)ntx * nty, s),
+              "hdof_mask_coc: clear tiles");
+    if (!p->mask_coc) return launch_mask(in, prev_hist, p, edge, spp, tiles, s);
+    const Coc coc = make_coc(*lens, cam->height, cam->tan_half_fovy);
+    return launch_mask(in, prev_hist, p, edge, spp, tiles, s, &coc, tile_r);
 }
 
 // ---------------------------------------------------------------------------
@@ -348,6 +425,7 @@ extern "C" int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_h
     clear_error();
     int rc;
     if ((rc = check_params(p, "hdof_mask_noalloc")) || (rc = check_gbuf(in, "hdof_mask_noalloc", false))) return rc;
+    HDOF_CHECK_ARG(!p->mask_coc, "hdof_mask_noalloc: the CoC-scaled mask (mask_coc) is not available here");
     HDOF_CHECK_ARG(edge && spp, "hdof_mask_noalloc: edge and spp outputs are required");
     const int W = in->width, H = in->height;
     bool var = p->variance_on && prev_hist;
@@ -369,7 +447,9 @@ namespace hdof {
 
 size_t mask_edge_args_size() { return sizeof(EdgeArgs<float4>); }
 void mask_edge_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
-    *reinterpret_cast<EdgeArgs<float4>*>(dst) = edge_args<float4>(&v.g, &v.params, v.edge, w.tiles);
+    const Coc coc = make_coc(v.lens, v.cam.height, v.cam.tan_half_fovy);
+    *reinterpret_cast<EdgeArgs<float4>*>(dst) =
+        edge_args<float4>(&v.g, &v.params, v.edge, w.tiles, v.params.mask_coc ? &coc : nullptr, w.tile_r);
     *gx = (v.g.width + B - 1) / B;
     *gy = (v.g.height + B - 1) / B;
 }
@@ -380,7 +460,8 @@ void mask_edge_launch_batch(const void* args, BatchGrid g, int blocks, cudaStrea
 
 size_t mask_spp_args_size() { return sizeof(SppArgs); }
 void mask_spp_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
-    *reinterpret_cast<SppArgs*>(dst) = spp_args(&v.g, &v.hist_in, &v.params, w.tiles, v.spp);
+    *reinterpret_cast<SppArgs*>(dst) =
+        spp_args(&v.g, &v.hist_in, &v.params, w.tiles, v.spp, v.params.mask_coc ? w.tile_r : nullptr);
     *gx = (v.g.width + 31) / 32;
     *gy = (v.g.height + 7) / 8;
 }

@@ -115,6 +115,8 @@ def load():
         "hdof_gbuffer": ([vp, P(hdof_camera), P(hdof_camera), P(hdof_params), vp, P(hdof_gbuf), vp], C.c_int),
         "hdof_workspace_bytes": ([i32, i32, P(hdof_params)], sz),
         "hdof_mask": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp, sz, vp], C.c_int),
+        "hdof_mask_coc": ([P(hdof_gbuf), P(hdof_history), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp,
+                           sz, vp], C.c_int),
         "hdof_mask_noalloc": ([P(hdof_gbuf), P(hdof_history), P(hdof_params), vp, vp, vp], C.c_int),
         "hdof_trace": ([vp, P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, vp, vp, vp, vp, vp, sz, P(hdof_tuning), vp],
                        C.c_int),
@@ -155,7 +157,7 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["hdof_version", "hdof_last_error", "hdof_sync", "hdof_default_params", "hdof_build_bvh",
             "hdof_bvh_destroy", "hdof_bvh_info", "hdof_closest_hits", "hdof_gbuffer", "hdof_workspace_bytes",
-            "hdof_mask", "hdof_mask_noalloc", "hdof_trace", "hdof_trace_hits", "hdof_reference_rt", "hdof_error_map",
+            "hdof_mask", "hdof_mask_coc", "hdof_mask_noalloc", "hdof_trace", "hdof_trace_hits", "hdof_reference_rt", "hdof_error_map",
             "hdof_postfilter", "hdof_reconstruct", "hdof_composite",
             "hdof_batch_create", "hdof_batch_update", "hdof_batch_render", "hdof_batch_render_range",
             "hdof_batch_destroy", "hdof_batch_bytes",
@@ -361,6 +363,13 @@ def hdof_mask(gbuf: GBuffer, prev_hist, p, edge, spp, workspace, stream=None):
                             _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
+def hdof_mask_coc(gbuf: GBuffer, prev_hist, cam, lns, p, edge, spp, workspace, stream=None):
+    """hdof_mask whose edge tiles reach their pixels' largest CoC radius when p.mask_coc = 1."""
+    _check(load().hdof_mask_coc(C.byref(gbuf.struct()), C.byref(prev_hist.struct()) if prev_hist is not None else None,
+                                C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)), _ptr(edge), _ptr(spp),
+                                _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
 def hdof_mask_noalloc(gbuf: GBuffer, prev_hist, p, edge, spp, stream=None):
     """hdof_mask for callers that cannot give the library device memory: the
     tile flags live in a fixed array inside the library (see include/hdof.h)."""
@@ -483,7 +492,7 @@ class Renderer:
         hin = self.hist[self.cur]
         hout = self.hist[1 - self.cur]
         hdof_gbuffer(self.bvh, cam, prev, p, self.g, stream, hint=self.g.tri)
-        hdof_mask(self.g, hin if with_history else None, p, self.edge, self.spp, self.ws, stream)
+        hdof_mask_coc(self.g, hin if with_history else None, cam, lns, p, self.edge, self.spp, self.ws, stream)
         hdof_trace(self.bvh, cam, lns, p, self.spp, self.rt, self.stats, self.ws, stream, hint=self.g.tri)
         hdof_postfilter(self.g, cam, lns, p, self.pp, self.ws, stream)
         hdof_reconstruct(self.rt, self.g, self.spp, cam, prev, lns, p, hin, hout, self.crt, self.hacc,

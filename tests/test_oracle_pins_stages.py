@@ -589,3 +589,39 @@ def test_temporal_per_pixel_blend_factor(orc, case):
     hn = np.array([B * args["hist_grey"]] * 3 + [B])
     cur = np.array([r[3] * r[0], r[3] * r[1], r[3] * r[2], r[3]])
     np.testing.assert_allclose(near, hn + al * (cur - hn), atol=1e-12)
+
+
+# ------------------------------------------------------ CoC-scaled mask ----
+
+def test_mask_reach_scales_with_coc(orc):
+    """A near square (z = 0.5) over an in-focus background (z = zf = 2):
+    edges lie in tile columns 3..6 (the 7-pixel footprint of the Gaussian +
+    Sobel around x = 64 and x = 96) and rows 1..4.  The tiles holding near
+    pixels have r = min(|c(0.5)| / 2, r_max) with c(0.5) = A H 1.5 / (0.5 zf t)
+    = 249.4 A px: A = 0.3 gives r = 37.4, a reach of ceil(37.4 / 16) = 3
+    tiles, so columns 1..8 are traced instead of the fixed dilation's 2..7;
+    a cap r_max = 16 brings the reach back to 1."""
+    W, H, T = 224, 96, 16
+    nd = np.zeros((H, W, 4))
+    nd[..., 2] = -1.0
+    nd[..., 3] = 2.0
+    nd[32:64, 64:96, 3] = 0.5
+    mv = np.zeros((H, W, 2))
+    t = math.tan(math.radians(30))
+    lens = hi.Lens(2.0, 0.3, 0.05)
+    assert abs(orc.coc(0.5, lens, H, t) / 2 - 124.7 * 0.3) < 0.05
+    cols = lambda spp: sorted({i // T for i in range(W) if spp[:, i].any()})  # noqa: E731
+    base = orc.mask(nd, mv, hi.Params(spp_max=8, tile=T, dilate=1, r_max=100.0), lens_=lens, tan_half_fovy=t)
+    assert sorted({i // T for i in range(W) if base["edge"][:, i].any()}) == [3, 4, 5, 6]
+    assert cols(base["spp"]) == [2, 3, 4, 5, 6, 7]
+    coc = orc.mask(nd, mv, hi.Params(spp_max=8, tile=T, dilate=1, r_max=100.0, mask_coc=1), lens_=lens,
+                   tan_half_fovy=t)
+    assert np.array_equal(coc["edge"], base["edge"])
+    assert cols(coc["spp"]) == [1, 2, 3, 4, 5, 6, 7, 8]
+    assert np.all(coc["spp"][:, T:9 * T] == 8) and not coc["spp"][:, :T].any() and not coc["spp"][:, 9 * T:].any()
+    capped = orc.mask(nd, mv, hi.Params(spp_max=8, tile=T, dilate=1, r_max=16.0, mask_coc=1), lens_=lens,
+                      tan_half_fovy=t)
+    assert np.array_equal(capped["spp"], base["spp"])
+    # without the lens the flag has nothing to scale by: the fixed dilation
+    nolens = orc.mask(nd, mv, hi.Params(spp_max=8, tile=T, dilate=1, r_max=100.0, mask_coc=1))
+    assert np.array_equal(nolens["spp"], base["spp"])
