@@ -218,7 +218,7 @@ def _reach_ties(nd, lens, t, p, edge_ties):
     return np.kron(tie, np.ones((T, T), bool))[:Hh, :W] | edge_ties
 
 
-@pytest.mark.parametrize("tile,dilate,A,W,Hh", [(16, 1, 0.03, 257, 131), (8, 0, 0.05, 200, 120), (5, 2, 0.08, 83, 59)])
+@pytest.mark.parametrize("tile,dilate,A,W,Hh", [(16, 1, 0.1, 257, 131), (8, 0, 0.05, 200, 120), (5, 2, 0.08, 83, 59)])
 def test_mask_coc_scaled(orc, tile, dilate, A, W, Hh):
     """The CoC-scaled mask (each edge tile reaches its pixels' largest CoC
     radius) against the oracle's, on random G-buffers: identical bits outside
@@ -240,7 +240,8 @@ def test_mask_coc_scaled(orc, tile, dilate, A, W, Hh):
     assert np.array_equal(host(edge)[~tie], ref["edge"][~tie])
     assert np.array_equal(host(spp)[~ties], ref["spp"][~ties])
     base = orc.mask(gb["nd"].astype(np.float64), gb["mv"].astype(np.float64), p.replace(mask_coc=0))
-    assert (ref["spp"] > 0).sum() > (base["spp"] > 0).sum()  # the blur widens the traced area
+    assert (ref["spp"] > 0).sum() >= (base["spp"] > 0).sum()  # the blur can only widen the traced area
+    assert not np.any((base["spp"] > 0) & (ref["spp"] == 0))
     p0 = p.replace(mask_coc=0)
     H.hdof_mask_coc(g, None, cam, lens, p0, edge, spp, workspace(W, Hh, p0))
     e2, s2 = _mask(g, None, p0)
