@@ -590,14 +590,34 @@ void orc_mask_coc(int32_t W, int32_t H, const double* nd, const double* mv, cons
  * h = sum w / n (hit ratio); empty layers (weight < 1e-6) give colour 0 and
  * CoC -1.
  * ---------------------------------------------------------------------- */
+/* Aperture shape and sample weights (Discussion: alternative bokeh shapes
+ * by the shape of the sampling kernel, spherical aberration by the relative
+ * weight of its samples).  blades = 0: the disk of radius A; blades = N >= 3:
+ * the regular N-gon inscribed in it, vertices at angles blade_rot + 2 pi k / N
+ * in the (right, up) plane.  Its norm: D(v) = |v| / g(phi), g(phi) =
+ * cos(pi/N) / cos(((phi - blade_rot) mod 2pi/N) - pi/N), so the aperture is
+ * {D(v) <= A}.  A sample at lens-plane radius rho weighs
+ * 1 + aberration (2 rho^2 / A^2 - 1) (mean 1 over the disk). */
+static double aperture_norm(double vx, double vy, const orc_params* p) {
+    double d = sqrt(vx * vx + vy * vy);
+    if (p->blades < 3 || d == 0.0) return d;
+    double sect = 2.0 * PI_D / p->blades;
+    double m = fmod(atan2(vy, vx) - p->blade_rot, sect);
+    if (m < 0.0) m += sect;
+    return d * cos(m - PI_D / p->blades) / cos(PI_D / p->blades);
+}
+static double aperture_weight(double t, const orc_params* p) { return 1.0 + p->aberration * (2.0 * t * t - 1.0); }
+
 /* Lens sample `smp` of pixel q (Ray Trace section: rays through random
  * points of the lens aperture, aimed at the pixel's point on the focus
  * plane): Philox(key = (seed, view*65536 + frame), ctr = (q, smp, 0, 0)) ->
- * u1, u2; lens point rho = A sqrt(u1), theta = 2 pi u2 in the (right, up)
- * plane; unit direction towards the focus-plane point of the pixel's pinhole
- * ray. */
+ * u1, u2; on the disk, lens point rho = A sqrt(u1), theta = 2 pi u2 in the
+ * (right, up) plane; on the N-gon, sector k = floor(N u2) and f = N u2 - k,
+ * point sqrt(u1) ((1 - f) V_k + f V_k+1) (uniform over the sector's
+ * triangle); unit direction towards the focus-plane point of the pixel's
+ * pinhole ray; *weight (may be NULL) = the sample's weight. */
 void orc_lens_ray(const orc_camera* cam, const orc_lens* lens, const orc_params* p, int64_t q, int32_t smp,
-                  double O[3], double dir[3]) {
+                  double O[3], double dir[3], double* weight) {
     int32_t W = cam->width, i = (int32_t)(q % W), j = (int32_t)(q / W);
     double A = lens->aperture_radius, zf = lens->focus_dist;
     uint32_t key[2] = {p->seed, (uint32_t)p->view * 65536u + (uint32_t)p->frame};
@@ -606,10 +626,22 @@ void orc_lens_ray(const orc_camera* cam, const orc_lens* lens, const orc_params*
     for (int k = 0; k < 3; ++k) Pf[k] = cam->pos[k] + zf * d[k];
     uint32_t ctr[4] = {(uint32_t)q, (uint32_t)smp, 0u, 0u}, x[4];
     orc_philox(ctr, key, x);
-    double rho = A * sqrt(u01(x[0])), th = 2.0 * PI_D * u01(x[1]);
-    for (int k = 0; k < 3; ++k) O[k] = cam->pos[k] + rho * cos(th) * cam->right[k] + rho * sin(th) * cam->up[k];
+    double lx, ly;
+    if (p->blades >= 3) {
+        double N = p->blades, s_ = sqrt(u01(x[0])), v = u01(x[1]) * N;
+        double k = floor(v), f = v - k;
+        double t0 = p->blade_rot + 2.0 * PI_D * k / N, t1 = p->blade_rot + 2.0 * PI_D * (k + 1.0) / N;
+        lx = A * s_ * ((1.0 - f) * cos(t0) + f * cos(t1));
+        ly = A * s_ * ((1.0 - f) * sin(t0) + f * sin(t1));
+    } else {
+        double rho = A * sqrt(u01(x[0])), th = 2.0 * PI_D * u01(x[1]);
+        lx = rho * cos(th);
+        ly = rho * sin(th);
+    }
+    for (int k = 0; k < 3; ++k) O[k] = cam->pos[k] + lx * cam->right[k] + ly * cam->up[k];
     sub3(Pf, O, dir);
     normalize3(dir);
+    if (weight) *weight = A > 0.0 ? aperture_weight(sqrt(lx * lx + ly * ly) / A, p) : 1.0;
 }
 
 static void trace_pixel(const oscene* s, const orc_camera* cam, const orc_lens* lens,
@@ -617,10 +649,10 @@ static void trace_pixel(const oscene* s, const orc_camera* cam, const orc_lens* 
     int32_t W = cam->width, H = cam->height;
     double t = cam->tan_half_fovy;
     double SwL[3] = {0, 0, 0}, SfL[3] = {0, 0, 0}, SfP[3] = {0, 0, 0};
-    double Sw = 0, Sf = 0, Swc = 0, Sfc = 0;
+    double Sw = 0, Sf = 0, Swc = 0, Sfc = 0, Ss = 0;
     for (int smp = 0; smp < n; ++smp) {
-        double O[3], dir[3];
-        orc_lens_ray(cam, lens, p, (int64_t)j * W + i, smp, O, dir);
+        double O[3], dir[3], ws;
+        orc_lens_ray(cam, lens, p, (int64_t)j * W + i, smp, O, dir, &ws);
         double th_, bary[3], n_[3], L[3], P[3], c;
         int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
         if (id >= 0) {
@@ -633,13 +665,14 @@ static void trace_pixel(const oscene* s, const orc_camera* cam, const orc_lens* 
             for (int k = 0; k < 3; ++k) { P[k] = O[k] + p->miss_dist * dir[k]; L[k] = 0.0; }
             c = orc_coc(INFINITY, lens, H, t);
         }
-        double w = clampd((c + SQRT2) / (2.0 * SQRT2), 0.0, 1.0), ac = fabs(c);
+        /* split weight, scaled by the sample's aperture weight (1 for the uniform disk) */
+        double w = ws * clampd((c + SQRT2) / (2.0 * SQRT2), 0.0, 1.0), wf = ws - w, ac = fabs(c);
         for (int k = 0; k < 3; ++k) {
             SwL[k] += w * L[k];
-            SfL[k] += (1.0 - w) * L[k];
-            SfP[k] += (1.0 - w) * P[k];
+            SfL[k] += wf * L[k];
+            SfP[k] += wf * P[k];
         }
-        Sw += w; Sf += 1.0 - w; Swc += w * ac; Sfc += (1.0 - w) * ac;
+        Sw += w; Sf += wf; Swc += w * ac; Sfc += wf * ac; Ss += ws;
     }
     int nok = Sw >= EMPTY_W, fok = Sf >= EMPTY_W;
     for (int k = 0; k < 3; ++k) {
@@ -647,7 +680,7 @@ static void trace_pixel(const oscene* s, const orc_camera* cam, const orc_lens* 
         rt[4 + k] = fok ? SfL[k] / Sf : 0.0;
         rt[8 + k] = fok ? SfP[k] / Sf : 0.0;
     }
-    rt[3] = Sw / n;
+    rt[3] = Sw / Ss;
     rt[7] = nok ? Swc / Sw : -1.0;
     rt[11] = fok ? Sfc / Sf : -1.0;
 }
@@ -892,6 +925,34 @@ double orc_disk_area(double r) {
     return a;
 }
 
+/* Shaped bokeh (blades >= 3 or aberration != 0): the thin lens images an
+ * aperture point O of a source at CoC c onto the screen offset
+ * (c / 2A) (-O_right, O_up) (screen y grows downwards), so a near source's
+ * bokeh is the aperture scaled to radius |c|/2 and mirrored left-right, a far
+ * source's mirrored top-bottom.  A receiver at screen offset o = (ox, oy)
+ * from source q lies at aperture norm D_near = D(-ox, oy) or D_far =
+ * D(ox, -oy) in units of pixels, and its weight is s(r_q - D) times the
+ * aperture weight at |o| / max(r_q, 1/2) (clamped to 1).  Normalised by the
+ * lattice area of that weighted soft shape (the same for both mirrors: each
+ * maps the integer lattice onto itself). */
+static int shaped(const orc_params* p) { return p->blades >= 3 || p->aberration != 0.0; }
+
+static double shaped_weight(double r, double D, double d, const orc_params* p) {
+    double s = soft_step(r - D);
+    if (s <= 0.0 || r < 1.0) return s;  /* a bokeh under a pixel wide shows no radial weighting */
+    double tt = d / r;
+    return s * aperture_weight(tt < 1.0 ? tt : 1.0, p);
+}
+
+double orc_shaped_area(double r, const orc_params* p) {
+    int K = (int)ceil(r + 0.5);
+    double a = 0.0;
+    for (int y = -K; y <= K; ++y)
+        for (int x = -K; x <= K; ++x)
+            a += shaped_weight(r, aperture_norm(x, y, p), sqrt((double)(x * x + y * y)), p);
+    return a;
+}
+
 static void postfilter_pixel(int32_t W, int32_t H, const orc_lens* lens, double t, const orc_params* p,
                              const double* nd, const double* col, const double* inv_area,
                              int32_t i, int32_t j, double* o) {
@@ -908,12 +969,17 @@ static void postfilter_pixel(int32_t W, int32_t H, const orc_lens* lens, double 
             double c = orc_coc(zq, lens, H, t);
             double r = fmin(fabs(c) * 0.5, p->r_max);
             double d = sqrt((double)(a * a + b * b));
-            double s = soft_step(r - d);
-            if (s <= 0.0) continue;
+            double s = soft_step(r - d), sf = s;
+            if (shaped(p)) {
+                /* receiver p at offset o = (-a, -b) from source q: D_near = D(a, -b), D_far = D(-a, b) */
+                s = shaped_weight(r, aperture_norm(a, -b, p), d, p);
+                sf = shaped_weight(r, aperture_norm(-a, b, p), d, p);
+            }
+            if (s <= 0.0 && sf <= 0.0) continue;
             double ia = inv_area[q];
             double wn = clampd((c + SQRT2) / (2.0 * SQRT2), 0.0, 1.0);
             double kz = clampd(1.0 - (zq - zp) / (p->kz_rel * zp), 0.0, 1.0);
-            double an = wn * s * ia, af = (1.0 - wn) * s * ia * kz;
+            double an = wn * s * ia, af = (1.0 - wn) * sf * ia * kz;
             for (int k = 0; k < 3; ++k) { Sn[k] += an * col[4 * q + k]; Sf[k] += af * col[4 * q + k]; }
             Wn += an;
             Wf += af;
@@ -934,7 +1000,7 @@ void orc_postfilter(int32_t W, int32_t H, const orc_lens* lens, double t, const 
 #pragma omp parallel for schedule(dynamic, 4)
     for (int32_t q = 0; q < W * H; ++q) {
         double r = fmin(fabs(orc_coc(nd[4 * (size_t)q + 3], lens, H, t)) * 0.5, p->r_max);
-        inv_area[q] = 1.0 / orc_disk_area(r);
+        inv_area[q] = 1.0 / (shaped(p) ? orc_shaped_area(r, p) : orc_disk_area(r));
     }
     if (pix) {
 #pragma omp parallel for schedule(dynamic, 16)
@@ -1004,7 +1070,7 @@ void orc_trace_records(const void* sp, const orc_camera* cam, const orc_lens* le
             if (!n) continue;
             for (int smp = 0; smp < n; ++smp) {
                 double O[3], dir[3];
-                orc_lens_ray(cam, lens, p, (int64_t)q, smp, O, dir);
+                orc_lens_ray(cam, lens, p, (int64_t)q, smp, O, dir, NULL);
                 double th_, bary[3], n_[3], L[3], P[3], z;
                 int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
                 if (id >= 0) {
@@ -1039,7 +1105,7 @@ void orc_trace_hits(const void* sp, const orc_camera* cam, const orc_lens* lens,
             size_t q = (size_t)j * W + i;
             for (int smp = 0; smp < spp[q]; ++smp) {
                 double O[3], dir[3], th_, bary[3];
-                orc_lens_ray(cam, lens, p, (int64_t)q, smp, O, dir);
+                orc_lens_ray(cam, lens, p, (int64_t)q, smp, O, dir, NULL);
                 int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
                 size_t r = (size_t)(off[q] + smp);
                 ids[r] = id;
@@ -1076,20 +1142,20 @@ void orc_reference_rt(const void* sp, const orc_camera* cam, const orc_lens* len
     for (int32_t j = 0; j < H; ++j)
         for (int32_t i = 0; i < W; ++i) {
             size_t q = (size_t)j * W + i;
-            double S[3] = {0, 0, 0};
+            double S[3] = {0, 0, 0}, n = 0.0;
             for (int32_t k = 0; k < passes; ++k) {
                 orc_params pk = *p;
                 pk.frame = (int32_t)(((uint32_t)p->frame + (uint32_t)k) & 0xFFFFu);
                 for (int smp = 0; smp < p->spp_max; ++smp) {
-                    double O[3], dir[3], th_, bary[3], n_[3], L[3];
-                    orc_lens_ray(cam, lens, &pk, (int64_t)q, smp, O, dir);
+                    double O[3], dir[3], th_, bary[3], n_[3], L[3], ws;
+                    orc_lens_ray(cam, lens, &pk, (int64_t)q, smp, O, dir, &ws);
+                    n += ws;
                     int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
                     if (id < 0) continue;
                     shade_hit(s, id, bary, dir, p, n_, L);
-                    for (int c = 0; c < 3; ++c) S[c] += L[c];
+                    for (int c = 0; c < 3; ++c) S[c] += ws * L[c];
                 }
             }
-            double n = (double)passes * p->spp_max;
             for (int c = 0; c < 3; ++c) out[4 * q + c] = S[c] / n;
             out[4 * q + 3] = 0.0;
         }

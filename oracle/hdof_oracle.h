@@ -98,6 +98,7 @@ void orc_composite(int32_t n, int32_t H, const orc_lens* lens, double tan_half_f
                    const double* pp, const double* crt, const double* crec, const double* hacc,
                    double* out);
 double orc_disk_area(double r);
+double orc_shaped_area(double r, const orc_params* p);
 /* ---- differentiable post-path with frozen visibility ---- */
 void orc_trace_records(const void* s, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
                        const uint8_t* spp, const int64_t* off, double* rec);
@@ -106,7 +107,7 @@ void orc_replay(int32_t W, int32_t H, const orc_lens* lens, double tan_half_fovy
 void orc_temporal_frozen(int32_t W, int32_t H, const orc_params* p, const double* rt, const uint8_t* spp,
                          const double* hs, double* crt, double* hacc, double* mom, uint8_t* hlen);
 void orc_lens_ray(const orc_camera* cam, const orc_lens* lens, const orc_params* p, int64_t q, int32_t smp,
-                  double O[3], double dir[3]);
+                  double O[3], double dir[3], double* weight);
 void orc_trace_hits(const void* s, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
                     const uint8_t* spp, const int64_t* off, int32_t* ids, double* ts, double* margin);
 void orc_reference_rt(const void* s, const orc_camera* cam, const orc_lens* lens, const orc_params* p,

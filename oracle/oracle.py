@@ -105,8 +105,11 @@ def lib():
         L.orc_replay.argtypes = [C.c_int32, C.c_int32, C.POINTER(Lens), C.c_double, up8, i64p, dp, dp]
         L.orc_temporal_frozen.argtypes = [C.c_int32, C.c_int32, C.POINTER(Params), dp, up8, dp, dp, dp, dp, up8]
         L.orc_disk_area.restype = C.c_double
+        L.orc_shaped_area.argtypes = [C.c_double, C.POINTER(Params)]
+        L.orc_shaped_area.restype = C.c_double
         L.orc_reference_rt.argtypes = [vp, C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), C.c_int32, dp]
-        L.orc_lens_ray.argtypes = [C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), C.c_int64, C.c_int32, dp, dp]
+        L.orc_lens_ray.argtypes = [C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), C.c_int64, C.c_int32, dp, dp,
+                                   dp]
         L.orc_trace_hits.argtypes = [vp, C.POINTER(Cam), C.POINTER(Lens), C.POINTER(Params), up8, i64p, ip, dp, dp]
         _lib = L
     return _lib
@@ -386,11 +389,16 @@ def reference_rt(oscene: OScene, cam_, lens_, params_, passes):
     return out
 
 
-def lens_ray(cam_, lens_, params_, q, smp):
-    """FP64 origin and unit direction of lens sample smp of pixel q."""
+def lens_ray(cam_, lens_, params_, q, smp, weight=False):
+    """FP64 origin and unit direction of lens sample smp of pixel q (and its
+    aperture weight when asked)."""
     O = (C.c_double * 3)()
     d = (C.c_double * 3)()
-    lib().orc_lens_ray(C.byref(cam(cam_)), C.byref(lens(lens_)), C.byref(params(params_)), int(q), int(smp), O, d)
+    w = C.c_double()
+    lib().orc_lens_ray(C.byref(cam(cam_)), C.byref(lens(lens_)), C.byref(params(params_)), int(q), int(smp), O, d,
+                       C.byref(w))
+    if weight:
+        return np.array(list(O)), np.array(list(d)), w.value
     return np.array(list(O)), np.array(list(d))
 
 
@@ -453,6 +461,11 @@ def post_forward(col, z, spp, rec, off, hs, cam_, lens_, params_, pp_pix=None):
 
 def disk_area(r: float) -> float:
     return lib().orc_disk_area(float(r))
+
+
+def shaped_area(r: float, params_) -> float:
+    """Lattice area of the weighted soft aperture shape of radius r."""
+    return lib().orc_shaped_area(float(r), C.byref(params(params_)))
 
 
 def num_threads() -> int:

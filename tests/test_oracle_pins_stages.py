@@ -625,3 +625,202 @@ def test_mask_reach_scales_with_coc(orc):
     # without the lens the flag has nothing to scale by: the fixed dilation
     nolens = orc.mask(nd, mv, hi.Params(spp_max=8, tile=T, dilate=1, r_max=100.0, mask_coc=1))
     assert np.array_equal(nolens["spp"], base["spp"])
+
+
+# --------------------------------------------- aperture shape and weights ----
+
+def _clip(poly, axis, bound, keep_le):
+    """Sutherland-Hodgman: the part of poly with coordinate `axis` <= bound
+    (keep_le) or >= bound."""
+    out = []
+    inside = (lambda v: v[axis] <= bound) if keep_le else (lambda v: v[axis] >= bound)
+    for k in range(len(poly)):
+        a, b = poly[k - 1], poly[k]
+        if inside(b):
+            if not inside(a):
+                t = (bound - a[axis]) / (b[axis] - a[axis])
+                out.append(a + t * (b - a))
+            out.append(b)
+        elif inside(a):
+            t = (bound - a[axis]) / (b[axis] - a[axis])
+            out.append(a + t * (b - a))
+    return out
+
+
+def _area(poly):
+    if len(poly) < 3:
+        return 0.0
+    x = np.array([v[0] for v in poly])
+    y = np.array([v[1] for v in poly])
+    return 0.5 * abs(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1)))
+
+
+def test_polygon_aperture_plane_is_the_polygon_convolution(orc):
+    """A triangular aperture (3 blades, a vertex up): the thin-lens image of a
+    fronto-parallel checker plane in the near field averages the pinhole image
+    over the aperture scaled to radius c/2 and mirrored top-bottom in screen
+    space (lens point O shows the plane point at screen offset
+    (c / 2A) (O_right, -O_up)); the expected value per pixel comes from exact
+    polygon/cell overlaps (Sutherland-Hodgman clipping).  1024 samples per
+    pixel: within 4 sigma_p / sqrt(N) on >= 99% of pixels."""
+    z, zf, A = 1.0, 2.0, 0.2
+    W = H = 20
+    cam = hi.Camera(width=W, height=H).f32()
+    lens = hi.Lens(zf, A, 0.05).f32()
+    p = hi.Params(spp_max=128, blades=3, blade_rot=math.pi / 2)
+    osc = orc.OScene(hi.plane_scene(z, half=50.0, cells=400.0))
+    t = cam.tan_half_fovy
+    c = lens.aperture_radius * H * (lens.focus_dist - z) / (z * lens.focus_dist * t)
+    th = [p.blade_rot + 2 * math.pi * k / 3 for k in range(3)]
+    shape = [np.array([c / 2 * math.cos(a), -c / 2 * math.sin(a)]) for a in th]
+    irr = p.k_ambient + max(0.0, -p.unit_lights()[0][2])
+    alb = (float(np.float32(0.2)), float(np.float32(0.8)))
+    a_ = W / H
+    cell = 2 * 50.0 / 400.0
+    mean = np.zeros((H, W))
+    sd = np.zeros((H, W))
+    for j in range(H):
+        for i in range(W):
+            poly = [v + np.array([i + 0.5, j + 0.5]) for v in shape]
+            tot = _area(poly)
+            xs = [v[0] for v in poly]
+            ys = [v[1] for v in poly]
+            X0 = (2 * min(xs) / W - 1) * a_ * t * z
+            X1 = (2 * max(xs) / W - 1) * a_ * t * z
+            Y0 = (1 - 2 * max(ys) / H) * t * z
+            Y1 = (1 - 2 * min(ys) / H) * t * z
+            m1 = m2 = 0.0
+            for cu in range(int(math.floor((X0 + 50) / cell)), int(math.floor((X1 + 50) / cell)) + 1):
+                for cv in range(int(math.floor((Y0 + 50) / cell)), int(math.floor((Y1 + 50) / cell)) + 1):
+                    sx0 = ((-50 + cu * cell) / (z * a_ * t) + 1) * 0.5 * W
+                    sx1 = ((-50 + (cu + 1) * cell) / (z * a_ * t) + 1) * 0.5 * W
+                    sy0 = (1 - (-50 + (cv + 1) * cell) / (z * t)) * 0.5 * H
+                    sy1 = (1 - (-50 + cv * cell) / (z * t)) * 0.5 * H
+                    q = _clip(_clip(_clip(_clip(poly, 0, sx0, False), 0, sx1, True), 1, sy0, False), 1, sy1, True)
+                    L = alb[(cu + cv) % 2] * irr
+                    ar = _area(q) / tot
+                    m1 += ar * L
+                    m2 += ar * L * L
+            mean[j, i] = m1
+            sd[j, i] = math.sqrt(max(0.0, m2 - m1 * m1))
+    assert (sd > 0).mean() > 0.3
+    spp = np.full((H, W), 128, np.uint8)
+    est = np.mean([orc.trace(osc, cam, lens, p.replace(frame=k), spp)[..., 0] for k in range(8)], 0)
+    e = np.abs(est - mean)
+    assert (e <= 4 * sd / math.sqrt(1024) + 1e-12).mean() >= 0.99
+    # the disk's image differs: the shape matters
+    disk = np.mean([orc.trace(osc, cam, lens, p.replace(frame=k, blades=0), spp)[..., 0] for k in range(8)], 0)
+    assert np.abs(disk - mean).max() > 3 * (4 * sd.max() / math.sqrt(1024))
+
+
+def _weighted_fraction(h, R, a):
+    """Fraction of the disk of radius R at the origin with x > h, each point
+    weighted by 1 + a (2 rho^2 / R^2 - 1) (total weight pi R^2): Gauss-Legendre
+    in theta with x = R sin(theta), where the integrand is smooth."""
+    if h >= R:
+        return 0.0
+    if h <= -R:
+        return 1.0
+    t0, t1 = math.asin(h / R), math.pi / 2
+    xg, wg = np.polynomial.legendre.leggauss(64)
+    th = 0.5 * (t1 - t0) * xg + 0.5 * (t1 + t0)
+    x = R * np.sin(th)
+    y = R * np.cos(th)  # half-chord
+    # integral over y in [-y, y] of 1 + a (2 (x^2 + y^2) / R^2 - 1)
+    f = 2 * y * (1 - a) + (2 * a / R ** 2) * (2 * x * x * y + 2 * y ** 3 / 3)
+    return float(0.5 * (t1 - t0) * np.sum(wg * f * R * np.cos(th))) / (math.pi * R * R)
+
+
+def test_aberration_weights_over_an_edge(orc):
+    """A circular aperture with sample weights 1 + a (2 rho^2 / A^2 - 1)
+    (a = 0.8: a bright rim): the image of a plane split by one straight albedo
+    edge is the weighted fraction of the blur disk on each side; pixels whose
+    disk avoids the edge are exact.  1024 weighted samples: within
+    4 (1 + a) (contrast / 2) / sqrt(N), and unlike the unweighted image."""
+    z, zf, A, ab = 1.0, 2.0, 0.2, 0.8
+    W = H = 20
+    cam = hi.Camera(width=W, height=H).f32()
+    lens = hi.Lens(zf, A, 0.05).f32()
+    p = hi.Params(spp_max=128, aberration=ab)
+    osc = orc.OScene(hi.plane_scene(z, half=50.0, cells=2.0))  # cell edges at X = 0 and Y = 0
+    t = cam.tan_half_fovy
+    R = lens.aperture_radius * H * (lens.focus_dist - z) / (z * lens.focus_dist * t) / 2
+    irr = p.k_ambient + max(0.0, -p.unit_lights()[0][2])
+    lo, hi_ = float(np.float32(0.2)) * irr, float(np.float32(0.8)) * irr
+    spp = np.full((H, W), 128, np.uint8)
+    est = np.mean([orc.trace(osc, cam, lens, p.replace(frame=k), spp)[..., 0] for k in range(8)], 0)
+    flat = np.mean([orc.trace(osc, cam, lens, p.replace(frame=k, aberration=0.0), spp)[..., 0] for k in range(8)], 0)
+    rows = [j for j in range(H) if abs(j + 0.5 - H / 2) > R + 1]  # away from the horizontal edge at Y = 0
+    tol = 4 * (1 + ab) * (hi_ - lo) / 2 / math.sqrt(1024)
+    e_w, e_flat = [], []
+    for j in rows:
+        upper = j + 0.5 < H / 2  # screen rows above the centre see Y > 0
+        for i in range(W):
+            h = W / 2 - (i + 0.5)  # screen offset of the edge X = 0 from the pixel centre
+            fr = _weighted_fraction(h, R, ab)  # weighted share of the disk right of the edge
+            right, left = (lo, hi_) if upper else (hi_, lo)  # checker parity of the two cells
+            exp = fr * right + (1 - fr) * left
+            if abs(h) >= R:
+                assert abs(est[j, i] - exp) < 1e-12
+            else:
+                assert abs(est[j, i] - exp) <= tol, (i, j, est[j, i], exp)
+                e_w.append(abs(est[j, i] - exp))
+                e_flat.append(abs(flat[j, i] - exp))
+    # the weights change the image next to the edge: the unweighted estimate misses it
+    assert np.mean(e_w) < 0.5 * np.mean(e_flat), (np.mean(e_w), np.mean(e_flat))
+
+
+def test_shaped_postfilter_orientation_and_unit_scatter(orc):
+    """One near source pixel (z = 0.5) on an in-focus background, triangular
+    aperture with a vertex up in the lens plane: its near bokeh points down on
+    the screen (mirrored left-right), so a receiver 0.8 r below it is covered
+    and one 0.8 r above is not; a far source's bokeh points up.  Every source
+    scatters a total near-layer weight of exactly 1."""
+    W, H = 41, 41
+    t = math.tan(math.radians(30))
+    lens = hi.Lens(2.0, 0.12, 0.05)
+    p = hi.Params(r_max=16.0, blades=3, blade_rot=math.pi / 2)
+    nd = np.zeros((H, W, 4))
+    nd[..., 2] = -1.0
+    nd[..., 3] = 2.0
+    nd[20, 20, 3] = 0.5
+    col = np.zeros((H, W, 4))
+    r = abs(orc.coc(0.5, lens, H, t)) / 2
+    assert 5 < r < 9
+    pp = orc.postfilter(nd, col, lens, t, p)
+    k = int(round(0.8 * r))
+    # background receivers cover themselves by 1/2 (in focus: w_near = 1/2, r = 0)
+    assert pp[20 + k, 20, 3] > 0.5 and pp[20 - k, 20, 3] == 0.5
+    others = np.ones((H, W), bool)
+    others[20, 20] = False
+    # background pixels weigh 1/2 on themselves (in focus: w_near = 1/2, r = 0)
+    total = pp[..., 3].sum() - 0.5 * others.sum()
+    assert abs(total - 1.0) < 1e-12
+    # a far source (z = 8 with the focus at 2): its bokeh points up
+    nd2 = nd.copy()
+    nd2[20, 20, 3] = 2.0
+    lens2 = hi.Lens(2.0, 0.3, 0.05)
+    rf = abs(orc.coc(8.0, lens2, H, t)) / 2
+    nd2[..., 3] = 8.0
+    col2 = np.zeros((H, W, 4))
+    col2[20, 20, :3] = 1.0
+    pp2 = orc.postfilter(nd2, col2, lens2, t, p)
+    kf = int(round(0.8 * rf))
+    assert pp2[20 - kf, 20, 0] > pp2[20 + kf, 20, 0] and pp2[20 + kf, 20, 0] == 0.0
+
+
+def test_shaped_area_limits(orc):
+    """The weighted lattice area of the soft shape approaches its continuous
+    integral: the N-gon's area (N / 2) r^2 sin(2 pi / N) without weights, and
+    pi (r^2 + 1/12) for the weighted disk (mean weight 1)."""
+    for N in (3, 5, 6):
+        p = hi.Params(blades=N, blade_rot=0.3)
+        for r in (20.0, 31.7):
+            cont = 0.5 * N * r * r * math.sin(2 * math.pi / N)
+            assert abs(orc.shaped_area(r, p) - cont) < 0.01 * cont
+    for a in (-1.0, 0.5, 1.0):
+        p = hi.Params(aberration=a)
+        for r in (20.0, 31.7):
+            cont = math.pi * (r * r + 1.0 / 12.0)
+            assert abs(orc.shaped_area(r, p) - cont) < 0.01 * cont
+    assert orc.shaped_area(12.3, hi.Params()) == orc.disk_area(12.3)
