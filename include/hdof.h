@@ -305,9 +305,13 @@ typedef struct hdof_tuning {
  * records in sample order.  min(spp[p], p->spp_max) lens rays
  * per pixel (the ray lists are sized for spp_max): Philox4x32-10
  * (key = (seed, view*65536+frame), counter = (pixel, sample, 0, 0)) gives
- * u1, u2 -> lens point rho = A sqrt(u1), theta = 2 pi u2; the ray aims at
- * the pixel's focus-plane point; closest hit; Lambert radiance; split
- * weight w = clamp((c(z) + sqrt2) / (2 sqrt2), 0, 1) into the near layer.
+ * u1, u2 -> lens point rho = A sqrt(u1), theta = 2 pi u2 (with blades = N:
+ * sector k = floor(N u2), f = N u2 - k, point sqrt(u1) ((1-f) V_k + f V_k+1)
+ * of the N-gon inscribed in the disk, vertex V_k at angle blade_rot +
+ * 2 pi k / N); the ray aims at the pixel's focus-plane point; closest hit;
+ * Lambert radiance; split weight w = clamp((c(z) + sqrt2) / (2 sqrt2), 0, 1)
+ * into the near layer; each sample weighs 1 + aberration (2 rho^2/A^2 - 1)
+ * in every layer sum (hit ratio = weighted near share).
  * rt: float [H][W][12] = (C_near rgb, h | C_far rgb, c_near | P_far xyz,
  * c_far); h = sum w / n is the hit ratio; an empty layer (weight < 1e-6)
  * has colour 0 and CoC -1.  Untraced pixels are not written.
@@ -377,7 +381,17 @@ int hdof_error_map(const float* a, const float* b, const uint8_t* region, int32_
  * (kz_rel z_p), 0, 1).  pp: float [H][W][4] = (alpha N + (1-alpha) F, alpha).
  * Gathers are bounded per 16x16 tile by the largest reaching CoC; where every
  * near source close to a tile has a large CoC, the taps of weight exactly 1
- * are summed from row prefix sums (the same sum, another rounding order). */
+ * are summed from row prefix sums (the same sum, another rounding order).
+ * Shaped bokeh (p->blades >= 3 or p->aberration != 0; the Discussion's
+ * alternative bokeh shapes and sample weights): the thin lens maps aperture
+ * point O of a source at CoC c to the screen offset (c / 2A)(-O_right, O_up),
+ * so the soft disk becomes the aperture shape at radius r_q, mirrored
+ * left-right for the near layer and top-bottom for the far layer: a source
+ * at (dx, dy) from the receiver weighs s(r_q - D(dx, -dy)) (near) or
+ * s(r_q - D(-dx, dy)) (far) times 1 + aberration (2 min(d / r_q, 1)^2 - 1)
+ * (1 while r_q < 1), D the aperture norm (hdof_params.blades), normalised by
+ * that shape's lattice area; computed by a separate gather (no row-prefix
+ * interior).  Not available in batches or the differentiable path. */
 int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, const hdof_lens* lens,
                     const hdof_params* p, float* pp, void* workspace, size_t workspace_bytes,
                     void* stream);

@@ -136,7 +136,8 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     l.pf_zq = align256(npx * sizeof(float));
     l.pf_tiles = align256(ptiles * sizeof(float4));
     l.pf_pre = align256(npx * sizeof(float4));
-    l.pf = l.pf_nrec + l.pf_frec + l.pf_rh + l.pf_zq + l.pf_tiles + l.pf_pre;
+    l.pf_bokeh = bokeh_scratch_bytes(p);
+    l.pf = l.pf_nrec + l.pf_frec + l.pf_rh + l.pf_zq + l.pf_tiles + l.pf_pre + l.pf_bokeh;
     const size_t mask = l.mask_tiles + l.mask_tile_r;
     l.pf_off = align256(mask > l.trace ? mask : l.trace);
     l.total = l.pf_off + l.pf;

@@ -74,6 +74,11 @@ int check_view(const hdof_view& v, int k, int dev) {
         return rc;
     HDOF_CHECK_ARG(v.g.dtype_nd == HDOF_F32 && v.g.dtype_col == HDOF_F32, "%s: batched views use FP32 G-buffers",
                    who);
+    if (bokeh_shaped(&v.params)) {
+        set_error("%s: shaped bokeh (blades, aberration) is not batched; render such views with the single-view calls",
+                  who);
+        return HDOF_EUNSUPPORTED;
+    }
     HDOF_CHECK_ARG(v.g.width == v.cam.width && v.g.height == v.cam.height && v.prev.width == v.cam.width &&
                        v.prev.height == v.cam.height,
                    "%s: size mismatch between gbuf and cameras", who);

@@ -83,6 +83,7 @@ struct WsLayout {
     size_t pf_zq;           // float per pixel: view depth
     size_t pf_tiles;        // float4 per 16x16 tile: largest r near, far; smallest r near
     size_t pf_pre;          // float4 per pixel: row-major inclusive row prefix of the near records
+    size_t pf_bokeh;        // shaped bokeh: aperture-norm and lattice-area tables (at the end of the region)
     size_t pf;              // sum of the post-filter regions (laid out in this order)
     size_t pf_off;          // where the post-filter regions start: after the mask and trace regions, so
                             // the post-filter can run concurrently with them
@@ -96,6 +97,11 @@ int ensure_area_table(cudaStream_t s);
 int area_table_size();
 // device address of the table ((x, a(x), slope, 0) per breakpoint) and its length
 int area_table(const float4** tab, int* n);
+
+// shaped bokeh (blades >= 3 or aberration != 0): the post-filter's own path
+bool bokeh_shaped(const hdof_params* p);
+size_t bokeh_scratch_bytes(const hdof_params* p);
+int launch_bokeh(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, void* scratch, cudaStream_t s);
 
 // launches shared by the frame calls and the differentiable post-path (arguments already checked)
 int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, int W, int H, float r_s, float var_ref,

@@ -615,6 +615,13 @@ namespace hdof {
 
 int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, float4* aux,
                       void* scratch, cudaStream_t s) {
+    if (bokeh_shaped(p)) {
+        if (aux) {
+            set_error("post-filter: shaped bokeh has no adjoint records");
+            return HDOF_EUNSUPPORTED;
+        }
+        return launch_bokeh(in, coc, p, pp, scratch, s);
+    }
     int rc;
     if ((rc = ensure_area_table(s))) return rc;
     const int W = in->width, H = in->height;

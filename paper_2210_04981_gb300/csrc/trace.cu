@@ -212,6 +212,9 @@ struct TraceArgs {
     Coc coc;
     Lights L;
     float A, zf, miss_dist;
+    int blades;              // aperture: 0 = disk, N >= 3 = regular N-gon inscribed in it
+    float blade_rot;         // polygon rotation (radians)
+    float aberration;        // sample weight 1 + aberration (2 rho^2 / A^2 - 1)
     uint2 key;
     int cap, smax;
     unsigned* status;
@@ -228,19 +231,37 @@ struct TraceArgs {
     const unsigned* ray_off;
 };
 
-// lens sample `smp` of pixel q: origin on the lens disk, unit direction to
-// the pixel's focus-plane point
-__device__ __forceinline__ void lens_ray(const TraceArgs& a, unsigned q, unsigned smp, float3& O, float3& dir) {
+// lens sample `smp` of pixel q: origin on the lens aperture (the disk, or
+// the regular N-gon: sector k = floor(N u2), f = N u2 - k, point
+// sqrt(u1) ((1 - f) V_k + f V_k+1), uniform over the sector's triangle),
+// unit direction to the pixel's focus-plane point; *w (may be NULL): the
+// sample's weight 1 + aberration (2 rho^2 / A^2 - 1)
+__device__ __forceinline__ void lens_ray(const TraceArgs& a, unsigned q, unsigned smp, float3& O, float3& dir,
+                                         float* w = nullptr) {
     const int W = a.cam.W;
     const int i = (int)(q % (unsigned)W), j = (int)(q / (unsigned)W);
     const float3 d = pinhole_dir(a.cam, i + 0.5f + a.cam.jx, j + 0.5f + a.cam.jy);
     const float3 Pf = a.cam.pos + a.zf * d;
     uint4 x = philox4x32_10(make_uint4(q, smp, 0u, 0u), a.key);
-    float rho = a.A * sqrtf(u01(x.x));
-    float sn, cs;
-    sincospif(2.f * u01(x.y), &sn, &cs);
-    O = a.cam.pos + (rho * cs) * a.cam.right + (rho * sn) * a.cam.up;
+    float lx, ly;
+    if (a.blades >= 3) {
+        const float N = (float)a.blades, s = a.A * sqrtf(u01(x.x)), v = u01(x.y) * N;
+        const float k = floorf(v), f = v - k;
+        float s0, c0, s1, c1;
+        sincosf(a.blade_rot + 6.28318530717958648f * k / N, &s0, &c0);
+        sincosf(a.blade_rot + 6.28318530717958648f * (k + 1.f) / N, &s1, &c1);
+        lx = s * ((1.f - f) * c0 + f * c1);
+        ly = s * ((1.f - f) * s0 + f * s1);
+    } else {
+        float rho = a.A * sqrtf(u01(x.x));
+        float sn, cs;
+        sincospif(2.f * u01(x.y), &sn, &cs);
+        lx = rho * cs;
+        ly = rho * sn;
+    }
+    O = a.cam.pos + lx * a.cam.right + ly * a.cam.up;
     dir = normalize(Pf - O);
+    if (w) *w = a.A > 0.f ? 1.f + a.aberration * (2.f * (lx * lx + ly * ly) / (a.A * a.A) - 1.f) : 1.f;
 }
 
 // where the rays of the trace come from: one view (the record is the kernel
@@ -542,10 +563,11 @@ __device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
     const unsigned q = __ldg(&a.queue[k]), ro = __ldg(&a.qoff[k]);
     const int n = min((int)a.spp[q], a.smax);
     float3 SwL = f3(0, 0, 0), SfL = f3(0, 0, 0), SfP = f3(0, 0, 0);
-    float Sw = 0.f, Sf = 0.f, Swc = 0.f, Sfc = 0.f;
+    float Sw = 0.f, Sf = 0.f, Swc = 0.f, Sfc = 0.f, Ss = 0.f;
     for (int smp = 0; smp < n; ++smp) {
         float3 O, dir;
-        lens_ray(a, q, (unsigned)smp, O, dir);
+        float ws;
+        lens_ray(a, q, (unsigned)smp, O, dir, &ws);
         const float2 rc = a.recs[ro + smp];
         const int slot = __float_as_int(rc.y);
         const bool hit = slot >= 0;
@@ -572,7 +594,8 @@ __device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
         if (a.rec)
             a.rec[ro + smp] = make_float4(L.x, L.y, L.z, hit ? dot(P - a.cam.pos, a.cam.fwd)
                                                              : __int_as_float(0x7f800000));
-        float w = w_near(c), wf = 1.f - w, ac = fabsf(c);
+        // split weight scaled by the sample's aperture weight (1 on the uniform disk)
+        float w = ws * w_near(c), wf = ws - w, ac = fabsf(c);
         SwL = SwL + w * L;
         SfL = SfL + wf * L;
         SfP = SfP + wf * P;
@@ -580,11 +603,12 @@ __device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
         Sf += wf;
         Swc += w * ac;
         Sfc += wf * ac;
+        Ss += ws;
     }
     bool nok = Sw >= HDOF_EMPTY_W, fok = Sf >= HDOF_EMPTY_W;
     float in = nok ? 1.f / Sw : 0.f, inf_ = fok ? 1.f / Sf : 0.f;
     float4* o = a.rt + 3 * (size_t)q;
-    o[0] = make_float4(SwL.x * in, SwL.y * in, SwL.z * in, Sw / (float)n);
+    o[0] = make_float4(SwL.x * in, SwL.y * in, SwL.z * in, Sw / Ss);
     o[1] = make_float4(SfL.x * inf_, SfL.y * inf_, SfL.z * inf_, nok ? Swc * in : -1.f);
     o[2] = make_float4(SfP.x * inf_, SfP.y * inf_, SfP.z * inf_, fok ? Sfc * inf_ : -1.f);
 }
@@ -629,6 +653,9 @@ TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens*
     a.A = lens->aperture_radius;
     a.zf = lens->focus_dist;
     a.miss_dist = p->miss_dist;
+    a.blades = p->blades;
+    a.blade_rot = p->blade_rot;
+    a.aberration = p->aberration;
     a.key = make_uint2(p->seed, (unsigned)p->view * 65536u + (unsigned)p->frame);
     a.cap = p->trav_cap > 0 ? p->trav_cap : 64 * (b->n_nodes + b->n_tris) + 64;
     a.smax = p->spp_max;
