@@ -686,8 +686,9 @@ def batch_measure(H, dev, K, Wm, n_views, flush, e2e=True, stage_times=True):
     return {
         "value": round(batch_ms, 4), "unit": "ms/frame", "steps": K, "views": len(views), "pixels": px,
         "triangles": [int(x.stats().n_tris) for x in bvhs],
-        "tuning": {"trace_block": tune.trace_block, "trace_refill": tune.trace_refill},
-        "tuning_ms": {f"{k[0]}x{k[1]}": round(v, 3) for k, v in tune_ms.items()},
+        "tuning": {"trace_block": tune.trace_block, "trace_refill": tune.trace_refill,
+                   "trace_chunk": tune.trace_chunk, "spatial_tile": tune.spatial_tile},
+        "tuning_ms": {"x".join(map(str, k)): round(v, 3) for k, v in tune_ms.items()},
         "plain_ms": round(plain_ms, 4), "speedup_vs_plain": round(plain_ms / batch_ms, 3),
         "mrays_per_s_frame": round(rays / (batch_ms * 1e-3) / 1e6, 1),
         "mrays_per_s_trace": round(rays / (stage_ms[3] * 1e-3) / 1e6, 1) if stage_ms is not None else None,

@@ -291,11 +291,17 @@ int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const 
  *   culling with its own hit: fast when the rays of neighbouring pixels stay
  *   close, i.e. for small lens apertures); 1..32 = ray level (one ray per
  *   lane; a warp fetches new rays for its idle lanes once fewer than this
- *   many of its 32 lanes still trace). */
+ *   many of its 32 lanes still trace).
+ * trace_chunk, spatial_tile: launch granularity of the trace's work queue and
+ *   of the batched spatial gather (see the fields).  No choice changes a
+ *   result: each ray's closest hit and each pixel's gather are computed the
+ *   same way whatever warp or block runs them. */
 typedef struct hdof_tuning {
     int32_t trace_block;
     int32_t trace_refill;
-    int32_t reserved[2];
+    int32_t trace_chunk;   /* queue chunk, 0..16: with packets, packets a warp claims per atomic (0 = 1);
+                              ray level, rays per claim in units of 32 (0 = exactly the idle lanes) */
+    int32_t spatial_tile;  /* batched spatial reconstruction's pixel tile: 0 or 8 (8x8), or 16 (16x16) */
 } hdof_tuning;
 
 /* Thin-lens distributed ray trace of the masked pixels (Ray Trace section).
@@ -353,7 +359,9 @@ int hdof_trace_hits(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_para
  * pixel, no mask, no post-process).  Every pixel is traced with spp_max lens
  * samples per pass (the sampling of hdof_trace); pass k draws its samples
  * with the Philox key of frame (p->frame + k) mod 65536.  out: float
- * [H][W][4] = (mean radiance over all passes x spp_max samples rgb, 0).
+ * [H][W][4] = (mean over the passes of each pass's weighted mean radiance
+ * rgb, 0); on the uniform disk (aberration 0) the plain mean of all
+ * passes x spp_max samples.
  * workspace: hdof_workspace_bytes(width, height, p) bytes (the post-filter
  * region holds each pass's trace output).  hint_tri as for hdof_trace. */
 int hdof_reference_rt(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,

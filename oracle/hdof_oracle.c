@@ -1131,9 +1131,11 @@ void orc_trace_hits(const void* sp, const orc_camera* cam, const orc_lens* lens,
 
 /* Full ray-traced depth of field (the reference the paper's Fig. 1 sets
  * beside the hybrid frame): the thin-lens image by distributed ray tracing,
- * every pixel, no mask.  out[q] = mean Lambert radiance of the closest hits
- * of passes x spp_max lens samples; pass k draws its samples with the key of
- * frame (frame + k) mod 65536.  Misses contribute 0. */
+ * every pixel, no mask.  out[q] = the mean over passes of each pass's
+ * weighted mean Lambert radiance of the closest hits of spp_max lens samples
+ * (sample weights as in the trace; 1 on the uniform disk, where this is the
+ * plain mean of all samples); pass k draws its samples with the key of frame
+ * (frame + k) mod 65536.  Misses contribute 0. */
 void orc_reference_rt(const void* sp, const orc_camera* cam, const orc_lens* lens, const orc_params* p,
                       int32_t passes, double* out) {
     const oscene* s = (const oscene*)sp;
@@ -1142,10 +1144,11 @@ void orc_reference_rt(const void* sp, const orc_camera* cam, const orc_lens* len
     for (int32_t j = 0; j < H; ++j)
         for (int32_t i = 0; i < W; ++i) {
             size_t q = (size_t)j * W + i;
-            double S[3] = {0, 0, 0}, n = 0.0;
+            double S[3] = {0, 0, 0};
             for (int32_t k = 0; k < passes; ++k) {
                 orc_params pk = *p;
                 pk.frame = (int32_t)(((uint32_t)p->frame + (uint32_t)k) & 0xFFFFu);
+                double Sk[3] = {0, 0, 0}, n = 0.0;
                 for (int smp = 0; smp < p->spp_max; ++smp) {
                     double O[3], dir[3], th_, bary[3], n_[3], L[3], ws;
                     orc_lens_ray(cam, lens, &pk, (int64_t)q, smp, O, dir, &ws);
@@ -1153,10 +1156,11 @@ void orc_reference_rt(const void* sp, const orc_camera* cam, const orc_lens* len
                     int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
                     if (id < 0) continue;
                     shade_hit(s, id, bary, dir, p, n_, L);
-                    for (int c = 0; c < 3; ++c) S[c] += ws * L[c];
+                    for (int c = 0; c < 3; ++c) Sk[c] += ws * L[c];
                 }
+                for (int c = 0; c < 3; ++c) S[c] += Sk[c] / n;
             }
-            for (int c = 0; c < 3; ++c) out[4 * q + c] = S[c] / n;
+            for (int c = 0; c < 3; ++c) out[4 * q + c] = S[c] / passes;
             out[4 * q + 3] = 0.0;
         }
 }

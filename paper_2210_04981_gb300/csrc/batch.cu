@@ -122,7 +122,8 @@ Layout layout(int n) {
 }
 
 // writes the host image of the device block; blocks[k] = stage k's grid
-int fill_image(const hdof_view* views, int n, unsigned* st, const Layout& L, char* img, int* blocks) {
+int fill_image(const hdof_view* views, int n, unsigned* st, const Layout& L, char* img, int* blocks,
+               const hdof_tuning& tune) {
     std::memset(img, 0, L.bytes);
     for (int k = 0; k < N_STAGES; ++k) {
         const size_t sz = kStages[k].size();
@@ -131,7 +132,9 @@ int fill_image(const hdof_view* views, int n, unsigned* st, const Layout& L, cha
         long long total = 0;
         for (int v = 0; v < n; ++v) {
             int gx = 0, gy = 0;
-            kStages[k].fill(views[v], view_ws(views[v]), st, img + L.args[k] + (size_t)v * sz, &gx, &gy);
+            ViewWs w = view_ws(views[v]);
+            w.spatial_tile = tune.spatial_tile;
+            kStages[k].fill(views[v], w, st, img + L.args[k] + (size_t)v * sz, &gx, &gy);
             prefix[v] = (int)total;
             gxs[v] = gx;
             total += (long long)gx * gy;
@@ -189,12 +192,16 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     *out = nullptr;
     HDOF_CHECK_ARG(views && n_views >= 1 && n_views <= 65536, "hdof_batch_create: need 1..65536 views, got %d",
                    (int)n_views);
-    hdof_tuning t = {128, 4, {0, 0}};
+    hdof_tuning t = {128, 4, 0, 0};
     if (tuning) t = *tuning;
     HDOF_CHECK_ARG(t.trace_block == 64 || t.trace_block == 128 || t.trace_block == 256,
                    "hdof_batch_create: trace_block %d not in {64, 128, 256}", (int)t.trace_block);
     HDOF_CHECK_ARG(t.trace_refill >= 0 && t.trace_refill <= 32, "hdof_batch_create: trace_refill %d not in 0..32",
                    (int)t.trace_refill);
+    HDOF_CHECK_ARG(t.trace_chunk >= 0 && t.trace_chunk <= 16, "hdof_batch_create: trace_chunk %d not in 0..16",
+                   (int)t.trace_chunk);
+    HDOF_CHECK_ARG(t.spatial_tile == 0 || t.spatial_tile == 8 || t.spatial_tile == 16,
+                   "hdof_batch_create: spatial_tile %d not in {0, 8, 16}", (int)t.spatial_tile);
     int dev = 0;
     HDOF_CUDA(cudaGetDevice(&dev), "hdof_batch_create: device");
     const int n = n_views;
@@ -214,7 +221,7 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     char* host = nullptr;
     HDOF_CUDA(cudaMallocHost(&host, L.bytes), "hdof_batch_create: host image");
     int blocks[N_STAGES] = {0};
-    if ((rc = fill_image(views, n, st, L, host, blocks))) {
+    if ((rc = fill_image(views, n, st, L, host, blocks, t))) {
         cudaFreeHost(host);
         return rc;
     }
@@ -297,7 +304,7 @@ extern "C" int hdof_batch_update(hdof_batch* b, const hdof_view* views, int32_t 
     // the previous upload may still read the host image
     HDOF_CUDA(cudaEventSynchronize(b->uploaded), "hdof_batch_update: previous upload");
     int blocks[N_STAGES];
-    if ((rc = fill_image(views, b->n, st, b->L, b->host, blocks))) return rc;
+    if ((rc = fill_image(views, b->n, st, b->L, b->host, blocks, b->tuning))) return rc;
     cudaStream_t s = as_stream(stream);
     HDOF_CUDA(cudaMemcpyAsync(b->dmem, b->host, b->L.bytes, cudaMemcpyHostToDevice, s), "hdof_batch_update: upload");
     HDOF_CUDA(cudaEventRecord(b->uploaded, s), "hdof_batch_update: event");
@@ -334,7 +341,8 @@ extern "C" int hdof_batch_render_range(const hdof_batch* b, int32_t first, int32
             case HDOF_STAGE_TRACE: {
                 const hdof_batch::Stage& t = b->stage[S_TRACE];
                 int rc = trace_launch_batch(b->scan_args, t.args, t.grid, t.blocks, b->n, b->gq,
-                                            b->tuning.trace_block, b->tuning.trace_refill, b->trace_blocks, s);
+                                            b->tuning.trace_block, b->tuning.trace_refill, b->tuning.trace_chunk,
+                                            b->trace_blocks, s);
                 if (rc) return rc;
                 break;
             }
@@ -343,10 +351,12 @@ extern "C" int hdof_batch_render_range(const hdof_batch* b, int32_t first, int32
                 run(S_PF_ROWSCAN);
                 run(S_PF_GATHER);
                 break;
-            case HDOF_STAGE_RECONSTRUCT:
+            case HDOF_STAGE_RECONSTRUCT: {
                 run(S_TEMPORAL);
-                run(S_SPATIAL);
+                const hdof_batch::Stage& g = b->stage[S_SPATIAL];
+                spatial_launch_batch_tile(g.args, g.grid, g.blocks, b->tuning.spatial_tile, s);
                 break;
+            }
             default: run(S_COMPOSITE); break;
         }
         HDOF_LAUNCHED("hdof_batch_render");

@@ -54,6 +54,7 @@ __device__ __forceinline__ const T& batch_record(const T* __restrict__ tab, int 
 struct ViewWs {
     uint8_t* tiles;      // mask tile flags
     float* tile_r;       // largest CoC radius per mask tile (CoC-scaled mask)
+    int spatial_tile;    // the batch's spatial gather tile (hdof_tuning.spatial_tile), 0 = default
     unsigned* counts;    // [2 * ntiles] traced pixels, rays per 16x16 tile
     unsigned* offsets;   // [ntiles]
     unsigned* roffsets;  // [ntiles]
@@ -89,6 +90,7 @@ inline ViewWs view_ws(const hdof_view& v) {
     ViewWs w;
     w.tiles = reinterpret_cast<uint8_t*>(base);
     w.tile_r = reinterpret_cast<float*>(base + L.mask_tiles);
+    w.spatial_tile = 0;
     w.counts = reinterpret_cast<unsigned*>(base);
     w.offsets = w.counts + 2 * ntiles;
     w.roffsets = w.offsets + ntiles;
@@ -133,6 +135,8 @@ int trace_batch_grid(int block, int refill, int* blocks);
 // persistent trace over the concatenated ray lists, and the per-pixel
 // resolve (grid of the trace records' gx x gy blocks per view)
 int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid resolve, int resolve_blocks, int n,
-                       unsigned* gq, int block, int refill, int blocks, cudaStream_t s);
+                       unsigned* gq, int block, int refill, int chunk, int blocks, cudaStream_t s);
+// the batched spatial gather with a pixel tile of 8 or 16
+void spatial_launch_batch_tile(const void* args, BatchGrid g, int blocks, int tile, cudaStream_t s);
 
 }  // namespace hdof

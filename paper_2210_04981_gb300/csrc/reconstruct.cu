@@ -263,23 +263,25 @@ __device__ __forceinline__ void spatial_pixel(const SpatialArgs& a, int i, int j
                             0.f);
 }
 
-// block = one 8x8 tile, one thread per pixel: the tile's traced pixels are
-// compacted (row-major) so the threads that run all gather for traced
-// pixels, in one round; small blocks keep many tiles resident where few of
-// their pixels are traced
+// block = one T x T tile (T = 8 or 16), one thread per pixel: the tile's
+// traced pixels are compacted (row-major) so the threads that run all gather
+// for traced pixels, in one round; small blocks keep many tiles resident
+// where few of their pixels are traced
 constexpr int SP_TILE = 8, SP_THREADS = SP_TILE * SP_TILE;
+template <int T>
 __device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int by) {
-    __shared__ unsigned char s_list[SP_THREADS];
-    __shared__ int s_cnt[SP_THREADS / 32];
+    constexpr int NT = T * T;
+    __shared__ unsigned char s_list[NT];
+    __shared__ int s_cnt[NT / 32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int i0 = bx * SP_TILE + (t % SP_TILE), j0 = by * SP_TILE + (t / SP_TILE);
+    const int i0 = bx * T + (t % T), j0 = by * T + (t / T);
     const bool traced = i0 < a.W && j0 < a.H && __ldg(&a.crt[(size_t)j0 * a.W + i0].w) >= 0.f;
     const unsigned tm = __ballot_sync(0xffffffffu, traced);
     if (lane == 0) s_cnt[w] = __popc(tm);
     __syncthreads();
     int off = 0, n = 0;
 #pragma unroll
-    for (int c = 0; c < SP_THREADS / 32; ++c) {
+    for (int c = 0; c < NT / 32; ++c) {
         off += c < w ? s_cnt[c] : 0;
         n += s_cnt[c];
     }
@@ -287,15 +289,18 @@ __device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int b
     __syncthreads();
     if (t < n) {
         const int li = s_list[t];
-        spatial_pixel(a, bx * SP_TILE + (li % SP_TILE), by * SP_TILE + (li / SP_TILE));
+        spatial_pixel(a, bx * T + (li % T), by * T + (li / T));
     }
 }
 
-__global__ void __launch_bounds__(SP_THREADS) k_spatial(SpatialArgs a) { spatial_body(a, blockIdx.x, blockIdx.y); }
-__global__ void __launch_bounds__(SP_THREADS) k_spatial_batch(const SpatialArgs* __restrict__ a, BatchGrid g) {
+__global__ void __launch_bounds__(SP_THREADS) k_spatial(SpatialArgs a) {
+    spatial_body<SP_TILE>(a, blockIdx.x, blockIdx.y);
+}
+template <int T>
+__global__ void __launch_bounds__(T * T) k_spatial_batch(const SpatialArgs* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
-    spatial_body(batch_record(a, v), bx, by);
+    spatial_body<T>(batch_record(a, v), bx, by);
 }
 
 TemporalArgs temporal_args(const float* rt, const hdof_gbuf* in, const uint8_t* spp, const hdof_camera* cam,
@@ -392,17 +397,22 @@ void temporal_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream
 }
 
 size_t spatial_args_size() { return sizeof(SpatialArgs); }
-void spatial_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int* gx, int* gy) {
+void spatial_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
     *reinterpret_cast<SpatialArgs*>(dst) =
         SpatialArgs{reinterpret_cast<const float4*>(v.crt), reinterpret_cast<const float2*>(v.hist_out.mom),
                     v.hist_out.hlen, v.cam.width, v.cam.height, v.params.r_s, v.params.var_ref,
                     reinterpret_cast<float4*>(v.crec), nullptr};
-    *gx = (v.cam.width + SP_TILE - 1) / SP_TILE;
-    *gy = (v.cam.height + SP_TILE - 1) / SP_TILE;
+    const int T = w.spatial_tile == 16 ? 16 : SP_TILE;
+    *gx = (v.cam.width + T - 1) / T;
+    *gy = (v.cam.height + T - 1) / T;
 }
 void spatial_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
+    spatial_launch_batch_tile(args, g, blocks, SP_TILE, s);
+}
+void spatial_launch_batch_tile(const void* args, BatchGrid g, int blocks, int tile, cudaStream_t s) {
     ProfScope ps_("batch_spatial", s);
-    k_spatial_batch<<<blocks, SP_THREADS, 0, s>>>(static_cast<const SpatialArgs*>(args), g);
+    if (tile == 16) k_spatial_batch<16><<<blocks, 256, 0, s>>>(static_cast<const SpatialArgs*>(args), g);
+    else k_spatial_batch<SP_TILE><<<blocks, SP_THREADS, 0, s>>>(static_cast<const SpatialArgs*>(args), g);
 }
 
 }  // namespace hdof

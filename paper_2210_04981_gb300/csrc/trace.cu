@@ -394,7 +394,8 @@ __device__ __forceinline__ void trace_rays_steps(const Src& src, RayLane& L, int
 }
 
 template <class Src>
-__device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, unsigned* head, int refill) {
+__device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, unsigned* head, int refill,
+                                                int chunk) {
     const unsigned FULL = 0xffffffffu;
     const float INF = __int_as_float(0x7f800000);
     const int lane = threadIdx.x & 31;
@@ -405,15 +406,33 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
     L.leaf = NO_LEAF;
     L.r = 0;
     int stack[HDOF_STACK];
+    // chunk > 0: the warp claims 32 x chunk rays per atomic into a warp-uniform
+    // pool and serves its idle lanes from it; chunk 0: exactly the idle lanes'
+    // count per atomic.  Which warp traces a ray does not change its hit.
+    unsigned pool = 0, pool_end = 0;
     while (true) {
         const unsigned need = __ballot_sync(FULL, !L.live && !L.done);
         if (need) {
             const int leader = __ffs(need) - 1;
-            unsigned base = 0;
-            if (lane == leader) base = atomicAdd(head, (unsigned)__popc(need));
-            base = __shfl_sync(FULL, base, leader);
-            if (!L.live && !L.done) {
-                const unsigned g = base + __popc(need & lt);
+            unsigned base = 0, navail = (unsigned)__popc(need);
+            if (chunk <= 0) {
+                if (lane == leader) base = atomicAdd(head, navail);
+                base = __shfl_sync(FULL, base, leader);
+            } else {
+                if (pool == pool_end) {
+                    unsigned b = 0;
+                    if (lane == leader) b = atomicAdd(head, 32u * (unsigned)chunk);
+                    b = __shfl_sync(FULL, b, leader);
+                    pool = b;
+                    pool_end = b + 32u * (unsigned)chunk;
+                }
+                base = pool;
+                navail = min(pool_end - pool, navail);
+                pool += navail;
+            }
+            const unsigned rk = __popc(need & lt);
+            if (!L.live && !L.done && rk < navail) {
+                const unsigned g = base + rk;
                 if (g < total) {
                     L.v = src.locate(g, L.r);
                     const TraceArgs& a = src.at(L.v);
@@ -474,16 +493,23 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
 // (closest_hit_warp); in a batched list the rays of one view go together.
 // Same records as the ray-level form.
 template <class Src>
-__device__ __forceinline__ void trace_packets_body(const Src& src, unsigned total, unsigned* head, int* stack) {
+__device__ __forceinline__ void trace_packets_body(const Src& src, unsigned total, unsigned* head, int* stack,
+                                                   int chunk) {
     const unsigned FULL = 0xffffffffu;
     const float INF = __int_as_float(0x7f800000);
     const int lane = threadIdx.x & 31;
+    const unsigned nc = chunk > 1 ? (unsigned)chunk : 1u;  // packets claimed per atomic
+    unsigned base = 0, left = 0;
     while (true) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(head, 32u);
-        base = __shfl_sync(FULL, base, 0);
+        if (!left) {
+            if (lane == 0) base = atomicAdd(head, 32u * nc);
+            base = __shfl_sync(FULL, base, 0);
+            left = nc;
+        }
         if (base >= total) break;
         const unsigned g = base + lane;
+        base += 32u;
+        --left;
         bool pending = g < total;
         unsigned r = 0;
         int v = 0;
@@ -529,28 +555,29 @@ __device__ __forceinline__ void trace_packets_body(const Src& src, unsigned tota
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS) k_trace_packets(TraceArgs a) {
+__global__ void __launch_bounds__(BS) k_trace_packets(TraceArgs a, int chunk) {
     __shared__ int s_stack[BS / 32][HDOF_STACK];
-    trace_packets_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], s_stack[threadIdx.x >> 5]);
+    trace_packets_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], s_stack[threadIdx.x >> 5], chunk);
 }
 
 template <int BS>
 __global__ void __launch_bounds__(BS) k_trace_packets_batch(const TraceArgs* __restrict__ tab,
-                                                            const unsigned* __restrict__ gq, int n, unsigned* head) {
+                                                            const unsigned* __restrict__ gq, int n, unsigned* head,
+                                                            int chunk) {
     __shared__ int s_stack[BS / 32][HDOF_STACK];
-    trace_packets_body(ManyViews{tab, gq, n}, __ldcg(&gq[n]), head, s_stack[threadIdx.x >> 5]);
+    trace_packets_body(ManyViews{tab, gq, n}, __ldcg(&gq[n]), head, s_stack[threadIdx.x >> 5], chunk);
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS) k_trace_rays(TraceArgs a, int refill) {
-    trace_rays_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], refill);
+__global__ void __launch_bounds__(BS) k_trace_rays(TraceArgs a, int refill, int chunk) {
+    trace_rays_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], refill, chunk);
 }
 
 template <int BS>
 __global__ void __launch_bounds__(BS) k_trace_rays_batch(const TraceArgs* __restrict__ tab,
                                                          const unsigned* __restrict__ gq, int n, unsigned* head,
-                                                         int refill) {
-    trace_rays_body(ManyViews{tab, gq, n}, __ldcg(&gq[n]), head, refill);
+                                                         int refill, int chunk) {
+    trace_rays_body(ManyViews{tab, gq, n}, __ldcg(&gq[n]), head, refill, chunk);
 }
 
 // per traced pixel (queue entry k): its samples' records in sample order ->
@@ -815,20 +842,20 @@ void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst, in
 int trace_batch_grid(int block, int refill, int* blocks) { return rays_grid(true, refill == 0, block, blocks); }
 
 int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid resolve, int resolve_blocks, int n,
-                       unsigned* gq, int block, int refill, int blocks, cudaStream_t s) {
+                       unsigned* gq, int block, int refill, int chunk, int blocks, cudaStream_t s) {
     k_ray_prefix<<<1, 1024, 0, s>>>(static_cast<const ScanArgs*>(scan_args), n, gq);
     HDOF_LAUNCHED("batched trace: ray prefix");
     const TraceArgs* a = static_cast<const TraceArgs*>(trace_args);
     {
         ProfScope ps_(refill == 0 ? "batch_trace_packets" : "batch_trace_rays", s);
         if (refill == 0) {  // warp packets
-            if (block == 64) k_trace_packets_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1);
-            else if (block == 256) k_trace_packets_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1);
-            else k_trace_packets_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1);
+            if (block == 64) k_trace_packets_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+            else if (block == 256) k_trace_packets_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+            else k_trace_packets_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, chunk);
         } else {  // ray level, dynamic fetch
-            if (block == 64) k_trace_rays_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, refill);
-            else if (block == 256) k_trace_rays_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, refill);
-            else k_trace_rays_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, refill);
+            if (block == 64) k_trace_rays_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, refill, chunk);
+            else if (block == 256) k_trace_rays_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, refill, chunk);
+            else k_trace_rays_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, refill, chunk);
     }
     HDOF_LAUNCHED("batched trace");
     }
@@ -847,9 +874,9 @@ using namespace hdof;
 constexpr float PACKET_K_MAX = 20.f;
 
 template <int BS>
-void launch_trace(const TraceArgs& a, int refill, int blocks, cudaStream_t s) {
-    if (refill == 0) k_trace_packets<BS><<<blocks, BS, 0, s>>>(a);
-    else k_trace_rays<BS><<<blocks, BS, 0, s>>>(a, refill);
+void launch_trace(const TraceArgs& a, int refill, int chunk, int blocks, cudaStream_t s) {
+    if (refill == 0) k_trace_packets<BS><<<blocks, BS, 0, s>>>(a, chunk);
+    else k_trace_rays<BS><<<blocks, BS, 0, s>>>(a, refill, chunk);
 }
 
 extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p,
@@ -871,6 +898,8 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
                        "hdof_trace: trace_block %d not in {64, 128, 256}", (int)t.trace_block);
         HDOF_CHECK_ARG(t.trace_refill >= 0 && t.trace_refill <= 32, "hdof_trace: trace_refill %d not in 0..32",
                        (int)t.trace_refill);
+        HDOF_CHECK_ARG(t.trace_chunk >= 0 && t.trace_chunk <= 16, "hdof_trace: trace_chunk %d not in 0..16",
+                       (int)t.trace_chunk);
     } else {
         const float K = lens->aperture_radius * (float)cam->height / (lens->focus_dist * cam->tan_half_fovy);
         t.trace_block = 128;
@@ -904,9 +933,9 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
     if ((rc = rays_grid(false, t.trace_refill == 0, t.trace_block, &blocks))) return rc;
     {
         ProfScope ps_(t.trace_refill == 0 ? "trace_packets" : "trace_rays", s);
-        if (t.trace_block == 64) launch_trace<64>(a, t.trace_refill, blocks, s);
-        else if (t.trace_block == 256) launch_trace<256>(a, t.trace_refill, blocks, s);
-        else launch_trace<128>(a, t.trace_refill, blocks, s);
+        if (t.trace_block == 64) launch_trace<64>(a, t.trace_refill, t.trace_chunk, blocks, s);
+        else if (t.trace_block == 256) launch_trace<256>(a, t.trace_refill, t.trace_chunk, blocks, s);
+        else launch_trace<128>(a, t.trace_refill, t.trace_chunk, blocks, s);
         HDOF_LAUNCHED("hdof_trace: trace");
     }
     ProfScope ps_("trace_resolve", s);

@@ -73,7 +73,8 @@ class hdof_view(C.Structure):
 
 
 class hdof_tuning(C.Structure):
-    _fields_ = [("trace_block", C.c_int32), ("trace_refill", C.c_int32), ("reserved", C.c_int32 * 2)]
+    _fields_ = [("trace_block", C.c_int32), ("trace_refill", C.c_int32), ("trace_chunk", C.c_int32),
+                ("spatial_tile", C.c_int32)]
 
 
 class hdof_post_state(C.Structure):
@@ -504,9 +505,10 @@ class Renderer:
 
 # ------------------------------------------------------ batched multi-view --
 
-def tuning(trace_block=128, trace_refill=0) -> hdof_tuning:
+def tuning(trace_block=128, trace_refill=0, trace_chunk=0, spatial_tile=0) -> hdof_tuning:
     t = hdof_tuning()
     t.trace_block, t.trace_refill = int(trace_block), int(trace_refill)
+    t.trace_chunk, t.spatial_tile = int(trace_chunk), int(spatial_tile)
     return t
 
 

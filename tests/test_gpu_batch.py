@@ -64,12 +64,16 @@ def _assert_same(a: H.Renderer, b: H.Renderer, tag):
         assert eq(getattr(ha, name)[tr], getattr(hb, name)[tr]), f"{tag}: history {name}"
 
 
-@pytest.mark.parametrize("block,refill", [(128, 0), (64, 0), (256, 0), (128, 16), (64, 32), (256, 1)])
-def test_batch_equals_single_view(small, block, refill):
+@pytest.mark.parametrize("block,refill,chunk,tile", [(128, 0, 0, 8), (64, 0, 0, 0), (256, 0, 3, 16), (128, 16, 0, 8),
+                                                     (64, 32, 2, 16), (256, 1, 8, 8), (128, 4, 1, 16), (64, 0, 16, 0)])
+def test_batch_equals_single_view(small, block, refill, chunk, tile):
+    """Every launch shape of the batched frame (trace block and form, queue
+    chunk, spatial stencil tile) renders each view bit for bit as the
+    single-view calls do."""
     scenes, bvhs, views = small
     rs = _singles(bvhs, views)
     b = H.Batch([bvhs[v.room] for v in views], [(v.width, v.height) for v in views], [v.params for v in views],
-                tune=H.tuning(block, refill))
+                tune=H.tuning(block, refill, chunk, tile))
     for k in range(3):
         _run_singles(rs, views, k)
         b.frame(*_frame_args(views, k))

@@ -360,7 +360,8 @@ def test_trace_hint_does_not_change_results():
 @pytest.mark.parametrize("aperture", [None, 0.08])
 def test_trace_forms_agree(aperture):
     """Warp packets and the ray-level trace (every block size, several refill
-    thresholds, with and without the hint) give the same trace bit for bit:
+    thresholds and queue chunks, with and without the hint) give the same
+    trace bit for bit:
     the box test never culls a box that could hold the closest hit, so the
     (t, id) minimum does not depend on the traversal order.  The small
     aperture is the room's (packets by default), 0.08 a wide one."""
@@ -376,7 +377,8 @@ def test_trace_forms_agree(aperture):
     spp = dev((rng.integers(0, 9, (Hh, W)) * (rng.uniform(size=(Hh, W)) < 0.6)).astype(np.uint8))
     outs = []
     for tune, hint in [(None, g.tri), (H.tuning(128, 0), None), (H.tuning(64, 0), g.tri), (H.tuning(256, 0), g.tri),
-                       (H.tuning(128, 4), g.tri), (H.tuning(64, 1), None), (H.tuning(256, 32), g.tri)]:
+                       (H.tuning(128, 4), g.tri), (H.tuning(64, 1), None), (H.tuning(256, 32), g.tri),
+                       (H.tuning(128, 0, 4), g.tri), (H.tuning(64, 4, 2), g.tri), (H.tuning(256, 8, 16), None)]:
         rt = torch.zeros((Hh, W, 12), dtype=torch.float32, device="cuda")
         stats = torch.zeros(2, dtype=torch.int32, device="cuda")
         H.hdof_trace(bvh, cam, lens, p, spp, rt, stats, workspace(W, Hh, p), hint=hint, tune=tune)
