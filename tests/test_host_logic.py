@@ -22,18 +22,22 @@ def test_autotune_picks_fastest_and_caches(tmp_path, monkeypatch):
     monkeypatch.setattr(autotune, "workload_shape", lambda b: shape)
     calls = []
 
-    def fake_time(batch, frame_args, block, refill, reps=5, warmup=2):
-        calls.append((block, refill))
-        return 1.0 + abs(block - 128) / 64.0 + abs(refill - 4) / 8.0
+    def fake_time(batch, frame_args, shape, reps=5, warmup=2):
+        block, refill, chunk, tile = shape
+        calls.append(tuple(shape))
+        return 1.0 + abs(block - 128) / 64.0 + abs(refill - 4) / 8.0 + abs(chunk - 2) / 16.0 + (tile == 8) / 32.0
 
     monkeypatch.setattr(autotune, "time_shape", fake_time)
     t, times = autotune.tune(object(), None)
-    assert (t.trace_block, t.trace_refill) == (128, 4)
-    assert sorted(calls) == sorted(autotune.CANDIDATES) and len(times) == len(autotune.CANDIDATES)
+    assert (t.trace_block, t.trace_refill, t.trace_chunk, t.spatial_tile) == (128, 4, 2, 16)
+    # staged: every (block, form) at chunk 0 and tile 8, then the chunks, then the tiles
+    n = len(autotune.CANDIDATES) + (len(autotune.CHUNKS) - 1) + (len(autotune.TILES) - 1)
+    assert len(calls) == len(set(calls)) == len(times) == n
+    assert {c[:2] for c in calls} >= set(autotune.CANDIDATES)
     # second call: a cache hit, nothing timed
     t2, times2 = autotune.tune(object(), None)
-    assert (t2.trace_block, t2.trace_refill) == (128, 4) and times2 == {}
-    assert len(calls) == len(autotune.CANDIDATES)
+    assert (t2.trace_block, t2.trace_refill, t2.trace_chunk, t2.spatial_tile) == (128, 4, 2, 16) and times2 == {}
+    assert len(calls) == n
     # the key separates GPUs and workloads
     assert autotune.signature(shape, "a") != autotune.signature(shape, "b")
     assert autotune.signature(shape, "a") != autotune.signature(shape[:1], "a")
