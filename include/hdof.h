@@ -22,6 +22,13 @@
  *   message of the calling thread's last failure.  Calls never throw.
  * - Kernel-side watchdogs (a capped traversal loop) never hang: they record
  *   HDOF_ETIMEOUT in a device status word that hdof_sync() reports.
+ * - The library keeps per-device state for the life of the process (the
+ *   post-filter's area table, the device addresses of its status word and of
+ *   hdof_mask_noalloc's tile array): do not keep using it across a
+ *   cudaDeviceReset of a device it has run on.
+ * - The first post-filter call on a device (hdof_postfilter, the batched
+ *   frame, hdof_post_forward/backward) uploads the area table and waits for
+ *   it; make that first call before capturing a stream into a graph.
  * - Camera space: the camera at `pos` looks along +fwd with +right, +up;
  *   the screen point of pixel (i, j) this frame is (i + 0.5 + jitter[0],
  *   j + 0.5 + jitter[1]).  Depth is view-space z (distance along fwd).

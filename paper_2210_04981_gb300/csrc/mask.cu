@@ -1,8 +1,8 @@
-// adaptive ray mask (Ray Trace section).  "Like Canny edge detection",
-// a Gaussian filter on the G-buffer reduces noise and jaggies, a Sobel kernel
-// on the filtered normal and depth finds geometry edges, and a temporally
-// accumulated luminance variance from previous frames adds rays where the
-// ray-traced output is noisy or new.
+// adaptive ray mask (Ray Trace section): the G-buffer is smoothed by a
+// Gaussian before a Sobel gradient of its normal and depth marks geometry
+// edges (the smoothing suppresses noise and staircase edges, as in Canny's
+// detector); a luminance variance accumulated over previous frames adds rays
+// where the traced result is still noisy or has just appeared.
 //
 // k_mask_edge: one 16x16 pixel block per CUDA block; the block's (16+6)^2
 //   nd halo is staged in shared memory once, the separable 5-tap Gaussian

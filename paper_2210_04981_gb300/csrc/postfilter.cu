@@ -1,7 +1,7 @@
 // post-process CoC filter of the sharp image (Design section: the sharp
-// rasterised image "undergoes post-process filtering"; the Reconstruction
-// section states its rejection rule: samples whose CoC radius is smaller
-// than their distance to the pixel are rejected).
+// rasterised image is blurred by a post-process filter; the Reconstruction
+// section gives the gather's rejection rule: a sample counts only if its CoC
+// radius reaches the pixel).
 //
 // Scatter-as-gather with soft disks.  Pixel q scatters its colour over
 // s(r_q - d), s(x) = clamp(x + 1/2, 0, 1), r_q = min(|c(z_q)|/2, r_max),

@@ -671,40 +671,49 @@ class PostPath:
         self.ws = torch.empty(hdof_post_workspace_bytes(W, H, p), dtype=torch.uint8, device=z.device)
         self.col4 = torch.zeros((H, W, 4), dtype=torch.float32, device=z.device)
 
-    def forward(self, col, zf, A):
-        self.col4[..., :3] = col
-        g = GBuffer.from_tensors(self.nd, self.col4)
-        hdof_post_forward(g, self.spp, self.rec, self.ray_off, self.hs, self.cam, _Lens(zf, A, self.focal), self.p,
-                          self.st, self.ws)
-        return self.st.out[..., :3]
+    def new_state(self):
+        """A state (and colour plane) of its own, e.g. one per autograd context."""
+        H, W = self.spp.shape
+        return PostState(W, H, self.spp.device), torch.zeros((H, W, 4), dtype=torch.float32, device=self.spp.device)
 
-    def backward(self, grad_out, zf, A):
+    def forward(self, col, zf, A, state=None):
+        st, col4 = state if state is not None else (self.st, self.col4)
+        col4[..., :3] = col
+        g = GBuffer.from_tensors(self.nd, col4)
+        hdof_post_forward(g, self.spp, self.rec, self.ray_off, self.hs, self.cam, _Lens(zf, A, self.focal), self.p,
+                          st, self.ws)
+        return st.out[..., :3]
+
+    def backward(self, grad_out, zf, A, state=None):
+        st, col4 = state if state is not None else (self.st, self.col4)
         H, W = self.spp.shape
         g4 = torch.zeros((H, W, 4), dtype=torch.float32, device=grad_out.device)
         g4[..., :3] = grad_out
         gcol = torch.empty_like(g4)
         glens = torch.empty(2, dtype=torch.float32, device=grad_out.device)
-        g = GBuffer.from_tensors(self.nd, self.col4)
+        g = GBuffer.from_tensors(self.nd, col4)
         hdof_post_backward(g, self.spp, self.rec, self.ray_off, self.hs, self.cam, _Lens(zf, A, self.focal), self.p,
-                           self.st, g4, gcol, glens, self.ws)
+                           st, g4, gcol, glens, self.ws)
         return gcol[..., :3], glens
 
 
 class HdofPost(torch.autograd.Function):
     """out = post-path(col [H,W,3], lens_params [2] = (focus, aperture)) with
-    the hand-written adjoint of hdof_post_backward."""
+    the hand-written adjoint of hdof_post_backward.  Each call keeps its own
+    forward state for its backward (no forward is re-run).  The lens enters
+    the C calls as a host record, so the forward reads lens_params back from
+    the device once."""
 
     @staticmethod
     def forward(ctx, col, lens_params, path: PostPath):
         zf, A = (float(x) for x in lens_params.detach().cpu().tolist())
-        out = path.forward(col.detach().contiguous(), zf, A).clone()
-        ctx.path, ctx.zf, ctx.A = path, zf, A
-        ctx.col = col.detach().contiguous()
+        state = path.new_state()
+        out = path.forward(col.detach().contiguous(), zf, A, state).clone()
+        ctx.path, ctx.zf, ctx.A, ctx.state = path, zf, A, state
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        path = ctx.path
-        path.forward(ctx.col, ctx.zf, ctx.A)  # the state buffers are shared: restore this call's
-        gcol, glens = path.backward(grad_out.contiguous().float(), ctx.zf, ctx.A)
+        gcol, glens = ctx.path.backward(grad_out.contiguous().float(), ctx.zf, ctx.A, ctx.state)
+        ctx.state = None
         return gcol, glens.to(grad_out.device), None

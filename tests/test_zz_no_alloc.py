@@ -58,3 +58,28 @@ def test_noalloc_mask_rejects_frames_beyond_capacity():
     with pytest.raises(H.HdofError) as ei:
         H.hdof_mask_noalloc(g, None, p, e, e.clone())
     assert ei.value.code == -1 and "capacity" in str(ei.value)
+
+
+def test_noalloc_mask_at_exact_capacity():
+    """A frame of exactly HDOF_MASK_NOALLOC_MAX_TILES tiles (256 x 256 at tile
+    1) is accepted and equals hdof_mask bit for bit; one more column of tiles
+    (257 x 256) is rejected."""
+    p = hi.Params(tile=1, dilate=2, spp_max=8)
+    W, Hh = 256, 256
+    gb = hi.random_gbuffer(W, Hh, seed=31)
+    g = _gbuf(gb)
+    e_ref = torch.empty((Hh, W), dtype=torch.uint8, device="cuda")
+    s_ref = torch.empty_like(e_ref)
+    ws = torch.empty(H.hdof_workspace_bytes(W, Hh, p), dtype=torch.uint8, device="cuda")
+    H.hdof_mask(g, None, p, e_ref, s_ref, ws)
+    e = torch.full_like(e_ref, 7)
+    s = torch.full_like(e_ref, 7)
+    H.hdof_mask_noalloc(g, None, p, e, s)
+    H.hdof_sync()
+    assert torch.equal(e, e_ref) and torch.equal(s, s_ref)
+    assert 0 < int((s_ref > 0).sum()) < W * Hh
+    g2 = H.GBuffer(257, 256)
+    e2 = torch.empty((256, 257), dtype=torch.uint8, device="cuda")
+    with pytest.raises(H.HdofError) as ei:
+        H.hdof_mask_noalloc(g2, None, p, e2, e2.clone())
+    assert ei.value.code == -1 and "capacity" in str(ei.value)
