@@ -271,7 +271,8 @@ def fp32_peak(H, dev, reps=6, iters=20000):
 STAGES = ["gbuffer", "mask", "trace", "postfilter", "reconstruct", "composite"]
 
 
-def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, flush, profile=False):
+def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, flush, profile=False,
+                  static=False):
     """Warm-up frames, then K consecutive timed frames (L2 flushed between
     them, outside the events) through the six C-ABI calls.  Returns the
     renderer, the per-frame stage times [K, 6] (ms), the per-kernel times of
@@ -282,7 +283,7 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
     stream = torch.cuda.current_stream()
 
     def params_of(k):
-        return p0.replace(frame=k % 65536, camera_moved=int(k > 0))
+        return p0.replace(frame=k % 65536, camera_moved=int(k > 0 and not static))
 
     def frame(k, ev=None):
         cam, prev, p = cams[k], cams[max(k - 1, 0)], params_of(k)
@@ -388,13 +389,16 @@ def kernel_roofline(name, kms, rays, z, lens, Hh, t, r_max, lane_peak, clock_mhz
     return None
 
 
-def quality(H, bvh, r, cam, lens, p, passes):
+def quality(H, bvh, r, cam, lens, p, passes, block=8):
     """The paper's Fig. 1 comparison on the renderer's last frame: a full
     ray-traced frame (every pixel, passes x spp_max lens samples, timed), the
     post-process-only frame (the composite with no traced pixels), and the
     error of the hybrid and post-process frames against the ray-traced one,
-    over all pixels and over the traced pixels (the blurry silhouettes)."""
+    over all pixels and over the traced pixels (the blurry silhouettes); also
+    on block x block means of the images, which separate a systematic error
+    from the Monte-Carlo noise of the few-sample hybrid frame."""
     import torch
+    import torch.nn.functional as F
     stream = torch.cuda.current_stream()
     zero = torch.zeros_like(r.spp)
     pp_only = torch.empty_like(r.out)
@@ -408,14 +412,45 @@ def quality(H, bvh, r, cam, lens, p, passes):
     rt_ms = e0.elapsed_time(e1)
     stats = torch.empty(H.ERR_SCRATCH, dtype=torch.float64, device=r.out.device)
     traced = (r.spp > 0).to(torch.uint8)
+
+    def pool(img):  # block means (analysis only), as a [H/b, W/b, 4] image
+        return F.avg_pool2d(img.permute(2, 0, 1)[None], block)[0].permute(1, 2, 0).contiguous()
+
+    tb = (F.avg_pool2d(traced[None, None].float(), block)[0, 0] > 0.5).to(torch.uint8).contiguous()
     res = {"reference": f"full ray trace, {passes * p.spp_max} lens samples per pixel",
            "reference_ms": round(rt_ms, 3), "traced_pixels": int(traced.sum())}
     for name, a, b in (("hybrid_vs_rt", r.out, rt), ("pp_vs_rt", pp_only, rt), ("hybrid_vs_pp", r.out, pp_only)):
         H.hdof_error_map(a, b, stats, region=traced)
         sm = H.error_summary(stats)
+        H.hdof_error_map(pool(a), pool(b), stats, region=tb)
+        smb = H.error_summary(stats)
         res[name] = {part: {k: (round(v, 6) if isinstance(v, float) else v) for k, v in sm[part].items()}
                      for part in ("all", "region")}
+        res[name][f"block{block}_region_mae"] = round(smb["region"]["mae"], 6)
     return res
+
+
+def quality_variants(H, bvh, W, Hh, lens, p0, dev, flush, frames, passes):
+    """Hybrid against full ray tracing after `frames` frames, in three
+    settings: the workload's (moving camera, fixed EMA weight), the moving
+    camera with per-pixel blend factors (alpha_k = 0.5), and a static camera
+    (fixed EMA); block-mean errors on the traced pixels, hybrid and
+    post-process."""
+    import torch
+    out = {}
+    for name, alpha_k, moving in (("moving_fixed_ema", 0.0, True), ("moving_per_pixel_alpha", 0.5, True),
+                                  ("static_fixed_ema", 0.0, False)):
+        p = p0.replace(alpha_k=alpha_k)
+        cams = [hi.room_camera(k if moving else 0, W, Hh) for k in range(frames + 1)]
+        r, _, _, _, _ = render_frames(H, bvh, W, Hh, cams, lens, p, dev, torch.float32, torch.float32, 0, frames,
+                                      flush, static=not moving)
+        last = frames - 1
+        q = quality(H, bvh, r, cams[last], lens, p.replace(frame=last, camera_moved=int(moving)), passes)
+        out[name] = {"hybrid_block8_mae": q["hybrid_vs_rt"]["block8_region_mae"],
+                     "pp_block8_mae": q["pp_vs_rt"]["block8_region_mae"],
+                     "hybrid_mae": q["hybrid_vs_rt"]["region"]["mae"], "pp_mae": q["pp_vs_rt"]["region"]["mae"]}
+        del r
+    return out
 
 
 def run_ours(args):
@@ -502,6 +537,8 @@ def run_ours(args):
                 "traffic": MEASURED_TRAFFIC.get((args.scene, storage, dom)), "kernel": dom, "peak_source": peak_src}
     last = args.warmup + 2 * K - 1
     qual = quality(H, bvh, r, cams[last], lens, p0.replace(frame=last % 65536, camera_moved=1), args.rt_passes)
+    if not args.no_compare and ws == 1:
+        qual["variants_after_8_frames"] = quality_variants(H, bvh, W, Hh, lens, p0, dev, flush, 8, args.rt_passes)
     e2e = None
     if not args.no_e2e:
         e_ms, h2d, d2h = e2e_frames(H, r, Hh, W, args.warmup, K, flush)

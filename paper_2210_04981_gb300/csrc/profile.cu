@@ -104,6 +104,13 @@ using namespace hdof;
 extern "C" int hdof_profile(int32_t on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on != 0;
+    // events for the next stretch of launches made up front, so that
+    // recording needs no event creation while the stream is being fed
+    while (on && g_pool.size() < 2048) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) break;
+        g_pool.push_back(e);
+    }
     return HDOF_OK;
 }
 
