@@ -4,11 +4,12 @@
 // detector); a luminance variance accumulated over previous frames adds rays
 // where the traced result is still noisy or has just appeared.
 //
-// k_mask_edge: one 16x16 pixel block per CUDA block; the block's (16+6)^2
-//   nd halo is staged in shared memory once, the separable 5-tap Gaussian
-//   runs as a row pass and a column pass in shared memory, then the 1/8
-//   scaled 3x3 Sobel; writes edge bits and marks the mask tiles that hold
-//   an edge.
+// k_mask_sweep: a warp walks down a strip of 32 columns (26 output columns
+//   plus the 3-pixel halos), one column per lane, keeping the separable 5-tap
+//   Gaussian and the 1/8-scaled 3x3 Sobel in registers (neighbour columns by
+//   warp shuffles, neighbour rows by register rings): no shared memory, each
+//   input pixel loaded once per strip.  Writes edge bits, marks the mask tiles
+//   that hold an edge and (CoC-scaled mask) their pixels' largest CoC radius.
 // k_mask_spp: per pixel, dilated tile flag and the variance term -> spp.
 #include <cmath>
 #include <mutex>
@@ -19,10 +20,6 @@
 namespace hdof {
 namespace {
 
-constexpr int B = 16;            // pixel block edge
-constexpr int HALO = 3;          // 2 (Gaussian) + 1 (Sobel)
-constexpr int SRC = B + 2 * HALO;  // 22
-constexpr int FIL = B + 2;         // 18: filtered values needed by the Sobel
 
 struct GaussW {
     float w[5];
@@ -42,113 +39,134 @@ struct EdgeArgs {
     float* tile_r;  // largest CoC radius per mask tile (atomic max of float bits); NULL: fixed dilation
 };
 
+// ---- register sweep form of the edge pass ----------------------------------
+// A warp owns a strip of 32 input columns (x0 - 3 .. x0 + 28) and SW_ROWS
+// output rows; it walks down the strip one input row at a time, lane = column:
+//   horizontal Gaussian of the new row from its +-1, +-2 neighbours (shuffles),
+//   vertical Gaussian from a ring of the last five horizontally filtered rows,
+//   per filtered row its horizontal Sobel difference f(x+1) - f(x-1) and
+//   smoothing f(x-1) + 2 f(x) + f(x+1) (+-1 shuffles, clamp-to-edge of the
+//   filtered image at the image border), and per output row the Sobel
+//   gradients from the last three of those.  Lanes 3..28 hold the 26 output
+//   columns.  Nothing goes through shared memory; each input pixel is loaded
+//   once per strip (plus the 3-pixel halos).  Edge flags and CoC radii are
+//   reduced per mask tile in registers and written once per tile row.
+constexpr int SW_OUT = 26;   // output columns per warp
+constexpr int SW_ROWS = 32;  // output rows per warp
+constexpr int SW_WARPS = 4;  // warps per block (side by side)
+
+__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+__device__ __forceinline__ float4 fma4(float w, float4 v, float4 a) {
+    return make_float4(fmaf(w, v.x, a.x), fmaf(w, v.y, a.y), fmaf(w, v.z, a.z), fmaf(w, v.w, a.w));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
+// flush a lane's per-tile edge flag and radius for tile row ty: lanes with the
+// same tile column combine, one lane per tile writes
 template <class ND>
-__device__ __forceinline__ void mask_edge_body(const EdgeArgs<ND>& ar, int bx, int by) {
-    __shared__ float4 src[SRC][SRC];
-    __shared__ float4 row[SRC][FIL];
-    __shared__ float4 fil[FIL][FIL];
-    const ND* __restrict__ nd = ar.nd;
-    const int W = ar.W, H = ar.H, tile = ar.tile, ntx = ar.ntx;
-    const GaussW g = ar.g;
-    const float tau = ar.tau;
-    uint8_t* __restrict__ edge = ar.edge;
-    uint8_t* __restrict__ tiles = ar.tiles;
-    const int x0 = bx * B, y0 = by * B;
-    const int tid = threadIdx.x;
-    // stage nd with clamp-to-edge (the Gaussian's border rule)
-    for (int k = tid; k < SRC * SRC; k += 256) {
-        int r = k / SRC, c = k % SRC;
-        int x = min(max(x0 - HALO + c, 0), W - 1), y = min(max(y0 - HALO + r, 0), H - 1);
-        src[r][c] = ld4(nd + (size_t)y * W + x);
+__device__ __forceinline__ void sw_flush(const EdgeArgs<ND>& ar, int ty, int tx, bool valid, bool& any_edge,
+                                         float& rmax) {
+    const unsigned grp = __match_any_sync(0xffffffffu, valid ? tx : -1);
+    const unsigned e = __ballot_sync(0xffffffffu, any_edge) & grp;
+    unsigned rb = __reduce_max_sync(grp, __float_as_uint(rmax));
+    const int lane = threadIdx.x & 31;
+    if (valid && lane == __ffs(grp) - 1) {
+        if (e) ar.tiles[ty * ar.ntx + tx] = 1;
+        if (ar.tile_r && rb) atomicMax(reinterpret_cast<unsigned*>(ar.tile_r) + ty * ar.ntx + tx, rb);
     }
-    __syncthreads();
-    if (ar.tile_r) {
-        // largest CoC radius min(|c(z)| / 2, r_max) of each mask tile's pixels:
-        // a shared-memory maximum per tile this block touches, then one global
-        // atomic maximum per tile (non-negative floats order as their bits)
-        __shared__ unsigned s_r[B][B];
-        const int tx0 = x0 / tile, ty0 = y0 / tile;
-        s_r[tid >> 4][tid & 15] = 0u;
-        __syncthreads();
-        const int i = x0 + (tid & 15), j = y0 + (tid >> 4);
-        if (i < W && j < H) {
-            const float r = fminf(fabsf(ar.coc(src[(tid >> 4) + HALO][(tid & 15) + HALO].w)) * 0.5f, ar.rmax);
-            atomicMax(&s_r[j / tile - ty0][i / tile - tx0], __float_as_uint(r));
-        }
-        __syncthreads();
-        const int nbx = min(x0 + B - 1, W - 1) / tile - tx0 + 1, nby = min(y0 + B - 1, H - 1) / tile - ty0 + 1;
-        if (tid < nbx * nby) {
-            const int a = tid % nbx, b = tid / nbx;
-            const unsigned v = s_r[b][a];
-            if (v) atomicMax(reinterpret_cast<unsigned*>(ar.tile_r) + (ty0 + b) * ntx + tx0 + a, v);
-        }
-    }
-    // row pass: filtered columns x0-1 .. x0+16 for all 22 staged rows
-    for (int k = tid; k < SRC * FIL; k += 256) {
-        int r = k / FIL, c = k % FIL;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-            float4 v = src[r][c + t];
-            a.x = fmaf(g.w[t], v.x, a.x);
-            a.y = fmaf(g.w[t], v.y, a.y);
-            a.z = fmaf(g.w[t], v.z, a.z);
-            a.w = fmaf(g.w[t], v.w, a.w);
-        }
-        row[r][c] = a;
-    }
-    __syncthreads();
-    // column pass: filtered rows y0-1 .. y0+16
-    for (int k = tid; k < FIL * FIL; k += 256) {
-        int r = k / FIL, c = k % FIL;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-            float4 v = row[r + t][c];
-            a.x = fmaf(g.w[t], v.x, a.x);
-            a.y = fmaf(g.w[t], v.y, a.y);
-            a.z = fmaf(g.w[t], v.z, a.z);
-            a.w = fmaf(g.w[t], v.w, a.w);
-        }
-        fil[r][c] = a;
-    }
-    __syncthreads();
-    const int lx = tid & 15, ly = tid >> 4;
-    const int i = x0 + lx, j = y0 + ly;
-    if (i >= W || j >= H) return;
-    // Sobel on the filtered image with clamp-to-edge (the Sobel's border rule):
-    // an out-of-image neighbour reads the filtered value of the border pixel.
-    // fil holds filtered rows y0-1 .. y0+16 and columns x0-1 .. x0+16.
-    const int cl = max(i - 1, 0) - (x0 - 1), cc = lx + 1, cr = min(i + 1, W - 1) - (x0 - 1);
-    const int ru = max(j - 1, 0) - (y0 - 1), rc = ly + 1, rd = min(j + 1, H - 1) - (y0 - 1);
-    const float4 f_ul = fil[ru][cl], f_uc = fil[ru][cc], f_ur = fil[ru][cr];
-    const float4 f_cl = fil[rc][cl], f_cr = fil[rc][cr];
-    const float4 f_dl = fil[rd][cl], f_dc = fil[rd][cc], f_dr = fil[rd][cr];
-    float gx[4], gy[4];
-    // gx: right column minus left column, rows weighted 1 2 1; gy: down row minus up row
-    gx[0] = (f_ur.x - f_ul.x) + 2.f * (f_cr.x - f_cl.x) + (f_dr.x - f_dl.x);
-    gx[1] = (f_ur.y - f_ul.y) + 2.f * (f_cr.y - f_cl.y) + (f_dr.y - f_dl.y);
-    gx[2] = (f_ur.z - f_ul.z) + 2.f * (f_cr.z - f_cl.z) + (f_dr.z - f_dl.z);
-    gx[3] = (f_ur.w - f_ul.w) + 2.f * (f_cr.w - f_cl.w) + (f_dr.w - f_dl.w);
-    gy[0] = (f_dl.x - f_ul.x) + 2.f * (f_dc.x - f_uc.x) + (f_dr.x - f_ur.x);
-    gy[1] = (f_dl.y - f_ul.y) + 2.f * (f_dc.y - f_uc.y) + (f_dr.y - f_ur.y);
-    gy[2] = (f_dl.z - f_ul.z) + 2.f * (f_dc.z - f_uc.z) + (f_dr.z - f_ur.z);
-    gy[3] = (f_dl.w - f_ul.w) + 2.f * (f_dc.w - f_uc.w) + (f_dr.w - f_ur.w);
-    for (int c = 0; c < 4; ++c) {
-        gx[c] *= 0.125f;
-        gy[c] *= 0.125f;
-    }
-    float en = sqrtf(gx[0] * gx[0] + gy[0] * gy[0] + gx[1] * gx[1] + gy[1] * gy[1] + gx[2] * gx[2] + gy[2] * gy[2]);
-    float ez = sqrtf(gx[3] * gx[3] + gy[3] * gy[3]) / fil[ly + 1][lx + 1].w;
-    float e = fmaxf(en, ez);
-    uint8_t bit = e > tau ? 1 : 0;
-    edge[(size_t)j * W + i] = bit;
-    if (bit) tiles[(j / tile) * ntx + i / tile] = 1;
+    any_edge = false;
+    rmax = 0.f;
 }
 
 template <class ND>
-__global__ void __launch_bounds__(256) k_mask_edge(EdgeArgs<ND> a) {
-    mask_edge_body(a, blockIdx.x, blockIdx.y);
+__device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, int by) {
+    const int W = ar.W, H = ar.H, tile = ar.tile;
+    const GaussW g = ar.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = (bx * SW_WARPS + warp) * SW_OUT;  // first output column of the strip
+    if (x0 >= W) return;                                // a whole warp leaves together
+    const int y0 = by * SW_ROWS, y1 = min(y0 + SW_ROWS, H);
+    const int x = x0 - 3 + lane;                      // this lane's column (may lie outside the image)
+    const int xc = min(max(x, 0), W - 1);
+    const bool out_lane = lane >= 3 && lane < 3 + SW_OUT && x < W;
+    const bool left_edge = x == 0, right_edge = x == W - 1;
+    const int tx = out_lane ? x / tile : -1;
+    float4 h0, h1, h2, h3, h4;                    // horizontally filtered rows yi-4 .. yi
+    float4 D0, D1, D2, S0, S1, S2;                // Sobel row terms of filtered rows fy-2 .. fy
+    float z1 = 1.f, z2 = 1.f;                     // filtered depth of rows fy-1, fy at this column
+    h0 = h1 = h2 = h3 = h4 = D0 = D1 = D2 = S0 = S1 = S2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool any_edge = false;
+    float rmax = 0.f;
+    int cur_ty = y0 / tile;
+    float4 vn = ld4(ar.nd + (size_t)min(max(y0 - 3, 0), H - 1) * W + xc);
+    for (int yi = y0 - 3; yi <= y1 + 2; ++yi) {
+        const float4 v = vn;
+        if (yi < y1 + 2) vn = ld4(ar.nd + (size_t)min(max(yi + 1, 0), H - 1) * W + xc);  // next row in flight
+        // horizontal Gaussian (lanes 2..29 are complete)
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+        h = fma4(g.w[0], shfl4(v, max(lane - 2, 0)), h);
+        h = fma4(g.w[1], shfl4(v, max(lane - 1, 0)), h);
+        h = fma4(g.w[2], v, h);
+        h = fma4(g.w[3], shfl4(v, min(lane + 1, 31)), h);
+        h = fma4(g.w[4], shfl4(v, min(lane + 2, 31)), h);
+        h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = h;
+        if (yi < y0 + 1) continue;  // the first filtered row the Sobel needs is y0 - 1 = yi - 2
+        // vertical Gaussian: filtered row fy = yi - 2
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        f = fma4(g.w[0], h0, f);
+        f = fma4(g.w[1], h1, f);
+        f = fma4(g.w[2], h2, f);
+        f = fma4(g.w[3], h3, f);
+        f = fma4(g.w[4], h4, f);
+        // Sobel row terms, clamp-to-edge of the filtered image at the image border
+        float4 fl = shfl4(f, max(lane - 1, 0)), fr = shfl4(f, min(lane + 1, 31));
+        if (left_edge) fl = f;
+        if (right_edge) fr = f;
+        D0 = D1; D1 = D2; D2 = sub4(fr, fl);
+        S0 = S1; S1 = S2; S2 = add4(add4(fl, fr), add4(f, f));
+        z1 = z2; z2 = f.w;
+        if (yi < y0 + 3) continue;  // output row j = yi - 3 needs filtered rows j-1 .. j+1
+        const int j = yi - 3;
+        // rows j - 1 and j + 1 clamped to the image (the Sobel's border rule)
+        const float4 Du = j == 0 ? D1 : D0, Dd = j == H - 1 ? D1 : D2;
+        const float4 Su = j == 0 ? S1 : S0, Sd = j == H - 1 ? S1 : S2;
+        if (j / tile != cur_ty) {
+            sw_flush(ar, cur_ty, tx, out_lane, any_edge, rmax);
+            cur_ty = j / tile;
+        }
+        const float4 gx4 = add4(add4(Du, Dd), add4(D1, D1));
+        const float4 gy4 = sub4(Sd, Su);
+        const float gx0 = gx4.x * 0.125f, gx1 = gx4.y * 0.125f, gx2 = gx4.z * 0.125f, gx3 = gx4.w * 0.125f;
+        const float gy0 = gy4.x * 0.125f, gy1 = gy4.y * 0.125f, gy2 = gy4.z * 0.125f, gy3 = gy4.w * 0.125f;
+        const float en = sqrtf(gx0 * gx0 + gy0 * gy0 + gx1 * gx1 + gy1 * gy1 + gx2 * gx2 + gy2 * gy2);
+        const float ez = sqrtf(gx3 * gx3 + gy3 * gy3) / z1;
+        const bool bit = fmaxf(en, ez) > ar.tau;
+        if (out_lane) {
+            ar.edge[(size_t)j * W + x] = bit ? 1 : 0;
+            any_edge |= bit;
+            if (ar.tile_r) rmax = fmaxf(rmax, fminf(fabsf(ar.coc(ldz(ar.nd + (size_t)j * W + x))) * 0.5f, ar.rmax));
+        }
+    }
+    sw_flush(ar, cur_ty, tx, out_lane, any_edge, rmax);
+}
+
+template <class ND>
+__global__ void __launch_bounds__(SW_WARPS * 32) k_mask_sweep(EdgeArgs<ND> a) {
+    mask_sweep_body(a, blockIdx.x, blockIdx.y);
+}
+__global__ void __launch_bounds__(SW_WARPS * 32) k_mask_sweep_batch(const EdgeArgs<float4>* __restrict__ a,
+                                                                     BatchGrid g) {
+    int v, bx, by;
+    g.locate(blockIdx.x, v, bx, by);
+    mask_sweep_body(batch_record(a, v), bx, by);
+}
+// grid of the sweep for a W x H frame
+inline dim3 sweep_grid(int W, int H) {
+    return dim3((W + SW_OUT * SW_WARPS - 1) / (SW_OUT * SW_WARPS), (H + SW_ROWS - 1) / SW_ROWS);
 }
 
 struct SppArgs {
@@ -299,12 +317,12 @@ SppArgs spp_args(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_
 int launch_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_params* p, uint8_t* edge, uint8_t* spp,
                 uint8_t* tiles, cudaStream_t s, const Coc* coc = nullptr, float* tile_r = nullptr) {
     const int W = in->width, H = in->height;
-    dim3 grid((W + B - 1) / B, (H + B - 1) / B);
+    const dim3 grid = sweep_grid(W, H);
     ProfScope ps_("mask", s);
     if (in->dtype_nd == HDOF_F32)
-        k_mask_edge<float4><<<grid, 256, 0, s>>>(edge_args<float4>(in, p, edge, tiles, coc, tile_r));
+        k_mask_sweep<float4><<<grid, SW_WARPS * 32, 0, s>>>(edge_args<float4>(in, p, edge, tiles, coc, tile_r));
     else
-        k_mask_edge<half4s><<<grid, 256, 0, s>>>(edge_args<half4s>(in, p, edge, tiles, coc, tile_r));
+        k_mask_sweep<half4s><<<grid, SW_WARPS * 32, 0, s>>>(edge_args<half4s>(in, p, edge, tiles, coc, tile_r));
     HDOF_LAUNCHED("mask: edge");
     dim3 g2((W + 31) / 32, (H + 7) / 8);
     k_mask_spp<<<g2, 256, 0, s>>>(spp_args(in, prev_hist, p, tiles, spp, coc ? tile_r : nullptr));
@@ -312,11 +330,6 @@ int launch_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_p
     return HDOF_OK;
 }
 
-__global__ void __launch_bounds__(256) k_mask_edge_batch(const EdgeArgs<float4>* __restrict__ a, BatchGrid g) {
-    int v, bx, by;
-    g.locate(blockIdx.x, v, bx, by);
-    mask_edge_body(batch_record(a, v), bx, by);
-}
 __global__ void __launch_bounds__(256) k_mask_spp_batch(const SppArgs* __restrict__ a, BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
@@ -450,12 +463,13 @@ void mask_edge_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, i
     const Coc coc = make_coc(v.lens, v.cam.height, v.cam.tan_half_fovy);
     *reinterpret_cast<EdgeArgs<float4>*>(dst) =
         edge_args<float4>(&v.g, &v.params, v.edge, w.tiles, v.params.mask_coc ? &coc : nullptr, w.tile_r);
-    *gx = (v.g.width + B - 1) / B;
-    *gy = (v.g.height + B - 1) / B;
+    const dim3 sg = sweep_grid(v.g.width, v.g.height);
+    *gx = (int)sg.x;
+    *gy = (int)sg.y;
 }
 void mask_edge_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
     ProfScope ps_("batch_mask_edge", s);
-    k_mask_edge_batch<<<blocks, 256, 0, s>>>(static_cast<const EdgeArgs<float4>*>(args), g);
+    k_mask_sweep_batch<<<blocks, SW_WARPS * 32, 0, s>>>(static_cast<const EdgeArgs<float4>*>(args), g);
 }
 
 size_t mask_spp_args_size() { return sizeof(SppArgs); }
