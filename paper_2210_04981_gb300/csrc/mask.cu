@@ -102,10 +102,15 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
     bool any_edge = false;
     float rmax = 0.f;
     int cur_ty = y0 / tile;
-    float4 vn = ld4(ar.nd + (size_t)min(max(y0 - 3, 0), H - 1) * W + xc);
+    // three rows in flight ahead of the one being filtered (loads of rows past
+    // the strip's end read clamped, valid rows and are not used)
+    auto row = [&](int y) { return ld4(ar.nd + (size_t)min(max(y, 0), H - 1) * W + xc); };
+    float4 va = row(y0 - 3), vb = row(y0 - 2), vc = row(y0 - 1);
     for (int yi = y0 - 3; yi <= y1 + 2; ++yi) {
-        const float4 v = vn;
-        if (yi < y1 + 2) vn = ld4(ar.nd + (size_t)min(max(yi + 1, 0), H - 1) * W + xc);  // next row in flight
+        const float4 v = va;
+        va = vb;
+        vb = vc;
+        vc = row(yi + 3);
         // horizontal Gaussian (lanes 2..29 are complete)
         float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
         h = fma4(g.w[0], shfl4(v, max(lane - 2, 0)), h);
@@ -183,77 +188,104 @@ struct SppArgs {
     const float* tile_r;  // CoC-scaled mask: largest CoC radius per tile; NULL: fixed dilation
 };
 
+// rays of pixel (i, j) that is not in a traced tile: the variance term
+__device__ __forceinline__ int variance_spp(const SppArgs& ar, int i, int j, float2 m) {
+    const int W = ar.W, H = ar.H;
+    float fx = floorf((float)i - m.x + 0.5f), fy = floorf((float)j - m.y + 0.5f);
+    int hl = 0;
+    float m1 = 0.f, m2 = 0.f;
+    if (fx >= 0.f && fy >= 0.f && fx < (float)W && fy < (float)H) {
+        size_t t = (size_t)fy * W + (size_t)fx;
+        hl = __ldg(&ar.hhlen[t]);
+        float2 mm = __ldg(&ar.hmom[t]);
+        m1 = mm.x;
+        m2 = mm.y;
+    }
+    float sig = sqrtf(fmaxf(0.f, m2 - m1 * m1));
+    bool young = hl < ar.hlen_young;
+    int s = 0;
+    if (hl >= 1 && (young || sig > ar.var_tau)) {
+        if (young) s = ar.spp_max;
+        else s = (int)fminf(fmaxf(ceilf((float)ar.spp_max * sig / ar.var_scale), 1.f), (float)ar.spp_max);
+    }
+    return s;
+}
+
+// block = 128 x 8 pixels, 4 consecutive pixels per thread (vector loads of
+// the motion vectors, one 4-byte store of the rays; the history reads of
+// the variance term are independent, so four are in flight per thread)
+constexpr int SPP_BX = 128, SPP_BY = 8;
 __device__ __forceinline__ void mask_spp_body(const SppArgs& ar, int bx, int by) {
     const int W = ar.W, H = ar.H, tile = ar.tile, ntx = ar.ntx, nty = ar.nty, dil = ar.dil;
     const uint8_t* __restrict__ tiles = ar.tiles;
-    const int variance_on = ar.variance_on, spp_max = ar.spp_max, hlen_young = ar.hlen_young;
-    const float2* __restrict__ mv = ar.mv;
-    const float2* __restrict__ hmom = ar.hmom;
-    const uint8_t* __restrict__ hhlen = ar.hhlen;
-    const float var_tau = ar.var_tau, var_scale = ar.var_scale;
-    uint8_t* __restrict__ spp = ar.spp;
-    // the dilated flag of every mask tile this 32x8 block touches, once, in
-    // shared memory (at most 32 x 8 tiles, for tile = 1)
-    __shared__ unsigned char s_on[8][32];
-    const int x0 = bx * 32, y0 = by * 8;
+    // the dilated flag of every mask tile this block touches, once, in shared
+    // memory (at most 128 x 8 tiles, for tile = 1)
+    __shared__ unsigned char s_on[SPP_BY][SPP_BX];
+    const int x0 = bx * SPP_BX, y0 = by * SPP_BY;
     const int tx0 = x0 / tile, ty0 = y0 / tile;
-    const int ntx_b = min(x0 + 31, W - 1) / tile - tx0 + 1, nty_b = min(y0 + 7, H - 1) / tile - ty0 + 1;
-    {
-        const int e = threadIdx.x, ey = e >> 5, ex = e & 31;
-        if (ey < nty_b && ex < ntx_b) {
-            const int tx = tx0 + ex, ty = ty0 + ey;
-            bool any = false;
-            if (!ar.tile_r) {
-                for (int b = max(ty - dil, 0); b <= min(ty + dil, nty - 1) && !any; ++b)
-                    for (int a = max(tx - dil, 0); a <= min(tx + dil, ntx - 1); ++a)
-                        if (__ldg(&tiles[b * ntx + a])) {
-                            any = true;
-                            break;
-                        }
-            } else {
-                // an edge tile reaches max(dil, ceil(r / tile)) tiles (at most 8),
-                // r its pixels' largest CoC radius
-                const float inv_tile = 1.f / (float)tile;
-                for (int b = max(ty - 8, 0); b <= min(ty + 8, nty - 1) && !any; ++b)
-                    for (int a = max(tx - 8, 0); a <= min(tx + 8, ntx - 1); ++a) {
-                        if (!__ldg(&tiles[b * ntx + a])) continue;
-                        const int reach =
-                            min(8, max(dil, (int)ceilf(__ldg(&ar.tile_r[b * ntx + a]) * inv_tile)));
-                        if (max(abs(a - tx), abs(b - ty)) <= reach) {
-                            any = true;
-                            break;
-                        }
+    const int ntx_b = min(x0 + SPP_BX - 1, W - 1) / tile - tx0 + 1, nty_b = min(y0 + SPP_BY - 1, H - 1) / tile - ty0 + 1;
+    for (int e = threadIdx.x; e < ntx_b * nty_b; e += 256) {
+        const int ey = e / ntx_b, ex = e % ntx_b;
+        const int tx = tx0 + ex, ty = ty0 + ey;
+        bool any = false;
+        if (!ar.tile_r) {
+            for (int b = max(ty - dil, 0); b <= min(ty + dil, nty - 1) && !any; ++b)
+                for (int a = max(tx - dil, 0); a <= min(tx + dil, ntx - 1); ++a)
+                    if (__ldg(&tiles[b * ntx + a])) {
+                        any = true;
+                        break;
                     }
-            }
-            s_on[ey][ex] = any ? 1 : 0;
+        } else {
+            // an edge tile reaches max(dil, ceil(r / tile)) tiles (at most 8),
+            // r its pixels' largest CoC radius
+            const float inv_tile = 1.f / (float)tile;
+            for (int b = max(ty - 8, 0); b <= min(ty + 8, nty - 1) && !any; ++b)
+                for (int a = max(tx - 8, 0); a <= min(tx + 8, ntx - 1); ++a) {
+                    if (!__ldg(&tiles[b * ntx + a])) continue;
+                    const int reach = min(8, max(dil, (int)ceilf(__ldg(&ar.tile_r[b * ntx + a]) * inv_tile)));
+                    if (max(abs(a - tx), abs(b - ty)) <= reach) {
+                        any = true;
+                        break;
+                    }
+                }
         }
+        s_on[ey][ex] = any ? 1 : 0;
     }
     __syncthreads();
-    int i = x0 + (threadIdx.x & 31), j = y0 + (threadIdx.x >> 5);
-    if (i >= W || j >= H) return;
-    size_t q = (size_t)j * W + i;
-    const bool on = s_on[j / tile - ty0][i / tile - tx0] != 0;
-    int s = on ? spp_max : 0;
-    if (!on && variance_on) {
-        float2 m = __ldg(&mv[q]);
-        float fx = floorf((float)i - m.x + 0.5f), fy = floorf((float)j - m.y + 0.5f);
-        int hl = 0;
-        float m1 = 0.f, m2 = 0.f;
-        if (fx >= 0.f && fy >= 0.f && fx < (float)W && fy < (float)H) {
-            size_t t = (size_t)fy * W + (size_t)fx;
-            hl = __ldg(&hhlen[t]);
-            float2 mm = __ldg(&hmom[t]);
-            m1 = mm.x;
-            m2 = mm.y;
-        }
-        float sig = sqrtf(fmaxf(0.f, m2 - m1 * m1));
-        bool young = hl < hlen_young;
-        if (hl >= 1 && (young || sig > var_tau)) {
-            if (young) s = spp_max;
-            else s = (int)fminf(fmaxf(ceilf((float)spp_max * sig / var_scale), 1.f), (float)spp_max);
+    const int i0 = x0 + 4 * (threadIdx.x & 31), j = y0 + (threadIdx.x >> 5);
+    if (i0 >= W || j >= H) return;
+    const size_t q = (size_t)j * W + i0;
+    const bool full = i0 + 3 < W && (q & 3) == 0;  // four pixels, 4-byte aligned row position
+    float2 m[4];
+    if (ar.variance_on) {
+        if (full && (q & 1) == 0) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(ar.mv + q));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(ar.mv + q + 2));
+            m[0] = make_float2(a.x, a.y);
+            m[1] = make_float2(a.z, a.w);
+            m[2] = make_float2(b.x, b.y);
+            m[3] = make_float2(b.z, b.w);
+        } else {
+            for (int k = 0; k < 4; ++k) m[k] = i0 + k < W ? __ldg(&ar.mv[q + k]) : make_float2(0.f, 0.f);
         }
     }
-    spp[q] = (uint8_t)s;
+    uint8_t out[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = i0 + k;
+        int sp = 0;
+        if (i < W) {
+            const bool on = s_on[j / tile - ty0][i / tile - tx0] != 0;
+            sp = on ? ar.spp_max : (ar.variance_on ? variance_spp(ar, i, j, m[k]) : 0);
+        }
+        out[k] = (uint8_t)sp;
+    }
+    if (full) {
+        *reinterpret_cast<uchar4*>(ar.spp + q) = make_uchar4(out[0], out[1], out[2], out[3]);
+    } else {
+        for (int k = 0; k < 4; ++k)
+            if (i0 + k < W) ar.spp[q + k] = out[k];
+    }
 }
 
 __global__ void __launch_bounds__(256) k_mask_spp(SppArgs a) { mask_spp_body(a, blockIdx.x, blockIdx.y); }
@@ -324,7 +356,7 @@ int launch_mask(const hdof_gbuf* in, const hdof_history* prev_hist, const hdof_p
     else
         k_mask_sweep<half4s><<<grid, SW_WARPS * 32, 0, s>>>(edge_args<half4s>(in, p, edge, tiles, coc, tile_r));
     HDOF_LAUNCHED("mask: edge");
-    dim3 g2((W + 31) / 32, (H + 7) / 8);
+    dim3 g2((W + SPP_BX - 1) / SPP_BX, (H + SPP_BY - 1) / SPP_BY);
     k_mask_spp<<<g2, 256, 0, s>>>(spp_args(in, prev_hist, p, tiles, spp, coc ? tile_r : nullptr));
     HDOF_LAUNCHED("mask: spp");
     return HDOF_OK;
@@ -476,8 +508,8 @@ size_t mask_spp_args_size() { return sizeof(SppArgs); }
 void mask_spp_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {
     *reinterpret_cast<SppArgs*>(dst) =
         spp_args(&v.g, &v.hist_in, &v.params, w.tiles, v.spp, v.params.mask_coc ? w.tile_r : nullptr);
-    *gx = (v.g.width + 31) / 32;
-    *gy = (v.g.height + 7) / 8;
+    *gx = (v.g.width + SPP_BX - 1) / SPP_BX;
+    *gy = (v.g.height + SPP_BY - 1) / SPP_BY;
 }
 void mask_spp_launch_batch(const void* args, BatchGrid g, int blocks, cudaStream_t s) {
     ProfScope ps_("batch_mask_spp", s);
