@@ -55,10 +55,6 @@ constexpr int SW_OUT = 26;   // output columns per warp
 constexpr int SW_ROWS = 32;  // output rows per warp
 constexpr int SW_WARPS = 4;  // warps per block (side by side)
 
-__device__ __forceinline__ float4 shfl4(float4 v, int src) {
-    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
-}
 __device__ __forceinline__ float4 fma4(float w, float4 v, float4 a) {
     return make_float4(fmaf(w, v.x, a.x), fmaf(w, v.y, a.y), fmaf(w, v.z, a.z), fmaf(w, v.w, a.w));
 }
@@ -93,7 +89,14 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
     const int x = x0 - 3 + lane;                      // this lane's column (may lie outside the image)
     const int xc = min(max(x, 0), W - 1);
     const bool out_lane = lane >= 3 && lane < 3 + SW_OUT && x < W;
-    const bool left_edge = x == 0, right_edge = x == W - 1;
+    // neighbour columns through the warp's own shared row (one 128-bit store,
+    // 128-bit loads): Gaussian taps at lane -2..+2 (clamped to the warp; only
+    // lanes 2..29 need complete sums), Sobel taps at lane -1, +1 with the
+    // filtered image's clamp-to-edge at the image border
+    __shared__ float4 s_row[SW_WARPS][32];
+    float4* srow = s_row[warp];
+    const int lm2 = max(lane - 2, 0), lm1 = max(lane - 1, 0), lp1 = min(lane + 1, 31), lp2 = min(lane + 2, 31);
+    const int sl = x == 0 ? lane : lm1, sr = x == W - 1 ? lane : lp1;
     const int tx = out_lane ? x / tile : -1;
     float4 h0, h1, h2, h3, h4;                    // horizontally filtered rows yi-4 .. yi
     float4 D0, D1, D2, S0, S1, S2;                // Sobel row terms of filtered rows fy-2 .. fy
@@ -112,12 +115,15 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
         vb = vc;
         vc = row(yi + 3);
         // horizontal Gaussian (lanes 2..29 are complete)
+        __syncwarp();
+        srow[lane] = v;
+        __syncwarp();
         float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
-        h = fma4(g.w[0], shfl4(v, max(lane - 2, 0)), h);
-        h = fma4(g.w[1], shfl4(v, max(lane - 1, 0)), h);
+        h = fma4(g.w[0], srow[lm2], h);
+        h = fma4(g.w[1], srow[lm1], h);
         h = fma4(g.w[2], v, h);
-        h = fma4(g.w[3], shfl4(v, min(lane + 1, 31)), h);
-        h = fma4(g.w[4], shfl4(v, min(lane + 2, 31)), h);
+        h = fma4(g.w[3], srow[lp1], h);
+        h = fma4(g.w[4], srow[lp2], h);
         h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = h;
         if (yi < y0 + 1) continue;  // the first filtered row the Sobel needs is y0 - 1 = yi - 2
         // vertical Gaussian: filtered row fy = yi - 2
@@ -128,9 +134,10 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
         f = fma4(g.w[3], h3, f);
         f = fma4(g.w[4], h4, f);
         // Sobel row terms, clamp-to-edge of the filtered image at the image border
-        float4 fl = shfl4(f, max(lane - 1, 0)), fr = shfl4(f, min(lane + 1, 31));
-        if (left_edge) fl = f;
-        if (right_edge) fr = f;
+        __syncwarp();
+        srow[lane] = f;
+        __syncwarp();
+        const float4 fl = srow[sl], fr = srow[sr];
         D0 = D1; D1 = D2; D2 = sub4(fr, fl);
         S0 = S1; S1 = S2; S2 = add4(add4(fl, fr), add4(f, f));
         z1 = z2; z2 = f.w;
@@ -160,10 +167,10 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
 }
 
 template <class ND>
-__global__ void __launch_bounds__(SW_WARPS * 32) k_mask_sweep(EdgeArgs<ND> a) {
+__global__ void __launch_bounds__(SW_WARPS * 32, 6) k_mask_sweep(EdgeArgs<ND> a) {
     mask_sweep_body(a, blockIdx.x, blockIdx.y);
 }
-__global__ void __launch_bounds__(SW_WARPS * 32) k_mask_sweep_batch(const EdgeArgs<float4>* __restrict__ a,
+__global__ void __launch_bounds__(SW_WARPS * 32, 6) k_mask_sweep_batch(const EdgeArgs<float4>* __restrict__ a,
                                                                      BatchGrid g) {
     int v, bx, by;
     g.locate(blockIdx.x, v, bx, by);
@@ -224,6 +231,26 @@ __device__ __forceinline__ void mask_spp_body(const SppArgs& ar, int bx, int by)
     const int x0 = bx * SPP_BX, y0 = by * SPP_BY;
     const int tx0 = x0 / tile, ty0 = y0 / tile;
     const int ntx_b = min(x0 + SPP_BX - 1, W - 1) / tile - tx0 + 1, nty_b = min(y0 + SPP_BY - 1, H - 1) / tile - ty0 + 1;
+    // this thread's pixels and their motion vectors first: the loads are in
+    // flight while the block builds its tile flags
+    const int i0 = x0 + 4 * (threadIdx.x & 31), j = y0 + (threadIdx.x >> 5);
+    const bool live = i0 < W && j < H;
+    const size_t q = live ? (size_t)j * W + i0 : 0;
+    const bool full = live && i0 + 3 < W && (q & 3) == 0;  // four pixels, 4-byte aligned row position
+    float2 m[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (live && ar.variance_on) {
+        if (full) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(ar.mv + q));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(ar.mv + q + 2));
+            m[0] = make_float2(a.x, a.y);
+            m[1] = make_float2(a.z, a.w);
+            m[2] = make_float2(b.x, b.y);
+            m[3] = make_float2(b.z, b.w);
+        } else {
+            for (int k = 0; k < 4; ++k)
+                if (i0 + k < W) m[k] = __ldg(&ar.mv[q + k]);
+        }
+    }
     for (int e = threadIdx.x; e < ntx_b * nty_b; e += 256) {
         const int ey = e / ntx_b, ex = e % ntx_b;
         const int tx = tx0 + ex, ty = ty0 + ey;
@@ -252,23 +279,7 @@ __device__ __forceinline__ void mask_spp_body(const SppArgs& ar, int bx, int by)
         s_on[ey][ex] = any ? 1 : 0;
     }
     __syncthreads();
-    const int i0 = x0 + 4 * (threadIdx.x & 31), j = y0 + (threadIdx.x >> 5);
     if (i0 >= W || j >= H) return;
-    const size_t q = (size_t)j * W + i0;
-    const bool full = i0 + 3 < W && (q & 3) == 0;  // four pixels, 4-byte aligned row position
-    float2 m[4];
-    if (ar.variance_on) {
-        if (full && (q & 1) == 0) {
-            const float4 a = __ldg(reinterpret_cast<const float4*>(ar.mv + q));
-            const float4 b = __ldg(reinterpret_cast<const float4*>(ar.mv + q + 2));
-            m[0] = make_float2(a.x, a.y);
-            m[1] = make_float2(a.z, a.w);
-            m[2] = make_float2(b.x, b.y);
-            m[3] = make_float2(b.z, b.w);
-        } else {
-            for (int k = 0; k < 4; ++k) m[k] = i0 + k < W ? __ldg(&ar.mv[q + k]) : make_float2(0.f, 0.f);
-        }
-    }
     uint8_t out[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
