@@ -98,6 +98,7 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
     const int lm2 = max(lane - 2, 0), lm1 = max(lane - 1, 0), lp1 = min(lane + 1, 31), lp2 = min(lane + 2, 31);
     const int sl = x == 0 ? lane : lm1, sr = x == W - 1 ? lane : lp1;
     const int tx = out_lane ? x / tile : -1;
+    const float tau64 = 64.f * ar.tau * ar.tau;
     float4 h0, h1, h2, h3, h4;                    // horizontally filtered rows yi-4 .. yi
     float4 D0, D1, D2, S0, S1, S2;                // Sobel row terms of filtered rows fy-2 .. fy
     float z1 = 1.f, z2 = 1.f;                     // filtered depth of rows fy-1, fy at this column
@@ -150,13 +151,15 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
             sw_flush(ar, cur_ty, tx, out_lane, any_edge, rmax);
             cur_ty = j / tile;
         }
-        const float4 gx4 = add4(add4(Du, Dd), add4(D1, D1));
-        const float4 gy4 = sub4(Sd, Su);
-        const float gx0 = gx4.x * 0.125f, gx1 = gx4.y * 0.125f, gx2 = gx4.z * 0.125f, gx3 = gx4.w * 0.125f;
-        const float gy0 = gy4.x * 0.125f, gy1 = gy4.y * 0.125f, gy2 = gy4.z * 0.125f, gy3 = gy4.w * 0.125f;
-        const float en = sqrtf(gx0 * gx0 + gy0 * gy0 + gx1 * gx1 + gy1 * gy1 + gx2 * gx2 + gy2 * gy2);
-        const float ez = sqrtf(gx3 * gx3 + gy3 * gy3) / z1;
-        const bool bit = fmaxf(en, ez) > ar.tau;
+        // e = max(|grad n|, |grad z| / z~) > tau with the Sobel's 1/8 scale folded
+        // into the threshold and both sides squared (no square root, no divide):
+        // |8 grad n|^2 > 64 tau^2  or  |8 grad z|^2 > 64 tau^2 z~^2
+        const float4 gx = add4(add4(Du, Dd), add4(D1, D1));
+        const float4 gy = sub4(Sd, Su);
+        const float en2 = fmaf(gx.x, gx.x, fmaf(gy.x, gy.x, fmaf(gx.y, gx.y, fmaf(gy.y, gy.y,
+                          fmaf(gx.z, gx.z, gy.z * gy.z)))));
+        const float ez2 = fmaf(gx.w, gx.w, gy.w * gy.w);
+        const bool bit = en2 > tau64 || ez2 > tau64 * z1 * z1;
         if (out_lane) {
             ar.edge[(size_t)j * W + x] = bit ? 1 : 0;
             any_edge |= bit;
