@@ -55,11 +55,43 @@ constexpr int SW_OUT = 26;   // output columns per warp
 constexpr int SW_ROWS = 32;  // output rows per warp
 constexpr int SW_WARPS = 4;  // warps per block (side by side)
 
-__device__ __forceinline__ float4 fma4(float w, float4 v, float4 a) {
-    return make_float4(fmaf(w, v.x, a.x), fmaf(w, v.y, a.y), fmaf(w, v.z, a.z), fmaf(w, v.w, a.w));
+// float4 arithmetic as two packed two-lane FP32 operations (Blackwell's
+// f32x2 forms: one instruction for two lanes, each rounded as its scalar form)
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pc, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%6, %7};\n\tfma.rn.f32x2 pr, pa, pb, pc;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
 }
-__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
-__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 pk_sub(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+struct V4 {
+    float2 a, b;  // (x, y), (z, w)
+};
+__device__ __forceinline__ V4 v4(float4 v) { return V4{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ V4 fma4(float w, V4 v, V4 c) {
+    const float2 ww = make_float2(w, w);
+    return V4{pk_fma(ww, v.a, c.a), pk_fma(ww, v.b, c.b)};
+}
+__device__ __forceinline__ V4 mul4(float w, V4 v) { return fma4(w, v, V4{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}); }
+__device__ __forceinline__ V4 add4(V4 x, V4 y) { return V4{pk_add(x.a, y.a), pk_add(x.b, y.b)}; }
+__device__ __forceinline__ V4 sub4(V4 x, V4 y) { return V4{pk_sub(x.a, y.a), pk_sub(x.b, y.b)}; }
 
 // flush a lane's per-tile edge flag and radius for tile row ty: lanes with the
 // same tile column combine, one lane per tile writes
@@ -99,13 +131,18 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
     const int sl = x == 0 ? lane : lm1, sr = x == W - 1 ? lane : lp1;
     const int tx = out_lane ? x / tile : -1;
     const float tau64 = 64.f * ar.tau * ar.tau;
-    float4 h0, h1, h2, h3, h4;                    // horizontally filtered rows yi-4 .. yi
-    float4 D0, D1, D2, S0, S1, S2;                // Sobel row terms of filtered rows fy-2 .. fy
-    float z1 = 1.f, z2 = 1.f;                     // filtered depth of rows fy-1, fy at this column
-    h0 = h1 = h2 = h3 = h4 = D0 = D1 = D2 = S0 = S1 = S2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const V4 zero4{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    // vertical Gaussian as running sums: A0..A3 hold the partial sums of the
+    // filtered rows yi-2 .. yi+1 (their taps from the rows read so far)
+    V4 A0 = zero4, A1 = zero4, A2 = zero4, A3 = zero4;
+    // Sobel as running sums over the filtered rows: P = D(j-1) + 2 D(j),
+    // Q = D(j), Sm = S(j-1), S0 = S(j) (D: horizontal difference, S: horizontal
+    // smoothing of a filtered row)
+    V4 P = zero4, Q = zero4, Sm = zero4, S0 = zero4;
+    float zj = 1.f;  // filtered depth of row j at this column
     bool any_edge = false;
     float rmax = 0.f;
-    int cur_ty = y0 / tile;
+    int cur_ty = y0 / tile, next_row = (cur_ty + 1) * tile;
     // three rows in flight ahead of the one being filtered (loads of rows past
     // the strip's end read clamped, valid rows and are not used)
     auto row = [&](int y) { return ld4(ar.nd + (size_t)min(max(y, 0), H - 1) * W + xc); };
@@ -115,51 +152,72 @@ __device__ __forceinline__ void mask_sweep_body(const EdgeArgs<ND>& ar, int bx, 
         va = vb;
         vb = vc;
         vc = row(yi + 3);
-        // horizontal Gaussian (lanes 2..29 are complete)
+        // horizontal Gaussian of input row yi (lanes 2..29 complete)
         __syncwarp();
         srow[lane] = v;
         __syncwarp();
-        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
-        h = fma4(g.w[0], srow[lm2], h);
-        h = fma4(g.w[1], srow[lm1], h);
-        h = fma4(g.w[2], v, h);
-        h = fma4(g.w[3], srow[lp1], h);
-        h = fma4(g.w[4], srow[lp2], h);
-        h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = h;
+        V4 h = mul4(g.w[0], v4(srow[lm2]));
+        h = fma4(g.w[1], v4(srow[lm1]), h);
+        h = fma4(g.w[2], v4(v), h);
+        h = fma4(g.w[3], v4(srow[lp1]), h);
+        h = fma4(g.w[4], v4(srow[lp2]), h);
+        // its taps into the running vertical sums; filtered row yi - 2 completes
+        const V4 f = fma4(g.w[4], h, A0);
+        A0 = fma4(g.w[3], h, A1);
+        A1 = fma4(g.w[2], h, A2);
+        A2 = fma4(g.w[1], h, A3);
+        A3 = mul4(g.w[0], h);
         if (yi < y0 + 1) continue;  // the first filtered row the Sobel needs is y0 - 1 = yi - 2
-        // vertical Gaussian: filtered row fy = yi - 2
-        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-        f = fma4(g.w[0], h0, f);
-        f = fma4(g.w[1], h1, f);
-        f = fma4(g.w[2], h2, f);
-        f = fma4(g.w[3], h3, f);
-        f = fma4(g.w[4], h4, f);
-        // Sobel row terms, clamp-to-edge of the filtered image at the image border
+        // Sobel row terms of filtered row fy = yi - 2
         __syncwarp();
-        srow[lane] = f;
+        srow[lane] = make_float4(f.a.x, f.a.y, f.b.x, f.b.y);
         __syncwarp();
-        const float4 fl = srow[sl], fr = srow[sr];
-        D0 = D1; D1 = D2; D2 = sub4(fr, fl);
-        S0 = S1; S1 = S2; S2 = add4(add4(fl, fr), add4(f, f));
-        z1 = z2; z2 = f.w;
-        if (yi < y0 + 3) continue;  // output row j = yi - 3 needs filtered rows j-1 .. j+1
-        const int j = yi - 3;
+        const V4 fl = v4(srow[sl]), fr = v4(srow[sr]);
+        const V4 Dn = sub4(fr, fl);
+        const V4 Sn = fma4(2.f, f, add4(fl, fr));
+        if (yi < y0 + 3) {  // filtered rows y0 - 1 and y0: prime the running sums
+            P = fma4(2.f, Dn, Q);
+            Q = Dn;
+            Sm = S0;
+            S0 = Sn;
+            zj = f.b.y;
+            continue;
+        }
+        // output row j = yi - 3 from filtered rows j - 1 (in P, Sm), j (Q, S0) and j + 1 (new);
         // rows j - 1 and j + 1 clamped to the image (the Sobel's border rule)
-        const float4 Du = j == 0 ? D1 : D0, Dd = j == H - 1 ? D1 : D2;
-        const float4 Su = j == 0 ? S1 : S0, Sd = j == H - 1 ? S1 : S2;
-        if (j / tile != cur_ty) {
+        const int j = yi - 3;
+        V4 gx, gy;
+        if (j == 0 && j == H - 1) {  // a one-row image: both neighbours are the row itself
+            gx = mul4(4.f, Q);
+            gy = zero4;
+        } else if (j == 0) {
+            gx = add4(fma4(2.f, Q, Q), Dn);
+            gy = sub4(Sn, S0);
+        } else if (j == H - 1) {
+            gx = add4(P, Q);
+            gy = sub4(S0, Sm);
+        } else {
+            gx = add4(P, Dn);
+            gy = sub4(Sn, Sm);
+        }
+        const float zc = zj;
+        P = fma4(2.f, Dn, Q);
+        Q = Dn;
+        Sm = S0;
+        S0 = Sn;
+        zj = f.b.y;
+        if (j >= next_row) {
             sw_flush(ar, cur_ty, tx, out_lane, any_edge, rmax);
             cur_ty = j / tile;
+            next_row = (cur_ty + 1) * tile;
         }
         // e = max(|grad n|, |grad z| / z~) > tau with the Sobel's 1/8 scale folded
         // into the threshold and both sides squared (no square root, no divide):
         // |8 grad n|^2 > 64 tau^2  or  |8 grad z|^2 > 64 tau^2 z~^2
-        const float4 gx = add4(add4(Du, Dd), add4(D1, D1));
-        const float4 gy = sub4(Sd, Su);
-        const float en2 = fmaf(gx.x, gx.x, fmaf(gy.x, gy.x, fmaf(gx.y, gx.y, fmaf(gy.y, gy.y,
-                          fmaf(gx.z, gx.z, gy.z * gy.z)))));
-        const float ez2 = fmaf(gx.w, gx.w, gy.w * gy.w);
-        const bool bit = en2 > tau64 || ez2 > tau64 * z1 * z1;
+        const float en2 = fmaf(gx.a.x, gx.a.x, fmaf(gy.a.x, gy.a.x, fmaf(gx.a.y, gx.a.y, fmaf(gy.a.y, gy.a.y,
+                          fmaf(gx.b.x, gx.b.x, gy.b.x * gy.b.x)))));
+        const float ez2 = fmaf(gx.b.y, gx.b.y, gy.b.y * gy.b.y);
+        const bool bit = en2 > tau64 || ez2 > tau64 * zc * zc;
         if (out_lane) {
             ar.edge[(size_t)j * W + x] = bit ? 1 : 0;
             any_edge |= bit;

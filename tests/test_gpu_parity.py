@@ -196,6 +196,21 @@ def test_mask_tile_and_dilation_shapes(orc, tile, dilate, W, Hh):
     assert edge.sum() > 0 and (spp > 0).sum() > 0
 
 
+@pytest.mark.parametrize("tile,dilate,W,Hh", [(1, 0, 1, 1), (4, 1, 7, 1), (4, 1, 1, 9), (2, 1, 3, 2), (16, 1, 33, 1),
+                                              (16, 1, 1, 40), (3, 2, 27, 5)])
+def test_mask_degenerate_shapes(orc, tile, dilate, W, Hh):
+    """Single pixels, single rows and columns and other slivers: the edge
+    pass's clamp-to-edge at every border (the Gaussian on the input, the
+    Sobel on the filtered image) against the oracle."""
+    gb = hi.random_gbuffer(W, Hh, seed=W * 31 + Hh)
+    p = hi.Params(spp_max=8, tile=tile, dilate=dilate)
+    edge, spp = _mask(gbuf_from(gb["nd"], gb["col"], gb["mv"]), None, p)
+    ref = orc.mask(gb["nd"].astype(np.float64), gb["mv"].astype(np.float64), p)
+    tie, tie_px = tie_tiles(ref["emetric"], p.edge_tau, p.tile, p.dilate)
+    assert np.array_equal(edge[~tie], ref["edge"][~tie])
+    assert np.array_equal(spp[~tie_px], ref["spp"][~tie_px])
+
+
 def _reach_ties(nd, lens, t, p, edge_ties):
     """Pixels whose spp may differ in the CoC-scaled mask: within reach + 1
     tiles of a tile whose largest CoC radius lies within 1e-4 tile of a
