@@ -102,6 +102,7 @@ class Params:
     blades: int = 0           # aperture polygon blades (0 = circle)
     blade_rot: float = 0.0    # polygon rotation (radians)
     aberration: float = 0.0   # radial weight of the lens samples, 1 + a (2 rho^2 / A^2 - 1)
+    spec_pref: float = 0.0    # composite: post-process share per unit of its specular intensity
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
@@ -120,9 +121,10 @@ class Scene:
     """Triangle soup with per-triangle material.
 
     verts f32 [V,3]; idx i32 [T,3]; mat f32 [T,8] = (albedo_a rgb, checker_n,
-    albedo_b rgb, 0) -- checker_n > 0 selects a checkerboard of n x n cells in
+    albedo_b rgb, k_s) -- checker_n > 0 selects a checkerboard of n x n cells in
     the triangle's (u,v) parameterisation, cells with even floor(n u)+floor(n v)
-    taking albedo_a; uv f32 [T,6] = (u0,v0,u1,v1,u2,v2)."""
+    taking albedo_a; k_s > 0 adds a white Blinn-Phong highlight of that
+    strength (0: Lambertian); uv f32 [T,6] = (u0,v0,u1,v1,u2,v2)."""
     verts: np.ndarray
     idx: np.ndarray
     mat: np.ndarray
@@ -217,6 +219,31 @@ def tiny_scene() -> Scene:
     return b.scene()
 
 
+def specular_scene(ks: float = 4.0) -> Scene:
+    """Glossy variant of the tiny scene: the checker background quad at z=2 and
+    three flat-faceted icospheres (subdivision 3, radius 0.07) at view depths
+    0.5 to 0.7, grey albedo 0.3 with Blinn-Phong strength ks: their highlights
+    are bright specular bokeh in the near field of a lens focused at 2."""
+    b = _Builder()
+    b.quad((-2, -2, 2), (2, -2, 2), (2, 2, 2), (-2, 2, 2),
+           (0.2, 0.2, 0.2, 8.0, 0.8, 0.8, 0.8, 0.0))
+    sphere = icosphere(3)
+    for c in ((-0.1, 0.08, 0.57), (0.12, 0.1, 0.67), (0.02, -0.12, 0.77)):
+        pts = sphere * 0.07 + np.array(c)
+        verts = pts.reshape(-1, 3)
+        b.mesh(verts, np.arange(verts.shape[0]).reshape(-1, 3), (0.3, 0.3, 0.3, 0.0, 0.3, 0.3, 0.3, ks))
+    return b.scene()
+
+
+def specular_config():
+    """128x128 frame of the glossy scene: focus 2.0, aperture 0.05, 16 spp,
+    specular preference 0.5."""
+    cam = Camera(width=128, height=128).f32()
+    lens = Lens(2.0, 0.05, 0.05).f32()
+    params = Params(spp_max=16, variance_on=0, r_max=16.0, seed=0, spec_pref=0.5)
+    return specular_scene(), cam, lens, params
+
+
 def plane_scene(z: float, half: float = 50.0, cells: float = 400.0) -> Scene:
     """Single fronto-parallel checker plane at depth z (Lambert, albedo 0.2/0.8)."""
     b = _Builder()
@@ -231,13 +258,14 @@ ROOM_HI = (6.0, 3.0, 8.5)
 
 def room_scene(seed: int = 0, n_boxes: int = 64, n_spheres: int = 32, subdiv: int = 4,
                aspect: float = 16.0 / 9.0, tan_half_fovy: float = math.tan(math.radians(30.0)),
-               n_near: int = 8, zmin_range=(0.3, 8.0), near_max: float = 1.0) -> Scene:
+               n_near: int = 8, zmin_range=(0.3, 8.0), near_max: float = 1.0, specular: float = 0.0) -> Scene:
     """Procedural room: 6 walls (12 triangles), axis-aligned boxes with edges in
     U[0.1,1.0] and icospheres with radius U[0.05,0.4].  Objects are shuffled;
     each gets a nearest-extent depth z_min ~ U[zmin_range] (the first ``n_near``
     forced below ``near_max``) and x, y uniform inside the view frustum (camera
     at the origin looking along +z) clipped to the room.  Per-object grey
-    albedo U[0.05,0.95]."""
+    albedo U[0.05,0.95]; ``specular`` > 0 gives the spheres that Blinn-Phong
+    strength k_s (the random draws, and so the geometry, do not change)."""
     rng = np.random.default_rng(seed)
     b = _Builder()
     (x0, y0, z0), (x1, y1, z1) = ROOM_LO, ROOM_HI
@@ -264,6 +292,8 @@ def room_scene(seed: int = 0, n_boxes: int = 64, n_spheres: int = 32, subdiv: in
         cx = rng.uniform(-hx, hx) if hx > 0 else 0.0
         cy = rng.uniform(-hy, hy) if hy > 0 else 0.0
         alb = grey(float(rng.uniform(0.05, 0.95)))
+        if kind == 1 and specular > 0:
+            alb = alb[:7] + (float(specular),)
         if kind == 0:
             lo = (cx - half[0], cy - half[1], zc - half[2])
             hi = (cx + half[0], cy + half[1], zc + half[2])

@@ -353,13 +353,17 @@ void orc_closest_hits(const void* s, int32_t n, const double* org, const double*
     }
 }
 
-/* Lambert shading of a hit (the paper's deferred shading; the workloads are
- * Lambertian with directional lights and no shadows):
- *   L = albedo * (k_a + sum_l E_l max(0, n . w_l)),
+/* Shading of a hit (the paper's deferred shading; directional lights, no
+ * shadows):
+ *   L = albedo * (k_a + sum_l E_l max(0, n . w_l)) + S (1, 1, 1),
+ *   S = k_s sum_{l: n . w_l > 0} E_l max(0, n . h_l)^32,  h_l = unit(w_l - dir),
  * n = geometric face normal turned to face the ray; albedo from the triangle's
- * material, a checkerboard of n x n cells over its (u,v) when checker_n > 0. */
+ * material, a checkerboard of n x n cells over its (u,v) when checker_n > 0;
+ * S is a white Blinn-Phong highlight (material k_s = mat[7]; the workloads'
+ * materials are Lambertian, k_s = 0, S = 0), returned in *spec when asked.
+ * dir is the unit direction of the ray that found the hit. */
 static void shade_hit(const oscene* s, int32_t tri, const double* bary, const double* dir,
-                      const orc_params* p, double n_out[3], double L[3]) {
+                      const orc_params* p, double n_out[3], double L[3], double* spec) {
     const double* v = s->v + 9 * (size_t)tri;
     double e1[3], e2[3], n[3];
     sub3(v + 3, v, e1);
@@ -378,14 +382,27 @@ static void shade_hit(const oscene* s, int32_t tri, const double* bary, const do
     }
     double irr = p->k_ambient;
     for (int l = 0; l < p->n_lights; ++l) irr += p->light_E[l] * fmax(0.0, dot3(n, p->light_dir[l]));
-    for (int k = 0; k < 3; ++k) { L[k] = alb[k] * irr; n_out[k] = n[k]; }
+    double S = 0.0;
+    if (m[7] > 0.0) {
+        for (int l = 0; l < p->n_lights; ++l) {
+            if (dot3(n, p->light_dir[l]) <= 0.0) continue;
+            double h[3];
+            sub3(p->light_dir[l], dir, h);
+            normalize3(h);
+            S += p->light_E[l] * pow(fmax(0.0, dot3(n, h)), 32.0);
+        }
+        S *= m[7];
+    }
+    for (int k = 0; k < 3; ++k) { L[k] = alb[k] * irr + S; n_out[k] = n[k]; }
+    if (spec) *spec = S;
 }
 
 /* ------------------------------------------------------------------------
  * G-buffer (Design: deferred shading produces the G-buffer and the sharp
  * image).  Rasterisation is restated as the closest hit of the pinhole ray
  * through each pixel's sample point (i + 0.5 + jx, j + 0.5 + jy).
- * nd = (n, view depth z), col = (L, luminance), tri = hit id (-1 = miss).
+ * nd = (n, view depth z), col = (L, S) with S the specular part of L,
+ * tri = hit id (-1 = miss).
  * mv = (i, j) - previous-frame index-space position of the hit point.
  * Misses: z = miss_dist, n = -fwd, L = 0.
  * ---------------------------------------------------------------------- */
@@ -401,7 +418,7 @@ void orc_gbuffer(const void* sp, const orc_camera* cam, const orc_camera* prev, 
             orc_pinhole_dir(cam, i + 0.5 + cam->jitter[0], j + 0.5 + cam->jitter[1], d);
             memcpy(dn, d, sizeof dn);
             normalize3(dn);
-            double t, bary[3], n[3], L[3], P[3];
+            double t, bary[3], n[3], L[3], P[3], S = 0.0;
             int32_t id = orc_closest_hit(s, cam->pos, dn, 1, &t, bary);
             double z;
             if (id >= 0) {
@@ -409,7 +426,7 @@ void orc_gbuffer(const void* sp, const orc_camera* cam, const orc_camera* prev, 
                 double v[3];
                 sub3(P, cam->pos, v);
                 z = dot3(v, cam->fwd);
-                shade_hit(s, id, bary, dn, p, n, L);
+                shade_hit(s, id, bary, dn, p, n, L, &S);
             } else {
                 z = p->miss_dist;
                 for (int k = 0; k < 3; ++k) {
@@ -421,7 +438,7 @@ void orc_gbuffer(const void* sp, const orc_camera* cam, const orc_camera* prev, 
             nd[4 * pix + 0] = n[0]; nd[4 * pix + 1] = n[1]; nd[4 * pix + 2] = n[2];
             nd[4 * pix + 3] = z;
             col[4 * pix + 0] = L[0]; col[4 * pix + 1] = L[1]; col[4 * pix + 2] = L[2];
-            col[4 * pix + 3] = luminance(L);
+            col[4 * pix + 3] = S;
             tri[pix] = id;
             double u[2];
             if (orc_project(prev, P, u)) {
@@ -660,7 +677,7 @@ static void trace_pixel(const oscene* s, const orc_camera* cam, const orc_lens* 
             double v[3];
             sub3(P, cam->pos, v);
             c = orc_coc(dot3(v, cam->fwd), lens, H, t);
-            shade_hit(s, id, bary, dir, p, n_, L);
+            shade_hit(s, id, bary, dir, p, n_, L, NULL);
         } else {
             for (int k = 0; k < 3; ++k) { P[k] = O[k] + p->miss_dist * dir[k]; L[k] = 0.0; }
             c = orc_coc(INFINITY, lens, H, t);
@@ -1020,14 +1037,17 @@ void orc_postfilter(int32_t W, int32_t H, const orc_lens* lens, double t, const 
  * Composite (Composite section).  Focus-zone weight from the pixel's CoC (the
  * reconstructed ray-traced CoC where traced, else the G-buffer depth's):
  *   f = clamp(sqrt2 + 0.5 - |c|, 0, 1)   (the hard |c| < sqrt2 softened over one px)
- * near branch: traced ? C_rec : C_pp   (specular-bokeh preference is zero for
- *   Lambert materials);
+ * near branch: traced ? lerp(C_rec, C_pp, clamp(spec_pref S_pp, 0, 1)) : C_pp,
+ *   S_pp the specular part of the post-process colour (pp_spec, the post-filter
+ *   of the specular plane; the preference for bright specular bokeh); without
+ *   pp_spec, or with spec_pref = 0, traced ? C_rec : C_pp;
  * far branch: traced ? lerp(C_rec, C_pp, clamp(H_acc / h_tau, 0, 1)) : C_pp;
  * C_blur = w_near(c(z_p)) near + (1 - w_near) far;  out = lerp(C_blur, sharp, f).
  * ---------------------------------------------------------------------- */
 void orc_composite(int32_t n, int32_t H, const orc_lens* lens, double t, const orc_params* p,
                    const double* nd, const double* col, const uint8_t* spp, const double* pp,
-                   const double* crt, const double* crec, const double* hacc, double* out) {
+                   const double* pp_spec, const double* crt, const double* crec, const double* hacc,
+                   double* out) {
     /* per-pixel: the planes are flat lists of n pixels of an image of height H */
 #pragma omp parallel for
     for (int32_t qi = 0; qi < n; ++qi) {
@@ -1038,8 +1058,10 @@ void orc_composite(int32_t n, int32_t H, const orc_lens* lens, double t, const o
             double f = clampd(SQRT2 + 0.5 - ce, 0.0, 1.0);
             double wn = clampd((c + SQRT2) / (2.0 * SQRT2), 0.0, 1.0);
             double b = traced ? clampd(hacc[q] / p->h_tau, 0.0, 1.0) : 0.0;
+            double sp = (traced && pp_spec && p->spec_pref > 0.0)
+                            ? clampd(p->spec_pref * pp_spec[4 * q], 0.0, 1.0) : 0.0;
             for (int k = 0; k < 3; ++k) {
-                double near_ = traced ? crec[4 * q + k] : pp[4 * q + k];
+                double near_ = traced ? crec[4 * q + k] + sp * (pp[4 * q + k] - crec[4 * q + k]) : pp[4 * q + k];
                 double far_ = traced ? crec[4 * q + k] + b * (pp[4 * q + k] - crec[4 * q + k]) : pp[4 * q + k];
                 double blur = wn * near_ + (1.0 - wn) * far_;
                 out[4 * q + k] = blur + f * (col[4 * q + k] - blur);
@@ -1078,7 +1100,7 @@ void orc_trace_records(const void* sp, const orc_camera* cam, const orc_lens* le
                     double v[3];
                     sub3(P, cam->pos, v);
                     z = dot3(v, cam->fwd);
-                    shade_hit(s, id, bary, dir, p, n_, L);
+                    shade_hit(s, id, bary, dir, p, n_, L, NULL);
                 } else {
                     z = INFINITY;
                     L[0] = L[1] = L[2] = 0.0;
@@ -1155,7 +1177,7 @@ void orc_reference_rt(const void* sp, const orc_camera* cam, const orc_lens* len
                     n += ws;
                     int32_t id = orc_closest_hit(s, O, dir, 1, &th_, bary);
                     if (id < 0) continue;
-                    shade_hit(s, id, bary, dir, p, n_, L);
+                    shade_hit(s, id, bary, dir, p, n_, L, NULL);
                     for (int c = 0; c < 3; ++c) Sk[c] += ws * L[c];
                 }
                 for (int c = 0; c < 3; ++c) S[c] += Sk[c] / n;

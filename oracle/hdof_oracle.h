@@ -49,6 +49,7 @@ typedef struct {
     double alpha_k;
     int32_t mask_coc, blades;
     double blade_rot, aberration;
+    double spec_pref;
 } orc_params;
 
 /* ---- counter-based RNG (Philox4x32-10, Salmon et al. SC'11) ---- */
@@ -95,8 +96,8 @@ void orc_postfilter(int32_t W, int32_t H, const orc_lens* lens, double tan_half_
                     int32_t n_pix, const int32_t* pix);
 void orc_composite(int32_t n, int32_t H, const orc_lens* lens, double tan_half_fovy,
                    const orc_params* p, const double* nd, const double* col, const uint8_t* spp,
-                   const double* pp, const double* crt, const double* crec, const double* hacc,
-                   double* out);
+                   const double* pp, const double* pp_spec, const double* crt, const double* crec,
+                   const double* hacc, double* out);
 double orc_disk_area(double r);
 double orc_shaped_area(double r, const orc_params* p);
 /* ---- differentiable post-path with frozen visibility ---- */

@@ -54,7 +54,8 @@ class Params(C.Structure):
                 ("miss_dist", C.c_double), ("ema_alpha", C.c_double), ("camera_moved", C.c_int32),
                 ("r_s", C.c_double), ("var_ref", C.c_double), ("r_max", C.c_double),
                 ("kz_rel", C.c_double), ("h_tau", C.c_double), ("alpha_k", C.c_double), ("mask_coc", C.c_int32),
-                ("blades", C.c_int32), ("blade_rot", C.c_double), ("aberration", C.c_double)]
+                ("blades", C.c_int32), ("blade_rot", C.c_double), ("aberration", C.c_double),
+                ("spec_pref", C.c_double)]
 
 
 _lib = None
@@ -97,7 +98,7 @@ def lib():
         L.orc_postfilter.argtypes = [C.c_int32, C.c_int32, C.POINTER(Lens), C.c_double,
                                      C.POINTER(Params), dp, dp, dp, C.c_int32, ip]
         L.orc_composite.argtypes = [C.c_int32, C.c_int32, C.POINTER(Lens), C.c_double,
-                                    C.POINTER(Params), dp, dp, up8, dp, dp, dp, dp, dp]
+                                    C.POINTER(Params), dp, dp, up8, dp, dp, dp, dp, dp, dp]
         L.orc_num_threads.restype = C.c_int32
         L.orc_disk_area.argtypes = [C.c_double]
         i64p = C.POINTER(C.c_int64)
@@ -155,7 +156,7 @@ def params(p) -> Params:
     for name in ("gauss_sigma", "edge_tau", "tile", "dilate", "spp_max", "variance_on", "var_tau",
                  "var_scale", "hlen_young", "seed", "frame", "view", "k_ambient", "miss_dist",
                  "ema_alpha", "camera_moved", "r_s", "var_ref", "r_max", "kz_rel", "h_tau", "alpha_k", "mask_coc",
-                 "blades", "blade_rot", "aberration"):
+                 "blades", "blade_rot", "aberration", "spec_pref"):
         setattr(o, name, getattr(p, name))
     lights = p.unit_lights()
     o.n_lights = len(lights)
@@ -323,14 +324,28 @@ def postfilter(nd, col, lens_, tan_half_fovy, params_, pix=None):
     return pp
 
 
-def composite(nd, col, spp, pp, crt, crec, hacc, lens_, tan_half_fovy, params_, height):
+def spec_plane(col):
+    """The G-buffer's specular part S (col[..., 3]) as the grey colour (S, S, S, S)."""
+    s = np.asarray(col, np.float64)[..., 3]
+    return np.ascontiguousarray(np.repeat(s[..., None], 4, axis=-1))
+
+
+def postfilter_spec(nd, col, lens_, tan_half_fovy, params_, pix=None):
+    """Specular part of the post-process colour: the post-filter of the
+    specular plane (x of the result is S_pp)."""
+    return postfilter(nd, spec_plane(col), lens_, tan_half_fovy, params_, pix=pix)
+
+
+def composite(nd, col, spp, pp, crt, crec, hacc, lens_, tan_half_fovy, params_, height, pp_spec=None):
     """Per-pixel composite of planes of any leading shape (image or pixel list);
-    ``height`` is the image height the CoC is measured against."""
+    ``height`` is the image height the CoC is measured against; ``pp_spec``
+    (the specular part of pp) enables the specular preference of spec_pref."""
     shape = np.asarray(spp).shape
     n = int(np.prod(shape))
     out = np.empty(shape + (4,))
+    ps = _d(pp_spec)[1] if pp_spec is not None else None
     lib().orc_composite(n, int(height), C.byref(lens(lens_)), float(tan_half_fovy), C.byref(params(params_)),
-                        _d(nd)[1], _d(col)[1], _u8(spp)[1], _d(pp)[1], _d(crt)[1], _d(crec)[1],
+                        _d(nd)[1], _d(col)[1], _u8(spp)[1], _d(pp)[1], ps, _d(crt)[1], _d(crec)[1],
                         _d(hacc)[1], _d(out)[1])
     return out
 
@@ -349,16 +364,19 @@ def frame(oscene, cam_, prev_cam, lens_, params_, hist=None, pp_pix=None):
     newh, crt, hacc = temporal(cam_, prev_cam, params_, rt, m["spp"], g["nd"], g["mv"], hist)
     crec = spatial(params_, crt, m["spp"], newh["mom"], newh["hlen"])
     t = cam_.tan_half_fovy
+    spec = params_.spec_pref > 0
     if pp_pix is None:
         pp = postfilter(g["nd"], g["col"], lens_, t, params_)
-        out = composite(g["nd"], g["col"], m["spp"], pp, crt, crec, hacc, lens_, t, params_, H)
+        pps = postfilter_spec(g["nd"], g["col"], lens_, t, params_) if spec else None
+        out = composite(g["nd"], g["col"], m["spp"], pp, crt, crec, hacc, lens_, t, params_, H, pp_spec=pps)
     else:
         pp = postfilter(g["nd"], g["col"], lens_, t, params_, pix=pp_pix)
+        pps = postfilter_spec(g["nd"], g["col"], lens_, t, params_, pix=pp_pix) if spec else None
         sel = np.asarray(pp_pix)
         flat = lambda a: a.reshape(H * W, *a.shape[2:])[sel]  # noqa: E731
         out = composite(flat(g["nd"]), flat(g["col"]), flat(m["spp"]), pp, flat(crt),
-                        flat(crec), flat(hacc), lens_, t, params_, H)
-    return dict(g=g, mask=m, rt=rt, hist=newh, crt=crt, hacc=hacc, crec=crec, pp=pp, out=out)
+                        flat(crec), flat(hacc), lens_, t, params_, H, pp_spec=pps)
+    return dict(g=g, mask=m, rt=rt, hist=newh, crt=crt, hacc=hacc, crec=crec, pp=pp, pp_spec=pps, out=out)
 
 
 def ray_offsets(spp):

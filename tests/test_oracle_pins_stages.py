@@ -824,3 +824,104 @@ def test_shaped_area_limits(orc):
             cont = math.pi * (r * r + 1.0 / 12.0)
             assert abs(orc.shaped_area(r, p) - cont) < 0.01 * cont
     assert orc.shaped_area(12.3, hi.Params()) == orc.disk_area(12.3)
+
+
+# ----------------------------------------- specular highlight and preference
+
+def _glossy_plane(z, ks, cells=40.0):
+    s = hi.plane_scene(z, half=50.0, cells=cells)
+    s.mat = s.mat.copy()
+    s.mat[:, 7] = ks
+    return s
+
+
+def test_blinn_phong_highlight_of_a_plane_lit_from_the_eye(orc):
+    """A fronto-parallel plane seen from the origin and lit from the camera's
+    side (w = -fwd): for the ray at angle theta to the axis the half vector of
+    light and viewer bisects them, so n . h = cos(theta / 2) and the highlight
+    is k_s E cos(theta/2)^32 = k_s E ((1 + cos theta) / 2)^16; the diffuse part
+    is the albedo (0.2 or 0.8) times n . w = 1.  With k_s = 0 the highlight is
+    0 and the colour is the diffuse part alone."""
+    W, H, z, ks = 24, 16, 2.0, 3.0
+    cam = hi.Camera(width=W, height=H).f32()
+    p = hi.Params(k_ambient=0.0, light_dir=[[0.0, 0.0, -1.0]], light_E=[1.0])
+    g = orc.gbuffer(orc.OScene(_glossy_plane(z, ks)), cam, cam, p)
+    t = cam.tan_half_fovy
+    sx = (2.0 * (np.arange(W) + 0.5) / W - 1.0) * t * W / H
+    sy = (2.0 * (np.arange(H) + 0.5) / H - 1.0) * t
+    tan2 = sx[None, :] ** 2 + sy[:, None] ** 2
+    cos_t = 1.0 / np.sqrt(1.0 + tan2)
+    S = ks * ((1.0 + cos_t) / 2.0) ** 16
+    np.testing.assert_allclose(g["col"][..., 3], S, rtol=1e-10)
+    diffuse = g["col"][..., :3] - g["col"][..., 3:4]
+    assert np.all(np.isclose(diffuse, 0.2, atol=1e-10) | np.isclose(diffuse, 0.8, atol=1e-10))
+    g0 = orc.gbuffer(orc.OScene(_glossy_plane(z, 0.0)), cam, cam, p)
+    assert np.all(g0["col"][..., 3] == 0.0)
+    np.testing.assert_allclose(g0["col"][..., :3], diffuse, atol=1e-12)
+
+
+def test_no_highlight_from_a_light_behind_the_surface(orc):
+    """A light behind the plane (w . n < 0 for the normal facing the camera)
+    gives neither diffuse light nor a highlight: the colour is the ambient
+    term alone, whatever k_s."""
+    W, H = 12, 10
+    cam = hi.Camera(width=W, height=H).f32()
+    p = hi.Params(k_ambient=0.25, light_dir=[[0.2, 0.1, 1.0]], light_E=[2.0])
+    g = orc.gbuffer(orc.OScene(_glossy_plane(2.0, 5.0)), cam, cam, p)
+    assert np.all(g["col"][..., 3] == 0.0)
+    rgb = g["col"][..., :3]
+    assert np.all(np.isclose(rgb, 0.25 * 0.2, atol=1e-12) | np.isclose(rgb, 0.25 * 0.8, atol=1e-12))
+
+
+def test_composite_specular_preference_hand_values(orc):
+    """One near, traced, blurred pixel (w_near = 1, focus weight 0): the near
+    branch is C_rec moved toward C_pp by clamp(spec_pref S_pp, 0, 1); without
+    a specular part or with spec_pref = 0 it is C_rec; an untraced pixel takes
+    C_pp whatever the preference."""
+    lens = hi.Lens(2.0, 0.05, 0.05)
+    t = math.tan(math.radians(30.0))
+    H = 128
+    z = 0.5
+    c = 0.05 * H * (2.0 - z) / (z * 2.0 * t)  # ~16.6 px: w_near = 1
+    nd = np.array([[0.0, 0.0, -1.0, z]])
+    col = np.array([[0.9, 0.9, 0.9, 0.0]])
+    crt = np.array([[0.0, 0.0, 0.0, c]])
+    crec = np.array([[1.0, 0.0, 0.2, 0.0]])
+    pp = np.array([[0.0, 1.0, 0.6, 1.0]])
+    pps = np.array([[0.5, 0.5, 0.5, 1.0]])
+    hacc = np.array([1.0])
+    traced = np.array([1], np.uint8)
+
+    def comp(spec_pref, spp=traced, pp_spec=pps):
+        return orc.composite(nd, col, spp, pp, crt, crec, hacc, lens, t, hi.Params(spec_pref=spec_pref), H,
+                             pp_spec=pp_spec)[0, :3]
+
+    np.testing.assert_allclose(comp(1.0), [0.5, 0.5, 0.4], atol=1e-15)
+    np.testing.assert_allclose(comp(0.5), [0.75, 0.25, 0.3], atol=1e-15)
+    np.testing.assert_allclose(comp(4.0), pp[0, :3], atol=1e-15)
+    np.testing.assert_allclose(comp(0.0), crec[0, :3], atol=1e-15)
+    np.testing.assert_allclose(comp(1.0, pp_spec=None), crec[0, :3], atol=1e-15)
+    np.testing.assert_allclose(comp(1.0, spp=np.array([0], np.uint8)), pp[0, :3], atol=1e-15)
+
+
+def test_specular_part_of_the_post_process_colour_is_its_share(orc):
+    """The post-filter is linear in the colour plane, so filtering the
+    specular plane (S, S, S) gives exactly the part of pp that S contributes:
+    pp(col) - pp(col - S) over the colour channels."""
+    W, Hh = 48, 40
+    gb = hi.random_gbuffer(W, Hh, seed=5)
+    col = gb["col"].astype(np.float64).copy()
+    rng = np.random.default_rng(5)
+    S = np.where(rng.random((Hh, W)) < 0.2, rng.uniform(0.5, 3.0, (Hh, W)), 0.0)
+    col[..., :3] += S[..., None]
+    col[..., 3] = S
+    nd = gb["nd"].astype(np.float64)
+    lens = hi.Lens(3.0, 0.05, 0.05)
+    t = math.tan(math.radians(30.0))
+    p = hi.Params(r_max=12.0)
+    diffuse = col.copy()
+    diffuse[..., :3] -= S[..., None]
+    share = orc.postfilter(nd, col, lens, t, p)[..., :3] - orc.postfilter(nd, diffuse, lens, t, p)[..., :3]
+    spec = orc.postfilter_spec(nd, col, lens, t, p)
+    np.testing.assert_allclose(spec[..., :3], share, atol=1e-12)
+    assert spec[..., 0].max() > 0.1  # the highlights do spread
