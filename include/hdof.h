@@ -113,11 +113,13 @@ typedef struct hdof_params {
     int32_t blades;      /* aperture: 0 = circle, 3..16 = regular polygon of that many blades */
     float blade_rot;     /* polygon rotation, radians */
     float aberration;    /* lens sample weight 1 + aberration (2 rho^2 / A^2 - 1), in [-1, 1] */
+    float spec_pref;     /* near branch: post-process share per unit of its specular intensity (Composite) */
 } hdof_params;
 
 /* G-buffer of one frame.  nd: (nx, ny, nz, z) per pixel, n the geometric
  * normal facing the viewer, z view depth (misses: z = miss_dist, n = -fwd);
- * col: (r, g, b, luminance) sharp shaded colour; mv: float2 motion (i, j)
+ * col: (r, g, b, S) sharp shaded colour and its specular part S (the
+ * highlight's luminance, 0 for Lambertian materials); mv: float2 motion (i, j)
  * minus the previous-frame index-space position of the surface point
  * (1e6 when the previous camera cannot see it); tri: original id of the hit
  * triangle, -1 for a miss.  mv and tri may be NULL for calls that do not
@@ -201,7 +203,10 @@ int hdof_probe_fma(int32_t blocks_per_sm, int32_t iters, float* sink, double* la
  * that merge mutual nearest neighbours (smallest union-box surface area
  * within 48 positions) until one cluster remains.  One triangle per leaf.
  * verts: float [n_verts][3]; idx: int32 [n_tris][3];
- * mat: float [n_tris][8] = (albedo_a rgb, checker_n, albedo_b rgb, 0);
+ * mat: float [n_tris][8] = (albedo_a rgb, checker_n, albedo_b rgb, k_s):
+ * Lambert diffuse of the albedo, plus for k_s > 0 a white Blinn-Phong
+ * highlight k_s sum_l E_l max(0, n . h_l)^32 (h_l the unit half vector of
+ * the light and the viewer; lights with n . w_l <= 0 give none);
  * uv: float [n_tris][6] (may be NULL when no material uses a checker).
  * All device pointers; they are read during the call only.  Synchronous
  * with respect to the host (returns once the structure is built).
@@ -448,6 +453,27 @@ int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, con
                    const float* crec, const float* hacc, const hdof_camera* cam,
                    const hdof_lens* lens, const hdof_params* p, float* out, void* stream);
 
+/* Specular-bokeh preference (Composite section): bright specular bokeh is
+ * taken from the post-process rather than the noisy ray trace, by the
+ * intensity of the post-process colour's specular part.
+ * hdof_postfilter_spec: that specular part, the post-filter of
+ * hdof_postfilter applied to the plane (S, S, S) of the G-buffer's col.w in
+ * place of the colour (the filter is linear in the colour, so this is
+ * exactly the share of S in pp).  pp_spec: float [H][W][4] = (S_pp, S_pp,
+ * S_pp, alpha).  workspace as for hdof_postfilter (its first 16 bytes per
+ * pixel hold the grey plane).
+ * hdof_composite_spec: hdof_composite whose near branch where traced is
+ * lerp(C_rec, C_pp, clamp(spec_pref S_pp, 0, 1)); pp_spec may be NULL and
+ * is ignored when spec_pref = 0 (then it equals hdof_composite).  Neither
+ * is batched; the differentiable path rejects spec_pref != 0
+ * (HDOF_EUNSUPPORTED). */
+int hdof_postfilter_spec(const hdof_gbuf* in, const hdof_camera* cam, const hdof_lens* lens,
+                         const hdof_params* p, float* pp_spec, void* workspace, size_t workspace_bytes,
+                         void* stream);
+int hdof_composite_spec(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* pp_spec,
+                        const float* crt, const float* crec, const float* hacc, const hdof_camera* cam,
+                        const hdof_lens* lens, const hdof_params* p, float* out, void* stream);
+
 /* ------------------------------------------------- batched multi-view -- */
 /* One view of a batch: its scene, cameras, lens, constants and buffers
  * (every pointer as for the single-view calls; FP32 G-buffer planes, mv
@@ -481,7 +507,9 @@ typedef struct hdof_batch hdof_batch;
 /* Prepares a batch: validates every view, builds each stage's per-view
  * launch records and block tables and copies them to device memory the
  * handle owns (synchronous).  The views' buffers must stay valid while the
- * handle is used.  tuning may be NULL (defaults 128 / 4). */
+ * handle is used.  tuning may be NULL (defaults 128 / 4).  Views with
+ * shaped bokeh or spec_pref != 0 return HDOF_EUNSUPPORTED (specular
+ * materials themselves are shaded as in the single-view calls). */
 int hdof_batch_create(const hdof_view* views, int32_t n_views, const hdof_tuning* tuning, hdof_batch** out,
                       void* stream);
 int hdof_batch_destroy(hdof_batch* batch);
@@ -563,9 +591,9 @@ int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const float* rec,
  * grad_lens (device float [2] = d/d focus_dist, d/d aperture_radius).  Gather
  * weights are recomputed, not stored; the lens gradient is reduced per block
  * in double precision and summed in a fixed order (deterministic).  Needs
- * aperture_radius > 0.  Both calls take the fixed EMA weight and the uniform
- * circular lens: alpha_k, blades and aberration other than 0 return
- * HDOF_EUNSUPPORTED. */
+ * aperture_radius > 0.  Both calls take the fixed EMA weight, the uniform
+ * circular lens and no specular preference: alpha_k, blades, aberration and
+ * spec_pref other than 0 return HDOF_EUNSUPPORTED. */
 int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
                        const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
                        const hdof_params* p, const hdof_post_state* st, const float* grad_out,

@@ -775,9 +775,9 @@ int check_post(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const 
                        st->pp_aux && st->out,
                    "%s: every state buffer is required", who);
     HDOF_CHECK_ARG(lens->aperture_radius > 0.f, "%s: the lens gradient needs an aperture > 0", who);
-    if (p->alpha_k != 0.f || p->blades != 0 || p->aberration != 0.f) {
-        set_error("%s: the differentiable path takes the fixed EMA weight and the uniform circular lens "
-                  "(alpha_k, blades and aberration must be 0)", who);
+    if (p->alpha_k != 0.f || p->blades != 0 || p->aberration != 0.f || p->spec_pref != 0.f) {
+        set_error("%s: the differentiable path takes the fixed EMA weight, the uniform circular lens and no "
+                  "specular preference (alpha_k, blades, aberration and spec_pref must be 0)", who);
         return HDOF_EUNSUPPORTED;
     }
     return HDOF_OK;
@@ -822,7 +822,7 @@ extern "C" int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const 
         return rc;
     Coc coc = make_coc(*lens, H, cam->tan_half_fovy);
     if ((rc = launch_postfilter(in, coc, p, st->pp, reinterpret_cast<float4*>(st->pp_aux), workspace, s))) return rc;
-    return launch_composite(in, spp, st->pp, st->crt, st->crec, st->hacc, coc, p->h_tau, st->out, s);
+    return launch_composite(in, spp, st->pp, nullptr, st->crt, st->crec, st->hacc, coc, p->h_tau, 0.f, st->out, s);
 }
 
 extern "C" int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,

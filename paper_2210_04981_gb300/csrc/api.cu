@@ -84,6 +84,7 @@ int check_params(const hdof_params* p, const char* who) {
     HDOF_CHECK_ARG(std::isfinite(p->blade_rot) && std::isfinite(p->aberration) && p->aberration >= -1.f &&
                        p->aberration <= 1.f,
                    "%s: blade_rot must be finite and aberration in [-1, 1]", who);
+    HDOF_CHECK_ARG(std::isfinite(p->spec_pref) && p->spec_pref >= 0.f, "%s: spec_pref must be >= 0", who);
     return HDOF_OK;
 }
 

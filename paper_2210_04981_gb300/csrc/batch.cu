@@ -79,6 +79,11 @@ int check_view(const hdof_view& v, int k, int dev) {
                   who);
         return HDOF_EUNSUPPORTED;
     }
+    if (v.params.spec_pref != 0.f) {
+        set_error("%s: the specular-bokeh preference (spec_pref) is not batched; render such views with the "
+                  "single-view calls", who);
+        return HDOF_EUNSUPPORTED;
+    }
     HDOF_CHECK_ARG(v.g.width == v.cam.width && v.g.height == v.cam.height && v.prev.width == v.cam.width &&
                        v.prev.height == v.cam.height,
                    "%s: size mismatch between gbuf and cameras", who);

@@ -249,7 +249,7 @@ __global__ void k_refit(const float* __restrict__ v, const int* __restrict__ idx
 
 __global__ void k_leaf_data(const float* __restrict__ v, const int* __restrict__ idx, const float* __restrict__ mat,
                             const float* __restrict__ uv, const int* __restrict__ ids, int n, Tri* tris,
-                            float4* mato, float2* uvo, int* slot_of) {
+                            float4* mato, float2* uvo, int* slot_of, int* specular) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int id = ids[k];
@@ -263,6 +263,7 @@ __global__ void k_leaf_data(const float* __restrict__ v, const int* __restrict__
     const float* m = mat + 8 * (size_t)id;
     mato[2 * k] = make_float4(m[0], m[1], m[2], m[3]);
     mato[2 * k + 1] = make_float4(m[4], m[5], m[6], m[7]);
+    if (m[7] > 0.f) atomicOr(specular, 1);
     if (uv) {
         const float* u = uv + 6 * (size_t)id;
         uvo[3 * k] = make_float2(u[0], u[1]);
@@ -603,7 +604,8 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
     size_t off_uv = off_mat + up256(sizeof(float4) * 2 * (size_t)n);
     size_t off_big = off_uv + up256(sizeof(float2) * 3 * (size_t)n);
     size_t off_slot = off_big + up256(sizeof(float4) * 2 * (size_t)(n_big > 0 ? n_big : 1));
-    size_t total = off_slot + sizeof(int) * (size_t)n;
+    size_t off_spec = off_slot + up256(sizeof(int) * (size_t)n);
+    size_t total = off_spec + sizeof(int);
     if ((e = cudaMalloc(&b->pool, total)) != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: cudaMalloc"));
     b->bytes = total;
     char* base = static_cast<char*>(b->pool);
@@ -619,10 +621,18 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
     e = cub::DeviceRadixSort::SortPairs(sort_tmp, sort_bytes, keys_in, keys_out, ids_in, ids_out, n, 0,
                                         separate ? 64 : 63, s);
     if (e != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: sort"));
+    int* spec_flag = reinterpret_cast<int*>(base + off_spec);
+    if ((e = cudaMemsetAsync(spec_flag, 0, sizeof(int), s)) != cudaSuccess)
+        return fail(cuda_fail(e, "hdof_build_bvh: clear"));
     k_leaf_data<<<blocks_for(n, 256), 256, 0, s>>>(verts, idx, mat, uv, ids_out, n, b->tris, b->mat, b->uv,
-                                                    b->slot_of);
+                                                    b->slot_of, spec_flag);
     if (n_big > 0) k_big_boxes<<<1, 64, 0, s>>>(b->tris, n - n_big, n_big, b->big_box);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: leaf data"));
+    int has_spec = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&has_spec, spec_flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fail(cuda_fail(e, "hdof_build_bvh: leaf data"));
+    b->specular = has_spec;
 
     int depth = 0;
     b->n_nodes = 0;

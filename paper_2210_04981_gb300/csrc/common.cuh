@@ -181,7 +181,7 @@ struct __align__(16) Tri {
 struct BvhView {
     const Node* nodes;
     const Tri* tris;
-    const float4* mat;  // sorted order: [2] per triangle (albedo_a rgb + checker_n, albedo_b)
+    const float4* mat;  // sorted order: [2] per triangle (albedo_a rgb + checker_n, albedo_b rgb + k_s)
     const float2* uv;   // sorted order: [3] per triangle
     int n_tris;
     int root;           // root reference (node 0, or a leaf)
@@ -189,6 +189,7 @@ struct BvhView {
     int big_count;      //   triangles tested by every ray after the traversal
     const float4* big_box;  // [2] per scene-sized triangle: (lo xyz, 0), (hi xyz, 0)
     const int* slot_of;     // sorted slot of each original triangle id
+    int specular;           // some material has k_s > 0 (else every material is Lambertian)
 };
 
 struct Ray {
@@ -620,8 +621,11 @@ __host__ __device__ inline Lights make_lights(const hdof_params& p) {
     return l;
 }
 
+// Shading of a hit seen along the unit direction d: Lambert diffuse under
+// directional lights, plus a white Blinn-Phong highlight (exponent 32) for
+// materials with k_s > 0, whose luminance is returned in spec.
 __device__ __forceinline__ void shade(const BvhView& bvh, const Lights& L, const Hit& h, float3 d, float3& n,
-                                      float3& rad) {
+                                      float3& rad, float& spec) {
     const Tri* tr = bvh.tris + h.slot;
     float4 p0 = __ldg(&tr->v0), p1 = __ldg(&tr->v1), p2 = __ldg(&tr->v2);
     float3 v0 = f3(p0.x, p0.y, p0.z);
@@ -643,6 +647,25 @@ __device__ __forceinline__ void shade(const BvhView& bvh, const Lights& L, const
     float irr = L.ka;
     for (int k = 0; k < L.n; ++k) irr += L.E[k] * fmaxf(0.f, dot(n, L.dir[k]));
     rad = irr * alb;
+    spec = 0.f;
+    if (bvh.specular) {
+        const float ks = __ldg(&bvh.mat[2 * h.slot + 1].w);
+        if (ks > 0.f) {
+            float s = 0.f;
+            for (int k = 0; k < L.n; ++k) {
+                if (dot(n, L.dir[k]) <= 0.f) continue;
+                float c = fmaxf(0.f, dot(n, normalize(L.dir[k] - d)));  // half vector of light and viewer
+                c *= c;
+                c *= c;
+                c *= c;
+                c *= c;
+                c *= c;
+                s += L.E[k] * c;
+            }
+            spec = ks * s;
+            rad = rad + f3(spec, spec, spec);
+        }
+    }
 }
 
 }  // namespace hdof

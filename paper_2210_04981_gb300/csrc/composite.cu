@@ -2,7 +2,11 @@
 // sqrt2) take the sharp rasterised colour; outside it, near geometry takes
 // the ray-traced colour and far geometry blends ray-traced and post-process
 // colour by the hit ratio, only below a threshold hit ratio so the edges of
-// the ray mask do not show.  One thread per pixel, float4 planes.
+// the ray mask do not show.  Near geometry whose post-process colour carries
+// a bright specular component leans toward the post-process colour instead
+// (its highlight bokeh is smooth there and noisy in the ray trace), by
+// clamp(spec_pref S_pp, 0, 1) with S_pp the post-filtered specular
+// luminance.  One thread per pixel, float4 planes.
 #include "batch.cuh"
 #include "internal.h"
 
@@ -15,12 +19,14 @@ struct CompositeArgs {
     const COL* col;
     const uint8_t* spp;
     const float4* pp;
+    const float4* pp_spec;  // post-filtered specular luminance in x; NULL: no preference
     const float4* crt;
     const float4* crec;
     const float* hacc;
     int W, H;
     Coc coc;
     float h_tau;
+    float spec_pref;
     float4* out;
 };
 
@@ -52,7 +58,8 @@ __device__ __forceinline__ void composite_body(const CompositeArgs<ND, COL>& a, 
         float4 r4 = __ldg(&crec[q]);
         float3 rec = f3(r4.x, r4.y, r4.z);
         float b = clamp01(__ldg(&hacc[q]) / h_tau);
-        nearc = rec;  // specular-bokeh preference: zero for Lambert materials
+        nearc = rec;
+        if (a.pp_spec) nearc = rec + clamp01(a.spec_pref * __ldg(&a.pp_spec[q].x)) * (cpp - rec);
         farc = rec + b * (cpp - rec);
     }
     float f = clamp01(HDOF_SQRT2 + 0.5f - ce);
@@ -75,28 +82,30 @@ __global__ void __launch_bounds__(256) k_composite_batch(const CompositeF32* __r
 }
 
 template <class ND, class COL>
-void launch(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
-            const float* hacc, Coc coc, float h_tau, float* out, cudaStream_t s) {
+void launch(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* pp_spec, const float* crt,
+            const float* crec, const float* hacc, Coc coc, float h_tau, float spec_pref, float* out, cudaStream_t s) {
     dim3 g((in->width + 31) / 32, (in->height + 7) / 8);
     ProfScope ps_("composite", s);
     k_composite<ND, COL><<<g, 256, 0, s>>>(CompositeArgs<ND, COL>{
         static_cast<const ND*>(in->nd), static_cast<const COL*>(in->col), spp, reinterpret_cast<const float4*>(pp),
-        reinterpret_cast<const float4*>(crt), reinterpret_cast<const float4*>(crec), hacc, in->width, in->height, coc,
-        h_tau, reinterpret_cast<float4*>(out)});
+        reinterpret_cast<const float4*>(pp_spec), reinterpret_cast<const float4*>(crt),
+        reinterpret_cast<const float4*>(crec), hacc, in->width, in->height, coc, h_tau, spec_pref,
+        reinterpret_cast<float4*>(out)});
 }
 
 }  // namespace
 
-int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
-                     const float* hacc, const Coc& coc, float h_tau, float* out, cudaStream_t s) {
+int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* pp_spec,
+                     const float* crt, const float* crec, const float* hacc, const Coc& coc, float h_tau,
+                     float spec_pref, float* out, cudaStream_t s) {
     if (in->dtype_nd == HDOF_F32 && in->dtype_col == HDOF_F32)
-        launch<float4, float4>(in, spp, pp, crt, crec, hacc, coc, h_tau, out, s);
+        launch<float4, float4>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s);
     else if (in->dtype_nd == HDOF_F16 && in->dtype_col == HDOF_BF16)
-        launch<half4s, bf164s>(in, spp, pp, crt, crec, hacc, coc, h_tau, out, s);
+        launch<half4s, bf164s>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s);
     else if (in->dtype_nd == HDOF_F16)
-        launch<half4s, float4>(in, spp, pp, crt, crec, hacc, coc, h_tau, out, s);
+        launch<half4s, float4>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s);
     else
-        launch<float4, bf164s>(in, spp, pp, crt, crec, hacc, coc, h_tau, out, s);
+        launch<float4, bf164s>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s);
     HDOF_LAUNCHED("composite");
     return HDOF_OK;
 }
@@ -105,9 +114,9 @@ int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, c
 
 using namespace hdof;
 
-extern "C" int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt,
-                              const float* crec, const float* hacc, const hdof_camera* cam, const hdof_lens* lens,
-                              const hdof_params* p, float* out, void* stream) {
+extern "C" int hdof_composite_spec(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* pp_spec,
+                                   const float* crt, const float* crec, const float* hacc, const hdof_camera* cam,
+                                   const hdof_lens* lens, const hdof_params* p, float* out, void* stream) {
     clear_error();
     int rc;
     if ((rc = check_camera(cam, "hdof_composite")) || (rc = check_lens(lens, "hdof_composite")) ||
@@ -115,8 +124,15 @@ extern "C" int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const flo
         return rc;
     HDOF_CHECK_ARG(spp && pp && crt && crec && hacc && out, "hdof_composite: NULL buffer");
     HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height, "hdof_composite: gbuf/camera size mismatch");
-    return launch_composite(in, spp, pp, crt, crec, hacc, make_coc(*lens, cam->height, cam->tan_half_fovy), p->h_tau,
-                            out, as_stream(stream));
+    return launch_composite(in, spp, pp, p->spec_pref > 0.f ? pp_spec : nullptr, crt, crec, hacc,
+                            make_coc(*lens, cam->height, cam->tan_half_fovy), p->h_tau, p->spec_pref, out,
+                            as_stream(stream));
+}
+
+extern "C" int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt,
+                              const float* crec, const float* hacc, const hdof_camera* cam, const hdof_lens* lens,
+                              const hdof_params* p, float* out, void* stream) {
+    return hdof_composite_spec(in, spp, pp, nullptr, crt, crec, hacc, cam, lens, p, out, stream);
 }
 
 namespace hdof {
@@ -127,6 +143,7 @@ void composite_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int
                                                          static_cast<const float4*>(v.g.col),
                                                          v.spp,
                                                          reinterpret_cast<const float4*>(v.pp),
+                                                         nullptr,
                                                          reinterpret_cast<const float4*>(v.crt),
                                                          reinterpret_cast<const float4*>(v.crec),
                                                          v.hacc,
@@ -134,6 +151,7 @@ void composite_fill(const hdof_view& v, const ViewWs&, unsigned*, void* dst, int
                                                          v.cam.height,
                                                          make_coc(v.lens, v.cam.height, v.cam.tan_half_fovy),
                                                          v.params.h_tau,
+                                                         0.f,
                                                          reinterpret_cast<float4*>(v.out)};
     *gx = (v.cam.width + 31) / 32;
     *gy = (v.cam.height + 7) / 8;

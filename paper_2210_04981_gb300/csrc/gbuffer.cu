@@ -40,11 +40,11 @@ __device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx,
     }
     Hit h = closest_hit(a.bvh, cam.pos, dn, a.cap, a.status, hint_slot);
     float3 n, rad, P;
-    float z;
+    float z, spec = 0.f;
     if (h.slot >= 0) {
         P = cam.pos + h.t * dn;
         z = dot(P - cam.pos, cam.fwd);
-        shade(a.bvh, a.L, h, dn, n, rad);
+        shade(a.bvh, a.L, h, dn, n, rad, spec);
     } else {
         z = a.miss_dist;
         P = cam.pos + z * d;
@@ -52,7 +52,7 @@ __device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx,
         rad = f3(0.f, 0.f, 0.f);
     }
     st4(a.nd + q, make_float4(n.x, n.y, n.z, z));
-    st4(a.col + q, make_float4(rad.x, rad.y, rad.z, luminance(rad)));
+    st4(a.col + q, make_float4(rad.x, rad.y, rad.z, spec));
     if (a.tri) a.tri[q] = h.id;
     if (a.mv) {
         float ux, uy;

@@ -109,8 +109,9 @@ int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, in
 // scratch: ws_layout(W, H, p).pf bytes (the post-filter regions)
 int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, float4* aux,
                       void* scratch, cudaStream_t s);
-int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* crt, const float* crec,
-                     const float* hacc, const Coc& coc, float h_tau, float* out, cudaStream_t s);
+int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* pp_spec,
+                     const float* crt, const float* crec, const float* hacc, const Coc& coc, float h_tau,
+                     float spec_pref, float* out, cudaStream_t s);
 
 }  // namespace hdof
 
@@ -128,6 +129,7 @@ struct hdof_bvh {
     float2* uv;
     float4* big_box;  // [2 * n_big]
     int* slot_of;     // [n_tris] sorted slot of each original triangle id
+    int specular;     // some material has a specular coefficient k_s > 0
     void* pool;  // single allocation holding all of the above
     hdof::BvhView view() const {
         hdof::BvhView v;
@@ -141,6 +143,7 @@ struct hdof_bvh {
         v.big_count = n_big;
         v.big_box = big_box;
         v.slot_of = slot_of;
+        v.specular = specular;
         return v;
     }
 };

@@ -695,6 +695,57 @@ extern "C" int hdof_postfilter(const hdof_gbuf* in, const hdof_camera* cam, cons
 }
 
 namespace hdof {
+namespace {
+
+// The specular luminance (col.w) of every pixel as an opaque grey colour.
+template <class COL>
+__global__ void __launch_bounds__(256) k_spec_plane(const COL* __restrict__ col, size_t n, float4* __restrict__ out) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float s = ld4(col + q).w;
+    out[q] = make_float4(s, s, s, s);
+}
+
+}  // namespace
+}  // namespace hdof
+
+extern "C" int hdof_postfilter_spec(const hdof_gbuf* in, const hdof_camera* cam, const hdof_lens* lens,
+                                    const hdof_params* p, float* pp_spec, void* workspace, size_t workspace_bytes,
+                                    void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_camera(cam, "hdof_postfilter_spec")) || (rc = check_lens(lens, "hdof_postfilter_spec")) ||
+        (rc = check_params(p, "hdof_postfilter_spec")) || (rc = check_gbuf(in, "hdof_postfilter_spec", false)))
+        return rc;
+    HDOF_CHECK_ARG(pp_spec, "hdof_postfilter_spec: pp_spec output is required");
+    HDOF_CHECK_ARG(in->width == cam->width && in->height == cam->height,
+                   "hdof_postfilter_spec: gbuf/camera size mismatch");
+    WsLayout L = ws_layout(in->width, in->height, p);
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= L.total, "hdof_postfilter_spec: workspace of %zu bytes < %zu",
+                   workspace_bytes, L.total);
+    // the grey plane sits below the post-filter's region (the mask and trace
+    // scratch, at least 16 bytes per pixel since spp_max >= 1)
+    const size_t n = (size_t)in->width * in->height;
+    HDOF_CHECK_ARG(n * sizeof(float4) <= L.pf_off, "hdof_postfilter_spec: no room for the specular plane");
+    float4* plane = static_cast<float4*>(workspace);
+    cudaStream_t s = as_stream(stream);
+    {
+        ProfScope ps_("pf_spec_plane", s);
+        const unsigned blocks = (unsigned)((n + 255) / 256);
+        if (in->dtype_col == HDOF_F32)
+            k_spec_plane<<<blocks, 256, 0, s>>>(static_cast<const float4*>(in->col), n, plane);
+        else
+            k_spec_plane<<<blocks, 256, 0, s>>>(static_cast<const bf164s*>(in->col), n, plane);
+    }
+    HDOF_LAUNCHED("specular plane");
+    hdof_gbuf g = *in;
+    g.dtype_col = HDOF_F32;
+    g.col = plane;
+    return launch_postfilter(&g, make_coc(*lens, in->height, cam->tan_half_fovy), p, pp_spec, nullptr,
+                             static_cast<char*>(workspace) + L.pf_off, s);
+}
+
+namespace hdof {
 
 size_t pf_prep_args_size() { return sizeof(PrepF32); }
 void pf_prep_fill(const hdof_view& v, const ViewWs& w, unsigned*, void* dst, int* gx, int* gy) {

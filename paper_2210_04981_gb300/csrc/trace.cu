@@ -611,7 +611,8 @@ __device__ __forceinline__ void resolve_body(const TraceArgs& a, int bx) {
             tri_bary(O, make_shear(dir), f3(p0.x, p0.y, p0.z), f3(p1.x, p1.y, p1.z), f3(p2.x, p2.y, p2.z), h.b0, h.b1,
                      h.b2);
             float3 nrm;
-            shade(a.bvh, a.L, h, dir, nrm, L);
+            float spec;
+            shade(a.bvh, a.L, h, dir, nrm, L, spec);
             P = O + rc.x * dir;
             c = a.coc(dot(P - a.cam.pos, a.cam.fwd));
         } else {

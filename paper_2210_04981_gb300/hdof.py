@@ -50,7 +50,7 @@ class hdof_params(C.Structure):
                 ("camera_moved", C.c_int32), ("r_s", C.c_float), ("var_ref", C.c_float),
                 ("r_max", C.c_float), ("kz_rel", C.c_float), ("h_tau", C.c_float),
                 ("alpha_k", C.c_float), ("mask_coc", C.c_int32), ("blades", C.c_int32), ("blade_rot", C.c_float),
-                ("aberration", C.c_float)]
+                ("aberration", C.c_float), ("spec_pref", C.c_float)]
 
 
 class hdof_gbuf(C.Structure):
@@ -134,6 +134,10 @@ def load():
                               P(hdof_params), P(hdof_history), P(hdof_history), vp, vp, vp, vp], C.c_int),
         "hdof_composite": ([P(hdof_gbuf), vp, vp, vp, vp, vp, P(hdof_camera), P(hdof_lens), P(hdof_params),
                             vp, vp], C.c_int),
+        "hdof_postfilter_spec": ([P(hdof_gbuf), P(hdof_camera), P(hdof_lens), P(hdof_params), vp, vp, sz, vp],
+                                 C.c_int),
+        "hdof_composite_spec": ([P(hdof_gbuf), vp, vp, vp, vp, vp, vp, P(hdof_camera), P(hdof_lens),
+                                 P(hdof_params), vp, vp], C.c_int),
         "hdof_batch_create": ([P(hdof_view), i32, P(hdof_tuning), P(vp), vp], C.c_int),
         "hdof_batch_update": ([vp, P(hdof_view), i32, vp], C.c_int),
         "hdof_batch_render": ([vp, vp], C.c_int),
@@ -159,7 +163,7 @@ def exported_symbols():
     return ["hdof_version", "hdof_last_error", "hdof_sync", "hdof_default_params", "hdof_build_bvh",
             "hdof_bvh_destroy", "hdof_bvh_info", "hdof_closest_hits", "hdof_gbuffer", "hdof_workspace_bytes",
             "hdof_mask", "hdof_mask_coc", "hdof_mask_noalloc", "hdof_trace", "hdof_trace_hits", "hdof_reference_rt", "hdof_error_map",
-            "hdof_postfilter", "hdof_reconstruct", "hdof_composite",
+            "hdof_postfilter", "hdof_postfilter_spec", "hdof_reconstruct", "hdof_composite", "hdof_composite_spec",
             "hdof_batch_create", "hdof_batch_update", "hdof_batch_render", "hdof_batch_render_range",
             "hdof_batch_destroy", "hdof_batch_bytes",
             "hdof_post_workspace_bytes", "hdof_post_forward", "hdof_post_backward", "hdof_profile",
@@ -212,7 +216,7 @@ def lens(l) -> hdof_lens:
 _PARAM_NAMES = ("gauss_sigma", "edge_tau", "tile", "dilate", "spp_max", "variance_on", "var_tau", "var_scale",
                 "hlen_young", "seed", "frame", "view", "k_ambient", "miss_dist", "trav_cap", "ema_alpha",
                 "camera_moved", "r_s", "var_ref", "r_max", "kz_rel", "h_tau", "alpha_k", "mask_coc", "blades",
-                "blade_rot", "aberration")
+                "blade_rot", "aberration", "spec_pref")
 
 
 def params(p=None) -> hdof_params:
@@ -453,6 +457,20 @@ def hdof_composite(gbuf: GBuffer, spp, pp, crt, crec, hacc, cam, lns, p, out, st
                                  _stream(stream)))
 
 
+def hdof_postfilter_spec(gbuf: GBuffer, cam, lns, p, pp_spec, workspace, stream=None):
+    """Post-filter of the specular plane col.w: pp_spec [H,W,4] = (S_pp x3, alpha)."""
+    _check(load().hdof_postfilter_spec(C.byref(gbuf.struct()), C.byref(camera(cam)), C.byref(lens(lns)),
+                                       C.byref(params(p)), _ptr(pp_spec), _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def hdof_composite_spec(gbuf: GBuffer, spp, pp, pp_spec, crt, crec, hacc, cam, lns, p, out, stream=None):
+    _check(load().hdof_composite_spec(C.byref(gbuf.struct()), _ptr(spp), _ptr(pp),
+                                      _ptr(pp_spec) if pp_spec is not None else None, _ptr(crt), _ptr(crec),
+                                      _ptr(hacc), C.byref(camera(cam)), C.byref(lens(lns)), C.byref(params(p)),
+                                      _ptr(out), _stream(stream)))
+
+
 # ---------------------------------------------------------- frame driver --
 
 class Renderer:
@@ -474,6 +492,7 @@ class Renderer:
         self.hacc = torch.empty((height, width), dtype=torch.float32, device=dev)
         self.crec = torch.empty((height, width, 4), dtype=torch.float32, device=dev)
         self.out = torch.empty((height, width, 4), dtype=torch.float32, device=dev)
+        self.pp_spec = None  # allocated by the first frame with spec_pref > 0
         self.stats = torch.zeros(2, dtype=torch.int32, device=dev)
         self.hist = [History(width, height, dev), History(width, height, dev)]
         self.cur = 0
@@ -498,7 +517,15 @@ class Renderer:
         hdof_postfilter(self.g, cam, lns, p, self.pp, self.ws, stream)
         hdof_reconstruct(self.rt, self.g, self.spp, cam, prev, lns, p, hin, hout, self.crt, self.hacc,
                          self.crec, stream)
-        hdof_composite(self.g, self.spp, self.pp, self.crt, self.crec, self.hacc, cam, lns, p, self.out, stream)
+        if p.spec_pref > 0:
+            if self.pp_spec is None:
+                self.pp_spec = torch.empty_like(self.pp)
+            hdof_postfilter_spec(self.g, cam, lns, p, self.pp_spec, self.ws, stream)
+            hdof_composite_spec(self.g, self.spp, self.pp, self.pp_spec, self.crt, self.crec, self.hacc, cam, lns,
+                                p, self.out, stream)
+        else:
+            hdof_composite(self.g, self.spp, self.pp, self.crt, self.crec, self.hacc, cam, lns, p, self.out,
+                           stream)
         self.cur = 1 - self.cur
         return self.out
 
