@@ -453,6 +453,46 @@ def quality_variants(H, bvh, W, Hh, lens, p0, dev, flush, frames, passes):
     return out
 
 
+def quality_glossy(H, W, Hh, lens, p0, dev, frames, passes, ks=2.0, pref=0.5):
+    """The Composite section's specular-bokeh preference on the workload's
+    room with glossy spheres (Blinn-Phong k_s = ks), static camera, after
+    `frames` frames: the last frame composited without and with the
+    preference (spec_pref = pref) and with the post-process alone, against
+    full ray tracing, over the traced pixels and over the near highlights
+    (traced pixels where clamp(pref S_pp, 0, 1) > 0.05)."""
+    import torch
+    scene = hi.room_scene(seed=0, aspect=W / Hh, specular=ks)
+    bvh = H.hdof_build_bvh(*(torch.from_numpy(a).to(dev) for a in (scene.verts, scene.idx, scene.mat, scene.uv)))
+    cam = hi.room_camera(0, W, Hh)
+    p = p0.replace(spec_pref=pref)
+    r = H.Renderer(bvh, W, Hh, p, device=dev)
+    for k in range(frames):
+        r.frame(cam, cam, lens, p.replace(frame=k, camera_moved=0))
+    last = p.replace(frame=frames - 1, camera_moved=0)
+    rt = torch.empty_like(r.out)
+    H.hdof_reference_rt(bvh, cam, lens, last, passes, rt, r.ws, hint=r.g.tri)
+    traced = (r.spp > 0).to(torch.uint8).contiguous()
+    hl = ((r.pp_spec[..., 0] * pref > 0.05) & (r.spp > 0)).to(torch.uint8).contiguous()
+    imgs = {"with_preference": r.out.clone(), "without_preference": torch.empty_like(r.out),
+            "post_process_only": torch.empty_like(r.out)}
+    H.hdof_composite(r.g, r.spp, r.pp, r.crt, r.crec, r.hacc, cam, lens, last.replace(spec_pref=0.0),
+                     imgs["without_preference"])
+    H.hdof_composite(r.g, torch.zeros_like(r.spp), r.pp, r.crt, r.crec, r.hacc, cam, lens, last,
+                     imgs["post_process_only"])
+    stats = torch.empty(H.ERR_SCRATCH, dtype=torch.float64, device=r.out.device)
+    out = {"k_s": ks, "spec_pref": pref, "traced_pixels": int(traced.sum()), "highlight_pixels": int(hl.sum())}
+    for name, img in imgs.items():
+        H.hdof_error_map(img, rt, stats, region=traced)
+        tr = H.error_summary(stats)["region"]
+        H.hdof_error_map(img, rt, stats, region=hl)
+        h = H.error_summary(stats)["region"]
+        out[name] = {"traced_mae": round(tr["mae"], 6), "highlight_mae": round(h["mae"], 6),
+                     "highlight_rmse": round(h["rmse"], 6)}
+    del r
+    bvh.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -539,6 +579,7 @@ def run_ours(args):
     qual = quality(H, bvh, r, cams[last], lens, p0.replace(frame=last % 65536, camera_moved=1), args.rt_passes)
     if not args.no_compare and ws == 1:
         qual["variants_after_8_frames"] = quality_variants(H, bvh, W, Hh, lens, p0, dev, flush, 8, args.rt_passes)
+        qual["glossy_static_after_8_frames"] = quality_glossy(H, W, Hh, lens, p0, dev, 8, args.rt_passes)
     e2e = None
     if not args.no_e2e:
         e_ms, h2d, d2h = e2e_frames(H, r, Hh, W, args.warmup, K, flush)
