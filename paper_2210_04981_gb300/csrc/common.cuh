@@ -192,9 +192,31 @@ struct BvhView {
     int specular;           // some material has k_s > 0 (else every material is Lambertian)
 };
 
+// Two floats in one 64-bit register pair, the operand form of the f32x2
+// instructions (each lane rounds as the scalar instruction).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+// (a.x b.x + c.x, a.y b.y + c.y), each rounded once
+__device__ __forceinline__ float2 fma_x2(f32x2 a, f32x2 b, f32x2 c) {
+    float2 r;
+    asm("{\n\t.reg .b64 t;\n\tfma.rn.f32x2 t, %2, %3, %4;\n\tmov.b64 {%0, %1}, t;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// A ray with its box-test constants in f32x2 form: per axis (1/d, 1/d) and
+// (-cl, -ch), cl and ch being o/d shifted so that the distances to a box's
+// l- and h-plane err outwards; one fma.rn.f32x2 of a box's (l, h) pair on an
+// axis gives both plane distances.
 struct Ray {
-    float3 o, d, id;  // id = 1 / d (finite)
-    float3 cl, ch;    // per axis: o id shifted so the l- and h-plane distances err outwards
+    float3 o, d;
+    f32x2 id2[3];
+    f32x2 off2[3];
 };
 
 // Plane distances are fma(l, id, -o id): (l - o) id (1 + d1) - (o id) d2 with
@@ -210,16 +232,22 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     r.o = o;
     r.d = d;
     const float tiny = 1e-20f;
-    r.id = f3(1.f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
-              1.f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
-              1.f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
-    const float3 ood = f3(o.x * r.id.x, o.y * r.id.y, o.z * r.id.z);
+    const float3 id = f3(1.f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
+                         1.f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
+                         1.f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+    const float3 ood = f3(o.x * id.x, o.y * id.y, o.z * id.z);
     const float3 e = f3(ldexpf(fabsf(ood.x), -22), ldexpf(fabsf(ood.y), -22), ldexpf(fabsf(ood.z), -22));
     // id > 0: l is the entry plane (distance lowered: offset raised), h the exit
-    r.cl = f3(r.id.x > 0.f ? ood.x + e.x : ood.x - e.x, r.id.y > 0.f ? ood.y + e.y : ood.y - e.y,
-              r.id.z > 0.f ? ood.z + e.z : ood.z - e.z);
-    r.ch = f3(r.id.x > 0.f ? ood.x - e.x : ood.x + e.x, r.id.y > 0.f ? ood.y - e.y : ood.y + e.y,
-              r.id.z > 0.f ? ood.z - e.z : ood.z + e.z);
+    const float3 cl = f3(id.x > 0.f ? ood.x + e.x : ood.x - e.x, id.y > 0.f ? ood.y + e.y : ood.y - e.y,
+                         id.z > 0.f ? ood.z + e.z : ood.z - e.z);
+    const float3 ch = f3(id.x > 0.f ? ood.x - e.x : ood.x + e.x, id.y > 0.f ? ood.y - e.y : ood.y + e.y,
+                         id.z > 0.f ? ood.z - e.z : ood.z + e.z);
+    r.id2[0] = pk2(id.x, id.x);
+    r.id2[1] = pk2(id.y, id.y);
+    r.id2[2] = pk2(id.z, id.z);
+    r.off2[0] = pk2(-cl.x, -ch.x);
+    r.off2[1] = pk2(-cl.y, -ch.y);
+    r.off2[2] = pk2(-cl.z, -ch.z);
     return r;
 }
 
@@ -237,24 +265,28 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // which tmax may be), a box that holds a point of the ray at a distance
 // <= tmax is not culled: the closest hit, the minimum of (t, id) over the
 // triangles the ray hits, does not depend on the order boxes are visited.
+// Direction octant: bit k set when component k is negative (its sign bit,
+// which is the sign of 1/d as make_ray forms it, -0 included).
+__device__ __forceinline__ int ray_octant(const Ray& r) {
+    return (int)(__float_as_uint(r.d.x) >> 31) | (int)(__float_as_uint(r.d.y) >> 31) << 1 |
+           (int)(__float_as_uint(r.d.z) >> 31) << 2;
+}
+
+// The box is given by its (l, h) pair on each axis.
+__device__ __forceinline__ bool slab_hit(const Ray& r, f32x2 x, f32x2 y, f32x2 z, float tmax, float& tn) {
+    const float2 tx = fma_x2(x, r.id2[0], r.off2[0]);
+    const float2 ty = fma_x2(y, r.id2[1], r.off2[1]);
+    const float2 tz = fma_x2(z, r.id2[2], r.off2[2]);
+    tn = fmaxf(fmaxf(fminf(tx.x, tx.y), fminf(ty.x, ty.y)), fmaxf(fminf(tz.x, tz.y), 0.f));
+    const float tf = fminf(fminf(fmaxf(tx.x, tx.y), fmaxf(ty.x, ty.y)), fminf(fmaxf(tz.x, tz.y), tmax));
+    return tn <= tf * 1.0000019f;
+}
+// the same test of a box given by its corners, returning the entry distance
+// (or +inf on a miss)
 __device__ __forceinline__ float slab(const Ray& r, float lx, float hx, float ly, float hy, float lz,
                                       float hz, float tmax) {
-    float tx0 = fmaf(lx, r.id.x, -r.cl.x), tx1 = fmaf(hx, r.id.x, -r.ch.x);
-    float ty0 = fmaf(ly, r.id.y, -r.cl.y), ty1 = fmaf(hy, r.id.y, -r.ch.y);
-    float tz0 = fmaf(lz, r.id.z, -r.cl.z), tz1 = fmaf(hz, r.id.z, -r.ch.z);
-    float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
-    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    return tn <= tf * 1.0000019f ? tn : __int_as_float(0x7f800000);
-}
-// the same test returning the hit flag, with the entry distance in tn
-__device__ __forceinline__ bool slab_hit(const Ray& r, float lx, float hx, float ly, float hy, float lz, float hz,
-                                         float tmax, float& tn) {
-    float tx0 = fmaf(lx, r.id.x, -r.cl.x), tx1 = fmaf(hx, r.id.x, -r.ch.x);
-    float ty0 = fmaf(ly, r.id.y, -r.cl.y), ty1 = fmaf(hy, r.id.y, -r.ch.y);
-    float tz0 = fmaf(lz, r.id.z, -r.cl.z), tz1 = fmaf(hz, r.id.z, -r.ch.z);
-    tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
-    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    return tn <= tf * 1.0000019f;
+    float tn;
+    return slab_hit(r, pk2(lx, hx), pk2(ly, hy), pk2(lz, hz), tmax, tn) ? tn : __int_as_float(0x7f800000);
 }
 
 // Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013).  Edge
@@ -376,25 +408,54 @@ __device__ __forceinline__ void hit_tri(const BvhView& bvh, int slot, float3 o, 
 extern __device__ unsigned long long g_trav_stats[4];
 #endif
 
+// three-input minimum and maximum (one instruction each on sm_100 and later;
+// exact, like the nested two-input forms)
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Box test for rays of a known octant (OCT bit k set: direction component k
 // negative), so the entry and exit plane of each axis are known and need no
 // per-axis min/max; OCT < 0: any direction (slab_hit).  With the outward
 // offsets of make_ray an axis's entry distance never exceeds its exit
 // distance (rounding is monotone), so the decisions and tn equal slab_hit's.
 template <int OCT>
-__device__ __forceinline__ bool slab_hit_oct(const Ray& r, float lx, float hx, float ly, float hy, float lz,
-                                             float hz, float tmax, float& tn) {
-    if (OCT < 0) return slab_hit(r, lx, hx, ly, hy, lz, hz, tmax, tn);
+__device__ __forceinline__ bool slab_hit_oct(const Ray& r, f32x2 x, f32x2 y, f32x2 z, float tmax, float& tn) {
+    if (OCT < 0) return slab_hit(r, x, y, z, tmax, tn);
     const bool nx = OCT & 1, ny = OCT & 2, nz = OCT & 4;
-    const float ex = fmaf(nx ? hx : lx, r.id.x, -(nx ? r.ch.x : r.cl.x));
-    const float fx = fmaf(nx ? lx : hx, r.id.x, -(nx ? r.cl.x : r.ch.x));
-    const float ey = fmaf(ny ? hy : ly, r.id.y, -(ny ? r.ch.y : r.cl.y));
-    const float fy = fmaf(ny ? ly : hy, r.id.y, -(ny ? r.cl.y : r.ch.y));
-    const float ez = fmaf(nz ? hz : lz, r.id.z, -(nz ? r.ch.z : r.cl.z));
-    const float fz = fmaf(nz ? lz : hz, r.id.z, -(nz ? r.cl.z : r.ch.z));
-    tn = fmaxf(fmaxf(ex, ey), fmaxf(ez, 0.f));
-    const float tf = fminf(fminf(fx, fy), fminf(fz, tmax));
+    const float2 tx = fma_x2(x, r.id2[0], r.off2[0]);  // (l-plane, h-plane) distances
+    const float2 ty = fma_x2(y, r.id2[1], r.off2[1]);
+    const float2 tz = fma_x2(z, r.id2[2], r.off2[2]);
+    tn = max3f(nx ? tx.y : tx.x, ny ? ty.y : ty.x, fmaxf(nz ? tz.y : tz.x, 0.f));
+    const float tf = min3f(nx ? tx.x : tx.y, ny ? ty.x : ty.y, fminf(nz ? tz.x : tz.y, tmax));
     return tn <= tf * 1.0000019f;
+}
+
+// A node's two child boxes as (l, h) pairs per axis.
+struct NodeBoxes {
+    f32x2 x0, y0, z0, x1, y1, z1;
+    int4 ch;
+};
+__device__ __forceinline__ NodeBoxes load_node(const Node* n) {
+    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(&n->xy0));
+    const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(&n->xy1));
+    const ulonglong2 z = __ldg(reinterpret_cast<const ulonglong2*>(&n->z01));
+    NodeBoxes nb;
+    nb.x0 = a.x;
+    nb.y0 = a.y;
+    nb.x1 = b.x;
+    nb.y1 = b.y;
+    nb.z0 = z.x;
+    nb.z1 = z.y;
+    nb.ch = __ldg(&n->child);
+    return nb;
 }
 
 // Closest hit: smallest t, equal t -> lower original id.  Stack traversal
@@ -428,12 +489,11 @@ __device__ __forceinline__ Hit closest_hit_oct(const BvhView& bvh, float3 o, flo
 #if HDOF_TRAV_STATS
             ++nv;
 #endif
-            const Node* n = bvh.nodes + cur;
-            float4 a = __ldg(&n->xy0), b = __ldg(&n->xy1), z = __ldg(&n->z01);
-            int4 ch = __ldg(&n->child);
+            const NodeBoxes nb = load_node(bvh.nodes + cur);
+            const int4 ch = nb.ch;
             float t0, t1;
-            const bool h0 = slab_hit_oct<OCT>(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t, t0);
-            const bool h1 = slab_hit_oct<OCT>(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t, t1);
+            const bool h0 = slab_hit_oct<OCT>(r, nb.x0, nb.y0, nb.z0, h.t, t0);
+            const bool h1 = slab_hit_oct<OCT>(r, nb.x1, nb.y1, nb.z1, h.t, t1);
             if (h0 && h1) {
                 int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
                 if (sp < HDOF_STACK) stack[sp++] = farc;
@@ -527,12 +587,11 @@ __device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool ac
 #if HDOF_TRAV_STATS
             ++nv;
 #endif
-            const Node* n = bvh.nodes + cur;
-            const float4 a = __ldg(&n->xy0), b = __ldg(&n->xy1), z = __ldg(&n->z01);
-            const int4 ch = __ldg(&n->child);
+            const NodeBoxes nb = load_node(bvh.nodes + cur);
+            const int4 ch = nb.ch;
             float t0 = 0.f, t1 = 0.f;
-            const bool h0 = act && slab_hit_oct<OCT>(r, a.x, a.y, a.z, a.w, z.x, z.y, h.t, t0);
-            const bool h1 = act && slab_hit_oct<OCT>(r, b.x, b.y, b.z, b.w, z.z, z.w, h.t, t1);
+            const bool h0 = act && slab_hit_oct<OCT>(r, nb.x0, nb.y0, nb.z0, h.t, t0);
+            const bool h1 = act && slab_hit_oct<OCT>(r, nb.x1, nb.y1, nb.z1, h.t, t1);
             const unsigned b0 = __ballot_sync(FULL, h0), b1 = __ballot_sync(FULL, h1);
             if (b0 && b1) {
                 // first the child nearer for most of the lanes that enter both
@@ -585,7 +644,7 @@ __device__ __forceinline__ bool closest_hit_warp(const BvhView& bvh, bool act, c
                                                  const Shear& sh, Hit& h, int cap, unsigned* status,
                                                  int* __restrict__ stack) {
     const unsigned FULL = 0xffffffffu;
-    const int oct = (r.id.x < 0.f ? 1 : 0) | (r.id.y < 0.f ? 2 : 0) | (r.id.z < 0.f ? 4 : 0);
+    const int oct = ray_octant(r);
     const unsigned am = __ballot_sync(FULL, act);
     const int o0 = __shfl_sync(FULL, oct, am ? __ffs(am) - 1 : 0);
     const int u = __all_sync(FULL, !act || oct == o0) ? o0 : -1;

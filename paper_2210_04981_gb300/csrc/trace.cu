@@ -330,12 +330,11 @@ __device__ __forceinline__ void trace_rays_steps(const Src& src, RayLane& L, int
             const bool can_step = L.live && L.cur >= 0 && L.cur != DONE_REF && L.steps <= src.at(L.v).cap;
             if (can_step) {
                 const TraceArgs& a = src.at(L.v);
-                const Node* n = a.bvh.nodes + L.cur;
-                float4 na = __ldg(&n->xy0), nb = __ldg(&n->xy1), nz = __ldg(&n->z01);
-                int4 ch = __ldg(&n->child);
+                const NodeBoxes nb = load_node(a.bvh.nodes + L.cur);
+                const int4 ch = nb.ch;
                 float t0, t1;
-                const bool h0 = slab_hit_oct<OCT>(L.ray, na.x, na.y, na.z, na.w, nz.x, nz.y, L.h.t, t0);
-                const bool h1 = slab_hit_oct<OCT>(L.ray, nb.x, nb.y, nb.z, nb.w, nz.z, nz.w, L.h.t, t1);
+                const bool h0 = slab_hit_oct<OCT>(L.ray, nb.x0, nb.y0, nb.z0, L.h.t, t0);
+                const bool h1 = slab_hit_oct<OCT>(L.ray, nb.x1, nb.y1, nb.z1, L.h.t, t1);
                 if (h0 && h1) {
                     int nearc = t0 <= t1 ? ch.x : ch.y, farc = t0 <= t1 ? ch.y : ch.x;
                     if (L.sp < HDOF_STACK) stack[L.sp++] = farc;
@@ -470,7 +469,7 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
         const unsigned lm = __ballot_sync(FULL, L.live);
         if (!lm) break;
         // the live lanes' common direction octant, if they share one
-        const int oct = (L.ray.id.x < 0.f ? 1 : 0) | (L.ray.id.y < 0.f ? 2 : 0) | (L.ray.id.z < 0.f ? 4 : 0);
+        const int oct = ray_octant(L.ray);
         const int o0 = __shfl_sync(FULL, oct, __ffs(lm) - 1);
         const int u = __all_sync(FULL, !L.live || oct == o0) ? o0 : -1;
         switch (u) {
