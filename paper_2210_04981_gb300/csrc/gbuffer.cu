@@ -24,21 +24,37 @@ struct GbufArgs {
 };
 
 // 16x8-pixel blocks; warp w covers the 8x4 sub-block ((w & 1) * 8, (w >> 1) * 4)
+// and traces its 32 primary rays as one packet (they are coherent: one node
+// fetch serves the warp).  stack: the warp's traversal stack.
 template <class ND, class COL>
-__device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx, int by) {
+__device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx, int by, int* __restrict__ stack) {
+    const float INF = __int_as_float(0x7f800000);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int i = bx * 16 + (w & 1) * 8 + (l & 7), j = by * 8 + (w >> 1) * 4 + (l >> 3);
     const Cam& cam = a.cam;
-    if (i >= cam.W || j >= cam.H) return;
-    size_t q = (size_t)j * cam.W + i;
+    const bool act = i < cam.W && j < cam.H;
+    const size_t q = act ? (size_t)j * cam.W + i : 0;
     float3 d = pinhole_dir(cam, i + 0.5f + cam.jx, j + 0.5f + cam.jy);
     float3 dn = normalize(d);
-    int hint_slot = -1;
-    if (a.hint) {
+    const Ray ray = make_ray(cam.pos, dn);
+    const Shear sh = make_shear(dn);
+    Hit h;
+    h.t = INF;
+    h.slot = -1;
+    h.id = 0x7fffffff;
+    h.b0 = h.b1 = h.b2 = 0.f;
+    if (act && a.hint) {  // the previous frame's primary hit bounds the search
         const int id = a.hint[q];
-        if (id >= 0 && id < a.bvh.n_tris) hint_slot = __ldg(&a.bvh.slot_of[id]);
+        if (id >= 0 && id < a.bvh.n_tris) hit_tri(a.bvh, __ldg(&a.bvh.slot_of[id]), cam.pos, sh, h);
     }
-    Hit h = closest_hit(a.bvh, cam.pos, dn, a.cap, a.status, hint_slot);
+    closest_hit_warp(a.bvh, act, ray, cam.pos, sh, h, a.cap, a.status, stack);
+    if (!act) return;
+    for (int k = 0; k < a.bvh.big_count; ++k) {
+        const float4 lo = __ldg(&a.bvh.big_box[2 * k]), hi = __ldg(&a.bvh.big_box[2 * k + 1]);
+        if (slab(ray, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, h.t) < INF)
+            hit_tri(a.bvh, a.bvh.big_first + k, cam.pos, sh, h);
+    }
+    if (h.slot < 0) h.id = -1;
     float3 n, rad, P;
     float z, spec = 0.f;
     if (h.slot >= 0) {
@@ -63,13 +79,15 @@ __device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx,
 
 template <class ND, class COL>
 __global__ void __launch_bounds__(128) k_gbuffer(GbufArgs<ND, COL> a) {
-    gbuffer_body(a, blockIdx.x, blockIdx.y);
+    __shared__ int s_stack[4][HDOF_STACK];
+    gbuffer_body(a, blockIdx.x, blockIdx.y, s_stack[threadIdx.x >> 5]);
 }
 
 __global__ void __launch_bounds__(128) k_gbuffer_batch(const GbufArgs<float4, float4>* __restrict__ a, BatchGrid g) {
     int v, bx, by;
+    __shared__ int s_stack[4][HDOF_STACK];
     g.locate(blockIdx.x, v, bx, by);
-    gbuffer_body(batch_record(a, v), bx, by);
+    gbuffer_body(batch_record(a, v), bx, by, s_stack[threadIdx.x >> 5]);
 }
 
 template <class ND, class COL>
