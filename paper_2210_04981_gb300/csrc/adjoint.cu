@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(256) k_spatial_bwd(const float4* __restrict__ 
             const float4 cy = __ldg(&crt[qq]), by = __ldg(&spb[qq]);
             const bool ty = cy.w >= 0.f;
             float d = sqrt_approx(fmaf(dx, dx, dy2));
-            float ux = rx - d + 0.5f, uy = fminf(cy.w * 0.5f, r_s) - d + 0.5f;
+            float ux = R - d, uy = fminf(fmaf(cy.w, 0.5f, 0.5f), r_s + 0.5f) - d;
             float sx = clamp01(ux), sy = ty ? clamp01(uy) : 0.f;
             float spx = (ux > 0.f && ux < 1.f) ? 1.f : 0.f;
             const float3 ay = ty ? ldf3(by) : f3(0.f, 0.f, 0.f);

@@ -42,8 +42,6 @@ __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 
 __device__ __forceinline__ float luminance(float3 c) { return 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z; }
 __device__ __forceinline__ float3 ld3(const float* p) { return f3(p[0], p[1], p[2]); }
 
-// soft step of the gather kernels: s(x) = clamp(x + 1/2, 0, 1)
-__device__ __forceinline__ float soft_step(float x) { return clamp01(x + 0.5f); }
 
 // --------------------------------------------------------------- camera --
 struct Cam {

@@ -232,6 +232,9 @@ __device__ __forceinline__ void spatial_pixel(const SpatialArgs& a, int i, int j
     // disk (the bounds lean outwards by 1e-3 pixel; the taps they add weigh 0)
     const float R = rp + 0.5f, R2 = R * R;
     const int K = (int)floorf(R + 1e-3f);
+    // s(r - d) = clamp(r + 1/2 - d, 0, 1): the half folded into the radii
+    // (R here; for the neighbour min(c/2 + 1/2, r_s + 1/2))
+    const float Rq = r_s + 0.5f;
     float3 S = f3(0, 0, 0);
     float Ws = 0.f;
     const int y0 = max(j - K, 0), y1 = min(j + K, H - 1);
@@ -247,7 +250,7 @@ __device__ __forceinline__ void spatial_pixel(const SpatialArgs& a, int i, int j
             const float d = sqrt_approx(fmaf(dx, dx, dy2));
             // an untraced neighbour (written as (0, 0, 0, -1)) weighs
             // clamp(-d, 0, 1) = 0 times colour 0: it adds nothing
-            const float wq = soft_step(rp - d) * soft_step(fminf(c.w * 0.5f, r_s) - d);
+            const float wq = clamp01(R - d) * clamp01(fminf(fmaf(c.w, 0.5f, 0.5f), Rq) - d);
             S.x = fmaf(wq, c.x, S.x);
             S.y = fmaf(wq, c.y, S.y);
             S.z = fmaf(wq, c.z, S.z);
