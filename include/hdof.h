@@ -201,7 +201,9 @@ int hdof_probe_fma(int32_t blocks_per_sm, int32_t iters, float* sink, double* la
  * the GPU by parallel locally-ordered clustering (Meister and Bittner 2018):
  * 63-bit Morton codes of the triangle centroids, radix sort, then rounds
  * that merge mutual nearest neighbours (smallest union-box surface area
- * within 48 positions) until one cluster remains.  One triangle per leaf.
+ * within 48 positions) until one cluster remains; the triangles are then
+ * stored in depth-first leaf order and subtrees of at most two triangles
+ * become leaves.
  * verts: float [n_verts][3]; idx: int32 [n_tris][3];
  * mat: float [n_tris][8] = (albedo_a rgb, checker_n, albedo_b rgb, k_s):
  * Lambert diffuse of the albedo, plus for k_s > 0 a white Blinn-Phong

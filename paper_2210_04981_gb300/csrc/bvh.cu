@@ -496,14 +496,92 @@ __global__ void k_dfs_index(const Node* __restrict__ nodes, int n, int root, con
 }
 
 __global__ void k_dfs_permute(const Node* __restrict__ nodes, int n, const int* __restrict__ parent,
-                              const int* __restrict__ index, int root, Node* out) {
+                              const int* __restrict__ index, const int* __restrict__ size, int root, Node* out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     Node nd = nodes[i];
     if (nd.child.x >= 0) nd.child.x = index[nd.child.x];
     if (nd.child.y >= 0) nd.child.y = index[nd.child.y];
     nd.child.z = i == root ? -1 : index[parent[i]];
+    nd.child.w = size[i];  // internal nodes of the subtree (kept for the leaf collapse)
     out[index[i]] = nd;
+}
+
+// Leaf collapse of the clustered tree (in pre-order: node 0 the root,
+// child.z the parent, child.w the subtree's internal node count; every leaf
+// one triangle).  The triangles are moved to depth-first leaf order, so the
+// triangles of any subtree occupy consecutive slots, and each subtree of at
+// most leaf_max triangles becomes one leaf over them: fewer traversal steps
+// for one more triangle test per extra triangle.  The tree's boxes and the
+// closest hits are unchanged.
+__device__ __forceinline__ int n_leaves(const Node* __restrict__ nodes, int ref) {
+    return ref >= 0 ? __ldg(&nodes[ref].child.w) + 1 : 1;
+}
+
+// first leaf position of each node's subtree: the leaves of every first-child
+// subtree that the path from the root passes on its left
+__global__ void k_leaf_first(const Node* __restrict__ nodes, int n, int* first) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int idx = 0, c = i;
+    for (int guard = 0; c != 0 && guard < n; ++guard) {  // a walk is at most the tree's depth
+        const int p = __ldg(&nodes[c].child.z);
+        const int4 ch = __ldg(&nodes[p].child);
+        if (c == ch.y) idx += n_leaves(nodes, ch.x);
+        c = p;
+    }
+    first[i] = idx;
+}
+
+// new slot of each tree triangle: its depth-first leaf position
+__global__ void k_leaf_slots(const Node* __restrict__ nodes, int n, int m, const int* __restrict__ first,
+                             int* newpos) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 ch = __ldg(&nodes[i].child);
+    const int f = first[i];
+    if (ch.x < 0 && ((~ch.x) >> 3) < m) newpos[(~ch.x) >> 3] = f;
+    if (ch.y < 0 && ((~ch.y) >> 3) < m) newpos[(~ch.y) >> 3] = f + n_leaves(nodes, ch.x);
+}
+
+// triangles, materials and texture coordinates to their new slots
+__global__ void k_tri_permute(const int* __restrict__ newpos, int m, const Tri* __restrict__ tin,
+                              const float4* __restrict__ min, const float2* __restrict__ uin, Tri* tout,
+                              float4* mout, float2* uout, int* slot_of) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int d = newpos[k];
+    if (d < 0 || d >= m) return;  // unreachable for a full binary tree over the m slots
+    const Tri t = tin[k];
+    tout[d] = t;
+    mout[2 * d] = min[2 * k];
+    mout[2 * d + 1] = min[2 * k + 1];
+    uout[3 * d] = uin[3 * k];
+    uout[3 * d + 1] = uin[3 * k + 1];
+    uout[3 * d + 2] = uin[3 * k + 2];
+    slot_of[__float_as_int(t.v0.w)] = d;
+}
+
+// leaf references to the new slots; subtrees of at most leaf_max triangles
+// become leaves (only child.x and child.y are written; child.w is read)
+__global__ void k_leaf_collapse(Node* nodes, int n, const int* __restrict__ first, int leaf_max) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int cx = nodes[i].child.x, cy = nodes[i].child.y;
+    const int c[2] = {cx, cy};
+    const int start[2] = {first[i], first[i] + (cx >= 0 ? nodes[cx].child.w + 1 : 1)};
+    int out[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (c[k] < 0) {
+            out[k] = leaf_ref(start[k], 1);
+        } else {
+            const int cnt = nodes[c[k]].child.w + 1;
+            out[k] = cnt <= leaf_max ? leaf_ref(start[k], cnt) : c[k];
+        }
+    }
+    nodes[i].child.x = out[0];
+    nodes[i].child.y = out[1];
 }
 
 }  // namespace
@@ -513,6 +591,43 @@ using namespace hdof;
 
 namespace {
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+#ifndef HDOF_PLOC_LEAF_MAX
+#define HDOF_PLOC_LEAF_MAX 2  // largest collapsed leaf of the clustered tree (<= 8; 1: no collapse); 2 measured fastest
+#endif
+
+// Leaf collapse of the relabelled clustered tree (ni internal nodes over the
+// first m triangle slots): see k_leaf_first .. k_leaf_collapse.
+cudaError_t collapse_leaves(hdof_bvh* b, int ni, int m, int leaf_max, cudaStream_t s) {
+    const size_t q1 = up256(4 * (size_t)ni), q2 = q1 + up256(4 * (size_t)m);
+    const size_t q3 = q2 + up256(sizeof(Tri) * (size_t)m), q4 = q3 + up256(2 * sizeof(float4) * (size_t)m);
+    const size_t tot = q4 + 3 * sizeof(float2) * (size_t)m;
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, tot);
+    if (e != cudaSuccess) return e;
+    char* c8 = static_cast<char*>(mem);
+    int* first = reinterpret_cast<int*>(c8);
+    int* newpos = reinterpret_cast<int*>(c8 + q1);
+    Tri* tcopy = reinterpret_cast<Tri*>(c8 + q2);
+    float4* mcopy = reinterpret_cast<float4*>(c8 + q3);
+    float2* ucopy = reinterpret_cast<float2*>(c8 + q4);
+    if ((e = cudaMemsetAsync(newpos, 0xff, 4 * (size_t)m, s)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(tcopy, b->tris, sizeof(Tri) * (size_t)m, cudaMemcpyDeviceToDevice, s)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(mcopy, b->mat, 2 * sizeof(float4) * (size_t)m, cudaMemcpyDeviceToDevice, s)) ==
+            cudaSuccess &&
+        (e = cudaMemcpyAsync(ucopy, b->uv, 3 * sizeof(float2) * (size_t)m, cudaMemcpyDeviceToDevice, s)) ==
+            cudaSuccess) {
+        k_leaf_first<<<blocks_for(ni, 256), 256, 0, s>>>(b->nodes, ni, first);
+        k_leaf_slots<<<blocks_for(ni, 256), 256, 0, s>>>(b->nodes, ni, m, first, newpos);
+        k_tri_permute<<<blocks_for(m, 256), 256, 0, s>>>(newpos, m, tcopy, mcopy, ucopy, b->tris, b->mat, b->uv,
+                                                         b->slot_of);
+        k_leaf_collapse<<<blocks_for(ni, 256), 256, 0, s>>>(b->nodes, ni, first, leaf_max);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(mem);
+    return e != cudaSuccess ? e : e2;
+}
 }  // namespace
 
 extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t* idx, int32_t n_tris,
@@ -743,7 +858,7 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
                 k_dfs_parent<<<nb, 256, 0, s>>>(b->nodes, ni, parent, nint);
                 k_dfs_size<<<nb, 256, 0, s>>>(b->nodes, ni, root_ref, parent, nint, arrived, size);
                 k_dfs_index<<<nb, 256, 0, s>>>(b->nodes, ni, root_ref, parent, size, index);
-                k_dfs_permute<<<nb, 256, 0, s>>>(b->nodes, ni, parent, index, root_ref, copy);
+                k_dfs_permute<<<nb, 256, 0, s>>>(b->nodes, ni, parent, index, size, root_ref, copy);
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess)
@@ -752,6 +867,8 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
             cudaFree(rt);
             if (e != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: relabel"));
             b->root = 0;
+            if (HDOF_PLOC_LEAF_MAX > 1 && (e = collapse_leaves(b, ni, m, HDOF_PLOC_LEAF_MAX, s)) != cudaSuccess)
+                return fail(cuda_fail(e, "hdof_build_bvh: leaf collapse"));
         }
     }
     b->depth = depth;

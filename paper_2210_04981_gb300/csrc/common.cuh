@@ -17,7 +17,7 @@
 #define HDOF_MV_OFFSCREEN 1e6f  // motion written when the previous camera cannot see a point
 #define HDOF_STACK 64           // traversal stack entries (> tree depth)
 #ifndef HDOF_LEAF_MAX
-#define HDOF_LEAF_MAX 1         // triangles per leaf (<= 8); single-triangle leaves measured fastest
+#define HDOF_LEAF_MAX 1         // triangles per leaf of the LBVH builder (<= 8)
 #endif
 #ifndef HDOF_BIG_MAX
 #define HDOF_BIG_MAX 0          // scene-sized triangles kept out of the tree (0: all in the tree)
