@@ -39,11 +39,13 @@ FALLBACK_HBM = 6800.0
 # The ALU-bound kernels are measured in FP32 lane-operations: one FP32
 # instruction executed by one lane (a fused multiply-add counts once), against
 # the measured FFMA lane-instruction rate of the FMA probe (hdof_probe_fma).
-# Traversal: two octant box tests per visited node, 14 FP32 instructions each
-# (6 FFMA plane distances, 6 FMNMX entry/exit, 1 FMUL exit widening, 1 FSETP),
-# and ~40 per watertight ray-triangle test, at the visit and test counts the
-# counting build (-DHDOF_TRAV_STATS=1) measured on the 1080p room's thin-lens
-# rays (per-ray traversal: the intrinsic work; warp packets execute more).
+# Traversal: two octant box tests per visited node, 14 FP32 operations each
+# (6 plane-distance FMAs, 6 min/max for entry and exit, 1 multiply widening the
+# exit, 1 compare; the kernel issues them as 3 packed f32x2 FMAs, 4 min/max
+# with three inputs, 1 multiply and 1 compare), and ~40 per watertight
+# ray-triangle test, at the visit and test counts the counting build
+# (-DHDOF_TRAV_STATS=1) measured on the 1080p room's thin-lens rays (per-ray
+# traversal: the intrinsic work; warp packets execute more).
 TRACE_VISITS_PER_RAY = 63.9
 TRACE_TESTS_PER_RAY = 6.3
 TRACE_OPS_PER_RAY = 28 * TRACE_VISITS_PER_RAY + 40 * TRACE_TESTS_PER_RAY
@@ -57,7 +59,10 @@ PF_OPS_PER_LOOKUP = 8
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
 # launch-list capture of the 1080p room frame, caches flushed before each launch)
 # of the current kernels; None where the kernel changed since the capture
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("room", "f32", "trace_packets"): 18548992,
+    ("room", "f32", "pf_gather"): 121877248,
+}
 
 
 def peaks():
@@ -320,14 +325,18 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
     wall = time.perf_counter() - wall0
     kern = {}
     if profile:
-        # the next K frames again with the library's per-kernel events (they
-        # add ~0.05 ms per frame, so the stage times above are taken without)
+        # the same K frames again (history reset, warm-up repeated) with the
+        # library's per-kernel events (they add ~0.05 ms per frame, so the
+        # stage times above are taken without)
+        r.reset_history()
+        for k in range(warmup):
+            frame(k)
         H.hdof_sync()
         H.hdof_profile_read()  # drop anything recorded before
         H.hdof_profile(True)
         for s in range(K):
             flush.zero_()
-            frame(warmup + K + s)
+            frame(warmup + s)
         torch.cuda.synchronize()
         H.hdof_profile(False)
         kern = {n: t / K for n, (_, t) in H.hdof_profile_read().items()}
@@ -338,30 +347,50 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
 
 
 def e2e_frames(H, r, Hh, W, warmup, K, flush):
-    """The same frames end to end: host camera/lens/params records into the C
-    calls, the RGBA32F image copied to pinned host memory inside the timed
-    region; returns mean ms per frame and the bytes moved."""
+    """The same frames end to end, run as a renderer would: host camera, lens
+    and params records into the C calls every frame, and every frame's
+    RGBA32F image read back to pinned host memory on a copy stream while the
+    next frame renders (two device output buffers and two host buffers; a
+    buffer is reused only after its previous copy finished).  One timed
+    region over the K frames, from before the first frame's first call to
+    the last image on the host; no L2 flush inside it (each frame streams
+    several hundred MB of planes, far more than the 129 MB L2).  Returns ms
+    per frame and the bytes moved per frame."""
     import ctypes
 
     import torch
     stream = torch.cuda.current_stream()
-    host_img = torch.empty((Hh, W, 4), dtype=torch.float32, pin_memory=True)
+    copy_stream = torch.cuda.Stream()
+    outs = [r.out, torch.empty_like(r.out)]
+    hosts = [torch.empty((Hh, W, 4), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     r.reset_history()
     for k in range(warmup):
         r.frame_fn(k)
     torch.cuda.synchronize()
-    e_ms = 0.0
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
     for s in range(K):
-        flush.zero_()
-        e0.record(stream)
+        b = s & 1
+        if s >= 2:
+            stream.wait_event(copied[b])  # frame s - 2's image has left this buffer
+        r.out = outs[b]
         r.frame_fn(warmup + s)
-        host_img.copy_(r.out, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e_ms += e0.elapsed_time(e1)
+        rendered[b].record(stream)
+        copy_stream.wait_event(rendered[b])
+        with torch.cuda.stream(copy_stream):
+            hosts[b].copy_(outs[b], non_blocking=True)
+        copied[b].record(copy_stream)
+    stream.wait_event(copied[(K - 1) & 1])
+    e1.record(stream)
+    e1.synchronize()
+    r.out = outs[0]
+    e_ms = e0.elapsed_time(e1)
     rec_bytes = ctypes.sizeof(H.hdof_camera) * 2 + ctypes.sizeof(H.hdof_lens) + ctypes.sizeof(H.hdof_params)
-    return e_ms / max(K, 1), int(rec_bytes), int(host_img.numel() * 4)
+    return e_ms / max(K, 1), int(rec_bytes), int(hosts[0].numel() * 4)
 
 
 def kernel_roofline(name, kms, rays, z, lens, Hh, t, r_max, lane_peak, clock_mhz, hbm, traffic_key):
@@ -575,7 +604,7 @@ def run_ours(args):
         gbs = ab[stg] / (mean_stage[STAGES.index(stg)] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 3),
                 "traffic": MEASURED_TRAFFIC.get((args.scene, storage, dom)), "kernel": dom, "peak_source": peak_src}
-    last = args.warmup + 2 * K - 1
+    last = args.warmup + K - 1  # the last frame the renderer drew
     qual = quality(H, bvh, r, cams[last], lens, p0.replace(frame=last % 65536, camera_moved=1), args.rt_passes)
     if not args.no_compare and ws == 1:
         qual["variants_after_8_frames"] = quality_variants(H, bvh, W, Hh, lens, p0, dev, flush, 8, args.rt_passes)
@@ -584,7 +613,9 @@ def run_ours(args):
     if not args.no_e2e:
         e_ms, h2d, d2h = e2e_frames(H, r, Hh, W, args.warmup, K, flush)
         e2e = {"value": round(e_ms, 4), "unit": "ms/frame", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "note": "h2d = camera/lens/params records passed by value to the C calls; d2h = RGBA32F image"}
+               "note": "h2d = camera/lens/params records passed by value to the C calls; d2h = RGBA32F image of "
+                       "every frame, read back on a copy stream while the next frame renders (double-buffered); "
+                       "one timed region over the frames, no L2 flush (the planes exceed L2)"}
     del r
     value = total_ms / (K * ws)
     out = {
