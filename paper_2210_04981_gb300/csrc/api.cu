@@ -7,8 +7,9 @@
 
 namespace hdof {
 
-// device status word: kernels OR in HDOF_STATUS_* bits, hdof_sync reads and clears it
-__device__ unsigned int g_status = 0;
+// device status word: kernels OR in HDOF_STATUS_* bits, hdof_sync reads and clears it;
+// words 2..7 hold the traversal counters of analysis builds (HDOF_TRAV_STATS)
+__device__ __align__(8) unsigned int g_status[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
 unsigned* status_ptr() {
     static unsigned* cached[64] = {nullptr};
@@ -145,9 +146,6 @@ WsLayout ws_layout(int W, int H, const hdof_params* p) {
     return l;
 }
 
-#if HDOF_TRAV_STATS
-__device__ unsigned long long g_trav_stats[4];
-#endif
 
 }  // namespace hdof
 
@@ -156,10 +154,11 @@ using namespace hdof;
 #if HDOF_TRAV_STATS
 // analysis builds only: read and clear (rays, node visits, triangle tests)
 extern "C" int hdof_debug_trav_stats(unsigned long long* out) {
-    unsigned long long z[4] = {0, 0, 0, 0};
+    unsigned long long z[3] = {0, 0, 0};
     cudaDeviceSynchronize();
-    cudaMemcpyFromSymbol(out, g_trav_stats, sizeof z);
-    cudaMemcpyToSymbol(g_trav_stats, z, sizeof z);
+    out[3] = 0;
+    cudaMemcpyFromSymbol(out, g_status, sizeof z, 8);
+    cudaMemcpyToSymbol(g_status, z, sizeof z, 8);
     return 0;
 }
 #endif

@@ -403,7 +403,11 @@ __device__ __forceinline__ void hit_tri(const BvhView& bvh, int slot, float3 o, 
 #define HDOF_TRAV_STATS 0  // count node visits and triangle tests (analysis builds only)
 #endif
 #if HDOF_TRAV_STATS
-extern __device__ unsigned long long g_trav_stats[4];
+// the counters (rays, node visits, triangle tests) sit in the status block
+// after the status word, whose address every traversal already has
+__device__ __forceinline__ void trav_stat(unsigned* status, int k, unsigned long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(status + 2) + k, v);
+}
 #endif
 
 // three-input minimum and maximum (one instruction each on sm_100 and later;
@@ -524,9 +528,9 @@ __device__ __forceinline__ Hit closest_hit_oct(const BvhView& bvh, float3 o, flo
         if (slab(r, lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, h.t) < INF) hit_tri(bvh, bvh.big_first + k, o, sh, h);
     }
 #if HDOF_TRAV_STATS
-    atomicAdd(&g_trav_stats[0], 1ull);
-    atomicAdd(&g_trav_stats[1], (unsigned long long)nv);
-    atomicAdd(&g_trav_stats[2], (unsigned long long)nt);
+    trav_stat(status, 0, 1ull);
+    trav_stat(status, 1, nv);
+    trav_stat(status, 2, nt);
 #endif
     if (h.slot < 0) h.id = -1;
     return h;
@@ -628,10 +632,10 @@ __device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool ac
     }
 #if HDOF_TRAV_STATS
     if (lane == 0) {
-        atomicAdd(&g_trav_stats[1], (unsigned long long)nv);
-        atomicAdd(&g_trav_stats[2], (unsigned long long)nt);
+        trav_stat(status, 1, nv);
+        trav_stat(status, 2, nt);
     }
-    if (act) atomicAdd(&g_trav_stats[0], 1ull);
+    if (act) trav_stat(status, 0, 1ull);
 #endif
     return true;
 }
