@@ -621,13 +621,14 @@ __device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool ac
 #endif
         }
         if (pop) {
+            // the cap counts pops: between two, a descent is at most the tree's depth
+            if (++steps > cap) {
+                if (lane == 0) atomicOr(status, HDOF_STATUS_TIMEOUT);
+                return false;
+            }
             if (sp == 0) break;
             __syncwarp();
             cur = stack[--sp];
-        }
-        if (++steps > cap) {
-            if (lane == 0) atomicOr(status, HDOF_STATUS_TIMEOUT);
-            return false;
         }
     }
 #if HDOF_TRAV_STATS
