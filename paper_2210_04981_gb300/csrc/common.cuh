@@ -561,8 +561,9 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
 }
 
 // Warp-wide closest hits: all 32 lanes call this together; the active lanes'
-// rays share one traversal (node references and the stack are warp-uniform,
-// the stack lives in the caller's shared memory, one per warp).  A node is
+// rays share one traversal (node references and the stack are warp-uniform;
+// the stack lives in registers, entry k in lane k mod 32, pushed by one lane's
+// move and popped by a shuffle, with no shared memory or warp barrier).  A node is
 // entered when any active lane's ray enters one of its children before that
 // lane's own closest hit so far; each lane tests the triangles of every leaf
 // the warp reaches.  A lane's own closest hit lies in a leaf whose every
@@ -575,11 +576,13 @@ __device__ __forceinline__ Hit closest_hit(const BvhView& bvh, float3 o, float3 
 // when the step cap was reached (the warp stops; status is flagged).
 template <int OCT>
 __device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool act, const Ray& r, float3 o,
-                                                     const Shear& sh, Hit& h, int cap, unsigned* status,
-                                                     int* __restrict__ stack) {
+                                                     const Shear& sh, Hit& h, int cap, unsigned* status) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     int cur = bvh.root, sp = 0, steps = 0;
+    // the warp's stack in registers: entry k in lane k & 31 of slo (k < 32) or shi
+    static_assert(HDOF_STACK <= 64, "the register stack holds 64 entries");
+    int slo = 0, shi = 0;
 #if HDOF_TRAV_STATS
     unsigned nv = 0, nt = 0;
 #endif
@@ -600,8 +603,12 @@ __device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool ac
                 // (or entered by more lanes): only the culling depends on it
                 const unsigned both = b0 & b1, nx = __ballot_sync(FULL, h0 && h1 && t0 <= t1);
                 const bool x_first = both ? 2 * __popc(nx) >= __popc(both) : __popc(b0) >= __popc(b1);
-                if (sp < HDOF_STACK) {
-                    if (lane == 0) stack[sp] = x_first ? ch.y : ch.x;
+                const int far = x_first ? ch.y : ch.x;
+                if (sp < 32) {
+                    if (lane == sp) slo = far;
+                    ++sp;
+                } else if (sp < HDOF_STACK) {
+                    if (lane == sp - 32) shi = far;
                     ++sp;
                 } else if (lane == 0) {
                     atomicOr(status, HDOF_STATUS_TIMEOUT);
@@ -627,8 +634,8 @@ __device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool ac
                 return false;
             }
             if (sp == 0) break;
-            __syncwarp();
-            cur = stack[--sp];
+            --sp;
+            cur = __shfl_sync(FULL, sp < 32 ? slo : shi, sp & 31);
         }
     }
 #if HDOF_TRAV_STATS
@@ -644,23 +651,22 @@ __device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool ac
 // the traversal specialised to the packet's octant when all its active rays
 // share one (the usual case for coherent rays), the general one otherwise
 __device__ __forceinline__ bool closest_hit_warp(const BvhView& bvh, bool act, const Ray& r, float3 o,
-                                                 const Shear& sh, Hit& h, int cap, unsigned* status,
-                                                 int* __restrict__ stack) {
+                                                 const Shear& sh, Hit& h, int cap, unsigned* status) {
     const unsigned FULL = 0xffffffffu;
     const int oct = ray_octant(r);
     const unsigned am = __ballot_sync(FULL, act);
     const int o0 = __shfl_sync(FULL, oct, am ? __ffs(am) - 1 : 0);
     const int u = __all_sync(FULL, !act || oct == o0) ? o0 : -1;
     switch (u) {
-        case 0: return closest_hit_warp_oct<0>(bvh, act, r, o, sh, h, cap, status, stack);
-        case 1: return closest_hit_warp_oct<1>(bvh, act, r, o, sh, h, cap, status, stack);
-        case 2: return closest_hit_warp_oct<2>(bvh, act, r, o, sh, h, cap, status, stack);
-        case 3: return closest_hit_warp_oct<3>(bvh, act, r, o, sh, h, cap, status, stack);
-        case 4: return closest_hit_warp_oct<4>(bvh, act, r, o, sh, h, cap, status, stack);
-        case 5: return closest_hit_warp_oct<5>(bvh, act, r, o, sh, h, cap, status, stack);
-        case 6: return closest_hit_warp_oct<6>(bvh, act, r, o, sh, h, cap, status, stack);
-        case 7: return closest_hit_warp_oct<7>(bvh, act, r, o, sh, h, cap, status, stack);
-        default: return closest_hit_warp_oct<-1>(bvh, act, r, o, sh, h, cap, status, stack);
+        case 0: return closest_hit_warp_oct<0>(bvh, act, r, o, sh, h, cap, status);
+        case 1: return closest_hit_warp_oct<1>(bvh, act, r, o, sh, h, cap, status);
+        case 2: return closest_hit_warp_oct<2>(bvh, act, r, o, sh, h, cap, status);
+        case 3: return closest_hit_warp_oct<3>(bvh, act, r, o, sh, h, cap, status);
+        case 4: return closest_hit_warp_oct<4>(bvh, act, r, o, sh, h, cap, status);
+        case 5: return closest_hit_warp_oct<5>(bvh, act, r, o, sh, h, cap, status);
+        case 6: return closest_hit_warp_oct<6>(bvh, act, r, o, sh, h, cap, status);
+        case 7: return closest_hit_warp_oct<7>(bvh, act, r, o, sh, h, cap, status);
+        default: return closest_hit_warp_oct<-1>(bvh, act, r, o, sh, h, cap, status);
     }
 }
 

@@ -27,7 +27,7 @@ struct GbufArgs {
 // and traces its 32 primary rays as one packet (they are coherent: one node
 // fetch serves the warp).  stack: the warp's traversal stack.
 template <class ND, class COL>
-__device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx, int by, int* __restrict__ stack) {
+__device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx, int by) {
     const float INF = __int_as_float(0x7f800000);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int i = bx * 16 + (w & 1) * 8 + (l & 7), j = by * 8 + (w >> 1) * 4 + (l >> 3);
@@ -47,7 +47,7 @@ __device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx,
         const int id = a.hint[q];
         if (id >= 0 && id < a.bvh.n_tris) hit_tri(a.bvh, __ldg(&a.bvh.slot_of[id]), cam.pos, sh, h);
     }
-    closest_hit_warp(a.bvh, act, ray, cam.pos, sh, h, a.cap, a.status, stack);
+    closest_hit_warp(a.bvh, act, ray, cam.pos, sh, h, a.cap, a.status);
     if (!act) return;
     for (int k = 0; k < a.bvh.big_count; ++k) {
         const float4 lo = __ldg(&a.bvh.big_box[2 * k]), hi = __ldg(&a.bvh.big_box[2 * k + 1]);
@@ -79,15 +79,13 @@ __device__ __forceinline__ void gbuffer_body(const GbufArgs<ND, COL>& a, int bx,
 
 template <class ND, class COL>
 __global__ void __launch_bounds__(128) k_gbuffer(GbufArgs<ND, COL> a) {
-    __shared__ int s_stack[4][HDOF_STACK];
-    gbuffer_body(a, blockIdx.x, blockIdx.y, s_stack[threadIdx.x >> 5]);
+    gbuffer_body(a, blockIdx.x, blockIdx.y);
 }
 
 __global__ void __launch_bounds__(128) k_gbuffer_batch(const GbufArgs<float4, float4>* __restrict__ a, BatchGrid g) {
     int v, bx, by;
-    __shared__ int s_stack[4][HDOF_STACK];
     g.locate(blockIdx.x, v, bx, by);
-    gbuffer_body(batch_record(a, v), bx, by, s_stack[threadIdx.x >> 5]);
+    gbuffer_body(batch_record(a, v), bx, by);
 }
 
 template <class ND, class COL>

@@ -492,7 +492,7 @@ __device__ __forceinline__ void trace_rays_body(const Src& src, unsigned total, 
 // (closest_hit_warp); in a batched list the rays of one view go together.
 // Same records as the ray-level form.
 template <class Src>
-__device__ __forceinline__ void trace_packets_body(const Src& src, unsigned total, unsigned* head, int* stack,
+__device__ __forceinline__ void trace_packets_body(const Src& src, unsigned total, unsigned* head,
                                                    int chunk) {
     const unsigned FULL = 0xffffffffu;
     const float INF = __int_as_float(0x7f800000);
@@ -538,7 +538,7 @@ __device__ __forceinline__ void trace_packets_body(const Src& src, unsigned tota
             }
             ray = make_ray(O, dir);
             sh = make_shear(dir);
-            closest_hit_warp(a.bvh, act, ray, O, sh, h, a.cap, a.status, stack);
+            closest_hit_warp(a.bvh, act, ray, O, sh, h, a.cap, a.status);
             if (act) {
                 const BvhView& bvh = a.bvh;
                 for (int k = 0; k < bvh.big_count; ++k) {
@@ -555,16 +555,14 @@ __device__ __forceinline__ void trace_packets_body(const Src& src, unsigned tota
 
 template <int BS>
 __global__ void __launch_bounds__(BS) k_trace_packets(TraceArgs a, int chunk) {
-    __shared__ int s_stack[BS / 32][HDOF_STACK];
-    trace_packets_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], s_stack[threadIdx.x >> 5], chunk);
+    trace_packets_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], chunk);
 }
 
 template <int BS>
 __global__ void __launch_bounds__(BS) k_trace_packets_batch(const TraceArgs* __restrict__ tab,
                                                             const unsigned* __restrict__ gq, int n, unsigned* head,
                                                             int chunk) {
-    __shared__ int s_stack[BS / 32][HDOF_STACK];
-    trace_packets_body(ManyViews{tab, gq, n}, __ldcg(&gq[n]), head, s_stack[threadIdx.x >> 5], chunk);
+    trace_packets_body(ManyViews{tab, gq, n}, __ldcg(&gq[n]), head, chunk);
 }
 
 template <int BS>
