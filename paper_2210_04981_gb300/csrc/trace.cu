@@ -553,8 +553,9 @@ __device__ __forceinline__ void trace_packets_body(const Src& src, unsigned tota
     }
 }
 
+// register budget for 40 resident warps per SM (measured faster than 36 at 56 registers)
 template <int BS>
-__global__ void __launch_bounds__(BS) k_trace_packets(TraceArgs a, int chunk) {
+__global__ void __launch_bounds__(BS, 1280 / BS) k_trace_packets(TraceArgs a, int chunk) {
     trace_packets_body(OneView{a}, __ldcg(&a.totals[2]), &a.totals[3], chunk);
 }
 
