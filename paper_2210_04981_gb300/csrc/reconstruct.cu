@@ -220,6 +220,19 @@ struct SpatialArgs {
     float4* aux;
 };
 
+// a traced pixel's reconstructed colour from its gathered sums: blended with
+// its own by beta = clamp(sigma_L / var_ref, 0, 1) (1 while its history is young)
+__device__ __forceinline__ void spatial_finish(const SpatialArgs& a, size_t q, const float4& cp, const float3& S,
+                                               float Ws) {
+    float2 m = __ldg(&a.mom[q]);
+    float sig = sqrtf(fmaxf(0.f, m.y - m.x * m.x));
+    float beta = __ldg(&a.hlen[q]) < 2 ? 1.f : clamp01(sig / a.var_ref);
+    float3 Csp = (1.f / Ws) * S;
+    if (a.aux) a.aux[q] = make_float4(Csp.x, Csp.y, Csp.z, Ws);  // kept for the adjoint
+    a.crec[q] = make_float4(cp.x + beta * (Csp.x - cp.x), cp.y + beta * (Csp.y - cp.y), cp.z + beta * (Csp.z - cp.z),
+                            0.f);
+}
+
 // the spatial gather of one traced pixel (i, j)
 __device__ __forceinline__ void spatial_pixel(const SpatialArgs& a, int i, int j) {
     const float4* __restrict__ crt = a.crt;
@@ -257,13 +270,57 @@ __device__ __forceinline__ void spatial_pixel(const SpatialArgs& a, int i, int j
             Ws += wq;
         }
     }
-    float2 m = __ldg(&a.mom[q]);
-    float sig = sqrtf(fmaxf(0.f, m.y - m.x * m.x));
-    float beta = __ldg(&a.hlen[q]) < 2 ? 1.f : clamp01(sig / a.var_ref);
-    float3 Csp = (1.f / Ws) * S;
-    if (a.aux) a.aux[q] = make_float4(Csp.x, Csp.y, Csp.z, Ws);  // kept for the adjoint
-    a.crec[q] = make_float4(cp.x + beta * (Csp.x - cp.x), cp.y + beta * (Csp.y - cp.y), cp.z + beta * (Csp.z - cp.z),
-                            0.f);
+    spatial_finish(a, q, cp, S, Ws);
+}
+
+// One thread gathers the horizontally adjacent pixels (i, j) and (i + 1, j)
+// (tl, tr: which of them is traced) over the union of their windows: each
+// tap is loaded once, and the right pixel's distance to a tap is the left
+// pixel's distance to the previous tap (the same float operations), so both
+// sums equal spatial_pixel's bit for bit (the union only adds taps of weight
+// exactly 0).  An untraced pixel of the pair gets reach 0 and is not written.
+__device__ __forceinline__ void spatial_pair(const SpatialArgs& a, int i, int j, bool tl, bool tr) {
+    const float4* __restrict__ crt = a.crt;
+    const int W = a.W, H = a.H;
+    const float r_s = a.r_s, Rq = r_s + 0.5f;
+    const size_t q = (size_t)j * W + i;
+    const float4 cl = tl ? __ldg(&crt[q]) : make_float4(0.f, 0.f, 0.f, -1.f);
+    const float4 cr = tr ? __ldg(&crt[q + 1]) : make_float4(0.f, 0.f, 0.f, -1.f);
+    const float Rl = tl ? fminf(cl.w * 0.5f, r_s) + 0.5f : 0.f;
+    const float Rr = tr ? fminf(cr.w * 0.5f, r_s) + 0.5f : 0.f;
+    const float Rl2 = Rl * Rl, Rr2 = Rr * Rr;
+    const int K = (int)floorf(fmaxf(Rl, Rr) + 1e-3f);
+    float3 Sl = f3(0, 0, 0), Sr = f3(0, 0, 0);
+    float Wl = 0.f, Wr = 0.f;
+    const int y0 = max(j - K, 0), y1 = min(j + K, H - 1);
+    for (int y = y0; y <= y1; ++y) {
+        const float dy = (float)(y - j), dy2 = dy * dy;
+        const int wl = (int)floorf(sqrtf(fmaxf(Rl2 - dy2, 0.f)) + 1e-3f);
+        const int wr = (int)floorf(sqrtf(fmaxf(Rr2 - dy2, 0.f)) + 1e-3f);
+        const int x0 = max(min(i - wl, i + 1 - wr), 0), x1 = min(max(i + wl, i + 1 + wr), W - 1);
+        const float4* row = crt + (size_t)y * W;
+        float dx = (float)(x0 - i);
+        float dprev = sqrt_approx(fmaf(dx - 1.f, dx - 1.f, dy2));  // the right pixel's distance to x0
+#pragma unroll SP_UNROLL
+        for (int x = x0; x <= x1; ++x, dx += 1.f) {
+            const float4 c = __ldg(&row[x]);
+            const float dl = sqrt_approx(fmaf(dx, dx, dy2)), dr = dprev;
+            const float rq = fminf(fmaf(c.w, 0.5f, 0.5f), Rq);
+            const float ql = clamp01(Rl - dl) * clamp01(rq - dl);
+            const float qr = clamp01(Rr - dr) * clamp01(rq - dr);
+            Sl.x = fmaf(ql, c.x, Sl.x);
+            Sl.y = fmaf(ql, c.y, Sl.y);
+            Sl.z = fmaf(ql, c.z, Sl.z);
+            Wl += ql;
+            Sr.x = fmaf(qr, c.x, Sr.x);
+            Sr.y = fmaf(qr, c.y, Sr.y);
+            Sr.z = fmaf(qr, c.z, Sr.z);
+            Wr += qr;
+            dprev = dl;
+        }
+    }
+    if (tl) spatial_finish(a, q, cl, Sl, Wl);
+    if (tr) spatial_finish(a, q + 1, cr, Sr, Wr);
 }
 
 // block = one T x T tile (T = 8 or 16), one thread per pixel: the tile's
@@ -296,8 +353,37 @@ __device__ __forceinline__ void spatial_body(const SpatialArgs& a, int bx, int b
     }
 }
 
-__global__ void __launch_bounds__(SP_THREADS) k_spatial(SpatialArgs a) {
-    spatial_body<SP_TILE>(a, blockIdx.x, blockIdx.y);
+// block = one 16x8 tile as 8x8 horizontal pixel pairs, one thread per pair:
+// the pairs holding a traced pixel are compacted so the threads that run
+// all gather, in one round
+constexpr int SPP_TW = 16, SPP_TH = 8, SPP_THREADS = SPP_TW * SPP_TH / 2;
+__global__ void __launch_bounds__(SPP_THREADS) k_spatial(SpatialArgs a) {
+    constexpr int NP = SPP_THREADS, PW = SPP_TW / 2;
+    __shared__ unsigned char s_list[NP];
+    __shared__ int s_cnt[NP / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int i0 = blockIdx.x * SPP_TW + 2 * (t % PW), j0 = blockIdx.y * SPP_TH + t / PW;
+    const bool row_in = j0 < a.H;
+    const bool tl = row_in && i0 < a.W && __ldg(&a.crt[(size_t)j0 * a.W + i0].w) >= 0.f;
+    const bool tr = row_in && i0 + 1 < a.W && __ldg(&a.crt[(size_t)j0 * a.W + i0 + 1].w) >= 0.f;
+    const bool act = tl || tr;
+    const unsigned tm = __ballot_sync(0xffffffffu, act);
+    if (lane == 0) s_cnt[w] = __popc(tm);
+    __syncthreads();
+    int off = 0, n = 0;
+#pragma unroll
+    for (int c = 0; c < NP / 32; ++c) {
+        off += c < w ? s_cnt[c] : 0;
+        n += s_cnt[c];
+    }
+    // the pair's slot and which of its pixels are traced
+    if (act) s_list[off + __popc(tm & ((1u << lane) - 1u))] = (unsigned char)(t | (tl ? 0x80 : 0) | (tr ? 0x40 : 0));
+    __syncthreads();
+    if (t < n) {
+        const int e = s_list[t], p = e & 0x3f;
+        spatial_pair(a, blockIdx.x * SPP_TW + 2 * (p % PW), blockIdx.y * SPP_TH + p / PW, (e & 0x80) != 0,
+                     (e & 0x40) != 0);
+    }
 }
 template <int T>
 __global__ void __launch_bounds__(T * T) k_spatial_batch(const SpatialArgs* __restrict__ a, BatchGrid g) {
@@ -337,9 +423,9 @@ TemporalArgs temporal_args(const float* rt, const hdof_gbuf* in, const uint8_t* 
 
 int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, int W, int H, float r_s, float var_ref,
                    float4* crec, float4* aux, cudaStream_t s) {
-    dim3 g2((W + SP_TILE - 1) / SP_TILE, (H + SP_TILE - 1) / SP_TILE);
+    dim3 g2((W + SPP_TW - 1) / SPP_TW, (H + SPP_TH - 1) / SPP_TH);
     ProfScope ps_("spatial", s);
-    k_spatial<<<g2, SP_THREADS, 0, s>>>(SpatialArgs{crt, mom, hlen, W, H, r_s, var_ref, crec, aux});
+    k_spatial<<<g2, SPP_THREADS, 0, s>>>(SpatialArgs{crt, mom, hlen, W, H, r_s, var_ref, crec, aux});
     HDOF_LAUNCHED("spatial reconstruction");
     return HDOF_OK;
 }
