@@ -594,9 +594,10 @@ __device__ __forceinline__ bool closest_hit_warp_oct(const BvhView& bvh, bool ac
 #endif
             const NodeBoxes nb = load_node(bvh.nodes + cur);
             const int4 ch = nb.ch;
-            float t0 = 0.f, t1 = 0.f;
-            const bool h0 = act && slab_hit_oct<OCT>(r, nb.x0, nb.y0, nb.z0, h.t, t0);
-            const bool h1 = act && slab_hit_oct<OCT>(r, nb.x1, nb.y1, nb.z1, h.t, t1);
+            float t0, t1;
+            // branch-free: an idle lane tests its placeholder ray and is masked out
+            const bool h0 = slab_hit_oct<OCT>(r, nb.x0, nb.y0, nb.z0, h.t, t0) & act;
+            const bool h1 = slab_hit_oct<OCT>(r, nb.x1, nb.y1, nb.z1, h.t, t1) & act;
             const unsigned b0 = __ballot_sync(FULL, h0), b1 = __ballot_sync(FULL, h1);
             if (b0 && b1) {
                 // first the child nearer for most of the lanes that enter both
