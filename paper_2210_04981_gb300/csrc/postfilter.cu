@@ -46,7 +46,7 @@ constexpr int GATHER_THREADS = 8 * (16 / PF_RY);
 #define HDOF_PF_MINB 16  // resident gather blocks per SM the register budget targets
 #endif
 #ifndef HDOF_PF_UNROLL
-#define HDOF_PF_UNROLL 4  // unroll of the gather's tap-pair loop
+#define HDOF_PF_UNROLL 1  // unroll of the gather's tap-pair loop (1, 2, 4, 8 swept: 1 fastest)
 #endif
 constexpr int PF_UNROLL = HDOF_PF_UNROLL;
 // Shared-memory carve-out (percent of the maximum) for the gather: the taps
