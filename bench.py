@@ -279,41 +279,62 @@ STAGES = ["gbuffer", "mask", "trace", "postfilter", "reconstruct", "composite"]
 def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, flush, profile=False,
                   static=False):
     """Warm-up frames, then K consecutive timed frames (L2 flushed between
-    them, outside the events) through the six C-ABI calls.  Returns the
-    renderer, the per-frame stage times [K, 6] (ms), the per-kernel times of
-    the library's profiler (mean ms per frame) and the per-frame
-    (traced pixels, rays)."""
+    them, outside the events) through the six C-ABI calls, as the Renderer
+    runs them: the post-filter on a side stream after the G-buffer,
+    concurrently with the mask, trace and reconstruction, the composite
+    after both.  Returns the renderer, the per-frame stage times [K, 6] (ms,
+    each stage between its own events on its stream), the per-kernel times
+    of the library's profiler (mean ms per frame), the per-frame (traced
+    pixels, rays), the wall time and the per-frame times [K] (ms, from the
+    frame's first call to the end of its composite)."""
     import torch
     r = H.Renderer(bvh, W, Hh, p0, device=dev, nd_dtype=nd_dt, col_dtype=col_dt)
     stream = torch.cuda.current_stream()
+    side = r.side
+    g_done, pf_done = torch.cuda.Event(), torch.cuda.Event()
 
     def params_of(k):
         return p0.replace(frame=k % 65536, camera_moved=int(k > 0 and not static))
 
-    def frame(k, ev=None):
+    # event slots: frame start, after G-buffer, mask, trace, reconstruct; post-filter start and end;
+    # composite start and end
+    SLOTS = ("f0", "g1", "m1", "t1", "r1", "p0", "p1", "c0", "c1")
+
+    def frame(k, ev=None, serial=False):
         cam, prev, p = cams[k], cams[max(k - 1, 0)], params_of(k)
         hin, hout = r.hist[r.cur], r.hist[1 - r.cur]
-        calls = [
-            lambda: H.hdof_gbuffer(bvh, cam, prev, p, r.g, hint=r.g.tri),
-            lambda: H.hdof_mask(r.g, hin, p, r.edge, r.spp, r.ws),
-            lambda: H.hdof_trace(bvh, cam, lens, p, r.spp, r.rt, r.stats, r.ws, hint=r.g.tri),
-            lambda: H.hdof_postfilter(r.g, cam, lens, p, r.pp, r.ws),
-            lambda: H.hdof_reconstruct(r.rt, r.g, r.spp, cam, prev, lens, p, hin, hout, r.crt, r.hacc, r.crec),
-            lambda: H.hdof_composite(r.g, r.spp, r.pp, r.crt, r.crec, r.hacc, cam, lens, p, r.out),
-        ]
-        for i, c in enumerate(calls):
+        pf_stream = stream if serial else side
+
+        def mark(name, s):
             if ev is not None:
-                ev[i].record(stream)
-            c()
-        if ev is not None:
-            ev[len(calls)].record(stream)
+                ev[name].record(s)
+
+        mark("f0", stream)
+        H.hdof_gbuffer(bvh, cam, prev, p, r.g, hint=r.g.tri)
+        mark("g1", stream)
+        g_done.record(stream)
+        pf_stream.wait_event(g_done)
+        mark("p0", pf_stream)
+        H.hdof_postfilter(r.g, cam, lens, p, r.pp, r.ws, stream=pf_stream)
+        mark("p1", pf_stream)
+        pf_done.record(pf_stream)
+        H.hdof_mask(r.g, hin, p, r.edge, r.spp, r.ws)
+        mark("m1", stream)
+        H.hdof_trace(bvh, cam, lens, p, r.spp, r.rt, r.stats, r.ws, hint=r.g.tri)
+        mark("t1", stream)
+        H.hdof_reconstruct(r.rt, r.g, r.spp, cam, prev, lens, p, hin, hout, r.crt, r.hacc, r.crec)
+        mark("r1", stream)
+        stream.wait_event(pf_done)
+        mark("c0", stream)
+        H.hdof_composite(r.g, r.spp, r.pp, r.crt, r.crec, r.hacc, cam, lens, p, r.out)
+        mark("c1", stream)
         r.cur = 1 - r.cur
 
     r.frame_fn = frame
     for k in range(warmup):
         frame(k)
     H.hdof_sync()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(K)]
+    evs = [{n: torch.cuda.Event(enable_timing=True) for n in SLOTS} for _ in range(K)]
     stats_all = torch.zeros((K, 2), dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
@@ -327,7 +348,8 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
     if profile:
         # the same K frames again (history reset, warm-up repeated) with the
         # library's per-kernel events (they add ~0.05 ms per frame, so the
-        # stage times above are taken without)
+        # stage times above are taken without), the post-filter serialised
+        # so that each kernel's events time it alone
         r.reset_history()
         for k in range(warmup):
             frame(k)
@@ -336,14 +358,17 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
         H.hdof_profile(True)
         for s in range(K):
             flush.zero_()
-            frame(warmup + s)
+            frame(warmup + s, serial=True)
         torch.cuda.synchronize()
         H.hdof_profile(False)
         kern = {n: t / K for n, (_, t) in H.hdof_profile_read().items()}
     H.hdof_sync()
-    stage_ms = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(len(STAGES))] for s in range(K)])
+    spans = {"gbuffer": ("f0", "g1"), "mask": ("g1", "m1"), "trace": ("m1", "t1"), "postfilter": ("p0", "p1"),
+             "reconstruct": ("t1", "r1"), "composite": ("c0", "c1")}
+    stage_ms = np.array([[evs[s][spans[n][0]].elapsed_time(evs[s][spans[n][1]]) for n in STAGES] for s in range(K)])
+    frame_ms = np.array([evs[s]["f0"].elapsed_time(evs[s]["c1"]) for s in range(K)])
     st = stats_all.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
-    return r, stage_ms, kern, st, wall
+    return r, stage_ms, kern, st, wall, frame_ms
 
 
 def e2e_frames(H, r, Hh, W, warmup, K, flush):
@@ -471,8 +496,8 @@ def quality_variants(H, bvh, W, Hh, lens, p0, dev, flush, frames, passes):
                                   ("static_fixed_ema", 0.0, False)):
         p = p0.replace(alpha_k=alpha_k)
         cams = [hi.room_camera(k if moving else 0, W, Hh) for k in range(frames + 1)]
-        r, _, _, _, _ = render_frames(H, bvh, W, Hh, cams, lens, p, dev, torch.float32, torch.float32, 0, frames,
-                                      flush, static=not moving)
+        r = render_frames(H, bvh, W, Hh, cams, lens, p, dev, torch.float32, torch.float32, 0, frames,
+                          flush, static=not moving)[0]
         last = frames - 1
         q = quality(H, bvh, r, cams[last], lens, p.replace(frame=last, camera_moved=int(moving)), passes)
         out[name] = {"hybrid_block8_mae": q["hybrid_vs_rt"]["block8_region_mae"],
@@ -558,11 +583,11 @@ def run_ours(args):
         torch.distributed.barrier()
     sampler = ClockSampler(local, period_ms=20)
     with sampler:
-        r, stage_ms, kern, st_all, wall = render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt,
-                                                        args.warmup, K, flush, profile=True)
+        r, stage_ms, kern, st_all, wall, frame_ms = render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt,
+                                                                  col_dt, args.warmup, K, flush, profile=True)
     if ws > 1:
         torch.distributed.barrier()
-    step_ms = stage_ms.sum(1)
+    step_ms = frame_ms
     total_ms = max_over_ranks(float(step_ms.sum()), dev)
     clocks = sampler.summary()
     traced, rays = st_all[:, 0], st_all[:, 1]
@@ -638,9 +663,9 @@ def run_ours(args):
     # "vs plain form": the same frames with mixed-precision storage, and the
     # 64-view batched frame against its single-view calls
     if not mixed and args.scene == "room" and not args.no_compare and ws == 1:
-        rm, sm_m, _, stm, _ = render_frames(H, bvh, W, Hh, cams, lens, p0, dev, torch.float16, torch.bfloat16,
-                                            args.warmup, K, flush)
-        mixed_ms = float(sm_m.sum(1).mean())
+        rm, sm_m, _, stm, _, fm_m = render_frames(H, bvh, W, Hh, cams, lens, p0, dev, torch.float16, torch.bfloat16,
+                                                  args.warmup, K, flush)
+        mixed_ms = float(fm_m.mean())
         out["mixed"] = {"value": round(mixed_ms, 4), "unit": "ms/frame",
                         "storage": "f16 normal/depth, bf16 colour, f32 elsewhere",
                         "speedup_vs_fp32": round(value / mixed_ms, 3),

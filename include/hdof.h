@@ -462,8 +462,10 @@ int hdof_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, con
  * hdof_postfilter applied to the plane (S, S, S) of the G-buffer's col.w in
  * place of the colour (the filter is linear in the colour, so this is
  * exactly the share of S in pp).  pp_spec: float [H][W][4] = (S_pp, S_pp,
- * S_pp, alpha).  workspace as for hdof_postfilter (its first 16 bytes per
- * pixel hold the grey plane).
+ * S_pp, alpha).  workspace as for hdof_postfilter, whose first 16 bytes per
+ * pixel (the mask's and the trace's region) hold the grey plane: unlike
+ * hdof_postfilter it must not run concurrently with hdof_mask, hdof_trace or
+ * hdof_postfilter on the same workspace.
  * hdof_composite_spec: hdof_composite whose near branch where traced is
  * lerp(C_rec, C_pp, clamp(spec_pref S_pp, 0, 1)); pp_spec may be NULL and
  * is ignored when spec_pref = 0 (then it equals hdof_composite).  Neither
@@ -528,8 +530,12 @@ size_t hdof_batch_bytes(const hdof_batch* batch);
 /* Enqueues the frame of every view of the batch: one launch per stage over
  * all views' blocks (G-buffer, mask, compaction, one persistent trace over
  * the concatenated ray queues, post-filter, reconstruction, composite).
- * Only kernel launches and device memsets: capturable into a CUDA graph.
- * Each view's results equal those of the single-view calls bit for bit. */
+ * The post-filter runs on a stream the handle owns, forked after the
+ * G-buffer and joined before the composite, concurrently with the mask,
+ * compaction, trace and reconstruction; the rest and the frame's completion
+ * are on `stream`.  Only kernel launches, device memsets and that event
+ * fork and join: capturable into a CUDA graph.  Each view's results equal
+ * those of the single-view calls bit for bit. */
 int hdof_batch_render(const hdof_batch* batch, void* stream);
 
 /* The batched frame's stages, in order; hdof_batch_render runs all of them. */

@@ -186,6 +186,8 @@ struct hdof_batch {
     char* host;              // pinned host image of the records (hdof_batch_update)
     cudaEvent_t uploaded;    // last upload of the host image
     std::vector<int> sizes;  // width, height, mask tile per view (fixed for the handle's life)
+    cudaStream_t side;       // the post-filter's stream in hdof_batch_render
+    cudaEvent_t fork, join;  // G-buffer done on the caller's stream; post-filter done on side
 };
 
 using namespace hdof;
@@ -231,15 +233,22 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
         return rc;
     }
     void* dmem = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr, fork = nullptr, join = nullptr;
+    cudaStream_t side = nullptr;
     cudaError_t e = cudaMalloc(&dmem, L.bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dmem, host, L.bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         if (dmem) cudaFree(dmem);
         if (ev) cudaEventDestroy(ev);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
         cudaFreeHost(host);
         return cuda_fail(e, "hdof_batch_create: upload");
     }
@@ -263,6 +272,9 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     b->L = L;
     b->host = host;
     b->uploaded = ev;
+    b->side = side;
+    b->fork = fork;
+    b->join = join;
     for (int v = 0; v < n; ++v) {
         b->sizes.push_back(views[v].cam.width);
         b->sizes.push_back(views[v].cam.height);
@@ -279,7 +291,11 @@ extern "C" int hdof_batch_destroy(hdof_batch* b) {
     cudaGetDevice(&cur);
     if (cur != b->device) cudaSetDevice(b->device);
     cudaError_t e = cudaEventSynchronize(b->uploaded);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->side);
     cudaEventDestroy(b->uploaded);
+    cudaEventDestroy(b->fork);
+    cudaEventDestroy(b->join);
+    cudaStreamDestroy(b->side);
     cudaError_t e2 = cudaFree(b->dmem);
     if (e == cudaSuccess) e = e2;
     cudaFreeHost(b->host);
@@ -369,6 +385,20 @@ extern "C" int hdof_batch_render_range(const hdof_batch* b, int32_t first, int32
     return HDOF_OK;
 }
 
+// The post-filter needs only the G-buffer and uses its own workspace
+// regions, so it runs on the batch's side stream, forked after the G-buffer
+// and joined before the composite, concurrently with the mask, compaction,
+// trace and reconstruction (a fork and join in a captured graph).
 extern "C" int hdof_batch_render(const hdof_batch* b, void* stream) {
-    return hdof_batch_render_range(b, 0, HDOF_BATCH_STAGES - 1, stream);
+    int rc;
+    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_GBUFFER, HDOF_STAGE_GBUFFER, stream))) return rc;
+    cudaStream_t s = as_stream(stream);
+    HDOF_CUDA(cudaEventRecord(b->fork, s), "hdof_batch_render: fork");
+    HDOF_CUDA(cudaStreamWaitEvent(b->side, b->fork, 0), "hdof_batch_render: fork");
+    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_POSTFILTER, HDOF_STAGE_POSTFILTER, b->side))) return rc;
+    HDOF_CUDA(cudaEventRecord(b->join, b->side), "hdof_batch_render: join");
+    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_MASK, HDOF_STAGE_TRACE, stream))) return rc;
+    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_RECONSTRUCT, HDOF_STAGE_RECONSTRUCT, stream))) return rc;
+    HDOF_CUDA(cudaStreamWaitEvent(s, b->join, 0), "hdof_batch_render: join");
+    return hdof_batch_render_range(b, HDOF_STAGE_COMPOSITE, HDOF_STAGE_COMPOSITE, stream);
 }

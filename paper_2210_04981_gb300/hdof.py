@@ -476,8 +476,12 @@ def hdof_composite_spec(gbuf: GBuffer, spp, pp, pp_spec, crt, crec, hacc, cam, l
 class Renderer:
     """Owns the device buffers of a width x height frame and enqueues the
     paper's per-frame sequence (G-buffer, mask, trace, post-filter,
-    reconstruction, composite) on one stream.  History is double-buffered
-    and swapped after each frame."""
+    reconstruction, composite).  The post-filter needs only the G-buffer
+    and has its own workspace region, so it runs on a side stream,
+    concurrently with the mask, trace and reconstruction, and the composite
+    waits for it; the frame's other calls and its completion are on the
+    caller's stream.  History is double-buffered and swapped after each
+    frame."""
 
     def __init__(self, bvh: Bvh, width, height, p, device="cuda", nd_dtype=torch.float32,
                  col_dtype=torch.float32):
@@ -498,6 +502,9 @@ class Renderer:
         self.cur = 0
         nbytes = hdof_workspace_bytes(width, height, p)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.side = torch.cuda.Stream(device=dev)  # the post-filter's stream
+        self._gbuf_done = torch.cuda.Event()
+        self._pf_done = torch.cuda.Event()
 
     @property
     def history(self) -> History:
@@ -509,23 +516,30 @@ class Renderer:
             h.reset()
 
     def frame(self, cam, prev, lns, p, stream=None, with_history=True):
+        main = stream if stream is not None else torch.cuda.current_stream(self.out.device)
         hin = self.hist[self.cur]
         hout = self.hist[1 - self.cur]
-        hdof_gbuffer(self.bvh, cam, prev, p, self.g, stream, hint=self.g.tri)
-        hdof_mask_coc(self.g, hin if with_history else None, cam, lns, p, self.edge, self.spp, self.ws, stream)
-        hdof_trace(self.bvh, cam, lns, p, self.spp, self.rt, self.stats, self.ws, stream, hint=self.g.tri)
-        hdof_postfilter(self.g, cam, lns, p, self.pp, self.ws, stream)
+        hdof_gbuffer(self.bvh, cam, prev, p, self.g, main, hint=self.g.tri)
+        # the post-filter on the side stream, after the G-buffer (it touches only
+        # the workspace's post-filter region)
+        self._gbuf_done.record(main)
+        self.side.wait_event(self._gbuf_done)
+        hdof_postfilter(self.g, cam, lns, p, self.pp, self.ws, self.side)
+        self._pf_done.record(self.side)
+        hdof_mask_coc(self.g, hin if with_history else None, cam, lns, p, self.edge, self.spp, self.ws, main)
+        hdof_trace(self.bvh, cam, lns, p, self.spp, self.rt, self.stats, self.ws, main, hint=self.g.tri)
         hdof_reconstruct(self.rt, self.g, self.spp, cam, prev, lns, p, hin, hout, self.crt, self.hacc,
-                         self.crec, stream)
+                         self.crec, main)
+        main.wait_event(self._pf_done)
         if p.spec_pref > 0:
+            # the specular plane's post-filter uses the whole workspace: after the trace and the post-filter
             if self.pp_spec is None:
                 self.pp_spec = torch.empty_like(self.pp)
-            hdof_postfilter_spec(self.g, cam, lns, p, self.pp_spec, self.ws, stream)
+            hdof_postfilter_spec(self.g, cam, lns, p, self.pp_spec, self.ws, main)
             hdof_composite_spec(self.g, self.spp, self.pp, self.pp_spec, self.crt, self.crec, self.hacc, cam, lns,
-                                p, self.out, stream)
+                                p, self.out, main)
         else:
-            hdof_composite(self.g, self.spp, self.pp, self.crt, self.crec, self.hacc, cam, lns, p, self.out,
-                           stream)
+            hdof_composite(self.g, self.spp, self.pp, self.crt, self.crec, self.hacc, cam, lns, p, self.out, main)
         self.cur = 1 - self.cur
         return self.out
 
