@@ -280,9 +280,10 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
                   static=False):
     """Warm-up frames, then K consecutive timed frames (L2 flushed between
     them, outside the events) through the six C-ABI calls, as the Renderer
-    runs them: the post-filter on a side stream after the G-buffer,
-    concurrently with the mask, trace and reconstruction, the composite
-    after both.  Returns the renderer, the per-frame stage times [K, 6] (ms,
+    runs them: forked from the caller's stream onto the Renderer's
+    high-priority critical-path stream, the post-filter on its low-priority
+    side stream after the G-buffer, concurrently with the mask, trace and
+    reconstruction, the composite after both, joined back at the end.  Returns the renderer, the per-frame stage times [K, 6] (ms,
     each stage between its own events on its stream), the per-kernel times
     of the library's profiler (mean ms per frame), the per-frame (traced
     pixels, rays), the wall time and the per-frame times [K] (ms, from the
@@ -290,7 +291,8 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
     import torch
     r = H.Renderer(bvh, W, Hh, p0, device=dev, nd_dtype=nd_dt, col_dtype=col_dt)
     stream = torch.cuda.current_stream()
-    side = r.side
+    crit, side = r.crit, r.side
+    start, done = torch.cuda.Event(), torch.cuda.Event()
     g_done, pf_done = torch.cuda.Event(), torch.cuda.Event()
 
     def params_of(k):
@@ -303,31 +305,35 @@ def render_frames(H, bvh, W, Hh, cams, lens, p0, dev, nd_dt, col_dt, warmup, K, 
     def frame(k, ev=None, serial=False):
         cam, prev, p = cams[k], cams[max(k - 1, 0)], params_of(k)
         hin, hout = r.hist[r.cur], r.hist[1 - r.cur]
-        pf_stream = stream if serial else side
+        pf_stream = crit if serial else side
 
         def mark(name, s):
             if ev is not None:
                 ev[name].record(s)
 
-        mark("f0", stream)
-        H.hdof_gbuffer(bvh, cam, prev, p, r.g, hint=r.g.tri)
-        mark("g1", stream)
-        g_done.record(stream)
+        start.record(stream)
+        crit.wait_event(start)
+        mark("f0", crit)
+        H.hdof_gbuffer(bvh, cam, prev, p, r.g, stream=crit, hint=r.g.tri)
+        mark("g1", crit)
+        g_done.record(crit)
         pf_stream.wait_event(g_done)
         mark("p0", pf_stream)
         H.hdof_postfilter(r.g, cam, lens, p, r.pp, r.ws, stream=pf_stream)
         mark("p1", pf_stream)
         pf_done.record(pf_stream)
-        H.hdof_mask(r.g, hin, p, r.edge, r.spp, r.ws)
-        mark("m1", stream)
-        H.hdof_trace(bvh, cam, lens, p, r.spp, r.rt, r.stats, r.ws, hint=r.g.tri)
-        mark("t1", stream)
-        H.hdof_reconstruct(r.rt, r.g, r.spp, cam, prev, lens, p, hin, hout, r.crt, r.hacc, r.crec)
-        mark("r1", stream)
-        stream.wait_event(pf_done)
-        mark("c0", stream)
-        H.hdof_composite(r.g, r.spp, r.pp, r.crt, r.crec, r.hacc, cam, lens, p, r.out)
-        mark("c1", stream)
+        H.hdof_mask(r.g, hin, p, r.edge, r.spp, r.ws, stream=crit)
+        mark("m1", crit)
+        H.hdof_trace(bvh, cam, lens, p, r.spp, r.rt, r.stats, r.ws, stream=crit, hint=r.g.tri)
+        mark("t1", crit)
+        H.hdof_reconstruct(r.rt, r.g, r.spp, cam, prev, lens, p, hin, hout, r.crt, r.hacc, r.crec, stream=crit)
+        mark("r1", crit)
+        crit.wait_event(pf_done)
+        mark("c0", crit)
+        H.hdof_composite(r.g, r.spp, r.pp, r.crt, r.crec, r.hacc, cam, lens, p, r.out, stream=crit)
+        mark("c1", crit)
+        done.record(crit)
+        stream.wait_event(done)
         r.cur = 1 - r.cur
 
     r.frame_fn = frame

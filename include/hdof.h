@@ -530,11 +530,12 @@ size_t hdof_batch_bytes(const hdof_batch* batch);
 /* Enqueues the frame of every view of the batch: one launch per stage over
  * all views' blocks (G-buffer, mask, compaction, one persistent trace over
  * the concatenated ray queues, post-filter, reconstruction, composite).
- * The post-filter runs on a stream the handle owns, forked after the
- * G-buffer and joined before the composite, concurrently with the mask,
- * compaction, trace and reconstruction; the rest and the frame's completion
- * are on `stream`.  Only kernel launches, device memsets and that event
- * fork and join: capturable into a CUDA graph.  Each view's results equal
+ * The frame is forked from `stream` onto two streams the handle owns: the
+ * critical path (highest priority) and the post-filter (lowest), forked
+ * after the G-buffer and joined before the composite, so the post-filter
+ * runs concurrently with the mask, compaction, trace and reconstruction;
+ * the frame is joined back to `stream` at its end.  Only kernel launches,
+ * device memsets and event forks and joins: capturable into a CUDA graph.  Each view's results equal
  * those of the single-view calls bit for bit. */
 int hdof_batch_render(const hdof_batch* batch, void* stream);
 

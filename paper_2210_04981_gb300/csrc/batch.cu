@@ -186,8 +186,9 @@ struct hdof_batch {
     char* host;              // pinned host image of the records (hdof_batch_update)
     cudaEvent_t uploaded;    // last upload of the host image
     std::vector<int> sizes;  // width, height, mask tile per view (fixed for the handle's life)
-    cudaStream_t side;       // the post-filter's stream in hdof_batch_render
-    cudaEvent_t fork, join;  // G-buffer done on the caller's stream; post-filter done on side
+    cudaStream_t crit;       // hdof_batch_render's critical path (highest priority)
+    cudaStream_t side;       // its post-filter (lowest priority)
+    cudaEvent_t start, fork, join, done;  // caller -> crit, crit -> side, side -> crit, crit -> caller
 };
 
 using namespace hdof;
@@ -233,21 +234,24 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
         return rc;
     }
     void* dmem = nullptr;
-    cudaEvent_t ev = nullptr, fork = nullptr, join = nullptr;
-    cudaStream_t side = nullptr;
+    cudaEvent_t ev = nullptr, evs[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t crit = nullptr, side = nullptr;
+    int least = 0, greatest = 0;
     cudaError_t e = cudaMalloc(&dmem, L.bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&evs[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&crit, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, least);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dmem, host, L.bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         if (dmem) cudaFree(dmem);
         if (ev) cudaEventDestroy(ev);
-        if (fork) cudaEventDestroy(fork);
-        if (join) cudaEventDestroy(join);
+        for (cudaEvent_t x : evs)
+            if (x) cudaEventDestroy(x);
+        if (crit) cudaStreamDestroy(crit);
         if (side) cudaStreamDestroy(side);
         cudaFreeHost(host);
         return cuda_fail(e, "hdof_batch_create: upload");
@@ -272,9 +276,12 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     b->L = L;
     b->host = host;
     b->uploaded = ev;
+    b->crit = crit;
     b->side = side;
-    b->fork = fork;
-    b->join = join;
+    b->start = evs[0];
+    b->fork = evs[1];
+    b->join = evs[2];
+    b->done = evs[3];
     for (int v = 0; v < n; ++v) {
         b->sizes.push_back(views[v].cam.width);
         b->sizes.push_back(views[v].cam.height);
@@ -291,10 +298,11 @@ extern "C" int hdof_batch_destroy(hdof_batch* b) {
     cudaGetDevice(&cur);
     if (cur != b->device) cudaSetDevice(b->device);
     cudaError_t e = cudaEventSynchronize(b->uploaded);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->crit);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->side);
     cudaEventDestroy(b->uploaded);
-    cudaEventDestroy(b->fork);
-    cudaEventDestroy(b->join);
+    for (cudaEvent_t x : {b->start, b->fork, b->join, b->done}) cudaEventDestroy(x);
+    cudaStreamDestroy(b->crit);
     cudaStreamDestroy(b->side);
     cudaError_t e2 = cudaFree(b->dmem);
     if (e == cudaSuccess) e = e2;
@@ -385,20 +393,31 @@ extern "C" int hdof_batch_render_range(const hdof_batch* b, int32_t first, int32
     return HDOF_OK;
 }
 
-// The post-filter needs only the G-buffer and uses its own workspace
-// regions, so it runs on the batch's side stream, forked after the G-buffer
-// and joined before the composite, concurrently with the mask, compaction,
-// trace and reconstruction (a fork and join in a captured graph).
+// The frame is forked from the caller's stream onto the batch's critical
+// path stream (highest priority: its kernels get the SMs first); the
+// post-filter needs only the G-buffer and uses its own workspace regions,
+// so it runs on the batch's side stream (lowest priority), forked after
+// the G-buffer and joined before the composite, concurrently with the mask,
+// compaction, trace and reconstruction; the frame is joined back to the
+// caller's stream at its end (forks and joins in a captured graph).
 extern "C" int hdof_batch_render(const hdof_batch* b, void* stream) {
+    clear_error();
+    HDOF_CHECK_ARG(b, "hdof_batch_render: batch is NULL");
+    cudaStream_t s = as_stream(stream), c = b->crit;
+    void* cv = static_cast<void*>(c);
     int rc;
-    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_GBUFFER, HDOF_STAGE_GBUFFER, stream))) return rc;
-    cudaStream_t s = as_stream(stream);
-    HDOF_CUDA(cudaEventRecord(b->fork, s), "hdof_batch_render: fork");
+    HDOF_CUDA(cudaEventRecord(b->start, s), "hdof_batch_render: fork");
+    HDOF_CUDA(cudaStreamWaitEvent(c, b->start, 0), "hdof_batch_render: fork");
+    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_GBUFFER, HDOF_STAGE_GBUFFER, cv))) return rc;
+    HDOF_CUDA(cudaEventRecord(b->fork, c), "hdof_batch_render: fork");
     HDOF_CUDA(cudaStreamWaitEvent(b->side, b->fork, 0), "hdof_batch_render: fork");
     if ((rc = hdof_batch_render_range(b, HDOF_STAGE_POSTFILTER, HDOF_STAGE_POSTFILTER, b->side))) return rc;
     HDOF_CUDA(cudaEventRecord(b->join, b->side), "hdof_batch_render: join");
-    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_MASK, HDOF_STAGE_TRACE, stream))) return rc;
-    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_RECONSTRUCT, HDOF_STAGE_RECONSTRUCT, stream))) return rc;
-    HDOF_CUDA(cudaStreamWaitEvent(s, b->join, 0), "hdof_batch_render: join");
-    return hdof_batch_render_range(b, HDOF_STAGE_COMPOSITE, HDOF_STAGE_COMPOSITE, stream);
+    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_MASK, HDOF_STAGE_TRACE, cv))) return rc;
+    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_RECONSTRUCT, HDOF_STAGE_RECONSTRUCT, cv))) return rc;
+    HDOF_CUDA(cudaStreamWaitEvent(c, b->join, 0), "hdof_batch_render: join");
+    if ((rc = hdof_batch_render_range(b, HDOF_STAGE_COMPOSITE, HDOF_STAGE_COMPOSITE, cv))) return rc;
+    HDOF_CUDA(cudaEventRecord(b->done, c), "hdof_batch_render: join");
+    HDOF_CUDA(cudaStreamWaitEvent(s, b->done, 0), "hdof_batch_render: join");
+    return HDOF_OK;
 }

@@ -473,15 +473,25 @@ def hdof_composite_spec(gbuf: GBuffer, spp, pp, pp_spec, crt, crec, hacc, cam, l
 
 # ---------------------------------------------------------- frame driver --
 
+def frame_priorities():
+    """(highest, lowest) stream priority of the device: the frame's critical
+    path and its concurrent post-filter."""
+    low, high = torch.cuda.Stream.priority_range()
+    return high, low
+
+
 class Renderer:
     """Owns the device buffers of a width x height frame and enqueues the
     paper's per-frame sequence (G-buffer, mask, trace, post-filter,
     reconstruction, composite).  The post-filter needs only the G-buffer
     and has its own workspace region, so it runs on a side stream,
     concurrently with the mask, trace and reconstruction, and the composite
-    waits for it; the frame's other calls and its completion are on the
-    caller's stream.  History is double-buffered and swapped after each
-    frame."""
+    waits for it.  The frame is forked from the caller's stream onto two
+    streams the Renderer owns, the critical path (G-buffer, mask, trace,
+    reconstruction, composite) at the highest priority so its kernels get
+    the SMs first, the post-filter at the lowest, and joined back to the
+    caller's stream at its end.  History is double-buffered and swapped
+    after each frame."""
 
     def __init__(self, bvh: Bvh, width, height, p, device="cuda", nd_dtype=torch.float32,
                  col_dtype=torch.float32):
@@ -502,9 +512,13 @@ class Renderer:
         self.cur = 0
         nbytes = hdof_workspace_bytes(width, height, p)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-        self.side = torch.cuda.Stream(device=dev)  # the post-filter's stream
+        high, low = frame_priorities()
+        self.crit = torch.cuda.Stream(device=dev, priority=high)  # the frame's critical path
+        self.side = torch.cuda.Stream(device=dev, priority=low)  # the post-filter
+        self._start = torch.cuda.Event()
         self._gbuf_done = torch.cuda.Event()
         self._pf_done = torch.cuda.Event()
+        self._done = torch.cuda.Event()
 
     @property
     def history(self) -> History:
@@ -516,7 +530,10 @@ class Renderer:
             h.reset()
 
     def frame(self, cam, prev, lns, p, stream=None, with_history=True):
-        main = stream if stream is not None else torch.cuda.current_stream(self.out.device)
+        caller = stream if stream is not None else torch.cuda.current_stream(self.out.device)
+        main = self.crit
+        self._start.record(caller)
+        main.wait_event(self._start)
         hin = self.hist[self.cur]
         hout = self.hist[1 - self.cur]
         hdof_gbuffer(self.bvh, cam, prev, p, self.g, main, hint=self.g.tri)
@@ -540,6 +557,8 @@ class Renderer:
                                 p, self.out, main)
         else:
             hdof_composite(self.g, self.spp, self.pp, self.crt, self.crec, self.hacc, cam, lns, p, self.out, main)
+        self._done.record(main)
+        caller.wait_event(self._done)
         self.cur = 1 - self.cur
         return self.out
 
