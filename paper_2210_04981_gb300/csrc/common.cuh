@@ -162,8 +162,10 @@ __device__ __forceinline__ float ldz(const half4s* p) { return __high2float(__ld
 // ------------------------------------------------------------------- BVH --
 // Binary BVH node: the boxes of both children in one 64-byte record, so one
 // fetch tests both.  Child reference >= 0: internal node; < 0: a leaf of
-// 1..8 consecutive sorted triangles, ~(first << 3 | (count - 1)).
-struct __align__(16) Node {
+// 1..8 consecutive sorted triangles, ~(first << 3 | (count - 1)).  Node
+// arrays start at an allocation's base, so every record is 64-byte aligned
+// (the traversal fetches it with two 256-bit loads).
+struct __align__(64) Node {
     float4 xy0;  // c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y
     float4 xy1;  // c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y
     float4 z01;  // c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z
@@ -445,18 +447,20 @@ struct NodeBoxes {
     f32x2 x0, y0, z0, x1, y1, z1;
     int4 ch;
 };
+// two 256-bit loads (the node is 64 bytes, 64-byte aligned): the boxes'
+// (l, h) pairs arrive as the 64-bit words the f32x2 box test takes
 __device__ __forceinline__ NodeBoxes load_node(const Node* n) {
-    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(&n->xy0));
-    const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(&n->xy1));
-    const ulonglong2 z = __ldg(reinterpret_cast<const ulonglong2*>(&n->z01));
+    unsigned long long a0, a1, a2, a3, b0, b1, b2, b3;
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(a0), "=l"(a1), "=l"(a2), "=l"(a3) : "l"(n));
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4+32];" : "=l"(b0), "=l"(b1), "=l"(b2), "=l"(b3) : "l"(n));
     NodeBoxes nb;
-    nb.x0 = a.x;
-    nb.y0 = a.y;
-    nb.x1 = b.x;
-    nb.y1 = b.y;
-    nb.z0 = z.x;
-    nb.z1 = z.y;
-    nb.ch = __ldg(&n->child);
+    nb.x0 = a0;  // xy0 = (c0.lo.x, c0.hi.x), (c0.lo.y, c0.hi.y)
+    nb.y0 = a1;
+    nb.x1 = a2;  // xy1
+    nb.y1 = a3;
+    nb.z0 = b0;  // z01 = (c0.lo.z, c0.hi.z), (c1.lo.z, c1.hi.z)
+    nb.z1 = b1;
+    nb.ch = make_int4((int)(unsigned)b2, (int)(unsigned)(b2 >> 32), (int)(unsigned)b3, (int)(unsigned)(b3 >> 32));
     return nb;
 }
 
