@@ -11,7 +11,7 @@
 // evaluated by binary search, which is exact up to float rounding.
 //
 // k_pf_prep: per pixel r + 1/2, z and the premultiplied near and far layer
-//   records (c w/a, w/a), the records split by pixel-index parity; per 16x16
+//   records (c w/a, w/a), row-major; per 16x16
 //   tile the largest r feeding each layer and the smallest r feeding the near
 //   layer.
 // k_pf_rowscan: the row prefix of the near records (row-major).
@@ -113,10 +113,8 @@ __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx,
         float4 col = ld4(a.col + q);
         a.rh[q] = r + 0.5f;
         a.zq[q] = z;
-        // records split by pixel-index parity: even pixels, then odd ones
-        const size_t qs = (q >> 1) + (q & 1) * (((size_t)W * H + 1) >> 1);
-        a.nrec[qs] = make_float4(col.x * an, col.y * an, col.z * an, an);
-        a.frec[qs] = make_float4(col.x * af, col.y * af, col.z * af, af);
+        a.nrec[q] = make_float4(col.x * an, col.y * an, col.z * an, an);
+        a.frec[q] = make_float4(col.x * af, col.y * af, col.z * af, af);
         rn = wn > 0.f ? r : -1.f;
         rf = wn < 1.f ? r : -1.f;
         rnmin = wn > 0.f ? r : INF;
@@ -146,7 +144,7 @@ __global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND, COL> a) { pf_prep_
 // in rounds of 256 consecutive pixels (a block scan per round plus the
 // running total): the summation order is fixed.
 struct RowScanArgs {
-    const float4* nrec;  // split by pixel-index parity
+    const float4* nrec;  // row-major
     int W, H;
     float4* pre;
 };
@@ -157,15 +155,14 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
 
 __device__ __forceinline__ void pf_rowscan_body(const RowScanArgs& a, int y) {
     const int W = a.W, t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const size_t half = ((size_t)W * a.H + 1) >> 1, row = (size_t)y * W;
+    const size_t row = (size_t)y * W;
     __shared__ float4 s_warp[8];
     float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int x0 = 0; x0 < W; x0 += 256) {
         const int x = x0 + t;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (x < W) {
-            const size_t q = row + x;
-            v = __ldg(&a.nrec[(q >> 1) + (q & 1) * half]);
+            v = __ldg(&a.nrec[row + x]);
         }
         // inclusive warp scan, then the warps' totals
         for (int o = 1; o < 32; o <<= 1) {
@@ -282,18 +279,22 @@ __device__ __forceinline__ void pf_tap(A (&a)[PF_NPX], float (&c)[PF_RY], float&
     pdx2 = dx2;
 }
 
+// two consecutive records (32 bytes, 32-byte aligned) in one 256-bit load
+__device__ __forceinline__ void ld_rec_pair(const float4* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // The taps of source row y from column xs to xe (inclusive) for the 2 x RY
-// block at (i, j).  Records are split by the parity of the pixel index (even
-// pixels first), so at each tap the threads of a row, two columns apart,
-// read consecutive records; taps go in pairs (even, odd index) with one
-// float2 load of r + 1/2 (and z) per pair.
+// block at (i, j).  Taps go in pairs (even, odd pixel index): one 256-bit
+// load of the two records and one float2 load of r + 1/2 (and z) per pair;
+// the threads of a row, two columns apart, read consecutive pairs.
 template <bool NEAR, bool MASK, class A>
 __device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF_RY], const float (&win2)[PF_RY],
-                                           int xs, int xe, int i, int y, int W, size_t half,
+                                           int xs, int xe, int i, int y, int W,
                                            const float* __restrict__ rh, const float* __restrict__ zq,
                                            const float4* __restrict__ rec) {
-    const float4* __restrict__ rec_e = rec;
-    const float4* __restrict__ rec_o = rec + half;
     const float2* __restrict__ rh2 = reinterpret_cast<const float2*>(rh);
     const float2* __restrict__ zq2 = reinterpret_cast<const float2*>(zq);
     float dx = (float)(xs - i);
@@ -304,7 +305,7 @@ __device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF
     const size_t gend = (size_t)y * W + xe + 1;
     if (g & 1) {  // an odd first tap on its own
         const float z = NEAR ? 0.f : __ldg(&zq[g]);
-        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[g]), z, __ldg(&rec_o[g >> 1]));
+        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[g]), z, __ldg(&rec[g]));
         ++g;
         dx += 1.f;
     }
@@ -313,7 +314,8 @@ __device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF
 #pragma unroll PF_UNROLL
     for (; m < mend; ++m, dx += 2.f) {
         const float2 r2 = __ldg(&rh2[m]);
-        const float4 e0 = __ldg(&rec_e[m]), e1 = __ldg(&rec_o[m]);
+        float4 e0, e1;
+        ld_rec_pair(rec + 2 * m, e0, e1);
         const float2 z2 = NEAR ? make_float2(0.f, 0.f) : __ldg(&zq2[m]);
         pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, r2.x, z2.x, e0);
         pf_tap<MASK>(a, c, pdx2, dyk, win2, dx + 1.f, r2.y, z2.y, e1);
@@ -321,7 +323,7 @@ __device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF
     if (gend & 1) {  // an even last tap on its own
         const size_t gl = gend - 1;
         const float z = NEAR ? 0.f : __ldg(&zq[gl]);
-        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[gl]), z, __ldg(&rec_e[gl >> 1]));
+        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[gl]), z, __ldg(&rec[gl]));
     }
 }
 
@@ -343,7 +345,6 @@ __device__ __forceinline__ void pf_layer(A (&a)[PF_NPX], float R, float Rin, int
     if (R < 0.f) return;  // nothing within reach feeds this layer
     // bounds lean outwards by 1e-3 pixel (float rounding); taps they add weigh 0
     const int G = (int)floorf(R + 1e-3f);
-    const size_t half = ((size_t)W * H + 1) >> 1;
     const int y0 = max(j - G, 0), y1 = min(j + PF_RY - 1 + G, H - 1);
     const float R2 = R * R, Rin2 = Rin * Rin;
     for (int y = y0; y <= y1; ++y) {
@@ -391,12 +392,12 @@ __device__ __forceinline__ void pf_layer(A (&a)[PF_NPX], float R, float Rin, int
         if (wmin >= 1) {
             // columns [i + 1 - wmin, i + wmin] lie in every pixel's interior
             const int ls = min(x1, i - wmin), rs = max(x0, i + wmin + 1);
-            if (x0 <= ls) pf_segment<NEAR, true>(a, dyk, win2, x0, ls, i, y, W, half, rh, zq, rec);
-            if (rs <= x1) pf_segment<NEAR, true>(a, dyk, win2, rs, x1, i, y, W, half, rh, zq, rec);
+            if (x0 <= ls) pf_segment<NEAR, true>(a, dyk, win2, x0, ls, i, y, W, rh, zq, rec);
+            if (rs <= x1) pf_segment<NEAR, true>(a, dyk, win2, rs, x1, i, y, W, rh, zq, rec);
         } else if (masked) {
-            pf_segment<NEAR, true>(a, dyk, win2, x0, x1, i, y, W, half, rh, zq, rec);
+            pf_segment<NEAR, true>(a, dyk, win2, x0, x1, i, y, W, rh, zq, rec);
         } else {
-            pf_segment<NEAR, false>(a, dyk, win2, x0, x1, i, y, W, half, rh, zq, rec);
+            pf_segment<NEAR, false>(a, dyk, win2, x0, x1, i, y, W, rh, zq, rec);
         }
     }
 }
