@@ -60,8 +60,8 @@ PF_OPS_PER_LOOKUP = 8
 # launch-list capture of the 1080p room frame, caches flushed before each launch)
 # of the current kernels; None where the kernel changed since the capture
 MEASURED_TRAFFIC = {
-    ("room", "f32", "trace_packets"): 18548992,
-    ("room", "f32", "pf_gather"): 121877248,
+    ("room", "f32", "trace_packets"): 18807552,
+    ("room", "f32", "pf_gather"): 120664832,
 }
 
 
@@ -601,7 +601,12 @@ def run_ours(args):
     var_px = int(((spp_h > 0) & (spp_h < p0.spp_max)).sum())
     mean_stage = stage_ms.mean(0)
     trace_ms = float(mean_stage[STAGES.index("trace")])
-    mrays = float(rays.mean()) / (trace_ms * 1e-3) / 1e6
+    # the trace call's own rate: its kernels (compaction, trace, resolve) as the serialised profiled pass
+    # times them over the same frames; in the timed frames the concurrent post-filter shares the SMs
+    # with them, which stretches the stage's span (trace_ms)
+    trace_alone = sum(kern.get(n, 0.0) for n in ("trace_compact", "trace_packets", "trace_rays", "trace_resolve"))
+    mrays = float(rays.mean()) / ((trace_alone or trace_ms) * 1e-3) / 1e6
+    mrays_concurrent = float(rays.mean()) / (trace_ms * 1e-3) / 1e6
     hbm, sm_med, peak_src = peaks()
     ab = algorithmic_bytes(W, Hh, float(traced.mean()), float(var_px), 8 if mixed else 16, 8 if mixed else 16)
     per_stage = {}
@@ -657,8 +662,10 @@ def run_ours(args):
                    "storage": "f16 normal/depth, bf16 colour, f32 elsewhere" if mixed else "f32",
                    "spp_max": p0.spp_max, "r_max": p0.r_max,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single", "l2": "flushed between steps (256 MiB write)"},
-        "mrays_per_s": round(mrays, 1), "rays_per_frame": int(rays.mean()),
+        "mrays_per_s": round(mrays, 1), "mrays_per_s_concurrent": round(mrays_concurrent, 1),
+        "rays_per_frame": int(rays.mean()),
         "traced_px_per_frame": int(traced.mean()), "trace_ms": round(trace_ms, 4),
+        "trace_call_alone_ms": round(trace_alone, 4),
         "stages": per_stage, "kernels_ms": kernels, "bvh_build_ms": round(bvh_ms, 3), "bvh_depth": int(st.depth),
         "scene_upload_ms": round(upload_ms, 3), "wall_s_timed": round(wall, 3),
         "roofline": roof, "roofline_alu_kernels": roofs,
