@@ -958,6 +958,30 @@ def run_diff(args):
     fwd = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     bwd = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
     clocks = sampler.summary()
+    # the same step with the lens on the device (the _dlens calls), captured
+    # once into a CUDA graph and replayed: no host work between the kernels
+    lens_dev = torch.tensor([zf, A], dtype=torch.float32, device=dev)
+    gst = path.new_state()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        path.forward_dev(C, lens_dev, gst)
+        path.backward_dev(Y, lens_dev, gst)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        path.forward_dev(C, lens_dev, gst)
+        path.backward_dev(Y, lens_dev, gst)
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        gev[k][0].record(stream)
+        graph.replay()
+        gev[k][1].record(stream)
+    torch.cuda.synchronize()
+    H.hdof_sync()
+    graph_ms = float(np.mean([a.elapsed_time(b) for a, b in gev]))
     # end to end: colour image in from pinned host memory, gradients out
     hC = torch.from_numpy(col).pin_memory()
     hg = torch.empty((Hh, W, 3), dtype=torch.float32).pin_memory()
@@ -987,6 +1011,7 @@ def run_diff(args):
                                "100k-triangle room traced at focus 2.5 / aperture 0.04; step at focus 2.0 / "
                                "aperture 0.03", "rays": n_rays, "l2": "flushed between steps (256 MiB write)"},
         "forward_ms": round(fwd, 4), "backward_ms": round(bwd, 4), "contributing_taps": taps,
+        "graph_step_ms": round(graph_ms, 4),
         "roofline": {"bound": "alu", "achieved": round(ach, 2), "peak": round(lane_peak, 2), "unit": "Tlane-op/s",
                      "frac": round(ach / lane_peak, 3), "traffic": None,
                      "kernel": "hdof_post_backward (post-filter adjoint dominates)",

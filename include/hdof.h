@@ -27,8 +27,9 @@
  *   hdof_mask_noalloc's tile array): do not keep using it across a
  *   cudaDeviceReset of a device it has run on.
  * - The first post-filter call on a device (hdof_postfilter, the batched
- *   frame, hdof_post_forward/backward) uploads the area table and waits for
- *   it; make that first call before capturing a stream into a graph.
+ *   frame, hdof_post_forward/backward and their _dlens forms) uploads the
+ *   area table and waits for it; make that first call before capturing a
+ *   stream into a graph.
  * - Camera space: the camera at `pos` looks along +fwd with +right, +up;
  *   the screen point of pixel (i, j) this frame is (i + 0.5 + jitter[0],
  *   j + 0.5 + jitter[1]).  Depth is view-space z (distance along fwd).
@@ -589,7 +590,8 @@ size_t hdof_post_workspace_bytes(int32_t width, int32_t height, const hdof_param
  * re-evaluated from the records at `lens` (each hit's CoC and split weight
  * change, not the hits), then the temporal step over the frozen samples, the
  * spatial gather, the post-filter and the composite run with the frame's
- * definitions.  Writes every buffer of *st. */
+ * definitions.  Writes every buffer of *st: rt, hacc, mom, crec and sp_aux
+ * at the traced pixels only, the others at every pixel. */
 int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
                       const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
                       const hdof_params* p, const hdof_post_state* st, void* workspace,
@@ -608,6 +610,26 @@ int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec
                        const hdof_params* p, const hdof_post_state* st, const float* grad_out,
                        float* grad_col, float* grad_lens, void* workspace, size_t workspace_bytes,
                        void* stream);
+
+/* hdof_post_forward / hdof_post_backward with the lens on the device:
+ * lens_dev = device float [2] (focus distance, aperture radius), read by the
+ * kernels when they run, so that a fitting step needs no read-back of the
+ * lens to the host and can be captured into a CUDA graph (each replay reads
+ * the array's values then).  Results are those of the host-record calls
+ * with the same lens, bit for bit (the CoC constants are computed with the
+ * same single-precision arithmetic).  The values are not checked on the
+ * host: a focus distance or aperture that is not finite and positive gives
+ * non-finite outputs (every access stays in bounds).  lens_dev NULL:
+ * HDOF_EINVAL; every other argument as in the host-record calls. */
+int hdof_post_forward_dlens(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                            const float* hist_samples, const hdof_camera* cam, const float* lens_dev,
+                            const hdof_params* p, const hdof_post_state* st, void* workspace,
+                            size_t workspace_bytes, void* stream);
+int hdof_post_backward_dlens(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                             const float* hist_samples, const hdof_camera* cam, const float* lens_dev,
+                             const hdof_params* p, const hdof_post_state* st, const float* grad_out,
+                             float* grad_col, float* grad_lens, void* workspace, size_t workspace_bytes,
+                             void* stream);
 
 #ifdef __cplusplus
 }

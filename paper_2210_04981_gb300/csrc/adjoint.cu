@@ -26,10 +26,21 @@ namespace {
 constexpr float RS2 = 0.35355339059327373f;  // 1 / (2 sqrt2): slope of w_near inside the focus zone
 
 struct LensD {
-    float K;    // A H / t
-    float izf;  // 1 / zf
-    float Ht;   // H / t
+    float K;           // A H / t
+    float izf;         // 1 / zf
+    float Ht;          // H / t
+    float t;           // tan(fovy / 2)
+    const float* dev;  // optional (zf, A) on the device: K and izf are read from it when a kernel starts
 };
+
+// K and izf of a lens on the device, by make_lensd's arithmetic
+__device__ __forceinline__ LensD lens_at(LensD L, int H) {
+    if (L.dev) {
+        L.K = __ldg(&L.dev[1]) * (float)H / L.t;
+        L.izf = 1.f / __ldg(&L.dev[0]);
+    }
+    return L;
+}
 
 __device__ __forceinline__ float coc_z(float z, const LensD& L) {
     return isinf(z) ? -L.K * L.izf : L.K * (1.f / z - L.izf);
@@ -96,6 +107,7 @@ __device__ __forceinline__ ReplaySums replay_sums(const float4* rec, unsigned fi
 __global__ void __launch_bounds__(256) k_replay(const float4* __restrict__ rec, const unsigned* __restrict__ ray_off,
                                                 const uint8_t* __restrict__ spp, int W, int H, LensD L,
                                                 float4* __restrict__ rt) {
+    L = lens_at(L, H);
     int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (i >= W || j >= H) return;
     size_t q = (size_t)j * W + i;
@@ -220,6 +232,7 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const float4* __restrict_
                                                        float4* __restrict__ gpp, float4* __restrict__ gcrec,
                                                        float4* __restrict__ gcrt, float* __restrict__ ghacc,
                                                        double2* partial) {
+    L = lens_at(L, H);
     int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
     float2 dth = make_float2(0.f, 0.f);
     if (i < W && j < H) {
@@ -376,6 +389,7 @@ __global__ void __launch_bounds__(256) k_temporal_replay_bwd(const float4* __res
                                                              const float* __restrict__ ghacc,
                                                              const float2* __restrict__ gmom, int W, int H, LensD L,
                                                              float al, int moved, double2* partial) {
+    L = lens_at(L, H);
     int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
     float2 dth = make_float2(0.f, 0.f);
     size_t q = (size_t)j * W + i;
@@ -599,6 +613,7 @@ __global__ void __launch_bounds__(64, HDOF_PFB_MINB) k_pf_bwd(const float4* __re
                                                const float4* __restrict__ tab, int ntab, int W, int H, LensD L,
                                                float rmax, float kz_rel, float4* __restrict__ gcol,
                                                double2* partial) {
+    L = lens_at(L, H);
     __shared__ int s_win;
     if (threadIdx.x == 0) s_win = 0;
     __syncthreads();
@@ -724,6 +739,15 @@ LensD make_lensd(const hdof_lens& l, int H, float t) {
     L.K = l.aperture_radius * (float)H / t;
     L.izf = 1.f / l.focus_dist;
     L.Ht = (float)H / t;
+    L.t = t;
+    L.dev = nullptr;
+    return L;
+}
+LensD make_lensd_dev(const float* lens_dev, int H, float t) {
+    LensD L{};
+    L.Ht = (float)H / t;
+    L.t = t;
+    L.dev = lens_dev;
     return L;
 }
 
@@ -765,7 +789,7 @@ int check_post(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const 
                const hdof_camera* cam, const hdof_lens* lens, const hdof_params* p, const hdof_post_state* st,
                const char* who) {
     int rc;
-    if ((rc = check_camera(cam, who)) || (rc = check_lens(lens, who)) || (rc = check_params(p, who)) ||
+    if ((rc = check_camera(cam, who)) || (lens && (rc = check_lens(lens, who))) || (rc = check_params(p, who)) ||
         (rc = check_gbuf(in, who, false)))
         return rc;
     HDOF_CHECK_ARG(in->dtype_nd == HDOF_F32 && in->dtype_col == HDOF_F32, "%s: the differentiable path is FP32", who);
@@ -774,7 +798,7 @@ int check_post(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const 
     HDOF_CHECK_ARG(st->rt && st->crt && st->hacc && st->mom && st->hlen && st->crec && st->sp_aux && st->pp &&
                        st->pp_aux && st->out,
                    "%s: every state buffer is required", who);
-    HDOF_CHECK_ARG(lens->aperture_radius > 0.f, "%s: the lens gradient needs an aperture > 0", who);
+    HDOF_CHECK_ARG(!lens || lens->aperture_radius > 0.f, "%s: the lens gradient needs an aperture > 0", who);
     if (p->alpha_k != 0.f || p->blades != 0 || p->aberration != 0.f || p->spec_pref != 0.f) {
         set_error("%s: the differentiable path takes the fixed EMA weight, the uniform circular lens and no "
                   "specular preference (alpha_k, blades, aberration and spec_pref must be 0)", who);
@@ -795,19 +819,23 @@ extern "C" size_t hdof_post_workspace_bytes(int32_t width, int32_t height, const
     return pf > bw ? pf : bw;
 }
 
-extern "C" int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
-                                 const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
-                                 const hdof_params* p, const hdof_post_state* st, void* workspace,
-                                 size_t workspace_bytes, void* stream) {
+namespace hdof {
+namespace {
+
+// the forward with the lens as a host record (lens) or on the device (lens_dev)
+int post_forward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                 const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens, const float* lens_dev,
+                 const hdof_params* p, const hdof_post_state* st, void* workspace, size_t workspace_bytes,
+                 void* stream, const char* who) {
     clear_error();
     int rc;
-    if ((rc = check_post(in, spp, rec, ray_off, cam, lens, p, st, "hdof_post_forward"))) return rc;
+    if ((rc = check_post(in, spp, rec, ray_off, cam, lens, p, st, who))) return rc;
     const int W = in->width, H = in->height;
-    HDOF_CHECK_ARG(workspace && workspace_bytes >= hdof_post_workspace_bytes(W, H, p),
-                   "hdof_post_forward: workspace of %zu bytes < %zu", workspace_bytes,
-                   hdof_post_workspace_bytes(W, H, p));
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= hdof_post_workspace_bytes(W, H, p), "%s: workspace of %zu bytes < %zu",
+                   who, workspace_bytes, hdof_post_workspace_bytes(W, H, p));
     cudaStream_t s = as_stream(stream);
-    LensD L = make_lensd(*lens, H, cam->tan_half_fovy);
+    const float t = cam->tan_half_fovy;
+    LensD L = lens ? make_lensd(*lens, H, t) : make_lensd_dev(lens_dev, H, t);
     dim3 g1((W + 31) / 32, (H + 7) / 8);
     k_replay<<<g1, 256, 0, s>>>(reinterpret_cast<const float4*>(rec), ray_off, spp, W, H, L,
                                 reinterpret_cast<float4*>(st->rt));
@@ -815,43 +843,46 @@ extern "C" int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const 
                                          reinterpret_cast<const float4*>(hist_samples), W, H, p->ema_alpha,
                                          p->camera_moved, reinterpret_cast<float4*>(st->crt), st->hacc,
                                          reinterpret_cast<float2*>(st->mom), st->hlen);
-    HDOF_LAUNCHED("hdof_post_forward: replay/temporal");
+    HDOF_LAUNCHED("post-path forward: replay/temporal");
     if ((rc = launch_spatial(reinterpret_cast<const float4*>(st->crt), reinterpret_cast<const float2*>(st->mom),
                              st->hlen, W, H, p->r_s, p->var_ref, reinterpret_cast<float4*>(st->crec),
                              reinterpret_cast<float4*>(st->sp_aux), s)))
         return rc;
-    Coc coc = make_coc(*lens, H, cam->tan_half_fovy);
-    if ((rc = launch_postfilter(in, coc, p, st->pp, reinterpret_cast<float4*>(st->pp_aux), workspace, s))) return rc;
-    return launch_composite(in, spp, st->pp, nullptr, st->crt, st->crec, st->hacc, coc, p->h_tau, 0.f, st->out, s);
+    // with lens_dev the kernels replace coc's lens by the device one
+    const hdof_lens unit = {1.f, 1.f, 1.f};
+    const Coc coc = make_coc(lens ? *lens : unit, H, t);
+    if ((rc = launch_postfilter(in, coc, p, st->pp, reinterpret_cast<float4*>(st->pp_aux), workspace, s, lens_dev, t)))
+        return rc;
+    return launch_composite(in, spp, st->pp, nullptr, st->crt, st->crec, st->hacc, coc, p->h_tau, 0.f, st->out, s,
+                            lens_dev, t);
 }
 
-extern "C" int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
-                                  const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
-                                  const hdof_params* p, const hdof_post_state* st, const float* grad_out,
-                                  float* grad_col, float* grad_lens, void* workspace, size_t workspace_bytes,
-                                  void* stream) {
+// the backward with the lens as a host record (lens) or on the device (lens_dev)
+int post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                  const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens, const float* lens_dev,
+                  const hdof_params* p, const hdof_post_state* st, const float* grad_out, float* grad_col,
+                  float* grad_lens, void* workspace, size_t workspace_bytes, void* stream, const char* who) {
     clear_error();
     int rc;
-    if ((rc = check_post(in, spp, rec, ray_off, cam, lens, p, st, "hdof_post_backward"))) return rc;
-    HDOF_CHECK_ARG(grad_out && grad_col && grad_lens, "hdof_post_backward: grad_out, grad_col, grad_lens required");
+    if ((rc = check_post(in, spp, rec, ray_off, cam, lens, p, st, who))) return rc;
+    HDOF_CHECK_ARG(grad_out && grad_col && grad_lens, "%s: grad_out, grad_col, grad_lens required", who);
     const int W = in->width, H = in->height;
-    HDOF_CHECK_ARG(workspace && workspace_bytes >= hdof_post_workspace_bytes(W, H, p),
-                   "hdof_post_backward: workspace of %zu bytes < %zu", workspace_bytes,
-                   hdof_post_workspace_bytes(W, H, p));
+    HDOF_CHECK_ARG(workspace && workspace_bytes >= hdof_post_workspace_bytes(W, H, p), "%s: workspace of %zu bytes < %zu",
+                   who, workspace_bytes, hdof_post_workspace_bytes(W, H, p));
     cudaStream_t s = as_stream(stream);
     if ((rc = ensure_area_table(s))) return rc;
     const float4* tab = nullptr;
     int ntab = 0;
     if ((rc = area_table(&tab, &ntab))) return rc;
     BwdWs b = bwd_layout(W, H, static_cast<char*>(workspace));
-    LensD L = make_lensd(*lens, H, cam->tan_half_fovy);
+    LensD L = lens ? make_lensd(*lens, H, cam->tan_half_fovy) : make_lensd_dev(lens_dev, H, cam->tan_half_fovy);
     const float4* nd = static_cast<const float4*>(in->nd);
     const float4* col = static_cast<const float4*>(in->col);
     float4* gcol = reinterpret_cast<float4*>(grad_col);
     dim3 g1((W + 31) / 32, (H + 7) / 8), g2((W + 15) / 16, (H + 15) / 16);
     const int n1 = g1.x * g1.y;
-    HDOF_CUDA(cudaMemsetAsync(b.gcrt, 0, 16 * (size_t)W * H, s), "hdof_post_backward: clear");
-    HDOF_CUDA(cudaMemsetAsync(b.gmom, 0, 8 * (size_t)W * H, s), "hdof_post_backward: clear");
+    HDOF_CUDA(cudaMemsetAsync(b.gcrt, 0, 16 * (size_t)W * H, s), "post-path backward: clear");
+    HDOF_CUDA(cudaMemsetAsync(b.gmom, 0, 8 * (size_t)W * H, s), "post-path backward: clear");
     k_composite_bwd<<<g1, 256, 0, s>>>(nd, col, spp, reinterpret_cast<const float4*>(st->pp),
                                        reinterpret_cast<const float4*>(st->crt), reinterpret_cast<const float4*>(st->crec),
                                        st->hacc, reinterpret_cast<const float4*>(grad_out), W, H, L, p->h_tau, gcol, b.gpp,
@@ -869,6 +900,63 @@ extern "C" int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const
     k_pf_bwd<<<g2, 64, 0, s>>>(nd, col, b.pfb, b.kbp, tab, ntab, W, H, L, p->r_max, p->kz_rel, gcol,
                                b.partial + 2 * n1);
     k_reduce<<<1, 1024, 0, s>>>(b.partial, b.n_partial, grad_lens);
-    HDOF_LAUNCHED("hdof_post_backward");
+    HDOF_LAUNCHED("post-path backward");
     return HDOF_OK;
+}
+
+}  // namespace
+}  // namespace hdof
+
+extern "C" int hdof_post_forward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                                 const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
+                                 const hdof_params* p, const hdof_post_state* st, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+    if (!lens) {
+        clear_error();
+        set_error("hdof_post_forward: lens is required");
+        return HDOF_EINVAL;
+    }
+    return post_forward(in, spp, rec, ray_off, hist_samples, cam, lens, nullptr, p, st, workspace, workspace_bytes,
+                        stream, "hdof_post_forward");
+}
+
+extern "C" int hdof_post_forward_dlens(const hdof_gbuf* in, const uint8_t* spp, const float* rec,
+                                       const uint32_t* ray_off, const float* hist_samples, const hdof_camera* cam,
+                                       const float* lens_dev, const hdof_params* p, const hdof_post_state* st,
+                                       void* workspace, size_t workspace_bytes, void* stream) {
+    if (!lens_dev) {
+        clear_error();
+        set_error("hdof_post_forward_dlens: lens_dev is required");
+        return HDOF_EINVAL;
+    }
+    return post_forward(in, spp, rec, ray_off, hist_samples, cam, nullptr, lens_dev, p, st, workspace,
+                        workspace_bytes, stream, "hdof_post_forward_dlens");
+}
+
+extern "C" int hdof_post_backward(const hdof_gbuf* in, const uint8_t* spp, const float* rec, const uint32_t* ray_off,
+                                  const float* hist_samples, const hdof_camera* cam, const hdof_lens* lens,
+                                  const hdof_params* p, const hdof_post_state* st, const float* grad_out,
+                                  float* grad_col, float* grad_lens, void* workspace, size_t workspace_bytes,
+                                  void* stream) {
+    if (!lens) {
+        clear_error();
+        set_error("hdof_post_backward: lens is required");
+        return HDOF_EINVAL;
+    }
+    return post_backward(in, spp, rec, ray_off, hist_samples, cam, lens, nullptr, p, st, grad_out, grad_col,
+                         grad_lens, workspace, workspace_bytes, stream, "hdof_post_backward");
+}
+
+extern "C" int hdof_post_backward_dlens(const hdof_gbuf* in, const uint8_t* spp, const float* rec,
+                                        const uint32_t* ray_off, const float* hist_samples, const hdof_camera* cam,
+                                        const float* lens_dev, const hdof_params* p, const hdof_post_state* st,
+                                        const float* grad_out, float* grad_col, float* grad_lens, void* workspace,
+                                        size_t workspace_bytes, void* stream) {
+    if (!lens_dev) {
+        clear_error();
+        set_error("hdof_post_backward_dlens: lens_dev is required");
+        return HDOF_EINVAL;
+    }
+    return post_backward(in, spp, rec, ray_off, hist_samples, cam, nullptr, lens_dev, p, st, grad_out, grad_col,
+                         grad_lens, workspace, workspace_bytes, stream, "hdof_post_backward_dlens");
 }

@@ -100,6 +100,15 @@ __host__ __device__ inline Coc make_coc(const hdof_lens& l, int H, float t) {
     c.izf = 1.f / l.focus_dist;
     return c;
 }
+// The same constants for a lens read on the device, lens = (focus distance,
+// aperture radius), by make_coc's arithmetic; lens NULL: c as given.
+__device__ __forceinline__ Coc lens_coc(const Coc& c, const float* lens, int H, float t) {
+    if (!lens) return c;
+    Coc o;
+    o.k = __ldg(&lens[1]) * (float)H / t;
+    o.izf = 1.f / __ldg(&lens[0]);
+    return o;
+}
 
 // Near-layer split weight, linear across the focus zone |c| < sqrt2.
 __device__ __forceinline__ float w_near(float c) {

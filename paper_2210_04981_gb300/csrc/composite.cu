@@ -28,6 +28,8 @@ struct CompositeArgs {
     float h_tau;
     float spec_pref;
     float4* out;
+    const float* lens;  // optional (focus distance, aperture radius) on the device, replacing coc's lens
+    float t;            // tan(fovy / 2), with lens
 };
 
 template <class ND, class COL>
@@ -40,7 +42,7 @@ __device__ __forceinline__ void composite_body(const CompositeArgs<ND, COL>& a, 
     const float4* __restrict__ crec = a.crec;
     const float* __restrict__ hacc = a.hacc;
     const int W = a.W, H = a.H;
-    const Coc coc = a.coc;
+    const Coc coc = lens_coc(a.coc, a.lens, H, a.t);
     const float h_tau = a.h_tau;
     float4* __restrict__ out = a.out;
     int i = bx * 32 + (threadIdx.x & 31), j = by * 8 + (threadIdx.x >> 5);
@@ -83,29 +85,30 @@ __global__ void __launch_bounds__(256) k_composite_batch(const CompositeF32* __r
 
 template <class ND, class COL>
 void launch(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* pp_spec, const float* crt,
-            const float* crec, const float* hacc, Coc coc, float h_tau, float spec_pref, float* out, cudaStream_t s) {
+            const float* crec, const float* hacc, Coc coc, float h_tau, float spec_pref, float* out, cudaStream_t s,
+            const float* lens_dev, float t) {
     dim3 g((in->width + 31) / 32, (in->height + 7) / 8);
     ProfScope ps_("composite", s);
     k_composite<ND, COL><<<g, 256, 0, s>>>(CompositeArgs<ND, COL>{
         static_cast<const ND*>(in->nd), static_cast<const COL*>(in->col), spp, reinterpret_cast<const float4*>(pp),
         reinterpret_cast<const float4*>(pp_spec), reinterpret_cast<const float4*>(crt),
         reinterpret_cast<const float4*>(crec), hacc, in->width, in->height, coc, h_tau, spec_pref,
-        reinterpret_cast<float4*>(out)});
+        reinterpret_cast<float4*>(out), lens_dev, t});
 }
 
 }  // namespace
 
 int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* pp_spec,
                      const float* crt, const float* crec, const float* hacc, const Coc& coc, float h_tau,
-                     float spec_pref, float* out, cudaStream_t s) {
+                     float spec_pref, float* out, cudaStream_t s, const float* lens_dev, float t) {
     if (in->dtype_nd == HDOF_F32 && in->dtype_col == HDOF_F32)
-        launch<float4, float4>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s);
+        launch<float4, float4>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s, lens_dev, t);
     else if (in->dtype_nd == HDOF_F16 && in->dtype_col == HDOF_BF16)
-        launch<half4s, bf164s>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s);
+        launch<half4s, bf164s>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s, lens_dev, t);
     else if (in->dtype_nd == HDOF_F16)
-        launch<half4s, float4>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s);
+        launch<half4s, float4>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s, lens_dev, t);
     else
-        launch<float4, bf164s>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s);
+        launch<float4, bf164s>(in, spp, pp, pp_spec, crt, crec, hacc, coc, h_tau, spec_pref, out, s, lens_dev, t);
     HDOF_LAUNCHED("composite");
     return HDOF_OK;
 }

@@ -108,10 +108,10 @@ int launch_spatial(const float4* crt, const float2* mom, const uint8_t* hlen, in
                    float4* crec, float4* aux, cudaStream_t s);
 // scratch: ws_layout(W, H, p).pf bytes (the post-filter regions)
 int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, float4* aux,
-                      void* scratch, cudaStream_t s);
+                      void* scratch, cudaStream_t s, const float* lens_dev = nullptr, float t = 0.f);
 int launch_composite(const hdof_gbuf* in, const uint8_t* spp, const float* pp, const float* pp_spec,
                      const float* crt, const float* crec, const float* hacc, const Coc& coc, float h_tau,
-                     float spec_pref, float* out, cudaStream_t s);
+                     float spec_pref, float* out, cudaStream_t s, const float* lens_dev = nullptr, float t = 0.f);
 
 }  // namespace hdof
 

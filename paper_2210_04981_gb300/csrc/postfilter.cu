@@ -95,6 +95,8 @@ struct PrepArgs {
     float4* nrec;   // (c w/a, w/a), near layer
     float4* frec;   // (c (1-w)/a, (1-w)/a), far layer
     float4* tmax;   // per tile: (max r feeding near, max r feeding far, min r feeding near (+inf: none), 0)
+    const float* lens;  // optional (focus distance, aperture radius) on the device, replacing coc's lens
+    float t;            // tan(fovy / 2), with lens
 };
 
 template <class ND, class COL>
@@ -106,7 +108,7 @@ __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx,
     if (i < W && j < H) {
         size_t q = (size_t)j * W + i;
         float z = ldz(a.nd + q);
-        float c = a.coc(z);
+        float c = lens_coc(a.coc, a.lens, H, a.t)(z);
         float r = fminf(fabsf(c) * 0.5f, a.rmax);
         float ia = 1.f / disk_area(r);
         float wn = w_near(c), an = wn * ia, af = (1.f - wn) * ia;
@@ -615,9 +617,9 @@ using namespace hdof;
 namespace hdof {
 
 int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p, float* pp, float4* aux,
-                      void* scratch, cudaStream_t s) {
+                      void* scratch, cudaStream_t s, const float* lens_dev, float t) {
     if (bokeh_shaped(p)) {
-        if (aux) {
+        if (aux || lens_dev) {
             set_error("post-filter: shaped bokeh has no adjoint records");
             return HDOF_EUNSUPPORTED;
         }
@@ -640,16 +642,16 @@ int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p,
         ProfScope ps_("pf_prep", s);
         if (f32n && f32c)
             k_pf_prep<<<grid, 256, 0, s>>>(
-                PrepArgs<float4, float4>{nd4, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+                PrepArgs<float4, float4>{nd4, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax, lens_dev, t});
         else if (f32n)
             k_pf_prep<<<grid, 256, 0, s>>>(
-                PrepArgs<float4, bf164s>{nd4, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+                PrepArgs<float4, bf164s>{nd4, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax, lens_dev, t});
         else if (f32c)
             k_pf_prep<<<grid, 256, 0, s>>>(
-                PrepArgs<half4s, float4>{ndh, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+                PrepArgs<half4s, float4>{ndh, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax, lens_dev, t});
         else
             k_pf_prep<<<grid, 256, 0, s>>>(
-                PrepArgs<half4s, bf164s>{ndh, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax});
+                PrepArgs<half4s, bf164s>{ndh, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax, lens_dev, t});
         HDOF_LAUNCHED("post-filter prep");
     }
     {

@@ -149,6 +149,10 @@ def load():
                                P(hdof_post_state), vp, sz, vp], C.c_int),
         "hdof_post_backward": ([P(hdof_gbuf), vp, vp, vp, vp, P(hdof_camera), P(hdof_lens), P(hdof_params),
                                 P(hdof_post_state), vp, vp, vp, vp, sz, vp], C.c_int),
+        "hdof_post_forward_dlens": ([P(hdof_gbuf), vp, vp, vp, vp, P(hdof_camera), vp, P(hdof_params),
+                                     P(hdof_post_state), vp, sz, vp], C.c_int),
+        "hdof_post_backward_dlens": ([P(hdof_gbuf), vp, vp, vp, vp, P(hdof_camera), vp, P(hdof_params),
+                                      P(hdof_post_state), vp, vp, vp, vp, sz, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -166,7 +170,8 @@ def exported_symbols():
             "hdof_postfilter", "hdof_postfilter_spec", "hdof_reconstruct", "hdof_composite", "hdof_composite_spec",
             "hdof_batch_create", "hdof_batch_update", "hdof_batch_render", "hdof_batch_render_range",
             "hdof_batch_destroy", "hdof_batch_bytes",
-            "hdof_post_workspace_bytes", "hdof_post_forward", "hdof_post_backward", "hdof_profile",
+            "hdof_post_workspace_bytes", "hdof_post_forward", "hdof_post_backward", "hdof_post_forward_dlens",
+            "hdof_post_backward_dlens", "hdof_profile",
             "hdof_profile_read", "hdof_probe_fma"]
 
 
@@ -710,6 +715,31 @@ def hdof_post_backward(gbuf: GBuffer, spp, rec, ray_off, hist_samples, cam, lns,
                                      _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
+def _lens_dev(lens_dev):
+    if not (lens_dev.is_cuda and lens_dev.dtype == torch.float32 and lens_dev.numel() == 2 and lens_dev.is_contiguous()):
+        raise ValueError("lens_dev must be a contiguous float32 CUDA tensor of 2 values (focus, aperture)")
+    return _ptr(lens_dev)
+
+
+def hdof_post_forward_dlens(gbuf: GBuffer, spp, rec, ray_off, hist_samples, cam, lens_dev, p, st: PostState,
+                            workspace, stream=None):
+    """hdof_post_forward with lens_dev = (focus, aperture) read on the device."""
+    _check(load().hdof_post_forward_dlens(C.byref(gbuf.struct()), _ptr(spp), _ptr(rec), _ptr(ray_off),
+                                          _ptr(hist_samples), C.byref(camera(cam)), _lens_dev(lens_dev),
+                                          C.byref(params(p)), C.byref(st.struct()), _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def hdof_post_backward_dlens(gbuf: GBuffer, spp, rec, ray_off, hist_samples, cam, lens_dev, p, st: PostState,
+                             grad_out, grad_col, grad_lens, workspace, stream=None):
+    """hdof_post_backward with lens_dev = (focus, aperture) read on the device."""
+    _check(load().hdof_post_backward_dlens(C.byref(gbuf.struct()), _ptr(spp), _ptr(rec), _ptr(ray_off),
+                                           _ptr(hist_samples), C.byref(camera(cam)), _lens_dev(lens_dev),
+                                           C.byref(params(p)), C.byref(st.struct()), _ptr(grad_out),
+                                           _ptr(grad_col), _ptr(grad_lens), _ptr(workspace),
+                                           workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
 class _Lens:
     def __init__(self, zf, A, f):
         self.focus_dist, self.aperture_radius, self.focal_length = zf, A, f
@@ -744,6 +774,27 @@ class PostPath:
                           st, self.ws)
         return st.out[..., :3]
 
+    def forward_dev(self, col, lens_dev, state=None):
+        """forward with lens_dev = device float32 [2] (focus, aperture)."""
+        st, col4 = state if state is not None else (self.st, self.col4)
+        col4[..., :3] = col
+        g = GBuffer.from_tensors(self.nd, col4)
+        hdof_post_forward_dlens(g, self.spp, self.rec, self.ray_off, self.hs, self.cam, lens_dev, self.p, st, self.ws)
+        return st.out[..., :3]
+
+    def backward_dev(self, grad_out, lens_dev, state=None):
+        """backward with lens_dev = device float32 [2] (focus, aperture)."""
+        st, col4 = state if state is not None else (self.st, self.col4)
+        H, W = self.spp.shape
+        g4 = torch.zeros((H, W, 4), dtype=torch.float32, device=grad_out.device)
+        g4[..., :3] = grad_out
+        gcol = torch.empty_like(g4)
+        glens = torch.empty(2, dtype=torch.float32, device=grad_out.device)
+        g = GBuffer.from_tensors(self.nd, col4)
+        hdof_post_backward_dlens(g, self.spp, self.rec, self.ray_off, self.hs, self.cam, lens_dev, self.p, st, g4,
+                                 gcol, glens, self.ws)
+        return gcol[..., :3], glens
+
     def backward(self, grad_out, zf, A, state=None):
         st, col4 = state if state is not None else (self.st, self.col4)
         H, W = self.spp.shape
@@ -760,20 +811,20 @@ class PostPath:
 class HdofPost(torch.autograd.Function):
     """out = post-path(col [H,W,3], lens_params [2] = (focus, aperture)) with
     the hand-written adjoint of hdof_post_backward.  Each call keeps its own
-    forward state for its backward (no forward is re-run).  The lens enters
-    the C calls as a host record, so the forward reads lens_params back from
-    the device once."""
+    forward state for its backward (no forward is re-run).  The lens stays on
+    the device (the _dlens calls read it there): no host synchronisation, so
+    a forward + backward step can be captured into a CUDA graph."""
 
     @staticmethod
     def forward(ctx, col, lens_params, path: PostPath):
-        zf, A = (float(x) for x in lens_params.detach().cpu().tolist())
+        lens_dev = lens_params.detach().to(device=col.device, dtype=torch.float32).contiguous()
         state = path.new_state()
-        out = path.forward(col.detach().contiguous(), zf, A, state).clone()
-        ctx.path, ctx.zf, ctx.A, ctx.state = path, zf, A, state
+        out = path.forward_dev(col.detach().contiguous(), lens_dev, state).clone()
+        ctx.path, ctx.lens_dev, ctx.state = path, lens_dev, state
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        gcol, glens = ctx.path.backward(grad_out.contiguous().float(), ctx.zf, ctx.A, ctx.state)
+        gcol, glens = ctx.path.backward_dev(grad_out.contiguous().float(), ctx.lens_dev, ctx.state)
         ctx.state = None
         return gcol, glens.to(grad_out.device), None

@@ -107,6 +107,19 @@ def test_invalid_arguments_rejected_before_launch(H):
     assert lib.hdof_batch_render(None, None) == -1
     assert lib.hdof_batch_update(None, views, 1, None) == -1
     assert lib.hdof_batch_destroy(None) == 0
+    # the post-path with the lens on the device: a NULL lens array, then the
+    # other arguments, are rejected on the host
+    st = H.hdof_post_state()
+    assert lib.hdof_post_forward_dlens(C.byref(g), None, None, None, None, C.byref(cam), None, C.byref(p),
+                                       C.byref(st), None, 0, None) == -1
+    lib.hdof_last_error(buf, 256)
+    assert b"lens_dev" in buf.value
+    assert lib.hdof_post_backward_dlens(C.byref(g), None, None, None, None, C.byref(cam), None, C.byref(p),
+                                        C.byref(st), None, None, None, None, 0, None) == -1
+    assert lib.hdof_post_forward_dlens(C.byref(g), None, None, None, None, C.byref(bad), C.c_void_p(256), C.byref(p),
+                                       C.byref(st), None, 0, None) == -1
+    lib.hdof_last_error(buf, 256)
+    assert b"image size" in buf.value
 
 
 def test_python_binding_requires_cuda_tensors(H):

@@ -203,3 +203,71 @@ def test_adam_fit_recovers_lens():
     theta = lens()
     zf, A = (float(v) for v in theta.detach().cpu())
     assert abs(zf - 2.5) < 0.05 and abs(A - 0.04) < 0.002, (zf, A)
+
+
+def _step_inputs(s, seed=5):
+    W, Hh = s["col"].shape[1], s["col"].shape[0]
+    C = torch.from_numpy(s["col"]).cuda()
+    Y = torch.from_numpy(np.random.default_rng(seed).uniform(-1, 1, (Hh, W, 3)).astype(np.float32)).cuda()
+    return C, Y
+
+
+def test_device_lens_calls_equal_host_lens_calls():
+    """hdof_post_forward_dlens / hdof_post_backward_dlens read (focus,
+    aperture) on the device and give the host-record calls' state, image and
+    gradients bit for bit."""
+    s = _setup(160, 120)
+    path = _path(s)
+    C, Y = _step_inputs(s)
+    zf, A = 2.0, 0.03
+    lens_dev = torch.tensor([zf, A], dtype=torch.float32, device="cuda")
+    sa, sb = path.new_state(), path.new_state()
+    names = ("rt", "crt", "hacc", "mom", "hlen", "crec", "sp_aux", "pp", "pp_aux", "out")
+    for st in (sa[0], sb[0]):  # some planes are written at traced pixels only
+        for n in names:
+            getattr(st, n).zero_()
+    path.forward(C, zf, A, sa)
+    path.forward_dev(C, lens_dev, sb)
+    for n in names:
+        assert torch.equal(getattr(sa[0], n), getattr(sb[0], n)), n
+    ga, la = path.backward(Y, zf, A, sa)
+    gb, lb = path.backward_dev(Y, lens_dev, sb)
+    H.hdof_sync()
+    assert torch.equal(ga, gb)
+    assert torch.equal(la, lb), (la, lb)
+    # the autograd op takes the device path: same values as the host-record calls
+    out = H.HdofPost.apply(C, lens_dev, path)
+    assert torch.equal(out, sa[0].out[..., :3])
+
+
+def test_post_step_captured_in_a_graph():
+    """A forward + backward step with the lens on the device, captured into a
+    CUDA graph once and replayed after new lens values are written into the
+    same array, equals the eager host-record calls at those values."""
+    s = _setup(160, 120)
+    path = _path(s)
+    C, Y = _step_inputs(s)
+    lens_dev = torch.tensor([2.0, 0.03], dtype=torch.float32, device="cuda")
+    state = path.new_state()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up outside the capture (the first calls load a table)
+        path.forward_dev(C, lens_dev, state)
+        path.backward_dev(Y, lens_dev, state)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        out = path.forward_dev(C, lens_dev, state)
+        gcol, glens = path.backward_dev(Y, lens_dev, state)
+    for zf, A in ((2.7, 0.045), (1.6, 0.02), (2.0, 0.03)):
+        lens_dev.copy_(torch.tensor([zf, A], dtype=torch.float32))
+        g.replay()
+        ref = path.new_state()
+        o_ref = path.forward(C, zf, A, ref).clone()
+        g_ref, l_ref = path.backward(Y, zf, A, ref)
+        H.hdof_sync()
+        assert torch.equal(out, o_ref), (zf, A)
+        assert torch.equal(gcol, g_ref), (zf, A)
+        assert torch.equal(glens, l_ref), (zf, A, glens, l_ref)
+
