@@ -96,6 +96,10 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", str(self.period)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # the timed region starts once the sampler is live (its first line is out)
+            t_end = time.perf_counter() + 3.0
+            while time.perf_counter() < t_end and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -944,20 +948,19 @@ def run_diff(args):
     torch.cuda.synchronize()
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
-    sampler = ClockSampler(0)
-    with sampler:
-        for k in range(K):
-            flush.zero_()
-            ev[k][0].record(stream)
-            path.forward(C, zf, A)
-            ev[k][1].record(stream)
-            path.backward(Y, zf, A)
-            ev[k][2].record(stream)
-        torch.cuda.synchronize()
+    sampler = ClockSampler(0, period_ms=20)
+    sampler.__enter__()  # sampled through the eager, graph and end-to-end loops below
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        path.forward(C, zf, A)
+        ev[k][1].record(stream)
+        path.backward(Y, zf, A)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
     H.hdof_sync()
     fwd = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     bwd = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
-    clocks = sampler.summary()
     # the same step with the lens on the device (the _dlens calls), captured
     # once into a CUDA graph and replayed: no host work between the kernels
     lens_dev = torch.tensor([zf, A], dtype=torch.float32, device=dev)
@@ -999,6 +1002,8 @@ def run_diff(args):
         e1.record(stream)
         e1.synchronize()
         e_ms += e0.elapsed_time(e1)
+    sampler.__exit__(None, None, None)
+    clocks = sampler.summary()
     taps = contributing_taps(z.astype(np.float64), hi.Lens(zf, A, 0.05), Hh, cam.tan_half_fovy, p.r_max)
     lane_peak = fp32_peak(H, dev) / 1e12
     ach = taps * PF_BWD_OPS_PER_TAP / (bwd * 1e-3) / 1e12
