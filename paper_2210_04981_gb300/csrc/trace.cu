@@ -57,7 +57,9 @@ __device__ __forceinline__ void count_body(const CountArgs& a, int bx, int by) {
 __global__ void __launch_bounds__(256) k_count(CountArgs a) { count_body(a, blockIdx.x, blockIdx.y); }
 
 // one block: exclusive scans of the per-tile pixel and ray counts -> queue
-// and ray offsets; totals -> stats
+// and ray offsets; totals -> stats.  Each thread takes SCAN_TPT consecutive
+// tiles per round (their count pairs in vector loads, a serial prefix), the
+// block scans the threads' sums: one round covers 1024 x SCAN_TPT tiles.
 struct ScanArgs {
     const unsigned* counts;
     int ntiles;
@@ -66,6 +68,8 @@ struct ScanArgs {
     unsigned* totals;
     unsigned* stats;
 };
+
+constexpr int SCAN_TPT = 8;
 
 __device__ __forceinline__ void scan_body(const ScanArgs& a) {
     const unsigned* __restrict__ counts = a.counts;
@@ -79,14 +83,41 @@ __device__ __forceinline__ void scan_body(const ScanArgs& a) {
     if (threadIdx.x == 0) carry[0] = carry[1] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int base = 0; base < ntiles; base += 1024) {
-        int t = base + threadIdx.x;
-        unsigned v[2] = {t < ntiles ? counts[2 * t] : 0u, t < ntiles ? counts[2 * t + 1] : 0u};
+    // 16-byte vectors when every array allows them (workspace regions do)
+    const bool vec = ((reinterpret_cast<uintptr_t>(counts) | reinterpret_cast<uintptr_t>(offsets) |
+                       reinterpret_cast<uintptr_t>(roffsets)) & 15) == 0;
+    for (int base = 0; base < ntiles; base += 1024 * SCAN_TPT) {
+        const int t0 = base + threadIdx.x * SCAN_TPT;
+        const bool whole = vec && t0 + SCAN_TPT <= ntiles;
+        unsigned c[2 * SCAN_TPT];  // (pixels, rays) of tiles t0 ...
+        if (whole) {
+            const uint4* p = reinterpret_cast<const uint4*>(counts + 2 * t0);
+#pragma unroll
+            for (int k = 0; k < SCAN_TPT / 2; ++k) {
+                const uint4 u = p[k];
+                c[4 * k] = u.x;
+                c[4 * k + 1] = u.y;
+                c[4 * k + 2] = u.z;
+                c[4 * k + 3] = u.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < SCAN_TPT; ++k) {
+                c[2 * k] = t0 + k < ntiles ? counts[2 * (t0 + k)] : 0u;
+                c[2 * k + 1] = t0 + k < ntiles ? counts[2 * (t0 + k) + 1] : 0u;
+            }
+        }
+        unsigned v[2] = {0u, 0u};
+#pragma unroll
+        for (int k = 0; k < SCAN_TPT; ++k) {
+            v[0] += c[2 * k];
+            v[1] += c[2 * k + 1];
+        }
         unsigned x[2] = {v[0], v[1]};
-        for (int c = 0; c < 2; ++c)
+        for (int cc = 0; cc < 2; ++cc)
             for (int o = 1; o < 32; o <<= 1) {
-                unsigned y = __shfl_up_sync(0xffffffffu, x[c], o);
-                if (lane >= o) x[c] += y;
+                unsigned y = __shfl_up_sync(0xffffffffu, x[cc], o);
+                if (lane >= o) x[cc] += y;
             }
         if (lane == 31) {
             wsum[0][w] = x[0];
@@ -104,14 +135,34 @@ __device__ __forceinline__ void scan_body(const ScanArgs& a) {
         __syncthreads();
         unsigned e0 = carry[0] + (w ? wsum[0][w - 1] : 0u) + x[0] - v[0];
         unsigned e1 = carry[1] + (w ? wsum[1][w - 1] : 0u) + x[1] - v[1];
-        if (t < ntiles) {
-            offsets[t] = e0;
-            roffsets[t] = e1;
+        unsigned o0[SCAN_TPT], o1[SCAN_TPT];
+#pragma unroll
+        for (int k = 0; k < SCAN_TPT; ++k) {
+            o0[k] = e0;
+            o1[k] = e1;
+            e0 += c[2 * k];
+            e1 += c[2 * k + 1];
+        }
+        if (whole) {
+            uint4* q0 = reinterpret_cast<uint4*>(offsets + t0);
+            uint4* q1 = reinterpret_cast<uint4*>(roffsets + t0);
+#pragma unroll
+            for (int k = 0; k < SCAN_TPT / 4; ++k) {
+                q0[k] = make_uint4(o0[4 * k], o0[4 * k + 1], o0[4 * k + 2], o0[4 * k + 3]);
+                q1[k] = make_uint4(o1[4 * k], o1[4 * k + 1], o1[4 * k + 2], o1[4 * k + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < SCAN_TPT; ++k)
+                if (t0 + k < ntiles) {
+                    offsets[t0 + k] = o0[k];
+                    roffsets[t0 + k] = o1[k];
+                }
         }
         __syncthreads();
-        if (threadIdx.x == 1023) {
-            carry[0] = e0 + v[0];
-            carry[1] = e1 + v[1];
+        if (threadIdx.x == 1023) {  // its running sums end at the round's totals
+            carry[0] = e0;
+            carry[1] = e1;
         }
         __syncthreads();
     }
