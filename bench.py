@@ -663,7 +663,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(total_ms / K, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "width": W, "height": Hh, "triangles": int(st.n_tris),
-                   "storage": "f16 normal/depth, bf16 colour, f32 elsewhere" if mixed else "f32",
+                   "storage": "f16 normal/depth, bf16 colour and post-filter records, f32 elsewhere" if mixed else "f32",
                    "spp_max": p0.spp_max, "r_max": p0.r_max,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single", "l2": "flushed between steps (256 MiB write)"},
         "mrays_per_s": round(mrays, 1), "mrays_per_s_concurrent": round(mrays_concurrent, 1),
@@ -684,7 +684,7 @@ def run_ours(args):
                                                   args.warmup, K, flush)
         mixed_ms = float(fm_m.mean())
         out["mixed"] = {"value": round(mixed_ms, 4), "unit": "ms/frame",
-                        "storage": "f16 normal/depth, bf16 colour, f32 elsewhere",
+                        "storage": "f16 normal/depth, bf16 colour and post-filter records, f32 elsewhere",
                         "speedup_vs_fp32": round(value / mixed_ms, 3),
                         "stages_ms": {n: round(float(v), 4) for n, v in zip(STAGES, sm_m.mean(0))},
                         "mrays_per_s": round(float(stm[:, 1].mean()) / (float(sm_m[:, 2].mean()) * 1e-3) / 1e6, 1)}

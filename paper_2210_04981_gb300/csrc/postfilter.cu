@@ -82,6 +82,18 @@ __device__ __forceinline__ float disk_area(float r) {
 // pixel feeds one layer only, so near and far are gathered in separate loops
 // with their own windows (in the workloads here the far field's blur is
 // small and the near field's large).
+// Layer records in the colour's precision: FP32 colour, float4 records; BF16
+// colour (the mixed form), BF16 records (8 bytes: a pair of taps in one
+// 128-bit load), accumulated in FP32 like the FP32 ones.
+template <class COL>
+struct RecOf {
+    using T = float4;
+};
+template <>
+struct RecOf<bf164s> {
+    using T = bf164s;
+};
+
 template <class ND, class COL>
 struct PrepArgs {
     const ND* nd;
@@ -92,8 +104,8 @@ struct PrepArgs {
     int ntx;
     float* rh;      // r + 1/2
     float* zq;      // view depth
-    float4* nrec;   // (c w/a, w/a), near layer
-    float4* frec;   // (c (1-w)/a, (1-w)/a), far layer
+    typename RecOf<COL>::T* nrec;  // (c w/a, w/a), near layer
+    typename RecOf<COL>::T* frec;  // (c (1-w)/a, (1-w)/a), far layer
     float4* tmax;   // per tile: (max r feeding near, max r feeding far, min r feeding near (+inf: none), 0)
     const float* lens;  // optional (focus distance, aperture radius) on the device, replacing coc's lens
     float t;            // tan(fovy / 2), with lens
@@ -115,8 +127,8 @@ __device__ __forceinline__ void pf_prep_body(const PrepArgs<ND, COL>& a, int bx,
         float4 col = ld4(a.col + q);
         a.rh[q] = r + 0.5f;
         a.zq[q] = z;
-        a.nrec[q] = make_float4(col.x * an, col.y * an, col.z * an, an);
-        a.frec[q] = make_float4(col.x * af, col.y * af, col.z * af, af);
+        st4(a.nrec + q, make_float4(col.x * an, col.y * an, col.z * an, an));
+        st4(a.frec + q, make_float4(col.x * af, col.y * af, col.z * af, af));
         rn = wn > 0.f ? r : -1.f;
         rf = wn < 1.f ? r : -1.f;
         rnmin = wn > 0.f ? r : INF;
@@ -145,17 +157,20 @@ __global__ void __launch_bounds__(256) k_pf_prep(PrepArgs<ND, COL> a) { pf_prep_
 // taps (all of weight exactly 1) as differences of it.  One block per row,
 // in rounds of 256 consecutive pixels (a block scan per round plus the
 // running total): the summation order is fixed.
-struct RowScanArgs {
-    const float4* nrec;  // row-major
+template <class REC>
+struct RowScanArgsT {
+    const REC* nrec;  // row-major
     int W, H;
     float4* pre;
 };
+using RowScanArgs = RowScanArgsT<float4>;
 
 __device__ __forceinline__ float4 add4(float4 a, float4 b) {
     return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
 
-__device__ __forceinline__ void pf_rowscan_body(const RowScanArgs& a, int y) {
+template <class REC>
+__device__ __forceinline__ void pf_rowscan_body(const RowScanArgsT<REC>& a, int y) {
     const int W = a.W, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const size_t row = (size_t)y * W;
     __shared__ float4 s_warp[8];
@@ -164,7 +179,7 @@ __device__ __forceinline__ void pf_rowscan_body(const RowScanArgs& a, int y) {
         const int x = x0 + t;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (x < W) {
-            v = __ldg(&a.nrec[row + x]);
+            v = ld4(a.nrec + row + x);
         }
         // inclusive warp scan, then the warps' totals
         for (int o = 1; o < 32; o <<= 1) {
@@ -184,7 +199,8 @@ __device__ __forceinline__ void pf_rowscan_body(const RowScanArgs& a, int y) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_pf_rowscan(RowScanArgs a) { pf_rowscan_body(a, blockIdx.x); }
+template <class REC>
+__global__ void __launch_bounds__(256) k_pf_rowscan(RowScanArgsT<REC> a) { pf_rowscan_body(a, blockIdx.x); }
 
 // Per target pixel: a layer's sums (S.x, S.y) and (S.z, W) as register
 // pairs so one packed FMA updates two of them; the far layer also holds its
@@ -237,8 +253,8 @@ template <class COL>
 struct GatherArgs {
     const float* rh;
     const float* zq;
-    const float4* nrec;
-    const float4* frec;
+    const typename RecOf<COL>::T* nrec;
+    const typename RecOf<COL>::T* frec;
     const COL* col;  // sharp colour (empty far layer)
     const float4* tmax;
     const float4* pre;  // row prefix of the near records
@@ -287,16 +303,26 @@ __device__ __forceinline__ void ld_rec_pair(const float4* p, float4& a, float4& 
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
         : "l"(p));
 }
+// two consecutive BF16 records (16 bytes, 16-byte aligned) in one 128-bit
+// load; a BF16 value is the high half of its FP32 bits
+__device__ __forceinline__ void ld_rec_pair(const bf164s* p, float4& a, float4& b) {
+    unsigned u0, u1, u2, u3;
+    asm("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(u0), "=r"(u1), "=r"(u2), "=r"(u3) : "l"(p));
+    a = make_float4(__uint_as_float(u0 << 16), __uint_as_float(u0 & 0xffff0000u), __uint_as_float(u1 << 16),
+                    __uint_as_float(u1 & 0xffff0000u));
+    b = make_float4(__uint_as_float(u2 << 16), __uint_as_float(u2 & 0xffff0000u), __uint_as_float(u3 << 16),
+                    __uint_as_float(u3 & 0xffff0000u));
+}
 
 // The taps of source row y from column xs to xe (inclusive) for the 2 x RY
 // block at (i, j).  Taps go in pairs (even, odd pixel index): one 256-bit
 // load of the two records and one float2 load of r + 1/2 (and z) per pair;
 // the threads of a row, two columns apart, read consecutive pairs.
-template <bool NEAR, bool MASK, class A>
+template <bool NEAR, bool MASK, class A, class REC>
 __device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF_RY], const float (&win2)[PF_RY],
                                            int xs, int xe, int i, int y, int W,
                                            const float* __restrict__ rh, const float* __restrict__ zq,
-                                           const float4* __restrict__ rec) {
+                                           const REC* __restrict__ rec) {
     const float2* __restrict__ rh2 = reinterpret_cast<const float2*>(rh);
     const float2* __restrict__ zq2 = reinterpret_cast<const float2*>(zq);
     float dx = (float)(xs - i);
@@ -307,7 +333,7 @@ __device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF
     const size_t gend = (size_t)y * W + xe + 1;
     if (g & 1) {  // an odd first tap on its own
         const float z = NEAR ? 0.f : __ldg(&zq[g]);
-        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[g]), z, __ldg(&rec[g]));
+        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[g]), z, ld4(rec + g));
         ++g;
         dx += 1.f;
     }
@@ -325,7 +351,7 @@ __device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF
     if (gend & 1) {  // an even last tap on its own
         const size_t gl = gend - 1;
         const float z = NEAR ? 0.f : __ldg(&zq[gl]);
-        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[gl]), z, __ldg(&rec[gl]));
+        pf_tap<MASK>(a, c, pdx2, dyk, win2, dx, __ldg(&rh[gl]), z, ld4(rec + gl));
     }
 }
 
@@ -340,10 +366,10 @@ __device__ __forceinline__ void pf_segment(A (&a)[PF_NPX], const float (&dyk)[PF
 // floor(sqrt(Rin^2 - dy^2)) are summed from the row prefix `pre` (two
 // loads); the columns inside every pixel's interior are skipped, the rest
 // are tapped with that interior masked out.
-template <bool NEAR, class A>
+template <bool NEAR, class A, class REC>
 __device__ __forceinline__ void pf_layer(A (&a)[PF_NPX], float R, float Rin, int i, int j, int W, int H,
                                          const float* __restrict__ rh, const float* __restrict__ zq,
-                                         const float4* __restrict__ rec, const float4* __restrict__ pre) {
+                                         const REC* __restrict__ rec, const float4* __restrict__ pre) {
     if (R < 0.f) return;  // nothing within reach feeds this layer
     // bounds lean outwards by 1e-3 pixel (float rounding); taps they add weigh 0
     const int G = (int)floorf(R + 1e-3f);
@@ -645,18 +671,24 @@ int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p,
                 PrepArgs<float4, float4>{nd4, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax, lens_dev, t});
         else if (f32n)
             k_pf_prep<<<grid, 256, 0, s>>>(
-                PrepArgs<float4, bf164s>{nd4, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax, lens_dev, t});
+                PrepArgs<float4, bf164s>{nd4, colb, W, H, coc, rm, ntx, w.rh, w.zq, reinterpret_cast<bf164s*>(w.nrec),
+                                              reinterpret_cast<bf164s*>(w.frec), w.tmax, lens_dev, t});
         else if (f32c)
             k_pf_prep<<<grid, 256, 0, s>>>(
                 PrepArgs<half4s, float4>{ndh, col4, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax, lens_dev, t});
         else
             k_pf_prep<<<grid, 256, 0, s>>>(
-                PrepArgs<half4s, bf164s>{ndh, colb, W, H, coc, rm, ntx, w.rh, w.zq, w.nrec, w.frec, w.tmax, lens_dev, t});
+                PrepArgs<half4s, bf164s>{ndh, colb, W, H, coc, rm, ntx, w.rh, w.zq, reinterpret_cast<bf164s*>(w.nrec),
+                                              reinterpret_cast<bf164s*>(w.frec), w.tmax, lens_dev, t});
         HDOF_LAUNCHED("post-filter prep");
     }
     {
         ProfScope ps_("pf_rowscan", s);
-        k_pf_rowscan<<<H, 256, 0, s>>>(RowScanArgs{w.nrec, W, H, w.pre});
+        if (f32c)
+            k_pf_rowscan<float4><<<H, 256, 0, s>>>(RowScanArgsT<float4>{w.nrec, W, H, w.pre});
+        else
+            k_pf_rowscan<bf164s><<<H, 256, 0, s>>>(
+                RowScanArgsT<bf164s>{reinterpret_cast<const bf164s*>(w.nrec), W, H, w.pre});
         HDOF_LAUNCHED("post-filter row prefix");
     }
     const int kt = gather_tiles(p->r_max);
@@ -671,7 +703,9 @@ int launch_postfilter(const hdof_gbuf* in, const Coc& coc, const hdof_params* p,
     } else {
         cudaFuncSetAttribute(k_pf_gather<bf164s>, cudaFuncAttributePreferredSharedMemoryCarveout, GATHER_CARVEOUT);
         k_pf_gather<bf164s><<<grid, GATHER_THREADS, 0, s>>>(
-            GatherArgs<bf164s>{w.rh, w.zq, w.nrec, w.frec, colb, w.tmax, w.pre, W, H, ntx, nty, kt, p->kz_rel, out,
+            GatherArgs<bf164s>{w.rh, w.zq, reinterpret_cast<const bf164s*>(w.nrec),
+                               reinterpret_cast<const bf164s*>(w.frec), colb, w.tmax, w.pre, W, H, ntx, nty, kt,
+                               p->kz_rel, out,
                                aux});
     }
     HDOF_LAUNCHED("post-filter gather");

@@ -1,6 +1,6 @@
-"""Mixed-precision storage (FP16 normal/depth, BF16 colour, FP32 accumulation,
-FP32 intersection and lens sampling) against the FP64 oracle, next to the
-FP32 plain form on the same inputs.
+"""Mixed-precision storage (FP16 normal/depth, BF16 colour and post-filter
+records, FP32 accumulation, FP32 intersection and lens sampling) against the
+FP64 oracle, next to the FP32 plain form on the same inputs.
 
 The bounds follow from the storage formats: FP16 keeps 11 significant bits
 (relative error <= 2^-11 ~ 4.9e-4 on normals and depth), BF16 keeps 8
