@@ -306,7 +306,11 @@ int hdof_mask_noalloc(const hdof_gbuf* in, const hdof_history* prev_hist, const 
  *   culling with its own hit: fast when the rays of neighbouring pixels stay
  *   close, i.e. for small lens apertures); 1..32 = ray level (one ray per
  *   lane; a warp fetches new rays for its idle lanes once fewer than this
- *   many of its 32 lanes still trace).
+ *   many of its 32 lanes still trace); -1 = each view in its default form:
+ *   warp packets when the view's CoC scale K = A H / (zf tan(fovy/2)) is
+ *   below 20 pixels, ray level with refill 4 otherwise (a batch traces the
+ *   two groups of views in two persistent launches, both of trace_block
+ *   threads).
  * trace_chunk, spatial_tile: launch granularity of the trace's work queue and
  *   of the batched spatial gather (see the fields).  No choice changes a
  *   result: each ray's closest hit and each pixel's gather are computed the
@@ -347,10 +351,11 @@ typedef struct hdof_tuning {
  * hdof_post_forward/backward re-evaluate at another focus and aperture;
  * rec holds stats[1] float4 entries (at most spp_max x W x H).
  * tune (host, may be NULL): the trace's form and block size (out-of-range
- * values are rejected with HDOF_EINVAL); NULL takes 128 threads and warp
- * packets when the lens's CoC scale K = A H / (zf tan(fovy/2)) is below 20
- * pixels (|c(z)| = K |zf/z - 1|: the lens rays of neighbouring pixels stay
- * close), ray level with refill 4 otherwise. */
+ * values are rejected with HDOF_EINVAL); NULL takes 128 threads and the
+ * default form (trace_refill -1): warp packets when the lens's CoC scale
+ * K = A H / (zf tan(fovy/2)) is below 20 pixels (|c(z)| = K |zf/z - 1|: the
+ * lens rays of neighbouring pixels stay close), ray level with refill 4
+ * otherwise. */
 int hdof_trace(const hdof_bvh* bvh, const hdof_camera* cam, const hdof_lens* lens,
                const hdof_params* p, const uint8_t* spp, const int32_t* hint_tri, float* rt,
                uint32_t* stats, float* rec, uint32_t* ray_off, void* workspace,
@@ -512,7 +517,8 @@ typedef struct hdof_batch hdof_batch;
 /* Prepares a batch: validates every view, builds each stage's per-view
  * launch records and block tables and copies them to device memory the
  * handle owns (synchronous).  The views' buffers must stay valid while the
- * handle is used.  tuning may be NULL (defaults 128 / 4).  Views with
+ * handle is used.  tuning may be NULL (128 threads,
+ * each view's trace in its default form: trace_refill -1).  Views with
  * shaped bokeh or spec_pref != 0 return HDOF_EUNSUPPORTED (specular
  * materials themselves are shaded as in the single-view calls). */
 int hdof_batch_create(const hdof_view* views, int32_t n_views, const hdof_tuning* tuning, hdof_batch** out,

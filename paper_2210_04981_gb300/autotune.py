@@ -3,8 +3,10 @@
 The batched frame has free choices that change its speed but not its
 results (hdof_tuning): the persistent trace's block size (64, 128 or 256
 threads) and form (warp packets, refill 0: a warp traverses for 32 coherent
-rays at once; or ray level with a refill threshold: a warp fetches new rays
-for its idle lanes once fewer than that many lanes still trace, 4 or 8), the
+rays at once; ray level with a refill threshold: a warp fetches new rays for
+its idle lanes once fewer than that many lanes still trace, 4 or 8; or each
+view in its default form, refill -1: packets for the views with a small CoC
+scale, ray level for the others, in two launches), the
 trace's queue chunk (how many packets, or rays in units of 32, a warp claims
 per atomic) and the spatial reconstruction's stencil tile (8x8 or 16x16
 pixels per block).  Every candidate renders bit-identical images, so the
@@ -26,7 +28,7 @@ import torch
 
 from . import hdof as H
 
-CANDIDATES = tuple((b, c) for b in (64, 128, 256) for c in (0, 4, 8))  # (trace_block, trace_refill)
+CANDIDATES = tuple((b, c) for b in (64, 128, 256) for c in (-1, 0, 4, 8))  # (trace_block, trace_refill)
 CHUNKS = (0, 2, 4)      # trace_chunk
 TILES = (8, 16)         # spatial_tile
 

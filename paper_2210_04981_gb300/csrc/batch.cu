@@ -122,7 +122,7 @@ Layout layout(int n) {
     L.zero = b;
     b = align256(b + (size_t)n * sizeof(ZeroRec));
     L.gq = b;
-    L.bytes = align256(b + (size_t)(n + 2) * sizeof(unsigned));
+    L.bytes = align256(b + (size_t)(2 * n + 4) * sizeof(unsigned));
     return L;
 }
 
@@ -181,7 +181,7 @@ struct hdof_batch {
     } stage[hdof::N_STAGES];
     const void* scan_args;
     const hdof::ZeroRec* zero;
-    unsigned* gq;  // [n + 2] queue prefix, total, head
+    unsigned* gq;  // [2 n + 4] ray prefix, total, head; with per-view forms a second one for the ray-level views
     hdof::Layout L;
     char* host;              // pinned host image of the records (hdof_batch_update)
     cudaEvent_t uploaded;    // last upload of the host image
@@ -200,11 +200,11 @@ extern "C" int hdof_batch_create(const hdof_view* views, int32_t n_views, const 
     *out = nullptr;
     HDOF_CHECK_ARG(views && n_views >= 1 && n_views <= 65536, "hdof_batch_create: need 1..65536 views, got %d",
                    (int)n_views);
-    hdof_tuning t = {128, 4, 0, 0};
+    hdof_tuning t = {128, -1, 0, 0};  // each view's trace in its default form
     if (tuning) t = *tuning;
     HDOF_CHECK_ARG(t.trace_block == 64 || t.trace_block == 128 || t.trace_block == 256,
                    "hdof_batch_create: trace_block %d not in {64, 128, 256}", (int)t.trace_block);
-    HDOF_CHECK_ARG(t.trace_refill >= 0 && t.trace_refill <= 32, "hdof_batch_create: trace_refill %d not in 0..32",
+    HDOF_CHECK_ARG(t.trace_refill >= -1 && t.trace_refill <= 32, "hdof_batch_create: trace_refill %d not in -1..32",
                    (int)t.trace_refill);
     HDOF_CHECK_ARG(t.trace_chunk >= 0 && t.trace_chunk <= 16, "hdof_batch_create: trace_chunk %d not in 0..16",
                    (int)t.trace_chunk);

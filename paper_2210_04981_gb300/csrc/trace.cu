@@ -22,6 +22,16 @@
 #include "internal.h"
 
 namespace hdof {
+
+// default form of a view's trace: warp packets below this CoC scale K =
+// A H / (zf tan(fovy/2)) (pixels of CoC per unit of zf/z - 1), ray level with
+// refill 4 above
+constexpr float PACKET_K_MAX = 20.f;
+static bool packet_view(const hdof_lens& l, const hdof_camera& c) {
+    const float K = l.aperture_radius * (float)c.height / (l.focus_dist * c.tan_half_fovy);
+    return K < PACKET_K_MAX;
+}
+
 namespace {
 
 constexpr int TB = 16;  // compaction tile edge
@@ -268,6 +278,7 @@ struct TraceArgs {
     float aberration;        // sample weight 1 + aberration (2 rho^2 / A^2 - 1)
     uint2 key;
     int cap, smax;
+    int packets;  // the view's default form is warp packets (packet_view)
     unsigned* status;
     const uint8_t* spp;
     const int* hint;   // optional per-pixel original id of the primary hit (< 0: none)
@@ -736,6 +747,7 @@ TraceArgs trace_args(const hdof_bvh* b, const hdof_camera* cam, const hdof_lens*
     a.key = make_uint2(p->seed, (unsigned)p->view * 65536u + (unsigned)p->frame);
     a.cap = p->trav_cap > 0 ? p->trav_cap : 64 * (b->n_nodes + b->n_tris) + 64;
     a.smax = p->spp_max;
+    a.packets = packet_view(*lens, *cam) ? 1 : 0;
     a.status = st;
     a.spp = spp;
     a.hint = hint;
@@ -772,9 +784,11 @@ __global__ void __launch_bounds__(256) k_resolve_batch(const TraceArgs* __restri
 
 // exclusive prefix of the views' ray counts: gq[v] is the first ray of view
 // v in the concatenated ray list, gq[n] the total; gq[n + 1] (the shared
-// fetch head) is reset.  One block.
-__global__ void __launch_bounds__(1024) k_ray_prefix(const ScanArgs* __restrict__ a, int n,
-                                                     unsigned* __restrict__ gq) {
+// fetch head) is reset.  cls >= 0: only the views whose default form is
+// warp packets (1) or ray level (0) count, the others hold no rays.  One
+// block.
+__global__ void __launch_bounds__(1024) k_ray_prefix(const ScanArgs* __restrict__ a, const TraceArgs* __restrict__ tab,
+                                                     int n, int cls, unsigned* __restrict__ gq) {
     __shared__ unsigned wsum[32];
     __shared__ unsigned carry;
     if (threadIdx.x == 0) carry = 0;
@@ -782,7 +796,7 @@ __global__ void __launch_bounds__(1024) k_ray_prefix(const ScanArgs* __restrict_
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < n; base += 1024) {
         int v = base + threadIdx.x;
-        unsigned c = v < n ? __ldcg(&a[v].totals[2]) : 0u, x = c;
+        unsigned c = v < n && (cls < 0 || tab[v].packets == cls) ? __ldcg(&a[v].totals[2]) : 0u, x = c;
         for (int o = 1; o < 32; o <<= 1) {
             unsigned y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
@@ -889,13 +903,48 @@ void trace_fill(const hdof_view& v, const ViewWs& w, unsigned* st, void* dst, in
     *gx = (v.cam.width * v.cam.height + 255) / 256;  // resolve: one thread per possible queue entry
     *gy = 1;
 }
-int trace_batch_grid(int block, int refill, int* blocks) { return rays_grid(true, refill == 0, block, blocks); }
+int trace_batch_grid(int block, int refill, int* blocks) {
+    if (refill == -1) {  // both forms run: the ray-level grid is cached for the launch
+        int r = 0, rc = rays_grid(true, false, block, &r);
+        if (rc) return rc;
+    }
+    return rays_grid(true, refill <= 0, block, blocks);
+}
 
 int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid resolve, int resolve_blocks, int n,
                        unsigned* gq, int block, int refill, int chunk, int blocks, cudaStream_t s) {
-    k_ray_prefix<<<1, 1024, 0, s>>>(static_cast<const ScanArgs*>(scan_args), n, gq);
-    HDOF_LAUNCHED("batched trace: ray prefix");
+    const ScanArgs* sa = static_cast<const ScanArgs*>(scan_args);
     const TraceArgs* a = static_cast<const TraceArgs*>(trace_args);
+    if (refill == -1) {
+        // each view in its default form: the packet views' rays in one list
+        // (prefix gq, head gq[n + 1]), the ray-level views' in another (gq2)
+        unsigned* gq2 = gq + n + 2;
+        int rblocks = 0, rc = rays_grid(true, false, block, &rblocks);
+        if (rc) return rc;
+        k_ray_prefix<<<1, 1024, 0, s>>>(sa, a, n, 1, gq);
+        k_ray_prefix<<<1, 1024, 0, s>>>(sa, a, n, 0, gq2);
+        HDOF_LAUNCHED("batched trace: ray prefixes");
+        {
+            ProfScope ps_("batch_trace_packets", s);
+            if (block == 64) k_trace_packets_batch<64><<<blocks, 64, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+            else if (block == 256) k_trace_packets_batch<256><<<blocks, 256, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+            else k_trace_packets_batch<128><<<blocks, 128, 0, s>>>(a, gq, n, gq + n + 1, chunk);
+            HDOF_LAUNCHED("batched trace: packet views");
+        }
+        {
+            ProfScope ps_("batch_trace_rays", s);
+            if (block == 64) k_trace_rays_batch<64><<<rblocks, 64, 0, s>>>(a, gq2, n, gq2 + n + 1, 4, chunk);
+            else if (block == 256) k_trace_rays_batch<256><<<rblocks, 256, 0, s>>>(a, gq2, n, gq2 + n + 1, 4, chunk);
+            else k_trace_rays_batch<128><<<rblocks, 128, 0, s>>>(a, gq2, n, gq2 + n + 1, 4, chunk);
+            HDOF_LAUNCHED("batched trace: ray-level views");
+        }
+        ProfScope ps_("batch_trace_resolve", s);
+        k_resolve_batch<<<resolve_blocks, 256, 0, s>>>(a, resolve);
+        HDOF_LAUNCHED("batched trace: resolve");
+        return HDOF_OK;
+    }
+    k_ray_prefix<<<1, 1024, 0, s>>>(sa, a, n, -1, gq);
+    HDOF_LAUNCHED("batched trace: ray prefix");
     {
         ProfScope ps_(refill == 0 ? "batch_trace_packets" : "batch_trace_rays", s);
         if (refill == 0) {  // warp packets
@@ -918,10 +967,6 @@ int trace_launch_batch(const void* scan_args, const void* trace_args, BatchGrid 
 }  // namespace hdof
 
 using namespace hdof;
-
-// default form of the single-view trace: warp packets below this CoC scale
-// (pixels of CoC per unit of zf/z - 1), ray level with refill 4 above
-constexpr float PACKET_K_MAX = 20.f;
 
 template <int BS>
 void launch_trace(const TraceArgs& a, int refill, int chunk, int blocks, cudaStream_t s) {
@@ -946,15 +991,15 @@ extern "C" int hdof_trace(const hdof_bvh* b, const hdof_camera* cam, const hdof_
         t = *tune;
         HDOF_CHECK_ARG(t.trace_block == 64 || t.trace_block == 128 || t.trace_block == 256,
                        "hdof_trace: trace_block %d not in {64, 128, 256}", (int)t.trace_block);
-        HDOF_CHECK_ARG(t.trace_refill >= 0 && t.trace_refill <= 32, "hdof_trace: trace_refill %d not in 0..32",
+        HDOF_CHECK_ARG(t.trace_refill >= -1 && t.trace_refill <= 32, "hdof_trace: trace_refill %d not in -1..32",
                        (int)t.trace_refill);
         HDOF_CHECK_ARG(t.trace_chunk >= 0 && t.trace_chunk <= 16, "hdof_trace: trace_chunk %d not in 0..16",
                        (int)t.trace_chunk);
     } else {
-        const float K = lens->aperture_radius * (float)cam->height / (lens->focus_dist * cam->tan_half_fovy);
         t.trace_block = 128;
-        t.trace_refill = K < PACKET_K_MAX ? 0 : 4;
+        t.trace_refill = -1;
     }
+    if (t.trace_refill == -1) t.trace_refill = packet_view(*lens, *cam) ? 0 : 4;
     const int W = cam->width, H = cam->height;
     WsLayout L = ws_layout(W, H, p);
     HDOF_CHECK_ARG(workspace && workspace_bytes >= L.trace, "hdof_trace: workspace of %zu bytes < %zu",

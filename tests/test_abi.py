@@ -102,7 +102,9 @@ def test_invalid_arguments_rejected_before_launch(H):
     assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(96, 1)), C.byref(h), None) == -1
     lib.hdof_last_error(buf, 256)
     assert b"trace_block" in buf.value
-    assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(128, -1)), C.byref(h), None) == -1
+    assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(128, -2)), C.byref(h), None) == -1
+    lib.hdof_last_error(buf, 256)
+    assert b"trace_refill" in buf.value
     assert lib.hdof_batch_create(views, 1, C.byref(H.tuning(128, 33)), C.byref(h), None) == -1
     assert lib.hdof_batch_render(None, None) == -1
     assert lib.hdof_batch_update(None, views, 1, None) == -1

@@ -84,6 +84,31 @@ def test_batch_equals_single_view(small, block, refill, chunk, tile):
     b.close()
 
 
+def test_batch_per_view_forms_equal_single_view(small):
+    """trace_refill -1: the views whose CoC scale K = A H / (zf tan(fovy/2))
+    is below 20 pixels are traced as warp packets and the others at ray
+    level, in two persistent launches over two ray lists; every view equals
+    its single-view calls bit for bit."""
+    import dataclasses
+    scenes, bvhs, views = small
+    wide = hi.Lens(1.0, 0.1, hi.ROOM_FOCAL).f32()
+    views = [dataclasses.replace(v, lens=wide) if k % 2 else v for k, v in enumerate(views)]
+    t = views[0].camera(0).tan_half_fovy
+    K = [v.lens.aperture_radius * v.height / (v.lens.focus_dist * t) for v in views]
+    assert any(k < 20 for k in K) and any(k >= 20 for k in K), K
+    rs = _singles(bvhs, views)
+    b = H.Batch([bvhs[v.room] for v in views], [(v.width, v.height) for v in views], [v.params for v in views],
+                tune=H.tuning(128, -1, 0, 8))
+    for k in range(3):
+        _run_singles(rs, views, k)
+        b.frame(*_frame_args(views, k))
+        H.hdof_sync()
+        assert sum(int(r.stats[1]) for r, kk in zip(rs, K) if kk >= 20) > 0  # the ray-level list is not empty
+        for i, (r, rb) in enumerate(zip(rs, b.views)):
+            _assert_same(r, rb, f"frame {k} view {i} (K {K[i]:.1f})")
+    b.close()
+
+
 def test_batch_graph_replay(small):
     """render() captured once in a CUDA graph; each frame rewrites the launch
     records (update) and replays the graph."""

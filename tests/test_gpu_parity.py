@@ -433,7 +433,7 @@ def test_trace_rejects_bad_tuning():
     bvh = bvh_of(scene)
     spp = dev(np.ones((128, 128), np.uint8))
     rt = torch.zeros((128, 128, 12), dtype=torch.float32, device="cuda")
-    for t in (H.tuning(96, 0), H.tuning(128, -1), H.tuning(128, 33)):
+    for t in (H.tuning(96, 0), H.tuning(128, -2), H.tuning(128, 33)):
         with pytest.raises(H.HdofError):
             H.hdof_trace(bvh, cam, lens, p, spp, rt, None, workspace(128, 128, p), tune=t)
 
