@@ -322,6 +322,7 @@ __global__ void k_depth(const int* __restrict__ leaf_parent, const Node* __restr
 #endif
 constexpr int PLOC_R = HDOF_PLOC_R;
 constexpr int PLOC_B = 256;
+constexpr int PLOC_SYNC = 8;  // clustering rounds between reads of the cluster count
 
 __device__ __forceinline__ float union_area(float4 alo, float4 ahi, float4 blo, float4 bhi) {
     float x = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
@@ -342,8 +343,21 @@ __global__ void k_ploc_init(const float* __restrict__ v, const int* __restrict__
     hgt[i] = 0;
 }
 
-__global__ void __launch_bounds__(PLOC_B) k_ploc_nn(int N, const float4* __restrict__ lo, const float4* __restrict__ hi,
-                                                    int* __restrict__ nn) {
+// Round control of the clustering on the device, so that the host need not
+// read the cluster count back every round: ctl[0] = live clusters N, ctl[1] =
+// pair neighbours this round (the last round found no mutual pair), ctl[2] =
+// the buffer holding the clusters.  The round kernels are launched over an
+// upper bound Nb >= N and do nothing once N <= 1.
+__global__ void k_ploc_ctl_init(int* ctl, int n) {
+    ctl[0] = n;
+    ctl[1] = 0;
+    ctl[2] = 0;
+}
+
+__global__ void __launch_bounds__(PLOC_B) k_ploc_nn(const int* __restrict__ ctl, const float4* __restrict__ lo,
+                                                    const float4* __restrict__ hi, int* __restrict__ nn) {
+    const int N = ctl[0];
+    if (N <= 1 || ctl[1]) return;  // done, or pairing neighbours: the whole block leaves
     __shared__ float4 slo[PLOC_B + 2 * PLOC_R], shi[PLOC_B + 2 * PLOC_R];
     const int base = blockIdx.x * PLOC_B - PLOC_R;
     for (int k = threadIdx.x; k < PLOC_B + 2 * PLOC_R; k += PLOC_B) {
@@ -372,11 +386,18 @@ __global__ void __launch_bounds__(PLOC_B) k_ploc_nn(int N, const float4* __restr
     nn[i] = bj;
 }
 
-// merge mutual nearest neighbours (or, when force_pairs, positions 2k and 2k+1)
-__global__ void k_ploc_merge(int N, const int* __restrict__ nn, int force_pairs, int* ref, float4* lo, float4* hi,
-                             int* hgt, int* valid, Node* nodes, unsigned* counter) {
+// merge mutual nearest neighbours (or, when force_pairs, positions 2k and 2k+1);
+// positions N .. Nb - 1 are marked invalid for the scan
+__global__ void k_ploc_merge(int Nb, const int* __restrict__ ctl, const int* __restrict__ nn, int* ref, float4* lo,
+                             float4* hi, int* hgt, int* valid, Node* nodes, unsigned* counter) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i >= Nb) return;
+    const int N = ctl[0], force_pairs = ctl[1];
+    if (N <= 1) return;
+    if (i >= N) {
+        valid[i] = 0;
+        return;
+    }
     int j = force_pairs ? ((i & 1) ? i - 1 : (i + 1 < N ? i + 1 : -1)) : nn[i];
     bool mutual = j >= 0 && (force_pairs || nn[j] == i);
     if (!mutual) {
@@ -402,17 +423,29 @@ __global__ void k_ploc_merge(int N, const int* __restrict__ nn, int force_pairs,
     valid[i] = 1;
 }
 
-__global__ void k_ploc_compact(int N, const int* __restrict__ valid, const int* __restrict__ pos,
-                               const int* __restrict__ ref, const float4* __restrict__ lo,
+__global__ void k_ploc_compact(int Nb, const int* __restrict__ ctl, const int* __restrict__ valid,
+                               const int* __restrict__ pos, const int* __restrict__ ref, const float4* __restrict__ lo,
                                const float4* __restrict__ hi, const int* __restrict__ hgt, int* ref2, float4* lo2,
                                float4* hi2, int* hgt2) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || !valid[i]) return;
+    if (i >= Nb) return;
+    const int N = ctl[0];
+    if (N <= 1 || i >= N || !valid[i]) return;
     int k = pos[i];
     ref2[k] = ref[i];
     lo2[k] = lo[i];
     hi2[k] = hi[i];
     hgt2[k] = hgt[i];
+}
+
+// the next round's N and mode, and the buffer the compaction filled (dst)
+__global__ void k_ploc_next(int* ctl, const int* __restrict__ valid, const int* __restrict__ pos, int dst) {
+    const int N = ctl[0];
+    if (N <= 1) return;
+    const int nN = pos[N - 1] + valid[N - 1];
+    ctl[1] = nN == N;  // no mutual pair this round: pair neighbours once
+    ctl[0] = nN;
+    ctl[2] = dst;
 }
 
 __global__ void k_big_boxes(const Tri* __restrict__ tris, int first, int n_big, float4* box) {
@@ -785,7 +818,7 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
         size_t o_hi1 = o_hi0 + up256(16 * (size_t)m), o_h0 = o_hi1 + up256(16 * (size_t)m);
         size_t o_h1 = o_h0 + up256(4 * (size_t)m), o_nn = o_h1 + up256(4 * (size_t)m);
         size_t o_val = o_nn + up256(4 * (size_t)m), o_pos = o_val + up256(4 * (size_t)m);
-        size_t o_scan = o_pos + up256(4 * (size_t)m), ptotal = o_scan + scan_bytes;
+        size_t o_ctl = o_pos + up256(4 * (size_t)m), o_scan = o_ctl + 256, ptotal = o_scan + scan_bytes;
         void* pt = nullptr;
         if ((e = cudaMalloc(&pt, ptotal)) != cudaSuccess) return fail(cuda_fail(e, "hdof_build_bvh: cudaMalloc"));
         char* c8 = static_cast<char*>(pt);
@@ -796,6 +829,7 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
         int* nn = reinterpret_cast<int*>(c8 + o_nn);
         int* valid = reinterpret_cast<int*>(c8 + o_val);
         int* pos = reinterpret_cast<int*>(c8 + o_pos);
+        int* ctl = reinterpret_cast<int*>(c8 + o_ctl);
         void* scan_tmp = c8 + o_scan;
         auto pfail = [&](int code) {
             cudaStreamSynchronize(s);
@@ -805,33 +839,42 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
         if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned), s)) != cudaSuccess)
             return pfail(cuda_fail(e, "hdof_build_bvh: clear"));
         k_ploc_init<<<blocks_for(m, 256), 256, 0, s>>>(verts, idx, ids_out, m, ref[0], lo[0], hi[0], hgt[0]);
-        int N = m, cur = 0, rounds = 0, force = 0;
-        while (N > 1) {
-            if (++rounds > 100000) {
+        k_ploc_ctl_init<<<1, 1, 0, s>>>(ctl, m);
+        // rounds run in batches of PLOC_SYNC with the cluster count kept on the
+        // device; the host reads it between batches for a tighter launch bound
+        int Nb = m, cur = 0, rounds = 0, buf = 0;
+        while (true) {
+            for (int r = 0; r < PLOC_SYNC; ++r) {
+                k_ploc_nn<<<blocks_for(Nb, PLOC_B), PLOC_B, 0, s>>>(ctl, lo[cur], hi[cur], nn);
+                k_ploc_merge<<<blocks_for(Nb, 256), 256, 0, s>>>(Nb, ctl, nn, ref[cur], lo[cur], hi[cur], hgt[cur],
+                                                                valid, b->nodes, counters);
+                e = cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, valid, pos, Nb, s);
+                if (e != cudaSuccess) return pfail(cuda_fail(e, "hdof_build_bvh: scan"));
+                k_ploc_compact<<<blocks_for(Nb, 256), 256, 0, s>>>(Nb, ctl, valid, pos, ref[cur], lo[cur], hi[cur],
+                                                                  hgt[cur], ref[1 - cur], lo[1 - cur], hi[1 - cur],
+                                                                  hgt[1 - cur]);
+                k_ploc_next<<<1, 1, 0, s>>>(ctl, valid, pos, 1 - cur);
+                cur = 1 - cur;
+            }
+            rounds += PLOC_SYNC;
+            int c[3];
+            if ((e = cudaGetLastError()) != cudaSuccess ||
+                (e = cudaMemcpyAsync(c, ctl, sizeof c, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(s)) != cudaSuccess)
+                return pfail(cuda_fail(e, "hdof_build_bvh: clustering"));
+            if (c[0] <= 1) {
+                buf = c[2];
+                break;
+            }
+            if (rounds > 100000) {
                 set_error("hdof_build_bvh: clustering did not converge");
                 return pfail(HDOF_ECUDA);
             }
-            if (!force) k_ploc_nn<<<blocks_for(N, PLOC_B), PLOC_B, 0, s>>>(N, lo[cur], hi[cur], nn);
-            k_ploc_merge<<<blocks_for(N, 256), 256, 0, s>>>(N, nn, force, ref[cur], lo[cur], hi[cur], hgt[cur], valid,
-                                                           b->nodes, counters);
-            e = cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, valid, pos, N, s);
-            if (e != cudaSuccess) return pfail(cuda_fail(e, "hdof_build_bvh: scan"));
-            k_ploc_compact<<<blocks_for(N, 256), 256, 0, s>>>(N, valid, pos, ref[cur], lo[cur], hi[cur], hgt[cur],
-                                                             ref[1 - cur], lo[1 - cur], hi[1 - cur], hgt[1 - cur]);
-            int last[2];
-            if ((e = cudaGetLastError()) != cudaSuccess ||
-                (e = cudaMemcpyAsync(&last[0], pos + N - 1, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(&last[1], valid + N - 1, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-                (e = cudaStreamSynchronize(s)) != cudaSuccess)
-                return pfail(cuda_fail(e, "hdof_build_bvh: clustering"));
-            int nN = last[0] + last[1];
-            force = (nN == N);  // no mutual pair this round: pair neighbours once
-            N = nN;
-            cur = 1 - cur;
+            Nb = c[0];
         }
         int root_ref = 0, h = 0;
-        if ((e = cudaMemcpyAsync(&root_ref, ref[cur], sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(&h, hgt[cur], sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        if ((e = cudaMemcpyAsync(&root_ref, ref[buf], sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&h, hgt[buf], sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return pfail(cuda_fail(e, "hdof_build_bvh: clustering"));
         cudaFree(pt);
