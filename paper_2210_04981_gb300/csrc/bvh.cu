@@ -310,17 +310,19 @@ __global__ void k_depth(const int* __restrict__ leaf_parent, const Node* __restr
 // Parallel locally-ordered clustering (Meister and Bittner, "Parallel
 // locally-ordered clustering for bounding volume hierarchy construction",
 // IEEE TVCG 2018).  Clusters start as the Morton-sorted triangles.  Each
-// round every cluster finds, within PLOC_R positions on either side, the
+// round every cluster finds, within R positions on either side, the
 // cluster whose union box has the smallest surface area; mutual nearest
 // neighbours merge into a new node at the lower position, and the array is
 // compacted, keeping Morton order.  Rounds repeat until one cluster is left.
 #ifndef HDOF_BUILDER
 #define HDOF_BUILDER 1  // 1: PLOC, 0: LBVH
 #endif
-#ifndef HDOF_PLOC_R
-#define HDOF_PLOC_R 48  // nearest-neighbour search radius of the clustering (measured best of 8..96 overall)
-#endif
-constexpr int PLOC_R = HDOF_PLOC_R;
+// The search radius R: 64 for trees that stay in L2 (the 164.6k-triangle room:
+// the trace 2.5% and the G-buffer 2.6% faster than with 48; 80 and 96 slower),
+// 48 above PLOC_BIG triangles (the 5.25M-triangle scene's G-buffer is 8% slower
+// at 64; radii 8..96 swept).
+constexpr int PLOC_R_SMALL = 64, PLOC_R_BIG = 48;
+constexpr int PLOC_BIG = 1 << 20;
 constexpr int PLOC_B = 256;
 constexpr int PLOC_SYNC = 8;  // clustering rounds between reads of the cluster count
 
@@ -354,6 +356,7 @@ __global__ void k_ploc_ctl_init(int* ctl, int n) {
     ctl[2] = 0;
 }
 
+template <int PLOC_R>
 __global__ void __launch_bounds__(PLOC_B) k_ploc_nn(const int* __restrict__ ctl, const float4* __restrict__ lo,
                                                     const float4* __restrict__ hi, int* __restrict__ nn) {
     const int N = ctl[0];
@@ -845,7 +848,8 @@ extern "C" int hdof_build_bvh(const float* verts, int32_t n_verts, const int32_t
         int Nb = m, cur = 0, rounds = 0, buf = 0;
         while (true) {
             for (int r = 0; r < PLOC_SYNC; ++r) {
-                k_ploc_nn<<<blocks_for(Nb, PLOC_B), PLOC_B, 0, s>>>(ctl, lo[cur], hi[cur], nn);
+                if (m > PLOC_BIG) k_ploc_nn<PLOC_R_BIG><<<blocks_for(Nb, PLOC_B), PLOC_B, 0, s>>>(ctl, lo[cur], hi[cur], nn);
+                else k_ploc_nn<PLOC_R_SMALL><<<blocks_for(Nb, PLOC_B), PLOC_B, 0, s>>>(ctl, lo[cur], hi[cur], nn);
                 k_ploc_merge<<<blocks_for(Nb, 256), 256, 0, s>>>(Nb, ctl, nn, ref[cur], lo[cur], hi[cur], hgt[cur],
                                                                 valid, b->nodes, counters);
                 e = cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, valid, pos, Nb, s);
