@@ -318,7 +318,7 @@ __global__ void k_depth(const int* __restrict__ leaf_parent, const Node* __restr
 #define HDOF_BUILDER 1  // 1: PLOC, 0: LBVH
 #endif
 // The search radius R: 64 for trees that stay in L2 (the 164.6k-triangle room:
-// the trace 2.5% and the G-buffer 2.6% faster than with 48; 80 and 96 slower),
+// the trace 2.5% and the G-buffer 2.6% faster than with 48; 56, 72, 80, 96 slower),
 // 48 above PLOC_BIG triangles (the 5.25M-triangle scene's G-buffer is 8% slower
 // at 64; radii 8..96 swept).
 constexpr int PLOC_R_SMALL = 64, PLOC_R_BIG = 48;
