@@ -893,7 +893,9 @@ def run_batch(args):
         "plain_ms": res["plain_ms"], "speedup_vs_plain": res["speedup_vs_plain"],
         "mrays_per_s_frame": res["mrays_per_s_frame"], "mrays_per_s_trace": res["mrays_per_s_trace"],
         "rays_per_frame": rays, "traced_px_per_frame": res["traced_px_per_frame"], "stages": stage_ms,
-        "bvh_build_ms": res["bvh_build_ms"], "roofline": roof, "e2e": res["e2e"], "gpu_launches": 16 * K,
+        "bvh_build_ms": res["bvh_build_ms"], "roofline": roof, "e2e": res["e2e"],
+        # 16 launches per batched frame, 18 when each view's trace takes its default form (two trace launches)
+        "gpu_launches": (18 if res["tuning"]["trace_refill"] == -1 else 16) * K,
         "clocks": res["clocks"],
     }
     if rank == 0:

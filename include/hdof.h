@@ -536,7 +536,9 @@ int hdof_batch_update(hdof_batch* batch, const hdof_view* views, int32_t n_views
 size_t hdof_batch_bytes(const hdof_batch* batch);
 /* Enqueues the frame of every view of the batch: one launch per stage over
  * all views' blocks (G-buffer, mask, compaction, one persistent trace over
- * the concatenated ray queues, post-filter, reconstruction, composite).
+ * the concatenated ray queues -- two, one per form, when each view takes
+ * its default form (trace_refill -1) -- post-filter, reconstruction,
+ * composite).
  * The frame is forked from `stream` onto two streams the handle owns: the
  * critical path (highest priority) and the post-filter (lowest), forked
  * after the G-buffer and joined before the composite, so the post-filter
@@ -551,7 +553,7 @@ enum {
     HDOF_STAGE_GBUFFER = 0,     /* 1 launch */
     HDOF_STAGE_MASK = 1,        /* tile clear, edge, spp: 3 launches */
     HDOF_STAGE_COMPACT = 2,     /* count, scan, scatter: 3 launches */
-    HDOF_STAGE_TRACE = 3,       /* ray prefix, persistent trace, resolve: 3 launches */
+    HDOF_STAGE_TRACE = 3,       /* ray prefix, persistent trace, resolve: 3 launches (5 with per-view forms) */
     HDOF_STAGE_POSTFILTER = 4,  /* prep, row prefix, gather: 3 launches */
     HDOF_STAGE_RECONSTRUCT = 5, /* temporal, spatial: 2 launches */
     HDOF_STAGE_COMPOSITE = 6,   /* 1 launch */
