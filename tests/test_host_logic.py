@@ -44,6 +44,26 @@ def test_autotune_picks_fastest_and_caches(tmp_path, monkeypatch):
     assert autotune.signature(shape, "a") == autotune.signature([tuple(v) for v in shape], "a")
 
 
+def test_autotune_takes_per_view_forms_when_fastest(tmp_path, monkeypatch):
+    """Each view in its default trace form (trace_refill -1: packets for the
+    narrow-lens views, ray level for the others) is a candidate of the first
+    stage at every block size and wins when it times fastest."""
+    from paper_2210_04981_gb300 import autotune
+    monkeypatch.setenv("HDOF_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "test-gpu")
+    monkeypatch.setattr(autotune, "workload_shape", lambda b: [(640, 480, 100000, 16, 32.0)])
+    assert {(b, -1) for b in (64, 128, 256)} <= set(autotune.CANDIDATES)
+
+    def fake_time(batch, frame_args, shape, reps=5, warmup=2):
+        block, refill, chunk, tile = shape
+        return (0.5 if refill == -1 else 1.0) + (block != 256) / 8.0 + chunk / 64.0 + (tile == 16) / 32.0
+
+    monkeypatch.setattr(autotune, "time_shape", fake_time)
+    t, _ = autotune.tune(object(), None)
+    assert (t.trace_block, t.trace_refill, t.trace_chunk, t.spatial_tile) == (256, -1, 0, 8)
+
+
+
 def _rank(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
                       LOCAL_RANK=str(rank))
