@@ -477,6 +477,32 @@ def post_forward(col, z, spp, rec, off, hs, cam_, lens_, params_, pp_pix=None):
     return dict(rt=rt, crt=crt, hacc=hacc, mom=mom, hlen=hlen, crec=crec, pp=pp, out=out)
 
 
+def post_colour_vjp(col, z, spp, rec, off, hs, cam_, lens_, params_, g):
+    """J^T g for J = d out[..., :3] / d col of post_forward (the gradient of
+    sum(out * g) in the sharp colour image), by the definition of the
+    Jacobian.  For a fixed lens the map is affine in col (every weight
+    depends on depth, CoC and the frozen radiance only), so the column of
+    pixel q is out(col + e_q) - out(col) exactly, up to FP64 rounding; every
+    weight is one scalar for the three channels, so a unit step on all three
+    channels of q gives its three columns at once.  H W + 1 forward maps:
+    small images only."""
+    col = np.asarray(col, np.float64)
+    g = np.asarray(g, np.float64)
+    H, W = np.asarray(spp).shape
+
+    def out(c):
+        return post_forward(c, z, spp, rec, off, hs, cam_, lens_, params_)["out"][..., :3]
+
+    base = out(col)
+    vjp = np.zeros((H, W, 3))
+    for j in range(H):
+        for i in range(W):
+            c = col.copy()
+            c[j, i, :] += 1.0
+            vjp[j, i, :] = ((out(c) - base) * g).sum(axis=(0, 1))
+    return vjp
+
+
 def disk_area(r: float) -> float:
     return lib().orc_disk_area(float(r))
 

@@ -108,6 +108,48 @@ def test_colour_gradient_is_the_adjoint(orc):
     assert abs(ref - rhs) <= 1e-3 * abs(ref), (ref, rhs)
 
 
+def test_colour_gradient_equals_the_oracle_vjp(orc):
+    """grad_col element by element against the oracle's J^T g (its Jacobian
+    in the colour image by definition, FP64: oracle.post_colour_vjp).  Both
+    sides take the same seeded mask (left half untraced, 1-8 rays elsewhere)
+    and trace their own hit records of the same room at the target lens."""
+    W, Hh = 32, 24
+    col, z = hi.diff_inputs(W, Hh, 3)
+    scene = hi.room_scene_target(3, 100_000, aspect=W / Hh)
+    cam = hi.Camera(width=W, height=Hh).f32()
+    target = hi.Lens(2.5, 0.04, 0.05).f32()
+    p = hi.room_params(r_max=32.0, camera_moved=0)
+    rng = np.random.default_rng(11)
+    spp = rng.integers(1, 9, (Hh, W)).astype(np.uint8)
+    spp[:, : W // 2] = 0
+    hs = hi.random_hist_samples(W, Hh, 3)
+    g = rng.normal(size=(Hh, W, 3))
+    zf, A = 2.2, 0.035
+    # GPU: the mask's hit records, then forward and adjoint
+    bvh = bvh_of(scene)
+    r = H.Renderer(bvh, W, Hh, p)
+    spp_d = torch.from_numpy(spp).cuda()
+    rec = torch.empty((int(spp.astype(np.int64).sum()), 4), dtype=torch.float32, device="cuda")
+    ray_off = torch.empty((Hh, W), dtype=torch.int32, device="cuda")
+    H.hdof_trace(bvh, cam, target, p, spp_d, r.rt, r.stats, r.ws, rec=rec, ray_off=ray_off)
+    H.hdof_sync()
+    path = H.PostPath(torch.from_numpy(z).cuda(), spp_d, rec, ray_off, torch.from_numpy(hs).cuda(), cam, p)
+    path.forward(torch.from_numpy(col).cuda(), zf, A)
+    gcol, _ = path.backward(torch.from_numpy(g.astype(np.float32)).cuda(), zf, A)
+    H.hdof_sync()
+    gcol = host(gcol)
+    # oracle: its own records of the same rays, its Jacobian by definition
+    osc = orc.OScene(scene)
+    orec, ooff = orc.trace_records(osc, cam, target, p, spp)
+    ref = orc.post_colour_vjp(col.astype(np.float64), z.astype(np.float64), spp, orec, ooff,
+                              hs.astype(np.float64), cam, hi.Lens(zf, A, 0.05).f32(), p,
+                              g.astype(np.float32).astype(np.float64))
+    scale = float(np.abs(ref).max())
+    ok = np.abs(gcol - ref) <= 1e-4 * scale
+    assert ok.mean() >= 0.999, report("grad_col", gcol, ref)
+    assert np.abs(ref - g).max() > 1e-2 * scale  # blur: J is not the identity
+
+
 def _loss_gpu(path, C, Y, zf, A):
     return float((path.forward(C, zf, A).double() * Y.double()).sum())
 

@@ -552,3 +552,32 @@ def test_post_path_is_affine_in_colour(orc):
     np.testing.assert_allclose(lhs, rhs, atol=1e-12)
     # and not trivially: the colour does move the output
     assert np.abs(f(c1) - f(c2)).max() > 0.1
+
+
+def test_post_colour_vjp_at_zero_aperture_is_g(orc):
+    """A = 0: the post-path is the identity in the colour image (the pin
+    above), so the oracle's VJP returns g itself."""
+    osc, cam, lens, p, spp, rec, off, col, z, hs = _post_setup(orc, W=16, Hh=12)
+    g = np.random.default_rng(4).normal(size=col.shape)
+    v = orc.post_colour_vjp(col, z, spp, rec, off, hs, cam, hi.Lens(2.5, 0.0, 0.05), p, g)
+    np.testing.assert_allclose(v, g, atol=1e-12)
+
+
+def test_post_colour_vjp_is_the_adjoint_of_the_forward(orc):
+    """<J x, y> = <x, J^T y>: J x from two forward maps (the map is affine),
+    J^T y from the oracle's VJP; x and y random on every channel (a weight
+    that mixed channels would break the identity), with traced pixels and
+    blur in the frame (J is not the identity)."""
+    osc, cam, lens, p, spp, rec, off, col, z, hs = _post_setup(orc, W=16, Hh=12)
+    spp = spp.copy()
+    spp[:, :8] = 0  # the left half untraced: both composite branches
+    rec, off = orc.trace_records(osc, cam, lens, p, spp)
+    assert (spp > 0).any() and (spp == 0).any()
+    rng = np.random.default_rng(5)
+    x, y = rng.normal(size=col.shape), rng.normal(size=col.shape)
+    f = lambda c: orc.post_forward(c, z, spp, rec, off, hs, cam, lens, p)["out"][..., :3]  # noqa: E731
+    jx = f(col + x) - f(col)
+    v = orc.post_colour_vjp(col, z, spp, rec, off, hs, cam, lens, p, y)
+    lhs, rhs = float((jx * y).sum()), float((x * v).sum())
+    assert abs(lhs - rhs) <= 1e-9 * max(abs(lhs), 1.0), (lhs, rhs)
+    assert np.abs(v - y).max() > 1e-2
