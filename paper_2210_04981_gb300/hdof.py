@@ -619,7 +619,7 @@ class Batch:
         self.bvhs = list(bvhs)
         self.params = list(ps)
         self.views = [Renderer(b, w, h, p, device) for b, (w, h), p in zip(self.bvhs, sizes, ps)]
-        self.tune = tune if tune is not None else tuning()
+        self.tune = tune if tune is not None else tuning(trace_refill=-1)  # each view's trace in its default form
         self.handle = None
 
     def __len__(self):
